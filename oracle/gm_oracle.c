@@ -1,0 +1,605 @@
+/*
+ * gm_oracle.c -- plain, slow FP64 CPU reference for batched galaxy-profile
+ * fitting (arxiv 2404.07780, "galmoss").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this file.  It shares no code, no
+ * header and no constant table with the CUDA library; it is written straight
+ * from the paper's definitions, in double precision, one pixel at a time:
+ *
+ *   light profiles at pixel centres ........ Sec. 4.1-4.2, Eqs. (r), (rmaj),
+ *        (rmin), (sersic-intensity), (expdisk_I), (ferrer_I), (BE_S),
+ *        (gaussion_I), (moffat_I), (sky_I)
+ *   sum of PSF-convolved components, direct zero-padded correlation with
+ *        the PSF, then the unconvolved components (the flat sky) ......
+ *        Sec. 2 (workflow) and the conv2d(..., padding="same") call of App. C
+ *   masked sigma-weighted chi^2 ............ Sec. 5.1, Eq. (chinu)
+ *   Jacobian by central finite differences . (no analytic derivative here)
+ *   Levenberg-Marquardt damped Gauss-Newton  Sec. 5.1 names LM as the
+ *        classical alternative; the damping/acceptance rules are spelled out
+ *        at or_fit_one() below
+ *   covariance uncertainty ................. Sec. 5.2,
+ *        sigma_p = sqrt(diag[(J^T W J)^-1]), W = 1/sigma^2
+ *
+ * Readings of points the paper leaves open (all listed in the design notes):
+ *   - pixel centres x_j = j + 0.5, y_i = H - 0.5 - i (row 0 at the top), as in
+ *     the grid built by the App. C listing;
+ *   - PSF application is a cross-correlation, M[i,j] = sum_ab P[a,b] *
+ *     I[i+a-c, j+b-c], zero outside the stamp, K odd, c = (K-1)/2 (torch
+ *     conv2d semantics);
+ *   - the elliptical radius (B = 0) is r = sqrt(X^2 + (Y/q)^2) with
+ *     X =  cos(pa) dx + sin(pa) dy, Y = -sin(pa) dx + cos(pa) dy;
+ *   - r is floored at 1e-4 px (the Sersic cusp);
+ *   - the King bracket is read as [A(r) - A(r_t)] so that I(0) = I0, and both
+ *     King and Ferrer are zero beyond their truncation radius;
+ *   - Gaussian FWHM = 2 sqrt(2 ln 2) sigma;
+ *   - mask: nonzero = excluded pixel.
+ *
+ * Parameter order of each component (geometric subset p_G first, then the
+ * radial subset p_L, following the split of Sec. 2):
+ *   SERSIC   x0 y0 q pa Ie Re n
+ *   EXPDISK  x0 y0 q pa I0 rs
+ *   FERRER   x0 y0 q pa I0 rout a b
+ *   KING     x0 y0 q pa I0 rc rt alpha
+ *   GAUSSIAN x0 y0 q pa I0 fwhm
+ *   MOFFAT   x0 y0 q pa I0 fwhm n
+ *   SKY      Isky
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_SERSIC 1
+#define OR_EXPDISK 2
+#define OR_FERRER 3
+#define OR_KING 4
+#define OR_GAUSSIAN 5
+#define OR_MOFFAT 6
+#define OR_SKY 7
+
+#define OR_MAX_COMP 8
+#define OR_MAX_SLOTS 16
+#define OR_RFLOOR 1e-4
+
+/* per-galaxy fit status */
+#define OR_RUNNING 0
+#define OR_CONVERGED 1
+#define OR_MAX_ITER 2
+#define OR_STALLED 3
+#define OR_SINGULAR 4
+#define OR_NONFINITE 5
+#define OR_BAD_INPUT 6
+#define OR_NO_DOF 7
+
+typedef struct {
+  int n_comp;
+  int kind[OR_MAX_COMP];
+  int convolve[OR_MAX_COMP];
+  int slot[OR_MAX_COMP][8];
+  int n_slots;
+  int is_free[OR_MAX_SLOTS];
+  int is_log[OR_MAX_SLOTS];
+  double lo[OR_MAX_SLOTS];
+  double hi[OR_MAX_SLOTS];
+} or_desc;
+
+typedef struct {
+  double tol;        /* relative chi^2 decrease that ends the fit */
+  double xtol;       /* relative step size that ends the fit */
+  int max_iter;      /* model+Jacobian evaluations allowed */
+  double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
+} or_opts;
+
+int or_n_params(int kind) {
+  switch (kind) {
+    case OR_SERSIC: return 7;
+    case OR_EXPDISK: return 6;
+    case OR_FERRER: return 8;
+    case OR_KING: return 8;
+    case OR_GAUSSIAN: return 6;
+    case OR_MOFFAT: return 7;
+    case OR_SKY: return 1;
+    default: return -1;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Regularised lower incomplete gamma P(a, x) = gamma(a, x) / Gamma(a).       */
+/* Power series for x < a + 1, Legendre continued fraction for Gamma(a, x)    */
+/* (evaluated with the modified Lentz method) otherwise.                      */
+/* ------------------------------------------------------------------------ */
+double or_gammp(double a, double x) {
+  if (!(a > 0.0) || x < 0.0) return NAN;
+  if (x == 0.0) return 0.0;
+  if (x < a + 1.0) {
+    /* P = x^a e^-x / Gamma(a+1) * sum_k x^k / ((a+1)...(a+k)) */
+    double term = 1.0, sum = 1.0, ap = a;
+    for (int k = 1; k < 100000; ++k) {
+      ap += 1.0;
+      term *= x / ap;
+      sum += term;
+      if (fabs(term) < fabs(sum) * 1e-17) break;
+    }
+    return sum * exp(-x + a * log(x) - lgamma(a + 1.0));
+  }
+  /* Q = x^a e^-x / Gamma(a) * 1/(x+1-a- 1(1-a)/(x+3-a- 2(2-a)/(x+5-a- ...))) */
+  const double tiny = 1e-300;
+  double b = x + 1.0 - a;
+  double c = 1.0 / tiny;
+  double d = 1.0 / b;
+  double h = d;
+  for (int i = 1; i < 100000; ++i) {
+    double an = -i * (i - a);
+    b += 2.0;
+    d = an * d + b;
+    if (fabs(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    d = 1.0 / d;
+    double del = d * c;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-17) break;
+  }
+  double q = exp(-x + a * log(x) - lgamma(a)) * h;
+  return 1.0 - q;
+}
+
+/* nu_n of Eq. (sersic-intensity): the half-light condition P(2n, nu) = 1/2,
+ * solved by plain bisection (P is increasing in x; the median of a
+ * Gamma(2n) variable lies below its mean 2n). */
+double or_sersic_b(double n) {
+  double a = 2.0 * n;
+  double lo = 0.0, hi = a;
+  while (or_gammp(a, hi) < 0.5) hi *= 2.0; /* never taken for a > 0, kept as a guard */
+  for (int it = 0; it < 400; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (or_gammp(a, mid) < 0.5) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* Elliptical radius of Eqs. (r)-(rmin) with B = 0, floored at OR_RFLOOR. */
+static double or_radius(double x, double y, double x0, double y0, double q, double pa) {
+  double dx = x - x0, dy = y - y0;
+  double X = cos(pa) * dx + sin(pa) * dy;
+  double Y = -sin(pa) * dx + cos(pa) * dy;
+  double r = sqrt(X * X + (Y / q) * (Y / q));
+  return r < OR_RFLOOR ? OR_RFLOOR : r;
+}
+
+/* Intensity of one component at the point (x, y); par in the order above.
+ * nu is nu_n of the Sersic index (or_sersic_b(par[6])) for a Sersic
+ * component and ignored otherwise. */
+double or_component_value(int kind, const double *par, double nu, double x, double y) {
+  if (kind == OR_SKY) return par[0]; /* Eq. (sky_I) */
+  double r = or_radius(x, y, par[0], par[1], par[2], par[3]);
+  switch (kind) {
+    case OR_SERSIC: { /* Eq. (sersic-intensity) */
+      double Ie = par[4], Re = par[5], n = par[6];
+      return Ie * exp(-nu * (pow(r / Re, 1.0 / n) - 1.0));
+    }
+    case OR_EXPDISK: { /* Eq. (expdisk_I) */
+      double I0 = par[4], rs = par[5];
+      return I0 * exp(-r / rs);
+    }
+    case OR_FERRER: { /* Eq. (ferrer_I), zero beyond r_out */
+      double I0 = par[4], rout = par[5], a = par[6], b = par[7];
+      if (r >= rout) return 0.0;
+      return I0 * pow(1.0 - pow(r / rout, 2.0 - b), a);
+    }
+    case OR_KING: { /* Eq. (BE_S), bracket read so that I(0) = I0 */
+      double I0 = par[4], rc = par[5], rt = par[6], al = par[7];
+      if (r >= rt) return 0.0;
+      double At = pow(1.0 + (rt / rc) * (rt / rc), -1.0 / al);
+      double Ar = pow(1.0 + (r / rc) * (r / rc), -1.0 / al);
+      return I0 * pow(1.0 - At, -al) * pow(Ar - At, al);
+    }
+    case OR_GAUSSIAN: { /* Eq. (gaussion_I), FWHM = 2 sqrt(2 ln 2) sigma */
+      double I0 = par[4], fwhm = par[5];
+      double sig = fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+      return I0 * exp(-r * r / (2.0 * sig * sig));
+    }
+    case OR_MOFFAT: { /* Eqs. (moffat_I), (moffat_rd) */
+      double I0 = par[4], fwhm = par[5], n = par[6];
+      double rd = fwhm / (2.0 * sqrt(pow(2.0, 1.0 / n) - 1.0));
+      return I0 * pow(1.0 + (r / rd) * (r / rd), -n);
+    }
+    default: return NAN;
+  }
+}
+
+static void or_gather(const or_desc *d, int c, const double *p, double *par) {
+  int np = or_n_params(d->kind[c]);
+  for (int k = 0; k < np; ++k) par[k] = p[d->slot[c][k]];
+}
+
+/* Image of one component on the H x W stamp (no PSF). */
+void or_component_image(int kind, const double *par, int H, int W, double *out) {
+  double nu = (kind == OR_SERSIC) ? or_sersic_b(par[6]) : 0.0;
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j)
+      out[(size_t)i * W + j] = or_component_value(kind, par, nu, j + 0.5, H - 0.5 - i);
+}
+
+/* Direct zero-padded cross-correlation with a K x K PSF, same-size output. */
+void or_correlate(const double *img, int H, int W, const double *psf, int K, double *out) {
+  int c = (K - 1) / 2;
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j) {
+      double s = 0.0;
+      for (int a = 0; a < K; ++a) {
+        int ii = i + a - c;
+        if (ii < 0 || ii >= H) continue;
+        for (int b = 0; b < K; ++b) {
+          int jj = j + b - c;
+          if (jj < 0 || jj >= W) continue;
+          s += psf[a * K + b] * img[(size_t)ii * W + jj];
+        }
+      }
+      out[(size_t)i * W + j] = s;
+    }
+}
+
+/* Full model of one galaxy: correlated sum of the convolved components plus
+ * the unconvolved ones.  work must hold 2*H*W doubles. */
+void or_model_one(const or_desc *d, const double *p, int H, int W, const double *psf, int K,
+                  double *model, double *work) {
+  size_t N = (size_t)H * W;
+  double *conv = work, *comp = work + N;
+  double par[8];
+  int any_conv = 0;
+  for (size_t t = 0; t < N; ++t) { conv[t] = 0.0; model[t] = 0.0; }
+  for (int c = 0; c < d->n_comp; ++c) {
+    or_gather(d, c, p, par);
+    or_component_image(d->kind[c], par, H, W, comp);
+    double *dst = d->convolve[c] ? conv : model;
+    if (d->convolve[c]) any_conv = 1;
+    for (size_t t = 0; t < N; ++t) dst[t] += comp[t];
+  }
+  if (any_conv) {
+    /* model currently holds the unconvolved part; add the correlated part */
+    or_correlate(conv, H, W, psf, K, comp);
+    for (size_t t = 0; t < N; ++t) model[t] += comp[t];
+  }
+}
+
+/* Eq. (chinu): chi^2 = sum Omega (D - M)^2 / sigma^2, Omega = (mask == 0). */
+double or_chi2_one(const double *model, const double *image, const double *sigma,
+                   const unsigned char *mask, size_t N) {
+  double s = 0.0;
+  for (size_t t = 0; t < N; ++t) {
+    if (mask && mask[t]) continue;
+    double r = image[t] - model[t];
+    s += r * r / (sigma[t] * sigma[t]);
+  }
+  return s;
+}
+
+/* Internal (fitted) coordinate of a slot: ln p for log slots, p otherwise. */
+static double or_to_u(const or_desc *d, int s, double p) { return d->is_log[s] ? log(p) : p; }
+static double or_from_u(const or_desc *d, int s, double u) { return d->is_log[s] ? exp(u) : u; }
+
+/* Central-difference Jacobian dM/du_s for every free slot s (in slot order),
+ * u the internal coordinate when `internal` is set, else the physical one.
+ * J is [n_free][H*W].  work must hold 4*H*W doubles. */
+void or_jacobian_one(const or_desc *d, const double *p, int H, int W, const double *psf, int K,
+                     int internal, double *J, double *work) {
+  size_t N = (size_t)H * W;
+  double pp[OR_MAX_SLOTS];
+  double *mp = work, *mm = work + N, *w2 = work + 2 * N;
+  int f = 0;
+  for (int s = 0; s < d->n_slots; ++s) {
+    if (!d->is_free[s]) continue;
+    int lg = internal && d->is_log[s];
+    double u = lg ? log(p[s]) : p[s];
+    double h = lg ? 1e-6 : 1e-6 * fmax(fabs(u), 1.0);
+    memcpy(pp, p, sizeof(double) * d->n_slots);
+    pp[s] = lg ? exp(u + h) : u + h;
+    or_model_one(d, pp, H, W, psf, K, mp, w2);
+    pp[s] = lg ? exp(u - h) : u - h;
+    or_model_one(d, pp, H, W, psf, K, mm, w2);
+    for (size_t t = 0; t < N; ++t) J[(size_t)f * N + t] = (mp[t] - mm[t]) / (2.0 * h);
+    ++f;
+  }
+}
+
+/* Cholesky factorisation in place (lower triangle), n x n row-major.
+ * Returns 0 on success, -1 if the matrix is not positive definite. */
+static int or_cholesky(double *A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+    if (!(s > 0.0)) return -1;
+    double l = sqrt(s);
+    A[j * n + j] = l;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = t / l;
+    }
+  }
+  return 0;
+}
+
+/* Solve L L^T x = b with the factor from or_cholesky. */
+static void or_chol_solve(const double *L, int n, const double *b, double *x) {
+  double y[OR_MAX_SLOTS];
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+}
+
+/* Gauss-Newton normal equations at p: chi^2, A = J^T W J, g = J^T W r with
+ * r = D - M and J taken in internal coordinates.  Returns chi^2. */
+static double or_normal_eq(const or_desc *d, const double *p, int H, int W, const double *psf, int K,
+                           const double *image, const double *sigma, const unsigned char *mask,
+                           int nf, double *A, double *g, double *J, double *model, double *work) {
+  size_t N = (size_t)H * W;
+  or_model_one(d, p, H, W, psf, K, model, work);
+  double chi2 = or_chi2_one(model, image, sigma, mask, N);
+  or_jacobian_one(d, p, H, W, psf, K, 1, J, work);
+  for (int a = 0; a < nf; ++a) {
+    g[a] = 0.0;
+    for (int b = 0; b < nf; ++b) A[a * nf + b] = 0.0;
+  }
+  for (size_t t = 0; t < N; ++t) {
+    if (mask && mask[t]) continue;
+    double w = 1.0 / (sigma[t] * sigma[t]);
+    double r = image[t] - model[t];
+    for (int a = 0; a < nf; ++a) {
+      double ja = J[(size_t)a * N + t];
+      g[a] += w * ja * r;
+      for (int b = 0; b < nf; ++b) A[a * nf + b] += w * ja * J[(size_t)b * N + t];
+    }
+  }
+  return chi2;
+}
+
+static void or_clamp(const or_desc *d, double *p) {
+  for (int s = 0; s < d->n_slots; ++s) {
+    if (p[s] < d->lo[s]) p[s] = d->lo[s];
+    if (p[s] > d->hi[s]) p[s] = d->hi[s];
+  }
+}
+
+/* Slots that some radial component uses as its position angle. */
+static void or_pa_slots(const or_desc *d, int *is_pa) {
+  for (int s = 0; s < OR_MAX_SLOTS; ++s) is_pa[s] = 0;
+  for (int c = 0; c < d->n_comp; ++c)
+    if (d->kind[c] != OR_SKY) is_pa[d->slot[c][3]] = 1;
+}
+
+/*
+ * Levenberg-Marquardt fit of one galaxy, in internal coordinates u.
+ *   1. Evaluate chi^2, A, g at the (clamped) start; this is iteration 1.
+ *   2. Damped step: solve (A + lambda diag(A)) delta = g by Cholesky, the
+ *      diagonal floored at 1e-12 max(diag A); a failed factorisation
+ *      multiplies lambda by lambda_up and retries (SINGULAR past lambda_max).
+ *   3. Trial p' = clamp(from_u(u + delta)); evaluate it (one iteration).
+ *   4. The step is "small" when every internal step satisfies
+ *      |u'_s - u_s| <= xtol (|u_s| + xtol).
+ *      chi^2' < chi^2: accept, lambda = max(lambda*lambda_down, lambda_min);
+ *      CONVERGED if (chi^2 - chi^2')/chi^2 < tol or the step was small.
+ *      Otherwise reject: CONVERGED at the kept point if the step was small,
+ *      else lambda *= lambda_up and STALLED past lambda_max.
+ *   5. MAX_ITER once max_iter evaluations have been spent.
+ * The covariance of Sec. 5.2 is taken from A at the best point; for a log
+ * slot sigma_p = p sigma_u.  Position angles are wrapped to [0, pi) at exit.
+ */
+static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int W,
+                       const double *psf, int K, const double *image, const double *sigma,
+                       const unsigned char *mask, double *chi2_out, int *dof_out, int *iters_out,
+                       int *status_out, double *sigma_p) {
+  size_t N = (size_t)H * W;
+  int nf = 0, fidx[OR_MAX_SLOTS];
+  for (int s = 0; s < d->n_slots; ++s)
+    if (d->is_free[s]) fidx[nf++] = s;
+  long nused = 0;
+  int bad = 0;
+  for (size_t t = 0; t < N; ++t) {
+    if (mask && mask[t]) continue;
+    ++nused;
+    if (!(sigma[t] > 0.0) || !isfinite(sigma[t]) || !isfinite(image[t])) bad = 1;
+  }
+  *dof_out = (int)(nused - nf);
+  *iters_out = 0;
+  *chi2_out = NAN;
+  if (sigma_p)
+    for (int s = 0; s < d->n_slots; ++s) sigma_p[s] = 0.0;
+  if (bad) { *status_out = OR_BAD_INPUT; return; }
+  if (nused - nf <= 0) { *status_out = OR_NO_DOF; return; }
+
+  double *J = malloc(sizeof(double) * nf * N);
+  double *model = malloc(sizeof(double) * N);
+  double *work = malloc(sizeof(double) * 4 * N);
+  double A[OR_MAX_SLOTS * OR_MAX_SLOTS], g[OR_MAX_SLOTS];
+  double At[OR_MAX_SLOTS * OR_MAX_SLOTS], gt[OR_MAX_SLOTS];
+  double M[OR_MAX_SLOTS * OR_MAX_SLOTS], delta[OR_MAX_SLOTS];
+  double pt[OR_MAX_SLOTS];
+
+  or_clamp(d, p);
+  double chi2 = or_normal_eq(d, p, H, W, psf, K, image, sigma, mask, nf, A, g, J, model, work);
+  int it = 1;
+  int status = OR_RUNNING;
+  double lambda = o->lambda0;
+  if (!isfinite(chi2)) status = OR_NONFINITE;
+  else if (chi2 == 0.0) status = OR_CONVERGED;
+
+  while (status == OR_RUNNING) {
+    if (it >= o->max_iter) { status = OR_MAX_ITER; break; }
+    double dmax = 0.0;
+    for (int a = 0; a < nf; ++a) dmax = fmax(dmax, A[a * nf + a]);
+    double dfloor = 1e-12 * dmax;
+    for (;;) {
+      for (int a = 0; a < nf; ++a)
+        for (int b = 0; b < nf; ++b) M[a * nf + b] = A[a * nf + b];
+      for (int a = 0; a < nf; ++a) M[a * nf + a] += lambda * fmax(A[a * nf + a], dfloor);
+      if (or_cholesky(M, nf) == 0) break;
+      lambda *= o->lambda_up;
+      if (lambda > o->lambda_max) { status = OR_SINGULAR; break; }
+    }
+    if (status != OR_RUNNING) break;
+    or_chol_solve(M, nf, g, delta);
+    memcpy(pt, p, sizeof(double) * d->n_slots);
+    for (int a = 0; a < nf; ++a) {
+      int s = fidx[a];
+      pt[s] = or_from_u(d, s, or_to_u(d, s, p[s]) + delta[a]);
+    }
+    or_clamp(d, pt);
+    double chi2t = or_normal_eq(d, pt, H, W, psf, K, image, sigma, mask, nf, At, gt, J, model, work);
+    ++it;
+    int small = 1;
+    for (int a = 0; a < nf; ++a) {
+      int s = fidx[a];
+      double u0 = or_to_u(d, s, p[s]), u1 = or_to_u(d, s, pt[s]);
+      if (fabs(u1 - u0) > o->xtol * (fabs(u0) + o->xtol)) small = 0;
+    }
+    if (isfinite(chi2t) && chi2t < chi2) {
+      double act = (chi2 - chi2t) / chi2;
+      memcpy(p, pt, sizeof(double) * d->n_slots);
+      memcpy(A, At, sizeof(double) * nf * nf);
+      memcpy(g, gt, sizeof(double) * nf);
+      chi2 = chi2t;
+      lambda = fmax(lambda * o->lambda_down, o->lambda_min);
+      if (act < o->tol || small || chi2 == 0.0) status = OR_CONVERGED;
+    } else if (small) {
+      status = OR_CONVERGED; /* the damped step is below resolution: nothing left to gain */
+    } else {
+      lambda *= o->lambda_up;
+      if (lambda > o->lambda_max) status = OR_STALLED;
+    }
+  }
+
+  *chi2_out = chi2;
+  *iters_out = it;
+  *status_out = status;
+  if (sigma_p && status != OR_NONFINITE) {
+    /* covariance: diag of A^-1 column by column through the Cholesky factor */
+    memcpy(M, A, sizeof(double) * nf * nf);
+    if (or_cholesky(M, nf) == 0) {
+      for (int a = 0; a < nf; ++a) {
+        double e[OR_MAX_SLOTS], x[OR_MAX_SLOTS];
+        for (int b = 0; b < nf; ++b) e[b] = (a == b) ? 1.0 : 0.0;
+        or_chol_solve(M, nf, e, x);
+        int s = fidx[a];
+        double su = sqrt(x[a]);
+        sigma_p[s] = d->is_log[s] ? p[s] * su : su;
+      }
+    } else {
+      for (int a = 0; a < nf; ++a) sigma_p[fidx[a]] = NAN;
+    }
+  }
+  int is_pa[OR_MAX_SLOTS];
+  or_pa_slots(d, is_pa);
+  for (int s = 0; s < d->n_slots; ++s)
+    if (is_pa[s]) p[s] -= M_PI * floor(p[s] / M_PI);
+  free(J);
+  free(model);
+  free(work);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Batch entry points (equal-size stamps; galaxies are independent).          */
+/* ------------------------------------------------------------------------ */
+
+int or_model_batch(const or_desc *d, int G, int H, int W, int K, const double *params,
+                   const double *psf, double *model) {
+  size_t N = (size_t)H * W;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int gi = 0; gi < G; ++gi) {
+    double *work = malloc(sizeof(double) * 2 * N);
+    or_model_one(d, params + (size_t)gi * d->n_slots, H, W, psf + (size_t)gi * K * K, K,
+                 model + (size_t)gi * N, work);
+    free(work);
+  }
+  return 0;
+}
+
+int or_component_images_batch(const or_desc *d, int G, int H, int W, int K, const double *params,
+                              const double *psf, double *comp) {
+  /* Each component's own contribution to the model: correlated with the PSF
+   * when the component is convolved.  comp is [G][n_comp][H*W]. */
+  size_t N = (size_t)H * W;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int gi = 0; gi < G; ++gi) {
+    double *tmp = malloc(sizeof(double) * N);
+    double par[8];
+    const double *p = params + (size_t)gi * d->n_slots;
+    for (int c = 0; c < d->n_comp; ++c) {
+      double *dst = comp + ((size_t)gi * d->n_comp + c) * N;
+      or_gather(d, c, p, par);
+      if (d->convolve[c]) {
+        or_component_image(d->kind[c], par, H, W, tmp);
+        or_correlate(tmp, H, W, psf + (size_t)gi * K * K, K, dst);
+      } else {
+        or_component_image(d->kind[c], par, H, W, dst);
+      }
+    }
+    free(tmp);
+  }
+  return 0;
+}
+
+int or_chi2_batch(const or_desc *d, int G, int H, int W, int K, const double *params,
+                  const double *psf, const double *image, const double *sigma,
+                  const unsigned char *mask, double *chi2) {
+  size_t N = (size_t)H * W;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int gi = 0; gi < G; ++gi) {
+    double *model = malloc(sizeof(double) * N);
+    double *work = malloc(sizeof(double) * 2 * N);
+    or_model_one(d, params + (size_t)gi * d->n_slots, H, W, psf + (size_t)gi * K * K, K, model, work);
+    chi2[gi] = or_chi2_one(model, image + (size_t)gi * N, sigma + (size_t)gi * N,
+                           mask ? mask + (size_t)gi * N : NULL, N);
+    free(model);
+    free(work);
+  }
+  return 0;
+}
+
+int or_jacobian_batch(const or_desc *d, int G, int H, int W, int K, const double *params,
+                      const double *psf, int internal, double *J) {
+  size_t N = (size_t)H * W;
+  int nf = 0;
+  for (int s = 0; s < d->n_slots; ++s) nf += d->is_free[s] ? 1 : 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int gi = 0; gi < G; ++gi) {
+    double *work = malloc(sizeof(double) * 4 * N);
+    or_jacobian_one(d, params + (size_t)gi * d->n_slots, H, W, psf + (size_t)gi * K * K, K, internal,
+                    J + (size_t)gi * nf * N, work);
+    free(work);
+  }
+  return 0;
+}
+
+int or_fit_batch(const or_desc *d, const or_opts *o, int G, int H, int W, int K, double *params,
+                 const double *psf, const double *image, const double *sigma,
+                 const unsigned char *mask, double *chi2, int *dof, int *iters, int *status,
+                 double *sigma_p) {
+  size_t N = (size_t)H * W;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int gi = 0; gi < G; ++gi) {
+    or_fit_one(d, o, params + (size_t)gi * d->n_slots, H, W, psf + (size_t)gi * K * K, K,
+               image + (size_t)gi * N, sigma + (size_t)gi * N, mask ? mask + (size_t)gi * N : NULL,
+               chi2 + gi, dof + gi, iters + gi, status + gi,
+               sigma_p ? sigma_p + (size_t)gi * d->n_slots : NULL);
+  }
+  return 0;
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+  extern int omp_get_max_threads(void);
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

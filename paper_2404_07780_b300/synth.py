@@ -1,0 +1,274 @@
+"""Seeded synthetic inputs for batched galaxy-profile fitting.
+
+This module holds configuration and random draws only: model descriptions
+(which component uses which parameter slot), parameter draws from the stated
+prior ranges, PSF and contaminant *descriptions*, mask geometry and the
+Gaussian noise draws.  It evaluates no light profile, no convolution and no
+chi^2; whoever consumes these inputs renders the images with its own forward
+model (the CUDA library for benchmark workloads, the FP64 oracle for test
+cases), so that the library and the oracle share nothing but these draws.
+
+The SDSS g-band sample of the paper (Sec. 3: 128x128 stamps, 41x41 PSFs,
+SExtractor masks) is not available; the draws below take its shapes and
+stand in for it.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Parameter order of each component kind: the geometric subset p_G (centre,
+# axis ratio, position angle) first, then the radial subset p_L (Sec. 2).
+PARAM_NAMES = {
+    "sersic": ("x0", "y0", "q", "pa", "Ie", "Re", "n"),
+    "expdisk": ("x0", "y0", "q", "pa", "I0", "rs"),
+    "ferrer": ("x0", "y0", "q", "pa", "I0", "rout", "a", "b"),
+    "king": ("x0", "y0", "q", "pa", "I0", "rc", "rt", "alpha"),
+    "gaussian": ("x0", "y0", "q", "pa", "I0", "fwhm"),
+    "moffat": ("x0", "y0", "q", "pa", "I0", "fwhm", "n"),
+    "sky": ("Isky",),
+}
+
+# Fitted in log space (positive scale and amplitude parameters) and default
+# bounds, by parameter role.
+_LOG_ROLES = {"Ie", "I0", "Re", "rs", "rout", "rc", "rt", "fwhm", "n", "alpha", "a"}
+_BIG = 1e30
+
+
+def _default_bounds(kind: str, role: str, H: int, W: int) -> tuple[float, float]:
+    if role == "x0":
+        return 0.0, float(W)
+    if role == "y0":
+        return 0.0, float(H)
+    if role == "q":
+        return 0.05, 1.0
+    if role == "pa":
+        return -_BIG, _BIG
+    if role in ("Ie", "I0"):
+        return 1e-8, 1e8
+    if role in ("Re", "rs", "rout", "rc", "rt", "fwhm"):
+        return 1e-2, 1e3
+    if role == "n":
+        return (0.2, 10.0) if kind == "sersic" else (1.01, 100.0)
+    if role == "alpha":
+        return 0.1, 10.0
+    if role == "a":
+        return 0.05, 20.0
+    if role == "b":
+        return -5.0, 1.99
+    return -_BIG, _BIG
+
+
+@dataclass
+class Component:
+    kind: str
+    convolve: bool
+    slots: list[int]
+
+
+@dataclass
+class ModelSpec:
+    """Which components make up the model and how they map onto parameter slots.
+
+    A slot shared by several components (for example a common centre) is one
+    fitted parameter.  free/log/lo/hi are per slot."""
+    components: list[Component] = field(default_factory=list)
+    names: list[str] = field(default_factory=list)
+    free: list[bool] = field(default_factory=list)
+    log: list[bool] = field(default_factory=list)
+    lo: list[float] = field(default_factory=list)
+    hi: list[float] = field(default_factory=list)
+
+    @property
+    def n_slots(self) -> int:
+        return len(self.names)
+
+    @property
+    def n_free(self) -> int:
+        return int(sum(self.free))
+
+    def slot(self, name: str) -> int:
+        return self.names.index(name)
+
+    def add(self, kind: str, prefix: str, H: int, W: int, convolve: bool = True,
+            shared: dict[str, int] | None = None, fixed: tuple[str, ...] = ()) -> "ModelSpec":
+        """Append a component; roles in `shared` reuse an existing slot."""
+        shared = shared or {}
+        slots = []
+        for role in PARAM_NAMES[kind]:
+            if role in shared:
+                slots.append(shared[role])
+                continue
+            lo, hi = _default_bounds(kind, role, H, W)
+            self.names.append(f"{prefix}.{role}")
+            self.free.append(role not in fixed)
+            self.log.append(role in _LOG_ROLES)
+            self.lo.append(lo)
+            self.hi.append(hi)
+            slots.append(len(self.names) - 1)
+        self.components.append(Component(kind, convolve, slots))
+        return self
+
+
+def single_sersic_sky(H: int, W: int) -> ModelSpec:
+    """One Sersic component (convolved) plus a flat sky (not convolved): 8 free slots."""
+    s = ModelSpec()
+    s.add("sersic", "bulge", H, W)
+    s.add("sky", "sky", H, W, convolve=False)
+    return s
+
+
+def bulge_disk_sky(H: int, W: int) -> ModelSpec:
+    """Sersic bulge + Sersic disk with n fixed at 1 sharing the centre, plus sky.
+
+    13 slots, 12 free (the bulge+disk recipe of App. B with a common centre)."""
+    s = ModelSpec()
+    s.add("sersic", "bulge", H, W)
+    s.add("sersic", "disk", H, W, shared={"x0": 0, "y0": 1}, fixed=("n",))
+    s.add("sky", "sky", H, W, convolve=False)
+    return s
+
+
+def bulge_bar_nucleus_sky(H: int, W: int) -> ModelSpec:
+    """Sersic bulge + Ferrer bar (a fixed) + circular Gaussian nucleus + sky, common centre."""
+    s = ModelSpec()
+    s.add("sersic", "bulge", H, W)
+    s.add("ferrer", "bar", H, W, shared={"x0": 0, "y0": 1}, fixed=("a",))
+    s.add("gaussian", "nuc", H, W, shared={"x0": 0, "y0": 1}, fixed=("q", "pa"))
+    s.add("sky", "sky", H, W, convolve=False)
+    return s
+
+
+def with_contaminants(base: ModelSpec, n: int, H: int, W: int) -> ModelSpec:
+    """`base` plus n free-standing Gaussian sources (used to render truth scenes)."""
+    s = ModelSpec(components=[Component(c.kind, c.convolve, list(c.slots)) for c in base.components],
+                  names=list(base.names), free=list(base.free), log=list(base.log),
+                  lo=list(base.lo), hi=list(base.hi))
+    for k in range(n):
+        s.add("gaussian", f"cont{k}", H, W)
+    return s
+
+
+# --------------------------------------------------------------------------
+# Draws
+# --------------------------------------------------------------------------
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _logu(g: np.random.Generator, lo: float, hi: float, size) -> np.ndarray:
+    return np.exp(g.uniform(math.log(lo), math.log(hi), size))
+
+
+@dataclass
+class Batch:
+    """One synthetic batch of equal-size stamps (all arrays numpy, FP64 unless noted)."""
+    spec: ModelSpec            # the fitted model
+    truth_spec: ModelSpec      # the model used to render the truth scene
+    H: int
+    W: int
+    K: int
+    truth: np.ndarray          # [G, truth_spec.n_slots]
+    init: np.ndarray           # [G, spec.n_slots] default starting point
+    psf_kind: str              # "gaussian" or "moffat"
+    psf_par: np.ndarray        # [G, n] component parameters of the PSF profile
+    mask: np.ndarray | None    # [G, H, W] uint8, nonzero = excluded
+    z: np.ndarray              # [G, H, W] standard normal noise draws
+    sky_var: float = 4.0
+    gain: float = 4.0
+
+    @property
+    def G(self) -> int:
+        return self.truth.shape[0]
+
+
+def psf_params(kind: str, fwhm: np.ndarray, K: int, beta: float = 3.0) -> np.ndarray:
+    """Component parameters of a circular PSF profile centred on pixel (c, c) of a K x K grid."""
+    c = K / 2.0  # centre of pixel (c, c) is at x = y = c + 0.5 = K / 2
+    G = fwhm.shape[0]
+    if kind == "gaussian":
+        return np.stack([np.full(G, c), np.full(G, c), np.ones(G), np.zeros(G), np.ones(G), fwhm], 1)
+    return np.stack([np.full(G, c), np.full(G, c), np.ones(G), np.zeros(G), np.ones(G), fwhm,
+                     np.full(G, beta)], 1)
+
+
+def draw_small(seed: int = 0, G: int = 16, H: int = 64, W: int = 64, K: int = 15) -> Batch:
+    """Plain single-Sersic batch: 16 x 64x64, Gaussian PSF FWHM 1.5 px on 15x15, no mask.
+
+    x0, y0 within +-2 px of the centre; Ie log-uniform 1-100; Re uniform 2-10;
+    n log-uniform 0.5-4; q uniform 0.3-1; PA uniform 0-pi; sky uniform 0-5."""
+    g = rng(seed)
+    spec = single_sersic_sky(H, W)
+    truth = np.stack([
+        W / 2 + g.uniform(-2, 2, G), H / 2 + g.uniform(-2, 2, G), g.uniform(0.3, 1.0, G),
+        g.uniform(0, math.pi, G), _logu(g, 1, 100, G), g.uniform(2, 10, G), _logu(g, 0.5, 4, G),
+        g.uniform(0, 5, G)], 1)
+    init = np.tile(np.array([W / 2, H / 2, 0.65, math.pi / 2, 10.0, 6.0, math.sqrt(2.0), 2.5]), (G, 1))
+    z = g.standard_normal((G, H, W))
+    return Batch(spec, spec, H, W, K, truth, init, "gaussian", psf_params("gaussian", np.full(G, 1.5), K),
+                 None, z)
+
+
+def draw_sdss(seed: int = 1000, G: int = 8192, H: int = 128, W: int = 128, K: int = 41,
+              max_blobs: int = 5) -> Batch:
+    """SDSS-shaped single-Sersic batch with contaminants hidden under a mask.
+
+    Sersic + sky; n log-uniform 0.5-6; Re uniform 2-25 px; q uniform 0.2-1;
+    log10 Ie uniform 0-3; centre within +-2 px; PA uniform 0-pi; sky uniform
+    0-5.  Per-galaxy Moffat PSF, beta = 3, FWHM uniform 1.2-1.8 px, 41x41.
+    0-5 elliptical mask blobs per stamp (semi-axis 2-8 px, q 0.3-1, centre at
+    least 10 px from the galaxy), each hiding a Gaussian contaminant whose
+    peak is 5-50 sky sigma."""
+    g = rng(seed)
+    spec = single_sersic_sky(H, W)
+    tspec = with_contaminants(spec, max_blobs, H, W)
+    x0 = W / 2 + g.uniform(-2, 2, G)
+    y0 = H / 2 + g.uniform(-2, 2, G)
+    gal = np.stack([x0, y0, g.uniform(0.2, 1.0, G), g.uniform(0, math.pi, G),
+                    10 ** g.uniform(0, 3, G), g.uniform(2, 25, G), _logu(g, 0.5, 6, G),
+                    g.uniform(0, 5, G)], 1)
+    fwhm = g.uniform(1.2, 1.8, G)
+    nblob = g.integers(0, max_blobs + 1, G)
+    sig_sky = math.sqrt(4.0)
+    cont = np.zeros((G, max_blobs, 6))
+    mask = np.zeros((G, H, W), np.uint8)
+    yy, xx = np.meshgrid(H - 0.5 - np.arange(H), np.arange(W) + 0.5, indexing="ij")
+    for gi in range(G):
+        for k in range(max_blobs):
+            semi = g.uniform(2, 8)
+            bq = g.uniform(0.3, 1.0)
+            bpa = g.uniform(0, math.pi)
+            rad = g.uniform(10 + semi, 0.5 * min(H, W) - 2)
+            ang = g.uniform(0, 2 * math.pi)
+            cx, cy = x0[gi] + rad * math.cos(ang), y0[gi] + rad * math.sin(ang)
+            peak = g.uniform(5, 50) * sig_sky
+            if k >= nblob[gi]:
+                continue
+            # contaminant: Gaussian with 3 sigma = semi-axis, same shape as the blob
+            cont[gi, k] = [cx, cy, bq, bpa, peak, 2.0 * math.sqrt(2.0 * math.log(2.0)) * semi / 3.0]
+            dx, dy = xx - cx, yy - cy
+            X = math.cos(bpa) * dx + math.sin(bpa) * dy
+            Y = -math.sin(bpa) * dx + math.cos(bpa) * dy
+            mask[gi][(X / semi) ** 2 + (Y / (bq * semi)) ** 2 <= 1.0] = 1
+    # unused contaminant slots: zero amplitude, harmless geometry
+    unused = cont[:, :, 4] == 0
+    cont[unused] = [W / 2, H / 2, 1.0, 0.0, 0.0, 1.0]
+    truth = np.concatenate([gal, cont.reshape(G, -1)], 1)
+    init = np.tile(np.array([W / 2, H / 2, 0.6, math.pi / 2, math.sqrt(1000.0), 13.5, math.sqrt(3.0), 2.5]),
+                   (G, 1))
+    z = g.standard_normal((G, H, W), dtype=np.float32)
+    return Batch(spec, tspec, H, W, K, truth, init, "moffat", psf_params("moffat", fwhm, K), mask, z)
+
+
+def noisy_image(model_true: np.ndarray, z: np.ndarray, sky_var: float = 4.0, gain: float = 4.0):
+    """Data and sigma map for a truth image: sigma^2 = sky_var + max(M, 0)/gain, D = M + sigma z."""
+    sigma = np.sqrt(sky_var + np.maximum(model_true, 0.0) / gain)
+    return model_true + sigma * z, sigma
+
+
+def galaxy_slots(batch: Batch) -> np.ndarray:
+    """The truth parameters restricted to the fitted model's slots."""
+    return batch.truth[:, : batch.spec.n_slots]
