@@ -1,0 +1,216 @@
+/*
+ * gm.h -- C ABI of libgm: batched galaxy-profile fitting on one B300 (sm_103a).
+ *
+ * The library evaluates, for a whole batch of galaxy stamps at once, the
+ * forward model of arxiv 2404.07780 ("galmoss"): light profiles on the
+ * elliptical radius (Sec. 4.1-4.2: Eqs. r, rmaj, rmin with B = 0, and
+ * sersic-intensity, expdisk_I, ferrer_I, BE_S, gaussion_I, moffat_I, sky_I),
+ * summed, correlated with each galaxy's PSF (Sec. 2 workflow, App. C conv2d
+ * with padding="same"), plus the unconvolved components; the masked
+ * sigma-weighted chi^2 (Sec. 5.1, Eq. chinu); the analytic Jacobian reduced to
+ * per-galaxy J^T W J and J^T W r; and a batched Levenberg-Marquardt update
+ * with the covariance uncertainty of Sec. 5.2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.  Every array argument is a DEVICE pointer on the current CUDA
+ *   device unless its comment says "host".  The caller owns all memory; the
+ *   library allocates nothing.  Scratch memory is the caller's `workspace`,
+ *   sized by the matching *_workspace_bytes() query and 256-byte aligned.
+ * Stream.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  gm_model and gm_chi2_grad only enqueue work; their outputs are
+ *   valid once the stream has synchronised.  gm_fit_batch synchronises the
+ *   stream to poll convergence and returns when the fit has finished.
+ * Layout.  Stamps are row-major, H rows x W columns; the pixel in row i,
+ *   column j has centre x = j + 0.5, y = H - 0.5 - i (row 0 at the top, the
+ *   grid of the App. C listing).  Galaxy g's stamp starts at element
+ *   g*H*W, its PSF at g*K*K.  The PSF is applied as a cross-correlation,
+ *   M[i,j] = sum_ab P[a,b] I[i+a-c, j+b-c] with c = (K-1)/2 and I = 0 outside
+ *   the stamp (torch conv2d semantics); K must be odd; the PSF is used as
+ *   given (normalise it yourself).
+ * Mask.  uint8, nonzero = pixel excluded (Omega = 0 in Eq. chinu); NULL means
+ *   every pixel is used.
+ * Parameters.  params is [n_gal][n_slots] FP64 in physical units: pixels and
+ *   radians.  Each component reads its parameters from the slots listed in
+ *   gm_component.slot, in this order (geometric subset first, Sec. 2):
+ *     GM_SERSIC   x0 y0 q pa Ie Re n
+ *     GM_EXPDISK  x0 y0 q pa I0 rs
+ *     GM_FERRER   x0 y0 q pa I0 rout a b        (zero for r >= rout)
+ *     GM_KING     x0 y0 q pa I0 rc rt alpha     (zero for r >= rt; bracket read
+ *                                                 so that I(0) = I0)
+ *     GM_GAUSSIAN x0 y0 q pa I0 fwhm            (fwhm = 2 sqrt(2 ln 2) sigma)
+ *     GM_MOFFAT   x0 y0 q pa I0 fwhm n
+ *     GM_SKY      Isky                          (flat, Eq. sky_I)
+ *   The elliptical radius is r = sqrt(X^2 + (Y/q)^2), X = cos(pa) dx +
+ *   sin(pa) dy, Y = -sin(pa) dx + cos(pa) dy, floored at 1e-4 px.  Two
+ *   components that list the same slot share that parameter.
+ * Errors.  Every entry point returns GM_OK (0) or a negative GM_E_* code and
+ *   never aborts; gm_last_error() returns a message for the calling thread's
+ *   last failure.  Per-galaxy problems are not call failures: they are
+ *   reported through status_out (GM_ST_*).
+ * Arithmetic.  Images FP32; profiles, correlation and per-tile reductions
+ *   FP32; per-galaxy sums, the Sersic constant nu_n, the Cholesky solve and
+ *   the LM state FP64.
+ */
+#ifndef GM_H
+#define GM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GM_MAX_COMP 8
+#define GM_MAX_SLOTS 16
+
+/* return codes */
+#define GM_OK 0
+#define GM_E_INVAL (-1)        /* bad argument (null pointer, bad size, bad descriptor) */
+#define GM_E_CUDA (-2)         /* a CUDA runtime call failed */
+#define GM_E_NOMEM (-3)        /* workspace smaller than the *_workspace_bytes() query */
+#define GM_E_UNSUPPORTED (-4)  /* valid request outside what this build handles */
+
+/* per-galaxy fit status (status_out) */
+#define GM_ST_RUNNING 0
+#define GM_ST_CONVERGED 1      /* accepted step with relative chi^2 decrease < tol, or step < xtol */
+#define GM_ST_MAX_ITER 2       /* max_iter model+Jacobian evaluations spent */
+#define GM_ST_STALLED 3        /* lambda exceeded lambda_max without a chi^2 decrease */
+#define GM_ST_SINGULAR 4       /* damped normal matrix not factorisable up to lambda_max */
+#define GM_ST_NONFINITE 5      /* chi^2 not finite at the starting point */
+#define GM_ST_BAD_INPUT 6      /* sigma <= 0 or a non-finite image/sigma on a used pixel */
+#define GM_ST_NO_DOF 7         /* used pixels <= free parameters */
+
+typedef enum {
+  GM_SERSIC = 1,
+  GM_EXPDISK = 2,
+  GM_FERRER = 3,
+  GM_KING = 4,
+  GM_GAUSSIAN = 5,
+  GM_MOFFAT = 6,
+  GM_SKY = 7
+} gm_kind;
+
+/* One light-profile component.  slot[k] is the parameter slot holding this
+ * component's k-th parameter (order in the header comment).  convolve = 1
+ * correlates the component with the PSF; 0 adds it after the PSF (the flat sky
+ * of Sec. 2 is added after the convolution). */
+typedef struct {
+  int32_t kind;
+  int32_t convolve;
+  int32_t slot[8];
+} gm_component;
+
+/* The model: components, and per slot whether it is fitted (is_free), fitted
+ * in log space (is_log: the LM works on ln p, for positive scale and
+ * amplitude parameters) and its bounds [lo, hi] (physical units; every trial
+ * point is clamped to them).  Host memory. */
+typedef struct {
+  int32_t n_comp;                    /* 1..GM_MAX_COMP */
+  gm_component comp[GM_MAX_COMP];
+  int32_t n_slots;                   /* 1..GM_MAX_SLOTS */
+  uint8_t is_free[GM_MAX_SLOTS];
+  uint8_t is_log[GM_MAX_SLOTS];
+  double lo[GM_MAX_SLOTS];
+  double hi[GM_MAX_SLOTS];
+} gm_model_desc;
+
+/* A batch of equal-size stamps.  The struct itself is host memory; the
+ * arrays it points to are device memory. */
+typedef struct {
+  int32_t n_gal;            /* galaxies, >= 0 */
+  int32_t H, W;             /* stamp rows, columns (1..4096) */
+  int32_t K;                /* PSF side, odd, 1..63 */
+  const float *image;       /* [n_gal][H][W] data D */
+  const float *sigma;       /* [n_gal][H][W] uncertainty sigma (> 0 on used pixels) */
+  const uint8_t *mask;      /* [n_gal][H][W] or NULL */
+  const float *psf;         /* [n_gal][K][K] */
+} gm_batch;
+
+/* Levenberg-Marquardt controls (host memory). */
+typedef struct {
+  double tol;          /* CONVERGED when an accepted step lowers chi^2 by < tol relative */
+  double xtol;         /* CONVERGED when every internal step |du| <= xtol (|u| + xtol) */
+  int32_t max_iter;    /* model+Jacobian evaluations per galaxy (the start counts as one) */
+  double lambda0;      /* initial damping */
+  double lambda_up;    /* lambda *= lambda_up on a rejected step or a failed factorisation */
+  double lambda_down;  /* lambda *= lambda_down on an accepted step ... */
+  double lambda_min;   /* ... but not below lambda_min */
+  double lambda_max;   /* STALLED / SINGULAR beyond this */
+} gm_fit_opts;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int gm_version(void);
+
+/* Message for the calling thread's last nonzero return (static storage, never NULL). */
+const char *gm_last_error(void);
+
+/*
+ * gm_model -- forward model of every galaxy (Sec. 2 workflow, Sec. 4 profiles).
+ *   params     [n_gal][n_slots] FP64
+ *   model_out  [n_gal][H][W] FP32: PSF-correlated sum of the convolved
+ *              components plus the unconvolved ones
+ *   comp_out   NULL or [n_gal][n_comp][H][W] FP32: each component's own
+ *              contribution (correlated when the component is convolved);
+ *              the stored image blocks of Sec. 2
+ *   workspace  gm_model_workspace_bytes(desc, batch) bytes
+ * Returns GM_E_INVAL for bad arguments, GM_E_NOMEM for a short workspace,
+ * GM_E_UNSUPPORTED when the channel count or K exceeds what fits on chip.
+ */
+size_t gm_model_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
+int gm_model(const gm_model_desc *desc, const gm_batch *batch, const double *params,
+             float *model_out, float *comp_out, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * gm_chi2_grad -- chi^2 of Eq. chinu and its derivatives for every galaxy.
+ *   params  [n_gal][n_slots] FP64
+ *   chi2    [n_gal] FP64
+ *   grad    NULL or [n_gal][n_slots] FP64: d chi^2 / d p in physical units,
+ *           = -2 (J^T W r) with r = D - M and W = Omega / sigma^2; 0 for fixed slots
+ *   jtj     NULL or [n_gal][n_slots][n_slots] FP64: J^T W J in physical units
+ *           (the Gauss-Newton half-Hessian); rows/columns of fixed slots are 0
+ *   workspace  gm_chi2_grad_workspace_bytes(desc, batch) bytes
+ * The Jacobian is analytic (chain rule through the elliptical radius and each
+ * profile), correlated with the PSF like the model.  A sigma <= 0 on a used
+ * pixel gives a non-finite chi2 for that galaxy.
+ */
+size_t gm_chi2_grad_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
+int gm_chi2_grad(const gm_model_desc *desc, const gm_batch *batch, const double *params,
+                 double *chi2, double *grad, double *jtj, void *workspace, size_t ws_bytes,
+                 void *stream);
+
+/*
+ * gm_fit_batch -- Levenberg-Marquardt fit of every galaxy (damped Gauss-Newton
+ * on Eq. chinu; Sec. 5.1 names LM as the classical alternative to gradient
+ * descent), with the covariance uncertainty of Sec. 5.2.
+ *   params_inout [n_gal][n_slots] FP64: starting point in, best fit out
+ *                (position angles wrapped to [0, pi))
+ *   opts         host; NULL = defaults (tol 1e-6, xtol 1e-10, max_iter 100,
+ *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10)
+ *   chi2_out     [n_gal] FP64 chi^2 at the best point
+ *   dof_out      [n_gal] int32: used pixels - free parameters (Sec. 5.1)
+ *   iters_out    [n_gal] int32: model+Jacobian evaluations spent
+ *   status_out   [n_gal] int32: GM_ST_*
+ *   sigma_p_out  NULL or [n_gal][n_slots] FP64: sqrt(diag (J^T W J)^-1) at the
+ *                best point, in physical units (p * sigma_ln p for log slots);
+ *                0 for fixed slots
+ *   workspace    gm_fit_workspace_bytes(desc, batch) bytes
+ * Each iteration: one model+Jacobian+reduction pass over the galaxies still
+ * running, then one LM step per galaxy: solve (A + lambda diag A) delta = g
+ * by FP64 Cholesky (A = J^T W J, g = J^T W r in internal coordinates: ln p
+ * for log slots), trial = clamp(p + delta), accept if chi^2 drops.
+ * Synchronises `stream` every few iterations to poll how many galaxies are
+ * still running; returns when none is or all have spent max_iter.
+ */
+size_t gm_fit_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
+int gm_fit_batch(const gm_model_desc *desc, const gm_batch *batch, double *params_inout,
+                 const gm_fit_opts *opts, double *chi2_out, int32_t *dof_out, int32_t *iters_out,
+                 int32_t *status_out, double *sigma_p_out, void *workspace, size_t ws_bytes,
+                 void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GM_H */

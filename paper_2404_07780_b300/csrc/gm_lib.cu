@@ -1,0 +1,531 @@
+// gm_lib.cu -- host side of libgm: argument checks, workspace layout, kernel
+// launches and the LM iteration loop behind the C ABI of include/gm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/gm.h"
+#include "gm_fused.cuh"
+#include "gm_lm.cuh"
+
+using namespace gm;
+
+namespace {
+
+thread_local char g_err[512] = "no error";
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define GM_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(GM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define GM_LAUNCHED(what)                                                                         \
+  do {                                                                                            \
+    cudaError_t e_ = cudaGetLastError();                                                          \
+    if (e_ != cudaSuccess) return fail(GM_E_CUDA, "launch %s: %s", what, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Everything derived from the model description once per call.
+struct Plan {
+  DescDev dd;
+  int conv[kMaxComp];
+  int chan_of_slot[kMaxSlots];  // s_out channel of a free slot (1 + accumulator index), -1 fixed
+  int Pc;                       // free slots touching a convolved component
+  int nch_conv, ncp, nch_tot, nacc;
+  int any_unconv;
+  int comp_chan[kMaxComp];
+};
+
+int check_desc(const gm_model_desc* d) {
+  if (!d) return fail(GM_E_INVAL, "desc is NULL");
+  if (d->n_comp < 1 || d->n_comp > GM_MAX_COMP)
+    return fail(GM_E_INVAL, "n_comp=%d outside 1..%d", d->n_comp, GM_MAX_COMP);
+  if (d->n_slots < 1 || d->n_slots > GM_MAX_SLOTS)
+    return fail(GM_E_INVAL, "n_slots=%d outside 1..%d", d->n_slots, GM_MAX_SLOTS);
+  for (int c = 0; c < d->n_comp; ++c) {
+    const int np = n_params(d->comp[c].kind);
+    if (np < 0) return fail(GM_E_INVAL, "component %d has unknown kind %d", c, d->comp[c].kind);
+    for (int k = 0; k < np; ++k)
+      if (d->comp[c].slot[k] < 0 || d->comp[c].slot[k] >= d->n_slots)
+        return fail(GM_E_INVAL, "component %d parameter %d uses slot %d outside 0..%d", c, k, d->comp[c].slot[k],
+                    d->n_slots - 1);
+  }
+  for (int s = 0; s < d->n_slots; ++s) {
+    if (!(d->lo[s] <= d->hi[s])) return fail(GM_E_INVAL, "slot %d has lo > hi", s);
+    if (d->is_log[s] && !(d->lo[s] > 0.0)) return fail(GM_E_INVAL, "log slot %d needs lo > 0", s);
+  }
+  return GM_OK;
+}
+
+int check_batch(const gm_batch* b, bool need_data) {
+  if (!b) return fail(GM_E_INVAL, "batch is NULL");
+  if (b->n_gal < 0) return fail(GM_E_INVAL, "n_gal=%d < 0", b->n_gal);
+  if (b->H < 1 || b->H > 4096 || b->W < 1 || b->W > 4096)
+    return fail(GM_E_INVAL, "stamp %dx%d outside 1..4096", b->H, b->W);
+  if (b->K < 1 || b->K > 63 || (b->K % 2) == 0) return fail(GM_E_INVAL, "PSF side K=%d must be odd, 1..63", b->K);
+  if (b->n_gal > 0) {
+    if (!b->psf) return fail(GM_E_INVAL, "batch.psf is NULL");
+    if (need_data && (!b->image || !b->sigma)) return fail(GM_E_INVAL, "batch.image/sigma is NULL");
+  }
+  return GM_OK;
+}
+
+// mode: MODE_MODEL (want_comp: per-component channels) or MODE_NORMAL
+int make_plan(const gm_model_desc* d, int mode, bool want_comp, Plan* pl) {
+  int rc = check_desc(d);
+  if (rc) return rc;
+  std::memset(pl, 0, sizeof(*pl));
+  DescDev& D = pl->dd;
+  D.n_comp = d->n_comp;
+  D.n_slots = d->n_slots;
+  bool touches_conv[kMaxSlots] = {};
+  for (int c = 0; c < d->n_comp; ++c) {
+    D.kind[c] = d->comp[c].kind;
+    D.np[c] = n_params(D.kind[c]);
+    pl->conv[c] = d->comp[c].convolve ? 1 : 0;
+    if (!pl->conv[c]) pl->any_unconv = 1;
+    for (int k = 0; k < 8; ++k) D.slot[c][k] = k < D.np[c] ? d->comp[c].slot[k] : 0;
+    if (pl->conv[c])
+      for (int k = 0; k < D.np[c]; ++k) touches_conv[D.slot[c][k]] = true;
+    if (D.kind[c] != SKY) D.is_pa[D.slot[c][3]] = 1;
+  }
+  for (int s = 0; s < d->n_slots; ++s) {
+    D.is_log[s] = d->is_log[s] ? 1 : 0;
+    D.lo[s] = d->lo[s];
+    D.hi[s] = d->hi[s];
+    pl->chan_of_slot[s] = -1;
+  }
+  // accumulator order: free slots of convolved components first, then the rest
+  int P = 0;
+  for (int s = 0; s < d->n_slots; ++s)
+    if (d->is_free[s] && touches_conv[s]) D.free_slot[P++] = s;
+  pl->Pc = P;
+  for (int s = 0; s < d->n_slots; ++s)
+    if (d->is_free[s] && !touches_conv[s]) D.free_slot[P++] = s;
+  D.P = P;
+  for (int f = 0; f < P; ++f) pl->chan_of_slot[D.free_slot[f]] = 1 + f;
+  for (int c = 0; c < kMaxComp; ++c) pl->comp_chan[c] = -1;
+  if (mode == MODE_NORMAL) {
+    pl->nch_conv = 1 + pl->Pc;
+    pl->nch_tot = 1 + P;
+    pl->nacc = 1 + P + P * (P + 1) / 2;
+  } else {
+    int nc = 1;
+    if (want_comp)
+      for (int c = 0; c < d->n_comp; ++c)
+        if (pl->conv[c]) pl->comp_chan[c] = nc++;
+    pl->nch_conv = nc;
+    int nt = nc;
+    if (want_comp)
+      for (int c = 0; c < d->n_comp; ++c)
+        if (!pl->conv[c]) pl->comp_chan[c] = nt++;
+    pl->nch_tot = nt;
+    pl->nacc = 0;
+  }
+  pl->ncp = (pl->nch_conv + 1) / 2;
+  if (pl->nch_conv > kMaxConvCh)
+    return fail(GM_E_UNSUPPORTED, "%d correlated channels (free parameters of convolved components + 1) exceed %d",
+                pl->nch_conv, kMaxConvCh);
+  return GM_OK;
+}
+
+struct Smem {
+  int rw, off_psf, off_in, off_out, off_cc, off_scale, off_red, total, threads;
+};
+
+// Shared-memory carve-up of one fused CTA.  The input row pitch rw (in float2)
+// is >= K + 33 (the window reads 2 columns past the halo) and == 2 mod 16, so
+// the 8 lanes of a quarter warp (8 consecutive rows) hit distinct 16-byte bank
+// groups on their 16-byte loads.
+Smem smem_plan(const Plan& pl, int K, int n_comp, int n_slots) {
+  Smem s;
+  s.threads = kGroupThreads * ((pl.ncp + 1) / 2);
+  int rw = std::max(kTile + K - 1, K + 33);
+  while (rw % 16 != 2) ++rw;
+  s.rw = rw;
+  const int HH = kTile + K - 1;
+  size_t off = 0;
+  s.off_psf = (int)off;
+  off += (size_t)K * (K + 1) * 8;
+  off = (off + 15) & ~(size_t)15;
+  s.off_in = (int)off;
+  s.off_out = (int)off;
+  const size_t in_bytes = (size_t)pl.ncp * HH * rw * 8;
+  const size_t out_bytes = (size_t)pl.nch_tot * kTilePix * 4;
+  off += std::max(in_bytes, out_bytes);
+  off = (off + 15) & ~(size_t)15;
+  s.off_cc = (int)off;
+  off += (size_t)n_comp * kCC * 4;
+  s.off_scale = (int)off;
+  off += (size_t)n_slots * 4;
+  off = (off + 15) & ~(size_t)15;
+  s.off_red = (int)off;
+  off += (size_t)(s.threads / 32) * std::max(pl.nacc, 1) * 4;
+  s.total = (int)off;
+  return s;
+}
+
+struct DevInfo {
+  int sms = 0, smem_optin = 0;
+};
+
+int dev_info(DevInfo* di) {
+  int dev = 0;
+  GM_CUDA(cudaGetDevice(&dev));
+  GM_CUDA(cudaDeviceGetAttribute(&di->sms, cudaDevAttrMultiProcessorCount, dev));
+  GM_CUDA(cudaDeviceGetAttribute(&di->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  return GM_OK;
+}
+
+typedef void (*FusedKernel)(FusedArgs);
+
+FusedKernel pick_kernel(int mode, int P) {
+  if (mode == MODE_MODEL) return k_fused<MODE_MODEL, 0>;
+  switch (P) {
+#define GM_CASE(n) \
+  case n:          \
+    return k_fused<MODE_NORMAL, n>;
+    GM_CASE(0) GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
+    GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12) GM_CASE(13) GM_CASE(14) GM_CASE(15) GM_CASE(16)
+#undef GM_CASE
+    default:
+      return nullptr;
+  }
+}
+
+void fill_args(FusedArgs& A, const Plan& pl, const gm_batch* b, const Smem& sm) {
+  std::memset(&A, 0, sizeof(A));
+  const DescDev& D = pl.dd;
+  A.n_comp = D.n_comp;
+  for (int c = 0; c < D.n_comp; ++c) {
+    A.kind[c] = D.kind[c];
+    A.conv[c] = pl.conv[c];
+    A.np[c] = D.np[c];
+    A.comp_chan[c] = pl.comp_chan[c];
+    for (int k = 0; k < 8; ++k) {
+      A.slot[c][k] = D.slot[c][k];
+      A.chan[c][k] = (pl.nacc > 0 && k < D.np[c]) ? pl.chan_of_slot[D.slot[c][k]] : -1;
+    }
+  }
+  A.any_unconv = pl.any_unconv;
+  A.nch_conv = pl.nch_conv;
+  A.ncp = pl.ncp;
+  A.nch_tot = pl.nch_tot;
+  A.n_slots = D.n_slots;
+  A.nacc = pl.nacc;
+  A.G = b->n_gal;
+  A.H = b->H;
+  A.W = b->W;
+  A.K = b->K;
+  A.tiles_x = (b->W + kTile - 1) / kTile;
+  A.n_tiles = A.tiles_x * ((b->H + kTile - 1) / kTile);
+  A.rw = sm.rw;
+  A.image = b->image;
+  A.sigma = b->sigma;
+  A.mask = b->mask;
+  A.psf = b->psf;
+  A.off_psf = sm.off_psf;
+  A.off_in = sm.off_in;
+  A.off_out = sm.off_out;
+  A.off_cc = sm.off_cc;
+  A.off_scale = sm.off_scale;
+  A.off_red = sm.off_red;
+}
+
+int prepare_fused(int mode, const Plan& pl, const Smem& sm, const DevInfo& di, int K, FusedKernel* out) {
+  FusedKernel k = pick_kernel(mode, pl.dd.P);
+  if (!k) return fail(GM_E_UNSUPPORTED, "no fused kernel for %d free parameters", pl.dd.P);
+  if (sm.total > di.smem_optin)
+    return fail(GM_E_UNSUPPORTED, "tile needs %d bytes of shared memory (K=%d, %d channels); the device allows %d",
+                sm.total, K, pl.nch_conv, di.smem_optin);
+  GM_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm.total));
+  *out = k;
+  return GM_OK;
+}
+
+// workspace carve-up
+struct WsModel {
+  size_t cconst, scale, total;
+};
+WsModel ws_model(const gm_model_desc* d, const gm_batch* b) {
+  WsModel w;
+  size_t off = 0;
+  const size_t G = (size_t)std::max(b->n_gal, 0);
+  w.cconst = off;
+  off += align256(G * d->n_comp * kCC * 4);
+  w.scale = off;
+  off += align256(G * d->n_slots * 4);
+  w.total = off;
+  return w;
+}
+
+struct WsChi2 {
+  WsModel m;
+  size_t partial, total;
+};
+WsChi2 ws_chi2(const gm_model_desc* d, const gm_batch* b, int P) {
+  WsChi2 w;
+  w.m = ws_model(d, b);
+  size_t off = w.m.total;
+  const size_t G = (size_t)std::max(b->n_gal, 0);
+  const size_t tiles = (size_t)((b->W + kTile - 1) / kTile) * ((b->H + kTile - 1) / kTile);
+  const size_t nacc = 1 + P + (size_t)P * (P + 1) / 2;
+  w.partial = off;
+  off += align256(G * tiles * nacc * 8);
+  w.total = off;
+  return w;
+}
+
+struct WsFit {
+  WsChi2 c;
+  size_t p_b, p_t, A_b, g_b, chi2_b, lam, it, status, nused, bad, list0, list1, counts, total;
+};
+WsFit ws_fit(const gm_model_desc* d, const gm_batch* b, int P) {
+  WsFit w;
+  w.c = ws_chi2(d, b, P);
+  size_t off = w.c.total;
+  const size_t G = (size_t)std::max(b->n_gal, 0), S = d->n_slots;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  w.p_b = take(G * S * 8);
+  w.p_t = take(G * S * 8);
+  w.A_b = take(G * (size_t)(P * (P + 1) / 2 + 1) * 8);
+  w.g_b = take(G * (size_t)(P + 1) * 8);
+  w.chi2_b = take(G * 8);
+  w.lam = take(G * 8);
+  w.it = take(G * 4);
+  w.status = take(G * 4);
+  w.nused = take(G * 4);
+  w.bad = take(G * 4);
+  w.list0 = take(G * 4);
+  w.list1 = take(G * 4);
+  w.counts = take(2 * 4);
+  w.total = off;
+  return w;
+}
+
+int count_free(const gm_model_desc* d) {
+  int P = 0;
+  for (int s = 0; s < d->n_slots && s < GM_MAX_SLOTS; ++s) P += d->is_free[s] ? 1 : 0;
+  return P;
+}
+
+LMOpts lm_opts(const gm_fit_opts* o) {
+  LMOpts L;
+  if (o) {
+    L.tol = o->tol;
+    L.xtol = o->xtol;
+    L.max_iter = o->max_iter;
+    L.lambda0 = o->lambda0;
+    L.lambda_up = o->lambda_up;
+    L.lambda_down = o->lambda_down;
+    L.lambda_min = o->lambda_min;
+    L.lambda_max = o->lambda_max;
+  } else {
+    L.tol = 1e-6;
+    L.xtol = 1e-10;
+    L.max_iter = 100;
+    L.lambda0 = 0.1;
+    L.lambda_up = 10.0;
+    L.lambda_down = 0.1;
+    L.lambda_min = 1e-7;
+    L.lambda_max = 1e10;
+  }
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gm_version(void) { return 100; }
+
+const char* gm_last_error(void) { return g_err; }
+
+size_t gm_model_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
+  if (!desc || !batch || check_desc(desc) || check_batch(batch, false)) return 0;
+  return ws_model(desc, batch).total;
+}
+
+int gm_model(const gm_model_desc* desc, const gm_batch* batch, const double* params, float* model_out,
+             float* comp_out, void* workspace, size_t ws_bytes, void* stream) {
+  int rc = check_batch(batch, false);
+  if (rc) return rc;
+  Plan pl;
+  rc = make_plan(desc, MODE_MODEL, comp_out != nullptr, &pl);
+  if (rc) return rc;
+  if (batch->n_gal == 0) return GM_OK;
+  if (!params || !model_out) return fail(GM_E_INVAL, "params/model_out is NULL");
+  const WsModel w = ws_model(desc, batch);
+  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+  DevInfo di;
+  if ((rc = dev_info(&di))) return rc;
+  const Smem sm = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots);
+  FusedKernel kf;
+  if ((rc = prepare_fused(MODE_MODEL, pl, sm, di, batch->K, &kf))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  float* cconst = (float*)(ws + w.cconst);
+  float* scale = (float*)(ws + w.scale);
+  const int G = batch->n_gal;
+  k_setup<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
+  GM_LAUNCHED("k_setup");
+  FusedArgs A;
+  fill_args(A, pl, batch, sm);
+  A.cconst = cconst;
+  A.scale = scale;
+  A.model_out = model_out;
+  A.comp_out = comp_out;
+  const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
+  kf<<<grid, sm.threads, sm.total, st>>>(A);
+  GM_LAUNCHED("k_fused(model)");
+  return GM_OK;
+}
+
+size_t gm_chi2_grad_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
+  if (!desc || !batch || check_desc(desc) || check_batch(batch, false)) return 0;
+  return ws_chi2(desc, batch, count_free(desc)).total;
+}
+
+int gm_chi2_grad(const gm_model_desc* desc, const gm_batch* batch, const double* params, double* chi2,
+                 double* grad, double* jtj, void* workspace, size_t ws_bytes, void* stream) {
+  int rc = check_batch(batch, true);
+  if (rc) return rc;
+  Plan pl;
+  rc = make_plan(desc, MODE_NORMAL, false, &pl);
+  if (rc) return rc;
+  if (batch->n_gal == 0) return GM_OK;
+  if (!params || !chi2) return fail(GM_E_INVAL, "params/chi2 is NULL");
+  const WsChi2 w = ws_chi2(desc, batch, pl.dd.P);
+  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+  DevInfo di;
+  if ((rc = dev_info(&di))) return rc;
+  const Smem sm = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots);
+  FusedKernel kf;
+  if ((rc = prepare_fused(MODE_NORMAL, pl, sm, di, batch->K, &kf))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  float* cconst = (float*)(ws + w.m.cconst);
+  float* scale = (float*)(ws + w.m.scale);
+  double* partial = (double*)(ws + w.partial);
+  const int G = batch->n_gal;
+  k_setup<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
+  GM_LAUNCHED("k_setup");
+  FusedArgs A;
+  fill_args(A, pl, batch, sm);
+  A.cconst = cconst;
+  A.scale = scale;
+  A.partial = partial;
+  const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
+  kf<<<grid, sm.threads, sm.total, st>>>(A);
+  GM_LAUNCHED("k_fused(normal)");
+  k_chi2_grad_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, A.n_tiles, partial, chi2, grad, jtj);
+  GM_LAUNCHED("k_chi2_grad_finish");
+  return GM_OK;
+}
+
+size_t gm_fit_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
+  if (!desc || !batch || check_desc(desc) || check_batch(batch, false)) return 0;
+  return ws_fit(desc, batch, count_free(desc)).total;
+}
+
+int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* params_inout, const gm_fit_opts* opts,
+                 double* chi2_out, int32_t* dof_out, int32_t* iters_out, int32_t* status_out, double* sigma_p_out,
+                 void* workspace, size_t ws_bytes, void* stream) {
+  int rc = check_batch(batch, true);
+  if (rc) return rc;
+  Plan pl;
+  rc = make_plan(desc, MODE_NORMAL, false, &pl);
+  if (rc) return rc;
+  if (batch->n_gal == 0) return GM_OK;
+  if (!params_inout || !chi2_out || !dof_out || !iters_out || !status_out)
+    return fail(GM_E_INVAL, "an output pointer is NULL");
+  const LMOpts O = lm_opts(opts);
+  if (O.max_iter < 1) return fail(GM_E_INVAL, "max_iter=%d < 1", O.max_iter);
+  if (!(O.lambda_up > 1.0) || !(O.lambda_down > 0.0) || !(O.lambda_down < 1.0) || !(O.lambda0 > 0.0))
+    return fail(GM_E_INVAL, "lambda controls must satisfy lambda0 > 0, up > 1, 0 < down < 1");
+  const WsFit w = ws_fit(desc, batch, pl.dd.P);
+  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+  DevInfo di;
+  if ((rc = dev_info(&di))) return rc;
+  const Smem sm = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots);
+  FusedKernel kf;
+  if ((rc = prepare_fused(MODE_NORMAL, pl, sm, di, batch->K, &kf))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  float* cconst = (float*)(ws + w.c.m.cconst);
+  float* scale = (float*)(ws + w.c.m.scale);
+  double* partial = (double*)(ws + w.c.partial);
+  LMState S;
+  S.p_b = (double*)(ws + w.p_b);
+  S.p_t = (double*)(ws + w.p_t);
+  S.A_b = (double*)(ws + w.A_b);
+  S.g_b = (double*)(ws + w.g_b);
+  S.chi2_b = (double*)(ws + w.chi2_b);
+  S.lam = (double*)(ws + w.lam);
+  S.it = (int*)(ws + w.it);
+  S.status = (int*)(ws + w.status);
+  S.nused = (int*)(ws + w.nused);
+  S.bad = (int*)(ws + w.bad);
+  S.list[0] = (int*)(ws + w.list0);
+  S.list[1] = (int*)(ws + w.list1);
+  S.count[0] = (int*)(ws + w.counts);
+  S.count[1] = S.count[0] + 1;
+  const int G = batch->n_gal;
+
+  k_validate<<<std::min(G, 4 * di.sms), 256, 0, st>>>(G, batch->H, batch->W, batch->image, batch->sigma,
+                                                      batch->mask, S.nused, S.bad);
+  GM_LAUNCHED("k_validate");
+  GM_CUDA(cudaMemsetAsync(S.count[0], 0, 2 * sizeof(int), st));
+  k_lm_init<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, O, G, batch->H, params_inout, cconst, scale);
+  GM_LAUNCHED("k_lm_init");
+
+  FusedArgs A;
+  fill_args(A, pl, batch, sm);
+  A.cconst = cconst;
+  A.scale = scale;
+  A.partial = partial;
+  const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
+  const int poll = 4;
+  for (int k = 0; k < O.max_iter; ++k) {
+    const int cur = k & 1;
+    A.list = S.list[cur];
+    A.count = S.count[cur];
+    kf<<<grid, sm.threads, sm.total, st>>>(A);
+    GM_LAUNCHED("k_fused(normal)");
+    GM_CUDA(cudaMemsetAsync(S.count[cur ^ 1], 0, sizeof(int), st));
+    k_lm_step<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, O, cur, batch->H, A.n_tiles, partial, cconst, scale);
+    GM_LAUNCHED("k_lm_step");
+    if ((k + 1) % poll == 0 || k + 1 == O.max_iter) {
+      int remaining = 0;
+      GM_CUDA(cudaMemcpyAsync(&remaining, S.count[cur ^ 1], sizeof(int), cudaMemcpyDeviceToHost, st));
+      GM_CUDA(cudaStreamSynchronize(st));
+      if (remaining == 0) break;
+    }
+  }
+  k_lm_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, G, params_inout, chi2_out, dof_out, iters_out,
+                                               status_out, sigma_p_out);
+  GM_LAUNCHED("k_lm_finish");
+  GM_CUDA(cudaStreamSynchronize(st));
+  return GM_OK;
+}
+
+}  // extern "C"

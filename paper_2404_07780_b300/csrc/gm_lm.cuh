@@ -1,0 +1,352 @@
+// gm_lm.cuh -- per-galaxy kernels around the fused pass: input validation,
+// set-up of the per-component constants, the Levenberg-Marquardt step (FP64
+// Cholesky on the damped normal equations) and the final outputs with the
+// covariance uncertainty sigma_p = sqrt(diag[(J^T W J)^-1]) of Sec. 5.2 of
+// arxiv 2404.07780.
+#pragma once
+
+#include "gm_profiles.cuh"
+
+namespace gm {
+
+constexpr int ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAX_ITER = 2, ST_STALLED = 3, ST_SINGULAR = 4,
+              ST_NONFINITE = 5, ST_BAD_INPUT = 6, ST_NO_DOF = 7;
+
+constexpr int kMaxAcc = 1 + kMaxSlots + kMaxSlots * (kMaxSlots + 1) / 2;
+
+// Model description as the per-galaxy kernels need it.
+struct DescDev {
+  int n_comp;
+  int kind[kMaxComp];
+  int np[kMaxComp];
+  int slot[kMaxComp][8];
+  int n_slots;
+  int P;                       // free slots
+  int free_slot[kMaxSlots];    // accumulator order -> slot
+  int is_log[kMaxSlots];
+  int is_pa[kMaxSlots];        // slot is some radial component's position angle
+  double lo[kMaxSlots], hi[kMaxSlots];
+};
+
+struct LMOpts {
+  double tol, xtol;
+  int max_iter;
+  double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
+};
+
+// Per-galaxy LM state, struct of arrays in the caller's workspace.
+struct LMState {
+  double* p_b;     // [G][S] best point
+  double* p_t;     // [G][S] point being evaluated
+  double* A_b;     // [G][P(P+1)/2] J^T W J at p_b (internal coordinates, packed upper)
+  double* g_b;     // [G][P] J^T W r at p_b
+  double* chi2_b;  // [G]
+  double* lam;     // [G]
+  int* it;         // [G] evaluations done
+  int* status;     // [G]
+  int* nused;      // [G] unmasked pixels
+  int* bad;        // [G] bad sigma / image on a used pixel
+  int* list[2];    // active galaxies, double-buffered by iteration parity
+  int* count[2];
+};
+
+__device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, int use_log, float* cc,
+                                    float* scale) {
+  double par[8];
+  for (int c = 0; c < D.n_comp; ++c) {
+    for (int k = 0; k < D.np[c]; ++k) par[k] = p[D.slot[c][k]];
+    setup_component(D.kind[c], par, H, cc + c * kCC);
+  }
+  for (int s = 0; s < D.n_slots; ++s) scale[s] = (use_log && D.is_log[s]) ? (float)p[s] : 1.f;
+}
+
+// Constants for every galaxy from caller parameters (gm_model, gm_chi2_grad).
+__global__ void k_setup(const __grid_constant__ DescDev D, int G, int H, const double* __restrict__ params,
+                        int use_log, float* cconst, float* scale) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  setup_galaxy(D, params + (size_t)g * D.n_slots, H, use_log, cconst + (size_t)g * D.n_comp * kCC,
+               scale + (size_t)g * D.n_slots);
+}
+
+// Used-pixel count and bad-input flag per galaxy (one block per galaxy, strided).
+__global__ void k_validate(int G, int H, int W, const float* __restrict__ image, const float* __restrict__ sigma,
+                           const uint8_t* __restrict__ mask, int* nused, int* bad) {
+  __shared__ int s_n[32], s_b[32];
+  const size_t HW = (size_t)H * W;
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    int n = 0, b = 0;
+    for (size_t t = threadIdx.x; t < HW; t += blockDim.x) {
+      const size_t gp = (size_t)g * HW + t;
+      if (mask && mask[gp]) continue;
+      ++n;
+      const float s = sigma[gp], d = image[gp];
+      if (!(s > 0.f) || !isfinite(s) || !isfinite(d)) b = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      n += __shfl_xor_sync(0xffffffffu, n, o);
+      b |= __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      s_n[warp] = n;
+      s_b[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tn = 0, tb = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        tn += s_n[w];
+        tb |= s_b[w];
+      }
+      nused[g] = tn;
+      bad[g] = tb;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ inline double to_u(const DescDev& D, int s, double p) { return D.is_log[s] ? log(p) : p; }
+__device__ inline double from_u(const DescDev& D, int s, double u) { return D.is_log[s] ? exp(u) : u; }
+
+__device__ inline void clamp_slots(const DescDev& D, double* p) {
+  for (int s = 0; s < D.n_slots; ++s) p[s] = fmin(fmax(p[s], D.lo[s]), D.hi[s]);
+}
+
+// Start of a fit: clamp the start point, set status from the validation and
+// queue the galaxies that can be fitted.
+__global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O, int G, int H,
+                          const double* __restrict__ params0, float* cconst, float* scale) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int NS = D.n_slots, P = D.P;
+  double* pb = S.p_b + (size_t)g * NS;
+  double* pt = S.p_t + (size_t)g * NS;
+  for (int s = 0; s < NS; ++s) pb[s] = params0[(size_t)g * NS + s];
+  clamp_slots(D, pb);
+  for (int s = 0; s < NS; ++s) pt[s] = pb[s];
+  S.it[g] = 0;
+  S.lam[g] = O.lambda0;
+  S.chi2_b[g] = CUDART_NAN;
+  int st = ST_RUNNING;
+  if (S.bad[g]) st = ST_BAD_INPUT;
+  else if (S.nused[g] - P <= 0) st = ST_NO_DOF;
+  S.status[g] = st;
+  if (st == ST_RUNNING) {
+    setup_galaxy(D, pt, H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
+    const int pos = atomicAdd(S.count[0], 1);
+    S.list[0][pos] = g;
+  }
+}
+
+// In-place Cholesky of an n x n row-major matrix (lower triangle); false if not
+// positive definite.
+__device__ inline bool cholesky(double* M, int n) {
+  for (int j = 0; j < n; ++j) {
+    double s = M[j * n + j];
+    for (int k = 0; k < j; ++k) s -= M[j * n + k] * M[j * n + k];
+    if (!(s > 0.0)) return false;
+    const double l = sqrt(s);
+    M[j * n + j] = l;
+    for (int i = j + 1; i < n; ++i) {
+      double t = M[i * n + j];
+      for (int k = 0; k < j; ++k) t -= M[i * n + k] * M[j * n + k];
+      M[i * n + j] = t / l;
+    }
+  }
+  return true;
+}
+
+__device__ inline void chol_solve(const double* L, int n, const double* b, double* x) {
+  double y[kMaxSlots];
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+}
+
+// Entry (f, h) of a row-major packed upper triangle of a symmetric P x P matrix.
+__device__ inline double packed(const double* Ap, int P, int f, int h) {
+  if (f > h) {
+    const int t = f;
+    f = h;
+    h = t;
+  }
+  return Ap[f * P - (f * (f - 1)) / 2 + (h - f)];
+}
+
+// One LM step for every galaxy evaluated in this iteration (list `cur`):
+// sum the tile partials of the pass, accept or reject the evaluated point,
+// test convergence, solve the damped normal equations for the next trial point
+// and queue the galaxy for the next pass (list `cur ^ 1`).  The rules are the
+// ones the FP64 oracle states: accept when chi^2 drops; CONVERGED when an
+// accepted step lowers chi^2 by less than tol relative or any evaluated step
+// is below xtol; STALLED / SINGULAR past lambda_max; MAX_ITER at max_iter.
+__global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O, int cur, int H,
+                          int n_tiles, const double* __restrict__ partial, float* cconst, float* scale) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= *S.count[cur]) return;
+  const int g = S.list[cur][gi];
+  const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
+  double* pb = S.p_b + (size_t)g * NS;
+  double* pt = S.p_t + (size_t)g * NS;
+  double* Ab = S.A_b + (size_t)g * NAp;
+  double* gb = S.g_b + (size_t)g * P;
+
+  // sums of the tile partials in tile order (deterministic)
+  double acc[kMaxAcc];
+  for (int e = 0; e < NA; ++e) acc[e] = 0.0;
+  const double* pp = partial + (size_t)g * n_tiles * NA;
+  for (int t = 0; t < n_tiles; ++t)
+    for (int e = 0; e < NA; ++e) acc[e] += pp[t * NA + e];
+  const double chi2_t = acc[0];
+
+  int st = ST_RUNNING;
+  const int it = S.it[g] + 1;
+  S.it[g] = it;
+  double lam = S.lam[g];
+  if (it == 1) {
+    if (!isfinite(chi2_t)) {
+      st = ST_NONFINITE;
+    } else {
+      for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
+      for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
+      S.chi2_b[g] = chi2_t;
+      if (chi2_t == 0.0) st = ST_CONVERGED;
+    }
+  } else {
+    bool small = true;
+    for (int f = 0; f < P; ++f) {
+      const int s = D.free_slot[f];
+      const double u0 = to_u(D, s, pb[s]), u1 = to_u(D, s, pt[s]);
+      if (fabs(u1 - u0) > O.xtol * (fabs(u0) + O.xtol)) small = false;
+    }
+    const double chi2_b = S.chi2_b[g];
+    if (isfinite(chi2_t) && chi2_t < chi2_b) {
+      const double act = (chi2_b - chi2_t) / chi2_b;
+      for (int s = 0; s < NS; ++s) pb[s] = pt[s];
+      for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
+      for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
+      S.chi2_b[g] = chi2_t;
+      lam = fmax(lam * O.lambda_down, O.lambda_min);
+      if (act < O.tol || small || chi2_t == 0.0) st = ST_CONVERGED;
+    } else if (small) {
+      st = ST_CONVERGED;
+    } else {
+      lam *= O.lambda_up;
+      if (lam > O.lambda_max) st = ST_STALLED;
+    }
+  }
+
+  if (st == ST_RUNNING && it >= O.max_iter) st = ST_MAX_ITER;
+  if (st == ST_RUNNING) {
+    double M[kMaxSlots * kMaxSlots], delta[kMaxSlots];
+    double dmax = 0.0;
+    for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ab, P, f, f));
+    const double dfloor = 1e-12 * dmax;
+    for (;;) {
+      for (int f = 0; f < P; ++f)
+        for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
+      for (int f = 0; f < P; ++f) M[f * P + f] += lam * fmax(packed(Ab, P, f, f), dfloor);
+      if (cholesky(M, P)) break;
+      lam *= O.lambda_up;
+      if (lam > O.lambda_max) {
+        st = ST_SINGULAR;
+        break;
+      }
+    }
+    if (st == ST_RUNNING) {
+      chol_solve(M, P, gb, delta);
+      for (int s = 0; s < NS; ++s) pt[s] = pb[s];
+      for (int f = 0; f < P; ++f) {
+        const int s = D.free_slot[f];
+        pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
+      }
+      clamp_slots(D, pt);
+      setup_galaxy(D, pt, H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
+      const int nxt = cur ^ 1;
+      const int pos = atomicAdd(S.count[nxt], 1);
+      S.list[nxt][pos] = g;
+    }
+  }
+  S.lam[g] = lam;
+  S.status[g] = st;
+}
+
+// Outputs of a fit: best point (position angles wrapped to [0, pi)), chi^2,
+// degrees of freedom, evaluations, status and the covariance error bars.
+__global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G, double* params_out,
+                            double* chi2_out, int* dof_out, int* iters_out, int* status_out,
+                            double* sigma_p_out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int NS = D.n_slots, P = D.P;
+  const double* pb = S.p_b + (size_t)g * NS;
+  const double pi = 3.14159265358979323846;
+  for (int s = 0; s < NS; ++s) {
+    double v = pb[s];
+    if (D.is_pa[s]) v -= pi * floor(v / pi);
+    params_out[(size_t)g * NS + s] = v;
+  }
+  chi2_out[g] = S.chi2_b[g];
+  dof_out[g] = S.nused[g] - P;
+  iters_out[g] = S.it[g];
+  status_out[g] = S.status[g];
+  if (sigma_p_out) {
+    double* sp = sigma_p_out + (size_t)g * NS;
+    for (int s = 0; s < NS; ++s) sp[s] = 0.0;
+    if (S.it[g] == 0 || S.status[g] == ST_NONFINITE) {
+      for (int f = 0; f < P; ++f) sp[D.free_slot[f]] = CUDART_NAN;
+      return;
+    }
+    const double* Ab = S.A_b + (size_t)g * (P * (P + 1) / 2);
+    double M[kMaxSlots * kMaxSlots];
+    for (int f = 0; f < P; ++f)
+      for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
+    if (!cholesky(M, P)) {
+      for (int f = 0; f < P; ++f) sp[D.free_slot[f]] = CUDART_NAN;
+      return;
+    }
+    for (int f = 0; f < P; ++f) {
+      double e[kMaxSlots], x[kMaxSlots];
+      for (int h = 0; h < P; ++h) e[h] = (h == f) ? 1.0 : 0.0;
+      chol_solve(M, P, e, x);
+      const int s = D.free_slot[f];
+      const double su = sqrt(x[f]);
+      sp[s] = D.is_log[s] ? pb[s] * su : su;
+    }
+  }
+}
+
+// gm_chi2_grad outputs from the tile partials (physical coordinates).
+__global__ void k_chi2_grad_finish(const __grid_constant__ DescDev D, int G, int n_tiles,
+                                   const double* __restrict__ partial, double* chi2, double* grad, double* jtj) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
+  double acc[kMaxAcc];
+  for (int e = 0; e < NA; ++e) acc[e] = 0.0;
+  const double* pp = partial + (size_t)g * n_tiles * NA;
+  for (int t = 0; t < n_tiles; ++t)
+    for (int e = 0; e < NA; ++e) acc[e] += pp[t * NA + e];
+  chi2[g] = acc[0];
+  if (grad) {
+    double* gr = grad + (size_t)g * NS;
+    for (int s = 0; s < NS; ++s) gr[s] = 0.0;
+    for (int f = 0; f < P; ++f) gr[D.free_slot[f]] = -2.0 * acc[1 + f];
+  }
+  if (jtj) {
+    double* J = jtj + (size_t)g * NS * NS;
+    for (int s = 0; s < NS * NS; ++s) J[s] = 0.0;
+    for (int f = 0; f < P; ++f)
+      for (int h = 0; h < P; ++h) J[D.free_slot[f] * NS + D.free_slot[h]] = packed(acc + 1 + P, P, f, h);
+  }
+}
+
+}  // namespace gm

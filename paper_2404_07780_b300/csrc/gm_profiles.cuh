@@ -1,0 +1,320 @@
+// gm_profiles.cuh -- per-galaxy set-up (FP64) and per-pixel light profiles with
+// their analytic parameter derivatives (FP32) for the fused kernels.
+//
+// Profiles follow Sec. 4.1-4.2 of arxiv 2404.07780: the elliptical radius of
+// Eqs. (r)-(rmin) with B = 0, and Eqs. (sersic-intensity), (expdisk_I),
+// (ferrer_I), (BE_S) (bracket read so that I(0) = I0), (gaussion_I),
+// (moffat_I)+(moffat_rd) and (sky_I).  Derivatives are the chain rule through
+// the radius:
+//   dr/dx0 = (-X c + (Y/q^2) s)/r     dr/dy0 = (-X s - (Y/q^2) c)/r
+//   dr/dq  = -Y^2/(q^3 r)             dr/dpa = X Y (1 - 1/q^2)/r
+// with X = c dx + s dy, Y = -s dx + c dy, c = cos pa, s = sin pa, and r
+// floored at 1e-4 px (geometric derivatives vanish under the floor).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace gm {
+
+constexpr int kMaxComp = 8;
+constexpr int kMaxSlots = 16;
+constexpr int kCC = 16;          // FP32 constants per component per galaxy
+constexpr float kRFloor = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+enum Kind { SERSIC = 1, EXPDISK = 2, FERRER = 3, KING = 4, GAUSSIAN = 5, MOFFAT = 6, SKY = 7 };
+
+__host__ __device__ inline int n_params(int kind) {
+  switch (kind) {
+    case SERSIC: return 7;
+    case EXPDISK: return 6;
+    case FERRER: return 8;
+    case KING: return 8;
+    case GAUSSIAN: return 6;
+    case MOFFAT: return 7;
+    case SKY: return 1;
+    default: return -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// nu_n of the Sersic profile (Sec. 4.1): the root of P(2n, x) = 1/2, i.e. the
+// radius r_e encloses half of the light.  Newton iteration on the series form
+// of the regularised lower incomplete gamma function,
+//   P(a, x) = x^a e^-x sum_{k>=0} x^k / Gamma(a + k + 1),
+// started from the asymptotic expansion of Ciotti & Bertin (1999) for n >= 0.36
+// and from the polynomial fit of MacArthur, Courteau & Holtzman (2003) below.
+// The root lies below a = 2n, where the series converges geometrically.
+// ---------------------------------------------------------------------------
+__device__ inline double lower_gamma_reg(double a, double x) {
+  if (x <= 0.0) return 0.0;
+  double term = 1.0 / a;  // Gamma(a) x^0 / Gamma(a + 1)
+  double sum = term;
+  for (int k = 1; k < 2000; ++k) {
+    term *= x / (a + k);
+    sum += term;
+    if (term < sum * 1e-17) break;
+  }
+  return sum * exp(a * log(x) - x - lgamma(a));
+}
+
+__device__ inline double sersic_nu(double n) {
+  const double a = 2.0 * n;
+  double x;
+  if (n >= 0.36) {
+    const double in = 1.0 / n;
+    x = 2.0 * n - 1.0 / 3.0 +
+        in * (4.0 / 405.0 + in * (46.0 / 25515.0 + in * (131.0 / 1148175.0 - in * (2194697.0 / 30690717750.0))));
+  } else {
+    x = 0.01945 + n * (-0.8902 + n * (10.95 + n * (-19.67 + n * 13.43)));
+    if (!(x > 0.0)) x = 0.5 * a;
+  }
+  const double lga = lgamma(a);
+  for (int it = 0; it < 60; ++it) {
+    const double f = lower_gamma_reg(a, x) - 0.5;
+    const double dens = exp((a - 1.0) * log(x) - x - lga);  // dP/dx
+    double xn = x - f / dens;
+    if (!(xn > 0.0)) xn = 0.5 * x;
+    const double dx = fabs(xn - x);
+    x = xn;
+    if (dx <= 1e-15 * x) break;
+  }
+  return x;
+}
+
+// dnu/dn by a central difference of the Newton solve (h = 1e-4 n).
+__device__ inline double sersic_dnu(double n) {
+  const double h = 1e-4 * n;
+  return (sersic_nu(n + h) - sersic_nu(n - h)) / (2.0 * h);
+}
+
+// ---------------------------------------------------------------------------
+// Per-component constants (FP32), computed in FP64 from the parameters.
+//   [0] xi (int bits) [1] yi (int bits) [2] xf [3] yf : dx = (j + xi) + xf,
+//       dy = (yi - i) + yf, an exact split of x_j - x0 and y_i - y0 so that
+//       the pixel offset keeps full FP32 precision far from the origin
+//   [4] cos pa [5] sin pa [6] 1/q [7] q   [8..15] kind specific:
+//   SERSIC   Ie, 1/Re, 1/n, nu, dnu/dn
+//   EXPDISK  I0, 1/rs
+//   FERRER   I0, 1/rout, a, 2 - b
+//   KING     I0, 1/rc, alpha, A_t, dA_t/drc, dA_t/drt, dA_t/dalpha, rt
+//            with A(r) = (1 + (r/rc)^2)^(-1/alpha), A_t = A(rt)
+//   GAUSSIAN I0, 1/sigma^2, 1/fwhm
+//   MOFFAT   I0, 1/rd, n, d ln rd / dn, 1/fwhm
+//   SKY      Isky
+// ---------------------------------------------------------------------------
+__device__ inline void setup_component(int kind, const double* par, int H, float* cc) {
+  for (int k = 0; k < kCC; ++k) cc[k] = 0.f;
+  if (kind == SKY) {
+    cc[8] = (float)par[0];
+    return;
+  }
+  const double x0 = par[0], y0 = par[1], q = par[2], pa = par[3];
+  const double sx = 0.5 - x0;
+  const double sxi = floor(sx);
+  const double ty = (double)H - 0.5 - y0;
+  const double tyi = floor(ty);
+  cc[0] = __int_as_float((int)sxi);
+  cc[1] = __int_as_float((int)tyi);
+  cc[2] = (float)(sx - sxi);
+  cc[3] = (float)(ty - tyi);
+  cc[4] = (float)cos(pa);
+  cc[5] = (float)sin(pa);
+  cc[6] = (float)(1.0 / q);
+  cc[7] = (float)q;
+  switch (kind) {
+    case SERSIC: {
+      const double n = par[6];
+      cc[8] = (float)par[4];
+      cc[9] = (float)(1.0 / par[5]);
+      cc[10] = (float)(1.0 / n);
+      cc[11] = (float)sersic_nu(n);
+      cc[12] = (float)sersic_dnu(n);
+      break;
+    }
+    case EXPDISK:
+      cc[8] = (float)par[4];
+      cc[9] = (float)(1.0 / par[5]);
+      break;
+    case FERRER:
+      cc[8] = (float)par[4];
+      cc[9] = (float)(1.0 / par[5]);
+      cc[10] = (float)par[6];
+      cc[11] = (float)(2.0 - par[7]);
+      break;
+    case KING: {
+      const double rc = par[5], rt = par[6], al = par[7];
+      const double xt2 = (rt / rc) * (rt / rc);
+      const double vt = 1.0 + xt2;
+      const double At = pow(vt, -1.0 / al);
+      cc[8] = (float)par[4];
+      cc[9] = (float)(1.0 / rc);
+      cc[10] = (float)al;
+      cc[11] = (float)At;
+      cc[12] = (float)(2.0 * xt2 / (al * rc) * At / vt);       // dA_t/drc
+      cc[13] = (float)(-2.0 * rt / (al * rc * rc) * At / vt);  // dA_t/drt
+      cc[14] = (float)(At * log(vt) / (al * al));              // dA_t/dalpha
+      cc[15] = (float)rt;
+      break;
+    }
+    case GAUSSIAN: {
+      const double fw = par[5];
+      const double sig = fw / (2.0 * sqrt(2.0 * log(2.0)));
+      cc[8] = (float)par[4];
+      cc[9] = (float)(1.0 / (sig * sig));
+      cc[10] = (float)(1.0 / fw);
+      break;
+    }
+    case MOFFAT: {
+      const double fw = par[5], n = par[6];
+      const double t = exp2(1.0 / n);
+      const double rd = fw / (2.0 * sqrt(t - 1.0));
+      cc[8] = (float)par[4];
+      cc[9] = (float)(1.0 / rd);
+      cc[10] = (float)n;
+      cc[11] = (float)(t * log(2.0) / (2.0 * n * n * (t - 1.0)));  // d ln rd / dn
+      cc[12] = (float)(1.0 / fw);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One component at stamp pixel (i, j): value and d value / d p_k for each of
+// the component's parameters (physical units, order of the ABI header).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float eval_component(int kind, const float* __restrict__ cc, int i, int j,
+                                                float (&d)[8]) {
+  if (kind == SKY) {
+    d[0] = 1.f;
+    return cc[8];
+  }
+  const float dx = (float)(j + __float_as_int(cc[0])) + cc[2];
+  const float dy = (float)(__float_as_int(cc[1]) - i) + cc[3];
+  const float c = cc[4], s = cc[5], iq = cc[6], q = cc[7];
+  const float X = fmaf(c, dx, s * dy);
+  const float Y = fmaf(-s, dx, c * dy);
+  const float Yq = Y * iq;
+  float r = sqrtf(fmaf(X, X, Yq * Yq));
+  const bool floored = r < kRFloor;
+  if (floored) r = kRFloor;
+  const float ir = 1.f / r;
+  float val = 0.f, dIdr = 0.f;
+  switch (kind) {
+    case SERSIC: {
+      const float Ie = cc[8], iRe = cc[9], in = cc[10], nu = cc[11], dnu = cc[12];
+      const float lt = log2f(r * iRe);            // log2(r / Re)
+      const float u = exp2f(lt * in);             // (r / Re)^(1/n)
+      const float e = exp2f(-nu * (u - 1.f) * kLog2e);
+      val = Ie * e;
+      const float vu = val * nu * u * in;         // I nu u / n
+      dIdr = -vu * ir;
+      d[4] = e;                                   // dI/dIe
+      d[5] = vu * iRe;                            // dI/dRe
+      d[6] = val * fmaf(-dnu, u - 1.f, nu * u * lt * kLn2 * in * in);  // dI/dn
+      break;
+    }
+    case EXPDISK: {
+      const float I0 = cc[8], irs = cc[9];
+      const float e = exp2f(-r * irs * kLog2e);
+      val = I0 * e;
+      dIdr = -val * irs;
+      d[4] = e;
+      d[5] = val * r * irs * irs;
+      break;
+    }
+    case FERRER: {
+      const float I0 = cc[8], irout = cc[9], a = cc[10], ex = cc[11];
+      const float x = r * irout;
+      float sv = 0.f, gg = 0.f;
+      if (x < 1.f) {
+        sv = exp2f(ex * log2f(x));                // (r/rout)^(2-b)
+        gg = 1.f - sv;
+      }
+      if (gg > 0.f) {
+        const float lg = log2f(gg);
+        const float ga1 = exp2f((a - 1.f) * lg);  // g^(a-1)
+        val = I0 * ga1 * gg;
+        const float t = a * I0 * ga1 * ex * sv;
+        dIdr = -t * ir;
+        d[4] = ga1 * gg;
+        d[5] = t * irout;                         // dI/drout
+        d[6] = val * lg * kLn2;                   // dI/da
+        d[7] = a * I0 * ga1 * sv * log2f(x) * kLn2;  // dI/db
+      } else {
+        d[4] = d[5] = d[6] = d[7] = 0.f;
+      }
+      break;
+    }
+    case KING: {
+      const float I0 = cc[8], irc = cc[9], al = cc[10], At = cc[11];
+      const float dAt_rc = cc[12], dAt_rt = cc[13], dAt_al = cc[14], rt = cc[15];
+      const float x2 = r * irc * r * irc;
+      const float v = 1.f + x2;
+      const float lv = log2f(v);
+      const float A = exp2f(-lv / al);
+      const float D = A - At, N = 1.f - At;
+      const float f = D / N;
+      if (r < rt && f > 0.f) {
+        const float lf = log2f(f);
+        const float fa1 = exp2f((al - 1.f) * lf);   // f^(alpha-1)
+        val = I0 * fa1 * f;
+        const float k = I0 * al * fa1 / N;          // dI/dA at fixed A_t
+        const float iN = 1.f / N;
+        dIdr = k * (-2.f * r * irc * irc / al) * A / v;
+        const float dA_rc = 2.f * x2 * irc / al * A / v;
+        d[4] = fa1 * f;
+        d[5] = k * ((dA_rc - dAt_rc) + D * iN * dAt_rc);
+        d[6] = k * dAt_rt * (A - 1.f) * iN;
+        const float dA_al = A * lv * kLn2 / (al * al);
+        d[7] = val * lf * kLn2 + k * ((dA_al - dAt_al) + D * iN * dAt_al);
+      } else {
+        d[4] = d[5] = d[6] = d[7] = 0.f;
+      }
+      break;
+    }
+    case GAUSSIAN: {
+      const float I0 = cc[8], is2 = cc[9], ifw = cc[10];
+      const float e = exp2f(-0.5f * r * r * is2 * kLog2e);
+      val = I0 * e;
+      dIdr = -val * r * is2;
+      d[4] = e;
+      d[5] = val * r * r * is2 * ifw;
+      break;
+    }
+    case MOFFAT: {
+      const float I0 = cc[8], ird = cc[9], n = cc[10], dlrd = cc[11], ifw = cc[12];
+      const float w = r * ird;
+      const float v = fmaf(w, w, 1.f);
+      const float lv = log2f(v);
+      const float e = exp2f(-n * lv);
+      val = I0 * e;
+      const float t = 2.f * n * val * w * w / v;     // rd dI/drd
+      dIdr = -t * ir;
+      d[4] = e;
+      d[5] = t * ifw;                                // dI/dfwhm
+      d[6] = -val * lv * kLn2 + t * dlrd;            // dI/dn
+      break;
+    }
+    default:
+      break;
+  }
+  if (floored) {
+    d[0] = d[1] = d[2] = d[3] = 0.f;
+  } else {
+    const float gr = dIdr * ir;
+    d[0] = gr * fmaf(-X, c, Yq * s * iq);           // dI/dx0
+    d[1] = gr * fmaf(-X, s, -Yq * c * iq);          // dI/dy0
+    d[2] = gr * (-Yq * Yq * iq);                    // dI/dq
+    d[3] = gr * (X * Yq * (q - iq));                // dI/dpa
+  }
+  return val;
+}
+
+}  // namespace gm
