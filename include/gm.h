@@ -74,7 +74,7 @@ extern "C" {
 
 /* per-galaxy fit status (status_out) */
 #define GM_ST_RUNNING 0
-#define GM_ST_CONVERGED 1      /* accepted step with relative chi^2 decrease < tol, or step < xtol */
+#define GM_ST_CONVERGED 1      /* chi^2 decrease < tol, step < xtol or GN decrement < gtol chi^2 */
 #define GM_ST_MAX_ITER 2       /* max_iter model+Jacobian evaluations spent */
 #define GM_ST_STALLED 3        /* lambda exceeded lambda_max without a chi^2 decrease */
 #define GM_ST_SINGULAR 4       /* damped normal matrix not factorisable up to lambda_max */
@@ -132,6 +132,8 @@ typedef struct {
 typedef struct {
   double tol;          /* CONVERGED when an accepted step lowers chi^2 by < tol relative */
   double xtol;         /* CONVERGED when every internal step |du| <= xtol (|u| + xtol) */
+  double gtol;         /* CONVERGED when the Gauss-Newton decrement g^T A^-1 g at the best
+                          point is <= gtol chi^2 (checked at the start and after each accept) */
   int32_t max_iter;    /* model+Jacobian evaluations per galaxy (the start counts as one) */
   double lambda0;      /* initial damping */
   double lambda_up;    /* lambda *= lambda_up on a rejected step or a failed factorisation */
@@ -186,7 +188,7 @@ int gm_chi2_grad(const gm_model_desc *desc, const gm_batch *batch, const double 
  * descent), with the covariance uncertainty of Sec. 5.2.
  *   params_inout [n_gal][n_slots] FP64: starting point in, best fit out
  *                (position angles wrapped to [0, pi))
- *   opts         host; NULL = defaults (tol 1e-6, xtol 1e-10, max_iter 100,
+ *   opts         host; NULL = defaults (tol 1e-6, xtol 1e-10, gtol 1e-10, max_iter 100,
  *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10)
  *   chi2_out     [n_gal] FP64 chi^2 at the best point
  *   dof_out      [n_gal] int32: used pixels - free parameters (Sec. 5.1)

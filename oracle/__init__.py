@@ -79,6 +79,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [
         ("tol", ctypes.c_double),
         ("xtol", ctypes.c_double),
+        ("gtol", ctypes.c_double),
         ("max_iter", ctypes.c_int),
         ("lambda0", ctypes.c_double),
         ("lambda_up", ctypes.c_double),
@@ -129,6 +130,7 @@ class FitOptions:
     """Levenberg-Marquardt controls (same meaning as the CUDA library's)."""
     tol: float = 1e-6
     xtol: float = 1e-10
+    gtol: float = 1e-10
     max_iter: int = 100
     lambda0: float = 1e-1
     lambda_up: float = 10.0
@@ -272,7 +274,7 @@ def fit(spec, params0, psf, image, sigma, mask=None, opts: FitOptions | None = N
     status = np.zeros(G, np.int32)
     sigma_p = np.zeros_like(params)
     d = _desc(spec)
-    o = _Opts(opts.tol, opts.xtol, opts.max_iter, opts.lambda0, opts.lambda_up, opts.lambda_down,
+    o = _Opts(opts.tol, opts.xtol, opts.gtol, opts.max_iter, opts.lambda0, opts.lambda_up, opts.lambda_down,
               opts.lambda_min, opts.lambda_max)
     _load().or_fit_batch(ctypes.byref(d), ctypes.byref(o), G, H, W, K, _ptr(params), _ptr(psf),
                          _ptr(image), _ptr(sigma), _ptr(mask), _ptr(chi2_out), _ptr(dof),

@@ -86,6 +86,7 @@ typedef struct {
 typedef struct {
   double tol;        /* relative chi^2 decrease that ends the fit */
   double xtol;       /* relative step size that ends the fit */
+  double gtol;       /* Gauss-Newton decrement (relative to chi^2) that ends the fit */
   int max_iter;      /* model+Jacobian evaluations allowed */
   double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
 } or_opts;
@@ -377,6 +378,22 @@ static void or_pa_slots(const or_desc *d, int *is_pa) {
     if (d->kind[c] != OR_SKY) is_pa[d->slot[c][3]] = 1;
 }
 
+/* Gauss-Newton decrement g^T A^-1 g: the chi^2 reduction a full Gauss-Newton
+ * step predicts from the current point (A regularised by 1e-12 max(diag A)
+ * on the diagonal).  Negative when A cannot be factorised. */
+static double or_gn_decrement(const double *A, const double *g, int nf) {
+  double M[OR_MAX_SLOTS * OR_MAX_SLOTS], x[OR_MAX_SLOTS];
+  double dmax = 0.0;
+  for (int a = 0; a < nf; ++a) dmax = fmax(dmax, A[a * nf + a]);
+  for (int a = 0; a < nf * nf; ++a) M[a] = A[a];
+  for (int a = 0; a < nf; ++a) M[a * nf + a] += 1e-12 * dmax;
+  if (or_cholesky(M, nf) != 0) return -1.0;
+  or_chol_solve(M, nf, g, x);
+  double s = 0.0;
+  for (int a = 0; a < nf; ++a) s += g[a] * x[a];
+  return s;
+}
+
 /*
  * Levenberg-Marquardt fit of one galaxy, in internal coordinates u.
  *   1. Evaluate chi^2, A, g at the (clamped) start; this is iteration 1.
@@ -390,7 +407,9 @@ static void or_pa_slots(const or_desc *d, int *is_pa) {
  *      CONVERGED if (chi^2 - chi^2')/chi^2 < tol or the step was small.
  *      Otherwise reject: CONVERGED at the kept point if the step was small,
  *      else lambda *= lambda_up and STALLED past lambda_max.
- *   5. MAX_ITER once max_iter evaluations have been spent.
+ *   5. At the start and after every accepted step: CONVERGED when the
+ *      Gauss-Newton decrement g^T A^-1 g <= gtol chi^2 (no step can gain more).
+ *   6. MAX_ITER once max_iter evaluations have been spent.
  * The covariance of Sec. 5.2 is taken from A at the best point; for a log
  * slot sigma_p = p sigma_u.  Position angles are wrapped to [0, pi) at exit.
  */
@@ -432,6 +451,10 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
   double lambda = o->lambda0;
   if (!isfinite(chi2)) status = OR_NONFINITE;
   else if (chi2 == 0.0) status = OR_CONVERGED;
+  if (status == OR_RUNNING) {
+    double gn = or_gn_decrement(A, g, nf);
+    if (gn >= 0.0 && gn <= o->gtol * chi2) status = OR_CONVERGED;
+  }
 
   while (status == OR_RUNNING) {
     if (it >= o->max_iter) { status = OR_MAX_ITER; break; }
@@ -470,6 +493,10 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
       chi2 = chi2t;
       lambda = fmax(lambda * o->lambda_down, o->lambda_min);
       if (act < o->tol || small || chi2 == 0.0) status = OR_CONVERGED;
+      if (status == OR_RUNNING) {
+        double gn = or_gn_decrement(A, g, nf);
+        if (gn >= 0.0 && gn <= o->gtol * chi2) status = OR_CONVERGED;
+      }
     } else if (small) {
       status = OR_CONVERGED; /* the damped step is below resolution: nothing left to gain */
     } else {

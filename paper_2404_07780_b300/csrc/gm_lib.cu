@@ -72,12 +72,19 @@ int check_desc(const gm_model_desc* d) {
   return GM_OK;
 }
 
-int check_batch(const gm_batch* b, bool need_data) {
+// Sizes only (what the workspace queries need).
+int check_sizes(const gm_batch* b) {
   if (!b) return fail(GM_E_INVAL, "batch is NULL");
   if (b->n_gal < 0) return fail(GM_E_INVAL, "n_gal=%d < 0", b->n_gal);
   if (b->H < 1 || b->H > 4096 || b->W < 1 || b->W > 4096)
     return fail(GM_E_INVAL, "stamp %dx%d outside 1..4096", b->H, b->W);
   if (b->K < 1 || b->K > 63 || (b->K % 2) == 0) return fail(GM_E_INVAL, "PSF side K=%d must be odd, 1..63", b->K);
+  return GM_OK;
+}
+
+int check_batch(const gm_batch* b, bool need_data) {
+  int rc = check_sizes(b);
+  if (rc) return rc;
   if (b->n_gal > 0) {
     if (!b->psf) return fail(GM_E_INVAL, "batch.psf is NULL");
     if (need_data && (!b->image || !b->sigma)) return fail(GM_E_INVAL, "batch.image/sigma is NULL");
@@ -333,6 +340,7 @@ LMOpts lm_opts(const gm_fit_opts* o) {
   if (o) {
     L.tol = o->tol;
     L.xtol = o->xtol;
+    L.gtol = o->gtol;
     L.max_iter = o->max_iter;
     L.lambda0 = o->lambda0;
     L.lambda_up = o->lambda_up;
@@ -342,6 +350,7 @@ LMOpts lm_opts(const gm_fit_opts* o) {
   } else {
     L.tol = 1e-6;
     L.xtol = 1e-10;
+    L.gtol = 1e-10;
     L.max_iter = 100;
     L.lambda0 = 0.1;
     L.lambda_up = 10.0;
@@ -361,7 +370,7 @@ int gm_version(void) { return 100; }
 const char* gm_last_error(void) { return g_err; }
 
 size_t gm_model_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
-  if (!desc || !batch || check_desc(desc) || check_batch(batch, false)) return 0;
+  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
   return ws_model(desc, batch).total;
 }
 
@@ -401,7 +410,7 @@ int gm_model(const gm_model_desc* desc, const gm_batch* batch, const double* par
 }
 
 size_t gm_chi2_grad_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
-  if (!desc || !batch || check_desc(desc) || check_batch(batch, false)) return 0;
+  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
   return ws_chi2(desc, batch, count_free(desc)).total;
 }
 
@@ -443,7 +452,7 @@ int gm_chi2_grad(const gm_model_desc* desc, const gm_batch* batch, const double*
 }
 
 size_t gm_fit_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
-  if (!desc || !batch || check_desc(desc) || check_batch(batch, false)) return 0;
+  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
   return ws_fit(desc, batch, count_free(desc)).total;
 }
 

@@ -29,7 +29,7 @@ struct DescDev {
 };
 
 struct LMOpts {
-  double tol, xtol;
+  double tol, xtol, gtol;
   int max_iter;
   double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
 };
@@ -181,13 +181,31 @@ __device__ inline double packed(const double* Ap, int P, int f, int h) {
   return Ap[f * P - (f * (f - 1)) / 2 + (h - f)];
 }
 
+// Gauss-Newton decrement g^T A^-1 g (A packed, regularised by 1e-12 max(diag A)
+// on the diagonal): the chi^2 reduction a full Gauss-Newton step predicts.
+// Negative when A cannot be factorised.
+__device__ inline double gn_decrement(const double* Ap, const double* g, int P) {
+  double M[kMaxSlots * kMaxSlots], x[kMaxSlots];
+  double dmax = 0.0;
+  for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ap, P, f, f));
+  for (int f = 0; f < P; ++f)
+    for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ap, P, f, h);
+  for (int f = 0; f < P; ++f) M[f * P + f] += 1e-12 * dmax;
+  if (!cholesky(M, P)) return -1.0;
+  chol_solve(M, P, g, x);
+  double s = 0.0;
+  for (int f = 0; f < P; ++f) s += g[f] * x[f];
+  return s;
+}
+
 // One LM step for every galaxy evaluated in this iteration (list `cur`):
 // sum the tile partials of the pass, accept or reject the evaluated point,
 // test convergence, solve the damped normal equations for the next trial point
 // and queue the galaxy for the next pass (list `cur ^ 1`).  The rules are the
 // ones the FP64 oracle states: accept when chi^2 drops; CONVERGED when an
-// accepted step lowers chi^2 by less than tol relative or any evaluated step
-// is below xtol; STALLED / SINGULAR past lambda_max; MAX_ITER at max_iter.
+// accepted step lowers chi^2 by less than tol relative, any evaluated step
+// is below xtol, or the Gauss-Newton decrement at the best point is at most
+// gtol chi^2; STALLED / SINGULAR past lambda_max; MAX_ITER at max_iter.
 __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O, int cur, int H,
                           int n_tiles, const double* __restrict__ partial, float* cconst, float* scale) {
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
@@ -211,6 +229,7 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
   const int it = S.it[g] + 1;
   S.it[g] = it;
   double lam = S.lam[g];
+  bool accepted = false;
   if (it == 1) {
     if (!isfinite(chi2_t)) {
       st = ST_NONFINITE;
@@ -218,6 +237,7 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
       for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
       for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
       S.chi2_b[g] = chi2_t;
+      accepted = true;
       if (chi2_t == 0.0) st = ST_CONVERGED;
     }
   } else {
@@ -235,6 +255,7 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
       for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
       S.chi2_b[g] = chi2_t;
       lam = fmax(lam * O.lambda_down, O.lambda_min);
+      accepted = true;
       if (act < O.tol || small || chi2_t == 0.0) st = ST_CONVERGED;
     } else if (small) {
       st = ST_CONVERGED;
@@ -244,6 +265,10 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
     }
   }
 
+  if (st == ST_RUNNING && accepted) {
+    const double gn = gn_decrement(Ab, gb, P);
+    if (gn >= 0.0 && gn <= O.gtol * S.chi2_b[g]) st = ST_CONVERGED;
+  }
   if (st == ST_RUNNING && it >= O.max_iter) st = ST_MAX_ITER;
   if (st == ST_RUNNING) {
     double M[kMaxSlots * kMaxSlots], delta[kMaxSlots];

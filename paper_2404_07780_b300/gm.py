@@ -1,0 +1,271 @@
+"""Thin Python binding of libgm (include/gm.h): argument marshalling only.
+
+Every step of the fitting path runs in the CUDA library; this module turns
+torch CUDA tensors into the pointers and sizes of the C ABI, allocates the
+caller-owned workspace with torch, and raises on any nonzero return.  There is
+no CPU fallback: without the compiled library or a CUDA device every call
+raises.
+
+Function names follow the C ABI: ``gm_model``, ``gm_chi2_grad``,
+``gm_fit_batch``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgm.so")
+
+MAX_COMP = 8
+MAX_SLOTS = 16
+KIND = {"sersic": 1, "expdisk": 2, "ferrer": 3, "king": 4, "gaussian": 5, "moffat": 6, "sky": 7}
+STATUS = {0: "RUNNING", 1: "CONVERGED", 2: "MAX_ITER", 3: "STALLED", 4: "SINGULAR", 5: "NONFINITE",
+          6: "BAD_INPUT", 7: "NO_DOF"}
+ST_CONVERGED = 1
+
+# every symbol include/gm.h declares
+EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model",
+           "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch")
+
+
+class GMError(RuntimeError):
+    pass
+
+
+class gm_component(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("convolve", ctypes.c_int32), ("slot", ctypes.c_int32 * 8)]
+
+
+class gm_model_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_comp", ctypes.c_int32),
+        ("comp", gm_component * MAX_COMP),
+        ("n_slots", ctypes.c_int32),
+        ("is_free", ctypes.c_uint8 * MAX_SLOTS),
+        ("is_log", ctypes.c_uint8 * MAX_SLOTS),
+        ("lo", ctypes.c_double * MAX_SLOTS),
+        ("hi", ctypes.c_double * MAX_SLOTS),
+    ]
+
+
+class gm_batch(ctypes.Structure):
+    _fields_ = [
+        ("n_gal", ctypes.c_int32),
+        ("H", ctypes.c_int32),
+        ("W", ctypes.c_int32),
+        ("K", ctypes.c_int32),
+        ("image", ctypes.c_void_p),
+        ("sigma", ctypes.c_void_p),
+        ("mask", ctypes.c_void_p),
+        ("psf", ctypes.c_void_p),
+    ]
+
+
+class gm_fit_opts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("xtol", ctypes.c_double),
+        ("gtol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("lambda0", ctypes.c_double),
+        ("lambda_up", ctypes.c_double),
+        ("lambda_down", ctypes.c_double),
+        ("lambda_min", ctypes.c_double),
+        ("lambda_max", ctypes.c_double),
+    ]
+
+
+@dataclass
+class FitOptions:
+    tol: float = 1e-6
+    xtol: float = 1e-10
+    gtol: float = 1e-10
+    max_iter: int = 100
+    lambda0: float = 1e-1
+    lambda_up: float = 10.0
+    lambda_down: float = 0.1
+    lambda_min: float = 1e-7
+    lambda_max: float = 1e10
+
+    def to_c(self) -> gm_fit_opts:
+        return gm_fit_opts(self.tol, self.xtol, self.gtol, self.max_iter, self.lambda0, self.lambda_up, self.lambda_down,
+                           self.lambda_min, self.lambda_max)
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree libgm.so (build it with paper_2404_07780_b300.build.build_lib)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GMError(f"{LIB_PATH} is missing: build the CUDA library first (python -c "
+                          "'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, S = ctypes.c_void_p, ctypes.c_size_t
+        lib.gm_version.restype = ctypes.c_int
+        lib.gm_version.argtypes = []
+        lib.gm_last_error.restype = ctypes.c_char_p
+        lib.gm_last_error.argtypes = []
+        for name in ("gm_model_workspace_bytes", "gm_chi2_grad_workspace_bytes", "gm_fit_workspace_bytes"):
+            f = getattr(lib, name)
+            f.restype = S
+            f.argtypes = [P, P]
+        lib.gm_model.restype = ctypes.c_int
+        lib.gm_model.argtypes = [P, P, P, P, P, P, S, P]
+        lib.gm_chi2_grad.restype = ctypes.c_int
+        lib.gm_chi2_grad.argtypes = [P, P, P, P, P, P, P, S, P]
+        lib.gm_fit_batch.restype = ctypes.c_int
+        lib.gm_fit_batch.argtypes = [P, P, P, P, P, P, P, P, P, P, S, P]
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise GMError(f"{what} failed ({rc}): {load().gm_last_error().decode()}")
+
+
+def desc_from_spec(spec) -> gm_model_desc:
+    """C descriptor from a ModelSpec (see synth.ModelSpec)."""
+    d = gm_model_desc()
+    d.n_comp = len(spec.components)
+    if d.n_comp > MAX_COMP or spec.n_slots > MAX_SLOTS:
+        raise GMError("model too large for the C descriptor")
+    for c, comp in enumerate(spec.components):
+        d.comp[c].kind = KIND[comp.kind]
+        d.comp[c].convolve = 1 if comp.convolve else 0
+        for k, s in enumerate(comp.slots):
+            d.comp[c].slot[k] = int(s)
+    d.n_slots = spec.n_slots
+    for s in range(spec.n_slots):
+        d.is_free[s] = 1 if spec.free[s] else 0
+        d.is_log[s] = 1 if spec.log[s] else 0
+        d.lo[s] = float(spec.lo[s])
+        d.hi[s] = float(spec.hi[s])
+    return d
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _cuda_tensor(t, dtype, name):
+    import torch
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise GMError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise GMError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+def make_batch(image, sigma, mask, psf):
+    """gm_batch over CUDA tensors image/sigma [G,H,W] f32, mask [G,H,W] u8 or None, psf [G,K,K] f32.
+
+    Returns (struct, keep) where keep holds the contiguous tensors alive."""
+    import torch
+    psf = _cuda_tensor(psf, torch.float32, "psf")
+    G, K = psf.shape[0], psf.shape[-1]
+    image = _cuda_tensor(image, torch.float32, "image")
+    sigma = _cuda_tensor(sigma, torch.float32, "sigma")
+    mask = _cuda_tensor(mask, torch.uint8, "mask")
+    ref = image if image is not None else None
+    if ref is None:
+        raise GMError("image is required to size the batch (use model_batch for gm_model)")
+    H, W = ref.shape[-2:]
+    b = gm_batch(G, H, W, K, _ptr(image), _ptr(sigma), _ptr(mask), _ptr(psf))
+    return b, (image, sigma, mask, psf)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def gm_model(spec_or_desc, params, psf, H: int, W: int, components: bool = False):
+    """Forward model of every galaxy: returns model [G,H,W] (and [G,n_comp,H,W] if components)."""
+    import torch
+    lib = load()
+    d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
+    psf = _cuda_tensor(psf, torch.float32, "psf")
+    params = _cuda_tensor(params, torch.float64, "params")
+    G, K = psf.shape[0], psf.shape[-1]
+    b = gm_batch(G, H, W, K, None, None, None, _ptr(psf))
+    dev = psf.device
+    model = torch.empty((G, H, W), dtype=torch.float32, device=dev)
+    comp = torch.empty((G, d.n_comp, H, W), dtype=torch.float32, device=dev) if components else None
+    nbytes = lib.gm_model_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    _check(lib.gm_model(ctypes.byref(d), ctypes.byref(b), _ptr(params), _ptr(model), _ptr(comp), _ptr(ws), nbytes,
+                        _stream()), "gm_model")
+    return (model, comp) if components else model
+
+
+def gm_chi2_grad(spec_or_desc, params, image, sigma, mask, psf, want_grad: bool = True, want_jtj: bool = False):
+    """chi^2 [G], d chi^2/dp [G,S] (physical units) and J^T W J [G,S,S] (or None)."""
+    import torch
+    lib = load()
+    d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
+    b, keep = make_batch(image, sigma, mask, psf)
+    params = _cuda_tensor(params, torch.float64, "params")
+    G, S = b.n_gal, d.n_slots
+    dev = keep[0].device
+    chi2 = torch.empty(G, dtype=torch.float64, device=dev)
+    grad = torch.empty((G, S), dtype=torch.float64, device=dev) if want_grad else None
+    jtj = torch.empty((G, S, S), dtype=torch.float64, device=dev) if want_jtj else None
+    nbytes = lib.gm_chi2_grad_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    _check(lib.gm_chi2_grad(ctypes.byref(d), ctypes.byref(b), _ptr(params), _ptr(chi2), _ptr(grad), _ptr(jtj),
+                            _ptr(ws), nbytes, _stream()), "gm_chi2_grad")
+    return chi2, grad, jtj
+
+
+class Fitter:
+    """Holds the workspace and output buffers of gm_fit_batch for one batch shape."""
+
+    def __init__(self, spec_or_desc, G: int, H: int, W: int, K: int, device="cuda"):
+        import torch
+        self.lib = load()
+        self.d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
+        self.shape = (G, H, W, K)
+        b = gm_batch(G, H, W, K, None, None, None, None)
+        self.ws_bytes = self.lib.gm_fit_workspace_bytes(ctypes.byref(self.d), ctypes.byref(b))
+        S = self.d.n_slots
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=device)
+        self.chi2 = torch.empty(G, dtype=torch.float64, device=device)
+        self.dof = torch.empty(G, dtype=torch.int32, device=device)
+        self.iters = torch.empty(G, dtype=torch.int32, device=device)
+        self.status = torch.empty(G, dtype=torch.int32, device=device)
+        self.sigma_p = torch.empty((G, S), dtype=torch.float64, device=device)
+
+    def fit(self, params, image, sigma, mask, psf, opts: FitOptions | None = None):
+        """Fit in place: params [G,S] f64 CUDA is overwritten with the best fit."""
+        import torch
+        b, keep = make_batch(image, sigma, mask, psf)
+        if (b.n_gal, b.H, b.W, b.K) != self.shape:
+            raise GMError(f"batch shape {(b.n_gal, b.H, b.W, b.K)} != fitter shape {self.shape}")
+        if not (params.is_cuda and params.dtype == torch.float64 and params.is_contiguous()):
+            raise GMError("params must be a contiguous float64 CUDA tensor")
+        o = (opts or FitOptions()).to_c()
+        _check(self.lib.gm_fit_batch(ctypes.byref(self.d), ctypes.byref(b), _ptr(params), ctypes.byref(o),
+                                     _ptr(self.chi2), _ptr(self.dof), _ptr(self.iters), _ptr(self.status),
+                                     _ptr(self.sigma_p), _ptr(self.ws), self.ws_bytes, _stream()), "gm_fit_batch")
+        return {"params": params, "chi2": self.chi2, "dof": self.dof, "iters": self.iters, "status": self.status,
+                "sigma_p": self.sigma_p}
+
+
+def gm_fit_batch(spec_or_desc, params0, image, sigma, mask, psf, opts: FitOptions | None = None):
+    """LM fit of every galaxy; returns a dict of CUDA tensors (params is a fitted copy of params0)."""
+    G, H, W = image.shape
+    K = psf.shape[-1]
+    f = Fitter(spec_or_desc, G, H, W, K, device=image.device)
+    params = params0.clone().contiguous()
+    out = f.fit(params, image, sigma, mask, psf, opts)
+    return {k: v.clone() if k != "params" else v for k, v in out.items()}

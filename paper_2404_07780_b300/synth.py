@@ -141,14 +141,9 @@ def bulge_bar_nucleus_sky(H: int, W: int) -> ModelSpec:
     return s
 
 
-def with_contaminants(base: ModelSpec, n: int, H: int, W: int) -> ModelSpec:
-    """`base` plus n free-standing Gaussian sources (used to render truth scenes)."""
-    s = ModelSpec(components=[Component(c.kind, c.convolve, list(c.slots)) for c in base.components],
-                  names=list(base.names), free=list(base.free), log=list(base.log),
-                  lo=list(base.lo), hi=list(base.hi))
-    for k in range(n):
-        s.add("gaussian", f"cont{k}", H, W)
-    return s
+def contaminant_spec(H: int, W: int) -> ModelSpec:
+    """One free-standing Gaussian source (convolved): the contaminants of truth scenes."""
+    return ModelSpec().add("gaussian", "cont", H, W)
 
 
 # --------------------------------------------------------------------------
@@ -165,20 +160,32 @@ def _logu(g: np.random.Generator, lo: float, hi: float, size) -> np.ndarray:
 
 @dataclass
 class Batch:
-    """One synthetic batch of equal-size stamps (all arrays numpy, FP64 unless noted)."""
+    """One synthetic batch of equal-size stamps (all arrays numpy, FP64 unless noted).
+
+    The truth scene is the fitted model at `truth` plus, for every k, the
+    contaminant component at `contaminants[:, k]` (zero amplitude when unused)."""
     spec: ModelSpec            # the fitted model
-    truth_spec: ModelSpec      # the model used to render the truth scene
     H: int
     W: int
     K: int
-    truth: np.ndarray          # [G, truth_spec.n_slots]
+    truth: np.ndarray          # [G, spec.n_slots]
     init: np.ndarray           # [G, spec.n_slots] default starting point
     psf_kind: str              # "gaussian" or "moffat"
     psf_par: np.ndarray        # [G, n] component parameters of the PSF profile
     mask: np.ndarray | None    # [G, H, W] uint8, nonzero = excluded
     z: np.ndarray              # [G, H, W] standard normal noise draws
+    contaminants: np.ndarray | None = None   # [G, n_blobs, 6] Gaussian parameters
     sky_var: float = 4.0
     gain: float = 4.0
+
+    def truth_parts(self):
+        """(spec, params [G, n_slots]) pairs whose model images sum to the truth scene."""
+        parts = [(self.spec, self.truth)]
+        if self.contaminants is not None:
+            cs = contaminant_spec(self.H, self.W)
+            for k in range(self.contaminants.shape[1]):
+                parts.append((cs, self.contaminants[:, k]))
+        return parts
 
     @property
     def G(self) -> int:
@@ -208,8 +215,7 @@ def draw_small(seed: int = 0, G: int = 16, H: int = 64, W: int = 64, K: int = 15
         g.uniform(0, 5, G)], 1)
     init = np.tile(np.array([W / 2, H / 2, 0.65, math.pi / 2, 10.0, 6.0, math.sqrt(2.0), 2.5]), (G, 1))
     z = g.standard_normal((G, H, W))
-    return Batch(spec, spec, H, W, K, truth, init, "gaussian", psf_params("gaussian", np.full(G, 1.5), K),
-                 None, z)
+    return Batch(spec, H, W, K, truth, init, "gaussian", psf_params("gaussian", np.full(G, 1.5), K), None, z)
 
 
 def draw_sdss(seed: int = 1000, G: int = 8192, H: int = 128, W: int = 128, K: int = 41,
@@ -224,7 +230,6 @@ def draw_sdss(seed: int = 1000, G: int = 8192, H: int = 128, W: int = 128, K: in
     peak is 5-50 sky sigma."""
     g = rng(seed)
     spec = single_sersic_sky(H, W)
-    tspec = with_contaminants(spec, max_blobs, H, W)
     x0 = W / 2 + g.uniform(-2, 2, G)
     y0 = H / 2 + g.uniform(-2, 2, G)
     gal = np.stack([x0, y0, g.uniform(0.2, 1.0, G), g.uniform(0, math.pi, G),
@@ -256,11 +261,10 @@ def draw_sdss(seed: int = 1000, G: int = 8192, H: int = 128, W: int = 128, K: in
     # unused contaminant slots: zero amplitude, harmless geometry
     unused = cont[:, :, 4] == 0
     cont[unused] = [W / 2, H / 2, 1.0, 0.0, 0.0, 1.0]
-    truth = np.concatenate([gal, cont.reshape(G, -1)], 1)
     init = np.tile(np.array([W / 2, H / 2, 0.6, math.pi / 2, math.sqrt(1000.0), 13.5, math.sqrt(3.0), 2.5]),
                    (G, 1))
     z = g.standard_normal((G, H, W), dtype=np.float32)
-    return Batch(spec, tspec, H, W, K, truth, init, "moffat", psf_params("moffat", fwhm, K), mask, z)
+    return Batch(spec, H, W, K, gal, init, "moffat", psf_params("moffat", fwhm, K), mask, z, cont)
 
 
 def noisy_image(model_true: np.ndarray, z: np.ndarray, sky_var: float = 4.0, gain: float = 4.0):
@@ -270,5 +274,5 @@ def noisy_image(model_true: np.ndarray, z: np.ndarray, sky_var: float = 4.0, gai
 
 
 def galaxy_slots(batch: Batch) -> np.ndarray:
-    """The truth parameters restricted to the fitted model's slots."""
-    return batch.truth[:, : batch.spec.n_slots]
+    """The truth parameters of the fitted model."""
+    return batch.truth

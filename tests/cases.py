@@ -1,0 +1,86 @@
+"""Seeded test cases shared by the parity tests.
+
+Inputs are drawn by paper_2404_07780_b300.synth (random numbers only) and
+rendered by the FP64 oracle; everything the CUDA path receives is the float32
+rounding of these arrays, and the oracle is re-run on exactly those rounded
+values, so both sides see identical bits.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+from paper_2404_07780_b300 import synth
+
+
+def psf_image(kind: str, par, K: int) -> np.ndarray:
+    """Unit-sum PSF rendered by the oracle, rounded to float32."""
+    p = oracle.component_image(kind, par, K, K)
+    return (p / p.sum()).astype(np.float32)
+
+
+def psf_stack(batch: synth.Batch) -> np.ndarray:
+    return np.stack([psf_image(batch.psf_kind, batch.psf_par[g], batch.K) for g in range(batch.G)])
+
+
+class Case:
+    """A batch ready for both paths: float32 arrays plus the float64 views the oracle uses."""
+
+    def __init__(self, spec, params, psf, image, sigma, mask, H, W, init=None, truth=None):
+        self.spec = spec
+        self.params = np.ascontiguousarray(params, np.float64)
+        self.init = None if init is None else np.ascontiguousarray(init, np.float64)
+        self.truth = truth
+        self.psf = np.ascontiguousarray(psf, np.float32)
+        self.image = np.ascontiguousarray(image, np.float32)
+        self.sigma = np.ascontiguousarray(sigma, np.float32)
+        self.mask = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+        self.H, self.W = H, W
+
+    @property
+    def G(self):
+        return self.params.shape[0]
+
+    def torch(self, device="cuda"):
+        import torch
+        t = lambda a: None if a is None else torch.from_numpy(a).to(device)
+        return dict(params=t(self.params), psf=t(self.psf), image=t(self.image), sigma=t(self.sigma),
+                    mask=t(self.mask))
+
+
+def from_batch(b: synth.Batch, at: str = "init") -> Case:
+    """Render the truth scene of a synth batch with the oracle and add the drawn noise."""
+    psf = psf_stack(b)
+    Mt = sum(oracle.model_images(sp, pa, psf.astype(np.float64), b.H, b.W) for sp, pa in b.truth_parts())
+    D, S = synth.noisy_image(Mt, b.z.astype(np.float64), b.sky_var, b.gain)
+    truth = synth.galaxy_slots(b)
+    params = b.init if at == "init" else truth
+    return Case(b.spec, params, psf, D, S, b.mask, b.H, b.W, init=b.init, truth=truth)
+
+
+def scale_of(spec) -> np.ndarray:
+    """Per-slot absolute scale used for parameter tolerances: 1 px, 1 rad, 1 sky unit, else |p|."""
+    s = np.zeros(spec.n_slots)
+    for i, name in enumerate(spec.names):
+        role = name.split(".")[-1]
+        s[i] = 1.0 if role in ("x0", "y0", "pa", "Isky") else 0.0
+    return s
+
+
+def pa_slots(spec):
+    return [i for i, n in enumerate(spec.names) if n.endswith(".pa")]
+
+
+def q_of_pa(spec, pa_slot):
+    """The axis-ratio slot of the component whose position angle lives in pa_slot."""
+    for comp in spec.components:
+        if comp.kind != "sky" and comp.slots[3] == pa_slot:
+            return comp.slots[2]
+    return None
+
+
+def angle_diff(a, b):
+    d = np.abs(a - b) % math.pi
+    return np.minimum(d, math.pi - d)

@@ -348,7 +348,7 @@ def test_lm_sky_only_closed_form():
     M = (g.uniform(size=(1, H, W)) < 0.2).astype(np.uint8)
     w = (M == 0) / S ** 2
     res = oracle.fit(spec, [[0.0]], np.ones((1, 1, 1)), D, S, M,
-                     oracle.FitOptions(tol=1e-14, max_iter=50))
+                     oracle.FitOptions(gtol=0.0, tol=1e-14, max_iter=50))
     assert res["params"][0, 0] == pytest.approx((w * D).sum() / w.sum(), rel=1e-10)
     assert res["sigma_p"][0, 0] == pytest.approx(w.sum() ** -0.5, rel=1e-8)
     assert res["dof"][0] == int((M == 0).sum()) - 1
@@ -365,7 +365,7 @@ def test_lm_covariance_of_linear_model():
     S = g.uniform(0.8, 1.5, (1, H, W))
     D = (7.0 * tmpl + 2.0 + S * g.standard_normal((H, W)))
     p0 = np.array([[10.2, 9.9, 0.8, 0.5, 1.0, 4.0, 0.0]])
-    res = oracle.fit(spec, p0, np.ones((1, 1, 1)), D, S, None, oracle.FitOptions(tol=1e-15, max_iter=50))
+    res = oracle.fit(spec, p0, np.ones((1, 1, 1)), D, S, None, oracle.FitOptions(gtol=0.0, tol=1e-15, max_iter=50))
     J = np.stack([tmpl.ravel(), np.ones(H * W)], 1)
     w = 1 / S.ravel() ** 2
     A = J.T @ (w[:, None] * J)
@@ -376,7 +376,7 @@ def test_lm_covariance_of_linear_model():
     # fitted in log space the amplitude has sigma_p = p sigma_(ln p): the same error bar
     spec.log[spec.slot("g.I0")] = True
     res = oracle.fit(spec, p0 * [1, 1, 1, 1, 5.0, 1, 1], np.ones((1, 1, 1)), D, S, None,
-                     oracle.FitOptions(tol=1e-15, max_iter=80))
+                     oracle.FitOptions(gtol=0.0, tol=1e-15, max_iter=80))
     np.testing.assert_allclose(res["params"][0, [4, 6]], sol, rtol=1e-9)
     np.testing.assert_allclose(res["sigma_p"][0, [4, 6]], np.sqrt(np.diag(cov)), rtol=1e-6)
 
@@ -390,7 +390,7 @@ def test_lm_exact_recovery_noiseless():
     # start a few percent away from the truth (the default start can fall into
     # other local minima; recovery, not the basin, is what this pins)
     start = truth * (1 + 0.04 * np.random.default_rng(1).uniform(-1, 1, truth.shape))
-    res = oracle.fit(b.spec, start, psf, D, S, None, oracle.FitOptions(tol=1e-15, xtol=1e-11, max_iter=200))
+    res = oracle.fit(b.spec, start, psf, D, S, None, oracle.FitOptions(gtol=0.0, tol=1e-15, xtol=1e-11, max_iter=200))
     assert (res["status"] == 1).all(), res["status"]
     err = np.abs(res["params"] - truth)
     err[:, 3] = np.minimum(err[:, 3], math.pi - err[:, 3])  # PA modulo pi
@@ -408,7 +408,7 @@ def test_lm_matches_minpack_on_tiny_galaxy():
     Mt = oracle.model_images(spec, truth, psf, H, W)
     D, S = synth.noisy_image(Mt, np.random.default_rng(2).standard_normal(Mt.shape))
     init = np.array([[8.0, 8.0, 0.6, 1.0, 12.0, 4.0, 1.0, 1.0]])
-    res = oracle.fit(spec, init, psf, D, S, None, oracle.FitOptions(tol=1e-14, max_iter=300))
+    res = oracle.fit(spec, init, psf, D, S, None, oracle.FitOptions(gtol=0.0, tol=1e-14, max_iter=300))
     assert res["status"][0] == 1
 
     logs = np.array(spec.log)
