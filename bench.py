@@ -1,0 +1,382 @@
+"""Benchmark: converged galaxy fits/s on the SDSS-shaped single-Sersic workload.
+
+Workload (synthetic, stands in for the paper's 8,289 SDSS g-band stamps):
+8,192 galaxies, 128x128 float32 stamps, Sersic + sky (8 free parameters),
+per-galaxy Moffat PSF (beta 3, FWHM 1.2-1.8 px, 41x41), sigma^2 = 4 + M/4,
+uint8 masks hiding 0-5 Gaussian contaminants, default-start Levenberg-Marquardt
+to a relative chi^2 decrease < 1e-6 (max 200 evaluations).
+
+A step is one gm_fit_batch call over the whole batch (validation, set-up,
+every LM iteration of fused model+Jacobian+chi^2 pass and FP64 step, final
+covariance).  `value` counts galaxies that ended CONVERGED.  Inputs are 1.2 GB
+per batch, larger than the 126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+The reference arm (--impl reference) is the FP64 CPU oracle timed on this
+host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+_ROOT = os.path.dirname(os.path.abspath(__file__))
+if _ROOT not in sys.path:
+    sys.path.insert(0, _ROOT)
+
+from paper_2404_07780_b300 import synth  # noqa: E402
+
+METRIC = "converged galaxy fits/sec on 1 B300 at matched χ² tol; model+Jacobian Gpix/s"
+UNIT = "fits/s"
+TOL = 1e-6
+MAX_ITER = 200
+PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
+
+
+def workload_config(G, H, K):
+    return {"workload": f"SDSS-shaped single-Sersic+sky fit, {G} x {H}x{H} float32 stamps, per-galaxy Moffat PSF "
+                        f"{K}x{K}, masked contaminants, default-start LM to dchi2/chi2<{TOL:g}",
+            "galaxies": G, "stamp": [H, H], "psf": [K, K], "free_params": 8, "tol": TOL, "max_iter": MAX_ITER,
+            "l2": "inputs 1.2 GB per batch > 126 MB L2 (no flush)"}
+
+
+# ---------------------------------------------------------------------------
+# multi-process plumbing (one process per GPU; galaxies are independent, so
+# every rank fits its own batch: weak scaling, no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a host scalar over ranks (the timing reduction; no data path)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank draws its own batch of the same recipe."""
+    return 1000 + rank
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# workload on the device (rendered by the library's own forward model)
+# ---------------------------------------------------------------------------
+
+def render_workload(b: synth.Batch, device):
+    """PSFs, truth images, noisy data and sigma maps on the device, rendered by gm_model."""
+    import torch
+    from paper_2404_07780_b300 import gm
+    G, K = b.G, b.K
+    psfspec = synth.ModelSpec().add("moffat", "psf", K, K, convolve=False)
+    one = torch.ones((G, 1, 1), dtype=torch.float32, device=device)
+    psf = gm.gm_model(psfspec, torch.from_numpy(b.psf_par).to(device), one, K, K)
+    psf = (psf / psf.sum((1, 2), keepdim=True)).contiguous()
+    Mt = torch.zeros((G, b.H, b.W), dtype=torch.float32, device=device)
+    for spec, par in b.truth_parts():
+        Mt += gm.gm_model(spec, torch.from_numpy(np.ascontiguousarray(par)).to(device), psf, b.H, b.W)
+    sigma = torch.sqrt(b.sky_var + Mt.clamp(min=0) / b.gain)
+    image = Mt + sigma * torch.from_numpy(b.z).to(device)
+    mask = torch.from_numpy(b.mask).to(device) if b.mask is not None else None
+    return image.contiguous(), sigma.contiguous(), mask, psf
+
+
+def inbounds_taps(H, W, K):
+    """Sum over output pixels of the PSF taps that fall inside the stamp."""
+    c = (K - 1) // 2
+    rows = sum(min(K, H - i + c) - max(0, c - i) for i in range(H))
+    cols = sum(min(K, W - j + c) - max(0, c - j) for j in range(W))
+    return rows * cols
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_fit(b: synth.Batch, idx):
+    """Render galaxies idx of the workload with the oracle and fit them with its LM; returns (converged, seconds)."""
+    import oracle
+    sub = synth.Batch(b.spec, b.H, b.W, b.K, b.truth[idx], b.init[idx], b.psf_kind, b.psf_par[idx],
+                      None if b.mask is None else b.mask[idx], b.z[idx],
+                      None if b.contaminants is None else b.contaminants[idx])
+    psf = np.stack([oracle.component_image(sub.psf_kind, sub.psf_par[g], sub.K, sub.K) for g in range(len(idx))])
+    psf = (psf / psf.sum((1, 2), keepdims=True)).astype(np.float32).astype(np.float64)
+    Mt = sum(oracle.model_images(sp, pa, psf, sub.H, sub.W) for sp, pa in sub.truth_parts())
+    D, S = synth.noisy_image(Mt, sub.z.astype(np.float64), sub.sky_var, sub.gain)
+    D = D.astype(np.float32).astype(np.float64)
+    S = S.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    r = oracle.fit(sub.spec, sub.init, psf, D, S, sub.mask, oracle.FitOptions(tol=TOL, max_iter=MAX_ITER))
+    dt = time.perf_counter() - t0
+    return int((r["status"] == 1).sum()), dt
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, world, rank):
+    """The FP64 oracle as it stands, on this host's cores, on bounded samples of the workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    per_step = max(1, min(64, threads))
+    b = synth.draw_sdss(seed=rank_seed(0), G=per_step * (args.warmup + args.steps))
+    conv = 0
+    secs = 0.0
+    for s in range(args.warmup + args.steps):
+        idx = np.arange(s * per_step, (s + 1) * per_step)
+        c, dt = oracle_sample_fit(b, idx)
+        if s >= args.warmup:
+            conv += c
+            secs += dt
+    value = conv / secs if secs > 0 else 0.0
+    G, H, K = args.galaxies, 128, 41
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(G, H, K),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} galaxies of the workload per step, {args.steps} timed steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2404_07780_b300 import gm
+    from paper_2404_07780_b300.build import build_lib
+
+    build_lib()
+    gm.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    G, H, K = args.galaxies, 128, 41
+    b = synth.draw_sdss(seed=rank_seed(rank), G=G, H=H, W=H, K=K)
+    image, sigma, mask, psf = render_workload(b, dev)
+    p0 = torch.from_numpy(b.init).to(dev)
+    fitter = gm.Fitter(b.spec, G, H, H, K, device=dev)
+    opts = gm.FitOptions(tol=TOL, max_iter=MAX_ITER)
+    params = torch.empty_like(p0)
+
+    def step():
+        params.copy_(p0)
+        return fitter.fit(params, image, sigma, mask, psf, opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    converged = 0
+    fused_ms = 0.0
+    evals = 0
+    launches = 0
+    iters = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        # library calls only: torch ops here would be slowed by the nvidia-smi sampler
+        step()
+        stats.append(gm.gm_fit_last_stats())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    for st in stats:
+        fused_ms += st["fused_ms"]
+        evals += st["galaxy_evals"]
+        launches += 3 + 2 * st["passes"]  # k_validate, k_lm_init, k_lm_finish; k_fused + k_lm_step per pass
+        converged += st["converged"]
+        iters.append(st["iters_sum"] / G)
+        print(f"step: library wall {st['wall_ms']:.1f} ms, fused {st['fused_ms']:.1f} ms, "
+              f"lm steps {st['step_ms']:.1f} ms, passes {st['passes']}", file=sys.stderr)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms_max = reduce_max(ms, world, dev)
+    conv_all = reduce_sum(converged, world, dev)
+    value = conv_all / (ms_max / 1e3)
+
+    # end to end through the public API from pinned host buffers
+    h_img = image.cpu().pin_memory()
+    h_sig = sigma.cpu().pin_memory()
+    h_msk = mask.cpu().pin_memory()
+    h_psf = psf.cpu().pin_memory()
+    h_p0 = p0.cpu().pin_memory()
+    h_out_p = torch.empty_like(h_p0).pin_memory()
+    h_out_st = torch.empty(G, dtype=torch.int32).pin_memory()
+    h_out_c2 = torch.empty(G, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_img, h_sig, h_msk, h_psf, h_p0))
+    d2h = sum(t.numel() * t.element_size() for t in (h_out_p, h_out_st, h_out_c2))
+    e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_conv = 0
+    for _ in range(e_steps):
+        d_img = h_img.to(dev, non_blocking=True)
+        d_sig = h_sig.to(dev, non_blocking=True)
+        d_msk = h_msk.to(dev, non_blocking=True)
+        d_psf = h_psf.to(dev, non_blocking=True)
+        d_p = h_p0.to(dev, non_blocking=True)
+        out = fitter.fit(d_p, d_img, d_sig, d_msk, d_psf, opts)
+        h_out_p.copy_(out["params"], non_blocking=True)
+        h_out_st.copy_(out["status"], non_blocking=True)
+        h_out_c2.copy_(out["chi2"], non_blocking=True)
+        torch.cuda.synchronize()
+        e_conv += int((h_out_st == gm.ST_CONVERGED).sum().item())
+    e_secs = reduce_max(time.perf_counter() - t0, world, dev)
+    e_value = reduce_sum(e_conv, world, dev) / e_secs
+
+    # roofline of the dominant kernel: the fused pass, FP32 ALU bound
+    taps = inbounds_taps(H, H, K)
+    nch = 1 + 7  # model + one channel per free parameter of the convolved Sersic
+    flops = 2.0 * nch * taps * evals
+    achieved = flops / (fused_ms / 1e3) / 1e12
+    gpix = evals * H * H / (fused_ms / 1e3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_fused<NORMAL,8>", "peak_source": "148 SMs x 128 FP32 FMA/clk x 2 x 2032 MHz"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = oracle.max_threads()
+        n = max(1, min(64, threads))
+        cb = synth.draw_sdss(seed=rank_seed(0), G=n, H=H, W=H, K=K)
+        c, dt = oracle_sample_fit(cb, np.arange(n))
+        cpu = {"value": c / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {n} galaxies of the workload recipe (seed {rank_seed(0)}), rendered and fitted by "
+                         f"the FP64 oracle, default start, tol {TOL:g}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(G, H, K), "gpix_per_s": gpix,
+                "converged_frac": converged / (G * args.steps), "mean_iters": float(np.mean(iters)),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--galaxies", type=int, default=8192, help="batch size per GPU (profiling runs use less)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -206,6 +206,23 @@ int gm_chi2_grad(const gm_model_desc *desc, const gm_batch *batch, const double 
  * still running; returns when none is or all have spent max_iter.
  */
 size_t gm_fit_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
+
+/* Counters of one gm_fit_batch call (host memory). */
+typedef struct {
+  int32_t passes;        /* fused model+Jacobian+reduction passes launched */
+  int64_t galaxy_evals;  /* galaxies evaluated, summed over the passes */
+  int64_t converged;     /* galaxies that ended GM_ST_CONVERGED */
+  int64_t iters_sum;     /* iters_out summed over the galaxies */
+  double fused_ms;       /* device time of the fused passes (CUDA events around each launch) */
+  double step_ms;        /* device time of the per-galaxy LM steps */
+  double wall_ms;        /* host wall time of the call */
+} gm_fit_stats;
+
+/* Counters of the calling thread's last successful gm_fit_batch; GM_E_INVAL if
+ * there was none or out is NULL.  Not part of the paper's method: it lets a
+ * caller relate throughput to the kernels' own time. */
+int gm_fit_last_stats(gm_fit_stats *out);
+
 int gm_fit_batch(const gm_model_desc *desc, const gm_batch *batch, double *params_inout,
                  const gm_fit_opts *opts, double *chi2_out, int32_t *dof_out, int32_t *iters_out,
                  int32_t *status_out, double *sigma_p_out, void *workspace, size_t ws_bytes,

@@ -227,8 +227,11 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
   }
 }
 
-template <int MODE, int P>
-__global__ void __launch_bounds__(256, 1) k_fused(const __grid_constant__ FusedArgs A) {
+// CPT = channel pairs per thread: 1 (128 threads per pair, up to 512 threads,
+// more warps to hide latency) or 2 (fewer, fatter threads; used when the
+// reduction of many free parameters needs more registers).
+template <int MODE, int P, int CPT>
+__global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_constant__ FusedArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   u64* s_psf = reinterpret_cast<u64*>(smem + A.off_psf);
   float2* s_in = reinterpret_cast<float2*>(smem + A.off_in);
@@ -287,10 +290,10 @@ __global__ void __launch_bounds__(256, 1) k_fused(const __grid_constant__ FusedA
     }
     __syncthreads();
 
-    // ---- 3. correlation: group = 4 warps = 2 channel pairs ----
+    // ---- 3. correlation: group = 4 warps = CPT channel pairs ----
     const int grp = tid / kGroupThreads;
-    const int cp0 = 2 * grp;
-    const int npair = min(2, A.ncp - cp0);
+    const int cp0 = CPT * grp;
+    const int npair = min(CPT, A.ncp - cp0);
     const int t = tid - grp * kGroupThreads;
     const int lane = t & 31, wig = t >> 5;
     const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
@@ -300,10 +303,10 @@ __global__ void __launch_bounds__(256, 1) k_fused(const __grid_constant__ FusedA
     const int a_hi = min(K, c - i0 + A.H - row0);
     u64 acc2[2][8];
     u64 acc1[1][8];
-    if (npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, cp0, HH, rw, K, row, col0, a_lo, a_hi);
+    if (CPT == 2 && npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, cp0, HH, rw, K, row, col0, a_lo, a_hi);
     else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, cp0, HH, rw, K, row, col0, a_lo, a_hi);
     __syncthreads();  // s_out aliases s_in
-    if (npair == 2) store_pairs<2>(acc2, s_out, cp0, A.nch_conv, row, col0);
+    if (CPT == 2 && npair == 2) store_pairs<2>(acc2, s_out, cp0, A.nch_conv, row, col0);
     else if (npair == 1) store_pairs<1>(acc1, s_out, cp0, A.nch_conv, row, col0);
     __syncthreads();
 

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 
@@ -16,6 +18,11 @@ using namespace gm;
 namespace {
 
 thread_local char g_err[512] = "no error";
+thread_local gm_fit_stats g_stats;
+thread_local bool g_have_stats = false;
+// CUDA events timing the passes of gm_fit_batch, created on first use and kept
+// for the life of the thread (three per iteration: fused start, fused end, step end).
+thread_local std::vector<cudaEvent_t> g_events;
 
 int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 int fail(int code, const char* fmt, ...) {
@@ -39,6 +46,8 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr int kMaxP1 = 10;  // largest free-parameter count served by the one-pair-per-thread kernel
 
 // Everything derived from the model description once per call.
 struct Plan {
@@ -159,9 +168,14 @@ struct Smem {
 // is >= K + 33 (the window reads 2 columns past the halo) and == 2 mod 16, so
 // the 8 lanes of a quarter warp (8 consecutive rows) hit distinct 16-byte bank
 // groups on their 16-byte loads.
+// Channel pairs per thread of the fused kernel: one (more warps) unless the
+// reduction of many free parameters needs the register budget of 256 threads.
+int pick_cpt(const Plan& pl) { return (pl.nacc == 0 || pl.dd.P <= kMaxP1) ? 1 : 2; }
+
 Smem smem_plan(const Plan& pl, int K, int n_comp, int n_slots) {
   Smem s;
-  s.threads = kGroupThreads * ((pl.ncp + 1) / 2);
+  const int cpt = pick_cpt(pl);
+  s.threads = kGroupThreads * ((pl.ncp + cpt - 1) / cpt);
   int rw = std::max(kTile + K - 1, K + 33);
   while (rw % 16 != 2) ++rw;
   s.rw = rw;
@@ -202,13 +216,14 @@ int dev_info(DevInfo* di) {
 typedef void (*FusedKernel)(FusedArgs);
 
 FusedKernel pick_kernel(int mode, int P) {
-  if (mode == MODE_MODEL) return k_fused<MODE_MODEL, 0>;
+  if (mode == MODE_MODEL) return k_fused<MODE_MODEL, 0, 1>;
   switch (P) {
-#define GM_CASE(n) \
-  case n:          \
-    return k_fused<MODE_NORMAL, n>;
-    GM_CASE(0) GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
-    GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12) GM_CASE(13) GM_CASE(14) GM_CASE(15) GM_CASE(16)
+#define GM_CASE(n, c) \
+  case n:             \
+    return k_fused<MODE_NORMAL, n, c>;
+    GM_CASE(0, 1) GM_CASE(1, 1) GM_CASE(2, 1) GM_CASE(3, 1) GM_CASE(4, 1) GM_CASE(5, 1) GM_CASE(6, 1)
+    GM_CASE(7, 1) GM_CASE(8, 1) GM_CASE(9, 1) GM_CASE(10, 1) GM_CASE(11, 2) GM_CASE(12, 2) GM_CASE(13, 2)
+    GM_CASE(14, 2) GM_CASE(15, 2) GM_CASE(16, 2)
 #undef GM_CASE
     default:
       return nullptr;
@@ -300,7 +315,7 @@ WsChi2 ws_chi2(const gm_model_desc* d, const gm_batch* b, int P) {
 
 struct WsFit {
   WsChi2 c;
-  size_t p_b, p_t, A_b, g_b, chi2_b, lam, it, status, nused, bad, list0, list1, counts, total;
+  size_t p_b, p_t, A_b, g_b, chi2_b, lam, it, status, nused, bad, list0, list1, counts, evals, total;
 };
 WsFit ws_fit(const gm_model_desc* d, const gm_batch* b, int P) {
   WsFit w;
@@ -325,6 +340,7 @@ WsFit ws_fit(const gm_model_desc* d, const gm_batch* b, int P) {
   w.list0 = take(G * 4);
   w.list1 = take(G * 4);
   w.counts = take(2 * 4);
+  w.evals = take(3 * 8);
   w.total = off;
   return w;
 }
@@ -367,6 +383,13 @@ extern "C" {
 
 int gm_version(void) { return 100; }
 
+int gm_fit_last_stats(gm_fit_stats* out) {
+  if (!out) return fail(GM_E_INVAL, "out is NULL");
+  if (!g_have_stats) return fail(GM_E_INVAL, "no gm_fit_batch has completed on this thread");
+  *out = g_stats;
+  return GM_OK;
+}
+
 const char* gm_last_error(void) { return g_err; }
 
 size_t gm_model_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
@@ -395,7 +418,7 @@ int gm_model(const gm_model_desc* desc, const gm_batch* batch, const double* par
   float* cconst = (float*)(ws + w.cconst);
   float* scale = (float*)(ws + w.scale);
   const int G = batch->n_gal;
-  k_setup<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
+  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
   GM_LAUNCHED("k_setup");
   FusedArgs A;
   fill_args(A, pl, batch, sm);
@@ -436,7 +459,7 @@ int gm_chi2_grad(const gm_model_desc* desc, const gm_batch* batch, const double*
   float* scale = (float*)(ws + w.m.scale);
   double* partial = (double*)(ws + w.partial);
   const int G = batch->n_gal;
-  k_setup<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
+  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
   GM_LAUNCHED("k_setup");
   FusedArgs A;
   fill_args(A, pl, batch, sm);
@@ -498,13 +521,22 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   S.list[1] = (int*)(ws + w.list1);
   S.count[0] = (int*)(ws + w.counts);
   S.count[1] = S.count[0] + 1;
+  S.evals = (unsigned long long*)(ws + w.evals);
   const int G = batch->n_gal;
+  const auto t_start = std::chrono::steady_clock::now();
+  g_have_stats = false;
+  while ((int)g_events.size() < 3 * O.max_iter) {
+    cudaEvent_t e;
+    GM_CUDA(cudaEventCreate(&e));
+    g_events.push_back(e);
+  }
+  GM_CUDA(cudaMemsetAsync(S.evals, 0, 3 * sizeof(unsigned long long), st));
 
   k_validate<<<std::min(G, 4 * di.sms), 256, 0, st>>>(G, batch->H, batch->W, batch->image, batch->sigma,
                                                       batch->mask, S.nused, S.bad);
   GM_LAUNCHED("k_validate");
   GM_CUDA(cudaMemsetAsync(S.count[0], 0, 2 * sizeof(int), st));
-  k_lm_init<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, O, G, batch->H, params_inout, cconst, scale);
+  k_lm_init<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, G, batch->H, params_inout, cconst, scale);
   GM_LAUNCHED("k_lm_init");
 
   FusedArgs A;
@@ -514,15 +546,20 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   A.partial = partial;
   const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
   const int poll = 4;
+  int passes = 0;
   for (int k = 0; k < O.max_iter; ++k) {
     const int cur = k & 1;
     A.list = S.list[cur];
     A.count = S.count[cur];
+    GM_CUDA(cudaEventRecord(g_events[3 * k], st));
     kf<<<grid, sm.threads, sm.total, st>>>(A);
     GM_LAUNCHED("k_fused(normal)");
+    GM_CUDA(cudaEventRecord(g_events[3 * k + 1], st));
     GM_CUDA(cudaMemsetAsync(S.count[cur ^ 1], 0, sizeof(int), st));
-    k_lm_step<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, O, cur, batch->H, A.n_tiles, partial, cconst, scale);
+    k_lm_step<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, cur, batch->H, A.n_tiles, partial, cconst, scale);
     GM_LAUNCHED("k_lm_step");
+    GM_CUDA(cudaEventRecord(g_events[3 * k + 2], st));
+    ++passes;
     if ((k + 1) % poll == 0 || k + 1 == O.max_iter) {
       int remaining = 0;
       GM_CUDA(cudaMemcpyAsync(&remaining, S.count[cur ^ 1], sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -533,7 +570,26 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   k_lm_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, G, params_inout, chi2_out, dof_out, iters_out,
                                                status_out, sigma_p_out);
   GM_LAUNCHED("k_lm_finish");
+  unsigned long long counters[3] = {0, 0, 0};
+  GM_CUDA(cudaMemcpyAsync(counters, S.evals, sizeof(counters), cudaMemcpyDeviceToHost, st));
   GM_CUDA(cudaStreamSynchronize(st));
+  gm_fit_stats fs;
+  fs.passes = passes;
+  fs.galaxy_evals = (int64_t)counters[0];
+  fs.converged = (int64_t)counters[1];
+  fs.iters_sum = (int64_t)counters[2];
+  fs.fused_ms = 0.0;
+  fs.step_ms = 0.0;
+  for (int k = 0; k < passes; ++k) {
+    float a = 0.f, b = 0.f;
+    GM_CUDA(cudaEventElapsedTime(&a, g_events[3 * k], g_events[3 * k + 1]));
+    GM_CUDA(cudaEventElapsedTime(&b, g_events[3 * k + 1], g_events[3 * k + 2]));
+    fs.fused_ms += a;
+    fs.step_ms += b;
+  }
+  fs.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  g_stats = fs;
+  g_have_stats = true;
   return GM_OK;
 }
 

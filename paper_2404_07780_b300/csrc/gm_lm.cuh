@@ -48,6 +48,7 @@ struct LMState {
   int* bad;        // [G] bad sigma / image on a used pixel
   int* list[2];    // active galaxies, double-buffered by iteration parity
   int* count[2];
+  unsigned long long* evals;  // [3]: galaxies evaluated over the passes, converged, iterations
 };
 
 __device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, int use_log, float* cc,
@@ -209,7 +210,9 @@ __device__ inline double gn_decrement(const double* Ap, const double* g, int P) 
 __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O, int cur, int H,
                           int n_tiles, const double* __restrict__ partial, float* cconst, float* scale) {
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= *S.count[cur]) return;
+  const int n_cur = *S.count[cur];
+  if (gi == 0) atomicAdd(S.evals, (unsigned long long)n_cur);
+  if (gi >= n_cur) return;
   const int g = S.list[cur][gi];
   const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
   double* pb = S.p_b + (size_t)g * NS;
@@ -323,6 +326,8 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
   dof_out[g] = S.nused[g] - P;
   iters_out[g] = S.it[g];
   status_out[g] = S.status[g];
+  if (S.status[g] == ST_CONVERGED) atomicAdd(S.evals + 1, 1ull);
+  atomicAdd(S.evals + 2, (unsigned long long)S.it[g]);
   if (sigma_p_out) {
     double* sp = sigma_p_out + (size_t)g * NS;
     for (int s = 0; s < NS; ++s) sp[s] = 0.0;

@@ -43,26 +43,53 @@ __host__ __device__ inline int n_params(int kind) {
 
 // ---------------------------------------------------------------------------
 // nu_n of the Sersic profile (Sec. 4.1): the root of P(2n, x) = 1/2, i.e. the
-// radius r_e encloses half of the light.  Newton iteration on the series form
-// of the regularised lower incomplete gamma function,
-//   P(a, x) = x^a e^-x sum_{k>=0} x^k / Gamma(a + k + 1),
-// started from the asymptotic expansion of Ciotti & Bertin (1999) for n >= 0.36
-// and from the polynomial fit of MacArthur, Courteau & Holtzman (2003) below.
-// The root lies below a = 2n, where the series converges geometrically.
+// radius r_e encloses half of the light.  P is the regularised lower
+// incomplete gamma function, summed as
+//   P(a, x) = pref * sum_k t_k,   pref = x^a e^-x / Gamma(a),
+//   t_0 = 1/a,  t_k = t_{k-1} x / (a + k),
+// which converges geometrically below x = a, where the root lies.  Newton's
+// method on x starts from the asymptotic expansion of Ciotti & Bertin (1999)
+// for n >= 0.36 and from the polynomial fit of MacArthur, Courteau & Holtzman
+// (2003) below; dP/dx = pref / x.
+//
+// dnu/dn follows from differentiating P(2n, nu(n)) = 1/2:
+//   dnu/dn = -2 (dP/da) / (dP/dx),
+//   dP/da  = P ln x - pref * sum_k t_k psi(a + k + 1),
+// with psi(a+k+1) = psi(a+1) + sum_{j=1..k} 1/(a+j) accumulated along the
+// series and psi(a+1) from the recurrence psi(z) = psi(z+1) - 1/z up to
+// z >= 10 and the asymptotic (Bernoulli) expansion there.
 // ---------------------------------------------------------------------------
-__device__ inline double lower_gamma_reg(double a, double x) {
-  if (x <= 0.0) return 0.0;
-  double term = 1.0 / a;  // Gamma(a) x^0 / Gamma(a + 1)
-  double sum = term;
-  for (int k = 1; k < 2000; ++k) {
-    term *= x / (a + k);
-    sum += term;
-    if (term < sum * 1e-17) break;
+__device__ inline double digamma_pos(double z) {
+  double acc = 0.0;
+  while (z < 10.0) {
+    acc -= 1.0 / z;
+    z += 1.0;
   }
-  return sum * exp(a * log(x) - x - lgamma(a));
+  const double iz = 1.0 / z, iz2 = iz * iz;
+  // ln z - 1/(2z) - B2/(2 z^2) - B4/(4 z^4) - ... with B2 = 1/6, B4 = -1/30,
+  // B6 = 1/42, B8 = -1/30, B10 = 5/66
+  const double tail = iz2 * (1.0 / 12.0 - iz2 * (1.0 / 120.0 - iz2 * (1.0 / 252.0 - iz2 * (1.0 / 240.0 - iz2 / 132.0))));
+  return acc + log(z) - 0.5 * iz - tail;
 }
 
-__device__ inline double sersic_nu(double n) {
+// sum_k t_k (and, when s1 != nullptr, sum_k t_k psi(a+k+1) given psi(a+1))
+__device__ inline double gamma_series(double a, double x, double psi1, double* s1) {
+  double t = 1.0 / a, s0 = t, psi = psi1, acc1 = t * psi;
+  for (int k = 1; k < 4000; ++k) {
+    const double ik = __drcp_rn(a + k);
+    t *= x * ik;
+    s0 += t;
+    if (s1) {
+      psi += ik;
+      acc1 += t * psi;
+    }
+    if (t < s0 * 1e-17) break;
+  }
+  if (s1) *s1 = acc1;
+  return s0;
+}
+
+__device__ inline void sersic_nu_dnu(double n, double* nu_out, double* dnu_out) {
   const double a = 2.0 * n;
   double x;
   if (n >= 0.36) {
@@ -75,21 +102,22 @@ __device__ inline double sersic_nu(double n) {
   }
   const double lga = lgamma(a);
   for (int it = 0; it < 60; ++it) {
-    const double f = lower_gamma_reg(a, x) - 0.5;
-    const double dens = exp((a - 1.0) * log(x) - x - lga);  // dP/dx
-    double xn = x - f / dens;
+    const double pref = exp(a * log(x) - x - lga);
+    const double f = pref * gamma_series(a, x, 0.0, nullptr) - 0.5;
+    double xn = x - f * x / pref;  // Newton: dP/dx = pref / x
     if (!(xn > 0.0)) xn = 0.5 * x;
     const double dx = fabs(xn - x);
     x = xn;
-    if (dx <= 1e-15 * x) break;
+    if (dx <= 1e-14 * x) break;
   }
-  return x;
-}
-
-// dnu/dn by a central difference of the Newton solve (h = 1e-4 n).
-__device__ inline double sersic_dnu(double n) {
-  const double h = 1e-4 * n;
-  return (sersic_nu(n + h) - sersic_nu(n - h)) / (2.0 * h);
+  const double lx = log(x);
+  const double pref = exp(a * lx - x - lga);
+  double s1 = 0.0;
+  const double s0 = gamma_series(a, x, digamma_pos(a + 1.0), &s1);
+  const double P = pref * s0;
+  const double dPda = P * lx - pref * s1;
+  *nu_out = x;
+  *dnu_out = -2.0 * dPda * x / pref;
 }
 
 // ---------------------------------------------------------------------------
@@ -132,8 +160,10 @@ __device__ inline void setup_component(int kind, const double* par, int H, float
       cc[8] = (float)par[4];
       cc[9] = (float)(1.0 / par[5]);
       cc[10] = (float)(1.0 / n);
-      cc[11] = (float)sersic_nu(n);
-      cc[12] = (float)sersic_dnu(n);
+      double nu, dnu;
+      sersic_nu_dnu(n, &nu, &dnu);
+      cc[11] = (float)nu;
+      cc[12] = (float)dnu;
       break;
     }
     case EXPDISK:

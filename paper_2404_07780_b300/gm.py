@@ -29,7 +29,8 @@ ST_CONVERGED = 1
 
 # every symbol include/gm.h declares
 EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model",
-           "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch")
+           "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch",
+           "gm_fit_last_stats")
 
 
 class GMError(RuntimeError):
@@ -79,6 +80,18 @@ class gm_fit_opts(ctypes.Structure):
     ]
 
 
+class gm_fit_stats(ctypes.Structure):
+    _fields_ = [
+        ("passes", ctypes.c_int32),
+        ("galaxy_evals", ctypes.c_int64),
+        ("converged", ctypes.c_int64),
+        ("iters_sum", ctypes.c_int64),
+        ("fused_ms", ctypes.c_double),
+        ("step_ms", ctypes.c_double),
+        ("wall_ms", ctypes.c_double),
+    ]
+
+
 @dataclass
 class FitOptions:
     tol: float = 1e-6
@@ -122,6 +135,8 @@ def load() -> ctypes.CDLL:
         lib.gm_chi2_grad.argtypes = [P, P, P, P, P, P, P, S, P]
         lib.gm_fit_batch.restype = ctypes.c_int
         lib.gm_fit_batch.argtypes = [P, P, P, P, P, P, P, P, P, P, S, P]
+        lib.gm_fit_last_stats.restype = ctypes.c_int
+        lib.gm_fit_last_stats.argtypes = [P]
         _lib = lib
     return _lib
 
@@ -259,6 +274,14 @@ class Fitter:
                                      _ptr(self.sigma_p), _ptr(self.ws), self.ws_bytes, _stream()), "gm_fit_batch")
         return {"params": params, "chi2": self.chi2, "dof": self.dof, "iters": self.iters, "status": self.status,
                 "sigma_p": self.sigma_p}
+
+
+def gm_fit_last_stats() -> dict:
+    """Counters of this thread's last gm_fit_batch: passes, galaxy_evals, converged, iters_sum, fused_ms,
+    step_ms, wall_ms."""
+    st = gm_fit_stats()
+    _check(load().gm_fit_last_stats(ctypes.byref(st)), "gm_fit_last_stats")
+    return {name: getattr(st, name) for name, _ in gm_fit_stats._fields_}
 
 
 def gm_fit_batch(spec_or_desc, params0, image, sigma, mask, psf, opts: FitOptions | None = None):

@@ -218,7 +218,7 @@ def near_truth(c: Case, seed=0, frac=0.02):
     return p
 
 
-FIT_TIGHT = dict(tol=1e-9, xtol=1e-10, gtol=1e-11, max_iter=200)
+FIT_TIGHT = dict(tol=1e-12, xtol=1e-10, gtol=1e-13, max_iter=200)
 
 
 def test_fit_near_truth_matches_oracle(gm):
