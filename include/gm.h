@@ -183,6 +183,34 @@ int gm_chi2_grad(const gm_model_desc *desc, const gm_batch *batch, const double 
                  void *stream);
 
 /*
+ * gm_chi2_grad_noalloc -- gm_chi2_grad for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a convenience of the library.
+ *
+ * Who needs it: code that must not call cudaMalloc (or torch's allocator) at
+ * the point where it evaluates chi^2 -- for example an optimiser or sampler
+ * plugged into a host framework that owns every device buffer and only lends
+ * it input and output pointers, or a pipeline stage that forbids allocation
+ * after start-up because cudaMalloc can synchronise the device and fragment
+ * memory.  Such callers still pass their inputs and outputs exactly as for
+ * gm_chi2_grad (same arguments, same results); only the workspace is gone.
+ *
+ * Scratch: a fixed array of GM_NOALLOC_SCRATCH_BYTES inside the library,
+ * reserved on every GPU that loads the library and held until the process
+ * exits.  A request whose gm_chi2_grad_workspace_bytes() exceeds it returns
+ * GM_E_NOMEM with a message (use gm_chi2_grad with your own workspace then).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array: calls that overlap on the GPU (two streams, or
+ * two host threads) race and corrupt each other's results, so serialise them.
+ * Nothing in the array carries over between calls (every call writes the
+ * parts it reads).  The function calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ */
+#define GM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int gm_chi2_grad_noalloc(const gm_model_desc *desc, const gm_batch *batch, const double *params,
+                         double *chi2, double *grad, double *jtj, void *stream);
+
+/*
  * gm_fit_batch -- Levenberg-Marquardt fit of every galaxy (damped Gauss-Newton
  * on Eq. chinu; Sec. 5.1 names LM as the classical alternative to gradient
  * descent), with the covariance uncertainty of Sec. 5.2.

@@ -8,12 +8,19 @@
 #include <vector>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/gm.h"
 #include "gm_fused.cuh"
 #include "gm_lm.cuh"
 
 using namespace gm;
+
+// Scratch of gm_chi2_grad_noalloc: a fixed array in device memory, reserved on
+// every GPU that loads this library.  Host code must not use its name as a
+// device address: the address comes from cudaGetSymbolAddress (see
+// noalloc_scratch below).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GM_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
@@ -594,3 +601,45 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
 }
 
 }  // extern "C"
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device with that device current.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  GM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(GM_E_UNSUPPORTED, "device ordinal %d beyond %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(GM_E_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch) on device %d: %s", dev, cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return GM_OK;
+}
+
+}  // namespace
+
+extern "C" int gm_chi2_grad_noalloc(const gm_model_desc* desc, const gm_batch* batch, const double* params,
+                                    double* chi2, double* grad, double* jtj, void* stream) {
+  int rc = check_batch(batch, true);
+  if (rc) return rc;
+  if ((rc = check_desc(desc))) return rc;
+  const size_t need = ws_chi2(desc, batch, count_free(desc)).total;
+  if (need > (size_t)GM_NOALLOC_SCRATCH_BYTES)
+    return fail(GM_E_NOMEM,
+                "gm_chi2_grad_noalloc: this batch needs %zu bytes of scratch but the built-in array holds %u; "
+                "split the batch or call gm_chi2_grad with your own workspace",
+                need, (unsigned)GM_NOALLOC_SCRATCH_BYTES);
+  void* ws = nullptr;
+  if ((rc = noalloc_scratch(&ws))) return rc;
+  return gm_chi2_grad(desc, batch, params, chi2, grad, jtj, ws, (size_t)GM_NOALLOC_SCRATCH_BYTES, stream);
+}

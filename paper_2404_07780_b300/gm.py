@@ -30,7 +30,7 @@ ST_CONVERGED = 1
 # every symbol include/gm.h declares
 EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model",
            "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch",
-           "gm_fit_last_stats")
+           "gm_fit_last_stats", "gm_chi2_grad_noalloc")
 
 
 class GMError(RuntimeError):
