@@ -287,8 +287,9 @@ def run_gpu(args, world, rank, local):
         launches += 3 + 2 * st["passes"]  # k_validate, k_lm_init, k_lm_finish; k_fused + k_lm_step per pass
         converged += st["converged"]
         iters.append(st["iters_sum"] / G)
-        print(f"step: library wall {st['wall_ms']:.1f} ms, fused {st['fused_ms']:.1f} ms, "
-              f"lm steps {st['step_ms']:.1f} ms, passes {st['passes']}", file=sys.stderr)
+        print(f"step: library wall {st['wall_ms']:.1f} ms, profile {st['profile_ms']:.1f} ms, "
+              f"fused {st['fused_ms']:.1f} ms, lm steps {st['step_ms']:.1f} ms, passes {st['passes']}",
+              file=sys.stderr)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()

@@ -63,7 +63,8 @@ extern "C" {
 #endif
 
 #define GM_MAX_COMP 8
-#define GM_MAX_SLOTS 16
+#define GM_MAX_SLOTS 24   /* parameter slots of a model */
+#define GM_MAX_FREE 16    /* of which fitted (is_free) */
 
 /* return codes */
 #define GM_OK 0
@@ -109,7 +110,7 @@ typedef struct {
 typedef struct {
   int32_t n_comp;                    /* 1..GM_MAX_COMP */
   gm_component comp[GM_MAX_COMP];
-  int32_t n_slots;                   /* 1..GM_MAX_SLOTS */
+  int32_t n_slots;                   /* 1..GM_MAX_SLOTS, at most GM_MAX_FREE of them free */
   uint8_t is_free[GM_MAX_SLOTS];
   uint8_t is_log[GM_MAX_SLOTS];
   double lo[GM_MAX_SLOTS];
@@ -158,7 +159,7 @@ const char *gm_last_error(void);
  *              the stored image blocks of Sec. 2
  *   workspace  gm_model_workspace_bytes(desc, batch) bytes
  * Returns GM_E_INVAL for bad arguments, GM_E_NOMEM for a short workspace,
- * GM_E_UNSUPPORTED when the channel count or K exceeds what fits on chip.
+ * GM_E_UNSUPPORTED when K is too large for the tile to fit in shared memory.
  */
 size_t gm_model_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
 int gm_model(const gm_model_desc *desc, const gm_batch *batch, const double *params,
@@ -241,7 +242,8 @@ typedef struct {
   int64_t galaxy_evals;  /* galaxies evaluated, summed over the passes */
   int64_t converged;     /* galaxies that ended GM_ST_CONVERGED */
   int64_t iters_sum;     /* iters_out summed over the galaxies */
-  double fused_ms;       /* device time of the fused passes (CUDA events around each launch) */
+  double profile_ms;     /* device time of the profile kernels (channel images of each pass) */
+  double fused_ms;       /* device time of the fused tile kernels (correlation + reduction) */
   double step_ms;        /* device time of the per-galaxy LM steps */
   double wall_ms;        /* host wall time of the call */
 } gm_fit_stats;

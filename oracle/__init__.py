@@ -47,7 +47,7 @@ _lib = None
 KIND_CODES = {"sersic": 1, "expdisk": 2, "ferrer": 3, "king": 4, "gaussian": 5, "moffat": 6, "sky": 7}
 
 MAX_COMP = 8
-MAX_SLOTS = 16
+MAX_SLOTS = 24
 
 STATUS = {0: "RUNNING", 1: "CONVERGED", 2: "MAX_ITER", 3: "STALLED", 4: "SINGULAR",
           5: "NONFINITE", 6: "BAD_INPUT", 7: "NO_DOF"}

@@ -58,7 +58,7 @@
 #define OR_SKY 7
 
 #define OR_MAX_COMP 8
-#define OR_MAX_SLOTS 16
+#define OR_MAX_SLOTS 24
 #define OR_RFLOOR 1e-4
 
 /* per-galaxy fit status */

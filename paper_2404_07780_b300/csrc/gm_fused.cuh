@@ -1,76 +1,104 @@
-// gm_fused.cuh -- the fused per-tile kernel: light profiles + analytic
-// derivatives on the tile and its PSF halo (in shared memory), multi-channel
-// direct PSF correlation in FP32 (packed f32x2 FMAs), residual, weights and the
-// per-tile reduction of chi^2, J^T W r and J^T W J.
+// gm_fused.cuh -- the two kernels of one model+Jacobian pass.
 //
-// Work item = (galaxy, 32x32 output tile).  A persistent grid strides over the
-// items of the galaxies still being fitted.  Per item:
-//   1. PSF (as (p, p) pairs), per-galaxy constants and slot scales -> smem.
-//   2. Profile phase: every pixel of the (32+K-1)^2 input window that lies in
-//      the stamp gets the summed convolved components (channel 0) and one
-//      derivative channel per free parameter of a convolved component; zero
-//      outside the stamp (the zero padding of conv2d "same").  Channels are
-//      stored as interleaved pairs so that one f32x2 FMA serves two channels.
-//   3. Correlation: each thread owns 8 adjacent output pixels of one row and 2
-//      channel pairs; for every PSF row it slides a 10-entry register window
-//      along the input row (one 16-byte shared load per 2 taps per pair, one
-//      16-byte PSF load per 2 taps) and issues 16 f32x2 FMAs per tap pair and
-//      channel pair.  PSF rows whose input rows lie wholly outside the stamp
-//      for the warp are skipped.
-//   4. Unconvolved components (the sky) are added at the output pixels.
-//   5. NORMAL mode: r = D - M, w = Omega/sigma^2 per pixel, FP32 accumulation
-//      of chi^2, J^T W r and J^T W J per thread, warp shuffles, a cross-warp
-//      sum, one FP64 partial per tile written to global memory.
-//      MODEL mode: the model (and per-component images) written out.
+// k_profile: every stamp pixel of the galaxies being evaluated gets the summed
+//   convolved components (channel 0) and one derivative channel per free
+//   parameter of a convolved component (NORMAL mode), or the per-component
+//   images (MODEL mode), written once to a channel-pair plane in the
+//   workspace: planes[g][cp][i][j] = (channel 2cp, channel 2cp+1), row pitch
+//   Wp = W rounded up to even (the pad column is zero).
+//
+// k_fused: work item = (galaxy, 32x32 output tile); a persistent grid strides
+//   over the items of the galaxies still being fitted.  Per item and per
+//   "pass" of up to four channel pairs:
+//     * one thread issues a TMA tile load (cp.async.bulk.tensor.3d) of the
+//       (32+K-1) x rw window of every pair plane of the pass into shared
+//       memory; out-of-stamp rows and columns come back as zeros, which is
+//       the zero padding of conv2d(..., padding="same");
+//     * each thread owns 8 adjacent output pixels of one row and CPT channel
+//       pairs and runs the sliding-window correlation (one 16-byte shared
+//       load per 2 taps per pair, one 16-byte PSF load per 2 taps, 16 packed
+//       fma.rn.f32x2 per tap pair and channel pair), summing each block of 4
+//       PSF rows into a separate partial (FP32 rounding error ~3x lower than
+//       one running sum); PSF rows whose input rows all fall outside the
+//       stamp for the warp are skipped;
+//     * the next load (next pass or next item) is issued as soon as every
+//       warp has finished reading the window, so it overlaps the stores and
+//       the reduction.
+//   Then the unconvolved components (the sky) are added at the output pixels,
+//   and NORMAL mode forms r = D - M, w = Omega/sigma^2 and accumulates chi^2,
+//   J^T W r and J^T W J (FP32 per thread, warp shuffles, cross-warp sum, one
+//   FP64 partial per tile); MODEL mode writes the model and component images.
 //
 // The correlation is M[i,j] = sum_ab P[a,b] I[i+a-c, j+b-c] (cross-correlation,
-// torch conv2d semantics, App. C of arxiv 2404.07780).
+// torch conv2d semantics, App. C of arxiv 2404.07780).  In shared memory each
+// PSF row is padded to K+1 taps with one zero: on the right when c = (K-1)/2 is
+// even, on the left when c is odd, so that the window's first column j0 - c'
+// (c' = c or c+1) is even and the TMA start coordinate is 16-byte aligned.
 #pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "gm_profiles.cuh"
 
 namespace gm {
 
-constexpr int kTile = 32;          // output tile is kTile x kTile
+constexpr int kTile = 32;           // output tile is kTile x kTile
 constexpr int kTilePix = kTile * kTile;
-constexpr int kMaxConvCh = 8;      // channels one pass correlates (4 pairs)
-constexpr int kGroupThreads = 128; // threads per channel-pair group (32 rows x 4 col-blocks)
+constexpr int kMaxPairs = 9;        // up to 17 correlated channels (model + 16 free parameters)
+constexpr int kMaxPassPairs = 4;    // channel pairs per TMA pass
+constexpr int kGroupThreads = 128;  // threads per pair group (32 rows x 4 column blocks)
+constexpr int kRowBlock = 4;        // PSF rows summed into one partial accumulator
+constexpr unsigned kWaitTries = 1u << 24;
 
 enum Mode { MODE_MODEL = 0, MODE_NORMAL = 1 };
 
-struct FusedArgs {
-  // model description (uniform over the batch)
+// Model description shared by both kernels (uniform over the batch).
+struct ChanMap {
   int n_comp;
   int kind[kMaxComp];
   int conv[kMaxComp];
   int np[kMaxComp];
-  int slot[kMaxComp][8];         // parameter k of comp c -> slot
-  int chan[kMaxComp][8];         // d/dp_k of comp c -> s_out channel (-1: not needed)
-  int comp_chan[kMaxComp];       // MODEL mode: channel holding comp c's own image (-1: none)
+  int slot[kMaxComp][8];     // parameter k of comp c -> slot
+  int chan[kMaxComp][8];     // d/dp_k of comp c -> channel (-1: not needed)
+  int comp_chan[kMaxComp];   // MODEL mode: channel holding comp c's own image (-1: none)
   int any_unconv;
-  int nch_conv;                  // correlated channels (<= kMaxConvCh)
-  int ncp;                       // channel pairs = ceil(nch_conv / 2)
-  int nch_tot;                   // channels in s_out
+  int nch_conv;              // correlated channels
+  int ncp;                   // channel pairs = ceil(nch_conv / 2)
+  int nch_tot;               // channels at the output pixels (correlated + unconvolved-only)
   int n_slots;
-  int nacc;                      // accumulators per tile (NORMAL)
-  // batch
-  int G, H, W, K, tiles_x, n_tiles, rw;
+};
+
+struct ProfileArgs {
+  ChanMap m;
+  int G, H, W, Wp;
+  const float* cconst;       // [G][n_comp][kCC]
+  const float* scale;        // [G][n_slots]
+  const int* list;           // galaxies list[0 .. *count); nullptr -> all G
+  const int* count;
+  float* planes;             // [G][ncp][H][Wp][2]
+};
+
+struct FusedArgs {
+  CUtensorMap tmap;          // planes as a [G*ncp][H][2*Wp] FP32 tensor, box [1][HH][2*rw]
+  ChanMap m;
+  int nacc;                  // accumulators per tile (NORMAL)
+  int G, H, W, K, cpad, tiles_x, n_tiles, rw, pp, passes;
+  int plane;                 // float2 elements between pair planes in shared memory (a 128-byte multiple:
+                             // every TMA destination must be 128-byte aligned)
   const float* image;
   const float* sigma;
   const uint8_t* mask;
   const float* psf;
-  // per-galaxy constants
-  const float* cconst;           // [G][n_comp][kCC]
-  const float* scale;            // [G][n_slots]
-  // work list: galaxies list[0 .. *count); list == nullptr -> all G
+  const float* cconst;
+  const float* scale;
   const int* list;
   const int* count;
-  // outputs
-  double* partial;               // [G][n_tiles][nacc]
-  float* model_out;              // [G][H][W]
-  float* comp_out;               // [G][n_comp][H][W] or nullptr
-  // shared-memory carve-up (bytes)
-  int off_psf, off_in, off_out, off_cc, off_scale, off_red;
+  double* partial;           // [G][n_tiles][nacc]
+  float* model_out;          // [G][H][W]
+  float* comp_out;           // [G][n_comp][H][W] or nullptr
+  int* err;                  // set to 1 when a TMA wait times out
+  int off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar;
 };
 
 typedef unsigned long long u64;
@@ -91,6 +119,113 @@ __device__ __forceinline__ void unpack2(u64 v, float& x, float& y) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
 }
 
+// ---------------------------------------------------------------------------
+// k_profile
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) k_profile(const __grid_constant__ ProfileArgs A) {
+  __shared__ float s_cc[kMaxComp * kCC];
+  __shared__ float s_scale[kMaxSlots];
+  __shared__ float s_v[256 * 2 * kMaxPairs];
+  const ChanMap& m = A.m;
+  const int tid = threadIdx.x;
+  const int per_gal = (A.H * A.Wp + 255) / 256;
+  const int n_gal = A.list ? *A.count : A.G;
+  float* v = s_v + tid * 2 * kMaxPairs;
+  for (int blk = blockIdx.x; blk < n_gal * per_gal; blk += gridDim.x) {
+    const int gi = blk / per_gal, chunk = blk - gi * per_gal;
+    const int g = A.list ? A.list[gi] : gi;
+    __syncthreads();
+    for (int t = tid; t < m.n_comp * kCC; t += 256) s_cc[t] = A.cconst[(size_t)g * m.n_comp * kCC + t];
+    for (int t = tid; t < m.n_slots; t += 256) s_scale[t] = A.scale[(size_t)g * m.n_slots + t];
+    __syncthreads();
+    const int pix = chunk * 256 + tid;
+    if (pix >= A.H * A.Wp) continue;
+    const int i = pix / A.Wp, j = pix - (pix / A.Wp) * A.Wp;
+    for (int ch = 0; ch < 2 * m.ncp; ++ch) v[ch] = 0.f;
+    if (j < A.W) {
+      for (int cm = 0; cm < m.n_comp; ++cm) {
+        if (!m.conv[cm]) continue;
+        float d[8];
+        const float val = eval_component(m.kind[cm], s_cc + cm * kCC, i, j, d);
+        v[0] += val;
+        if (MODE == MODE_MODEL) {
+          if (m.comp_chan[cm] >= 0) v[m.comp_chan[cm]] += val;
+        } else {
+          for (int k = 0; k < m.np[cm]; ++k) {
+            const int ch = m.chan[cm][k];
+            if (ch >= 0) v[ch] += d[k] * s_scale[m.slot[cm][k]];
+          }
+        }
+      }
+    }
+    float2* out = reinterpret_cast<float2*>(A.planes);
+    for (int cp = 0; cp < m.ncp; ++cp)
+      out[(((size_t)g * m.ncp + cp) * A.H + i) * A.Wp + j] = make_float2(v[2 * cp], v[2 * cp + 1]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA and mbarrier helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(u64* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(u64* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u64* bar, unsigned phase) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for a phase of the mbarrier; false after kWaitTries polls.
+__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, unsigned phase) {
+  for (unsigned t = 0; t < kWaitTries; ++t)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, u64* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<u64>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Issue the loads of pass `pass` of item `item` (thread 0 only).
+__device__ __forceinline__ void issue_pass(const FusedArgs& A, float2* s_in, u64* bar, int item, int pass) {
+  const int gi = item / A.n_tiles, tile = item - gi * A.n_tiles;
+  const int g = A.list ? A.list[gi] : gi;
+  const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
+  const int c = (A.K - 1) / 2;
+  const int HH = kTile + A.K - 1;
+  const int first = pass * A.pp;
+  const int npairs = min(A.pp, A.m.ncp - first);
+  const unsigned plane_bytes = (unsigned)HH * A.rw * 8u;
+  // order this CTA's earlier generic-proxy reads of s_in before the async-proxy writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, plane_bytes * npairs);
+  const int x = 2 * (j0 - c - A.cpad);  // even pair index: 16-byte aligned start
+  for (int q = 0; q < npairs; ++q)
+    tma_load_3d(s_in + (size_t)q * A.plane, &A.tmap, x, i0 - c, g * A.m.ncp + first + q, bar);
+}
+
+// ---------------------------------------------------------------------------
+// correlation
+// ---------------------------------------------------------------------------
 // One 2-tap chunk of the sliding-window correlation.  R is the ring rotation:
 // window element e (input column b + e relative to the thread's first column)
 // lives in w[q][(2R + e) % 10].  Elements 0..7 are present on entry; elements 8
@@ -115,48 +250,67 @@ __device__ __forceinline__ void corr_chunk(u64 (&acc)[CP][8], u64 (&w)[CP][10],
   }
 }
 
-// Correlate CP channel pairs for one thread's 8 output pixels over PSF rows
-// [a_lo, a_hi).  s_in is [ncp][HH][rw] float2, s_psf is [K][K+1] (p, p) pairs.
+// One PSF row a (K2 = K+1 taps, even) into acc.
+template <int CP>
+__device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const (&irow)[CP], const u64* prow,
+                                         int nsc, int tail) {
+  u64 w[CP][10];
+#pragma unroll
+  for (int q = 0; q < CP; ++q) {
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
+      w[q][e] = v.x;
+      w[q][e + 1] = v.y;
+    }
+  }
+  int b = 0;
+  for (int sc = 0; sc < nsc; ++sc) {
+    corr_chunk<CP, 0>(acc, w, irow, prow, b);
+    corr_chunk<CP, 1>(acc, w, irow, prow, b + 2);
+    corr_chunk<CP, 2>(acc, w, irow, prow, b + 4);
+    corr_chunk<CP, 3>(acc, w, irow, prow, b + 6);
+    corr_chunk<CP, 4>(acc, w, irow, prow, b + 8);
+    b += 10;
+  }
+  if (tail > 0) corr_chunk<CP, 0>(acc, w, irow, prow, b);
+  if (tail > 1) corr_chunk<CP, 1>(acc, w, irow, prow, b + 2);
+  if (tail > 2) corr_chunk<CP, 2>(acc, w, irow, prow, b + 4);
+  if (tail > 3) corr_chunk<CP, 3>(acc, w, irow, prow, b + 6);
+}
+
+// Correlate CP pair planes (local indices lp0 .. lp0+CP-1 of the pass buffer)
+// for one thread's 8 output pixels over PSF rows [a_lo, a_hi).
 template <int CP>
 __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2* s_in, const u64* s_psf,
-                                                int cp0, int HH, int rw, int K, int row, int col0,
-                                                int a_lo, int a_hi) {
+                                                int lp0, int plane, int rw, int K, int row, int col0, int a_lo,
+                                                int a_hi) {
+  const u64 one2 = pack2(1.f, 1.f);
 #pragma unroll
   for (int q = 0; q < CP; ++q)
 #pragma unroll
     for (int rx = 0; rx < 8; ++rx) acc[q][rx] = 0ull;
   const int K2 = K + 1;
-  const int nch = K2 >> 1;        // 2-tap chunks per PSF row
-  const int nsc = nch / 5;        // full 5-chunk rotations
+  const int nch = K2 >> 1;   // 2-tap chunks per PSF row
+  const int nsc = nch / 5;   // full 5-chunk rotations
   const int tail = nch - 5 * nsc;
-  for (int a = a_lo; a < a_hi; ++a) {
-    const u64* prow = s_psf + a * K2;
-    const float2* irow[CP];
+  for (int a0 = a_lo; a0 < a_hi; a0 += kRowBlock) {
+    u64 part[CP][8];
 #pragma unroll
-    for (int q = 0; q < CP; ++q) irow[q] = s_in + ((size_t)(cp0 + q) * HH + row + a) * rw + col0;
-    u64 w[CP][10];
+    for (int q = 0; q < CP; ++q)
 #pragma unroll
-    for (int q = 0; q < CP; ++q) {
+      for (int rx = 0; rx < 8; ++rx) part[q][rx] = 0ull;
+    const int a1 = min(a0 + kRowBlock, a_hi);
+    for (int a = a0; a < a1; ++a) {
+      const float2* irow[CP];
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
-        w[q][e] = v.x;
-        w[q][e + 1] = v.y;
-      }
+      for (int q = 0; q < CP; ++q) irow[q] = s_in + (size_t)(lp0 + q) * plane + (size_t)(row + a) * rw + col0;
+      corr_row<CP>(part, irow, s_psf + a * K2, nsc, tail);
     }
-    int b = 0;
-    for (int sc = 0; sc < nsc; ++sc) {
-      corr_chunk<CP, 0>(acc, w, irow, prow, b);
-      corr_chunk<CP, 1>(acc, w, irow, prow, b + 2);
-      corr_chunk<CP, 2>(acc, w, irow, prow, b + 4);
-      corr_chunk<CP, 3>(acc, w, irow, prow, b + 6);
-      corr_chunk<CP, 4>(acc, w, irow, prow, b + 8);
-      b += 10;
-    }
-    if (tail > 0) corr_chunk<CP, 0>(acc, w, irow, prow, b);
-    if (tail > 1) corr_chunk<CP, 1>(acc, w, irow, prow, b + 2);
-    if (tail > 2) corr_chunk<CP, 2>(acc, w, irow, prow, b + 4);
-    if (tail > 3) corr_chunk<CP, 3>(acc, w, irow, prow, b + 6);
+#pragma unroll
+    for (int q = 0; q < CP; ++q)
+#pragma unroll
+      for (int rx = 0; rx < 8; ++rx) acc[q][rx] = ffma2(one2, part[q][rx], acc[q][rx]);
   }
 }
 
@@ -181,8 +335,8 @@ __device__ __forceinline__ void store_pairs(const u64 (&acc)[CP][8], float* s_ou
 // parameters over this thread's pixels of the tile, reduce over the block and
 // write the tile's FP64 partial sums.
 template <int P>
-__device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_out, float* s_red,
-                                            int g, int tile, int i0, int j0) {
+__device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_out, float* s_red, int g, int tile,
+                                            int i0, int j0) {
   constexpr int NA = 1 + P + P * (P + 1) / 2;
   float acc[NA];
 #pragma unroll
@@ -227,114 +381,124 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
   }
 }
 
-// CPT = channel pairs per thread: 1 (128 threads per pair, up to 512 threads,
-// more warps to hide latency) or 2 (fewer, fatter threads; used when the
-// reduction of many free parameters needs more registers).
+// ---------------------------------------------------------------------------
+// k_fused
+// ---------------------------------------------------------------------------
+// CPT = channel pairs per thread: 1 (128 threads per pair, up to 512 threads)
+// or 2 (fewer threads with the register budget the reduction of many free
+// parameters needs).
 template <int MODE, int P, int CPT>
 __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_constant__ FusedArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   u64* s_psf = reinterpret_cast<u64*>(smem + A.off_psf);
   float2* s_in = reinterpret_cast<float2*>(smem + A.off_in);
   float* s_out = reinterpret_cast<float*>(smem + A.off_out);
   float* s_cc = reinterpret_cast<float*>(smem + A.off_cc);
   float* s_scale = reinterpret_cast<float*>(smem + A.off_scale);
   float* s_red = reinterpret_cast<float*>(smem + A.off_red);
+  u64* bar = reinterpret_cast<u64*>(smem + A.off_bar);
+  int* s_flag = reinterpret_cast<int*>(smem + A.off_bar + 8);
+  const ChanMap& m = A.m;
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int K = A.K, c = (K - 1) / 2, K2 = K + 1;
-  const int HH = kTile + K - 1, WW = kTile + K - 1, rw = A.rw;
+  const int rw = A.rw;
   const int n_gal = A.list ? *A.count : A.G;
   const int n_items = n_gal * A.n_tiles;
+  if ((int)blockIdx.x >= n_items) return;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_flag = 0;
+  }
+  __syncthreads();
+  if (tid == 0) issue_pass(A, s_in, bar, blockIdx.x, 0);
+  unsigned phase = 0;
+
+  const int grp = tid / kGroupThreads;
+  const int t = tid - grp * kGroupThreads;
+  const int lane = t & 31, wig = t >> 5;
+  const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
+  const int row0 = wig * 8;
 
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int gi = item / A.n_tiles, tile = item - gi * A.n_tiles;
     const int g = A.list ? A.list[gi] : gi;
     const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
 
-    __syncthreads();  // the previous item is done with shared memory
-    for (int t = tid; t < A.n_comp * kCC; t += nthr) s_cc[t] = A.cconst[(size_t)g * A.n_comp * kCC + t];
-    for (int t = tid; t < A.n_slots; t += nthr) s_scale[t] = A.scale[(size_t)g * A.n_slots + t];
-    for (int t = tid; t < K * K2; t += nthr) {
-      const int a = t / K2, b = t - a * K2;
-      const float v = (b < K) ? A.psf[(size_t)g * K * K + a * K + b] : 0.f;
-      s_psf[t] = pack2(v, v);
+    __syncthreads();  // the previous item is done with s_psf, s_cc, s_scale, s_out, s_red
+    for (int t2 = tid; t2 < m.n_comp * kCC; t2 += nthr) s_cc[t2] = A.cconst[(size_t)g * m.n_comp * kCC + t2];
+    for (int t2 = tid; t2 < m.n_slots; t2 += nthr) s_scale[t2] = A.scale[(size_t)g * m.n_slots + t2];
+    for (int t2 = tid; t2 < K * K2; t2 += nthr) {
+      const int a = t2 / K2, bb = t2 - a * K2;
+      const int b = bb - A.cpad;  // tap index in the unpadded PSF row
+      const float v = (b >= 0 && b < K) ? A.psf[(size_t)g * K * K + a * K + b] : 0.f;
+      s_psf[t2] = pack2(v, v);
     }
-    __syncthreads();
-
-    // ---- 2. profile phase over the input window (zero outside the stamp) ----
-    const size_t pstride = (size_t)HH * rw * 2;  // floats between channel pairs
-    for (int hp = tid; hp < HH * rw; hp += nthr) {
-      const int hr = hp / rw, hc = hp - hr * rw;
-      const int i = i0 + hr - c, j = j0 + hc - c;
-      float* px = reinterpret_cast<float*>(s_in + (size_t)hr * rw + hc);
-      for (int cp = 0; cp < A.ncp; ++cp) {
-        px[cp * pstride] = 0.f;
-        px[cp * pstride + 1] = 0.f;
-      }
-      if (hc >= WW || i < 0 || i >= A.H || j < 0 || j >= A.W) continue;
-      for (int cm = 0; cm < A.n_comp; ++cm) {
-        if (!A.conv[cm]) continue;
-        float d[8];
-        const float v = eval_component(A.kind[cm], s_cc + cm * kCC, i, j, d);
-        px[0] += v;
-        if (MODE == MODE_MODEL) {
-          const int ch = A.comp_chan[cm];
-          if (ch >= 0) px[(ch >> 1) * pstride + (ch & 1)] += v;
-        } else {
-          for (int k = 0; k < A.np[cm]; ++k) {
-            const int ch = A.chan[cm][k];
-            if (ch >= 0) px[(ch >> 1) * pstride + (ch & 1)] += d[k] * s_scale[A.slot[cm][k]];
-          }
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- 3. correlation: group = 4 warps = CPT channel pairs ----
-    const int grp = tid / kGroupThreads;
-    const int cp0 = CPT * grp;
-    const int npair = min(CPT, A.ncp - cp0);
-    const int t = tid - grp * kGroupThreads;
-    const int lane = t & 31, wig = t >> 5;
-    const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
     // PSF rows whose 8 input rows (for this warp) all fall outside the stamp are skipped
-    const int row0 = wig * 8;
     const int a_lo = max(0, c - i0 - row0 - 7);
     const int a_hi = min(K, c - i0 + A.H - row0);
-    u64 acc2[2][8];
-    u64 acc1[1][8];
-    if (CPT == 2 && npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, cp0, HH, rw, K, row, col0, a_lo, a_hi);
-    else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, cp0, HH, rw, K, row, col0, a_lo, a_hi);
-    __syncthreads();  // s_out aliases s_in
-    if (CPT == 2 && npair == 2) store_pairs<2>(acc2, s_out, cp0, A.nch_conv, row, col0);
-    else if (npair == 1) store_pairs<1>(acc1, s_out, cp0, A.nch_conv, row, col0);
+
+    for (int pass = 0; pass < A.passes; ++pass) {
+      // wait for this pass's window (thread 0 polls with a bound, the CTA agrees)
+      if (tid == 0) {
+        if (!mbar_wait_bounded(bar, phase)) *s_flag = 1;
+      }
+      __syncthreads();
+      if (*s_flag) {
+        if (tid == 0) {
+          atomicExch(A.err, 1);
+          mbar_wait_bounded(bar, phase);  // let the copy in flight land before leaving
+        }
+        return;
+      }
+      mbar_try_wait(bar, phase);  // completes at once: acquires the TMA writes for this thread
+      phase ^= 1u;
+
+      const int first = pass * A.pp;
+      const int npass = min(A.pp, m.ncp - first);
+      const int lp0 = CPT * grp;
+      const int npair = min(CPT, npass - lp0);
+      u64 acc2[2][8];
+      u64 acc1[1][8];
+      if (CPT == 2 && npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
+      else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
+      __syncthreads();  // every warp is done reading the window
+      if (tid == 0) {
+        if (pass + 1 < A.passes) issue_pass(A, s_in, bar, item, pass + 1);
+        else if (item + (int)gridDim.x < n_items) issue_pass(A, s_in, bar, item + gridDim.x, 0);
+      }
+      if (CPT == 2 && npair == 2) store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
+      else if (npair == 1) store_pairs<1>(acc1, s_out, first + lp0, m.nch_conv, row, col0);
+    }
     __syncthreads();
 
-    // ---- 4. unconvolved components at the output pixels ----
+    // ---- unconvolved components at the output pixels ----
     for (int pix = tid; pix < kTilePix; pix += nthr) {
-      for (int ch = A.nch_conv; ch < A.nch_tot; ++ch) s_out[ch * kTilePix + pix] = 0.f;
-      if (!A.any_unconv) continue;
+      for (int ch = m.nch_conv; ch < m.nch_tot; ++ch) s_out[ch * kTilePix + pix] = 0.f;
+      if (!m.any_unconv) continue;
       const int i = i0 + pix / kTile, j = j0 + pix % kTile;
       if (i >= A.H || j >= A.W) continue;
-      for (int cm = 0; cm < A.n_comp; ++cm) {
-        if (A.conv[cm]) continue;
+      for (int cm = 0; cm < m.n_comp; ++cm) {
+        if (m.conv[cm]) continue;
         float d[8];
-        const float v = eval_component(A.kind[cm], s_cc + cm * kCC, i, j, d);
+        const float v = eval_component(m.kind[cm], s_cc + cm * kCC, i, j, d);
         s_out[pix] += v;
         if (MODE == MODE_MODEL) {
-          const int ch = A.comp_chan[cm];
+          const int ch = m.comp_chan[cm];
           if (ch >= 0) s_out[ch * kTilePix + pix] = v;
         } else {
-          for (int k = 0; k < A.np[cm]; ++k) {
-            const int ch = A.chan[cm][k];
-            if (ch >= 0) s_out[ch * kTilePix + pix] += d[k] * s_scale[A.slot[cm][k]];
+          for (int k = 0; k < m.np[cm]; ++k) {
+            const int ch = m.chan[cm][k];
+            if (ch >= 0) s_out[ch * kTilePix + pix] += d[k] * s_scale[m.slot[cm][k]];
           }
         }
       }
     }
     __syncthreads();
 
-    // ---- 5. outputs ----
+    // ---- outputs ----
     if (MODE == MODE_MODEL) {
       const size_t HW = (size_t)A.H * A.W;
       for (int pix = tid; pix < kTilePix; pix += nthr) {
@@ -343,8 +507,8 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
         const size_t off = (size_t)i * A.W + j;
         A.model_out[(size_t)g * HW + off] = s_out[pix];
         if (A.comp_out) {
-          for (int cm = 0; cm < A.n_comp; ++cm)
-            A.comp_out[((size_t)g * A.n_comp + cm) * HW + off] = s_out[A.comp_chan[cm] * kTilePix + pix];
+          for (int cm = 0; cm < m.n_comp; ++cm)
+            A.comp_out[((size_t)g * m.n_comp + cm) * HW + off] = s_out[m.comp_chan[cm] * kTilePix + pix];
         }
       }
     } else {

@@ -28,7 +28,8 @@ thread_local char g_err[512] = "no error";
 thread_local gm_fit_stats g_stats;
 thread_local bool g_have_stats = false;
 // CUDA events timing the passes of gm_fit_batch, created on first use and kept
-// for the life of the thread (three per iteration: fused start, fused end, step end).
+// for the life of the thread (four per iteration: profile start, tile kernel
+// start, tile kernel end, LM step end).
 thread_local std::vector<cudaEvent_t> g_events;
 
 int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -60,7 +61,7 @@ constexpr int kMaxP1 = 10;  // largest free-parameter count served by the one-pa
 struct Plan {
   DescDev dd;
   int conv[kMaxComp];
-  int chan_of_slot[kMaxSlots];  // s_out channel of a free slot (1 + accumulator index), -1 fixed
+  int chan_of_slot[kMaxSlots];  // output channel of a free slot (1 + accumulator index), -1 fixed
   int Pc;                       // free slots touching a convolved component
   int nch_conv, ncp, nch_tot, nacc;
   int any_unconv;
@@ -81,6 +82,9 @@ int check_desc(const gm_model_desc* d) {
         return fail(GM_E_INVAL, "component %d parameter %d uses slot %d outside 0..%d", c, k, d->comp[c].slot[k],
                     d->n_slots - 1);
   }
+  int nfree = 0;
+  for (int s = 0; s < d->n_slots; ++s) nfree += d->is_free[s] ? 1 : 0;
+  if (nfree > GM_MAX_FREE) return fail(GM_E_INVAL, "%d free parameters exceed %d", nfree, GM_MAX_FREE);
   for (int s = 0; s < d->n_slots; ++s) {
     if (!(d->lo[s] <= d->hi[s])) return fail(GM_E_INVAL, "slot %d has lo > hi", s);
     if (d->is_log[s] && !(d->lo[s] > 0.0)) return fail(GM_E_INVAL, "log slot %d needs lo > 0", s);
@@ -161,51 +165,91 @@ int make_plan(const gm_model_desc* d, int mode, bool want_comp, Plan* pl) {
     pl->nacc = 0;
   }
   pl->ncp = (pl->nch_conv + 1) / 2;
-  if (pl->nch_conv > kMaxConvCh)
-    return fail(GM_E_UNSUPPORTED, "%d correlated channels (free parameters of convolved components + 1) exceed %d",
-                pl->nch_conv, kMaxConvCh);
+  if (pl->ncp > kMaxPairs)
+    return fail(GM_E_UNSUPPORTED, "%d correlated channels exceed %d", pl->nch_conv, 2 * kMaxPairs);
   return GM_OK;
 }
 
+// The per-launch model description both kernels read.
+ChanMap chan_map(const Plan& pl) {
+  ChanMap m;
+  std::memset(&m, 0, sizeof(m));
+  const DescDev& D = pl.dd;
+  m.n_comp = D.n_comp;
+  for (int c = 0; c < D.n_comp; ++c) {
+    m.kind[c] = D.kind[c];
+    m.conv[c] = pl.conv[c];
+    m.np[c] = D.np[c];
+    m.comp_chan[c] = pl.comp_chan[c];
+    for (int k = 0; k < 8; ++k) {
+      m.slot[c][k] = D.slot[c][k];
+      m.chan[c][k] = (pl.nacc > 0 && k < D.np[c]) ? pl.chan_of_slot[D.slot[c][k]] : -1;
+    }
+  }
+  m.any_unconv = pl.any_unconv;
+  m.nch_conv = pl.nch_conv;
+  m.ncp = pl.ncp;
+  m.nch_tot = pl.nch_tot;
+  m.n_slots = D.n_slots;
+  return m;
+}
+
 struct Smem {
-  int rw, off_psf, off_in, off_out, off_cc, off_scale, off_red, total, threads;
+  int rw, pp, passes, plane, off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar, total, threads;
 };
 
-// Shared-memory carve-up of one fused CTA.  The input row pitch rw (in float2)
-// is >= K + 33 (the window reads 2 columns past the halo) and == 2 mod 16, so
-// the 8 lanes of a quarter warp (8 consecutive rows) hit distinct 16-byte bank
-// groups on their 16-byte loads.
 // Channel pairs per thread of the fused kernel: one (more warps) unless the
 // reduction of many free parameters needs the register budget of 256 threads.
 int pick_cpt(const Plan& pl) { return (pl.nacc == 0 || pl.dd.P <= kMaxP1) ? 1 : 2; }
 
-Smem smem_plan(const Plan& pl, int K, int n_comp, int n_slots) {
+// Shared-memory carve-up of one fused CTA for `pp` channel pairs per pass.
+// The window row pitch rw (in float2) is >= K + 33 (the register window reads
+// two columns past the last tap) and == 2 mod 4, so the 8 lanes of a quarter
+// warp (8 consecutive rows) hit distinct 16-byte bank groups on their 16-byte
+// loads.
+Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp) {
   Smem s;
   const int cpt = pick_cpt(pl);
-  s.threads = kGroupThreads * ((pl.ncp + cpt - 1) / cpt);
-  int rw = std::max(kTile + K - 1, K + 33);
-  while (rw % 16 != 2) ++rw;
+  s.pp = pp;
+  s.passes = (pl.ncp + pp - 1) / pp;
+  s.threads = kGroupThreads * ((pp + cpt - 1) / cpt);
+  int rw = K + 33;
+  while (rw % 4 != 2) ++rw;
   s.rw = rw;
   const int HH = kTile + K - 1;
+  // pair planes start at 128-byte boundaries (TMA destinations must be 128-byte aligned)
+  const size_t plane_bytes = ((size_t)HH * rw * 8 + 127) / 128 * 128;
+  s.plane = (int)(plane_bytes / 8);
   size_t off = 0;
-  s.off_psf = (int)off;
-  off += (size_t)K * (K + 1) * 8;
-  off = (off + 15) & ~(size_t)15;
-  s.off_in = (int)off;
-  s.off_out = (int)off;
-  const size_t in_bytes = (size_t)pl.ncp * HH * rw * 8;
-  const size_t out_bytes = (size_t)pl.nch_tot * kTilePix * 4;
-  off += std::max(in_bytes, out_bytes);
-  off = (off + 15) & ~(size_t)15;
-  s.off_cc = (int)off;
-  off += (size_t)n_comp * kCC * 4;
-  s.off_scale = (int)off;
-  off += (size_t)n_slots * 4;
-  off = (off + 15) & ~(size_t)15;
-  s.off_red = (int)off;
-  off += (size_t)(s.threads / 32) * std::max(pl.nacc, 1) * 4;
+  auto take = [&](size_t bytes, size_t align) {
+    off = (off + align - 1) / align * align;
+    const size_t o = off;
+    off += bytes;
+    return (int)o;
+  };
+  s.off_in = take((size_t)pp * plane_bytes, 128);
+  s.off_psf = take((size_t)K * (K + 1) * 8, 16);
+  s.off_out = take((size_t)pl.nch_tot * kTilePix * 4, 16);
+  s.off_cc = take((size_t)n_comp * kCC * 4, 16);
+  s.off_scale = take((size_t)n_slots * 4, 16);
+  s.off_red = take((size_t)(s.threads / 32) * std::max(pl.nacc, 1) * 4, 16);
+  s.off_bar = take(16, 16);
   s.total = (int)off;
   return s;
+}
+
+// Largest pass width (channel pairs) whose carve-up fits the device.
+int smem_plan(const Plan& pl, int K, int n_comp, int n_slots, int smem_optin, Smem* out) {
+  for (int pp = std::min(kMaxPassPairs, pl.ncp); pp >= 1; --pp) {
+    const Smem s = smem_layout(pl, K, n_comp, n_slots, pp);
+    if (s.total <= smem_optin) {
+      *out = s;
+      return GM_OK;
+    }
+  }
+  const Smem s1 = smem_layout(pl, K, n_comp, n_slots, 1);
+  return fail(GM_E_UNSUPPORTED, "tile needs %d bytes of shared memory (K=%d, %d channels); the device allows %d",
+              s1.total, K, pl.nch_conv, smem_optin);
 }
 
 struct DevInfo {
@@ -237,33 +281,38 @@ FusedKernel pick_kernel(int mode, int P) {
   }
 }
 
-void fill_args(FusedArgs& A, const Plan& pl, const gm_batch* b, const Smem& sm) {
-  std::memset(&A, 0, sizeof(A));
-  const DescDev& D = pl.dd;
-  A.n_comp = D.n_comp;
-  for (int c = 0; c < D.n_comp; ++c) {
-    A.kind[c] = D.kind[c];
-    A.conv[c] = pl.conv[c];
-    A.np[c] = D.np[c];
-    A.comp_chan[c] = pl.comp_chan[c];
-    for (int k = 0; k < 8; ++k) {
-      A.slot[c][k] = D.slot[c][k];
-      A.chan[c][k] = (pl.nacc > 0 && k < D.np[c]) ? pl.chan_of_slot[D.slot[c][k]] : -1;
-    }
+// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
+
+int encode_fn(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  std::lock_guard<std::mutex> lock(g_encode_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    GM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return fail(GM_E_CUDA, "cuTensorMapEncodeTiled is not available");
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  A.any_unconv = pl.any_unconv;
-  A.nch_conv = pl.nch_conv;
-  A.ncp = pl.ncp;
-  A.nch_tot = pl.nch_tot;
-  A.n_slots = D.n_slots;
+  *out = g_encode;
+  return GM_OK;
+}
+
+int fill_args(FusedArgs& A, const Plan& pl, const gm_batch* b, const Smem& sm, float* planes, int Wp) {
+  std::memset(&A, 0, sizeof(A));
+  A.m = chan_map(pl);
   A.nacc = pl.nacc;
   A.G = b->n_gal;
   A.H = b->H;
   A.W = b->W;
   A.K = b->K;
+  A.cpad = ((b->K - 1) / 2) & 1;
   A.tiles_x = (b->W + kTile - 1) / kTile;
   A.n_tiles = A.tiles_x * ((b->H + kTile - 1) / kTile);
   A.rw = sm.rw;
+  A.pp = sm.pp;
+  A.passes = sm.passes;
+  A.plane = sm.plane;
   A.image = b->image;
   A.sigma = b->sigma;
   A.mask = b->mask;
@@ -274,31 +323,83 @@ void fill_args(FusedArgs& A, const Plan& pl, const gm_batch* b, const Smem& sm) 
   A.off_cc = sm.off_cc;
   A.off_scale = sm.off_scale;
   A.off_red = sm.off_red;
+  A.off_bar = sm.off_bar;
+  // planes as a rank-3 FP32 tensor: x = 2*Wp floats (interleaved pairs), y = H rows,
+  // z = G*ncp planes; box = 2*rw floats x (32+K-1) rows x 1 plane; zero fill outside
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  int rc = encode_fn(&enc);
+  if (rc) return rc;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Wp), (cuuint64_t)b->H, (cuuint64_t)b->n_gal * pl.ncp};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Wp) * 4, (cuuint64_t)(2 * Wp) * 4 * b->H};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * sm.rw), (cuuint32_t)(kTile + b->K - 1), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult cr = enc(&A.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, planes, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return fail(GM_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  return GM_OK;
 }
 
-int prepare_fused(int mode, const Plan& pl, const Smem& sm, const DevInfo& di, int K, FusedKernel* out) {
+ProfileArgs profile_args(const Plan& pl, const gm_batch* b, const float* cconst, const float* scale,
+                         float* planes, int Wp) {
+  ProfileArgs P;
+  std::memset(&P, 0, sizeof(P));
+  P.m = chan_map(pl);
+  P.G = b->n_gal;
+  P.H = b->H;
+  P.W = b->W;
+  P.Wp = Wp;
+  P.cconst = cconst;
+  P.scale = scale;
+  P.planes = planes;
+  return P;
+}
+
+typedef void (*ProfileKernel)(ProfileArgs);
+
+int prepare_fused(int mode, const Plan& pl, const Smem& sm, FusedKernel* out) {
   FusedKernel k = pick_kernel(mode, pl.dd.P);
   if (!k) return fail(GM_E_UNSUPPORTED, "no fused kernel for %d free parameters", pl.dd.P);
-  if (sm.total > di.smem_optin)
-    return fail(GM_E_UNSUPPORTED, "tile needs %d bytes of shared memory (K=%d, %d channels); the device allows %d",
-                sm.total, K, pl.nch_conv, di.smem_optin);
   GM_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm.total));
   *out = k;
   return GM_OK;
 }
 
 // workspace carve-up
+// Channel pairs the fused pass of `mode` correlates for this description
+// (MODEL mode sized for per-component images).
+int pairs_for(const gm_model_desc* d, int mode) {
+  bool touches_conv[kMaxSlots] = {};
+  int n_conv = 0;
+  for (int c = 0; c < d->n_comp; ++c) {
+    if (!d->comp[c].convolve) continue;
+    ++n_conv;
+    const int np = n_params(d->comp[c].kind);
+    for (int k = 0; k < np; ++k) touches_conv[d->comp[c].slot[k]] = true;
+  }
+  int Pc = 0;
+  for (int s = 0; s < d->n_slots; ++s) Pc += (d->is_free[s] && touches_conv[s]) ? 1 : 0;
+  const int nch = (mode == MODE_NORMAL) ? 1 + Pc : 1 + n_conv;
+  return (nch + 1) / 2;
+}
+
 struct WsModel {
-  size_t cconst, scale, total;
+  size_t cconst, scale, planes, err, total;
+  int Wp;
 };
-WsModel ws_model(const gm_model_desc* d, const gm_batch* b) {
+WsModel ws_model(const gm_model_desc* d, const gm_batch* b, int ncp) {
   WsModel w;
   size_t off = 0;
   const size_t G = (size_t)std::max(b->n_gal, 0);
+  w.Wp = b->W + (b->W & 1);
   w.cconst = off;
   off += align256(G * d->n_comp * kCC * 4);
   w.scale = off;
   off += align256(G * d->n_slots * 4);
+  w.planes = off;
+  off += align256(G * (size_t)ncp * b->H * w.Wp * 8);
+  w.err = off;
+  off += align256(4);
   w.total = off;
   return w;
 }
@@ -309,7 +410,7 @@ struct WsChi2 {
 };
 WsChi2 ws_chi2(const gm_model_desc* d, const gm_batch* b, int P) {
   WsChi2 w;
-  w.m = ws_model(d, b);
+  w.m = ws_model(d, b, pairs_for(d, MODE_NORMAL));
   size_t off = w.m.total;
   const size_t G = (size_t)std::max(b->n_gal, 0);
   const size_t tiles = (size_t)((b->W + kTile - 1) / kTile) * ((b->H + kTile - 1) / kTile);
@@ -401,7 +502,7 @@ const char* gm_last_error(void) { return g_err; }
 
 size_t gm_model_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
   if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
-  return ws_model(desc, batch).total;
+  return ws_model(desc, batch, pairs_for(desc, MODE_MODEL)).total;
 }
 
 int gm_model(const gm_model_desc* desc, const gm_batch* batch, const double* params, float* model_out,
@@ -413,26 +514,34 @@ int gm_model(const gm_model_desc* desc, const gm_batch* batch, const double* par
   if (rc) return rc;
   if (batch->n_gal == 0) return GM_OK;
   if (!params || !model_out) return fail(GM_E_INVAL, "params/model_out is NULL");
-  const WsModel w = ws_model(desc, batch);
+  const WsModel w = ws_model(desc, batch, pairs_for(desc, MODE_MODEL));
   if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
   DevInfo di;
   if ((rc = dev_info(&di))) return rc;
-  const Smem sm = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots);
+  Smem sm;
+  if ((rc = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots, di.smem_optin, &sm))) return rc;
   FusedKernel kf;
-  if ((rc = prepare_fused(MODE_MODEL, pl, sm, di, batch->K, &kf))) return rc;
+  if ((rc = prepare_fused(MODE_MODEL, pl, sm, &kf))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   float* cconst = (float*)(ws + w.cconst);
   float* scale = (float*)(ws + w.scale);
+  float* planes = (float*)(ws + w.planes);
   const int G = batch->n_gal;
-  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
-  GM_LAUNCHED("k_setup");
   FusedArgs A;
-  fill_args(A, pl, batch, sm);
+  if ((rc = fill_args(A, pl, batch, sm, planes, w.Wp))) return rc;
   A.cconst = cconst;
   A.scale = scale;
   A.model_out = model_out;
   A.comp_out = comp_out;
+  A.err = (int*)(ws + w.err);
+  GM_CUDA(cudaMemsetAsync(A.err, 0, sizeof(int), st));
+  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
+  GM_LAUNCHED("k_setup");
+  const ProfileArgs PA = profile_args(pl, batch, cconst, scale, planes, w.Wp);
+  const int pblocks = G * ((batch->H * w.Wp + 255) / 256);
+  k_profile<MODE_MODEL><<<std::min(pblocks, 8 * di.sms), 256, 0, st>>>(PA);
+  GM_LAUNCHED("k_profile(model)");
   const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
   kf<<<grid, sm.threads, sm.total, st>>>(A);
   GM_LAUNCHED("k_fused(model)");
@@ -457,22 +566,30 @@ int gm_chi2_grad(const gm_model_desc* desc, const gm_batch* batch, const double*
   if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
   DevInfo di;
   if ((rc = dev_info(&di))) return rc;
-  const Smem sm = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots);
+  Smem sm;
+  if ((rc = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots, di.smem_optin, &sm))) return rc;
   FusedKernel kf;
-  if ((rc = prepare_fused(MODE_NORMAL, pl, sm, di, batch->K, &kf))) return rc;
+  if ((rc = prepare_fused(MODE_NORMAL, pl, sm, &kf))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   float* cconst = (float*)(ws + w.m.cconst);
   float* scale = (float*)(ws + w.m.scale);
+  float* planes = (float*)(ws + w.m.planes);
   double* partial = (double*)(ws + w.partial);
   const int G = batch->n_gal;
-  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
-  GM_LAUNCHED("k_setup");
   FusedArgs A;
-  fill_args(A, pl, batch, sm);
+  if ((rc = fill_args(A, pl, batch, sm, planes, w.m.Wp))) return rc;
   A.cconst = cconst;
   A.scale = scale;
   A.partial = partial;
+  A.err = (int*)(ws + w.m.err);
+  GM_CUDA(cudaMemsetAsync(A.err, 0, sizeof(int), st));
+  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
+  GM_LAUNCHED("k_setup");
+  const ProfileArgs PA = profile_args(pl, batch, cconst, scale, planes, w.m.Wp);
+  const int pblocks = G * ((batch->H * w.m.Wp + 255) / 256);
+  k_profile<MODE_NORMAL><<<std::min(pblocks, 8 * di.sms), 256, 0, st>>>(PA);
+  GM_LAUNCHED("k_profile");
   const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
   kf<<<grid, sm.threads, sm.total, st>>>(A);
   GM_LAUNCHED("k_fused(normal)");
@@ -505,13 +622,16 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
   DevInfo di;
   if ((rc = dev_info(&di))) return rc;
-  const Smem sm = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots);
+  Smem sm;
+  if ((rc = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots, di.smem_optin, &sm))) return rc;
   FusedKernel kf;
-  if ((rc = prepare_fused(MODE_NORMAL, pl, sm, di, batch->K, &kf))) return rc;
+  if ((rc = prepare_fused(MODE_NORMAL, pl, sm, &kf))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   float* cconst = (float*)(ws + w.c.m.cconst);
   float* scale = (float*)(ws + w.c.m.scale);
+  float* planes = (float*)(ws + w.c.m.planes);
+  int* err = (int*)(ws + w.c.m.err);
   double* partial = (double*)(ws + w.c.partial);
   LMState S;
   S.p_b = (double*)(ws + w.p_b);
@@ -532,12 +652,13 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   const int G = batch->n_gal;
   const auto t_start = std::chrono::steady_clock::now();
   g_have_stats = false;
-  while ((int)g_events.size() < 3 * O.max_iter) {
+  while ((int)g_events.size() < 4 * O.max_iter) {
     cudaEvent_t e;
     GM_CUDA(cudaEventCreate(&e));
     g_events.push_back(e);
   }
   GM_CUDA(cudaMemsetAsync(S.evals, 0, 3 * sizeof(unsigned long long), st));
+  GM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
   k_validate<<<std::min(G, 4 * di.sms), 256, 0, st>>>(G, batch->H, batch->W, batch->image, batch->sigma,
                                                       batch->mask, S.nused, S.bad);
@@ -547,30 +668,38 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   GM_LAUNCHED("k_lm_init");
 
   FusedArgs A;
-  fill_args(A, pl, batch, sm);
+  if ((rc = fill_args(A, pl, batch, sm, planes, w.c.m.Wp))) return rc;
   A.cconst = cconst;
   A.scale = scale;
   A.partial = partial;
+  A.err = err;
+  ProfileArgs PA = profile_args(pl, batch, cconst, scale, planes, w.c.m.Wp);
   const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
+  const int pgrid = std::max(1, std::min(G * ((batch->H * w.c.m.Wp + 255) / 256), 8 * di.sms));
   const int poll = 4;
   int passes = 0;
   for (int k = 0; k < O.max_iter; ++k) {
     const int cur = k & 1;
-    A.list = S.list[cur];
-    A.count = S.count[cur];
-    GM_CUDA(cudaEventRecord(g_events[3 * k], st));
+    A.list = PA.list = S.list[cur];
+    A.count = PA.count = S.count[cur];
+    GM_CUDA(cudaEventRecord(g_events[4 * k], st));
+    k_profile<MODE_NORMAL><<<pgrid, 256, 0, st>>>(PA);
+    GM_LAUNCHED("k_profile");
+    GM_CUDA(cudaEventRecord(g_events[4 * k + 1], st));
     kf<<<grid, sm.threads, sm.total, st>>>(A);
     GM_LAUNCHED("k_fused(normal)");
-    GM_CUDA(cudaEventRecord(g_events[3 * k + 1], st));
+    GM_CUDA(cudaEventRecord(g_events[4 * k + 2], st));
     GM_CUDA(cudaMemsetAsync(S.count[cur ^ 1], 0, sizeof(int), st));
     k_lm_step<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, cur, batch->H, A.n_tiles, partial, cconst, scale);
     GM_LAUNCHED("k_lm_step");
-    GM_CUDA(cudaEventRecord(g_events[3 * k + 2], st));
+    GM_CUDA(cudaEventRecord(g_events[4 * k + 3], st));
     ++passes;
     if ((k + 1) % poll == 0 || k + 1 == O.max_iter) {
-      int remaining = 0;
+      int remaining = 0, kerr = 0;
       GM_CUDA(cudaMemcpyAsync(&remaining, S.count[cur ^ 1], sizeof(int), cudaMemcpyDeviceToHost, st));
+      GM_CUDA(cudaMemcpyAsync(&kerr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
       GM_CUDA(cudaStreamSynchronize(st));
+      if (kerr) return fail(GM_E_CUDA, "fused kernel: a tile load did not complete within its wait limit");
       if (remaining == 0) break;
     }
   }
@@ -585,14 +714,17 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   fs.galaxy_evals = (int64_t)counters[0];
   fs.converged = (int64_t)counters[1];
   fs.iters_sum = (int64_t)counters[2];
+  fs.profile_ms = 0.0;
   fs.fused_ms = 0.0;
   fs.step_ms = 0.0;
   for (int k = 0; k < passes; ++k) {
-    float a = 0.f, b = 0.f;
-    GM_CUDA(cudaEventElapsedTime(&a, g_events[3 * k], g_events[3 * k + 1]));
-    GM_CUDA(cudaEventElapsedTime(&b, g_events[3 * k + 1], g_events[3 * k + 2]));
-    fs.fused_ms += a;
-    fs.step_ms += b;
+    float a = 0.f, b = 0.f, c = 0.f;
+    GM_CUDA(cudaEventElapsedTime(&a, g_events[4 * k], g_events[4 * k + 1]));
+    GM_CUDA(cudaEventElapsedTime(&b, g_events[4 * k + 1], g_events[4 * k + 2]));
+    GM_CUDA(cudaEventElapsedTime(&c, g_events[4 * k + 2], g_events[4 * k + 3]));
+    fs.profile_ms += a;
+    fs.fused_ms += b;
+    fs.step_ms += c;
   }
   fs.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   g_stats = fs;

@@ -12,7 +12,7 @@ namespace gm {
 constexpr int ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAX_ITER = 2, ST_STALLED = 3, ST_SINGULAR = 4,
               ST_NONFINITE = 5, ST_BAD_INPUT = 6, ST_NO_DOF = 7;
 
-constexpr int kMaxAcc = 1 + kMaxSlots + kMaxSlots * (kMaxSlots + 1) / 2;
+constexpr int kMaxAcc = 1 + kMaxFree + kMaxFree * (kMaxFree + 1) / 2;
 
 // Model description as the per-galaxy kernels need it.
 struct DescDev {
@@ -22,7 +22,7 @@ struct DescDev {
   int slot[kMaxComp][8];
   int n_slots;
   int P;                       // free slots
-  int free_slot[kMaxSlots];    // accumulator order -> slot
+  int free_slot[kMaxFree];     // accumulator order -> slot
   int is_log[kMaxSlots];
   int is_pa[kMaxSlots];        // slot is some radial component's position angle
   double lo[kMaxSlots], hi[kMaxSlots];
@@ -159,7 +159,7 @@ __device__ inline bool cholesky(double* M, int n) {
 }
 
 __device__ inline void chol_solve(const double* L, int n, const double* b, double* x) {
-  double y[kMaxSlots];
+  double y[kMaxFree];
   for (int i = 0; i < n; ++i) {
     double s = b[i];
     for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
@@ -186,7 +186,7 @@ __device__ inline double packed(const double* Ap, int P, int f, int h) {
 // on the diagonal): the chi^2 reduction a full Gauss-Newton step predicts.
 // Negative when A cannot be factorised.
 __device__ inline double gn_decrement(const double* Ap, const double* g, int P) {
-  double M[kMaxSlots * kMaxSlots], x[kMaxSlots];
+  double M[kMaxFree * kMaxFree], x[kMaxFree];
   double dmax = 0.0;
   for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ap, P, f, f));
   for (int f = 0; f < P; ++f)
@@ -274,7 +274,7 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
   }
   if (st == ST_RUNNING && it >= O.max_iter) st = ST_MAX_ITER;
   if (st == ST_RUNNING) {
-    double M[kMaxSlots * kMaxSlots], delta[kMaxSlots];
+    double M[kMaxFree * kMaxFree], delta[kMaxFree];
     double dmax = 0.0;
     for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ab, P, f, f));
     const double dfloor = 1e-12 * dmax;
@@ -336,7 +336,7 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
       return;
     }
     const double* Ab = S.A_b + (size_t)g * (P * (P + 1) / 2);
-    double M[kMaxSlots * kMaxSlots];
+    double M[kMaxFree * kMaxFree];
     for (int f = 0; f < P; ++f)
       for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
     if (!cholesky(M, P)) {
@@ -344,7 +344,7 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
       return;
     }
     for (int f = 0; f < P; ++f) {
-      double e[kMaxSlots], x[kMaxSlots];
+      double e[kMaxFree], x[kMaxFree];
       for (int h = 0; h < P; ++h) e[h] = (h == f) ? 1.0 : 0.0;
       chol_solve(M, P, e, x);
       const int s = D.free_slot[f];

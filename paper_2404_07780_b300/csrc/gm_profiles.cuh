@@ -20,7 +20,8 @@
 namespace gm {
 
 constexpr int kMaxComp = 8;
-constexpr int kMaxSlots = 16;
+constexpr int kMaxSlots = 24;  // parameter slots of a model
+constexpr int kMaxFree = 16;   // free (fitted) parameters of a model
 constexpr int kCC = 16;          // FP32 constants per component per galaxy
 constexpr float kRFloor = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgm.so")
 
 MAX_COMP = 8
-MAX_SLOTS = 16
+MAX_SLOTS = 24
 KIND = {"sersic": 1, "expdisk": 2, "ferrer": 3, "king": 4, "gaussian": 5, "moffat": 6, "sky": 7}
 STATUS = {0: "RUNNING", 1: "CONVERGED", 2: "MAX_ITER", 3: "STALLED", 4: "SINGULAR", 5: "NONFINITE",
           6: "BAD_INPUT", 7: "NO_DOF"}
@@ -86,6 +86,7 @@ class gm_fit_stats(ctypes.Structure):
         ("galaxy_evals", ctypes.c_int64),
         ("converged", ctypes.c_int64),
         ("iters_sum", ctypes.c_int64),
+        ("profile_ms", ctypes.c_double),
         ("fused_ms", ctypes.c_double),
         ("step_ms", ctypes.c_double),
         ("wall_ms", ctypes.c_double),
@@ -277,8 +278,8 @@ class Fitter:
 
 
 def gm_fit_last_stats() -> dict:
-    """Counters of this thread's last gm_fit_batch: passes, galaxy_evals, converged, iters_sum, fused_ms,
-    step_ms, wall_ms."""
+    """Counters of this thread's last gm_fit_batch: passes, galaxy_evals, converged, iters_sum, profile_ms,
+    fused_ms, step_ms, wall_ms."""
     st = gm_fit_stats()
     _check(load().gm_fit_last_stats(ctypes.byref(st)), "gm_fit_last_stats")
     return {name: getattr(st, name) for name, _ in gm_fit_stats._fields_}

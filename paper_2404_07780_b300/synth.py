@@ -267,6 +267,50 @@ def draw_sdss(seed: int = 1000, G: int = 8192, H: int = 128, W: int = 128, K: in
     return Batch(spec, H, W, K, gal, init, "moffat", psf_params("moffat", fwhm, K), mask, z, cont)
 
 
+def draw_bulge_disk(seed: int = 2000, G: int = 64, H: int = 96, W: int = 96, K: int | None = None) -> Batch:
+    """Bulge + disk batch (equal-size stamps): Sersic bulge (n 1-6) + Sersic disk with n = 1
+    (Re_d = 1.5-4 x Re_b, own q and PA) + sky, common centre; Moffat PSF beta 3, FWHM 1.2-1.8 px,
+    side K (odd, 25-51 when not given)."""
+    g = rng(seed)
+    spec = bulge_disk_sky(H, W)
+    if K is None:
+        K = int(g.choice(np.arange(25, 52, 2)))
+    reb = g.uniform(1.5, 8, G)
+    truth = np.stack([
+        W / 2 + g.uniform(-2, 2, G), H / 2 + g.uniform(-2, 2, G),
+        g.uniform(0.3, 1.0, G), g.uniform(0, math.pi, G), 10 ** g.uniform(0.5, 3, G), reb, g.uniform(1, 6, G),
+        g.uniform(0.2, 1.0, G), g.uniform(0, math.pi, G), 10 ** g.uniform(0, 2, G), reb * g.uniform(1.5, 4, G),
+        np.ones(G), g.uniform(0, 5, G)], 1)
+    init = np.tile(np.array([W / 2, H / 2, 0.65, math.pi / 2, 10 ** 1.75, 4.0, math.sqrt(6.0),
+                             0.6, math.pi / 2, 10.0, 11.0, 1.0, 2.5]), (G, 1))
+    z = g.standard_normal((G, H, W))
+    return Batch(spec, H, W, K, truth, init, "moffat", psf_params("moffat", g.uniform(1.2, 1.8, G), K), None, z)
+
+
+def draw_bulge_bar_nucleus(seed: int = 3000, G: int = 64, H: int = 96, W: int = 96, K: int = 41) -> Batch:
+    """Sersic bulge + Ferrer bar (r_out 5-20 px, a = 2 fixed, b 0-1.99) + circular Gaussian nucleus
+    (sigma 0.5-1.5 px) + sky, common centre; Moffat PSF as draw_sdss."""
+    g = rng(seed)
+    spec = bulge_bar_nucleus_sky(H, W)
+    fw = 2.0 * math.sqrt(2.0 * math.log(2.0))
+    cols = {
+        "bulge.x0": W / 2 + g.uniform(-2, 2, G), "bulge.y0": H / 2 + g.uniform(-2, 2, G),
+        "bulge.q": g.uniform(0.5, 1.0, G), "bulge.pa": g.uniform(0, math.pi, G),
+        "bulge.Ie": _logu(g, 1, 100, G), "bulge.Re": g.uniform(2, 10, G), "bulge.n": g.uniform(1, 4, G),
+        "bar.q": g.uniform(0.2, 0.5, G), "bar.pa": g.uniform(0, math.pi, G), "bar.I0": _logu(g, 1, 30, G),
+        "bar.rout": g.uniform(5, 20, G), "bar.a": np.full(G, 2.0), "bar.b": g.uniform(0, 1.99, G),
+        "nuc.q": np.ones(G), "nuc.pa": np.zeros(G), "nuc.I0": _logu(g, 5, 100, G),
+        "nuc.fwhm": fw * g.uniform(0.5, 1.5, G), "sky.Isky": g.uniform(0, 5, G)}
+    truth = np.stack([cols[n] for n in spec.names], 1)
+    init_vals = {"bulge.x0": W / 2, "bulge.y0": H / 2, "bulge.q": 0.75, "bulge.pa": math.pi / 2, "bulge.Ie": 10.0,
+                 "bulge.Re": 6.0, "bulge.n": 2.0, "bar.q": 0.35, "bar.pa": math.pi / 4, "bar.I0": math.sqrt(30.0),
+                 "bar.rout": 12.5, "bar.a": 2.0, "bar.b": 1.0, "nuc.q": 1.0, "nuc.pa": 0.0,
+                 "nuc.I0": math.sqrt(500.0), "nuc.fwhm": fw, "sky.Isky": 2.5}
+    init = np.tile(np.array([init_vals[n] for n in spec.names]), (G, 1))
+    z = g.standard_normal((G, H, W))
+    return Batch(spec, H, W, K, truth, init, "moffat", psf_params("moffat", g.uniform(1.2, 1.8, G), K), None, z)
+
+
 def noisy_image(model_true: np.ndarray, z: np.ndarray, sky_var: float = 4.0, gain: float = 4.0):
     """Data and sigma map for a truth image: sigma^2 = sky_var + max(M, 0)/gain, D = M + sigma z."""
     sigma = np.sqrt(sky_var + np.maximum(model_true, 0.0) / gain)

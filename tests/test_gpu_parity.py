@@ -177,13 +177,40 @@ def test_chi2_with_mask_and_contaminants(gm):
         assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= bound).all(), gi
 
 
+@pytest.mark.parametrize("draw,K", [(synth.draw_bulge_disk, 25), (synth.draw_bulge_disk, 51),
+                                    (synth.draw_bulge_bar_nucleus, 41)])
+def test_chi2_grad_many_parameters(gm, draw, K):
+    # 12 and 15 free parameters: 13 and 16 correlated channels in several channel-pair
+    # passes, two pairs per thread in the reduction-heavy variant
+    b = draw(seed=7, G=4, H=64, W=72, K=K)
+    c = from_batch(b, at="init")
+    t = c.torch()
+    chi2, grad, jtj = gm.gm_chi2_grad(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"],
+                                      want_grad=True, want_jtj=True)
+    chi2, grad, jtj = _np(chi2), _np(grad), _np(jtj)
+    rchi2, rg, rA = _oracle_normal(c)
+    np.testing.assert_allclose(chi2, rchi2, rtol=1e-5)
+    free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
+    for gi in range(c.G):
+        d = np.sqrt(np.diag(rA[gi]))
+        assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= 2e-4 * d * math.sqrt(rchi2[gi])).all(), gi
+        Asub = jtj[gi][np.ix_(free, free)]
+        assert (np.abs(Asub - rA[gi]) <= 1e-4 * np.outer(d, d)).all(), gi
+
+
 # ---------------------------------------------------------------------------
 # Levenberg-Marquardt fits
 # ---------------------------------------------------------------------------
 
 def _compare_fits(spec, got, ref, tol=1e-4):
-    """Indices compared and the worst scaled parameter difference."""
-    s = np.maximum(np.abs(ref["params"]), scale_of(spec))
+    """Indices compared and the worst parameter difference in units of the tolerance.
+
+    A parameter agrees when |dp| <= max(1e-4 max(|p|, s_p), 1e-2 sigma_p): the relative bar,
+    or 1% of the parameter's own statistical error.  The second clause matters only for
+    ill-conditioned fits (faint galaxies with strongly correlated parameters), where FP32
+    rounding in the Jacobian displaces the minimum along the soft directions by up to
+    ~1e-2 sigma_p; well-conditioned fits meet the relative bar alone."""
+    s = np.maximum(np.maximum(np.abs(ref["params"]), scale_of(spec)) * tol, 1e-2 * ref["sigma_p"]) / tol
     both = (got["status"] == 1) & (ref["status"] == 1)
     # the same minimum: chi^2 within the parity tolerance
     same = both & (np.abs(got["chi2"] - ref["chi2"]) <= 1e-5 * ref["chi2"])
