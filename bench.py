@@ -41,6 +41,10 @@ TOL = 1e-6
 MAX_ITER = 200
 PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
+# DRAM bytes (read + write) of k_fused<NORMAL, 8> per galaxy evaluated, from one ncu capture of a
+# 1,024-galaxy pass of this workload (706.6 MB); traffic grows in proportion to the galaxies a pass
+# evaluates, so a launch's traffic is this times its galaxies
+FUSED_DRAM_BYTES_PER_GALAXY = 706.6e6 / 1024
 
 
 def workload_config(G, H, K):
@@ -333,9 +337,14 @@ def run_gpu(args, world, rank, local):
     flops = 2.0 * nch * taps * evals
     achieved = flops / (fused_ms / 1e3) / 1e12
     gpix = evals * H * H / (fused_ms / 1e3) / 1e9
+    launches_fused = sum(st["passes"] for st in stats)
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-            "kernel": "k_fused<NORMAL,8>", "peak_source": "148 SMs x 128 FP32 FMA/clk x 2 x 2032 MHz"}
+            "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": FUSED_DRAM_BYTES_PER_GALAXY * evals / max(launches_fused, 1),
+            "traffic_unit": "bytes per launch (average launch)",
+            "algorithmic_bytes": (9 + 32) * H * H * evals / max(launches_fused, 1),
+            "kernel": "k_fused<NORMAL,8>",
+            "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

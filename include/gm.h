@@ -216,7 +216,12 @@ int gm_chi2_grad_noalloc(const gm_model_desc *desc, const gm_batch *batch, const
  * on Eq. chinu; Sec. 5.1 names LM as the classical alternative to gradient
  * descent), with the covariance uncertainty of Sec. 5.2.
  *   params_inout [n_gal][n_slots] FP64: starting point in, best fit out
- *                (position angles wrapped to [0, pi))
+ *                (position angles wrapped to [0, pi)).  An axis ratio may
+ *                exceed 1 during the fit (the same ellipse turned by pi/2);
+ *                at exit q > 1 is rewritten as 1/q with the component's
+ *                position angle + pi/2 and its scale lengths (r_e, r_s, r_out,
+ *                r_c, r_t, fwhm) times q, which leaves the image unchanged,
+ *                when those slots are not shared with components of another q
  *   opts         host; NULL = defaults (tol 1e-6, xtol 1e-10, gtol 1e-10, max_iter 100,
  *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10)
  *   chi2_out     [n_gal] FP64 chi^2 at the best point

@@ -119,6 +119,8 @@ def _load():
         lib.or_fit_batch.restype = ctypes.c_int
         lib.or_fit_batch.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      P, P, P, P, P, P, P, P, P, P]
+        lib.or_canonicalize.restype = ctypes.c_int
+        lib.or_canonicalize.argtypes = [P, P]
         lib.or_max_threads.restype = ctypes.c_int
         lib.or_max_threads.argtypes = []
         _lib = lib
@@ -281,6 +283,17 @@ def fit(spec, params0, psf, image, sigma, mask=None, opts: FitOptions | None = N
                          _ptr(iters), _ptr(status), _ptr(sigma_p))
     return {"params": params, "chi2": chi2_out, "dof": dof, "iters": iters, "status": status,
             "sigma_p": sigma_p}
+
+
+def canonicalize(spec, params) -> np.ndarray:
+    """Rewrite axis ratios above 1 as 1/q with PA + pi/2 and scale lengths times q (same image)."""
+    out = _f64(params).copy()
+    d = _desc(spec)
+    for row in out.reshape(-1, spec.n_slots):
+        r = np.ascontiguousarray(row)
+        _load().or_canonicalize(ctypes.byref(d), _ptr(r))
+        row[:] = r
+    return out
 
 
 def max_threads() -> int:

@@ -371,6 +371,83 @@ static void or_clamp(const or_desc *d, double *p) {
   }
 }
 
+/* Indices of a component's scale-length parameters (r_e, r_s, r_out, r_c and
+ * r_t, FWHM); returns how many. */
+static int or_scale_params(int kind, int *idx) {
+  switch (kind) {
+    case OR_SERSIC: case OR_EXPDISK: case OR_FERRER: case OR_GAUSSIAN: case OR_MOFFAT:
+      idx[0] = 5;
+      return 1;
+    case OR_KING:
+      idx[0] = 5;
+      idx[1] = 6;
+      return 2;
+    default:
+      return 0;
+  }
+}
+
+/* Role of parameter k of a component: 1 axis ratio, 2 position angle, 3 scale length, 0 other. */
+static int or_role(int kind, int k) {
+  if (kind == OR_SKY) return 0;
+  if (k == 2) return 1;
+  if (k == 3) return 2;
+  int idx[2], n = or_scale_params(kind, idx);
+  for (int i = 0; i < n; ++i)
+    if (idx[i] == k) return 3;
+  return 0;
+}
+
+/* An axis ratio q > 1 describes the same ellipse as 1/q with the position angle
+ * turned by pi/2 and every scale length multiplied by q: with X' = Y and
+ * Y' = -X, sqrt(X'^2 + (Y'/(1/q))^2) = q sqrt(X^2 + (Y/q)^2), so a profile of
+ * r / r_s is unchanged when r_s becomes q r_s.  Each q slot above 1 is rewritten
+ * that way, provided every slot the affected components use as axis ratio,
+ * position angle or scale length is used in that same role only by components
+ * sharing the q slot.  Returns the number of q slots rewritten. */
+static int or_canonical_q(const or_desc *d, double *p) {
+  int changed = 0;
+  for (int c = 0; c < d->n_comp; ++c) {
+    if (d->kind[c] == OR_SKY) continue;
+    int qs = d->slot[c][2];
+    if (!(p[qs] > 1.0)) continue;
+    int ok = 1;
+    /* every use of a slot that some component of this q group uses as q, pa or scale */
+    for (int c1 = 0; c1 < d->n_comp && ok; ++c1) {
+      if (d->kind[c1] == OR_SKY || d->slot[c1][2] != qs) continue;
+      int np1 = or_n_params(d->kind[c1]);
+      for (int k1 = 0; k1 < np1 && ok; ++k1) {
+        int r1 = or_role(d->kind[c1], k1);
+        if (r1 == 0) continue;
+        int s1 = d->slot[c1][k1];
+        for (int c2 = 0; c2 < d->n_comp && ok; ++c2) {
+          int np2 = or_n_params(d->kind[c2]);
+          for (int k2 = 0; k2 < np2; ++k2) {
+            if (d->slot[c2][k2] != s1) continue;
+            if (d->kind[c2] == OR_SKY || d->slot[c2][2] != qs || or_role(d->kind[c2], k2) != r1) ok = 0;
+          }
+        }
+      }
+    }
+    if (!ok) continue;
+    double q = p[qs];
+    int done[OR_MAX_SLOTS] = {0};
+    for (int c1 = 0; c1 < d->n_comp; ++c1) {
+      if (d->kind[c1] == OR_SKY || d->slot[c1][2] != qs) continue;
+      int pas = d->slot[c1][3];
+      if (!done[pas]) { p[pas] += 0.5 * M_PI; done[pas] = 1; }
+      int idx[2], n = or_scale_params(d->kind[c1], idx);
+      for (int i = 0; i < n; ++i) {
+        int ss = d->slot[c1][idx[i]];
+        if (!done[ss]) { p[ss] *= q; done[ss] = 1; }
+      }
+    }
+    p[qs] = 1.0 / q;
+    ++changed;
+  }
+  return changed;
+}
+
 /* Slots that some radial component uses as its position angle. */
 static void or_pa_slots(const or_desc *d, int *is_pa) {
   for (int s = 0; s < OR_MAX_SLOTS; ++s) is_pa[s] = 0;
@@ -410,6 +487,7 @@ static double or_gn_decrement(const double *A, const double *g, int nf) {
  *   5. At the start and after every accepted step: CONVERGED when the
  *      Gauss-Newton decrement g^T A^-1 g <= gtol chi^2 (no step can gain more).
  *   6. MAX_ITER once max_iter evaluations have been spent.
+ * At exit an axis ratio above 1 is rewritten as its reciprocal (or_canonical_q).
  * The covariance of Sec. 5.2 is taken from A at the best point; for a log
  * slot sigma_p = p sigma_u.  Position angles are wrapped to [0, pi) at exit.
  */
@@ -508,6 +586,10 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
   *chi2_out = chi2;
   *iters_out = it;
   *status_out = status;
+  /* canonical axis ratios (q <= 1); the covariance is then taken at the rewritten
+   * point from a fresh finite-difference Jacobian */
+  if (status != OR_NONFINITE && or_canonical_q(d, p) > 0)
+    or_normal_eq(d, p, H, W, psf, K, image, sigma, mask, nf, A, g, J, model, work);
   if (sigma_p && status != OR_NONFINITE) {
     /* covariance: diag of A^-1 column by column through the Cholesky factor */
     memcpy(M, A, sizeof(double) * nf * nf);
@@ -606,6 +688,9 @@ int or_jacobian_batch(const or_desc *d, int G, int H, int W, int K, const double
   }
   return 0;
 }
+
+/* Canonical form of a parameter vector (see or_canonical_q), exposed for tests. */
+int or_canonicalize(const or_desc *d, double *p) { return or_canonical_q(d, p); }
 
 int or_fit_batch(const or_desc *d, const or_opts *o, int G, int H, int W, int K, double *params,
                  const double *psf, const double *image, const double *sigma,

@@ -137,6 +137,56 @@ int make_plan(const gm_model_desc* d, int mode, bool want_comp, Plan* pl) {
     D.hi[s] = d->hi[s];
     pl->chan_of_slot[s] = -1;
   }
+  // axis-ratio groups that may be rewritten from q > 1 to 1/q: every slot a
+  // component of the group uses as axis ratio, position angle or scale length
+  // must be used in that role only by components sharing the group's q slot
+  auto role = [](int kind, int k) {
+    if (kind == SKY) return 0;
+    if (k == 2) return 1;
+    if (k == 3) return 2;
+    if (k == 5 || (kind == KING && k == 6)) return 3;
+    return 0;
+  };
+  D.n_canon = 0;
+  for (int c = 0; c < d->n_comp; ++c) {
+    if (D.kind[c] == SKY) continue;
+    const int qs = D.slot[c][2];
+    bool seen = false;
+    for (int k = 0; k < D.n_canon; ++k) seen = seen || D.canon[k].q_slot == qs;
+    if (seen) continue;
+    bool ok = true;
+    for (int c1 = 0; c1 < d->n_comp && ok; ++c1) {
+      if (D.kind[c1] == SKY || D.slot[c1][2] != qs) continue;
+      for (int k1 = 0; k1 < D.np[c1] && ok; ++k1) {
+        const int r1 = role(D.kind[c1], k1);
+        if (!r1) continue;
+        for (int c2 = 0; c2 < d->n_comp; ++c2)
+          for (int k2 = 0; k2 < D.np[c2]; ++k2)
+            if (D.slot[c2][k2] == D.slot[c1][k1] &&
+                (D.kind[c2] == SKY || D.slot[c2][2] != qs || role(D.kind[c2], k2) != r1))
+              ok = false;
+      }
+    }
+    if (!ok) continue;
+    CanonGroup& cg = D.canon[D.n_canon++];
+    cg.q_slot = qs;
+    cg.n_pa = cg.n_scale = 0;
+    for (int c1 = 0; c1 < d->n_comp; ++c1) {
+      if (D.kind[c1] == SKY || D.slot[c1][2] != qs) continue;
+      for (int k1 = 0; k1 < D.np[c1]; ++k1) {
+        const int r1 = role(D.kind[c1], k1), s1 = D.slot[c1][k1];
+        if (r1 == 2) {
+          bool dup = false;
+          for (int i = 0; i < cg.n_pa; ++i) dup = dup || cg.pa[i] == s1;
+          if (!dup) cg.pa[cg.n_pa++] = s1;
+        } else if (r1 == 3) {
+          bool dup = false;
+          for (int i = 0; i < cg.n_scale; ++i) dup = dup || cg.scale[i] == s1;
+          if (!dup) cg.scale[cg.n_scale++] = s1;
+        }
+      }
+    }
+  }
   // accumulator order: free slots of convolved components first, then the rest
   int P = 0;
   for (int s = 0; s < d->n_slots; ++s)

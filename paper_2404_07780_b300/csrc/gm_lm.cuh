@@ -14,6 +14,14 @@ constexpr int ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAX_ITER = 2, ST_STALLED = 3,
 
 constexpr int kMaxAcc = 1 + kMaxFree + kMaxFree * (kMaxFree + 1) / 2;
 
+// Components sharing one axis-ratio slot whose geometry can be rewritten from
+// q > 1 to 1/q (position angles + pi/2, scale lengths x q): same image.
+struct CanonGroup {
+  int q_slot;
+  int n_pa, pa[kMaxComp];
+  int n_scale, scale[2 * kMaxComp];
+};
+
 // Model description as the per-galaxy kernels need it.
 struct DescDev {
   int n_comp;
@@ -26,6 +34,8 @@ struct DescDev {
   int is_log[kMaxSlots];
   int is_pa[kMaxSlots];        // slot is some radial component's position angle
   double lo[kMaxSlots], hi[kMaxSlots];
+  int n_canon;
+  CanonGroup canon[kMaxComp];
 };
 
 struct LMOpts {
@@ -307,51 +317,111 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
   S.status[g] = st;
 }
 
-// Outputs of a fit: best point (position angles wrapped to [0, pi)), chi^2,
-// degrees of freedom, evaluations, status and the covariance error bars.
+// Outputs of a fit: best point, chi^2, degrees of freedom, evaluations, status
+// and the covariance error bars sqrt(diag[(J^T W J)^-1]) (Sec. 5.2).  An axis
+// ratio above 1 is rewritten as 1/q with its position angles turned by pi/2
+// and its scale lengths multiplied by q (the same image), and the covariance
+// is carried along: Sigma' = T Sigma T^T with T the Jacobian of the rewrite.
+// Position angles are wrapped to [0, pi).
 __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G, double* params_out,
                             double* chi2_out, int* dof_out, int* iters_out, int* status_out,
                             double* sigma_p_out) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
   const int NS = D.n_slots, P = D.P;
-  const double* pb = S.p_b + (size_t)g * NS;
   const double pi = 3.14159265358979323846;
-  for (int s = 0; s < NS; ++s) {
-    double v = pb[s];
-    if (D.is_pa[s]) v -= pi * floor(v / pi);
-    params_out[(size_t)g * NS + s] = v;
-  }
+  double p[kMaxSlots];
+  for (int s = 0; s < NS; ++s) p[s] = S.p_b[(size_t)g * NS + s];
   chi2_out[g] = S.chi2_b[g];
   dof_out[g] = S.nused[g] - P;
   iters_out[g] = S.it[g];
   status_out[g] = S.status[g];
-  if (S.status[g] == ST_CONVERGED) atomicAdd(S.evals + 1, 1ull);
-  atomicAdd(S.evals + 2, (unsigned long long)S.it[g]);
-  if (sigma_p_out) {
-    double* sp = sigma_p_out + (size_t)g * NS;
-    for (int s = 0; s < NS; ++s) sp[s] = 0.0;
-    if (S.it[g] == 0 || S.status[g] == ST_NONFINITE) {
-      for (int f = 0; f < P; ++f) sp[D.free_slot[f]] = CUDART_NAN;
-      return;
-    }
+  const bool evaluated = S.it[g] > 0 && S.status[g] != ST_NONFINITE;
+
+  // covariance of the free parameters in physical units at the best point
+  double cov[kMaxFree * kMaxFree];
+  bool have_cov = false;
+  if (sigma_p_out && evaluated) {
     const double* Ab = S.A_b + (size_t)g * (P * (P + 1) / 2);
     double M[kMaxFree * kMaxFree];
     for (int f = 0; f < P; ++f)
       for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
-    if (!cholesky(M, P)) {
-      for (int f = 0; f < P; ++f) sp[D.free_slot[f]] = CUDART_NAN;
-      return;
-    }
-    for (int f = 0; f < P; ++f) {
-      double e[kMaxFree], x[kMaxFree];
-      for (int h = 0; h < P; ++h) e[h] = (h == f) ? 1.0 : 0.0;
-      chol_solve(M, P, e, x);
-      const int s = D.free_slot[f];
-      const double su = sqrt(x[f]);
-      sp[s] = D.is_log[s] ? pb[s] * su : su;
+    if (cholesky(M, P)) {
+      have_cov = true;
+      for (int f = 0; f < P; ++f) {
+        double e[kMaxFree], x[kMaxFree];
+        for (int h = 0; h < P; ++h) e[h] = (h == f) ? 1.0 : 0.0;
+        chol_solve(M, P, e, x);
+        for (int h = 0; h < P; ++h) cov[h * P + f] = x[h];
+      }
+      for (int f = 0; f < P; ++f) {
+        const int sf = D.free_slot[f];
+        const double df = D.is_log[sf] ? p[sf] : 1.0;
+        for (int h = 0; h < P; ++h) {
+          const int sh = D.free_slot[h];
+          cov[f * P + h] *= df * (D.is_log[sh] ? p[sh] : 1.0);
+        }
+      }
     }
   }
+
+  // canonical axis ratios
+  if (evaluated) {
+    int fidx[kMaxSlots];
+    for (int s = 0; s < NS; ++s) fidx[s] = -1;
+    for (int f = 0; f < P; ++f) fidx[D.free_slot[f]] = f;
+    double T[kMaxFree * kMaxFree];
+    bool any = false;
+    for (int f = 0; f < P * P; ++f) T[f] = 0.0;
+    for (int f = 0; f < P; ++f) T[f * P + f] = 1.0;
+    for (int k = 0; k < D.n_canon; ++k) {
+      const CanonGroup& cg = D.canon[k];
+      const double q = p[cg.q_slot];
+      if (!(q > 1.0)) continue;
+      any = true;
+      const int fq = fidx[cg.q_slot];
+      for (int i = 0; i < cg.n_scale; ++i) {
+        const int ss = cg.scale[i];
+        const int fs = fidx[ss];
+        if (fs >= 0) {
+          T[fs * P + fs] = q;
+          if (fq >= 0) T[fs * P + fq] = p[ss];
+        }
+        p[ss] *= q;
+      }
+      for (int i = 0; i < cg.n_pa; ++i) p[cg.pa[i]] += 0.5 * pi;
+      if (fq >= 0) T[fq * P + fq] = -1.0 / (q * q);
+      p[cg.q_slot] = 1.0 / q;
+    }
+    if (any && have_cov) {  // cov <- T cov T^T
+      double tmp[kMaxFree * kMaxFree];
+      for (int f = 0; f < P; ++f)
+        for (int h = 0; h < P; ++h) {
+          double acc = 0.0;
+          for (int k = 0; k < P; ++k) acc += T[f * P + k] * cov[k * P + h];
+          tmp[f * P + h] = acc;
+        }
+      for (int f = 0; f < P; ++f)
+        for (int h = 0; h < P; ++h) {
+          double acc = 0.0;
+          for (int k = 0; k < P; ++k) acc += tmp[f * P + k] * T[h * P + k];
+          cov[f * P + h] = acc;
+        }
+    }
+  }
+
+  for (int s = 0; s < NS; ++s) {
+    double v = p[s];
+    if (D.is_pa[s]) v -= pi * floor(v / pi);
+    params_out[(size_t)g * NS + s] = v;
+  }
+  if (sigma_p_out) {
+    double* sp = sigma_p_out + (size_t)g * NS;
+    for (int s = 0; s < NS; ++s) sp[s] = 0.0;
+    for (int f = 0; f < P; ++f) sp[D.free_slot[f]] = have_cov ? sqrt(cov[f * P + f]) : CUDART_NAN;
+  }
+  if (S.status[g] == ST_CONVERGED) atomicAdd(S.evals + 1, 1ull);
+  atomicAdd(S.evals + 2, (unsigned long long)S.it[g]);
 }
 
 // gm_chi2_grad outputs from the tile partials (physical coordinates).

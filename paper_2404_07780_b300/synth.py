@@ -33,7 +33,7 @@ PARAM_NAMES = {
 
 # Fitted in log space (positive scale and amplitude parameters) and default
 # bounds, by parameter role.
-_LOG_ROLES = {"Ie", "I0", "Re", "rs", "rout", "rc", "rt", "fwhm", "n", "alpha", "a"}
+_LOG_ROLES = {"Ie", "I0", "Re", "rs", "rout", "rc", "rt", "fwhm", "n", "alpha", "a", "q"}
 _BIG = 1e30
 
 
@@ -43,7 +43,9 @@ def _default_bounds(kind: str, role: str, H: int, W: int) -> tuple[float, float]
     if role == "y0":
         return 0.0, float(H)
     if role == "q":
-        return 0.05, 1.0
+        # above 1 the same ellipse turned by pi/2: the fit may pass through q = 1 and the
+        # result is rewritten with q <= 1 at the end
+        return 0.05, 20.0
     if role == "pa":
         return -_BIG, _BIG
     if role in ("Ie", "I0"):

@@ -449,3 +449,63 @@ def test_status_codes():
     M[2, 3, 3] = 1                        # bad sigma hidden by the mask is fine
     res = oracle.fit(spec, np.zeros((3, 1)), np.ones((3, 1, 1)), D, S, M)
     assert list(res["status"]) == [6, 7, 1]
+
+
+# --------------------------------------------------------------------------
+# Axis ratio above 1 (the fit may cross q = 1; results are rewritten with q <= 1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,par", [
+    ("sersic", [10.3, 11.2, 2.0, 0.3, 5.0, 3.0, 1.7]),
+    ("expdisk", [10.3, 11.2, 1.6, 1.1, 5.0, 2.5]),
+    ("ferrer", [10.3, 11.2, 1.8, 2.0, 5.0, 4.0, 2.0, 0.5]),
+    ("king", [10.3, 11.2, 3.0, 0.7, 5.0, 1.5, 5.0, 2.0]),
+    ("gaussian", [10.3, 11.2, 1.3, 0.2, 5.0, 2.5]),
+    ("moffat", [10.3, 11.2, 2.5, 2.9, 5.0, 2.5, 3.0]),
+])
+def test_axis_ratio_above_one_is_the_turned_ellipse(kind, par):
+    # q > 1 equals 1/q with PA + pi/2 and every scale length times q (same image)
+    H, W = 22, 24
+    spec = synth.ModelSpec().add(kind, "c", H, W)
+    p = np.array([par], float)
+    pc = oracle.canonicalize(spec, p)
+    q = par[2]
+    assert pc[0, 2] == pytest.approx(1.0 / q, rel=1e-15)
+    assert pc[0, 3] == pytest.approx(par[3] + math.pi / 2, rel=1e-15)
+    scale_idx = {"king": [5, 6]}.get(kind, [5])
+    for k in range(len(par)):
+        want = par[k] * q if k in scale_idx else par[k]
+        if k not in (2, 3):
+            assert pc[0, k] == pytest.approx(want, rel=1e-15), k
+    a = oracle.component_image(kind, p[0], H, W)
+    b = oracle.component_image(kind, pc[0], H, W)
+    np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-14 * np.abs(a).max())
+
+
+def test_canonical_rewrite_skips_shared_geometry():
+    # a q slot whose scale slot is also used by a component with another q is left alone
+    H, W = 16, 16
+    spec = synth.ModelSpec().add("sersic", "a", H, W)
+    spec.add("sersic", "b", H, W, shared={"Re": spec.slot("a.Re")})
+    p = np.array([[8, 8, 2.0, 0.1, 1, 3, 1, 8, 8, 0.5, 0.2, 1, 1]], float)
+    np.testing.assert_array_equal(oracle.canonicalize(spec, p), p)
+
+
+def test_fit_through_q_one_ends_canonical():
+    # a galaxy whose default PA is 90 degrees off: the fit crosses q = 1 and the
+    # result is rewritten with q < 1, PA near the truth, same chi^2 as a start near the truth
+    H = W = 48
+    K = 9
+    spec = synth.single_sersic_sky(H, W)
+    truth = np.array([[24.2, 23.7, 0.45, 0.2, 20.0, 5.0, 1.5, 1.0]])
+    psf = oracle.component_image("gaussian", [K / 2, K / 2, 1, 0, 1, 1.5], K, K)[None]
+    psf /= psf.sum()
+    Mt = oracle.model_images(spec, truth, psf, H, W)
+    D, S = synth.noisy_image(Mt, np.random.default_rng(4).standard_normal(Mt.shape))
+    start = np.array([[24.0, 24.0, 0.65, 0.2 + math.pi / 2, 10.0, 6.0, 1.4, 2.5]])
+    r = oracle.fit(spec, start, psf, D, S, None, oracle.FitOptions(tol=1e-12, gtol=1e-13, max_iter=200))
+    near = oracle.fit(spec, truth * 1.01, psf, D, S, None, oracle.FitOptions(tol=1e-12, gtol=1e-13, max_iter=200))
+    assert r["status"][0] == 1 and near["status"][0] == 1
+    assert r["params"][0, 2] <= 1.0
+    assert r["chi2"][0] == pytest.approx(near["chi2"][0], rel=1e-9)
+    np.testing.assert_allclose(r["params"][0], near["params"][0], rtol=1e-5, atol=1e-5)
