@@ -184,6 +184,25 @@ int gm_chi2_grad(const gm_model_desc *desc, const gm_batch *batch, const double 
                  void *stream);
 
 /*
+ * gm_grad_adjoint -- chi^2 of Eq. chinu and d chi^2/dp by the adjoint of the
+ * PSF correlation: with v = P^T (w r) (the same-size zero-padded correlation
+ * with the PSF flipped in both axes),
+ *   d chi^2/dp = -2 [ sum_pix (dI_conv/dp) v + sum_pix w r dI_unconv/dp ],
+ * so a pass costs two single-channel correlations whatever the number of free
+ * parameters (gm_chi2_grad correlates 1 + P channels and also returns
+ * J^T W J).  The paper fits by gradient descent on this gradient (Sec. 5.1,
+ * torch autograd); this is that gradient computed by hand.
+ *   params  [n_gal][n_slots] FP64
+ *   chi2    [n_gal] FP64
+ *   grad    NULL or [n_gal][n_slots] FP64, physical units, 0 for fixed slots
+ *   workspace  gm_grad_adjoint_workspace_bytes(desc, batch) bytes
+ * Asynchronous on `stream` like gm_chi2_grad.
+ */
+size_t gm_grad_adjoint_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
+int gm_grad_adjoint(const gm_model_desc *desc, const gm_batch *batch, const double *params, double *chi2,
+                    double *grad, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * gm_chi2_grad_noalloc -- gm_chi2_grad for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a convenience of the library.
  *

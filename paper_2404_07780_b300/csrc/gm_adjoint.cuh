@@ -1,0 +1,287 @@
+// gm_adjoint.cuh -- chi^2 and its gradient by the adjoint of the PSF
+// correlation: two single-channel correlations per pass, whatever the number
+// of free parameters.
+//
+// With M = P (*) I_conv + I_unconv (cross-correlation with zero padding) and
+// r = D - M, w = Omega / sigma^2 (Eq. chinu of arxiv 2404.07780):
+//   d chi^2 / dp = -2 sum_pix w r dM/dp
+//                = -2 [ sum_pix' (dI_conv/dp)(pix') v(pix') + sum_pix w r dI_unconv/dp ],
+//   v = P^T (w r),
+// and the adjoint of the same-size zero-padded correlation is the same-size
+// zero-padded correlation with the PSF flipped in both axes
+// (sum_ab P[a,b] u[i-a+c, j-b+c] = sum_a'b' P[K-1-a', K-1-b'] u[i+a'-c, j+b'-c]).
+//
+// Each pass is three kernels:
+//   k_profile_pairs   I_conv of two galaxies per pixel into one pair plane
+//   k_adjoint<RESID>  correlate I_conv with P -> M, add the unconvolved part,
+//                     write u = w r into a second pair plane; chi^2 and the
+//                     unconvolved gradient terms per tile
+//   k_adjoint<ADJ>    correlate u with the flipped P -> v, evaluate the
+//                     convolved profiles' derivatives at the pixel and
+//                     accumulate sum v dI/dp per tile
+// Two galaxies share one f32x2 lane pair: the plane holds (galaxy 2k, galaxy
+// 2k+1) and the PSF pair is (P_2k[a,b], P_2k+1[a,b]), so every packed FMA does
+// useful work although each galaxy has a single channel.  Windows are loaded
+// by TMA exactly as in the fused pass (gm_fused.cuh).
+#pragma once
+
+#include "gm_fused.cuh"
+#include "gm_lm.cuh"
+
+namespace gm {
+
+enum AdjMode { ADJ_RESID = 0, ADJ_GRAD = 1 };
+
+struct AdjArgs {
+  CUtensorMap tmap;          // input pair planes [(G+1)/2][H][2*Wp] FP32
+  ChanMap m;
+  int P;                     // free slots (accumulator order)
+  int conv_acc[kMaxComp][8]; // accumulator of d/dp_k of a convolved comp c (-1 none)
+  int unconv_acc[kMaxComp][8];  // same for unconvolved comps
+  int nacc;                  // 1 + P
+  int G, H, W, Wp, K, cpad, tiles_x, n_tiles, rw, plane;
+  const float* image;
+  const float* sigma;
+  const uint8_t* mask;
+  const float* psf;
+  const float* cconst;
+  float* u_planes;           // RESID: output pair planes of u = w r
+  double* partial;           // [G][n_tiles][nacc]: RESID writes [0] chi^2 and unconvolved terms,
+                             //                     ADJ adds the convolved terms to a second copy
+  int* err;
+  int off_psf, off_in, off_cc, off_red, off_bar;
+};
+
+// I_conv of galaxies 2k and 2k+1 (the second zero past the end) into pair plane k.
+__global__ void __launch_bounds__(256) k_profile_pairs(const __grid_constant__ ProfileArgs A) {
+  __shared__ float s_cc[2][kMaxComp * kCC];
+  const ChanMap& m = A.m;
+  const int tid = threadIdx.x;
+  const int per_pair = (A.H * A.Wp + 255) / 256;
+  const int n_pairs = (A.G + 1) / 2;
+  for (int blk = blockIdx.x; blk < n_pairs * per_pair; blk += gridDim.x) {
+    const int gp = blk / per_pair, chunk = blk - gp * per_pair;
+    __syncthreads();
+    for (int t = tid; t < 2 * m.n_comp * kCC; t += 256) {
+      const int h = t / (m.n_comp * kCC), e = t - h * (m.n_comp * kCC);
+      const int g = 2 * gp + h;
+      s_cc[h][e] = (g < A.G) ? A.cconst[(size_t)g * m.n_comp * kCC + e] : 0.f;
+    }
+    __syncthreads();
+    const int pix = chunk * 256 + tid;
+    if (pix >= A.H * A.Wp) continue;
+    const int i = pix / A.Wp, j = pix - (pix / A.Wp) * A.Wp;
+    float v[2] = {0.f, 0.f};
+    if (j < A.W) {
+      for (int h = 0; h < 2; ++h) {
+        if (2 * gp + h >= A.G) continue;
+        for (int cm = 0; cm < m.n_comp; ++cm) {
+          if (!m.conv[cm]) continue;
+          float d[8];
+          v[h] += eval_component(m.kind[cm], s_cc[h] + cm * kCC, i, j, d);
+        }
+      }
+    }
+    reinterpret_cast<float2*>(A.planes)[((size_t)gp * A.H + i) * A.Wp + j] = make_float2(v[0], v[1]);
+  }
+}
+
+__device__ __forceinline__ void adj_issue(const AdjArgs& A, float2* s_in, u64* bar, int item) {
+  const int gp = item / A.n_tiles, tile = item - gp * A.n_tiles;
+  const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
+  const int c = (A.K - 1) / 2;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, (unsigned)(kTile + A.K - 1) * A.rw * 8u);
+  tma_load_3d(s_in, &A.tmap, 2 * (j0 - c - A.cpad), i0 - c, gp, bar);
+}
+
+template <int MODE, int P>
+__global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  u64* s_psf = reinterpret_cast<u64*>(smem + A.off_psf);
+  float2* s_in = reinterpret_cast<float2*>(smem + A.off_in);
+  float* s_cc = reinterpret_cast<float*>(smem + A.off_cc);
+  float* s_red = reinterpret_cast<float*>(smem + A.off_red);
+  u64* bar = reinterpret_cast<u64*>(smem + A.off_bar);
+  int* s_flag = reinterpret_cast<int*>(smem + A.off_bar + 8);
+  const ChanMap& m = A.m;
+  constexpr int NA = 1 + P;
+
+  const int tid = threadIdx.x;
+  const int K = A.K, c = (K - 1) / 2, K2 = K + 1;
+  const int n_pairs = (A.G + 1) / 2;
+  const int n_items = n_pairs * A.n_tiles;
+  if ((int)blockIdx.x >= n_items) return;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_flag = 0;
+  }
+  __syncthreads();
+  if (tid == 0) adj_issue(A, s_in, bar, blockIdx.x);
+  unsigned phase = 0;
+  const int lane = tid & 31, wig = tid >> 5;
+  const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
+  const int row0 = wig * 8;
+  const int ncc = m.n_comp * kCC;
+
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int gp = item / A.n_tiles, tile = item - gp * A.n_tiles;
+    const int g0 = 2 * gp, g1 = 2 * gp + 1;
+    const bool has1 = g1 < A.G;
+    const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
+
+    __syncthreads();  // the previous item is done with s_psf, s_cc, s_red
+    for (int t = tid; t < 2 * ncc; t += blockDim.x) {
+      const int h = t / ncc, e = t - h * ncc;
+      const int g = g0 + h;
+      s_cc[t] = (g < A.G) ? A.cconst[(size_t)g * ncc + e] : 0.f;
+    }
+    for (int t = tid; t < K * K2; t += blockDim.x) {
+      const int a = t / K2, bb = t - a * K2;
+      const int b = bb - A.cpad;
+      float v0 = 0.f, v1 = 0.f;
+      if (b >= 0 && b < K) {
+        // RESID correlates with P, ADJ with P flipped in both axes (the adjoint)
+        const int src = (MODE == ADJ_RESID) ? a * K + b : (K - 1 - a) * K + (K - 1 - b);
+        v0 = A.psf[(size_t)g0 * K * K + src];
+        v1 = has1 ? A.psf[(size_t)g1 * K * K + src] : 0.f;
+      }
+      s_psf[t] = pack2(v0, v1);
+    }
+    const int a_lo = max(0, c - i0 - row0 - 7);
+    const int a_hi = min(K, c - i0 + A.H - row0);
+
+    if (tid == 0) {
+      if (!mbar_wait_bounded(bar, phase)) *s_flag = 1;
+    }
+    __syncthreads();
+    if (*s_flag) {
+      if (tid == 0) {
+        atomicExch(A.err, 1);
+        mbar_wait_bounded(bar, phase);
+      }
+      return;
+    }
+    mbar_try_wait(bar, phase);
+    phase ^= 1u;
+    u64 acc[1][8];
+    correlate_pairs<1>(acc, s_in, s_psf, 0, A.plane, A.rw, K, row, col0, a_lo, a_hi);
+    __syncthreads();  // every warp is done reading the window
+    if (tid == 0 && item + (int)gridDim.x < n_items) adj_issue(A, s_in, bar, item + gridDim.x);
+
+    // ---- epilogue: this thread's 8 pixels, both galaxies, straight from registers ----
+    float red[2][NA];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int e = 0; e < NA; ++e) red[h][e] = 0.f;
+    const int i = i0 + row;
+#pragma unroll
+    for (int rx = 0; rx < 8; ++rx) {
+      const int j = j0 + col0 + rx;
+      float vv[2];
+      unpack2(acc[0][rx], vv[0], vv[1]);
+      if (MODE == ADJ_RESID) {
+        float uu[2] = {0.f, 0.f};
+        if (i < A.H && j < A.W) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !has1) continue;
+            const int g = g0 + h;
+            float Mv = vv[h];
+            for (int cm = 0; cm < m.n_comp; ++cm) {
+              if (m.conv[cm]) continue;
+              float d[8];
+              Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
+            }
+            const size_t gpx = ((size_t)g * A.H + i) * A.W + j;
+            if (A.mask && A.mask[gpx]) continue;
+            const float isg = 1.f / A.sigma[gpx];
+            const float rr = (A.image[gpx] - Mv) * isg;
+            red[h][0] = fmaf(rr, rr, red[h][0]);
+            const float wr = rr * isg;  // w r = (D - M) / sigma^2
+            uu[h] = wr;
+            for (int cm = 0; cm < m.n_comp; ++cm) {
+              if (m.conv[cm]) continue;
+              float d[8];
+              eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                if (k >= m.np[cm]) break;
+                const int f = A.unconv_acc[cm][k];
+#pragma unroll
+                for (int ff = 0; ff < P; ++ff)
+                  if (ff == f) red[h][1 + ff] = fmaf(wr, d[k], red[h][1 + ff]);
+              }
+            }
+          }
+        }
+        if (i < A.H && j < A.Wp)
+          reinterpret_cast<float2*>(A.u_planes)[((size_t)gp * A.H + i) * A.Wp + j] = make_float2(uu[0], uu[1]);
+      } else {
+        if (i < A.H && j < A.W) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !has1) continue;
+            for (int cm = 0; cm < m.n_comp; ++cm) {
+              if (!m.conv[cm]) continue;
+              float d[8];
+              eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                if (k >= m.np[cm]) break;
+                const int f = A.conv_acc[cm][k];
+#pragma unroll
+                for (int ff = 0; ff < P; ++ff)
+                  if (ff == f) red[h][1 + ff] = fmaf(vv[h], d[k], red[h][1 + ff]);
+              }
+            }
+          }
+        }
+      }
+    }
+    // ---- block reduction: warp shuffles, then across the 4 warps, FP64 per tile ----
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int e = 0; e < NA; ++e) {
+        float v = red[h][e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[(wig * 2 + h) * NA + e] = v;
+      }
+    __syncthreads();
+    for (int t = tid; t < 2 * NA; t += blockDim.x) {
+      const int h = t / NA, e = t - h * NA;
+      const int g = g0 + h;
+      if (g >= A.G) continue;
+      double s = 0.0;
+      for (int w = 0; w < 4; ++w) s += (double)s_red[(w * 2 + h) * NA + e];
+      A.partial[((size_t)g * A.n_tiles + tile) * NA + e] = s;
+    }
+  }
+}
+
+// chi^2 and d chi^2/dp = -2 (unconvolved + convolved terms) from the two passes' partials.
+__global__ void k_adjoint_finish(const __grid_constant__ DescDev D, int G, int n_tiles,
+                                 const double* __restrict__ part_resid, const double* __restrict__ part_adj,
+                                 double* chi2, double* grad) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int P = D.P, n_slots = D.n_slots;
+  const int* free_slot = D.free_slot;
+  const int NA = 1 + P;
+  double acc[1 + kMaxFree];
+  for (int e = 0; e < NA; ++e) acc[e] = 0.0;
+  for (int t = 0; t < n_tiles; ++t)
+    for (int e = 0; e < NA; ++e)
+      acc[e] += part_resid[((size_t)g * n_tiles + t) * NA + e] + (e > 0 ? part_adj[((size_t)g * n_tiles + t) * NA + e] : 0.0);
+  chi2[g] = acc[0];
+  if (grad) {
+    for (int s = 0; s < n_slots; ++s) grad[(size_t)g * n_slots + s] = 0.0;
+    for (int f = 0; f < P; ++f) grad[(size_t)g * n_slots + free_slot[f]] = -2.0 * acc[1 + f];
+  }
+}
+
+}  // namespace gm

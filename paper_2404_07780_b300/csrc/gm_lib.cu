@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "../../include/gm.h"
+#include "gm_adjoint.cuh"
 #include "gm_fused.cuh"
 #include "gm_lm.cuh"
 
@@ -779,6 +780,179 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   fs.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   g_stats = fs;
   g_have_stats = true;
+  return GM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint gradient
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+typedef void (*AdjKernel)(AdjArgs);
+
+AdjKernel pick_adjoint(int mode, int P) {
+#define GM_ADJ(n)                                                        \
+  case n:                                                                \
+    return mode == ADJ_RESID ? k_adjoint<ADJ_RESID, n> : k_adjoint<ADJ_GRAD, n>;
+  switch (P) {
+    GM_ADJ(0) GM_ADJ(1) GM_ADJ(2) GM_ADJ(3) GM_ADJ(4) GM_ADJ(5) GM_ADJ(6) GM_ADJ(7) GM_ADJ(8)
+    GM_ADJ(9) GM_ADJ(10) GM_ADJ(11) GM_ADJ(12) GM_ADJ(13) GM_ADJ(14) GM_ADJ(15) GM_ADJ(16)
+    default:
+      return nullptr;
+  }
+#undef GM_ADJ
+}
+
+struct WsAdj {
+  size_t cconst, scale, mplanes, uplanes, part_r, part_a, err, total;
+  int Wp;
+};
+
+WsAdj ws_adj(const gm_model_desc* d, const gm_batch* b, int P) {
+  WsAdj w;
+  size_t off = 0;
+  const size_t G = (size_t)std::max(b->n_gal, 0);
+  const size_t pairs = (G + 1) / 2;
+  const size_t tiles = (size_t)((b->W + kTile - 1) / kTile) * ((b->H + kTile - 1) / kTile);
+  w.Wp = b->W + (b->W & 1);
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  w.cconst = take(G * d->n_comp * kCC * 4);
+  w.scale = take(G * d->n_slots * 4);
+  w.mplanes = take(pairs * b->H * w.Wp * 8);
+  w.uplanes = take(pairs * b->H * w.Wp * 8);
+  w.part_r = take(G * tiles * (1 + P) * 8);
+  w.part_a = take(G * tiles * (1 + P) * 8);
+  w.err = take(4);
+  w.total = off;
+  return w;
+}
+
+int encode_pairs(CUtensorMap* map, float* planes, int Wp, int H, int n_planes, int rw, int K) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  int rc = encode_fn(&enc);
+  if (rc) return rc;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Wp), (cuuint64_t)H, (cuuint64_t)n_planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Wp) * 4, (cuuint64_t)(2 * Wp) * 4 * H};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * rw), (cuuint32_t)(kTile + K - 1), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, planes, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return fail(GM_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  return GM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gm_grad_adjoint_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
+  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
+  return ws_adj(desc, batch, count_free(desc)).total;
+}
+
+int gm_grad_adjoint(const gm_model_desc* desc, const gm_batch* batch, const double* params, double* chi2,
+                    double* grad, void* workspace, size_t ws_bytes, void* stream) {
+  int rc = check_batch(batch, true);
+  if (rc) return rc;
+  Plan pl;
+  rc = make_plan(desc, MODE_NORMAL, false, &pl);
+  if (rc) return rc;
+  if (batch->n_gal == 0) return GM_OK;
+  if (!params || !chi2) return fail(GM_E_INVAL, "params/chi2 is NULL");
+  const int P = pl.dd.P;
+  const WsAdj w = ws_adj(desc, batch, P);
+  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+  DevInfo di;
+  if ((rc = dev_info(&di))) return rc;
+  const int G = batch->n_gal, K = batch->K, H = batch->H;
+  const int n_pairs = (G + 1) / 2;
+  char* ws = (char*)workspace;
+  float* cconst = (float*)(ws + w.cconst);
+  float* scale = (float*)(ws + w.scale);
+  float* mplanes = (float*)(ws + w.mplanes);
+  float* uplanes = (float*)(ws + w.uplanes);
+  double* part_r = (double*)(ws + w.part_r);
+  double* part_a = (double*)(ws + w.part_a);
+  int* err = (int*)(ws + w.err);
+
+  AdjArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.m = chan_map(pl);
+  A.P = P;
+  A.nacc = 1 + P;
+  for (int c = 0; c < desc->n_comp; ++c)
+    for (int k = 0; k < 8; ++k) {
+      const int f = (k < pl.dd.np[c]) ? pl.chan_of_slot[pl.dd.slot[c][k]] - 1 : -1;
+      A.conv_acc[c][k] = pl.conv[c] ? f : -1;
+      A.unconv_acc[c][k] = pl.conv[c] ? -1 : f;
+    }
+  A.G = G;
+  A.H = H;
+  A.W = batch->W;
+  A.Wp = w.Wp;
+  A.K = K;
+  A.cpad = ((K - 1) / 2) & 1;
+  A.tiles_x = (batch->W + kTile - 1) / kTile;
+  A.n_tiles = A.tiles_x * ((H + kTile - 1) / kTile);
+  int rw = K + 33;
+  while (rw % 4 != 2) ++rw;
+  A.rw = rw;
+  const size_t plane_bytes = ((size_t)(kTile + K - 1) * rw * 8 + 127) / 128 * 128;
+  A.plane = (int)(plane_bytes / 8);
+  A.image = batch->image;
+  A.sigma = batch->sigma;
+  A.mask = batch->mask;
+  A.psf = batch->psf;
+  A.cconst = cconst;
+  A.err = err;
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t align) {
+    off = (off + align - 1) / align * align;
+    const size_t o = off;
+    off += bytes;
+    return (int)o;
+  };
+  A.off_in = take(plane_bytes, 128);
+  A.off_psf = take((size_t)K * (K + 1) * 8, 16);
+  A.off_cc = take((size_t)2 * desc->n_comp * kCC * 4, 16);
+  A.off_red = take((size_t)4 * 2 * (1 + P) * 4, 16);
+  A.off_bar = take(16, 16);
+  const int smem = (int)off;
+  if (smem > di.smem_optin) return fail(GM_E_UNSUPPORTED, "adjoint tile needs %d bytes of shared memory", smem);
+  AdjKernel kr = pick_adjoint(ADJ_RESID, P), ka = pick_adjoint(ADJ_GRAD, P);
+  if (!kr || !ka) return fail(GM_E_UNSUPPORTED, "no adjoint kernel for %d free parameters", P);
+  GM_CUDA(cudaFuncSetAttribute((const void*)kr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  GM_CUDA(cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int occ = 1;
+  GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)kr, 128, smem));
+  const int grid = std::max(1, std::min(n_pairs * A.n_tiles, std::max(occ, 1) * di.sms));
+
+  cudaStream_t st = (cudaStream_t)stream;
+  GM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, H, params, 0, cconst, scale);
+  GM_LAUNCHED("k_setup");
+  ProfileArgs PA = profile_args(pl, batch, cconst, scale, mplanes, w.Wp);
+  const int pgrid = std::max(1, std::min(n_pairs * ((H * w.Wp + 255) / 256), 8 * di.sms));
+  k_profile_pairs<<<pgrid, 256, 0, st>>>(PA);
+  GM_LAUNCHED("k_profile_pairs");
+  if ((rc = encode_pairs(&A.tmap, mplanes, w.Wp, H, n_pairs, rw, K))) return rc;
+  A.u_planes = uplanes;
+  A.partial = part_r;
+  kr<<<grid, 128, smem, st>>>(A);
+  GM_LAUNCHED("k_adjoint(resid)");
+  if ((rc = encode_pairs(&A.tmap, uplanes, w.Wp, H, n_pairs, rw, K))) return rc;
+  A.partial = part_a;
+  ka<<<grid, 128, smem, st>>>(A);
+  GM_LAUNCHED("k_adjoint(grad)");
+  k_adjoint_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, A.n_tiles, part_r, part_a, chi2, grad);
+  GM_LAUNCHED("k_adjoint_finish");
   return GM_OK;
 }
 

@@ -327,3 +327,67 @@ def test_fit_status_codes(gm):
     oi = oracle_inputs(c)
     ref = oracle.fit(c.spec, c.params, oi["psf"], oi["image"], oi["sigma"], c.mask)
     np.testing.assert_array_equal(st, ref["status"])
+
+
+# ---------------------------------------------------------------------------
+# adjoint gradient (gm_grad_adjoint) and the torch autograd function
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("draw,G,H,W,K", [(synth.draw_small, 7, 64, 64, 15),
+                                          (synth.draw_bulge_bar_nucleus, 5, 96, 96, 41),
+                                          (synth.draw_bulge_disk, 4, 64, 72, 25)])
+def test_grad_adjoint_matches_normal_equations(gm, draw, G, H, W, K):
+    # the adjoint gradient (two correlations) against the 1+P-channel pass, odd G included
+    b = draw(seed=9, G=G) if draw is synth.draw_small else draw(seed=9, G=G, H=H, W=W, K=K)
+    c = from_batch(b, at="init")
+    t = c.torch()
+    chi2, grad = gm.gm_grad_adjoint(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"])
+    rchi2, rgrad, rjtj = gm.gm_chi2_grad(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"],
+                                         want_grad=True, want_jtj=True)
+    chi2, grad, rchi2, rgrad, rjtj = map(_np, (chi2, grad, rchi2, rgrad, rjtj))
+    np.testing.assert_allclose(chi2, rchi2, rtol=1e-5)
+    for gi in range(c.G):
+        bound = 2e-4 * np.sqrt(np.abs(np.diag(rjtj[gi]))) * math.sqrt(rchi2[gi])
+        assert (np.abs(grad[gi] - rgrad[gi]) <= bound + 1e-300).all(), gi
+
+
+def test_grad_adjoint_vs_oracle_finite_differences(gm):
+    # 64 galaxies of the bulge + bar + nucleus model (96x96, K = 41): d chi^2 / dp against
+    # central FP64 finite differences of the oracle's chi^2 (relative step 1e-6)
+    b = synth.draw_bulge_bar_nucleus(seed=31, G=64)
+    c = from_batch(b, at="init")
+    t = c.torch()
+    chi2, grad = gm.gm_grad_adjoint(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"])
+    chi2, grad = _np(chi2), _np(grad)
+    rchi2, rg, rA = _oracle_normal(c)
+    np.testing.assert_allclose(chi2, rchi2, rtol=1e-5)
+    free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
+    for gi in range(c.G):
+        bound = 2e-4 * np.sqrt(np.diag(rA[gi])) * math.sqrt(rchi2[gi])
+        assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= bound).all(), gi
+
+
+def test_chi2_autograd_function_and_adam(gm):
+    import torch
+    b = synth.draw_small(seed=13, G=6)
+    c = from_batch(b, at="init")
+    t = c.torch()
+    f = gm.Chi2(c.spec, t["image"], t["sigma"], t["mask"], t["psf"])
+    p = t["params"].clone().requires_grad_(True)
+    loss = f(p).sum()
+    loss.backward()
+    _, grad = gm.gm_grad_adjoint(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"])
+    np.testing.assert_allclose(_np(p.grad), _np(grad), rtol=0, atol=0)
+    # the paper's fitting mode: a torch optimiser stepping the parameters on chi^2
+    q = t["params"].clone()
+    free = torch.tensor(c.spec.free, device=q.device)
+    u = q.clone().requires_grad_(True)
+    opt = torch.optim.Adam([u], lr=0.02)
+    first = None
+    for _ in range(30):
+        opt.zero_grad()
+        val = f(torch.where(free, u, q)).sum()
+        first = float(val.detach()) if first is None else first
+        val.backward()
+        opt.step()
+    assert float(f(torch.where(free, u, q)).sum().detach()) < first
