@@ -23,8 +23,8 @@
  *   stream to poll convergence and returns when the fit has finished.
  * Layout.  Stamps are row-major, H rows x W columns; the pixel in row i,
  *   column j has centre x = j + 0.5, y = H - 0.5 - i (row 0 at the top, the
- *   grid of the App. C listing).  Galaxy g's stamp starts at element
- *   g*H*W, its PSF at g*K*K.  The PSF is applied as a cross-correlation,
+ *   grid of the App. C listing).  Stamps and PSFs may all have one size or
+ *   differ per galaxy (gm_batch.geom).  The PSF is applied as a cross-correlation,
  *   M[i,j] = sum_ab P[a,b] I[i+a-c, j+b-c] with c = (K-1)/2 and I = 0 outside
  *   the stamp (torch conv2d semantics); K must be odd; the PSF is used as
  *   given (normalise it yourself).
@@ -117,16 +117,27 @@ typedef struct {
   double hi[GM_MAX_SLOTS];
 } gm_model_desc;
 
-/* A batch of equal-size stamps.  The struct itself is host memory; the
- * arrays it points to are device memory. */
+/* A batch of stamps.  The struct itself is host memory; image, sigma, mask
+ * and psf are device memory, geom is host memory.
+ *
+ * Equal stamps (geom == NULL): every stamp is H x W, every PSF K x K; stamp g
+ * starts at element g*H*W, its PSF at g*K*K.
+ * Uneven stamps (geom != NULL): geom[3g .. 3g+2] = (h_g, w_g, k_g) gives
+ * galaxy g's stamp rows and columns (1..4096) and odd PSF side (1..63); H, W
+ * and K are not read.  Stamps are packed back to back in galaxy order (stamp g
+ * starts at sum_{g'<g} h_g' w_g'), PSFs likewise (sum_{g'<g} k_g'^2), and every
+ * per-pixel output (model, components) follows the same packing.  The calls
+ * read geom before they return and copy the derived tables to the workspace
+ * with cudaMemcpyAsync from pageable memory, which may synchronise the stream. */
 typedef struct {
   int32_t n_gal;            /* galaxies, >= 0 */
-  int32_t H, W;             /* stamp rows, columns (1..4096) */
-  int32_t K;                /* PSF side, odd, 1..63 */
-  const float *image;       /* [n_gal][H][W] data D */
-  const float *sigma;       /* [n_gal][H][W] uncertainty sigma (> 0 on used pixels) */
-  const uint8_t *mask;      /* [n_gal][H][W] or NULL */
-  const float *psf;         /* [n_gal][K][K] */
+  int32_t H, W;             /* stamp rows, columns (1..4096); equal stamps only */
+  int32_t K;                /* PSF side, odd, 1..63; equal stamps only */
+  const float *image;       /* data D, [n_gal][H][W] or packed */
+  const float *sigma;       /* uncertainty sigma (> 0 on used pixels), same layout */
+  const uint8_t *mask;      /* same layout, or NULL */
+  const float *psf;         /* [n_gal][K][K] or packed */
+  const int32_t *geom;      /* NULL, or host [n_gal][3] = (h, w, k) of each galaxy */
 } gm_batch;
 
 /* Levenberg-Marquardt controls (host memory). */

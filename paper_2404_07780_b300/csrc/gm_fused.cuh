@@ -1,19 +1,26 @@
 // gm_fused.cuh -- the two kernels of one model+Jacobian pass.
 //
-// k_profile: every stamp pixel of the galaxies being evaluated gets the summed
-//   convolved components (channel 0) and one derivative channel per free
-//   parameter of a convolved component (NORMAL mode), or the per-component
-//   images (MODEL mode), written once to a channel-pair plane in the
-//   workspace: planes[g][cp][i][j] = (channel 2cp, channel 2cp+1), row pitch
-//   Wp = W rounded up to even (the pad column is zero).
+// Work item = (galaxy, 32x32 output tile).  Stamps and PSFs may differ in size
+// from galaxy to galaxy: each item looks its galaxy's geometry up in the
+// GalGeom table (gm_geom.cuh).
 //
-// k_fused: work item = (galaxy, 32x32 output tile); a persistent grid strides
-//   over the items of the galaxies still being fitted.  Per item and per
-//   "pass" of up to four channel pairs:
+// k_planes: every stamp pixel of the items' tiles gets the summed convolved
+//   components (channel 0) and one derivative channel per free parameter of a
+//   convolved component (NORMAL mode), or the per-component images (MODEL
+//   mode), written once to the galaxy's channel-pair planes in the workspace:
+//   planes[cp][i][j] = (channel 2cp, channel 2cp+1), row pitch Wp = W rounded
+//   up to even (the pad column is zero).
+//
+// k_fused: a persistent grid takes items from an atomic queue (item b first
+//   for CTA b, then gridDim.x + atomicAdd(queue, 1)); the host orders the
+//   items by decreasing cost (PSF area, then stamp size), so the last items
+//   handed out are the cheap ones.  Per item and per "pass" of up to four
+//   channel pairs:
 //     * one thread issues a TMA tile load (cp.async.bulk.tensor.3d) of the
 //       (32+K-1) x rw window of every pair plane of the pass into shared
-//       memory; out-of-stamp rows and columns come back as zeros, which is
-//       the zero padding of conv2d(..., padding="same");
+//       memory, through the tensor map of the galaxy's (H, W, K) class;
+//       out-of-stamp rows and columns come back as zeros, which is the zero
+//       padding of conv2d(..., padding="same");
 //     * each thread owns 8 adjacent output pixels of one row and CPT channel
 //       pairs and runs the sliding-window correlation (one 16-byte shared
 //       load per 2 taps per pair, one 16-byte PSF load per 2 taps, 16 packed
@@ -23,7 +30,8 @@
 //       stamp for the warp are skipped;
 //     * the next load (next pass or next item) is issued as soon as every
 //       warp has finished reading the window, so it overlaps the stores and
-//       the reduction.
+//       the reduction.  Thread 0 claims the next item and reads its record at
+//       the start of the current one, while the other warps correlate.
 //   Then the unconvolved components (the sky) are added at the output pixels,
 //   and NORMAL mode forms r = D - M, w = Omega/sigma^2 and accumulates chi^2,
 //   J^T W r and J^T W J (FP32 per thread, warp shuffles, cross-warp sum, one
@@ -39,11 +47,12 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "gm_geom.cuh"
 #include "gm_profiles.cuh"
 
 namespace gm {
 
-constexpr int kTile = 32;           // output tile is kTile x kTile
+constexpr int kTile = kTileSide;    // output tile is kTile x kTile
 constexpr int kTilePix = kTile * kTile;
 constexpr int kMaxPairs = 9;        // up to 17 correlated channels (model + 16 free parameters)
 constexpr int kMaxPassPairs = 4;    // channel pairs per TMA pass
@@ -69,6 +78,7 @@ struct ChanMap {
   int n_slots;
 };
 
+// Arguments of the adjoint path's profile kernel (equal stamps).
 struct ProfileArgs {
   ChanMap m;
   int G, H, W, Wp;
@@ -79,26 +89,49 @@ struct ProfileArgs {
   float* planes;             // [G][ncp][H][Wp][2]
 };
 
+// Arguments of k_planes.
+struct PlaneArgs {
+  ChanMap m;
+  const GalGeom* geo;        // [G]
+  const int2* items;         // (galaxy, tile) items of this pass
+  const int* n_items_dev;    // item count on the device (a fit's pass), or nullptr
+  int n_items;               // item count when n_items_dev is nullptr
+  const float* cconst;       // [G][n_comp][kCC]
+  const float* scale;        // [G][n_slots]
+  float* planes;             // pair planes, galaxy g from geo[g].plane
+  int* zero[3];              // counters set to 0 for the next kernels (nullptr: none)
+};
+
 struct FusedArgs {
-  CUtensorMap tmap;          // planes as a [G*ncp][H][2*Wp] FP32 tensor, box [1][HH][2*rw]
+  CUtensorMap tmap;          // equal stamps: planes as a [G*ncp][H][2*Wp] FP32 tensor, box [1][32+K-1][2*rw]
+  const CUtensorMap* maps;   // uneven stamps: one such map per (H, W, K) class, in global memory; else nullptr
   ChanMap m;
   int nacc;                  // accumulators per tile (NORMAL)
-  int G, H, W, K, cpad, tiles_x, n_tiles, rw, pp, passes;
+  int pp, passes;
   int plane;                 // float2 elements between pair planes in shared memory (a 128-byte multiple:
                              // every TMA destination must be 128-byte aligned)
+  const GalGeom* geo;
+  const int2* items;
+  const int* n_items_dev;
+  int n_items;
+  int* queue;                // next item - gridDim.x (zero at launch)
   const float* image;
   const float* sigma;
   const uint8_t* mask;
   const float* psf;
   const float* cconst;
   const float* scale;
-  const int* list;
-  const int* count;
-  double* partial;           // [G][n_tiles][nacc]
-  float* model_out;          // [G][H][W]
-  float* comp_out;           // [G][n_comp][H][W] or nullptr
+  double* partial;           // [tile0_g + tile][nacc]
+  float* model_out;          // stamp g from geo[g].pix
+  float* comp_out;           // [n_comp] images per stamp from n_comp * geo[g].pix, or nullptr
   int* err;                  // set to 1 when a TMA wait times out
-  int off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar;
+  int off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar, off_info;
+};
+
+// One item as thread 0 stages it in shared memory for the CTA.
+struct ItemInfo {
+  int valid, g, tile, pad;
+  GalGeom geo;
 };
 
 typedef unsigned long long u64;
@@ -120,48 +153,54 @@ __device__ __forceinline__ void unpack2(u64 v, float& x, float& y) {
 }
 
 // ---------------------------------------------------------------------------
-// k_profile
+// k_planes
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(256) k_profile(const __grid_constant__ ProfileArgs A) {
+__global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArgs A) {
   __shared__ float s_cc[kMaxComp * kCC];
   __shared__ float s_scale[kMaxSlots];
   __shared__ float s_v[256 * 2 * kMaxPairs];
   const ChanMap& m = A.m;
   const int tid = threadIdx.x;
-  const int per_gal = (A.H * A.Wp + 255) / 256;
-  const int n_gal = A.list ? *A.count : A.G;
+  if (blockIdx.x == 0 && tid < 3 && A.zero[tid]) *A.zero[tid] = 0;
+  const int n = A.n_items_dev ? *A.n_items_dev : A.n_items;
   float* v = s_v + tid * 2 * kMaxPairs;
-  for (int blk = blockIdx.x; blk < n_gal * per_gal; blk += gridDim.x) {
-    const int gi = blk / per_gal, chunk = blk - gi * per_gal;
-    const int g = A.list ? A.list[gi] : gi;
+  float2* out = reinterpret_cast<float2*>(A.planes);
+  for (int item = blockIdx.x; item < n; item += gridDim.x) {
+    const int2 it = A.items[item];
+    const int g = it.x;
+    const GalGeom& G = A.geo[g];
+    const int H = G.H, W = G.W, Wp = G.Wp;
+    const int i0 = (it.y / G.tiles_x) * kTile, j0 = (it.y % G.tiles_x) * kTile;
+    const size_t pbase = (size_t)(G.plane >> 1);
     __syncthreads();
     for (int t = tid; t < m.n_comp * kCC; t += 256) s_cc[t] = A.cconst[(size_t)g * m.n_comp * kCC + t];
     for (int t = tid; t < m.n_slots; t += 256) s_scale[t] = A.scale[(size_t)g * m.n_slots + t];
     __syncthreads();
-    const int pix = chunk * 256 + tid;
-    if (pix >= A.H * A.Wp) continue;
-    const int i = pix / A.Wp, j = pix - (pix / A.Wp) * A.Wp;
-    for (int ch = 0; ch < 2 * m.ncp; ++ch) v[ch] = 0.f;
-    if (j < A.W) {
-      for (int cm = 0; cm < m.n_comp; ++cm) {
-        if (!m.conv[cm]) continue;
-        float d[8];
-        const float val = eval_component(m.kind[cm], s_cc + cm * kCC, i, j, d);
-        v[0] += val;
-        if (MODE == MODE_MODEL) {
-          if (m.comp_chan[cm] >= 0) v[m.comp_chan[cm]] += val;
-        } else {
-          for (int k = 0; k < m.np[cm]; ++k) {
-            const int ch = m.chan[cm][k];
-            if (ch >= 0) v[ch] += d[k] * s_scale[m.slot[cm][k]];
+    for (int r = 0; r < kTilePix / 256; ++r) {
+      const int pix = r * 256 + tid;
+      const int i = i0 + pix / kTile, j = j0 + pix % kTile;
+      if (i >= H || j >= Wp) continue;
+      for (int ch = 0; ch < 2 * m.ncp; ++ch) v[ch] = 0.f;
+      if (j < W) {
+        for (int cm = 0; cm < m.n_comp; ++cm) {
+          if (!m.conv[cm]) continue;
+          float d[8];
+          const float val = eval_component(m.kind[cm], s_cc + cm * kCC, i, j, d);
+          v[0] += val;
+          if (MODE == MODE_MODEL) {
+            if (m.comp_chan[cm] >= 0) v[m.comp_chan[cm]] += val;
+          } else {
+            for (int k = 0; k < m.np[cm]; ++k) {
+              const int ch = m.chan[cm][k];
+              if (ch >= 0) v[ch] += d[k] * s_scale[m.slot[cm][k]];
+            }
           }
         }
       }
+      for (int cp = 0; cp < m.ncp; ++cp)
+        out[pbase + ((size_t)cp * H + i) * Wp + j] = make_float2(v[2 * cp], v[2 * cp + 1]);
     }
-    float2* out = reinterpret_cast<float2*>(A.planes);
-    for (int cp = 0; cp < m.ncp; ++cp)
-      out[(((size_t)g * m.ncp + cp) * A.H + i) * A.Wp + j] = make_float2(v[2 * cp], v[2 * cp + 1]);
   }
 }
 
@@ -205,22 +244,39 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Issue the loads of pass `pass` of item `item` (thread 0 only).
-__device__ __forceinline__ void issue_pass(const FusedArgs& A, float2* s_in, u64* bar, int item, int pass) {
-  const int gi = item / A.n_tiles, tile = item - gi * A.n_tiles;
-  const int g = A.list ? A.list[gi] : gi;
-  const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
-  const int c = (A.K - 1) / 2;
-  const int HH = kTile + A.K - 1;
+// Thread 0: read item `item` of this pass into *dst (valid = 0 past the end).
+__device__ __forceinline__ void fetch_item(const FusedArgs& A, int n_items, int item, ItemInfo* dst) {
+  if (item >= n_items) {
+    dst->valid = 0;
+    return;
+  }
+  const int2 it = A.items[item];
+  dst->valid = 1;
+  dst->g = it.x;
+  dst->tile = it.y;
+  dst->geo = A.geo[it.x];
+}
+
+// Thread 0: issue the loads of pass `pass` of item I.
+__device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I, float2* s_in, u64* bar, int pass) {
+  const GalGeom& G = I.geo;
+  const int K = G.K, c = (K - 1) / 2, cpad = c & 1;
+  const int i0 = (I.tile / G.tiles_x) * kTile, j0 = (I.tile % G.tiles_x) * kTile;
   const int first = pass * A.pp;
   const int npairs = min(A.pp, A.m.ncp - first);
-  const unsigned plane_bytes = (unsigned)HH * A.rw * 8u;
+  const unsigned plane_bytes = (unsigned)(kTile + K - 1) * G.rw * 8u;
+  const CUtensorMap* map = &A.tmap;
+  if (A.maps) {
+    map = A.maps + G.cls;
+    // the map was written to global memory by an ordinary copy: order that write before the TMA unit reads it
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<u64>(map))
+                 : "memory");
+  }
   // order this CTA's earlier generic-proxy reads of s_in before the async-proxy writes
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_expect_tx(bar, plane_bytes * npairs);
-  const int x = 2 * (j0 - c - A.cpad);  // even pair index: 16-byte aligned start
-  for (int q = 0; q < npairs; ++q)
-    tma_load_3d(s_in + (size_t)q * A.plane, &A.tmap, x, i0 - c, g * A.m.ncp + first + q, bar);
+  const int x = 2 * (j0 - c - cpad);  // even pair index: 16-byte aligned start
+  for (int q = 0; q < npairs; ++q) tma_load_3d(s_in + (size_t)q * A.plane, map, x, i0 - c, G.z0 + first + q, bar);
 }
 
 // ---------------------------------------------------------------------------
@@ -335,18 +391,17 @@ __device__ __forceinline__ void store_pairs(const u64 (&acc)[CP][8], float* s_ou
 // parameters over this thread's pixels of the tile, reduce over the block and
 // write the tile's FP64 partial sums.
 template <int P>
-__device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_out, float* s_red, int g, int tile,
-                                            int i0, int j0) {
+__device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_out, float* s_red, size_t base, int H,
+                                            int W, size_t prow, int i0, int j0) {
   constexpr int NA = 1 + P + P * (P + 1) / 2;
   float acc[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) acc[e] = 0.f;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const size_t base = (size_t)g * A.H * A.W;
   for (int pix = tid; pix < kTilePix; pix += nthr) {
     const int i = i0 + pix / kTile, j = j0 + pix % kTile;
-    if (i >= A.H || j >= A.W) continue;
-    const size_t gp = base + (size_t)i * A.W + j;
+    if (i >= H || j >= W) continue;
+    const size_t gp = base + (size_t)i * W + j;
     if (A.mask && A.mask[gp]) continue;
     const float isg = 1.f / A.sigma[gp];
     const float rr = (A.image[gp] - s_out[pix]) * isg;  // (D - M) / sigma
@@ -377,7 +432,7 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
   for (int e = tid; e < NA; e += nthr) {
     double s = 0.0;
     for (int w = 0; w < nwarp; ++w) s += (double)s_red[w * NA + e];
-    A.partial[((size_t)g * A.n_tiles + tile) * NA + e] = s;
+    A.partial[prow * NA + e] = s;
   }
 }
 
@@ -398,23 +453,22 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
   float* s_red = reinterpret_cast<float*>(smem + A.off_red);
   u64* bar = reinterpret_cast<u64*>(smem + A.off_bar);
   int* s_flag = reinterpret_cast<int*>(smem + A.off_bar + 8);
+  ItemInfo* s_info = reinterpret_cast<ItemInfo*>(smem + A.off_info);  // [2], alternating per item
   const ChanMap& m = A.m;
 
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int K = A.K, c = (K - 1) / 2, K2 = K + 1;
-  const int rw = A.rw;
-  const int n_gal = A.list ? *A.count : A.G;
-  const int n_items = n_gal * A.n_tiles;
+  const int n_items = A.n_items_dev ? *A.n_items_dev : A.n_items;
   if ((int)blockIdx.x >= n_items) return;
 
   if (tid == 0) {
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
+    fetch_item(A, n_items, blockIdx.x, &s_info[0]);
+    issue_pass(A, s_info[0], s_in, bar, 0);
   }
-  __syncthreads();
-  if (tid == 0) issue_pass(A, s_in, bar, blockIdx.x, 0);
   unsigned phase = 0;
+  int slot = 0;
 
   const int grp = tid / kGroupThreads;
   const int t = tid - grp * kGroupThreads;
@@ -422,23 +476,32 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
   const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
   const int row0 = wig * 8;
 
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int gi = item / A.n_tiles, tile = item - gi * A.n_tiles;
-    const int g = A.list ? A.list[gi] : gi;
-    const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
+  for (;;) {
+    __syncthreads();  // the previous item is done with s_psf, s_cc, s_scale, s_out, s_red and s_info[slot ^ 1]
+    const ItemInfo& I = s_info[slot];
+    if (!I.valid) break;
+    if (tid == 0) {
+      // claim and read the next item now; its loads are issued after this item's last window
+      const int nxt = (int)gridDim.x + atomicAdd(A.queue, 1);
+      fetch_item(A, n_items, nxt, &s_info[slot ^ 1]);
+    }
+    const int g = I.g;
+    const int H = I.geo.H, W = I.geo.W, K = I.geo.K, rw = I.geo.rw;
+    const int c = (K - 1) / 2, K2 = K + 1, cpad = c & 1;
+    const int i0 = (I.tile / I.geo.tiles_x) * kTile, j0 = (I.tile % I.geo.tiles_x) * kTile;
+    const float* psf = A.psf + I.geo.psf;
 
-    __syncthreads();  // the previous item is done with s_psf, s_cc, s_scale, s_out, s_red
     for (int t2 = tid; t2 < m.n_comp * kCC; t2 += nthr) s_cc[t2] = A.cconst[(size_t)g * m.n_comp * kCC + t2];
     for (int t2 = tid; t2 < m.n_slots; t2 += nthr) s_scale[t2] = A.scale[(size_t)g * m.n_slots + t2];
     for (int t2 = tid; t2 < K * K2; t2 += nthr) {
       const int a = t2 / K2, bb = t2 - a * K2;
-      const int b = bb - A.cpad;  // tap index in the unpadded PSF row
-      const float v = (b >= 0 && b < K) ? A.psf[(size_t)g * K * K + a * K + b] : 0.f;
+      const int b = bb - cpad;  // tap index in the unpadded PSF row
+      const float v = (b >= 0 && b < K) ? psf[a * K + b] : 0.f;
       s_psf[t2] = pack2(v, v);
     }
     // PSF rows whose 8 input rows (for this warp) all fall outside the stamp are skipped
     const int a_lo = max(0, c - i0 - row0 - 7);
-    const int a_hi = min(K, c - i0 + A.H - row0);
+    const int a_hi = min(K, c - i0 + H - row0);
 
     for (int pass = 0; pass < A.passes; ++pass) {
       // wait for this pass's window (thread 0 polls with a bound, the CTA agrees)
@@ -466,8 +529,8 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
       else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
       __syncthreads();  // every warp is done reading the window
       if (tid == 0) {
-        if (pass + 1 < A.passes) issue_pass(A, s_in, bar, item, pass + 1);
-        else if (item + (int)gridDim.x < n_items) issue_pass(A, s_in, bar, item + gridDim.x, 0);
+        if (pass + 1 < A.passes) issue_pass(A, I, s_in, bar, pass + 1);
+        else if (s_info[slot ^ 1].valid) issue_pass(A, s_info[slot ^ 1], s_in, bar, 0);
       }
       if (CPT == 2 && npair == 2) store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
       else if (npair == 1) store_pairs<1>(acc1, s_out, first + lp0, m.nch_conv, row, col0);
@@ -479,7 +542,7 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
       for (int ch = m.nch_conv; ch < m.nch_tot; ++ch) s_out[ch * kTilePix + pix] = 0.f;
       if (!m.any_unconv) continue;
       const int i = i0 + pix / kTile, j = j0 + pix % kTile;
-      if (i >= A.H || j >= A.W) continue;
+      if (i >= H || j >= W) continue;
       for (int cm = 0; cm < m.n_comp; ++cm) {
         if (m.conv[cm]) continue;
         float d[8];
@@ -499,21 +562,23 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
     __syncthreads();
 
     // ---- outputs ----
+    const size_t pix0 = (size_t)I.geo.pix;
     if (MODE == MODE_MODEL) {
-      const size_t HW = (size_t)A.H * A.W;
+      const size_t HW = (size_t)H * W;
       for (int pix = tid; pix < kTilePix; pix += nthr) {
         const int i = i0 + pix / kTile, j = j0 + pix % kTile;
-        if (i >= A.H || j >= A.W) continue;
-        const size_t off = (size_t)i * A.W + j;
-        A.model_out[(size_t)g * HW + off] = s_out[pix];
+        if (i >= H || j >= W) continue;
+        const size_t off = (size_t)i * W + j;
+        A.model_out[pix0 + off] = s_out[pix];
         if (A.comp_out) {
           for (int cm = 0; cm < m.n_comp; ++cm)
-            A.comp_out[((size_t)g * m.n_comp + cm) * HW + off] = s_out[m.comp_chan[cm] * kTilePix + pix];
+            A.comp_out[(size_t)m.n_comp * pix0 + cm * HW + off] = s_out[m.comp_chan[cm] * kTilePix + pix];
         }
       }
     } else {
-      reduce_tile<P>(A, s_out, s_red, g, tile, i0, j0);
+      reduce_tile<P>(A, s_out, s_red, pix0, H, W, (size_t)I.geo.tile0 + I.tile, i0, j0);
     }
+    slot ^= 1;
   }
 }
 

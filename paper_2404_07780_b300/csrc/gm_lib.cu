@@ -8,11 +8,14 @@
 #include <vector>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <mutex>
 
 #include "../../include/gm.h"
 #include "gm_adjoint.cuh"
 #include "gm_fused.cuh"
+#include "gm_geom.cuh"
 #include "gm_lm.cuh"
 
 using namespace gm;
@@ -93,14 +96,22 @@ int check_desc(const gm_model_desc* d) {
   return GM_OK;
 }
 
+int check_hwk(int H, int W, int K, const char* what, int g) {
+  if (H < 1 || H > 4096 || W < 1 || W > 4096)
+    return g < 0 ? fail(GM_E_INVAL, "%s stamp %dx%d outside 1..4096", what, H, W)
+                 : fail(GM_E_INVAL, "%s stamp %d is %dx%d, outside 1..4096", what, g, H, W);
+  if (K < 1 || K > 63 || (K % 2) == 0)
+    return g < 0 ? fail(GM_E_INVAL, "%s PSF side K=%d must be odd, 1..63", what, K)
+                 : fail(GM_E_INVAL, "%s PSF %d has side %d; it must be odd, 1..63", what, g, K);
+  return GM_OK;
+}
+
 // Sizes only (what the workspace queries need).
 int check_sizes(const gm_batch* b) {
   if (!b) return fail(GM_E_INVAL, "batch is NULL");
   if (b->n_gal < 0) return fail(GM_E_INVAL, "n_gal=%d < 0", b->n_gal);
-  if (b->H < 1 || b->H > 4096 || b->W < 1 || b->W > 4096)
-    return fail(GM_E_INVAL, "stamp %dx%d outside 1..4096", b->H, b->W);
-  if (b->K < 1 || b->K > 63 || (b->K % 2) == 0) return fail(GM_E_INVAL, "PSF side K=%d must be odd, 1..63", b->K);
-  return GM_OK;
+  if (b->geom) return GM_OK;  // per-galaxy sizes are checked by plan_geom
+  return check_hwk(b->H, b->W, b->K, "batch", -1);
 }
 
 int check_batch(const gm_batch* b, bool need_data) {
@@ -246,30 +257,25 @@ ChanMap chan_map(const Plan& pl) {
 }
 
 struct Smem {
-  int rw, pp, passes, plane, off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar, total, threads;
+  int pp, passes, plane, off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar, off_info, total, threads;
 };
 
 // Channel pairs per thread of the fused kernel: one (more warps) unless the
 // reduction of many free parameters needs the register budget of 256 threads.
 int pick_cpt(const Plan& pl) { return (pl.nacc == 0 || pl.dd.P <= kMaxP1) ? 1 : 2; }
 
-// Shared-memory carve-up of one fused CTA for `pp` channel pairs per pass.
-// The window row pitch rw (in float2) is >= K + 33 (the register window reads
-// two columns past the last tap) and == 2 mod 4, so the 8 lanes of a quarter
-// warp (8 consecutive rows) hit distinct 16-byte bank groups on their 16-byte
-// loads.
+// Shared-memory carve-up of one fused CTA for `pp` channel pairs per pass and
+// PSF sides up to K.  Each pair plane holds a (32+K-1) x window_pitch(K)
+// window and starts at a 128-byte boundary (TMA destinations must be
+// 128-byte aligned).
 Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp) {
   Smem s;
   const int cpt = pick_cpt(pl);
   s.pp = pp;
   s.passes = (pl.ncp + pp - 1) / pp;
   s.threads = kGroupThreads * ((pp + cpt - 1) / cpt);
-  int rw = K + 33;
-  while (rw % 4 != 2) ++rw;
-  s.rw = rw;
   const int HH = kTile + K - 1;
-  // pair planes start at 128-byte boundaries (TMA destinations must be 128-byte aligned)
-  const size_t plane_bytes = ((size_t)HH * rw * 8 + 127) / 128 * 128;
+  const size_t plane_bytes = ((size_t)HH * window_pitch(K) * 8 + 127) / 128 * 128;
   s.plane = (int)(plane_bytes / 8);
   size_t off = 0;
   auto take = [&](size_t bytes, size_t align) {
@@ -285,6 +291,7 @@ Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp) {
   s.off_scale = take((size_t)n_slots * 4, 16);
   s.off_red = take((size_t)(s.threads / 32) * std::max(pl.nacc, 1) * 4, 16);
   s.off_bar = take(16, 16);
+  s.off_info = take(2 * sizeof(ItemInfo), 16);
   s.total = (int)off;
   return s;
 }
@@ -349,138 +356,179 @@ int encode_fn(PFN_cuTensorMapEncodeTiled_v12000* out) {
   return GM_OK;
 }
 
-int fill_args(FusedArgs& A, const Plan& pl, const gm_batch* b, const Smem& sm, float* planes, int Wp) {
-  std::memset(&A, 0, sizeof(A));
-  A.m = chan_map(pl);
-  A.nacc = pl.nacc;
-  A.G = b->n_gal;
-  A.H = b->H;
-  A.W = b->W;
-  A.K = b->K;
-  A.cpad = ((b->K - 1) / 2) & 1;
-  A.tiles_x = (b->W + kTile - 1) / kTile;
-  A.n_tiles = A.tiles_x * ((b->H + kTile - 1) / kTile);
-  A.rw = sm.rw;
-  A.pp = sm.pp;
-  A.passes = sm.passes;
-  A.plane = sm.plane;
-  A.image = b->image;
-  A.sigma = b->sigma;
-  A.mask = b->mask;
-  A.psf = b->psf;
-  A.off_psf = sm.off_psf;
-  A.off_in = sm.off_in;
-  A.off_out = sm.off_out;
-  A.off_cc = sm.off_cc;
-  A.off_scale = sm.off_scale;
-  A.off_red = sm.off_red;
-  A.off_bar = sm.off_bar;
-  // planes as a rank-3 FP32 tensor: x = 2*Wp floats (interleaved pairs), y = H rows,
-  // z = G*ncp planes; box = 2*rw floats x (32+K-1) rows x 1 plane; zero fill outside
+// Pair planes of H x W stamps as a rank-3 FP32 tensor: x = 2*Wp floats
+// (interleaved pairs), y = H rows, z = n_planes planes; box = 2*window_pitch(K)
+// floats x (32+K-1) rows x 1 plane; zero fill outside.
+int encode_planes(CUtensorMap* map, float* base, int H, int W, int K, long long n_planes) {
   PFN_cuTensorMapEncodeTiled_v12000 enc;
   int rc = encode_fn(&enc);
   if (rc) return rc;
-  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Wp), (cuuint64_t)b->H, (cuuint64_t)b->n_gal * pl.ncp};
-  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Wp) * 4, (cuuint64_t)(2 * Wp) * 4 * b->H};
-  const cuuint32_t box[3] = {(cuuint32_t)(2 * sm.rw), (cuuint32_t)(kTile + b->K - 1), 1};
+  const int Wp = W + (W & 1), rw = window_pitch(K);
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Wp), (cuuint64_t)H, (cuuint64_t)n_planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Wp) * 4, (cuuint64_t)(2 * Wp) * 4 * H};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * rw), (cuuint32_t)(kTile + K - 1), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult cr = enc(&A.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, planes, dims, strides, box, estr,
+  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(GM_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
   return GM_OK;
 }
 
-ProfileArgs profile_args(const Plan& pl, const gm_batch* b, const float* cconst, const float* scale,
-                         float* planes, int Wp) {
-  ProfileArgs P;
-  std::memset(&P, 0, sizeof(P));
-  P.m = chan_map(pl);
-  P.G = b->n_gal;
-  P.H = b->H;
-  P.W = b->W;
-  P.Wp = Wp;
-  P.cconst = cconst;
-  P.scale = scale;
-  P.planes = planes;
-  return P;
-}
+// ---------------------------------------------------------------------------
+// batch geometry
+// ---------------------------------------------------------------------------
+// One class of stamps with the same (H, W, K): its planes are one tensor.
+struct ClassInfo {
+  int H, W, K, n;
+  size_t base;  // first float of the class's planes in the plane buffer
+};
 
-typedef void (*ProfileKernel)(ProfileArgs);
+struct GeomPlan {
+  int G = 0, ncp = 0;
+  bool ragged = false;
+  int H = 0, W = 0, K = 0;   // equal stamps: the sizes; uneven: the largest of each
+  long long n_items = 0;     // (galaxy, tile) items of one pass over every galaxy
+  size_t plane_floats = 0;   // size of the pair-plane buffer
+  std::vector<ClassInfo> cls;
+  // host tables of an uneven batch (built when asked for)
+  std::vector<GalGeom> geo;
+  std::vector<int> order;
+  std::vector<int2> items;
+};
 
-int prepare_fused(int mode, const Plan& pl, const Smem& sm, FusedKernel* out) {
-  FusedKernel k = pick_kernel(mode, pl.dd.P);
-  if (!k) return fail(GM_E_UNSUPPORTED, "no fused kernel for %d free parameters", pl.dd.P);
-  GM_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm.total));
-  *out = k;
+size_t round_floats(size_t n) { return (n + 63) / 64 * 64; }  // 256-byte multiples
+
+// Sizes, classes and (tables = true, uneven stamps) the geometry table, the
+// processing order (decreasing cost: PSF area, then tiles) and the item list.
+int plan_geom(const gm_batch* b, int ncp, bool tables, GeomPlan* gp) {
+  int rc = check_sizes(b);
+  if (rc) return rc;
+  gp->G = b->n_gal;
+  gp->ncp = ncp;
+  gp->ragged = b->geom != nullptr;
+  gp->cls.clear();
+  gp->geo.clear();
+  gp->order.clear();
+  gp->items.clear();
+  const long long G = b->n_gal;
+  if (!gp->ragged) {
+    gp->H = b->H;
+    gp->W = b->W;
+    gp->K = b->K;
+    const GalGeom g1 = uniform_geom(0, b->H, b->W, b->K, ncp);
+    gp->n_items = G * g1.n_tiles;
+    gp->plane_floats = (size_t)G * ncp * b->H * g1.Wp * 2;
+    gp->cls.push_back(ClassInfo{b->H, b->W, b->K, (int)G, 0});
+  } else {
+    std::map<std::tuple<int, int, int>, int> cid;
+    std::vector<int> cls_of(tables ? G : 0), rank(tables ? G : 0);
+    gp->H = gp->W = gp->K = 1;
+    long long items = 0;
+    for (long long g = 0; g < G; ++g) {
+      const int h = b->geom[3 * g], w = b->geom[3 * g + 1], k = b->geom[3 * g + 2];
+      if ((rc = check_hwk(h, w, k, "uneven batch:", (int)g))) return rc;
+      auto it = cid.find(std::make_tuple(h, w, k));
+      int c;
+      if (it == cid.end()) {
+        c = (int)gp->cls.size();
+        cid.emplace(std::make_tuple(h, w, k), c);
+        gp->cls.push_back(ClassInfo{h, w, k, 0, 0});
+      } else {
+        c = it->second;
+      }
+      if (tables) {
+        cls_of[g] = c;
+        rank[g] = gp->cls[c].n;
+      }
+      ++gp->cls[c].n;
+      gp->H = std::max(gp->H, h);
+      gp->W = std::max(gp->W, w);
+      gp->K = std::max(gp->K, k);
+      items += (long long)((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile);
+    }
+    gp->n_items = items;
+    size_t off = 0;
+    for (ClassInfo& c : gp->cls) {
+      c.base = off;
+      off += round_floats((size_t)c.n * ncp * c.H * (c.W + (c.W & 1)) * 2);
+    }
+    gp->plane_floats = off;
+    if (tables) {
+      gp->geo.resize(G);
+      long long pix = 0, psf = 0, tile0 = 0;
+      for (long long g = 0; g < G; ++g) {
+        const ClassInfo& c = gp->cls[cls_of[g]];
+        GalGeom r = uniform_geom(0, c.H, c.W, c.K, ncp);
+        r.pix = pix;
+        r.psf = psf;
+        r.plane = (long long)c.base + (long long)rank[g] * ncp * c.H * r.Wp * 2;
+        r.tile0 = (int)tile0;
+        r.cls = cls_of[g];
+        r.z0 = rank[g] * ncp;
+        gp->geo[g] = r;
+        pix += (long long)c.H * c.W;
+        psf += (long long)c.K * c.K;
+        tile0 += r.n_tiles;
+      }
+      gp->order.resize(G);
+      for (long long g = 0; g < G; ++g) gp->order[g] = (int)g;
+      const std::vector<GalGeom>& geo = gp->geo;
+      std::stable_sort(gp->order.begin(), gp->order.end(), [&](int x, int y) {
+        if (geo[x].K != geo[y].K) return geo[x].K > geo[y].K;
+        return geo[x].n_tiles > geo[y].n_tiles;
+      });
+      gp->items.reserve(items);
+      for (int g : gp->order)
+        for (int t = 0; t < geo[g].n_tiles; ++t) gp->items.push_back(make_int2(g, t));
+    }
+  }
+  if (gp->n_items > 0x7fffffffLL)
+    return fail(GM_E_UNSUPPORTED, "%lld tiles in one batch exceed 2^31 - 1", gp->n_items);
   return GM_OK;
 }
 
-// workspace carve-up
-// Channel pairs the fused pass of `mode` correlates for this description
-// (MODEL mode sized for per-component images).
-int pairs_for(const gm_model_desc* d, int mode) {
-  bool touches_conv[kMaxSlots] = {};
-  int n_conv = 0;
-  for (int c = 0; c < d->n_comp; ++c) {
-    if (!d->comp[c].convolve) continue;
-    ++n_conv;
-    const int np = n_params(d->comp[c].kind);
-    for (int k = 0; k < np; ++k) touches_conv[d->comp[c].slot[k]] = true;
-  }
-  int Pc = 0;
-  for (int s = 0; s < d->n_slots; ++s) Pc += (d->is_free[s] && touches_conv[s]) ? 1 : 0;
-  const int nch = (mode == MODE_NORMAL) ? 1 + Pc : 1 + n_conv;
-  return (nch + 1) / 2;
-}
-
-struct WsModel {
-  size_t cconst, scale, planes, err, total;
-  int Wp;
+// Workspace shared by the model, chi^2 and fit calls.  geo .. maps are
+// adjacent so that an uneven batch's host tables go over in one copy.
+struct WsCore {
+  size_t geo, order, items, maps, table_end, cconst, scale, planes, partial, err, queue, total;
 };
-WsModel ws_model(const gm_model_desc* d, const gm_batch* b, int ncp) {
-  WsModel w;
+
+WsCore ws_core(const gm_model_desc* d, const GeomPlan& gp, int nacc) {
+  WsCore w;
   size_t off = 0;
-  const size_t G = (size_t)std::max(b->n_gal, 0);
-  w.Wp = b->W + (b->W & 1);
-  w.cconst = off;
-  off += align256(G * d->n_comp * kCC * 4);
-  w.scale = off;
-  off += align256(G * d->n_slots * 4);
-  w.planes = off;
-  off += align256(G * (size_t)ncp * b->H * w.Wp * 8);
-  w.err = off;
-  off += align256(4);
-  w.total = off;
-  return w;
-}
-
-struct WsChi2 {
-  WsModel m;
-  size_t partial, total;
-};
-WsChi2 ws_chi2(const gm_model_desc* d, const gm_batch* b, int P) {
-  WsChi2 w;
-  w.m = ws_model(d, b, pairs_for(d, MODE_NORMAL));
-  size_t off = w.m.total;
-  const size_t G = (size_t)std::max(b->n_gal, 0);
-  const size_t tiles = (size_t)((b->W + kTile - 1) / kTile) * ((b->H + kTile - 1) / kTile);
-  const size_t nacc = 1 + P + (size_t)P * (P + 1) / 2;
-  w.partial = off;
-  off += align256(G * tiles * nacc * 8);
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  const size_t G = (size_t)std::max(gp.G, 0);
+  w.geo = take(G * sizeof(GalGeom));
+  w.order = take(G * 4);
+  w.items = take((size_t)gp.n_items * 8);
+  w.maps = take(gp.ragged ? gp.cls.size() * sizeof(CUtensorMap) : 0);
+  w.table_end = off;
+  w.cconst = take(G * d->n_comp * kCC * 4);
+  w.scale = take(G * d->n_slots * 4);
+  w.planes = take(gp.plane_floats * 4);
+  w.partial = take(nacc > 0 ? (size_t)gp.n_items * nacc * 8 : 0);
+  w.err = take(4);
+  w.queue = take(4);
   w.total = off;
   return w;
 }
 
 struct WsFit {
-  WsChi2 c;
-  size_t p_b, p_t, A_b, g_b, chi2_b, lam, it, status, nused, bad, list0, list1, counts, evals, total;
+  WsCore c;
+  size_t p_b, p_t, A_b, g_b, chi2_b, lam, it, status, nused, bad, list0, list1, counts, items0, items1, icounts,
+      evals, total;
 };
-WsFit ws_fit(const gm_model_desc* d, const gm_batch* b, int P) {
+
+WsFit ws_fit(const gm_model_desc* d, const GeomPlan& gp, int P) {
   WsFit w;
-  w.c = ws_chi2(d, b, P);
+  w.c = ws_core(d, gp, 1 + P + P * (P + 1) / 2);
   size_t off = w.c.total;
-  const size_t G = (size_t)std::max(b->n_gal, 0), S = d->n_slots;
+  const size_t G = (size_t)std::max(gp.G, 0), S = d->n_slots;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off += align256(bytes);
@@ -499,9 +547,116 @@ WsFit ws_fit(const gm_model_desc* d, const gm_batch* b, int P) {
   w.list0 = take(G * 4);
   w.list1 = take(G * 4);
   w.counts = take(2 * 4);
+  w.items0 = take((size_t)gp.n_items * 8);
+  w.items1 = take((size_t)gp.n_items * 8);
+  w.icounts = take(2 * 4);
   w.evals = take(3 * 8);
   w.total = off;
   return w;
+}
+
+// Kernel arguments that depend only on the model and the shared-memory plan.
+void fill_args(FusedArgs& A, const Plan& pl, const Smem& sm) {
+  std::memset(&A, 0, sizeof(A));
+  A.m = chan_map(pl);
+  A.nacc = pl.nacc;
+  A.pp = sm.pp;
+  A.passes = sm.passes;
+  A.plane = sm.plane;
+  A.off_psf = sm.off_psf;
+  A.off_in = sm.off_in;
+  A.off_out = sm.off_out;
+  A.off_cc = sm.off_cc;
+  A.off_scale = sm.off_scale;
+  A.off_red = sm.off_red;
+  A.off_bar = sm.off_bar;
+  A.off_info = sm.off_info;
+}
+
+// Geometry table, processing order, the item list of a pass over every galaxy
+// and the tensor maps of the planes: built on the device for equal stamps (one
+// map, passed by value), copied from the host for uneven ones (one map per
+// class, in the workspace).
+int put_tables(const GeomPlan& gp, const WsCore& w, char* ws, const DevInfo& di, cudaStream_t st, FusedArgs* A) {
+  float* planes = (float*)(ws + w.planes);
+  GalGeom* geo = (GalGeom*)(ws + w.geo);
+  int* order = (int*)(ws + w.order);
+  int2* items = (int2*)(ws + w.items);
+  A->geo = geo;
+  if (!gp.ragged) {
+    const long long n = std::max<long long>(gp.n_items, gp.G);
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8LL * di.sms));
+    k_geom_uniform<<<blocks, 256, 0, st>>>(gp.G, gp.H, gp.W, gp.K, gp.ncp, geo, order, items);
+    GM_LAUNCHED("k_geom_uniform");
+    A->maps = nullptr;
+    return encode_planes(&A->tmap, planes, gp.H, gp.W, gp.K, (long long)gp.G * gp.ncp);
+  }
+  thread_local std::vector<unsigned char> stage;
+  stage.assign(w.table_end, 0);
+  std::memcpy(stage.data() + w.geo, gp.geo.data(), gp.geo.size() * sizeof(GalGeom));
+  std::memcpy(stage.data() + w.order, gp.order.data(), gp.order.size() * sizeof(int));
+  std::memcpy(stage.data() + w.items, gp.items.data(), gp.items.size() * sizeof(int2));
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(stage.data() + w.maps);
+  for (size_t c = 0; c < gp.cls.size(); ++c) {
+    const ClassInfo& ci = gp.cls[c];
+    int rc = encode_planes(&maps[c], planes + ci.base, ci.H, ci.W, ci.K, (long long)ci.n * gp.ncp);
+    if (rc) return rc;
+  }
+  GM_CUDA(cudaMemcpyAsync(ws, stage.data(), w.table_end, cudaMemcpyHostToDevice, st));
+  A->maps = (const CUtensorMap*)(ws + w.maps);
+  return GM_OK;
+}
+
+// Profile-kernel arguments of the adjoint path (equal stamps).
+ProfileArgs profile_args(const Plan& pl, const gm_batch* b, const float* cconst, const float* scale,
+                         float* planes, int Wp) {
+  ProfileArgs P;
+  std::memset(&P, 0, sizeof(P));
+  P.m = chan_map(pl);
+  P.G = b->n_gal;
+  P.H = b->H;
+  P.W = b->W;
+  P.Wp = Wp;
+  P.cconst = cconst;
+  P.scale = scale;
+  P.planes = planes;
+  return P;
+}
+
+PlaneArgs plane_args(const Plan& pl, const GalGeom* geo, const float* cconst, const float* scale, float* planes) {
+  PlaneArgs P;
+  std::memset(&P, 0, sizeof(P));
+  P.m = chan_map(pl);
+  P.geo = geo;
+  P.cconst = cconst;
+  P.scale = scale;
+  P.planes = planes;
+  return P;
+}
+
+int prepare_fused(int mode, const Plan& pl, const Smem& sm, FusedKernel* out) {
+  FusedKernel k = pick_kernel(mode, pl.dd.P);
+  if (!k) return fail(GM_E_UNSUPPORTED, "no fused kernel for %d free parameters", pl.dd.P);
+  GM_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm.total));
+  *out = k;
+  return GM_OK;
+}
+
+// Channel pairs the fused pass of `mode` correlates for this description
+// (MODEL mode sized for per-component images).
+int pairs_for(const gm_model_desc* d, int mode) {
+  bool touches_conv[kMaxSlots] = {};
+  int n_conv = 0;
+  for (int c = 0; c < d->n_comp; ++c) {
+    if (!d->comp[c].convolve) continue;
+    ++n_conv;
+    const int np = n_params(d->comp[c].kind);
+    for (int k = 0; k < np; ++k) touches_conv[d->comp[c].slot[k]] = true;
+  }
+  int Pc = 0;
+  for (int s = 0; s < d->n_slots; ++s) Pc += (d->is_free[s] && touches_conv[s]) ? 1 : 0;
+  const int nch = (mode == MODE_NORMAL) ? 1 + Pc : 1 + n_conv;
+  return (nch + 1) / 2;
 }
 
 int count_free(const gm_model_desc* d) {
@@ -509,6 +664,8 @@ int count_free(const gm_model_desc* d) {
   for (int s = 0; s < d->n_slots && s < GM_MAX_SLOTS; ++s) P += d->is_free[s] ? 1 : 0;
   return P;
 }
+
+int n_acc(int P) { return 1 + P + P * (P + 1) / 2; }
 
 LMOpts lm_opts(const gm_fit_opts* o) {
   LMOpts L;
@@ -536,6 +693,69 @@ LMOpts lm_opts(const gm_fit_opts* o) {
   return L;
 }
 
+// One model+Jacobian pass over every galaxy (gm_model: MODE_MODEL;
+// gm_chi2_grad: MODE_NORMAL, tile partials in the workspace).
+struct PassCall {
+  Plan pl;
+  GeomPlan gp;
+  WsCore w;
+  Smem sm;
+  FusedKernel kf;
+  FusedArgs A;
+  PlaneArgs PA;
+  DevInfo di;
+};
+
+int setup_pass(int mode, const gm_model_desc* desc, const gm_batch* batch, const double* params, void* workspace,
+               size_t ws_bytes, cudaStream_t st, PassCall* pc) {
+  char* ws = (char*)workspace;
+  const int G = batch->n_gal;
+  pc->w = ws_core(desc, pc->gp, pc->pl.nacc);
+  if (!workspace || ws_bytes < pc->w.total)
+    return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, pc->w.total);
+  int rc;
+  if ((rc = dev_info(&pc->di))) return rc;
+  if ((rc = smem_plan(pc->pl, pc->gp.K, desc->n_comp, desc->n_slots, pc->di.smem_optin, &pc->sm))) return rc;
+  if ((rc = prepare_fused(mode, pc->pl, pc->sm, &pc->kf))) return rc;
+  fill_args(pc->A, pc->pl, pc->sm);
+  if ((rc = put_tables(pc->gp, pc->w, ws, pc->di, st, &pc->A))) return rc;
+  FusedArgs& A = pc->A;
+  float* cconst = (float*)(ws + pc->w.cconst);
+  float* scale = (float*)(ws + pc->w.scale);
+  float* planes = (float*)(ws + pc->w.planes);
+  A.items = (const int2*)(ws + pc->w.items);
+  A.n_items = (int)pc->gp.n_items;
+  A.queue = (int*)(ws + pc->w.queue);
+  A.image = batch->image;
+  A.sigma = batch->sigma;
+  A.mask = batch->mask;
+  A.psf = batch->psf;
+  A.cconst = cconst;
+  A.scale = scale;
+  A.partial = (double*)(ws + pc->w.partial);
+  A.err = (int*)(ws + pc->w.err);
+  pc->PA = plane_args(pc->pl, A.geo, cconst, scale, planes);
+  pc->PA.items = A.items;
+  pc->PA.n_items = A.n_items;
+  pc->PA.zero[0] = A.queue;
+  GM_CUDA(cudaMemsetAsync(A.err, 0, sizeof(int), st));
+  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pc->pl.dd, G, A.geo, 0, params, 0, cconst, scale);
+  GM_LAUNCHED("k_setup");
+  return GM_OK;
+}
+
+int launch_pass(int mode, PassCall* pc, cudaStream_t st) {
+  const long long n = pc->gp.n_items;
+  const int pgrid = (int)std::max<long long>(1, std::min<long long>(n, 8LL * pc->di.sms));
+  if (mode == MODE_MODEL) k_planes<MODE_MODEL><<<pgrid, 256, 0, st>>>(pc->PA);
+  else k_planes<MODE_NORMAL><<<pgrid, 256, 0, st>>>(pc->PA);
+  GM_LAUNCHED("k_planes");
+  const int grid = (int)std::max<long long>(1, std::min<long long>(n, pc->di.sms));
+  pc->kf<<<grid, pc->sm.threads, pc->sm.total, st>>>(pc->A);
+  GM_LAUNCHED("k_fused");
+  return GM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -552,106 +772,58 @@ int gm_fit_last_stats(gm_fit_stats* out) {
 const char* gm_last_error(void) { return g_err; }
 
 size_t gm_model_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
-  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
-  return ws_model(desc, batch, pairs_for(desc, MODE_MODEL)).total;
+  if (!desc || !batch || check_desc(desc)) return 0;
+  GeomPlan gp;
+  if (plan_geom(batch, pairs_for(desc, MODE_MODEL), false, &gp)) return 0;
+  return ws_core(desc, gp, 0).total;
 }
 
 int gm_model(const gm_model_desc* desc, const gm_batch* batch, const double* params, float* model_out,
              float* comp_out, void* workspace, size_t ws_bytes, void* stream) {
   int rc = check_batch(batch, false);
   if (rc) return rc;
-  Plan pl;
-  rc = make_plan(desc, MODE_MODEL, comp_out != nullptr, &pl);
-  if (rc) return rc;
+  PassCall pc;
+  if ((rc = make_plan(desc, MODE_MODEL, comp_out != nullptr, &pc.pl))) return rc;
+  if ((rc = plan_geom(batch, pc.pl.ncp, true, &pc.gp))) return rc;
   if (batch->n_gal == 0) return GM_OK;
   if (!params || !model_out) return fail(GM_E_INVAL, "params/model_out is NULL");
-  const WsModel w = ws_model(desc, batch, pairs_for(desc, MODE_MODEL));
-  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
-  DevInfo di;
-  if ((rc = dev_info(&di))) return rc;
-  Smem sm;
-  if ((rc = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots, di.smem_optin, &sm))) return rc;
-  FusedKernel kf;
-  if ((rc = prepare_fused(MODE_MODEL, pl, sm, &kf))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  char* ws = (char*)workspace;
-  float* cconst = (float*)(ws + w.cconst);
-  float* scale = (float*)(ws + w.scale);
-  float* planes = (float*)(ws + w.planes);
-  const int G = batch->n_gal;
-  FusedArgs A;
-  if ((rc = fill_args(A, pl, batch, sm, planes, w.Wp))) return rc;
-  A.cconst = cconst;
-  A.scale = scale;
-  A.model_out = model_out;
-  A.comp_out = comp_out;
-  A.err = (int*)(ws + w.err);
-  GM_CUDA(cudaMemsetAsync(A.err, 0, sizeof(int), st));
-  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
-  GM_LAUNCHED("k_setup");
-  const ProfileArgs PA = profile_args(pl, batch, cconst, scale, planes, w.Wp);
-  const int pblocks = G * ((batch->H * w.Wp + 255) / 256);
-  k_profile<MODE_MODEL><<<std::min(pblocks, 8 * di.sms), 256, 0, st>>>(PA);
-  GM_LAUNCHED("k_profile(model)");
-  const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
-  kf<<<grid, sm.threads, sm.total, st>>>(A);
-  GM_LAUNCHED("k_fused(model)");
-  return GM_OK;
+  if ((rc = setup_pass(MODE_MODEL, desc, batch, params, workspace, ws_bytes, st, &pc))) return rc;
+  pc.A.model_out = model_out;
+  pc.A.comp_out = comp_out;
+  return launch_pass(MODE_MODEL, &pc, st);
 }
 
 size_t gm_chi2_grad_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
-  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
-  return ws_chi2(desc, batch, count_free(desc)).total;
+  if (!desc || !batch || check_desc(desc)) return 0;
+  GeomPlan gp;
+  if (plan_geom(batch, pairs_for(desc, MODE_NORMAL), false, &gp)) return 0;
+  return ws_core(desc, gp, n_acc(count_free(desc))).total;
 }
 
 int gm_chi2_grad(const gm_model_desc* desc, const gm_batch* batch, const double* params, double* chi2,
                  double* grad, double* jtj, void* workspace, size_t ws_bytes, void* stream) {
   int rc = check_batch(batch, true);
   if (rc) return rc;
-  Plan pl;
-  rc = make_plan(desc, MODE_NORMAL, false, &pl);
-  if (rc) return rc;
+  PassCall pc;
+  if ((rc = make_plan(desc, MODE_NORMAL, false, &pc.pl))) return rc;
+  if ((rc = plan_geom(batch, pc.pl.ncp, true, &pc.gp))) return rc;
   if (batch->n_gal == 0) return GM_OK;
   if (!params || !chi2) return fail(GM_E_INVAL, "params/chi2 is NULL");
-  const WsChi2 w = ws_chi2(desc, batch, pl.dd.P);
-  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
-  DevInfo di;
-  if ((rc = dev_info(&di))) return rc;
-  Smem sm;
-  if ((rc = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots, di.smem_optin, &sm))) return rc;
-  FusedKernel kf;
-  if ((rc = prepare_fused(MODE_NORMAL, pl, sm, &kf))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  char* ws = (char*)workspace;
-  float* cconst = (float*)(ws + w.m.cconst);
-  float* scale = (float*)(ws + w.m.scale);
-  float* planes = (float*)(ws + w.m.planes);
-  double* partial = (double*)(ws + w.partial);
+  if ((rc = setup_pass(MODE_NORMAL, desc, batch, params, workspace, ws_bytes, st, &pc))) return rc;
+  if ((rc = launch_pass(MODE_NORMAL, &pc, st))) return rc;
   const int G = batch->n_gal;
-  FusedArgs A;
-  if ((rc = fill_args(A, pl, batch, sm, planes, w.m.Wp))) return rc;
-  A.cconst = cconst;
-  A.scale = scale;
-  A.partial = partial;
-  A.err = (int*)(ws + w.m.err);
-  GM_CUDA(cudaMemsetAsync(A.err, 0, sizeof(int), st));
-  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, batch->H, params, 0, cconst, scale);
-  GM_LAUNCHED("k_setup");
-  const ProfileArgs PA = profile_args(pl, batch, cconst, scale, planes, w.m.Wp);
-  const int pblocks = G * ((batch->H * w.m.Wp + 255) / 256);
-  k_profile<MODE_NORMAL><<<std::min(pblocks, 8 * di.sms), 256, 0, st>>>(PA);
-  GM_LAUNCHED("k_profile");
-  const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
-  kf<<<grid, sm.threads, sm.total, st>>>(A);
-  GM_LAUNCHED("k_fused(normal)");
-  k_chi2_grad_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, A.n_tiles, partial, chi2, grad, jtj);
+  k_chi2_grad_finish<<<(G + 127) / 128, 128, 0, st>>>(pc.pl.dd, G, pc.A.geo, pc.A.partial, chi2, grad, jtj);
   GM_LAUNCHED("k_chi2_grad_finish");
   return GM_OK;
 }
 
 size_t gm_fit_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
-  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
-  return ws_fit(desc, batch, count_free(desc)).total;
+  if (!desc || !batch || check_desc(desc)) return 0;
+  GeomPlan gp;
+  if (plan_geom(batch, pairs_for(desc, MODE_NORMAL), false, &gp)) return 0;
+  return ws_fit(desc, gp, count_free(desc)).total;
 }
 
 int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* params_inout, const gm_fit_opts* opts,
@@ -660,8 +832,9 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   int rc = check_batch(batch, true);
   if (rc) return rc;
   Plan pl;
-  rc = make_plan(desc, MODE_NORMAL, false, &pl);
-  if (rc) return rc;
+  if ((rc = make_plan(desc, MODE_NORMAL, false, &pl))) return rc;
+  GeomPlan gp;
+  if ((rc = plan_geom(batch, pl.ncp, true, &gp))) return rc;
   if (batch->n_gal == 0) return GM_OK;
   if (!params_inout || !chi2_out || !dof_out || !iters_out || !status_out)
     return fail(GM_E_INVAL, "an output pointer is NULL");
@@ -669,20 +842,21 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   if (O.max_iter < 1) return fail(GM_E_INVAL, "max_iter=%d < 1", O.max_iter);
   if (!(O.lambda_up > 1.0) || !(O.lambda_down > 0.0) || !(O.lambda_down < 1.0) || !(O.lambda0 > 0.0))
     return fail(GM_E_INVAL, "lambda controls must satisfy lambda0 > 0, up > 1, 0 < down < 1");
-  const WsFit w = ws_fit(desc, batch, pl.dd.P);
+  const WsFit w = ws_fit(desc, gp, pl.dd.P);
   if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
   DevInfo di;
   if ((rc = dev_info(&di))) return rc;
   Smem sm;
-  if ((rc = smem_plan(pl, batch->K, desc->n_comp, desc->n_slots, di.smem_optin, &sm))) return rc;
+  if ((rc = smem_plan(pl, gp.K, desc->n_comp, desc->n_slots, di.smem_optin, &sm))) return rc;
   FusedKernel kf;
   if ((rc = prepare_fused(MODE_NORMAL, pl, sm, &kf))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
-  float* cconst = (float*)(ws + w.c.m.cconst);
-  float* scale = (float*)(ws + w.c.m.scale);
-  float* planes = (float*)(ws + w.c.m.planes);
-  int* err = (int*)(ws + w.c.m.err);
+  float* cconst = (float*)(ws + w.c.cconst);
+  float* scale = (float*)(ws + w.c.scale);
+  float* planes = (float*)(ws + w.c.planes);
+  int* err = (int*)(ws + w.c.err);
+  int* queue = (int*)(ws + w.c.queue);
   double* partial = (double*)(ws + w.c.partial);
   LMState S;
   S.p_b = (double*)(ws + w.p_b);
@@ -699,6 +873,10 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   S.list[1] = (int*)(ws + w.list1);
   S.count[0] = (int*)(ws + w.counts);
   S.count[1] = S.count[0] + 1;
+  S.items[0] = (int2*)(ws + w.items0);
+  S.items[1] = (int2*)(ws + w.items1);
+  S.icount[0] = (int*)(ws + w.icounts);
+  S.icount[1] = S.icount[0] + 1;
   S.evals = (unsigned long long*)(ws + w.evals);
   const int G = batch->n_gal;
   const auto t_start = std::chrono::steady_clock::now();
@@ -708,40 +886,51 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
     GM_CUDA(cudaEventCreate(&e));
     g_events.push_back(e);
   }
-  GM_CUDA(cudaMemsetAsync(S.evals, 0, 3 * sizeof(unsigned long long), st));
-  GM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-
-  k_validate<<<std::min(G, 4 * di.sms), 256, 0, st>>>(G, batch->H, batch->W, batch->image, batch->sigma,
-                                                      batch->mask, S.nused, S.bad);
-  GM_LAUNCHED("k_validate");
-  GM_CUDA(cudaMemsetAsync(S.count[0], 0, 2 * sizeof(int), st));
-  k_lm_init<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, G, batch->H, params_inout, cconst, scale);
-  GM_LAUNCHED("k_lm_init");
 
   FusedArgs A;
-  if ((rc = fill_args(A, pl, batch, sm, planes, w.c.m.Wp))) return rc;
+  fill_args(A, pl, sm);
+  if ((rc = put_tables(gp, w.c, ws, di, st, &A))) return rc;
+  A.queue = queue;
+  A.image = batch->image;
+  A.sigma = batch->sigma;
+  A.mask = batch->mask;
+  A.psf = batch->psf;
   A.cconst = cconst;
   A.scale = scale;
   A.partial = partial;
   A.err = err;
-  ProfileArgs PA = profile_args(pl, batch, cconst, scale, planes, w.c.m.Wp);
-  const int grid = std::max(1, std::min(G * A.n_tiles, di.sms));
-  const int pgrid = std::max(1, std::min(G * ((batch->H * w.c.m.Wp + 255) / 256), 8 * di.sms));
+  const int* order = (const int*)(ws + w.c.order);
+
+  GM_CUDA(cudaMemsetAsync(S.evals, 0, 3 * sizeof(unsigned long long), st));
+  GM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  GM_CUDA(cudaMemsetAsync(S.count[0], 0, 2 * sizeof(int), st));
+  GM_CUDA(cudaMemsetAsync(S.icount[0], 0, 2 * sizeof(int), st));
+  k_validate<<<std::min(G, 4 * di.sms), 256, 0, st>>>(G, A.geo, batch->image, batch->sigma, batch->mask, S.nused,
+                                                      S.bad);
+  GM_LAUNCHED("k_validate");
+  k_lm_init<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, G, A.geo, order, params_inout, cconst, scale);
+  GM_LAUNCHED("k_lm_init");
+
+  PlaneArgs PA = plane_args(pl, A.geo, cconst, scale, planes);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(gp.n_items, di.sms));
+  const int pgrid = (int)std::max<long long>(1, std::min<long long>(gp.n_items, 8LL * di.sms));
   const int poll = 4;
   int passes = 0;
   for (int k = 0; k < O.max_iter; ++k) {
     const int cur = k & 1;
-    A.list = PA.list = S.list[cur];
-    A.count = PA.count = S.count[cur];
+    A.items = PA.items = S.items[cur];
+    A.n_items_dev = PA.n_items_dev = S.icount[cur];
+    PA.zero[0] = queue;
+    PA.zero[1] = S.count[cur ^ 1];
+    PA.zero[2] = S.icount[cur ^ 1];
     GM_CUDA(cudaEventRecord(g_events[4 * k], st));
-    k_profile<MODE_NORMAL><<<pgrid, 256, 0, st>>>(PA);
-    GM_LAUNCHED("k_profile");
+    k_planes<MODE_NORMAL><<<pgrid, 256, 0, st>>>(PA);
+    GM_LAUNCHED("k_planes");
     GM_CUDA(cudaEventRecord(g_events[4 * k + 1], st));
     kf<<<grid, sm.threads, sm.total, st>>>(A);
     GM_LAUNCHED("k_fused(normal)");
     GM_CUDA(cudaEventRecord(g_events[4 * k + 2], st));
-    GM_CUDA(cudaMemsetAsync(S.count[cur ^ 1], 0, sizeof(int), st));
-    k_lm_step<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, cur, batch->H, A.n_tiles, partial, cconst, scale);
+    k_lm_step<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, cur, A.geo, partial, cconst, scale);
     GM_LAUNCHED("k_lm_step");
     GM_CUDA(cudaEventRecord(g_events[4 * k + 3], st));
     ++passes;
@@ -833,27 +1022,12 @@ WsAdj ws_adj(const gm_model_desc* d, const gm_batch* b, int P) {
   return w;
 }
 
-int encode_pairs(CUtensorMap* map, float* planes, int Wp, int H, int n_planes, int rw, int K) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc;
-  int rc = encode_fn(&enc);
-  if (rc) return rc;
-  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Wp), (cuuint64_t)H, (cuuint64_t)n_planes};
-  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Wp) * 4, (cuuint64_t)(2 * Wp) * 4 * H};
-  const cuuint32_t box[3] = {(cuuint32_t)(2 * rw), (cuuint32_t)(kTile + K - 1), 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, planes, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) return fail(GM_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-  return GM_OK;
-}
-
 }  // namespace
 
 extern "C" {
 
 size_t gm_grad_adjoint_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
-  if (!desc || !batch || check_desc(desc) || check_sizes(batch)) return 0;
+  if (!desc || !batch || check_desc(desc) || check_sizes(batch) || batch->geom) return 0;
   return ws_adj(desc, batch, count_free(desc)).total;
 }
 
@@ -861,6 +1035,7 @@ int gm_grad_adjoint(const gm_model_desc* desc, const gm_batch* batch, const doub
                     double* grad, void* workspace, size_t ws_bytes, void* stream) {
   int rc = check_batch(batch, true);
   if (rc) return rc;
+  if (batch->geom) return fail(GM_E_UNSUPPORTED, "gm_grad_adjoint takes equal stamps only (batch.geom must be NULL)");
   Plan pl;
   rc = make_plan(desc, MODE_NORMAL, false, &pl);
   if (rc) return rc;
@@ -936,18 +1111,18 @@ int gm_grad_adjoint(const gm_model_desc* desc, const gm_batch* batch, const doub
 
   cudaStream_t st = (cudaStream_t)stream;
   GM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, H, params, 0, cconst, scale);
+  k_setup<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, G, nullptr, H, params, 0, cconst, scale);
   GM_LAUNCHED("k_setup");
   ProfileArgs PA = profile_args(pl, batch, cconst, scale, mplanes, w.Wp);
   const int pgrid = std::max(1, std::min(n_pairs * ((H * w.Wp + 255) / 256), 8 * di.sms));
   k_profile_pairs<<<pgrid, 256, 0, st>>>(PA);
   GM_LAUNCHED("k_profile_pairs");
-  if ((rc = encode_pairs(&A.tmap, mplanes, w.Wp, H, n_pairs, rw, K))) return rc;
+  if ((rc = encode_planes(&A.tmap, mplanes, H, batch->W, K, n_pairs))) return rc;
   A.u_planes = uplanes;
   A.partial = part_r;
   kr<<<grid, 128, smem, st>>>(A);
   GM_LAUNCHED("k_adjoint(resid)");
-  if ((rc = encode_pairs(&A.tmap, uplanes, w.Wp, H, n_pairs, rw, K))) return rc;
+  if ((rc = encode_planes(&A.tmap, uplanes, H, batch->W, K, n_pairs))) return rc;
   A.partial = part_a;
   ka<<<grid, 128, smem, st>>>(A);
   GM_LAUNCHED("k_adjoint(grad)");
@@ -989,7 +1164,8 @@ extern "C" int gm_chi2_grad_noalloc(const gm_model_desc* desc, const gm_batch* b
   int rc = check_batch(batch, true);
   if (rc) return rc;
   if ((rc = check_desc(desc))) return rc;
-  const size_t need = ws_chi2(desc, batch, count_free(desc)).total;
+  const size_t need = gm_chi2_grad_workspace_bytes(desc, batch);
+  if (need == 0) return fail(GM_E_INVAL, "gm_chi2_grad_noalloc: %s", g_err);
   if (need > (size_t)GM_NOALLOC_SCRATCH_BYTES)
     return fail(GM_E_NOMEM,
                 "gm_chi2_grad_noalloc: this batch needs %zu bytes of scratch but the built-in array holds %u; "

@@ -5,6 +5,7 @@
 // arxiv 2404.07780.
 #pragma once
 
+#include "gm_geom.cuh"
 #include "gm_profiles.cuh"
 
 namespace gm {
@@ -58,6 +59,8 @@ struct LMState {
   int* bad;        // [G] bad sigma / image on a used pixel
   int* list[2];    // active galaxies, double-buffered by iteration parity
   int* count[2];
+  int2* items[2];  // their (galaxy, tile) items, same parity
+  int* icount[2];
   unsigned long long* evals;  // [3]: galaxies evaluated over the passes, converged, iterations
 };
 
@@ -72,23 +75,24 @@ __device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, in
 }
 
 // Constants for every galaxy from caller parameters (gm_model, gm_chi2_grad).
-__global__ void k_setup(const __grid_constant__ DescDev D, int G, int H, const double* __restrict__ params,
-                        int use_log, float* cconst, float* scale) {
+// Stamp heights from geo, or H for every galaxy when geo is nullptr.
+__global__ void k_setup(const __grid_constant__ DescDev D, int G, const GalGeom* __restrict__ geo, int H,
+                        const double* __restrict__ params, int use_log, float* cconst, float* scale) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
-  setup_galaxy(D, params + (size_t)g * D.n_slots, H, use_log, cconst + (size_t)g * D.n_comp * kCC,
+  setup_galaxy(D, params + (size_t)g * D.n_slots, geo ? geo[g].H : H, use_log, cconst + (size_t)g * D.n_comp * kCC,
                scale + (size_t)g * D.n_slots);
 }
 
 // Used-pixel count and bad-input flag per galaxy (one block per galaxy, strided).
-__global__ void k_validate(int G, int H, int W, const float* __restrict__ image, const float* __restrict__ sigma,
-                           const uint8_t* __restrict__ mask, int* nused, int* bad) {
+__global__ void k_validate(int G, const GalGeom* __restrict__ geo, const float* __restrict__ image,
+                           const float* __restrict__ sigma, const uint8_t* __restrict__ mask, int* nused, int* bad) {
   __shared__ int s_n[32], s_b[32];
-  const size_t HW = (size_t)H * W;
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    const size_t HW = (size_t)geo[g].H * geo[g].W, base = (size_t)geo[g].pix;
     int n = 0, b = 0;
     for (size_t t = threadIdx.x; t < HW; t += blockDim.x) {
-      const size_t gp = (size_t)g * HW + t;
+      const size_t gp = base + t;
       if (mask && mask[gp]) continue;
       ++n;
       const float s = sigma[gp], d = image[gp];
@@ -124,12 +128,24 @@ __device__ inline void clamp_slots(const DescDev& D, double* p) {
   for (int s = 0; s < D.n_slots; ++s) p[s] = fmin(fmax(p[s], D.lo[s]), D.hi[s]);
 }
 
+// Queue galaxy g and its tiles for the pass of list `l`.
+__device__ inline void queue_galaxy(const LMState& S, int l, int g, const GalGeom& geo) {
+  const int pos = atomicAdd(S.count[l], 1);
+  S.list[l][pos] = g;
+  const int nt = geo.n_tiles;
+  const int ipos = atomicAdd(S.icount[l], nt);
+  for (int t = 0; t < nt; ++t) S.items[l][ipos + t] = make_int2(g, t);
+}
+
 // Start of a fit: clamp the start point, set status from the validation and
-// queue the galaxies that can be fitted.
-__global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O, int G, int H,
+// queue the galaxies that can be fitted, in the processing order `order`
+// (most expensive first).
+__global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O, int G,
+                          const GalGeom* __restrict__ geo, const int* __restrict__ order,
                           const double* __restrict__ params0, float* cconst, float* scale) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= G) return;
+  const int g = order[pos];
   const int NS = D.n_slots, P = D.P;
   double* pb = S.p_b + (size_t)g * NS;
   double* pt = S.p_t + (size_t)g * NS;
@@ -144,9 +160,8 @@ __global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O
   else if (S.nused[g] - P <= 0) st = ST_NO_DOF;
   S.status[g] = st;
   if (st == ST_RUNNING) {
-    setup_galaxy(D, pt, H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
-    const int pos = atomicAdd(S.count[0], 1);
-    S.list[0][pos] = g;
+    setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
+    queue_galaxy(S, 0, g, geo[g]);
   }
 }
 
@@ -217,8 +232,9 @@ __device__ inline double gn_decrement(const double* Ap, const double* g, int P) 
 // accepted step lowers chi^2 by less than tol relative, any evaluated step
 // is below xtol, or the Gauss-Newton decrement at the best point is at most
 // gtol chi^2; STALLED / SINGULAR past lambda_max; MAX_ITER at max_iter.
-__global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O, int cur, int H,
-                          int n_tiles, const double* __restrict__ partial, float* cconst, float* scale) {
+__global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O, int cur,
+                          const GalGeom* __restrict__ geo, const double* __restrict__ partial, float* cconst,
+                          float* scale) {
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_cur = *S.count[cur];
   if (gi == 0) atomicAdd(S.evals, (unsigned long long)n_cur);
@@ -233,7 +249,8 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
   // sums of the tile partials in tile order (deterministic)
   double acc[kMaxAcc];
   for (int e = 0; e < NA; ++e) acc[e] = 0.0;
-  const double* pp = partial + (size_t)g * n_tiles * NA;
+  const int n_tiles = geo[g].n_tiles;
+  const double* pp = partial + (size_t)geo[g].tile0 * NA;
   for (int t = 0; t < n_tiles; ++t)
     for (int e = 0; e < NA; ++e) acc[e] += pp[t * NA + e];
   const double chi2_t = acc[0];
@@ -307,10 +324,8 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
         pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
       }
       clamp_slots(D, pt);
-      setup_galaxy(D, pt, H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
-      const int nxt = cur ^ 1;
-      const int pos = atomicAdd(S.count[nxt], 1);
-      S.list[nxt][pos] = g;
+      setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
+      queue_galaxy(S, cur ^ 1, g, geo[g]);
     }
   }
   S.lam[g] = lam;
@@ -425,14 +440,15 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
 }
 
 // gm_chi2_grad outputs from the tile partials (physical coordinates).
-__global__ void k_chi2_grad_finish(const __grid_constant__ DescDev D, int G, int n_tiles,
+__global__ void k_chi2_grad_finish(const __grid_constant__ DescDev D, int G, const GalGeom* __restrict__ geo,
                                    const double* __restrict__ partial, double* chi2, double* grad, double* jtj) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
   const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
   double acc[kMaxAcc];
   for (int e = 0; e < NA; ++e) acc[e] = 0.0;
-  const double* pp = partial + (size_t)g * n_tiles * NA;
+  const int n_tiles = geo[g].n_tiles;
+  const double* pp = partial + (size_t)geo[g].tile0 * NA;
   for (int t = 0; t < n_tiles; ++t)
     for (int e = 0; e < NA; ++e) acc[e] += pp[t * NA + e];
   chi2[g] = acc[0];

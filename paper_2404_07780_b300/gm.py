@@ -63,6 +63,7 @@ class gm_batch(ctypes.Structure):
         ("sigma", ctypes.c_void_p),
         ("mask", ctypes.c_void_p),
         ("psf", ctypes.c_void_p),
+        ("geom", ctypes.c_void_p),
     ]
 
 
@@ -186,22 +187,51 @@ def _cuda_tensor(t, dtype, name):
     return t.contiguous()
 
 
-def make_batch(image, sigma, mask, psf):
-    """gm_batch over CUDA tensors image/sigma [G,H,W] f32, mask [G,H,W] u8 or None, psf [G,K,K] f32.
+def geom_array(geom) -> np.ndarray:
+    """Per-galaxy (h, w, k) of an uneven batch as a contiguous int32 [G, 3] array."""
+    g = np.ascontiguousarray(np.asarray(geom, dtype=np.int32).reshape(-1, 3))
+    return g
 
-    Returns (struct, keep) where keep holds the contiguous tensors alive."""
+
+def _geom_ptr(g):
+    return None if g is None else ctypes.c_void_p(g.ctypes.data)
+
+
+def packed_sizes(geom: np.ndarray):
+    """(pixels, PSF elements) of an uneven batch packed back to back."""
+    g = geom.astype(np.int64)
+    return int((g[:, 0] * g[:, 1]).sum()), int((g[:, 2] ** 2).sum())
+
+
+def make_batch(image, sigma, mask, psf, geom=None):
+    """gm_batch over CUDA tensors.
+
+    Equal stamps (geom None): image/sigma [G,H,W] f32, mask [G,H,W] u8 or None, psf [G,K,K] f32.
+    Uneven stamps: geom [G,3] = (h, w, k) per galaxy (host), image/sigma/mask packed back to back
+    (sum h*w elements), psf packed (sum k*k elements).
+
+    Returns (struct, keep) where keep holds the contiguous tensors (and geom) alive."""
     import torch
     psf = _cuda_tensor(psf, torch.float32, "psf")
-    G, K = psf.shape[0], psf.shape[-1]
     image = _cuda_tensor(image, torch.float32, "image")
     sigma = _cuda_tensor(sigma, torch.float32, "sigma")
     mask = _cuda_tensor(mask, torch.uint8, "mask")
-    ref = image if image is not None else None
-    if ref is None:
-        raise GMError("image is required to size the batch (use model_batch for gm_model)")
-    H, W = ref.shape[-2:]
-    b = gm_batch(G, H, W, K, _ptr(image), _ptr(sigma), _ptr(mask), _ptr(psf))
-    return b, (image, sigma, mask, psf)
+    if image is None:
+        raise GMError("image is required to size the batch (use gm_model for the forward model alone)")
+    if geom is None:
+        G, K = psf.shape[0], psf.shape[-1]
+        H, W = image.shape[-2:]
+        b = gm_batch(G, H, W, K, _ptr(image), _ptr(sigma), _ptr(mask), _ptr(psf), None)
+        return b, (image, sigma, mask, psf)
+    g = geom_array(geom)
+    npix, npsf = packed_sizes(g)
+    for name, t in (("image", image), ("sigma", sigma), ("mask", mask)):
+        if t is not None and t.numel() != npix:
+            raise GMError(f"{name} holds {t.numel()} elements; the geometry packs {npix}")
+    if psf.numel() != npsf:
+        raise GMError(f"psf holds {psf.numel()} elements; the geometry packs {npsf}")
+    b = gm_batch(len(g), 0, 0, 0, _ptr(image), _ptr(sigma), _ptr(mask), _ptr(psf), _geom_ptr(g))
+    return b, (image, sigma, mask, psf, g)
 
 
 def _stream():
@@ -209,31 +239,48 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def gm_model(spec_or_desc, params, psf, H: int, W: int, components: bool = False):
-    """Forward model of every galaxy: returns model [G,H,W] (and [G,n_comp,H,W] if components)."""
+def gm_model(spec_or_desc, params, psf, H: int = 0, W: int = 0, components: bool = False, geom=None):
+    """Forward model of every galaxy.
+
+    Equal stamps: returns model [G,H,W] (and [G,n_comp,H,W] if components).  Uneven stamps
+    (geom [G,3] = (h, w, k), psf packed): returns the packed model [sum h*w] (and the packed
+    components [sum n_comp*h*w], galaxy by galaxy, component by component)."""
     import torch
     lib = load()
     d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
     psf = _cuda_tensor(psf, torch.float32, "psf")
     params = _cuda_tensor(params, torch.float64, "params")
-    G, K = psf.shape[0], psf.shape[-1]
-    b = gm_batch(G, H, W, K, None, None, None, _ptr(psf))
     dev = psf.device
-    model = torch.empty((G, H, W), dtype=torch.float32, device=dev)
-    comp = torch.empty((G, d.n_comp, H, W), dtype=torch.float32, device=dev) if components else None
+    if geom is None:
+        G, K = psf.shape[0], psf.shape[-1]
+        b = gm_batch(G, H, W, K, None, None, None, _ptr(psf), None)
+        shape, cshape = (G, H, W), (G, d.n_comp, H, W)
+        g = None
+    else:
+        g = geom_array(geom)
+        npix, npsf = packed_sizes(g)
+        if psf.numel() != npsf:
+            raise GMError(f"psf holds {psf.numel()} elements; the geometry packs {npsf}")
+        b = gm_batch(len(g), 0, 0, 0, None, None, None, _ptr(psf), _geom_ptr(g))
+        shape, cshape = (npix,), (d.n_comp * npix,)
+    model = torch.empty(shape, dtype=torch.float32, device=dev)
+    comp = torch.empty(cshape, dtype=torch.float32, device=dev) if components else None
     nbytes = lib.gm_model_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    if nbytes == 0 and b.n_gal > 0:
+        raise GMError(f"gm_model_workspace_bytes: {lib.gm_last_error().decode()}")
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
     _check(lib.gm_model(ctypes.byref(d), ctypes.byref(b), _ptr(params), _ptr(model), _ptr(comp), _ptr(ws), nbytes,
                         _stream()), "gm_model")
     return (model, comp) if components else model
 
 
-def gm_chi2_grad(spec_or_desc, params, image, sigma, mask, psf, want_grad: bool = True, want_jtj: bool = False):
-    """chi^2 [G], d chi^2/dp [G,S] (physical units) and J^T W J [G,S,S] (or None)."""
+def gm_chi2_grad(spec_or_desc, params, image, sigma, mask, psf, want_grad: bool = True, want_jtj: bool = False,
+                 geom=None):
+    """chi^2 [G], d chi^2/dp [G,S] (physical units) and J^T W J [G,S,S] (or None); geom as make_batch."""
     import torch
     lib = load()
     d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
-    b, keep = make_batch(image, sigma, mask, psf)
+    b, keep = make_batch(image, sigma, mask, psf, geom)
     params = _cuda_tensor(params, torch.float64, "params")
     G, S = b.n_gal, d.n_slots
     dev = keep[0].device
@@ -241,6 +288,8 @@ def gm_chi2_grad(spec_or_desc, params, image, sigma, mask, psf, want_grad: bool 
     grad = torch.empty((G, S), dtype=torch.float64, device=dev) if want_grad else None
     jtj = torch.empty((G, S, S), dtype=torch.float64, device=dev) if want_jtj else None
     nbytes = lib.gm_chi2_grad_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    if nbytes == 0 and G > 0:
+        raise GMError(f"gm_chi2_grad_workspace_bytes: {lib.gm_last_error().decode()}")
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
     _check(lib.gm_chi2_grad(ctypes.byref(d), ctypes.byref(b), _ptr(params), _ptr(chi2), _ptr(grad), _ptr(jtj),
                             _ptr(ws), nbytes, _stream()), "gm_chi2_grad")
@@ -303,15 +352,24 @@ def _make_chi2_function():
 
 
 class Fitter:
-    """Holds the workspace and output buffers of gm_fit_batch for one batch shape."""
+    """Holds the workspace and output buffers of gm_fit_batch for one batch geometry
+    (G equal H x W stamps with K x K PSFs, or an uneven batch given by geom [G,3])."""
 
-    def __init__(self, spec_or_desc, G: int, H: int, W: int, K: int, device="cuda"):
+    def __init__(self, spec_or_desc, G: int, H: int = 0, W: int = 0, K: int = 0, device="cuda", geom=None):
         import torch
         self.lib = load()
         self.d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
-        self.shape = (G, H, W, K)
-        b = gm_batch(G, H, W, K, None, None, None, None)
+        self.geom = None if geom is None else geom_array(geom)
+        if self.geom is not None:
+            G = len(self.geom)
+            b = gm_batch(G, 0, 0, 0, None, None, None, None, _geom_ptr(self.geom))
+            self.shape = ("uneven", G)
+        else:
+            b = gm_batch(G, H, W, K, None, None, None, None, None)
+            self.shape = (G, H, W, K)
         self.ws_bytes = self.lib.gm_fit_workspace_bytes(ctypes.byref(self.d), ctypes.byref(b))
+        if self.ws_bytes == 0 and G > 0:
+            raise GMError(f"gm_fit_workspace_bytes: {self.lib.gm_last_error().decode()}")
         S = self.d.n_slots
         self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=device)
         self.chi2 = torch.empty(G, dtype=torch.float64, device=device)
@@ -323,9 +381,10 @@ class Fitter:
     def fit(self, params, image, sigma, mask, psf, opts: FitOptions | None = None):
         """Fit in place: params [G,S] f64 CUDA is overwritten with the best fit."""
         import torch
-        b, keep = make_batch(image, sigma, mask, psf)
-        if (b.n_gal, b.H, b.W, b.K) != self.shape:
-            raise GMError(f"batch shape {(b.n_gal, b.H, b.W, b.K)} != fitter shape {self.shape}")
+        b, keep = make_batch(image, sigma, mask, psf, self.geom)
+        shape = ("uneven", b.n_gal) if self.geom is not None else (b.n_gal, b.H, b.W, b.K)
+        if shape != self.shape:
+            raise GMError(f"batch shape {shape} != fitter shape {self.shape}")
         if not (params.is_cuda and params.dtype == torch.float64 and params.is_contiguous()):
             raise GMError("params must be a contiguous float64 CUDA tensor")
         o = (opts or FitOptions()).to_c()
@@ -344,11 +403,15 @@ def gm_fit_last_stats() -> dict:
     return {name: getattr(st, name) for name, _ in gm_fit_stats._fields_}
 
 
-def gm_fit_batch(spec_or_desc, params0, image, sigma, mask, psf, opts: FitOptions | None = None):
-    """LM fit of every galaxy; returns a dict of CUDA tensors (params is a fitted copy of params0)."""
-    G, H, W = image.shape
-    K = psf.shape[-1]
-    f = Fitter(spec_or_desc, G, H, W, K, device=image.device)
+def gm_fit_batch(spec_or_desc, params0, image, sigma, mask, psf, opts: FitOptions | None = None, geom=None):
+    """LM fit of every galaxy; returns a dict of CUDA tensors (params is a fitted copy of params0).
+    geom as make_batch."""
+    if geom is None:
+        G, H, W = image.shape
+        K = psf.shape[-1]
+        f = Fitter(spec_or_desc, G, H, W, K, device=image.device)
+    else:
+        f = Fitter(spec_or_desc, len(geom_array(geom)), device=image.device, geom=geom)
     params = params0.clone().contiguous()
     out = f.fit(params, image, sigma, mask, psf, opts)
     return {k: v.clone() if k != "params" else v for k, v in out.items()}

@@ -313,6 +313,102 @@ def draw_bulge_bar_nucleus(seed: int = 3000, G: int = 64, H: int = 96, W: int = 
     return Batch(spec, H, W, K, truth, init, "moffat", psf_params("moffat", g.uniform(1.2, 1.8, G), K), None, z)
 
 
+@dataclass
+class RaggedBatch:
+    """A batch whose stamps and PSFs differ in size from galaxy to galaxy.
+
+    geom[g] = (h, w, k): stamp rows and columns and PSF side of galaxy g.
+    Per-pixel arrays are packed back to back in galaxy order (the layout of
+    gm_batch.geom); `galaxy(g)` views one galaxy as a one-galaxy Batch."""
+    spec: ModelSpec            # the fitted model (position bounds sized for the largest stamp)
+    geom: np.ndarray           # [G, 3] int32
+    truth: np.ndarray          # [G, spec.n_slots]
+    init: np.ndarray           # [G, spec.n_slots]
+    psf_kind: str
+    psf_par: np.ndarray        # [G, n] PSF profile parameters (centred on each PSF's own grid)
+    mask: np.ndarray | None    # packed uint8 [sum h*w]
+    z: np.ndarray              # packed standard normal draws [sum h*w]
+    sky_var: float = 4.0
+    gain: float = 4.0
+
+    @property
+    def G(self) -> int:
+        return self.truth.shape[0]
+
+    def pix_offsets(self) -> np.ndarray:
+        """[G+1] start of each stamp in the packed arrays."""
+        hw = self.geom[:, 0].astype(np.int64) * self.geom[:, 1]
+        return np.concatenate([[0], np.cumsum(hw)])
+
+    def psf_offsets(self) -> np.ndarray:
+        """[G+1] start of each PSF in the packed PSF array."""
+        return np.concatenate([[0], np.cumsum(self.geom[:, 2].astype(np.int64) ** 2)])
+
+    def galaxy(self, g: int) -> Batch:
+        h, w, k = (int(v) for v in self.geom[g])
+        o = self.pix_offsets()
+        sl = slice(o[g], o[g + 1])
+        mask = None if self.mask is None else self.mask[sl].reshape(1, h, w)
+        return Batch(self.spec, h, w, k, self.truth[g:g + 1], self.init[g:g + 1], self.psf_kind,
+                     self.psf_par[g:g + 1], mask, self.z[sl].reshape(1, h, w).astype(np.float64),
+                     None, self.sky_var, self.gain)
+
+
+def draw_uneven_bulge_disk(seed: int = 2000, G: int = 32768, sides=(48, 64, 96, 128, 192, 256),
+                           ks=tuple(range(25, 52, 2))) -> RaggedBatch:
+    """Uneven bulge + disk batch: square stamps with side uniform over `sides`, Moffat PSF
+    (beta 3, FWHM 1.2-1.8 px) with odd side uniform over `ks`; Sersic bulge (n 1-6) + Sersic
+    disk with n = 1 (Re_d = 1.5-4 x Re_b, own q and PA) + sky, common centre within +-2 px of
+    the stamp centre.  Radii scale with the stamp side (bulge Re 1.5-8 px at side 96)."""
+    g = rng(seed)
+    side = g.choice(np.asarray(sides), G)
+    k = g.choice(np.asarray(ks), G)
+    geom = np.stack([side, side, k], 1).astype(np.int32)
+    smax = int(max(sides))
+    spec = bulge_disk_sky(smax, smax)
+    f = side / 96.0
+    reb = g.uniform(1.5, 8, G) * f
+    truth = np.stack([
+        side / 2 + g.uniform(-2, 2, G), side / 2 + g.uniform(-2, 2, G),
+        g.uniform(0.3, 1.0, G), g.uniform(0, math.pi, G), 10 ** g.uniform(0.5, 3, G), reb, g.uniform(1, 6, G),
+        g.uniform(0.2, 1.0, G), g.uniform(0, math.pi, G), 10 ** g.uniform(0, 2, G), reb * g.uniform(1.5, 4, G),
+        np.ones(G), g.uniform(0, 5, G)], 1)
+    init = np.stack([side / 2, side / 2, np.full(G, 0.65), np.full(G, math.pi / 2), np.full(G, 10 ** 1.75),
+                     4.0 * f, np.full(G, math.sqrt(6.0)), np.full(G, 0.6), np.full(G, math.pi / 2),
+                     np.full(G, 10.0), 11.0 * f, np.ones(G), np.full(G, 2.5)], 1)
+    fwhm = g.uniform(1.2, 1.8, G)
+    c = k / 2.0  # each PSF centred on pixel (c, c) of its own k x k grid, as psf_params
+    psf_par = np.stack([c, c, np.ones(G), np.zeros(G), np.ones(G), fwhm, np.full(G, 3.0)], 1)
+    npix = int((side.astype(np.int64) ** 2).sum())
+    z = g.standard_normal(npix, dtype=np.float32)
+    return RaggedBatch(spec, geom, truth, init, "moffat", psf_par, None, z)
+
+
+def draw_uneven_sersic(seed: int, geom, mask_frac: float = 0.0, ie=(1.0, 100.0)) -> RaggedBatch:
+    """Single Sersic + sky on stamps of the given (h, w, k) each, Moffat PSF (beta 3, FWHM
+    1.2-1.8 px): centre within +-1 px of the stamp centre, Ie log-uniform over `ie`, Re uniform
+    1.5-0.3 min(h, w) (at least 1.5), n log-uniform 0.5-4, q uniform 0.3-1, PA uniform 0-pi,
+    sky uniform 0-5; with mask_frac > 0 each pixel is masked with that probability."""
+    g = rng(seed)
+    geom = np.asarray(geom, np.int32).reshape(-1, 3)
+    G = len(geom)
+    h, w, k = (geom[:, i].astype(np.float64) for i in range(3))
+    hmax, wmax = int(geom[:, 0].max()), int(geom[:, 1].max())
+    spec = single_sersic_sky(hmax, wmax)
+    re_hi = np.maximum(0.3 * np.minimum(h, w), 1.5)
+    truth = np.stack([w / 2 + g.uniform(-1, 1, G), h / 2 + g.uniform(-1, 1, G), g.uniform(0.3, 1.0, G),
+                      g.uniform(0, math.pi, G), _logu(g, ie[0], ie[1], G), 1.5 + g.uniform(0, 1, G) * (re_hi - 1.5),
+                      _logu(g, 0.5, 4, G), g.uniform(0, 5, G)], 1)
+    init = np.stack([w / 2, h / 2, np.full(G, 0.65), np.full(G, math.pi / 2), np.full(G, 10.0),
+                     0.5 * (1.5 + re_hi), np.full(G, math.sqrt(2.0)), np.full(G, 2.5)], 1)
+    psf_par = np.stack([k / 2, k / 2, np.ones(G), np.zeros(G), np.ones(G), g.uniform(1.2, 1.8, G),
+                        np.full(G, 3.0)], 1)
+    npix = int((geom[:, 0].astype(np.int64) * geom[:, 1]).sum())
+    z = g.standard_normal(npix)
+    mask = (g.uniform(0, 1, npix) < mask_frac).astype(np.uint8) if mask_frac > 0 else None
+    return RaggedBatch(spec, geom, truth, init, "moffat", psf_par, mask, z)
+
+
 def noisy_image(model_true: np.ndarray, z: np.ndarray, sky_var: float = 4.0, gain: float = 4.0):
     """Data and sigma map for a truth image: sigma^2 = sky_var + max(M, 0)/gain, D = M + sigma z."""
     sigma = np.sqrt(sky_var + np.maximum(model_true, 0.0) / gain)

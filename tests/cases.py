@@ -84,3 +84,48 @@ def q_of_pa(spec, pa_slot):
 def angle_diff(a, b):
     d = np.abs(a - b) % math.pi
     return np.minimum(d, math.pi - d)
+
+
+class UnevenCase:
+    """An uneven batch (stamps and PSFs of per-galaxy size) as packed float32 arrays, plus the
+    one-galaxy Cases the oracle runs on."""
+
+    def __init__(self, spec, geom, cases):
+        self.spec = spec
+        self.geom = np.ascontiguousarray(geom, np.int32)
+        self.cases = cases
+        self.params = np.concatenate([c.params for c in cases])
+        self.init = np.concatenate([c.init for c in cases])
+        self.truth = np.concatenate([c.truth for c in cases])
+        self.psf = np.concatenate([c.psf.ravel() for c in cases])
+        self.image = np.concatenate([c.image.ravel() for c in cases])
+        self.sigma = np.concatenate([c.sigma.ravel() for c in cases])
+        masked = [c.mask is not None for c in cases]
+        self.mask = (np.concatenate([(c.mask if c.mask is not None else np.zeros(c.image.shape, np.uint8)).ravel()
+                                     for c in cases]) if any(masked) else None)
+
+    @property
+    def G(self):
+        return len(self.cases)
+
+    def offsets(self):
+        hw = self.geom[:, 0].astype(np.int64) * self.geom[:, 1]
+        return np.concatenate([[0], np.cumsum(hw)])
+
+    def split(self, packed, per_pixel=1):
+        """Per-galaxy [per_pixel, h, w] views of a packed per-pixel array."""
+        o = self.offsets() * per_pixel
+        return [np.asarray(packed[o[g]:o[g + 1]]).reshape(per_pixel, self.geom[g, 0], self.geom[g, 1])
+                for g in range(self.G)]
+
+    def torch(self, device="cuda"):
+        import torch
+        t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return dict(params=t(self.params), psf=t(self.psf), image=t(self.image), sigma=t(self.sigma),
+                    mask=t(self.mask))
+
+
+def uneven_from(rb: synth.RaggedBatch, at: str = "init") -> UnevenCase:
+    """Render every galaxy of an uneven synth batch with the oracle (one-galaxy batches)."""
+    cases = [from_batch(rb.galaxy(g), at=at) for g in range(rb.G)]
+    return UnevenCase(rb.spec, rb.geom, cases)

@@ -33,12 +33,39 @@ def test_exports_every_declared_symbol(lib):
     assert lib.gm_version() == 100
 
 
-def test_struct_layout_matches_header(lib):
-    # sizes of the C structs as laid out by the C compiler for include/gm.h
-    assert ctypes.sizeof(gm.gm_component) == 40
-    assert ctypes.sizeof(gm.gm_model_desc) == 4 + 8 * 40 + 4 + 24 + 24 + 24 * 8 * 2
-    assert ctypes.sizeof(gm.gm_batch) == 16 + 4 * 8
-    assert ctypes.sizeof(gm.gm_fit_opts) == 9 * 8
+_LAYOUT_PROBE = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "gm.h"
+#define F(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("gm_component %zu\n", sizeof(gm_component));
+  printf("gm_model_desc %zu\n", sizeof(gm_model_desc));
+  printf("gm_batch %zu\n", sizeof(gm_batch));
+  printf("gm_fit_opts %zu\n", sizeof(gm_fit_opts));
+  printf("gm_fit_stats %zu\n", sizeof(gm_fit_stats));
+  F(gm_model_desc, lo); F(gm_model_desc, hi); F(gm_batch, image); F(gm_batch, psf); F(gm_batch, geom);
+  F(gm_fit_opts, max_iter); F(gm_fit_opts, lambda0); F(gm_fit_stats, profile_ms);
+  return 0;
+}
+"""
+
+
+def test_struct_layout_matches_header(lib, tmp_path):
+    # sizes and offsets of the C structs as the C compiler lays out include/gm.h, against the binding's ctypes
+    import subprocess
+    src = tmp_path / "probe.c"
+    src.write_text(_LAYOUT_PROBE)
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                      text=True).stdout.splitlines())
+    for name in ("gm_component", "gm_model_desc", "gm_batch", "gm_fit_opts", "gm_fit_stats"):
+        assert int(out[name]) == ctypes.sizeof(getattr(gm, name)), name
+    for key, v in out.items():
+        if "." in key:
+            struct, field = key.split(".")
+            assert int(v) == getattr(getattr(gm, struct), field).offset, key
 
 
 def _desc_batch(G=4, H=64, W=64, K=15):
@@ -104,3 +131,31 @@ def test_many_parameter_models_size_their_workspace(lib):
 def test_fit_stats_before_any_fit(lib):
     st = gm.gm_fit_stats()
     assert lib.gm_fit_last_stats(ctypes.byref(st)) == -1
+
+
+def test_uneven_geometry_sizes_and_rejections(lib):
+    spec = synth.single_sersic_sky(64, 64)
+    d = gm.desc_from_spec(spec)
+
+    def batch(geom):
+        g = gm.geom_array(geom)
+        return gm.gm_batch(len(g), 0, 0, 0, None, None, None, None, ctypes.c_void_p(g.ctypes.data)), g
+
+    # 3 galaxies: 2 + 4 + 1 tiles; the chi^2 workspace holds one FP64 partial per tile
+    b, keep = batch([(40, 64, 25), (64, 64, 41), (9, 7, 1)])
+    m = lib.gm_model_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    c = lib.gm_chi2_grad_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    f = lib.gm_fit_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    assert 0 < m < c < f
+    assert c - m >= 7 * 45 * 8
+    for bad in ([(64, 64, 14)], [(0, 64, 15)], [(64, 5000, 15)], [(64, 64, 65)], [(64, 64, -1)]):
+        b, keep = batch(bad)
+        assert lib.gm_fit_workspace_bytes(ctypes.byref(d), ctypes.byref(b)) == 0
+        assert "uneven batch" in lib.gm_last_error().decode()
+    # the adjoint gradient takes equal stamps only: refused before any device work
+    b, keep = batch([(40, 64, 25)])
+    fake = ctypes.c_void_p(16)
+    b.image = b.sigma = b.psf = fake
+    assert lib.gm_grad_adjoint_workspace_bytes(ctypes.byref(d), ctypes.byref(b)) == 0
+    rc = lib.gm_grad_adjoint(ctypes.byref(d), ctypes.byref(b), fake, fake, None, fake, 1 << 20, None)
+    assert rc == -4 and "equal stamps" in lib.gm_last_error().decode()
