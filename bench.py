@@ -288,7 +288,7 @@ def run_gpu(args, world, rank, local):
     for st in stats:
         fused_ms += st["fused_ms"]
         evals += st["galaxy_evals"]
-        launches += 3 + 2 * st["passes"]  # k_validate, k_lm_init, k_lm_finish; k_fused + k_lm_step per pass
+        launches += 4 + 3 * st["passes"]  # geometry, validation, init, finish; k_planes, k_fused, k_lm_step per pass
         converged += st["converged"]
         iters.append(st["iters_sum"] / G)
         print(f"step: library wall {st['wall_ms']:.1f} ms, profile {st['profile_ms']:.1f} ms, "
@@ -373,6 +373,173 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# uneven workload: stamps and PSFs of per-galaxy size in one batch
+# ---------------------------------------------------------------------------
+
+UNEVEN_SIDES = (48, 64, 96, 128, 192, 256)
+UNEVEN_KS = tuple(range(25, 52, 2))
+
+
+def render_uneven(rb: synth.RaggedBatch, device):
+    """Packed PSFs (unit sum), data and sigma of an uneven batch, rendered by gm_model."""
+    import torch
+    from paper_2404_07780_b300 import gm
+    G = rb.G
+    k = rb.geom[:, 2].astype(np.int64)
+    psf_geom = np.stack([k, k, np.ones_like(k)], 1)
+    psfspec = synth.ModelSpec().add("moffat", "psf", 64, 64, convolve=False)
+    one = torch.ones(G, dtype=torch.float32, device=device)
+    psf = gm.gm_model(psfspec, torch.from_numpy(rb.psf_par).to(device), one, geom=psf_geom)
+    gid = torch.repeat_interleave(torch.arange(G, device=device), torch.from_numpy(k * k).to(device))
+    sums = torch.zeros(G, dtype=torch.float64, device=device).index_add_(0, gid, psf.double())
+    psf = (psf / sums[gid].float()).contiguous()
+    M = gm.gm_model(rb.spec, torch.from_numpy(rb.truth).to(device), psf, geom=rb.geom)
+    sigma = torch.sqrt(rb.sky_var + M.clamp(min=0) / rb.gain)
+    image = M + sigma * torch.from_numpy(rb.z).to(device=device, dtype=torch.float32)
+    del M
+    return image.contiguous(), sigma.contiguous(), psf
+
+
+def uneven_config(G):
+    return {"workload": f"uneven bulge+disk+sky fit, {G} stamps of side uniform over {list(UNEVEN_SIDES)} "
+                        f"(float32), per-galaxy Moffat PSF of odd side 25-51, 12 free parameters, default-start LM "
+                        f"to dchi2/chi2<{TOL:g}",
+            "galaxies": G, "sides": list(UNEVEN_SIDES), "psf_sides": [UNEVEN_KS[0], UNEVEN_KS[-1]],
+            "free_params": 12, "tol": TOL, "max_iter": MAX_ITER,
+            "l2": "inputs ~5.8 GB per batch > 126 MB L2 (no flush)"}
+
+
+def run_uneven(args, world, rank, local):
+    """Uneven workload: G bulge+disk+sky galaxies on square stamps of mixed side with mixed PSF
+    sides, one gm_fit_batch call per step (one persistent pass per LM iteration, CUDA graph)."""
+    import torch
+    from paper_2404_07780_b300 import gm
+    from paper_2404_07780_b300.build import build_lib
+
+    build_lib()
+    gm.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    G = args.galaxies
+    rb = synth.draw_uneven_bulge_disk(seed=2000 + rank, G=G, sides=UNEVEN_SIDES, ks=UNEVEN_KS)
+    image, sigma, psf = render_uneven(rb, dev)
+    p0 = torch.from_numpy(rb.init).to(dev)
+    fitter = gm.Fitter(rb.spec, G, device=dev, geom=rb.geom)
+    opts = gm.FitOptions(tol=TOL, max_iter=MAX_ITER)
+    params = torch.empty_like(p0)
+
+    def step():
+        params.copy_(p0)
+        return fitter.fit(params, image, sigma, None, psf, opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        step()
+        stats.append(gm.gm_fit_last_stats())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    for st in stats:
+        print(f"step: library wall {st['wall_ms']:.1f} ms, profile {st['profile_ms']:.1f} ms, "
+              f"fused {st['fused_ms']:.1f} ms, lm steps {st['step_ms']:.1f} ms, passes {st['passes']}",
+              file=sys.stderr)
+    converged = sum(st["converged"] for st in stats)
+    fused_ms = sum(st["fused_ms"] for st in stats)
+    launches = sum(4 + 3 * st["passes"] for st in stats)
+    ms_max = reduce_max(ms, world, dev)
+    value = reduce_sum(converged, world, dev) / (ms_max / 1e3)
+
+    # per-galaxy work: every step repeats the same deterministic fits
+    iters = fitter.iters.cpu().numpy().astype(np.float64)
+    taps = np.zeros(G)
+    for side in UNEVEN_SIDES:
+        for k in UNEVEN_KS:
+            sel = (rb.geom[:, 0] == side) & (rb.geom[:, 2] == k)
+            if sel.any():
+                taps[sel] = inbounds_taps(side, side, k)
+    nch = 1 + 11  # model + one channel per free parameter of the convolved bulge and disk
+    flops = args.steps * float((2.0 * nch * taps * iters).sum())
+    pix = args.steps * float((rb.geom[:, 0].astype(np.float64) * rb.geom[:, 1] * iters).sum())
+    achieved = flops / (fused_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_fused<NORMAL,12> (uneven items, per-class TMA maps)",
+            "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
+
+    # end to end through the public API from pinned host buffers
+    h_img = image.cpu().pin_memory()
+    h_sig = sigma.cpu().pin_memory()
+    h_psf = psf.cpu().pin_memory()
+    h_p0 = p0.cpu().pin_memory()
+    h_out_p = torch.empty_like(h_p0).pin_memory()
+    h_out_st = torch.empty(G, dtype=torch.int32).pin_memory()
+    h_out_c2 = torch.empty(G, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_img, h_sig, h_psf, h_p0))
+    d2h = sum(t.numel() * t.element_size() for t in (h_out_p, h_out_st, h_out_c2))
+    e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_conv = 0
+    for _ in range(e_steps):
+        d_img = h_img.to(dev, non_blocking=True)
+        d_sig = h_sig.to(dev, non_blocking=True)
+        d_psf = h_psf.to(dev, non_blocking=True)
+        d_p = h_p0.to(dev, non_blocking=True)
+        out = fitter.fit(d_p, d_img, d_sig, None, d_psf, opts)
+        h_out_p.copy_(out["params"], non_blocking=True)
+        h_out_st.copy_(out["status"], non_blocking=True)
+        h_out_c2.copy_(out["chi2"], non_blocking=True)
+        torch.cuda.synchronize()
+        e_conv += int((h_out_st == gm.ST_CONVERGED).sum().item())
+    e_secs = reduce_max(time.perf_counter() - t0, world, dev)
+    e_value = reduce_sum(e_conv, world, dev) / e_secs
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = oracle.max_threads()
+        n = max(1, min(32, threads))
+        # one class of the recipe (96x96 stamps, 41x41 PSF): the oracle fits a batch of equal stamps
+        cb = synth.draw_uneven_bulge_disk(seed=2000, G=n, sides=(96,), ks=(41,))
+        sub = synth.Batch(cb.spec, 96, 96, 41, cb.truth, cb.init, cb.psf_kind, cb.psf_par, None,
+                          cb.z.reshape(n, 96, 96).astype(np.float64))
+        c, dt = oracle_sample_fit(sub, np.arange(n))
+        cpu = {"value": c / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{n} galaxies of the recipe's 96x96 / K=41 class (seed 2000), rendered and fitted by the "
+                         f"FP64 oracle, default start, tol {TOL:g}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": uneven_config(G), "gpix_per_s": pix / (fused_ms / 1e3) / 1e9,
+                "converged_frac": converged / (G * args.steps), "mean_iters": float(iters.mean()),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_gradient(args, world, rank, local):
     """Gradient workload: d chi^2/dp of the bulge + bar + nucleus + sky model (15 free
     parameters) for 4,096 galaxies of 96x96 with a 41x41 Moffat PSF, by the adjoint
@@ -435,16 +602,22 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--galaxies", type=int, default=8192, help="batch size per GPU (profiling runs use less)")
+    ap.add_argument("--galaxies", type=int, default=None,
+                    help="batch size per GPU (default 8192 for fit, 32768 for uneven; profiling runs use less)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
-    ap.add_argument("--workload", default="fit", choices=["fit", "gradient"],
-                    help="fit: the LM fit of the SDSS-shaped batch (default); gradient: adjoint chi^2 gradient")
+    ap.add_argument("--workload", default="fit", choices=["fit", "uneven", "gradient"],
+                    help="fit: the LM fit of the SDSS-shaped batch (default); uneven: bulge+disk fits on stamps and "
+                         "PSFs of mixed size; gradient: adjoint chi^2 gradient")
     args = ap.parse_args()
+    if args.galaxies is None:
+        args.galaxies = 32768 if args.workload == "uneven" else 8192
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
     if args.workload == "gradient":
         return run_gradient(args, world, rank, local)
+    if args.workload == "uneven":
+        return run_uneven(args, world, rank, local)
     return run_gpu(args, world, rank, local)
 
 

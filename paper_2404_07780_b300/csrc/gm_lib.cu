@@ -693,6 +693,39 @@ LMOpts lm_opts(const gm_fit_opts* o) {
   return L;
 }
 
+// LM iterations per CUDA-graph replay in gm_fit_batch (and between convergence polls).
+constexpr int kGraphIters = 4;
+
+// Ends a capture left open by an error and frees the graph of one gm_fit_batch call.
+struct GraphGuard {
+  cudaStream_t capturing = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~GraphGuard() {
+    if (capturing) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(capturing, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+// A stream of the current device used only to record the fit graph (the
+// caller's stream may be the legacy default stream, which cannot capture).
+int capture_stream(cudaStream_t* out) {
+  constexpr int kDevs = 64;
+  thread_local cudaStream_t streams[kDevs] = {};
+  int dev = 0;
+  GM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kDevs) return fail(GM_E_UNSUPPORTED, "device ordinal %d beyond %d", dev, kDevs);
+  if (!streams[dev]) GM_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+  *out = streams[dev];
+  return GM_OK;
+}
+
 // One model+Jacobian pass over every galaxy (gm_model: MODE_MODEL;
 // gm_chi2_grad: MODE_NORMAL, tile partials in the workspace).
 struct PassCall {
@@ -881,7 +914,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   const int G = batch->n_gal;
   const auto t_start = std::chrono::steady_clock::now();
   g_have_stats = false;
-  while ((int)g_events.size() < 4 * O.max_iter) {
+  while ((int)g_events.size() < 4 * kGraphIters) {
     cudaEvent_t e;
     GM_CUDA(cudaEventCreate(&e));
     g_events.push_back(e);
@@ -914,34 +947,55 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   PlaneArgs PA = plane_args(pl, A.geo, cconst, scale, planes);
   const int grid = (int)std::max<long long>(1, std::min<long long>(gp.n_items, di.sms));
   const int pgrid = (int)std::max<long long>(1, std::min<long long>(gp.n_items, 8LL * di.sms));
-  const int poll = 4;
-  int passes = 0;
-  for (int k = 0; k < O.max_iter; ++k) {
-    const int cur = k & 1;
+  // U iterations captured once as a CUDA graph and replayed, one convergence poll per
+  // replay.  U is even (or covers max_iter in one replay), so every replay starts on list 0.
+  const int U = std::min(kGraphIters, O.max_iter);
+  GraphGuard gg;
+  cudaStream_t cap;
+  if ((rc = capture_stream(&cap))) return rc;
+  GM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  gg.capturing = cap;
+  for (int u = 0; u < U; ++u) {
+    const int cur = u & 1;
     A.items = PA.items = S.items[cur];
     A.n_items_dev = PA.n_items_dev = S.icount[cur];
     PA.zero[0] = queue;
     PA.zero[1] = S.count[cur ^ 1];
     PA.zero[2] = S.icount[cur ^ 1];
-    GM_CUDA(cudaEventRecord(g_events[4 * k], st));
-    k_planes<MODE_NORMAL><<<pgrid, 256, 0, st>>>(PA);
+    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u], cap, cudaEventRecordExternal));
+    k_planes<MODE_NORMAL><<<pgrid, 256, 0, cap>>>(PA);
     GM_LAUNCHED("k_planes");
-    GM_CUDA(cudaEventRecord(g_events[4 * k + 1], st));
-    kf<<<grid, sm.threads, sm.total, st>>>(A);
+    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 1], cap, cudaEventRecordExternal));
+    kf<<<grid, sm.threads, sm.total, cap>>>(A);
     GM_LAUNCHED("k_fused(normal)");
-    GM_CUDA(cudaEventRecord(g_events[4 * k + 2], st));
-    k_lm_step<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, cur, A.geo, partial, cconst, scale);
+    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 2], cap, cudaEventRecordExternal));
+    k_lm_step<<<(G + 31) / 32, 32, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst, scale);
     GM_LAUNCHED("k_lm_step");
-    GM_CUDA(cudaEventRecord(g_events[4 * k + 3], st));
-    ++passes;
-    if ((k + 1) % poll == 0 || k + 1 == O.max_iter) {
-      int remaining = 0, kerr = 0;
-      GM_CUDA(cudaMemcpyAsync(&remaining, S.count[cur ^ 1], sizeof(int), cudaMemcpyDeviceToHost, st));
-      GM_CUDA(cudaMemcpyAsync(&kerr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-      GM_CUDA(cudaStreamSynchronize(st));
-      if (kerr) return fail(GM_E_CUDA, "fused kernel: a tile load did not complete within its wait limit");
-      if (remaining == 0) break;
+    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 3], cap, cudaEventRecordExternal));
+  }
+  gg.capturing = nullptr;
+  GM_CUDA(cudaStreamEndCapture(cap, &gg.graph));
+  GM_CUDA(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+  int passes = 0;
+  double profile_ms = 0.0, fused_ms = 0.0, step_ms = 0.0;
+  for (int k = 0; k < O.max_iter; k += U) {
+    GM_CUDA(cudaGraphLaunch(gg.exec, st));
+    passes += U;
+    int remaining = 0, kerr = 0;
+    GM_CUDA(cudaMemcpyAsync(&remaining, S.count[U & 1], sizeof(int), cudaMemcpyDeviceToHost, st));
+    GM_CUDA(cudaMemcpyAsync(&kerr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GM_CUDA(cudaStreamSynchronize(st));
+    for (int u = 0; u < U; ++u) {
+      float a = 0.f, b = 0.f, c = 0.f;
+      GM_CUDA(cudaEventElapsedTime(&a, g_events[4 * u], g_events[4 * u + 1]));
+      GM_CUDA(cudaEventElapsedTime(&b, g_events[4 * u + 1], g_events[4 * u + 2]));
+      GM_CUDA(cudaEventElapsedTime(&c, g_events[4 * u + 2], g_events[4 * u + 3]));
+      profile_ms += a;
+      fused_ms += b;
+      step_ms += c;
     }
+    if (kerr) return fail(GM_E_CUDA, "fused kernel: a tile load did not complete within its wait limit");
+    if (remaining == 0) break;
   }
   k_lm_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, G, params_inout, chi2_out, dof_out, iters_out,
                                                status_out, sigma_p_out);
@@ -954,18 +1008,9 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   fs.galaxy_evals = (int64_t)counters[0];
   fs.converged = (int64_t)counters[1];
   fs.iters_sum = (int64_t)counters[2];
-  fs.profile_ms = 0.0;
-  fs.fused_ms = 0.0;
-  fs.step_ms = 0.0;
-  for (int k = 0; k < passes; ++k) {
-    float a = 0.f, b = 0.f, c = 0.f;
-    GM_CUDA(cudaEventElapsedTime(&a, g_events[4 * k], g_events[4 * k + 1]));
-    GM_CUDA(cudaEventElapsedTime(&b, g_events[4 * k + 1], g_events[4 * k + 2]));
-    GM_CUDA(cudaEventElapsedTime(&c, g_events[4 * k + 2], g_events[4 * k + 3]));
-    fs.profile_ms += a;
-    fs.fused_ms += b;
-    fs.step_ms += c;
-  }
+  fs.profile_ms = profile_ms;
+  fs.fused_ms = fused_ms;
+  fs.step_ms = step_ms;
   fs.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   g_stats = fs;
   g_have_stats = true;
