@@ -293,6 +293,28 @@ int gm_fit_batch(const gm_model_desc *desc, const gm_batch *batch, double *param
                  int32_t *status_out, double *sigma_p_out, void *workspace, size_t ws_bytes,
                  void *stream);
 
+/*
+ * Launch-shape tuning of the fused model+Jacobian pass (not part of the
+ * paper's method: the hook of the autotuner in paper_2404_07780_b300/tune.py).
+ *
+ * gm_tune_set makes every later NORMAL-mode pass (gm_chi2_grad, gm_fit_batch,
+ * gm_chi2_grad_noalloc) whose largest PSF side is K and that fits P free
+ * parameters use this launch shape:
+ *   pairs_per_pass    channel pairs loaded and correlated per shared-memory pass, 1..4
+ *   pairs_per_thread  1 or 2
+ *   groups            groups of 128 threads, 1..4 (1..2 with 2 pairs per thread);
+ *                     pairs_per_pass <= pairs_per_thread * groups
+ * pairs_per_pass = 0 removes the (K, P) entry.  A shape that the device's
+ * shared memory or the built kernels cannot run is ignored at launch in favour
+ * of the default shape.  Results agree between shapes to FP32 rounding of the
+ * per-tile sums.  The table is process-wide; gm_tune_clear empties it.
+ * gm_tune_last_shape reports the shape of the calling thread's last planned
+ * pass.  Returns GM_OK, or GM_E_INVAL for arguments outside these ranges.
+ */
+int gm_tune_set(int32_t K, int32_t P, int32_t pairs_per_pass, int32_t pairs_per_thread, int32_t groups);
+int gm_tune_clear(void);
+int gm_tune_last_shape(int32_t *pairs_per_pass, int32_t *pairs_per_thread, int32_t *groups);
+
 #ifdef __cplusplus
 }
 #endif

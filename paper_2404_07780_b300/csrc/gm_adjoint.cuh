@@ -52,6 +52,7 @@ struct AdjArgs {
   int off_psf, off_in, off_cc, off_red, off_bar;
 };
 
+#ifdef GM_HOST_TU
 // I_conv of galaxies 2k and 2k+1 (the second zero past the end) into pair plane k.
 __global__ void __launch_bounds__(256) k_profile_pairs(const __grid_constant__ ProfileArgs A) {
   __shared__ float s_cc[2][kMaxComp * kCC];
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(256) k_profile_pairs(const __grid_constant__ P
     reinterpret_cast<float2*>(A.planes)[((size_t)gp * A.H + i) * A.Wp + j] = make_float2(v[0], v[1]);
   }
 }
+#endif  // GM_HOST_TU
 
 __device__ __forceinline__ void adj_issue(const AdjArgs& A, float2* s_in, u64* bar, int item) {
   const int gp = item / A.n_tiles, tile = item - gp * A.n_tiles;
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
   }
 }
 
+#ifdef GM_HOST_TU
 // chi^2 and d chi^2/dp = -2 (unconvolved + convolved terms) from the two passes' partials.
 __global__ void k_adjoint_finish(const __grid_constant__ DescDev D, int G, int n_tiles,
                                  const double* __restrict__ part_resid, const double* __restrict__ part_adj,
@@ -283,5 +286,6 @@ __global__ void k_adjoint_finish(const __grid_constant__ DescDev D, int G, int n
     for (int f = 0; f < P; ++f) grad[(size_t)g * n_slots + free_slot[f]] = -2.0 * acc[1 + f];
   }
 }
+#endif  // GM_HOST_TU
 
 }  // namespace gm

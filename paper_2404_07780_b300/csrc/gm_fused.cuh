@@ -519,10 +519,14 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
       mbar_try_wait(bar, phase);  // completes at once: acquires the TMA writes for this thread
       phase ^= 1u;
 
+      // the pass's pairs spread evenly over the groups: group q takes npass / ngroups
+      // pairs, one more for the first npass % ngroups groups (at most CPT)
       const int first = pass * A.pp;
       const int npass = min(A.pp, m.ncp - first);
-      const int lp0 = CPT * grp;
-      const int npair = min(CPT, npass - lp0);
+      const int ngroups = nthr / kGroupThreads;
+      const int base = npass / ngroups, rem = npass - base * ngroups;
+      const int npair = base + (grp < rem ? 1 : 0);
+      const int lp0 = grp * base + min(grp, rem);
       u64 acc2[2][8];
       u64 acc1[1][8];
       if (CPT == 2 && npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);

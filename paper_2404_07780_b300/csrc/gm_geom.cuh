@@ -54,6 +54,7 @@ __host__ __device__ inline GalGeom uniform_geom(long long g, int H, int W, int K
   return r;
 }
 
+#ifdef GM_HOST_TU
 // Geometry table, processing order and the item list of one pass over every
 // galaxy, for G equal stamps.
 __global__ void k_geom_uniform(int G, int H, int W, int K, int ncp, GalGeom* geo, int* order, int2* items) {
@@ -67,5 +68,6 @@ __global__ void k_geom_uniform(int G, int H, int W, int K, int ncp, GalGeom* geo
   const long long n = (long long)G * nt;
   for (long long q = t0; q < n; q += stride) items[q] = make_int2((int)(q / nt), (int)(q % nt));
 }
+#endif  // GM_HOST_TU
 
 }  // namespace gm

@@ -1,0 +1,9 @@
+// Instances of k_fused, list 2 of gm_instances.h.
+#include "gm_fused.cuh"
+#include "gm_instances.h"
+
+namespace gm {
+#define GM_X(M, P, C) template __global__ void k_fused<M, P, C>(const __grid_constant__ FusedArgs);
+GM_FUSED_LIST_2(GM_X)
+#undef GM_X
+}  // namespace gm

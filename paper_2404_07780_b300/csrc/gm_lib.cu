@@ -1,5 +1,7 @@
 // gm_lib.cu -- host side of libgm: argument checks, workspace layout, kernel
 // launches and the LM iteration loop behind the C ABI of include/gm.h.
+// The per-galaxy kernels of the headers are compiled here only (gm_inst_*.cu hold the tile kernels).
+#define GM_HOST_TU 1
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,7 +18,18 @@
 #include "gm_adjoint.cuh"
 #include "gm_fused.cuh"
 #include "gm_geom.cuh"
+#include "gm_instances.h"
 #include "gm_lm.cuh"
+
+namespace gm {
+// the tile kernels are instantiated in gm_inst_*.cu
+#define GM_X(M, P, C) extern template __global__ void k_fused<M, P, C>(const __grid_constant__ FusedArgs);
+GM_FUSED_ALL(GM_X)
+#undef GM_X
+#define GM_X(M, P) extern template __global__ void k_adjoint<M, P>(const __grid_constant__ AdjArgs);
+GM_ADJ_ALL(GM_X)
+#undef GM_X
+}  // namespace gm
 
 using namespace gm;
 
@@ -256,24 +269,37 @@ ChanMap chan_map(const Plan& pl) {
   return m;
 }
 
+typedef void (*FusedKernel)(FusedArgs);
+
+// The fused kernel for (mode, P, pairs per thread), or nullptr when not built.
+FusedKernel pick_kernel(int mode, int P, int cpt) {
+#define GM_X(M, PP, C) \
+  if (mode == M && (M == MODE_MODEL || P == PP) && cpt == C) return k_fused<M, PP, C>;
+  GM_FUSED_ALL(GM_X)
+#undef GM_X
+  return nullptr;
+}
+
 struct Smem {
-  int pp, passes, plane, off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar, off_info, total, threads;
+  int pp, cpt, groups, passes, plane, off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar, off_info, total,
+      threads;
 };
 
-// Channel pairs per thread of the fused kernel: one (more warps) unless the
+// Channel pairs per thread of the fused kernel by default: one (more warps) unless the
 // reduction of many free parameters needs the register budget of 256 threads.
 int pick_cpt(const Plan& pl) { return (pl.nacc == 0 || pl.dd.P <= kMaxP1) ? 1 : 2; }
 
-// Shared-memory carve-up of one fused CTA for `pp` channel pairs per pass and
-// PSF sides up to K.  Each pair plane holds a (32+K-1) x window_pitch(K)
-// window and starts at a 128-byte boundary (TMA destinations must be
-// 128-byte aligned).
-Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp) {
+// Shared-memory carve-up of one fused CTA for `pp` channel pairs per pass,
+// `groups` groups of 128 threads holding up to `cpt` pairs each, and PSF sides
+// up to K.  Each pair plane holds a (32+K-1) x window_pitch(K) window and
+// starts at a 128-byte boundary (TMA destinations must be 128-byte aligned).
+Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp, int cpt, int groups) {
   Smem s;
-  const int cpt = pick_cpt(pl);
   s.pp = pp;
+  s.cpt = cpt;
+  s.groups = groups;
   s.passes = (pl.ncp + pp - 1) / pp;
-  s.threads = kGroupThreads * ((pp + cpt - 1) / cpt);
+  s.threads = kGroupThreads * groups;
   const int HH = kTile + K - 1;
   const size_t plane_bytes = ((size_t)HH * window_pitch(K) * 8 + 127) / 128 * 128;
   s.plane = (int)(plane_bytes / 8);
@@ -296,16 +322,53 @@ Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp) {
   return s;
 }
 
-// Largest pass width (channel pairs) whose carve-up fits the device.
+// Launch shapes set by the autotuner (gm_tune_set), keyed by (largest PSF side, free parameters).
+struct TuneShape {
+  int pp, cpt, groups;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, TuneShape> g_tune;
+thread_local TuneShape g_last_shape = {0, 0, 0};
+
+// A shape the fused kernel can run: its instance exists, every pair of a pass has a
+// thread group (pp <= cpt * groups, the thread count within the instance's launch
+// bound) and the carve-up fits the device.
+bool shape_ok(const Plan& pl, int K, int n_comp, int n_slots, int smem_optin, int mode, const TuneShape& t,
+              Smem* out) {
+  if (t.pp < 1 || t.pp > std::min(kMaxPassPairs, pl.ncp) || (t.cpt != 1 && t.cpt != 2)) return false;
+  if (t.groups < 1 || t.groups > (t.cpt == 1 ? 4 : 2) || t.pp > t.cpt * t.groups) return false;
+  if (!pick_kernel(mode, pl.dd.P, t.cpt)) return false;
+  const Smem s = smem_layout(pl, K, n_comp, n_slots, t.pp, t.cpt, t.groups);
+  if (s.total > smem_optin) return false;
+  *out = s;
+  return true;
+}
+
+// The tuned shape for (K, P) when one is set and valid, else the widest pass that fits
+// with the default pairs per thread.
 int smem_plan(const Plan& pl, int K, int n_comp, int n_slots, int smem_optin, Smem* out) {
-  for (int pp = std::min(kMaxPassPairs, pl.ncp); pp >= 1; --pp) {
-    const Smem s = smem_layout(pl, K, n_comp, n_slots, pp);
-    if (s.total <= smem_optin) {
-      *out = s;
+  const int mode = pl.nacc > 0 ? MODE_NORMAL : MODE_MODEL;
+  if (mode == MODE_NORMAL) {
+    TuneShape t = {0, 0, 0};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(std::make_pair(K, pl.dd.P));
+      if (it != g_tune.end()) t = it->second;
+    }
+    if (t.pp > 0 && shape_ok(pl, K, n_comp, n_slots, smem_optin, mode, t, out)) {
+      g_last_shape = t;
       return GM_OK;
     }
   }
-  const Smem s1 = smem_layout(pl, K, n_comp, n_slots, 1);
+  const int cpt = pick_cpt(pl);
+  for (int pp = std::min(kMaxPassPairs, pl.ncp); pp >= 1; --pp) {
+    const TuneShape t = {pp, cpt, (pp + cpt - 1) / cpt};
+    if (shape_ok(pl, K, n_comp, n_slots, smem_optin, mode, t, out)) {
+      g_last_shape = t;
+      return GM_OK;
+    }
+  }
+  const Smem s1 = smem_layout(pl, K, n_comp, n_slots, 1, cpt, 1);
   return fail(GM_E_UNSUPPORTED, "tile needs %d bytes of shared memory (K=%d, %d channels); the device allows %d",
               s1.total, K, pl.nch_conv, smem_optin);
 }
@@ -320,23 +383,6 @@ int dev_info(DevInfo* di) {
   GM_CUDA(cudaDeviceGetAttribute(&di->sms, cudaDevAttrMultiProcessorCount, dev));
   GM_CUDA(cudaDeviceGetAttribute(&di->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   return GM_OK;
-}
-
-typedef void (*FusedKernel)(FusedArgs);
-
-FusedKernel pick_kernel(int mode, int P) {
-  if (mode == MODE_MODEL) return k_fused<MODE_MODEL, 0, 1>;
-  switch (P) {
-#define GM_CASE(n, c) \
-  case n:             \
-    return k_fused<MODE_NORMAL, n, c>;
-    GM_CASE(0, 1) GM_CASE(1, 1) GM_CASE(2, 1) GM_CASE(3, 1) GM_CASE(4, 1) GM_CASE(5, 1) GM_CASE(6, 1)
-    GM_CASE(7, 1) GM_CASE(8, 1) GM_CASE(9, 1) GM_CASE(10, 1) GM_CASE(11, 2) GM_CASE(12, 2) GM_CASE(13, 2)
-    GM_CASE(14, 2) GM_CASE(15, 2) GM_CASE(16, 2)
-#undef GM_CASE
-    default:
-      return nullptr;
-  }
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
@@ -635,7 +681,7 @@ PlaneArgs plane_args(const Plan& pl, const GalGeom* geo, const float* cconst, co
 }
 
 int prepare_fused(int mode, const Plan& pl, const Smem& sm, FusedKernel* out) {
-  FusedKernel k = pick_kernel(mode, pl.dd.P);
+  FusedKernel k = pick_kernel(mode, pl.dd.P, sm.cpt);
   if (!k) return fail(GM_E_UNSUPPORTED, "no fused kernel for %d free parameters", pl.dd.P);
   GM_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm.total));
   *out = k;
@@ -803,6 +849,37 @@ int gm_fit_last_stats(gm_fit_stats* out) {
 }
 
 const char* gm_last_error(void) { return g_err; }
+
+int gm_tune_set(int32_t K, int32_t P, int32_t pairs_per_pass, int32_t pairs_per_thread, int32_t groups) {
+  if (K < 1 || K > 63 || (K % 2) == 0) return fail(GM_E_INVAL, "gm_tune_set: K=%d must be odd, 1..63", K);
+  if (P < 0 || P > GM_MAX_FREE) return fail(GM_E_INVAL, "gm_tune_set: P=%d outside 0..%d", P, GM_MAX_FREE);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (pairs_per_pass == 0) {
+    g_tune.erase(std::make_pair(K, P));
+    return GM_OK;
+  }
+  if (pairs_per_pass < 1 || pairs_per_pass > kMaxPassPairs || (pairs_per_thread != 1 && pairs_per_thread != 2) ||
+      groups < 1 || groups > (pairs_per_thread == 1 ? 4 : 2) || pairs_per_pass > pairs_per_thread * groups)
+    return fail(GM_E_INVAL, "gm_tune_set: shape (%d pairs/pass, %d pairs/thread, %d groups) is not a launch shape",
+                pairs_per_pass, pairs_per_thread, groups);
+  g_tune[std::make_pair(K, P)] = TuneShape{pairs_per_pass, pairs_per_thread, groups};
+  return GM_OK;
+}
+
+int gm_tune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.clear();
+  return GM_OK;
+}
+
+int gm_tune_last_shape(int32_t* pairs_per_pass, int32_t* pairs_per_thread, int32_t* groups) {
+  if (!pairs_per_pass || !pairs_per_thread || !groups) return fail(GM_E_INVAL, "gm_tune_last_shape: NULL output");
+  if (g_last_shape.pp == 0) return fail(GM_E_INVAL, "gm_tune_last_shape: no pass planned on this thread yet");
+  *pairs_per_pass = g_last_shape.pp;
+  *pairs_per_thread = g_last_shape.cpt;
+  *groups = g_last_shape.groups;
+  return GM_OK;
+}
 
 size_t gm_model_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
   if (!desc || !batch || check_desc(desc)) return 0;
@@ -1027,16 +1104,11 @@ namespace {
 typedef void (*AdjKernel)(AdjArgs);
 
 AdjKernel pick_adjoint(int mode, int P) {
-#define GM_ADJ(n)                                                        \
-  case n:                                                                \
-    return mode == ADJ_RESID ? k_adjoint<ADJ_RESID, n> : k_adjoint<ADJ_GRAD, n>;
-  switch (P) {
-    GM_ADJ(0) GM_ADJ(1) GM_ADJ(2) GM_ADJ(3) GM_ADJ(4) GM_ADJ(5) GM_ADJ(6) GM_ADJ(7) GM_ADJ(8)
-    GM_ADJ(9) GM_ADJ(10) GM_ADJ(11) GM_ADJ(12) GM_ADJ(13) GM_ADJ(14) GM_ADJ(15) GM_ADJ(16)
-    default:
-      return nullptr;
-  }
-#undef GM_ADJ
+#define GM_X(M, PP) \
+  if (mode == M && P == PP) return k_adjoint<M, PP>;
+  GM_ADJ_ALL(GM_X)
+#undef GM_X
+  return nullptr;
 }
 
 struct WsAdj {

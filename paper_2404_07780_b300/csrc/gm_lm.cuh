@@ -74,6 +74,7 @@ __device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, in
   for (int s = 0; s < D.n_slots; ++s) scale[s] = (use_log && D.is_log[s]) ? (float)p[s] : 1.f;
 }
 
+#ifdef GM_HOST_TU
 // Constants for every galaxy from caller parameters (gm_model, gm_chi2_grad).
 // Stamp heights from geo, or H for every galaxy when geo is nullptr.
 __global__ void k_setup(const __grid_constant__ DescDev D, int G, const GalGeom* __restrict__ geo, int H,
@@ -83,7 +84,9 @@ __global__ void k_setup(const __grid_constant__ DescDev D, int G, const GalGeom*
   setup_galaxy(D, params + (size_t)g * D.n_slots, geo ? geo[g].H : H, use_log, cconst + (size_t)g * D.n_comp * kCC,
                scale + (size_t)g * D.n_slots);
 }
+#endif  // GM_HOST_TU
 
+#ifdef GM_HOST_TU
 // Used-pixel count and bad-input flag per galaxy (one block per galaxy, strided).
 __global__ void k_validate(int G, const GalGeom* __restrict__ geo, const float* __restrict__ image,
                            const float* __restrict__ sigma, const uint8_t* __restrict__ mask, int* nused, int* bad) {
@@ -120,6 +123,7 @@ __global__ void k_validate(int G, const GalGeom* __restrict__ geo, const float* 
     __syncthreads();
   }
 }
+#endif  // GM_HOST_TU
 
 __device__ inline double to_u(const DescDev& D, int s, double p) { return D.is_log[s] ? log(p) : p; }
 __device__ inline double from_u(const DescDev& D, int s, double u) { return D.is_log[s] ? exp(u) : u; }
@@ -137,6 +141,7 @@ __device__ inline void queue_galaxy(const LMState& S, int l, int g, const GalGeo
   for (int t = 0; t < nt; ++t) S.items[l][ipos + t] = make_int2(g, t);
 }
 
+#ifdef GM_HOST_TU
 // Start of a fit: clamp the start point, set status from the validation and
 // queue the galaxies that can be fitted, in the processing order `order`
 // (most expensive first).
@@ -164,6 +169,7 @@ __global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O
     queue_galaxy(S, 0, g, geo[g]);
   }
 }
+#endif  // GM_HOST_TU
 
 // In-place Cholesky of an n x n row-major matrix (lower triangle); false if not
 // positive definite.
@@ -224,6 +230,7 @@ __device__ inline double gn_decrement(const double* Ap, const double* g, int P) 
   return s;
 }
 
+#ifdef GM_HOST_TU
 // One LM step for every galaxy evaluated in this iteration (list `cur`):
 // sum the tile partials of the pass, accept or reject the evaluated point,
 // test convergence, solve the damped normal equations for the next trial point
@@ -331,7 +338,9 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
   S.lam[g] = lam;
   S.status[g] = st;
 }
+#endif  // GM_HOST_TU
 
+#ifdef GM_HOST_TU
 // Outputs of a fit: best point, chi^2, degrees of freedom, evaluations, status
 // and the covariance error bars sqrt(diag[(J^T W J)^-1]) (Sec. 5.2).  An axis
 // ratio above 1 is rewritten as 1/q with its position angles turned by pi/2
@@ -438,7 +447,9 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
   if (S.status[g] == ST_CONVERGED) atomicAdd(S.evals + 1, 1ull);
   atomicAdd(S.evals + 2, (unsigned long long)S.it[g]);
 }
+#endif  // GM_HOST_TU
 
+#ifdef GM_HOST_TU
 // gm_chi2_grad outputs from the tile partials (physical coordinates).
 __global__ void k_chi2_grad_finish(const __grid_constant__ DescDev D, int G, const GalGeom* __restrict__ geo,
                                    const double* __restrict__ partial, double* chi2, double* grad, double* jtj) {
@@ -464,5 +475,6 @@ __global__ void k_chi2_grad_finish(const __grid_constant__ DescDev D, int G, con
       for (int h = 0; h < P; ++h) J[D.free_slot[f] * NS + D.free_slot[h]] = packed(acc + 1 + P, P, f, h);
   }
 }
+#endif  // GM_HOST_TU
 
 }  // namespace gm

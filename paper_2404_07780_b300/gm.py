@@ -30,7 +30,8 @@ ST_CONVERGED = 1
 # every symbol include/gm.h declares
 EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model",
            "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch",
-           "gm_fit_last_stats", "gm_chi2_grad_noalloc", "gm_grad_adjoint_workspace_bytes", "gm_grad_adjoint")
+           "gm_fit_last_stats", "gm_chi2_grad_noalloc", "gm_grad_adjoint_workspace_bytes", "gm_grad_adjoint",
+           "gm_tune_set", "gm_tune_clear", "gm_tune_last_shape")
 
 
 class GMError(RuntimeError):
@@ -143,7 +144,16 @@ def load() -> ctypes.CDLL:
         lib.gm_grad_adjoint.argtypes = [P, P, P, P, P, P, S, P]
         lib.gm_fit_last_stats.restype = ctypes.c_int
         lib.gm_fit_last_stats.argtypes = [P]
+        I32 = ctypes.c_int32
+        lib.gm_tune_set.restype = ctypes.c_int
+        lib.gm_tune_set.argtypes = [I32, I32, I32, I32, I32]
+        lib.gm_tune_clear.restype = ctypes.c_int
+        lib.gm_tune_clear.argtypes = []
+        lib.gm_tune_last_shape.restype = ctypes.c_int
+        lib.gm_tune_last_shape.argtypes = [P, P, P]
         _lib = lib
+        from . import tune
+        tune.apply_cache(lib)
     return _lib
 
 
@@ -393,6 +403,22 @@ class Fitter:
                                      _ptr(self.sigma_p), _ptr(self.ws), self.ws_bytes, _stream()), "gm_fit_batch")
         return {"params": params, "chi2": self.chi2, "dof": self.dof, "iters": self.iters, "status": self.status,
                 "sigma_p": self.sigma_p}
+
+
+def gm_tune_set(K: int, P: int, pairs_per_pass: int, pairs_per_thread: int, groups: int):
+    """Launch shape of the fused pass for largest PSF side K and P free parameters (0 pairs_per_pass clears)."""
+    _check(load().gm_tune_set(K, P, pairs_per_pass, pairs_per_thread, groups), "gm_tune_set")
+
+
+def gm_tune_clear():
+    _check(load().gm_tune_clear(), "gm_tune_clear")
+
+
+def gm_tune_last_shape() -> tuple[int, int, int]:
+    """(pairs_per_pass, pairs_per_thread, groups) of this thread's last planned pass."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().gm_tune_last_shape(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "gm_tune_last_shape")
+    return a.value, b.value, c.value
 
 
 def gm_fit_last_stats() -> dict:

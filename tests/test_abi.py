@@ -159,3 +159,31 @@ def test_uneven_geometry_sizes_and_rejections(lib):
     assert lib.gm_grad_adjoint_workspace_bytes(ctypes.byref(d), ctypes.byref(b)) == 0
     rc = lib.gm_grad_adjoint(ctypes.byref(d), ctypes.byref(b), fake, fake, None, fake, 1 << 20, None)
     assert rc == -4 and "equal stamps" in lib.gm_last_error().decode()
+
+
+def test_tune_set_rejects_shapes_that_are_not_launch_shapes(lib):
+    assert lib.gm_tune_set(41, 8, 4, 1, 4) == 0
+    assert lib.gm_tune_set(41, 8, 0, 0, 0) == 0       # clears the entry
+    assert lib.gm_tune_set(40, 8, 4, 1, 4) == -1      # even PSF side
+    assert lib.gm_tune_set(41, 17, 4, 1, 4) == -1     # more free parameters than the ABI allows
+    assert lib.gm_tune_set(41, 8, 5, 1, 4) == -1      # more than 4 pairs per pass
+    assert lib.gm_tune_set(41, 8, 4, 1, 3) == -1      # a pair without a thread group
+    assert lib.gm_tune_set(41, 8, 2, 2, 3) == -1      # 3 groups of 2-pair threads exceed 256 threads
+    assert lib.gm_tune_set(41, 8, 2, 3, 1) == -1      # 3 pairs per thread is not built
+    assert lib.gm_tune_clear() == 0
+
+
+def test_tune_cache_round_trip(lib, tmp_path):
+    from paper_2404_07780_b300 import tune
+    path = str(tmp_path / "tuning.json")
+    e = {"K": 41, "P": 8, "pairs_per_pass": 4, "pairs_per_thread": 1, "groups": 4, "ms": 1.0}
+    tune.save([e], path, device="test-device")
+    tune.save([dict(e, K=25, P=12, pairs_per_pass=2, pairs_per_thread=2, groups=2)], path, device="test-device")
+    assert len(tune.read_cache(path)["test-device"]["entries"]) == 2
+    assert tune.apply_cache(lib, path, device="test-device") == 2
+    assert tune.apply_cache(lib, path, device="another-device") == 0
+    assert all(lib.gm_tune_set(K, P, 0, 0, 0) == 0 for K, P in ((41, 8), (25, 12)))
+    # every shape the tuner tries is one gm_tune_set accepts
+    for shape in tune.SHAPES:
+        assert lib.gm_tune_set(41, 8, *shape) == 0, shape
+    assert lib.gm_tune_clear() == 0
