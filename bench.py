@@ -41,10 +41,13 @@ TOL = 1e-6
 MAX_ITER = 200
 PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
-# DRAM bytes (read + write) of k_fused<NORMAL, 8> per galaxy evaluated, from one ncu capture of a
-# 1,024-galaxy pass of this workload (706.6 MB); traffic grows in proportion to the galaxies a pass
+# DRAM bytes (read + write) of k_fused<NORMAL, 8, 2> per galaxy evaluated, from one ncu capture of a
+# 1,024-galaxy pass of this workload (704.5 MB); traffic grows in proportion to the galaxies a pass
 # evaluates, so a launch's traffic is this times its galaxies
-FUSED_DRAM_BYTES_PER_GALAXY = 706.6e6 / 1024
+FUSED_DRAM_BYTES_PER_GALAXY = 704.46e6 / 1024
+# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,615.9 MB
+# for a 2,048-galaxy pass of 45.59 M pixels)
+UNEVEN_DRAM_BYTES_PER_PIXEL = 2615.9e6 / 45591296
 
 
 def workload_config(G, H, K):
@@ -343,7 +346,7 @@ def run_gpu(args, world, rank, local):
             "traffic": FUSED_DRAM_BYTES_PER_GALAXY * evals / max(launches_fused, 1),
             "traffic_unit": "bytes per launch (average launch)",
             "algorithmic_bytes": (9 + 32) * H * H * evals / max(launches_fused, 1),
-            "kernel": "k_fused<NORMAL,8>",
+            "kernel": "k_fused<NORMAL,8,2>",
             "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
 
     cpu = None
@@ -478,8 +481,11 @@ def run_uneven(args, world, rank, local):
     pix = args.steps * float((rb.geom[:, 0].astype(np.float64) * rb.geom[:, 1] * iters).sum())
     achieved = flops / (fused_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-            "kernel": "k_fused<NORMAL,12> (uneven items, per-class TMA maps)",
+            "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": UNEVEN_DRAM_BYTES_PER_PIXEL * pix / max(sum(st["passes"] for st in stats), 1),
+            "traffic_unit": "bytes per launch (average launch)",
+            "algorithmic_bytes": 56.0 * pix / max(sum(st["passes"] for st in stats), 1),
+            "kernel": "k_fused<NORMAL,12,2> (uneven items, per-class TMA maps)",
             "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
 
     # end to end through the public API from pinned host buffers
