@@ -1,0 +1,149 @@
+"""The learned initialiser's tensor-core layers (include/gm_cnn.h) against the
+FP64 CNN reference (oracle/cnn.py) on the same BF16-rounded inputs.
+
+Tolerances: FP32 outputs (weight gradients, the last dense layer) carry only
+FP32 accumulation error: |d| <= 1e-4 * sqrt(sum of squared terms) per
+element.  BF16 outputs add one BF16 rounding of the result (relative 2^-8):
+|d| <= 2^-8 |ref| + 1e-4 * sqrt(sum of squared terms)."""
+import numpy as np
+import pytest
+
+from oracle import cnn as ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2404_07780_b300 import cnn
+    from paper_2404_07780_b300.build import build_lib
+    build_lib()
+    cnn.lib()
+    return cnn
+
+
+def _bf(a, seed=None):
+    """A BF16 CUDA tensor and the float64 values it holds."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).to("cuda").to(torch.bfloat16).contiguous()
+    return t, t.float().cpu().numpy().astype(np.float64)
+
+
+def _f32(a):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).to("cuda")
+    return t, t.cpu().numpy().astype(np.float64)
+
+
+def _close(got, want, scale, bf16_out):
+    got = np.asarray(got, np.float64)
+    tol = 1e-4 * scale + (2.0 ** -8 * np.abs(want) if bf16_out else 0.0) + 1e-30
+    bad = np.abs(got - want) > tol
+    assert not bad.any(), (int(bad.sum()), float(np.abs(got - want)[bad].max()), got[bad][:4], want[bad][:4])
+
+
+def _np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+# (n, h, w, ci, co): the four layers of the network, a ragged spatial size, and a batch
+# large enough for many M tiles
+CONVS = [(4, 64, 64, 1, 32), (4, 32, 32, 32, 64), (4, 16, 16, 64, 128), (4, 8, 8, 128, 128), (3, 13, 9, 8, 16),
+         (64, 16, 16, 64, 128)]
+
+
+@pytest.mark.parametrize("shape", CONVS)
+def test_conv_forward(C, shape):
+    n, h, w, ci, co = shape
+    rng = np.random.default_rng(1)
+    x, xr = _bf(rng.normal(size=(n, h, w, ci)))
+    W, Wr = _bf(rng.normal(size=(co, 3, 3, ci)) / np.sqrt(9 * ci))
+    b, br = _f32(rng.normal(size=co) * 0.1)
+    for relu in (False, True):
+        y = _np(C.conv_fwd(x, W, b, relu=relu))
+        want = ref.conv_fwd(xr, Wr, br, relu=relu)
+        scale = np.sqrt(ref.conv_fwd(xr ** 2, Wr ** 2) + br ** 2)
+        _close(y, want, scale, True)
+    C.check_device_error()
+
+
+@pytest.mark.parametrize("shape", [s for s in CONVS if s[3] % 8 == 0])
+def test_conv_backward_data(C, shape):
+    n, h, w, ci, co = shape
+    rng = np.random.default_rng(2)
+    ho, wo = (h + 1) // 2, (w + 1) // 2
+    dy, dyr = _bf(rng.normal(size=(n, ho, wo, co)))
+    W, Wr = _bf(rng.normal(size=(co, 3, 3, ci)) / np.sqrt(9 * ci))
+    mask, maskr = _bf(np.maximum(rng.normal(size=(n, h, w, ci)), 0.0))
+    for m, mr in ((None, None), (mask, maskr)):
+        dx = _np(C.conv_bwd_data(dy, W, h, w, mask=m))
+        want = ref.conv_bwd_data(dyr, Wr, h, w, mask=mr)
+        scale = np.sqrt(ref.conv_bwd_data(dyr ** 2, Wr ** 2, h, w))
+        _close(dx, want, scale, True)
+    C.check_device_error()
+
+
+@pytest.mark.parametrize("shape", CONVS)
+def test_conv_backward_weight(C, shape):
+    n, h, w, ci, co = shape
+    rng = np.random.default_rng(3)
+    ho, wo = (h + 1) // 2, (w + 1) // 2
+    x, xr = _bf(rng.normal(size=(n, h, w, ci)))
+    dy, dyr = _bf(rng.normal(size=(n, ho, wo, co)))
+    dw, db = C.conv_bwd_weight(x, dy)
+    want_w, want_b = ref.conv_bwd_weight(xr, dyr)
+    sw, sb = ref.conv_bwd_weight(xr ** 2, dyr ** 2)
+    _close(_np(dw), want_w, np.sqrt(sw), False)
+    _close(_np(db), want_b, np.sqrt(sb), False)
+    C.check_device_error()
+
+
+@pytest.mark.parametrize("n,fin,fout", [(64, 2048, 256), (300, 256, 16), (8, 64, 32), (1000, 128, 264)])
+def test_dense_forward_and_backward(C, n, fin, fout):
+    rng = np.random.default_rng(4)
+    x, xr = _bf(rng.normal(size=(n, fin)))
+    W, Wr = _bf(rng.normal(size=(fout, fin)) / np.sqrt(fin))
+    b, br = _f32(rng.normal(size=fout) * 0.1)
+    scale = np.sqrt((xr ** 2) @ (Wr ** 2).T + br ** 2)
+    _close(_np(C.dense_fwd(x, W, b, relu=True)), ref.dense_fwd(xr, Wr, br, relu=True), scale, True)
+    _close(_np(C.dense_fwd(x, W, b, relu=False, fp32_out=True)), ref.dense_fwd(xr, Wr, br), scale, False)
+    dy, dyr = _bf(rng.normal(size=(n, fout)))
+    mask, maskr = _bf(np.maximum(rng.normal(size=(n, fin)), 0.0))
+    _close(_np(C.dense_bwd_data(dy, W, mask=mask)), ref.dense_bwd_data(dyr, Wr, mask=maskr),
+           np.sqrt((dyr ** 2) @ (Wr ** 2)), True)
+    dw, db = C.dense_bwd_weight(x, dy)
+    ww, wb = ref.dense_bwd_weight(xr, dyr)
+    _close(_np(dw), ww, np.sqrt((dyr ** 2).T @ (xr ** 2)), False)
+    _close(_np(db), wb, np.sqrt((dyr ** 2).sum(0)), False)
+    C.check_device_error()
+
+
+def test_prep_loss_and_adam(C):
+    import torch
+    rng = np.random.default_rng(5)
+    img, imgr = _f32(rng.normal(size=(5, 12, 10)) * 30.0)
+    got = _np(C.prep(img, 0.5))[..., 0]
+    want = ref.prep(imgr, 0.5)
+    assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 1e-6)
+
+    pred, predr = _f32(rng.normal(size=(37, 16)))
+    tgt, tgtr = _f32(rng.normal(size=(37, 14)))
+    loss, dpred = C.mse(pred, tgt, 14)
+    wl, wd = ref.mse(predr, tgtr, 14)
+    assert abs(loss.item() - wl) <= 1e-5 * wl
+    assert np.all(np.abs(_np(dpred) - wd) <= 2.0 ** -8 * np.abs(wd) + 1e-12)
+
+    p, pr = _f32(rng.normal(size=1000))
+    g, gr = _f32(rng.normal(size=1000))
+    m = torch.zeros(1000, device="cuda")
+    v = torch.zeros(1000, device="cuda")
+    pb = torch.empty(1000, dtype=torch.bfloat16, device="cuda")
+    mr, vr = np.zeros(1000), np.zeros(1000)
+    for step in (1, 2, 3):
+        C.adam(p, g, m, v, pb, 1e-3, step)
+        pr, mr, vr = ref.adam(pr, gr, mr, vr, 1e-3, 0.9, 0.999, 1e-8, step)
+    np.testing.assert_allclose(p.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(_np(pb), pr, rtol=2.0 ** -8, atol=1e-6)
