@@ -155,20 +155,8 @@ class ClockSampler:
 
 def render_workload(b: synth.Batch, device):
     """PSFs, truth images, noisy data and sigma maps on the device, rendered by gm_model."""
-    import torch
-    from paper_2404_07780_b300 import gm
-    G, K = b.G, b.K
-    psfspec = synth.ModelSpec().add("moffat", "psf", K, K, convolve=False)
-    one = torch.ones((G, 1, 1), dtype=torch.float32, device=device)
-    psf = gm.gm_model(psfspec, torch.from_numpy(b.psf_par).to(device), one, K, K)
-    psf = (psf / psf.sum((1, 2), keepdim=True)).contiguous()
-    Mt = torch.zeros((G, b.H, b.W), dtype=torch.float32, device=device)
-    for spec, par in b.truth_parts():
-        Mt += gm.gm_model(spec, torch.from_numpy(np.ascontiguousarray(par)).to(device), psf, b.H, b.W)
-    sigma = torch.sqrt(b.sky_var + Mt.clamp(min=0) / b.gain)
-    image = Mt + sigma * torch.from_numpy(b.z).to(device=device, dtype=torch.float32)
-    mask = torch.from_numpy(b.mask).to(device) if b.mask is not None else None
-    return image.contiguous(), sigma.contiguous(), mask, psf
+    from paper_2404_07780_b300 import workloads
+    return workloads.render_equal(b, device)
 
 
 def inbounds_taps(H, W, K):
@@ -386,22 +374,8 @@ UNEVEN_KS = tuple(range(25, 52, 2))
 
 def render_uneven(rb: synth.RaggedBatch, device):
     """Packed PSFs (unit sum), data and sigma of an uneven batch, rendered by gm_model."""
-    import torch
-    from paper_2404_07780_b300 import gm
-    G = rb.G
-    k = rb.geom[:, 2].astype(np.int64)
-    psf_geom = np.stack([k, k, np.ones_like(k)], 1)
-    psfspec = synth.ModelSpec().add("moffat", "psf", 64, 64, convolve=False)
-    one = torch.ones(G, dtype=torch.float32, device=device)
-    psf = gm.gm_model(psfspec, torch.from_numpy(rb.psf_par).to(device), one, geom=psf_geom)
-    gid = torch.repeat_interleave(torch.arange(G, device=device), torch.from_numpy(k * k).to(device))
-    sums = torch.zeros(G, dtype=torch.float64, device=device).index_add_(0, gid, psf.double())
-    psf = (psf / sums[gid].float()).contiguous()
-    M = gm.gm_model(rb.spec, torch.from_numpy(rb.truth).to(device), psf, geom=rb.geom)
-    sigma = torch.sqrt(rb.sky_var + M.clamp(min=0) / rb.gain)
-    image = M + sigma * torch.from_numpy(rb.z).to(device=device, dtype=torch.float32)
-    del M
-    return image.contiguous(), sigma.contiguous(), psf
+    from paper_2404_07780_b300 import workloads
+    return workloads.render_uneven(rb, device)
 
 
 def uneven_config(G):

@@ -355,11 +355,12 @@ class RaggedBatch:
 
 
 def draw_uneven_bulge_disk(seed: int = 2000, G: int = 32768, sides=(48, 64, 96, 128, 192, 256),
-                           ks=tuple(range(25, 52, 2))) -> RaggedBatch:
+                           ks=tuple(range(25, 52, 2)), noise: bool = True) -> RaggedBatch:
     """Uneven bulge + disk batch: square stamps with side uniform over `sides`, Moffat PSF
     (beta 3, FWHM 1.2-1.8 px) with odd side uniform over `ks`; Sersic bulge (n 1-6) + Sersic
     disk with n = 1 (Re_d = 1.5-4 x Re_b, own q and PA) + sky, common centre within +-2 px of
-    the stamp centre.  Radii scale with the stamp side (bulge Re 1.5-8 px at side 96)."""
+    the stamp centre.  Radii scale with the stamp side (bulge Re 1.5-8 px at side 96).  With
+    noise=False no noise is drawn (z is empty; the caller supplies its own draws)."""
     g = rng(seed)
     side = g.choice(np.asarray(sides), G)
     k = g.choice(np.asarray(ks), G)
@@ -380,7 +381,7 @@ def draw_uneven_bulge_disk(seed: int = 2000, G: int = 32768, sides=(48, 64, 96, 
     c = k / 2.0  # each PSF centred on pixel (c, c) of its own k x k grid, as psf_params
     psf_par = np.stack([c, c, np.ones(G), np.zeros(G), np.ones(G), fwhm, np.full(G, 3.0)], 1)
     npix = int((side.astype(np.int64) ** 2).sum())
-    z = g.standard_normal(npix, dtype=np.float32)
+    z = g.standard_normal(npix, dtype=np.float32) if noise else np.zeros(0, np.float32)
     return RaggedBatch(spec, geom, truth, init, "moffat", psf_par, None, z)
 
 

@@ -118,24 +118,13 @@ def tune_workloads(path: str = CACHE, G: int = 512, verbose: bool = True) -> lis
     recipe, rendered by the library) and merge them into the cache."""
     import numpy as np
     import torch
-    from . import gm, synth
+    from . import gm, synth, workloads
     dev = torch.device("cuda")
     entries = []
 
     def render(b):
-        G_, K = b.G, b.K
-        psfspec = synth.ModelSpec().add("moffat" if b.psf_kind == "moffat" else "gaussian", "psf", K, K,
-                                        convolve=False)
-        one = torch.ones((G_, 1, 1), dtype=torch.float32, device=dev)
-        psf = gm.gm_model(psfspec, torch.from_numpy(b.psf_par).to(dev), one, K, K)
-        psf = (psf / psf.sum((1, 2), keepdim=True)).contiguous()
-        M = torch.zeros((G_, b.H, b.W), dtype=torch.float32, device=dev)
-        for spec, par in b.truth_parts():
-            M += gm.gm_model(spec, torch.from_numpy(np.ascontiguousarray(par)).to(dev), psf, b.H, b.W)
-        sigma = torch.sqrt(b.sky_var + M.clamp(min=0) / b.gain)
-        image = M + sigma * torch.from_numpy(b.z).to(device=dev, dtype=torch.float32)
-        mask = torch.from_numpy(b.mask).to(dev) if b.mask is not None else None
-        return torch.from_numpy(b.init).to(dev), image.contiguous(), sigma.contiguous(), mask, psf
+        image, sigma, mask, psf = workloads.render_equal(b, dev)
+        return torch.from_numpy(b.init).to(dev), image, sigma, mask, psf
 
     batches = [synth.draw_small(seed=1, G=G), synth.draw_sdss(seed=1000, G=G)]
     batches += [synth.draw_bulge_disk(seed=2000, G=G, H=128, W=128, K=k) for k in range(25, 52, 2)]
