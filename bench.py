@@ -520,6 +520,189 @@ def run_uneven(args, world, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# learned-initialiser workload
+# ---------------------------------------------------------------------------
+
+def run_learned(args, world, rank, local):
+    """Learned initialiser: train the CNN on the GPU on `--train-samples` stamps rendered by
+    gm_model, then time the learned pipeline (network input preparation, inference, LM fit from
+    the predicted start, default-start refits of the galaxies that do not converge) on 65,536
+    bulge+disk galaxies of 128x128 with per-galaxy Moffat PSFs of side 25-51.  The default-start
+    fit of the same batch is timed beside it."""
+    import torch
+    from paper_2404_07780_b300 import cnn, gm, workloads
+    from paper_2404_07780_b300.build import build_lib
+
+    build_lib()
+    gm.load()
+    cnn.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    G = args.galaxies
+    side = 128
+
+    # training (a one-off cost, timed on its own)
+    t0 = time.perf_counter()
+    X, T, codec = cnn.make_training_set(args.train_samples, seed=4000 + rank, side=side, device=dev)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = cnn.Net(seed=rank, device=dev)
+    t0 = time.perf_counter()
+    losses = cnn.train(net, X, T, codec.dv, epochs=args.epochs, batch=512, lr=2e-3,
+                       log=lambda m: print(m, file=sys.stderr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, T
+
+    rb = synth.draw_uneven_bulge_disk(seed=4100 + rank, G=G, sides=(side,), ks=UNEVEN_KS)
+    image, sigma, psf = workloads.render_uneven(rb, dev)
+    p_def = torch.from_numpy(rb.init).to(dev)
+    fitter = gm.Fitter(rb.spec, G, device=dev, geom=rb.geom)
+    opts = gm.FitOptions(tol=TOL, max_iter=MAX_ITER)
+    stream = torch.cuda.current_stream()
+    img3 = image.view(G, side, side)
+
+    def learned_step():
+        p0 = cnn.learned_start(net, img3, codec, rb.spec)
+        return cnn.fit_with_fallback(fitter, rb.spec, p0, p_def, image, sigma, None, psf, opts, geom=rb.geom)
+
+    # the default-start fit of the same batch (one warm-up, one timed)
+    params = torch.empty_like(p_def)
+    params.copy_(p_def)
+    fitter.fit(params, image, sigma, None, psf, opts)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    params.copy_(p_def)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    d = {k: v.clone() for k, v in fitter.fit(params, image, sigma, None, psf, opts).items()}
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_default = e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        learned_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    conv = 0
+    evals = 0
+    refits = 0
+    fused_ms = 0.0
+    for _ in range(args.steps):
+        r, info = learned_step()
+        conv += int((r["status"] == gm.ST_CONVERGED).sum().item())
+        evals += info["evals"]
+        refits += info["refits"]
+        fused_ms += info["fused_ms"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms_max = reduce_max(ms, world, dev)
+    value = reduce_sum(conv, world, dev) / (ms_max / 1e3)
+
+    # inference alone (network input preparation + forward), for the tensor-core roofline
+    inf_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        net.predict(cnn.prep(img3, 1.0 / cnn.SKY_SIGMA))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        inf_ms.append(e0.elapsed_time(e1))
+    macs = 0
+    hw = 64
+    for kind, i, o in cnn.LAYERS:
+        if kind == "conv":
+            hw //= 2
+            macs += hw * hw * o * 9 * i
+        else:
+            macs += i * o
+    inf_tflops = 2.0 * macs * G / (min(inf_ms) / 1e3) / 1e12
+    peak_bf16 = None
+    try:
+        with open(PEAKS_PATH) as f:
+            peak_bf16 = json.load(f).get("bf16_tflops")
+    except (OSError, ValueError):
+        pass
+
+    # roofline of the dominant kernel (the fused pass): algorithmic FLOPs of the evaluations
+    # spent, at the mean in-bounds taps of the batch's PSF sides
+    taps = np.array([inbounds_taps(side, side, int(k)) for k in rb.geom[:, 2]], np.float64)
+    flops = 2.0 * (1 + 11) * taps.mean() * evals
+    achieved = flops / (fused_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_fused<NORMAL,12,2> (evaluations x mean taps of the batch)",
+            "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
+    c2_d, c2_l = d["chi2"].cpu().numpy(), r["chi2"].cpu().numpy()
+    dof = d["dof"].cpu().numpy().astype(np.float64)
+    dchi = (c2_l - c2_d) / np.sqrt(2 * dof)
+    it_d = float(d["iters"].float().mean().item())
+    it_l = evals / (G * args.steps)
+    conv_d = int((d["status"] == gm.ST_CONVERGED).sum().item())
+
+    # end to end through the public API from pinned host buffers
+    h_img, h_sig, h_psf = image.cpu().pin_memory(), sigma.cpu().pin_memory(), psf.cpu().pin_memory()
+    h_out = torch.empty((G, rb.spec.n_slots), dtype=torch.float64).pin_memory()
+    h_st = torch.empty(G, dtype=torch.int32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_img, h_sig, h_psf))
+    d2h = h_out.numel() * 8 + h_st.numel() * 4
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_conv = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        di, ds, dp = h_img.to(dev, non_blocking=True), h_sig.to(dev, non_blocking=True), h_psf.to(dev, non_blocking=True)
+        p0 = cnn.learned_start(net, di.view(G, side, side), codec, rb.spec)
+        out, _ = cnn.fit_with_fallback(fitter, rb.spec, p0, p_def, di, ds, None, dp, opts, geom=rb.geom)
+        h_out.copy_(out["params"], non_blocking=True)
+        h_st.copy_(out["status"], non_blocking=True)
+        torch.cuda.synchronize()
+        e_conv += int((h_st == gm.ST_CONVERGED).sum().item())
+    e_secs = reduce_max(time.perf_counter() - t0, world, dev)
+    e_value = reduce_sum(e_conv, world, dev) / e_secs
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 fit, bf16 network", "data": "synthetic",
+                "config": {"workload": f"learned initialiser + LM refinement, {G} bulge+disk+sky galaxies, "
+                                       f"{side}x{side} float32 stamps, per-galaxy Moffat PSF of odd side 25-51, "
+                                       f"12 free parameters, tol {TOL:g}; network trained on "
+                                       f"{args.train_samples} rendered stamps, {args.epochs} epoch(s)",
+                           "galaxies": G, "train_samples": args.train_samples, "epochs": args.epochs,
+                           "l2": "inputs ~1.1 GB per batch > 126 MB L2 (no flush)"},
+                "default_start": {"fits_per_s": conv_d / (ms_default / 1e3), "ms": ms_default,
+                                  "converged_frac": conv_d / G, "mean_iters": it_d},
+                "learned_start": {"converged_frac": conv / (G * args.steps), "mean_iters": it_l,
+                                  "fallback_refits_per_step": refits / args.steps,
+                                  "chi2_better_by_1sigma_frac": float(np.mean(dchi < -1)),
+                                  "chi2_worse_by_1sigma_frac": float(np.mean(dchi > 1))},
+                "speedup_vs_default_start": value / (conv_d / (ms_default / 1e3)),
+                "training": {"samples": args.train_samples, "epochs": args.epochs, "data_s": t_data,
+                             "train_s": t_train, "samples_per_s": args.train_samples * args.epochs / t_train,
+                             "loss_per_epoch": losses},
+                "inference": {"ms": min(inf_ms), "stamps_per_s": G / (min(inf_ms) / 1e3),
+                              "tflops": inf_tflops, "bf16_peak_tflops": peak_bf16,
+                              "frac": (inf_tflops / peak_bf16) if peak_bf16 else None},
+                "roofline": roof,
+                "cpu_baseline": None,
+                "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_gradient(args, world, rank, local):
     """Gradient workload: d chi^2/dp of the bulge + bar + nucleus + sky model (15 free
     parameters) for 4,096 galaxies of 96x96 with a 41x41 Moffat PSF, by the adjoint
@@ -585,12 +768,14 @@ def main():
     ap.add_argument("--galaxies", type=int, default=None,
                     help="batch size per GPU (default 8192 for fit, 32768 for uneven; profiling runs use less)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
-    ap.add_argument("--workload", default="fit", choices=["fit", "uneven", "gradient"],
+    ap.add_argument("--train-samples", type=int, default=1 << 20, help="learned workload: training stamps")
+    ap.add_argument("--epochs", type=int, default=1, help="learned workload: training epochs")
+    ap.add_argument("--workload", default="fit", choices=["fit", "uneven", "gradient", "learned"],
                     help="fit: the LM fit of the SDSS-shaped batch (default); uneven: bulge+disk fits on stamps and "
                          "PSFs of mixed size; gradient: adjoint chi^2 gradient")
     args = ap.parse_args()
     if args.galaxies is None:
-        args.galaxies = 32768 if args.workload == "uneven" else 8192
+        args.galaxies = {"uneven": 32768, "learned": 65536}.get(args.workload, 8192)
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
@@ -598,6 +783,8 @@ def main():
         return run_gradient(args, world, rank, local)
     if args.workload == "uneven":
         return run_uneven(args, world, rank, local)
+    if args.workload == "learned":
+        return run_learned(args, world, rank, local)
     return run_gpu(args, world, rank, local)
 
 

@@ -477,15 +477,17 @@ def fit_with_fallback(fitter, spec, p_learned, p_default, image, sigma, mask, ps
     """LM from the learned start for every galaxy; the ones that do not converge from it are
     fitted again from the default start and keep the refit when it converged or reached a
     lower chi^2.  Equal stamps (image [G,H,W]) or an uneven batch (geom [G,3], packed arrays).
-    Returns (result dict of CUDA tensors, number of refits, galaxy evaluations of both fits)."""
+    Returns (result dict of CUDA tensors, info) with info = {"refits", "evals" (galaxy
+    evaluations of both fits), "fused_ms" (device time of their fused tile kernels)}."""
     import torch
     params = p_learned.clone().contiguous()
     res = {k: v.clone() for k, v in fitter.fit(params, image, sigma, mask, psf, opts).items()}
-    evals = _gm.gm_fit_last_stats()["galaxy_evals"]
+    st = _gm.gm_fit_last_stats()
+    info = {"refits": 0, "evals": st["galaxy_evals"], "fused_ms": st["fused_ms"]}
     bad = torch.nonzero(res["status"] != _gm.ST_CONVERGED).flatten()
     n = int(bad.numel())
     if n == 0:
-        return res, 0, evals
+        return res, info
     p2 = p_default[bad].clone().contiguous()
     if geom is None:
         sub = [None if t is None else t[bad].contiguous() for t in (image, sigma, mask, psf)]
@@ -498,9 +500,10 @@ def fit_with_fallback(fitter, spec, p_learned, p_default, image, sigma, mask, ps
         sub = [_take(image, po, idx), _take(sigma, po, idx), _take(mask, po, idx), _take(psf, ko, idx)]
         f2 = _gm.Fitter(spec, n, device=image.device, geom=g[idx])
     r2 = f2.fit(p2, sub[0], sub[1], sub[2], sub[3], opts)
-    evals += _gm.gm_fit_last_stats()["galaxy_evals"]
+    st = _gm.gm_fit_last_stats()
+    info = {"refits": n, "evals": info["evals"] + st["galaxy_evals"], "fused_ms": info["fused_ms"] + st["fused_ms"]}
     take = (r2["status"] == _gm.ST_CONVERGED) | (r2["chi2"] < res["chi2"][bad])
     idx_t = bad[take]
     for k in ("params", "chi2", "dof", "iters", "status", "sigma_p"):
         res[k][idx_t] = r2[k][take]
-    return res, n, evals
+    return res, info

@@ -78,7 +78,8 @@ def test_trained_network_saves_lm_iterations(C):
     f = gm.Fitter(rb.spec, G, device=dev, geom=rb.geom)
     d = {k: v.clone() for k, v in f.fit(p_def.clone(), image, sigma, None, psf, opts).items()}
     p_learn = C.learned_start(net, image.view(G, 128, 128), codec, rb.spec)
-    r, refits, _ = C.fit_with_fallback(f, rb.spec, p_learn, p_def, image, sigma, None, psf, opts, geom=rb.geom)
+    r, info = C.fit_with_fallback(f, rb.spec, p_learn, p_def, image, sigma, None, psf, opts, geom=rb.geom)
+    refits = info["refits"]
     it_d = d["iters"].float().mean().item()
     it_l = r["iters"].float().mean().item()
     conv_d = (d["status"] == 1).float().mean().item()
