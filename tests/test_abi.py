@@ -19,17 +19,21 @@ def lib():
     return gm.load()
 
 
-def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "gm.h")).read()
+def declared_symbols(header="gm.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(gm_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
-    decl = declared_symbols()
-    assert set(decl) == set(gm.EXPORTS), decl
-    for name in decl:
-        assert hasattr(lib, name), name
+    from paper_2404_07780_b300 import cnn
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert headers == ["gm.h", "gm_cnn.h"], headers
+    for header, bound in (("gm.h", gm.EXPORTS), ("gm_cnn.h", cnn.EXPORTS)):
+        decl = declared_symbols(header)
+        assert set(decl) == set(bound), (header, decl)
+        for name in decl:
+            assert hasattr(lib, name), name
     assert lib.gm_version() == 100
 
 
