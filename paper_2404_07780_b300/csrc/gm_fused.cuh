@@ -62,6 +62,8 @@ constexpr unsigned kWaitTries = 1u << 24;
 
 enum Mode { MODE_MODEL = 0, MODE_NORMAL = 1 };
 
+typedef unsigned long long u64;
+
 // Model description shared by both kernels (uniform over the batch).
 struct ChanMap {
   int n_comp;
@@ -119,8 +121,11 @@ struct FusedArgs {
   const float* sigma;
   const uint8_t* mask;
   const float* psf;
-  const float* cconst;
-  const float* scale;
+  const u64* psf_pad;        // [G][psf_stride]: each PSF as K rows of K+1 duplicated taps (pack2(v, v)),
+                             // padded as in shared memory, copied into s_psf by the bulk-copy unit
+  int psf_stride;            // u64 elements per galaxy in psf_pad (an even number)
+  const float* cconst;       // [G][n_comp][kCC]
+  const float* scale;        // [G][scale_stride(n_slots)]
   double* partial;           // [tile0_g + tile][nacc]
   float* model_out;          // stamp g from geo[g].pix
   float* comp_out;           // [n_comp] images per stamp from n_comp * geo[g].pix, or nullptr
@@ -133,8 +138,6 @@ struct ItemInfo {
   int valid, g, tile, pad;
   GalGeom geo;
 };
-
-typedef unsigned long long u64;
 
 __device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
   u64 d;
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
     const size_t pbase = (size_t)(G.plane >> 1);
     __syncthreads();
     for (int t = tid; t < m.n_comp * kCC; t += 256) s_cc[t] = A.cconst[(size_t)g * m.n_comp * kCC + t];
-    for (int t = tid; t < m.n_slots; t += 256) s_scale[t] = A.scale[(size_t)g * m.n_slots + t];
+    for (int t = tid; t < m.n_slots; t += 256) s_scale[t] = A.scale[(size_t)g * scale_stride(m.n_slots) + t];
     __syncthreads();
     for (int r = 0; r < kTilePix / 256; ++r) {
       const int pix = r * 256 + tid;
@@ -244,6 +247,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Contiguous global -> shared copy by the bulk-copy unit (16-byte aligned, size a 16-byte multiple).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, u64* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(reinterpret_cast<u64>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // Thread 0: read item `item` of this pass into *dst (valid = 0 past the end).
 __device__ __forceinline__ void fetch_item(const FusedArgs& A, int n_items, int item, ItemInfo* dst) {
   if (item >= n_items) {
@@ -257,8 +267,11 @@ __device__ __forceinline__ void fetch_item(const FusedArgs& A, int n_items, int 
   dst->geo = A.geo[it.x];
 }
 
-// Thread 0: issue the loads of pass `pass` of item I.
-__device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I, float2* s_in, u64* bar, int pass) {
+// Thread 0: issue the loads of pass `pass` of item I.  Pass 0 also brings the
+// galaxy's padded PSF rows into s_psf and its constants into the item's
+// constant buffers (s_cc, s_scale of `slot`), on the same mbarrier.
+__device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I, float2* s_in, u64* bar, int pass,
+                                           u64* s_psf, float* s_cc, float* s_scale) {
   const GalGeom& G = I.geo;
   const int K = G.K, c = (K - 1) / 2, cpad = c & 1;
   const int i0 = (I.tile / G.tiles_x) * kTile, j0 = (I.tile % G.tiles_x) * kTile;
@@ -272,11 +285,19 @@ __device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<u64>(map))
                  : "memory");
   }
-  // order this CTA's earlier generic-proxy reads of s_in before the async-proxy writes
+  const unsigned psf_bytes = (unsigned)K * (K + 1) * 8u;
+  const unsigned cc_bytes = (unsigned)A.m.n_comp * kCC * 4u;
+  const unsigned sc_bytes = (unsigned)scale_stride(A.m.n_slots) * 4u;
+  // order this CTA's earlier generic-proxy reads of the buffers before the async-proxy writes
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(bar, plane_bytes * npairs);
+  mbar_expect_tx(bar, plane_bytes * npairs + (pass == 0 ? psf_bytes + cc_bytes + sc_bytes : 0u));
   const int x = 2 * (j0 - c - cpad);  // even pair index: 16-byte aligned start
   for (int q = 0; q < npairs; ++q) tma_load_3d(s_in + (size_t)q * A.plane, map, x, i0 - c, G.z0 + first + q, bar);
+  if (pass == 0) {
+    bulk_load(s_psf, A.psf_pad + (size_t)I.g * A.psf_stride, psf_bytes, bar);
+    bulk_load(s_cc, A.cconst + (size_t)I.g * A.m.n_comp * kCC, cc_bytes, bar);
+    bulk_load(s_scale, A.scale + (size_t)I.g * scale_stride(A.m.n_slots), sc_bytes, bar);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -448,13 +469,14 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
   u64* s_psf = reinterpret_cast<u64*>(smem + A.off_psf);
   float2* s_in = reinterpret_cast<float2*>(smem + A.off_in);
   float* s_out = reinterpret_cast<float*>(smem + A.off_out);
-  float* s_cc = reinterpret_cast<float*>(smem + A.off_cc);
-  float* s_scale = reinterpret_cast<float*>(smem + A.off_scale);
+  float* s_cc0 = reinterpret_cast<float*>(smem + A.off_cc);        // [2][n_comp * kCC], alternating per item
+  float* s_scale0 = reinterpret_cast<float*>(smem + A.off_scale);  // [2][scale_stride(n_slots)]
   float* s_red = reinterpret_cast<float*>(smem + A.off_red);
   u64* bar = reinterpret_cast<u64*>(smem + A.off_bar);
   int* s_flag = reinterpret_cast<int*>(smem + A.off_bar + 8);
   ItemInfo* s_info = reinterpret_cast<ItemInfo*>(smem + A.off_info);  // [2], alternating per item
   const ChanMap& m = A.m;
+  const int cc_n = m.n_comp * kCC, sc_n = scale_stride(m.n_slots);
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int n_items = A.n_items_dev ? *A.n_items_dev : A.n_items;
@@ -465,7 +487,7 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
     fetch_item(A, n_items, blockIdx.x, &s_info[0]);
-    issue_pass(A, s_info[0], s_in, bar, 0);
+    issue_pass(A, s_info[0], s_in, bar, 0, s_psf, s_cc0, s_scale0);
   }
   unsigned phase = 0;
   int slot = 0;
@@ -485,20 +507,12 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
       const int nxt = (int)gridDim.x + atomicAdd(A.queue, 1);
       fetch_item(A, n_items, nxt, &s_info[slot ^ 1]);
     }
-    const int g = I.g;
     const int H = I.geo.H, W = I.geo.W, K = I.geo.K, rw = I.geo.rw;
-    const int c = (K - 1) / 2, K2 = K + 1, cpad = c & 1;
+    const int c = (K - 1) / 2;
     const int i0 = (I.tile / I.geo.tiles_x) * kTile, j0 = (I.tile % I.geo.tiles_x) * kTile;
-    const float* psf = A.psf + I.geo.psf;
-
-    for (int t2 = tid; t2 < m.n_comp * kCC; t2 += nthr) s_cc[t2] = A.cconst[(size_t)g * m.n_comp * kCC + t2];
-    for (int t2 = tid; t2 < m.n_slots; t2 += nthr) s_scale[t2] = A.scale[(size_t)g * m.n_slots + t2];
-    for (int t2 = tid; t2 < K * K2; t2 += nthr) {
-      const int a = t2 / K2, bb = t2 - a * K2;
-      const int b = bb - cpad;  // tap index in the unpadded PSF row
-      const float v = (b >= 0 && b < K) ? psf[a * K + b] : 0.f;
-      s_psf[t2] = pack2(v, v);
-    }
+    // this item's PSF rows (s_psf) and constants arrive with its first window
+    const float* s_cc = s_cc0 + slot * cc_n;
+    const float* s_scale = s_scale0 + slot * sc_n;
     // PSF rows whose 8 input rows (for this warp) all fall outside the stamp are skipped
     const int a_lo = max(0, c - i0 - row0 - 7);
     const int a_hi = min(K, c - i0 + H - row0);
@@ -533,8 +547,9 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
       else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
       __syncthreads();  // every warp is done reading the window
       if (tid == 0) {
-        if (pass + 1 < A.passes) issue_pass(A, I, s_in, bar, pass + 1);
-        else if (s_info[slot ^ 1].valid) issue_pass(A, s_info[slot ^ 1], s_in, bar, 0);
+        if (pass + 1 < A.passes) issue_pass(A, I, s_in, bar, pass + 1, s_psf, nullptr, nullptr);
+        else if (s_info[slot ^ 1].valid)
+          issue_pass(A, s_info[slot ^ 1], s_in, bar, 0, s_psf, s_cc0 + (slot ^ 1) * cc_n, s_scale0 + (slot ^ 1) * sc_n);
       }
       if (CPT == 2 && npair == 2) store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
       else if (npair == 1) store_pairs<1>(acc1, s_out, first + lp0, m.nch_conv, row, col0);

@@ -26,6 +26,10 @@ struct GalGeom {
 };
 static_assert(sizeof(GalGeom) == 64, "GalGeom is one 64-byte record");
 
+// Per-galaxy stride (floats) of the slot-scale array: n_slots rounded up to a
+// multiple of 4, so every galaxy's row is a 16-byte multiple (bulk copies).
+__host__ __device__ inline int scale_stride(int n_slots) { return (n_slots + 3) & ~3; }
+
 // Shared-memory row pitch (in float2) of a (32+K-1)-row correlation window:
 // >= K + 33 (the register window reads two columns past the last tap) and
 // == 2 mod 4, so the 8 lanes of a quarter warp (8 consecutive rows) hit

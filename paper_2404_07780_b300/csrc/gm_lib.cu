@@ -313,8 +313,8 @@ Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp, int cpt
   s.off_in = take((size_t)pp * plane_bytes, 128);
   s.off_psf = take((size_t)K * (K + 1) * 8, 16);
   s.off_out = take((size_t)pl.nch_tot * kTilePix * 4, 16);
-  s.off_cc = take((size_t)n_comp * kCC * 4, 16);
-  s.off_scale = take((size_t)n_slots * 4, 16);
+  s.off_cc = take((size_t)2 * n_comp * kCC * 4, 16);             // two items' constants
+  s.off_scale = take((size_t)2 * scale_stride(n_slots) * 4, 16);
   s.off_red = take((size_t)(s.threads / 32) * std::max(pl.nacc, 1) * 4, 16);
   s.off_bar = take(16, 16);
   s.off_info = take(2 * sizeof(ItemInfo), 16);
@@ -537,7 +537,8 @@ int plan_geom(const gm_batch* b, int ncp, bool tables, GeomPlan* gp) {
 // Workspace shared by the model, chi^2 and fit calls.  geo .. maps are
 // adjacent so that an uneven batch's host tables go over in one copy.
 struct WsCore {
-  size_t geo, order, items, maps, table_end, cconst, scale, planes, partial, err, queue, total;
+  size_t geo, order, items, maps, table_end, cconst, scale, psf_pad, planes, partial, err, queue, total;
+  int psf_stride;  // u64 elements per galaxy in psf_pad: K(K+1) for the batch's largest K
 };
 
 WsCore ws_core(const gm_model_desc* d, const GeomPlan& gp, int nacc) {
@@ -555,7 +556,9 @@ WsCore ws_core(const gm_model_desc* d, const GeomPlan& gp, int nacc) {
   w.maps = take(gp.ragged ? gp.cls.size() * sizeof(CUtensorMap) : 0);
   w.table_end = off;
   w.cconst = take(G * d->n_comp * kCC * 4);
-  w.scale = take(G * d->n_slots * 4);
+  w.scale = take(G * scale_stride(d->n_slots) * 4);
+  w.psf_stride = gp.K * (gp.K + 1);
+  w.psf_pad = take(G * (size_t)w.psf_stride * 8);
   w.planes = take(gp.plane_floats * 4);
   w.partial = take(nacc > 0 ? (size_t)gp.n_items * nacc * 8 : 0);
   w.err = take(4);
@@ -739,6 +742,32 @@ LMOpts lm_opts(const gm_fit_opts* o) {
   return L;
 }
 
+// Each galaxy's PSF as the fused kernel holds it in shared memory: K rows of
+// K+1 taps (one zero on the left when c = (K-1)/2 is odd, else on the right),
+// each tap duplicated into both halves of an f32x2 lane pair.
+__global__ void k_psf_pad(int G, const GalGeom* __restrict__ geo, const float* __restrict__ psf, int stride,
+                          unsigned long long* out) {
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    const int K = geo[g].K, K2 = K + 1, cpad = ((K - 1) / 2) & 1;
+    const float* p = psf + geo[g].psf;
+    for (int e = threadIdx.x; e < K * K2; e += blockDim.x) {
+      const int a = e / K2, b = e - a * K2 - cpad;
+      const float v = (b >= 0 && b < K) ? p[a * K + b] : 0.f;
+      out[(size_t)g * stride + e] = pack2(v, v);
+    }
+  }
+}
+
+int launch_psf_pad(int G, const GalGeom* geo, const float* psf, const WsCore& w, char* ws, const DevInfo& di,
+                   cudaStream_t st, FusedArgs* A) {
+  A->psf_pad = (const u64*)(ws + w.psf_pad);
+  A->psf_stride = w.psf_stride;
+  k_psf_pad<<<std::max(1, std::min(G, 8 * di.sms)), 256, 0, st>>>(G, geo, psf, w.psf_stride,
+                                                                    (unsigned long long*)(ws + w.psf_pad));
+  GM_LAUNCHED("k_psf_pad");
+  return GM_OK;
+}
+
 // LM iterations per CUDA-graph replay in gm_fit_batch (and between convergence polls).
 constexpr int kGraphIters = 4;
 
@@ -798,6 +827,7 @@ int setup_pass(int mode, const gm_model_desc* desc, const gm_batch* batch, const
   if ((rc = prepare_fused(mode, pc->pl, pc->sm, &pc->kf))) return rc;
   fill_args(pc->A, pc->pl, pc->sm);
   if ((rc = put_tables(pc->gp, pc->w, ws, pc->di, st, &pc->A))) return rc;
+  if ((rc = launch_psf_pad(G, pc->A.geo, batch->psf, pc->w, ws, pc->di, st, &pc->A))) return rc;
   FusedArgs& A = pc->A;
   float* cconst = (float*)(ws + pc->w.cconst);
   float* scale = (float*)(ws + pc->w.scale);
@@ -1000,6 +1030,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   FusedArgs A;
   fill_args(A, pl, sm);
   if ((rc = put_tables(gp, w.c, ws, di, st, &A))) return rc;
+  if ((rc = launch_psf_pad(G, A.geo, batch->psf, w.c, ws, di, st, &A))) return rc;
   A.queue = queue;
   A.image = batch->image;
   A.sigma = batch->sigma;
@@ -1129,7 +1160,7 @@ WsAdj ws_adj(const gm_model_desc* d, const gm_batch* b, int P) {
     return o;
   };
   w.cconst = take(G * d->n_comp * kCC * 4);
-  w.scale = take(G * d->n_slots * 4);
+  w.scale = take(G * scale_stride(d->n_slots) * 4);
   w.mplanes = take(pairs * b->H * w.Wp * 8);
   w.uplanes = take(pairs * b->H * w.Wp * 8);
   w.part_r = take(G * tiles * (1 + P) * 8);

@@ -82,7 +82,7 @@ __global__ void k_setup(const __grid_constant__ DescDev D, int G, const GalGeom*
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
   setup_galaxy(D, params + (size_t)g * D.n_slots, geo ? geo[g].H : H, use_log, cconst + (size_t)g * D.n_comp * kCC,
-               scale + (size_t)g * D.n_slots);
+               scale + (size_t)g * scale_stride(D.n_slots));
 }
 #endif  // GM_HOST_TU
 
@@ -165,7 +165,7 @@ __global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O
   else if (S.nused[g] - P <= 0) st = ST_NO_DOF;
   S.status[g] = st;
   if (st == ST_RUNNING) {
-    setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
+    setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * scale_stride(NS));
     queue_galaxy(S, 0, g, geo[g]);
   }
 }
@@ -331,7 +331,7 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
         pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
       }
       clamp_slots(D, pt);
-      setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * NS);
+      setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * scale_stride(NS));
       queue_galaxy(S, cur ^ 1, g, geo[g]);
     }
   }
