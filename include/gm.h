@@ -41,6 +41,9 @@
  *     GM_GAUSSIAN x0 y0 q pa I0 fwhm            (fwhm = 2 sqrt(2 ln 2) sigma)
  *     GM_MOFFAT   x0 y0 q pa I0 fwhm n
  *     GM_SKY      Isky                          (flat, Eq. sky_I)
+ *     GM_TILTED_SKY Isky kx ky                  (Isky + kx (x - W/2) + ky (y - H/2), the
+ *                                                 tilted sky of Eq. new_sky_I, measured from
+ *                                                 the stamp centre)
  *   The elliptical radius is r = sqrt(X^2 + (Y/q)^2), X = cos(pa) dx +
  *   sin(pa) dy, Y = -sin(pa) dx + cos(pa) dy, floored at 1e-4 px.  Two
  *   components that list the same slot share that parameter.
@@ -90,7 +93,8 @@ typedef enum {
   GM_KING = 4,
   GM_GAUSSIAN = 5,
   GM_MOFFAT = 6,
-  GM_SKY = 7
+  GM_SKY = 7,
+  GM_TILTED_SKY = 8
 } gm_kind;
 
 /* One light-profile component.  slot[k] is the parameter slot holding this
@@ -115,6 +119,15 @@ typedef struct {
   uint8_t is_log[GM_MAX_SLOTS];
   double lo[GM_MAX_SLOTS];
   double hi[GM_MAX_SLOTS];
+  /* Magnitudes instead of amplitudes (Sec. 4.1-4.2): when amp_is_mag[c] is 1, the
+   * amplitude slot of component c (Ie or I0) holds a magnitude m, and the
+   * amplitude is the one that gives the component the total flux
+   * 10^(-0.4 (m - mag_zero[c])): Eqs. sersicLtot, expdiskI0, ferrerI0 and
+   * moffatI0 with r_box = 1 (B = 0), and I0 = flux / (2 pi q sigma^2) for the
+   * Gaussian.  Not available for King and the skies (GM_E_UNSUPPORTED); the
+   * slot must not be fitted in log space. */
+  uint8_t amp_is_mag[GM_MAX_COMP];
+  double mag_zero[GM_MAX_COMP];
 } gm_model_desc;
 
 /* A batch of stamps.  The struct itself is host memory; image, sigma, mask
@@ -292,6 +305,33 @@ int gm_fit_batch(const gm_model_desc *desc, const gm_batch *batch, double *param
                  const gm_fit_opts *opts, double *chi2_out, int32_t *dof_out, int32_t *iters_out,
                  int32_t *status_out, double *sigma_p_out, void *workspace, size_t ws_bytes,
                  void *stream);
+
+/*
+ * gm_fit_adam -- the paper's own way of fitting (Sec. 5.1: gradient descent
+ * embedded in torch, Sec. 2 workflow; its examples run 1,000 iterations): Adam
+ * steps on chi^2 with the adjoint gradient of gm_grad_adjoint, for a fixed
+ * number of iterations, all galaxies at once.  Equal stamps only.
+ *   params_inout [n_gal][n_slots] FP64: the start in, the lowest-chi^2 point
+ *                evaluated out (in canonical form, as gm_fit_batch returns it)
+ *   chi2_out     [n_gal] FP64: chi^2 at that point
+ *   workspace    gm_fit_adam_workspace_bytes(desc, batch) bytes
+ * Steps are taken in internal coordinates (ln p for log slots, p otherwise)
+ * and clamped to the bounds; the step of a linear slot is scaled by
+ * max(|p at the start|, 1), so lr is a relative step for every slot.
+ * Synchronises the stream once at the end.  The paper gives no learning rate
+ * or moments for its optimiser: they are the caller's choice here.
+ */
+typedef struct {
+  int32_t n_iter;   /* gradient evaluations followed by a step */
+  double lr;        /* step size (relative, see above) */
+  double beta1;     /* first-moment decay, e.g. 0.9 */
+  double beta2;     /* second-moment decay, e.g. 0.999 */
+  double eps;       /* e.g. 1e-8 */
+} gm_adam_opts;
+
+size_t gm_fit_adam_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
+int gm_fit_adam(const gm_model_desc *desc, const gm_batch *batch, double *params_inout, const gm_adam_opts *opts,
+                double *chi2_out, void *workspace, size_t ws_bytes, void *stream);
 
 /*
  * Launch-shape tuning of the fused model+Jacobian pass (not part of the

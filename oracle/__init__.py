@@ -44,7 +44,7 @@ _SRC = os.path.join(_HERE, "gm_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_gm_oracle.so")
 _lib = None
 
-KIND_CODES = {"sersic": 1, "expdisk": 2, "ferrer": 3, "king": 4, "gaussian": 5, "moffat": 6, "sky": 7}
+KIND_CODES = {"sersic": 1, "expdisk": 2, "ferrer": 3, "king": 4, "gaussian": 5, "moffat": 6, "sky": 7, "tsky": 8}
 
 MAX_COMP = 8
 MAX_SLOTS = 24
@@ -72,6 +72,8 @@ class _Desc(ctypes.Structure):
         ("is_log", ctypes.c_int * MAX_SLOTS),
         ("lo", ctypes.c_double * MAX_SLOTS),
         ("hi", ctypes.c_double * MAX_SLOTS),
+        ("amp_is_mag", ctypes.c_int * MAX_COMP),
+        ("mag_zero", ctypes.c_double * MAX_COMP),
     ]
 
 
@@ -99,6 +101,8 @@ def _load():
         lib.or_gammp.argtypes = [ctypes.c_double, ctypes.c_double]
         lib.or_sersic_b.restype = ctypes.c_double
         lib.or_sersic_b.argtypes = [ctypes.c_double]
+        lib.or_mag_amplitude.restype = ctypes.c_double
+        lib.or_mag_amplitude.argtypes = [ctypes.c_int, P, ctypes.c_double]
         lib.or_component_value.restype = ctypes.c_double
         lib.or_component_value.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double]
@@ -150,6 +154,9 @@ def _desc(spec) -> _Desc:
         d.convolve[c] = 1 if comp.convolve else 0
         for k, s in enumerate(comp.slots):
             d.slot[c][k] = int(s)
+        if getattr(comp, "mag_zero", None) is not None:
+            d.amp_is_mag[c] = 1
+            d.mag_zero[c] = float(comp.mag_zero)
     d.n_slots = spec.n_slots
     for s in range(spec.n_slots):
         d.is_free[s] = 1 if spec.free[s] else 0
@@ -175,6 +182,12 @@ def gammp(a: float, x: float) -> float:
 def sersic_b(n: float) -> float:
     """nu_n of Eq. sersic-intensity: P(2n, nu_n) = 1/2 (Sec. 4.1)."""
     return _load().or_sersic_b(float(n))
+
+
+def mag_amplitude(kind: str, par, m0: float) -> float:
+    """Amplitude (Ie or I0) that gives the profile with parameters par, whose amplitude
+    slot holds a magnitude m, the total flux 10^(-0.4 (m - m0))."""
+    return _load().or_mag_amplitude(KIND_CODES[kind], _ptr(_f64(par)), float(m0))
 
 
 def component_value(kind: str, par, x: float, y: float) -> float:
@@ -299,3 +312,43 @@ def canonicalize(spec, params) -> np.ndarray:
 def max_threads() -> int:
     """OpenMP threads the oracle's batch loops use."""
     return _load().or_max_threads()
+
+
+def fit_adam(spec, params0, psf, image, sigma, mask=None, n_iter: int = 100, lr: float = 0.01, beta1: float = 0.9,
+             beta2: float = 0.999, eps: float = 1e-8):
+    """Gradient descent with Adam (Kingma & Ba 2015) on chi^2, the paper's own way of fitting
+    (Sec. 5.1), with the gradient -2 J^T W r of the finite-difference Jacobian.  Steps in
+    internal coordinates (ln p for log slots) scaled by 1 for log slots and max(|p0|, 1)
+    otherwise, clamped to the bounds; returns (lowest-chi^2 point evaluated in canonical
+    form, its chi^2) after n_iter steps and a final evaluation."""
+    p = np.clip(_f64(params0).copy(), spec.lo, spec.hi)
+    G, S = p.shape
+    free = np.array(spec.free, bool)
+    logs = np.array(spec.log, bool)
+    scale = np.where(logs, 1.0, np.maximum(np.abs(p), 1.0))
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    best = p.copy()
+    best_c2 = np.full(G, np.inf)
+    img, sig = _f64(image), _f64(sigma)
+    w = 1.0 / sig ** 2
+    if mask is not None:
+        w = w * (np.asarray(mask) == 0)
+    H, W = img.shape[1:]
+    for t in range(1, n_iter + 2):
+        M = model_images(spec, p, psf, H, W)
+        c2 = (w * (img - M) ** 2).sum((1, 2))
+        better = np.isfinite(c2) & (c2 < best_c2)
+        best[better], best_c2[better] = p[better], c2[better]
+        if t == n_iter + 1:
+            break
+        J = jacobian(spec, p, psf, H, W)  # [G][free][H][W], physical units
+        g = np.zeros_like(p)
+        g[:, free] = -2.0 * np.einsum("gfhw,ghw->gf", J, w * (img - M))
+        gu = np.where(logs, g * p, g)
+        m = beta1 * m + (1 - beta1) * gu
+        v = beta2 * v + (1 - beta2) * gu * gu
+        du = lr * scale * (m / (1 - beta1 ** t)) / (np.sqrt(v / (1 - beta2 ** t)) + eps)
+        u = np.where(logs, np.log(np.where(logs, p, 1.0)), p) - np.where(free, du, 0.0)
+        p = np.clip(np.where(logs, np.exp(np.where(logs, u, 0.0)), u), spec.lo, spec.hi)
+    return canonicalize(spec, best), best_c2

@@ -44,8 +44,12 @@
  *   GAUSSIAN x0 y0 q pa I0 fwhm
  *   MOFFAT   x0 y0 q pa I0 fwhm n
  *   SKY      Isky
+ *   TSKY     Isky kx ky   (tilted sky, Eq. new_sky_I: Isky + kx (x - W/2) + ky (y - H/2))
  */
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -56,6 +60,7 @@
 #define OR_GAUSSIAN 5
 #define OR_MOFFAT 6
 #define OR_SKY 7
+#define OR_TSKY 8
 
 #define OR_MAX_COMP 8
 #define OR_MAX_SLOTS 24
@@ -81,6 +86,8 @@ typedef struct {
   int is_log[OR_MAX_SLOTS];
   double lo[OR_MAX_SLOTS];
   double hi[OR_MAX_SLOTS];
+  int amp_is_mag[OR_MAX_COMP];  /* amplitude slot holds a magnitude ... */
+  double mag_zero[OR_MAX_COMP]; /* ... with this zero point */
 } or_desc;
 
 typedef struct {
@@ -100,6 +107,7 @@ int or_n_params(int kind) {
     case OR_GAUSSIAN: return 6;
     case OR_MOFFAT: return 7;
     case OR_SKY: return 1;
+    case OR_TSKY: return 3;
     default: return -1;
   }
 }
@@ -174,6 +182,7 @@ static double or_radius(double x, double y, double x0, double y0, double q, doub
  * component and ignored otherwise. */
 double or_component_value(int kind, const double *par, double nu, double x, double y) {
   if (kind == OR_SKY) return par[0]; /* Eq. (sky_I) */
+  if (kind == OR_TSKY) return par[0] + par[1] * x + par[2] * y; /* Eq. (new_sky_I); x, y from the stamp centre */
   double r = or_radius(x, y, par[0], par[1], par[2], par[3]);
   switch (kind) {
     case OR_SERSIC: { /* Eq. (sersic-intensity) */
@@ -210,17 +219,53 @@ double or_component_value(int kind, const double *par, double nu, double x, doub
   }
 }
 
+/* Amplitude of a component whose amplitude slot par[4] holds a magnitude m with
+ * zero point m0: the amplitude giving the total flux F = 10^(-0.4 (m - m0))
+ * (Sec. 4.1 Eq. sersicLtot, Sec. 4.2 Eqs. expdiskI0, ferrerI0, moffatI0, with
+ * r_box = 1 for B = 0; the Gaussian's flux 2 pi q sigma^2 I0).  NAN for the
+ * kinds without such a relation. */
+double or_mag_amplitude(int kind, const double *par, double m0) {
+  const double lnF = -0.4 * log(10.0) * (par[4] - m0);
+  const double q = par[2];
+  switch (kind) {
+    case OR_SERSIC: {
+      const double re = par[5], n = par[6], nu = or_sersic_b(n);
+      return exp(2.0 * n * log(nu) + lnF - log(2.0 * M_PI * q * re * re * n) - lgamma(2.0 * n) - nu);
+    }
+    case OR_EXPDISK: return exp(lnF) / (2.0 * M_PI * q * par[5] * par[5]);
+    case OR_FERRER: {
+      const double rout = par[5], a = par[6], b = par[7], c = 1.0 + 2.0 / (2.0 - b);
+      const double lnbeta = lgamma(a) + lgamma(c) - lgamma(a + c);
+      return exp(lnF - log(M_PI * q * rout * rout * a) - lnbeta);
+    }
+    case OR_GAUSSIAN: {
+      const double sig = par[5] / (2.0 * sqrt(2.0 * log(2.0)));
+      return exp(lnF) / (2.0 * M_PI * q * sig * sig);
+    }
+    case OR_MOFFAT: {
+      const double fw = par[5], n = par[6], rd = fw / (2.0 * sqrt(pow(2.0, 1.0 / n) - 1.0));
+      return (n - 1.0) * exp(lnF) / (M_PI * q * rd * rd);
+    }
+    default: return NAN;
+  }
+}
+
+/* Parameters of component c from the slot vector p, in profile units (a
+ * magnitude replaced by its amplitude). */
 static void or_gather(const or_desc *d, int c, const double *p, double *par) {
   int np = or_n_params(d->kind[c]);
   for (int k = 0; k < np; ++k) par[k] = p[d->slot[c][k]];
+  if (d->amp_is_mag[c]) par[4] = or_mag_amplitude(d->kind[c], par, d->mag_zero[c]);
 }
 
 /* Image of one component on the H x W stamp (no PSF). */
 void or_component_image(int kind, const double *par, int H, int W, double *out) {
   double nu = (kind == OR_SERSIC) ? or_sersic_b(par[6]) : 0.0;
+  /* the tilted sky is measured from the stamp centre (W/2, H/2) */
+  double xc = kind == OR_TSKY ? 0.5 * W : 0.0, yc = kind == OR_TSKY ? 0.5 * H : 0.0;
   for (int i = 0; i < H; ++i)
     for (int j = 0; j < W; ++j)
-      out[(size_t)i * W + j] = or_component_value(kind, par, nu, j + 0.5, H - 0.5 - i);
+      out[(size_t)i * W + j] = or_component_value(kind, par, nu, j + 0.5 - xc, H - 0.5 - i - yc);
 }
 
 /* Direct zero-padded cross-correlation with a K x K PSF, same-size output. */
@@ -388,8 +433,10 @@ static int or_scale_params(int kind, int *idx) {
 }
 
 /* Role of parameter k of a component: 1 axis ratio, 2 position angle, 3 scale length, 0 other. */
+static int or_flat(int kind) { return kind == OR_SKY || kind == OR_TSKY; }
+
 static int or_role(int kind, int k) {
-  if (kind == OR_SKY) return 0;
+  if (or_flat(kind)) return 0;
   if (k == 2) return 1;
   if (k == 3) return 2;
   int idx[2], n = or_scale_params(kind, idx);
@@ -408,13 +455,13 @@ static int or_role(int kind, int k) {
 static int or_canonical_q(const or_desc *d, double *p) {
   int changed = 0;
   for (int c = 0; c < d->n_comp; ++c) {
-    if (d->kind[c] == OR_SKY) continue;
+    if (or_flat(d->kind[c])) continue;
     int qs = d->slot[c][2];
     if (!(p[qs] > 1.0)) continue;
     int ok = 1;
     /* every use of a slot that some component of this q group uses as q, pa or scale */
     for (int c1 = 0; c1 < d->n_comp && ok; ++c1) {
-      if (d->kind[c1] == OR_SKY || d->slot[c1][2] != qs) continue;
+      if (or_flat(d->kind[c1]) || d->slot[c1][2] != qs) continue;
       int np1 = or_n_params(d->kind[c1]);
       for (int k1 = 0; k1 < np1 && ok; ++k1) {
         int r1 = or_role(d->kind[c1], k1);
@@ -424,7 +471,7 @@ static int or_canonical_q(const or_desc *d, double *p) {
           int np2 = or_n_params(d->kind[c2]);
           for (int k2 = 0; k2 < np2; ++k2) {
             if (d->slot[c2][k2] != s1) continue;
-            if (d->kind[c2] == OR_SKY || d->slot[c2][2] != qs || or_role(d->kind[c2], k2) != r1) ok = 0;
+            if (or_flat(d->kind[c2]) || d->slot[c2][2] != qs || or_role(d->kind[c2], k2) != r1) ok = 0;
           }
         }
       }
@@ -433,7 +480,7 @@ static int or_canonical_q(const or_desc *d, double *p) {
     double q = p[qs];
     int done[OR_MAX_SLOTS] = {0};
     for (int c1 = 0; c1 < d->n_comp; ++c1) {
-      if (d->kind[c1] == OR_SKY || d->slot[c1][2] != qs) continue;
+      if (or_flat(d->kind[c1]) || d->slot[c1][2] != qs) continue;
       int pas = d->slot[c1][3];
       if (!done[pas]) { p[pas] += 0.5 * M_PI; done[pas] = 1; }
       int idx[2], n = or_scale_params(d->kind[c1], idx);
@@ -452,7 +499,7 @@ static int or_canonical_q(const or_desc *d, double *p) {
 static void or_pa_slots(const or_desc *d, int *is_pa) {
   for (int s = 0; s < OR_MAX_SLOTS; ++s) is_pa[s] = 0;
   for (int c = 0; c < d->n_comp; ++c)
-    if (d->kind[c] != OR_SKY) is_pa[d->slot[c][3]] = 1;
+    if (!or_flat(d->kind[c])) is_pa[d->slot[c][3]] = 1;
 }
 
 /* Gauss-Newton decrement g^T A^-1 g: the chi^2 reduction a full Gauss-Newton

@@ -37,6 +37,8 @@ struct DescDev {
   double lo[kMaxSlots], hi[kMaxSlots];
   int n_canon;
   CanonGroup canon[kMaxComp];
+  int mag[kMaxComp];           // amplitude slot holds a magnitude ...
+  double mag_zero[kMaxComp];   // ... with this zero point
 };
 
 struct LMOpts {
@@ -64,12 +66,12 @@ struct LMState {
   unsigned long long* evals;  // [3]: galaxies evaluated over the passes, converged, iterations
 };
 
-__device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, int use_log, float* cc,
+__device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, int W, int use_log, float* cc,
                                     float* scale) {
   double par[8];
   for (int c = 0; c < D.n_comp; ++c) {
     for (int k = 0; k < D.np[c]; ++k) par[k] = p[D.slot[c][k]];
-    setup_component(D.kind[c], par, H, cc + c * kCC);
+    setup_component(D.kind[c], par, H, W, D.mag[c], D.mag_zero[c], cc + c * kCC);
   }
   for (int s = 0; s < D.n_slots; ++s) scale[s] = (use_log && D.is_log[s]) ? (float)p[s] : 1.f;
 }
@@ -77,12 +79,12 @@ __device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, in
 #ifdef GM_HOST_TU
 // Constants for every galaxy from caller parameters (gm_model, gm_chi2_grad).
 // Stamp heights from geo, or H for every galaxy when geo is nullptr.
-__global__ void k_setup(const __grid_constant__ DescDev D, int G, const GalGeom* __restrict__ geo, int H,
+__global__ void k_setup(const __grid_constant__ DescDev D, int G, const GalGeom* __restrict__ geo, int H, int W,
                         const double* __restrict__ params, int use_log, float* cconst, float* scale) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
-  setup_galaxy(D, params + (size_t)g * D.n_slots, geo ? geo[g].H : H, use_log, cconst + (size_t)g * D.n_comp * kCC,
-               scale + (size_t)g * scale_stride(D.n_slots));
+  setup_galaxy(D, params + (size_t)g * D.n_slots, geo ? geo[g].H : H, geo ? geo[g].W : W, use_log,
+               cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * scale_stride(D.n_slots));
 }
 #endif  // GM_HOST_TU
 
@@ -165,7 +167,8 @@ __global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O
   else if (S.nused[g] - P <= 0) st = ST_NO_DOF;
   S.status[g] = st;
   if (st == ST_RUNNING) {
-    setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * scale_stride(NS));
+    setup_galaxy(D, pt, geo[g].H, geo[g].W, 1, cconst + (size_t)g * D.n_comp * kCC,
+                 scale + (size_t)g * scale_stride(NS));
     queue_galaxy(S, 0, g, geo[g]);
   }
 }
@@ -331,7 +334,8 @@ __global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O
         pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
       }
       clamp_slots(D, pt);
-      setup_galaxy(D, pt, geo[g].H, 1, cconst + (size_t)g * D.n_comp * kCC, scale + (size_t)g * scale_stride(NS));
+      setup_galaxy(D, pt, geo[g].H, geo[g].W, 1, cconst + (size_t)g * D.n_comp * kCC,
+                   scale + (size_t)g * scale_stride(NS));
       queue_galaxy(S, cur ^ 1, g, geo[g]);
     }
   }
@@ -474,6 +478,90 @@ __global__ void k_chi2_grad_finish(const __grid_constant__ DescDev D, int G, con
     for (int f = 0; f < P; ++f)
       for (int h = 0; h < P; ++h) J[D.free_slot[f] * NS + D.free_slot[h]] = packed(acc + 1 + P, P, f, h);
   }
+}
+#endif  // GM_HOST_TU
+
+#ifdef GM_HOST_TU
+// ---------------------------------------------------------------------------
+// gradient-descent (Adam) fit on the adjoint gradient
+// ---------------------------------------------------------------------------
+struct AdamState {
+  double* m;          // [G][S] first moment, internal coordinates (ln p for log slots)
+  double* v;          // [G][S] second moment
+  double* scale;      // [G][S] step scale: 1 for log slots, max(|p0|, 1) otherwise
+  double* best;       // [G][S] lowest-chi^2 point evaluated (the caller's params)
+  double* best_chi2;  // [G]
+};
+
+__global__ void k_adam_init(const __grid_constant__ DescDev D, int G, double* params, double* cur, AdamState S) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int NS = D.n_slots;
+  double* p = params + (size_t)g * NS;
+  clamp_slots(D, p);
+  for (int s = 0; s < NS; ++s) {
+    cur[(size_t)g * NS + s] = p[s];
+    S.m[(size_t)g * NS + s] = 0.0;
+    S.v[(size_t)g * NS + s] = 0.0;
+    S.scale[(size_t)g * NS + s] = D.is_log[s] ? 1.0 : fmax(fabs(p[s]), 1.0);
+  }
+  S.best_chi2[g] = CUDART_INF;
+}
+
+__device__ inline void adam_keep_best(const DescDev& D, int g, const double* cur, double chi2, const AdamState& S) {
+  const int NS = D.n_slots;
+  if (isfinite(chi2) && chi2 < S.best_chi2[g]) {
+    S.best_chi2[g] = chi2;
+    for (int s = 0; s < NS; ++s) S.best[(size_t)g * NS + s] = cur[(size_t)g * NS + s];
+  }
+}
+
+// Keep the evaluated point if it is the best so far, then one Adam step (bias-corrected,
+// c1 = 1 - beta1^t, c2 = 1 - beta2^t) in internal coordinates, clamped to the bounds.
+__global__ void k_adam_step(const __grid_constant__ DescDev D, int G, double* cur, const double* __restrict__ grad,
+                            const double* __restrict__ chi2, AdamState S, double lr, double b1, double b2, double eps,
+                            double c1, double c2, int last) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int NS = D.n_slots;
+  adam_keep_best(D, g, cur, chi2[g], S);
+  double* p = cur + (size_t)g * NS;
+  for (int f = 0; f < D.P; ++f) {
+    const int s = D.free_slot[f];
+    const size_t e = (size_t)g * NS + s;
+    const double gp = grad[e];
+    const double gu = D.is_log[s] ? gp * p[s] : gp;  // d chi^2 / du
+    const double m = b1 * S.m[e] + (1.0 - b1) * gu;
+    const double v = b2 * S.v[e] + (1.0 - b2) * gu * gu;
+    S.m[e] = m;
+    S.v[e] = v;
+    const double du = lr * S.scale[e] * (m / c1) / (sqrt(v / c2) + eps);
+    p[s] = from_u(D, s, to_u(D, s, p[s]) - du);
+  }
+  clamp_slots(D, p);
+  (void)last;
+}
+
+// The final evaluation, then the best point in canonical form: an axis ratio
+// above 1 rewritten as 1/q with the position angles turned by pi/2 and the
+// scale lengths times q (the same image), position angles wrapped to [0, pi).
+__global__ void k_adam_finish(const __grid_constant__ DescDev D, int G, const double* cur,
+                              const double* __restrict__ chi2, AdamState S) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  adam_keep_best(D, g, cur, chi2[g], S);
+  const double pi = 3.14159265358979323846;
+  double* p = S.best + (size_t)g * D.n_slots;
+  for (int k = 0; k < D.n_canon; ++k) {
+    const CanonGroup& cg = D.canon[k];
+    const double q = p[cg.q_slot];
+    if (!(q > 1.0)) continue;
+    for (int i = 0; i < cg.n_scale; ++i) p[cg.scale[i]] *= q;
+    for (int i = 0; i < cg.n_pa; ++i) p[cg.pa[i]] += 0.5 * pi;
+    p[cg.q_slot] = 1.0 / q;
+  }
+  for (int s = 0; s < D.n_slots; ++s)
+    if (D.is_pa[s]) p[s] -= pi * floor(p[s] / pi);
 }
 #endif  // GM_HOST_TU
 

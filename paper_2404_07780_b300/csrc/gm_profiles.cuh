@@ -26,8 +26,16 @@ constexpr int kCC = 16;          // FP32 constants per component per galaxy
 constexpr float kRFloor = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
+constexpr double kPiD = 3.14159265358979323846;
 
-enum Kind { SERSIC = 1, EXPDISK = 2, FERRER = 3, KING = 4, GAUSSIAN = 5, MOFFAT = 6, SKY = 7 };
+enum Kind { SERSIC = 1, EXPDISK = 2, FERRER = 3, KING = 4, GAUSSIAN = 5, MOFFAT = 6, SKY = 7, TSKY = 8 };
+
+// Flag on the kind a tile kernel passes to eval_component: the amplitude slot
+// holds a magnitude (the chain-rule constants are in the component's cc).
+constexpr int kMagFlag = 16;
+
+// Flat and tilted sky: no centre, axis ratio or position angle.
+__host__ __device__ inline bool is_flat(int kind) { return kind == SKY || kind == TSKY; }
 
 __host__ __device__ inline int n_params(int kind) {
   switch (kind) {
@@ -38,6 +46,7 @@ __host__ __device__ inline int n_params(int kind) {
     case GAUSSIAN: return 6;
     case MOFFAT: return 7;
     case SKY: return 1;
+    case TSKY: return 3;
     default: return -1;
   }
 }
@@ -135,11 +144,30 @@ __device__ inline void sersic_nu_dnu(double n, double* nu_out, double* dnu_out) 
 //   GAUSSIAN I0, 1/sigma^2, 1/fwhm
 //   MOFFAT   I0, 1/rd, n, d ln rd / dn, 1/fwhm
 //   SKY      Isky
+//   TSKY     Isky, kx, ky; cc[0] = 0.5 - W/2, cc[1] = H/2 - 0.5 (pixel (i, j) lies at
+//            x - W/2 = j + cc[0], y - H/2 = cc[1] - i)
 // ---------------------------------------------------------------------------
-__device__ inline void setup_component(int kind, const double* par, int H, float* cc) {
+// Magnitude mode (mag = 1, par[4] = m): the amplitude is the one giving the total
+// flux F = 10^(-0.4 (m - m0)) (Eqs. sersicLtot, expdiskI0, ferrerI0, moffatI0,
+// r_box = 1; the Gaussian's flux 2 pi q sigma^2 I0), and the free cc entries
+// hold d ln(amplitude) / d p for the shape parameters p it depends on:
+//   SERSIC   cc[13] q, cc[14] Re, cc[15] n
+//   EXPDISK  cc[13] q, cc[14] rs
+//   FERRER   cc[12] q, cc[13] rout, cc[14] a, cc[15] b
+//   GAUSSIAN cc[13] q, cc[14] fwhm
+//   MOFFAT   cc[13] q, cc[14] fwhm, cc[15] n
+__device__ inline void setup_component(int kind, const double* par, int H, int W, int mag, double m0, float* cc) {
   for (int k = 0; k < kCC; ++k) cc[k] = 0.f;
   if (kind == SKY) {
     cc[8] = (float)par[0];
+    return;
+  }
+  if (kind == TSKY) {
+    cc[0] = (float)(0.5 - 0.5 * W);
+    cc[1] = (float)(0.5 * H - 0.5);
+    cc[8] = (float)par[0];
+    cc[9] = (float)par[1];
+    cc[10] = (float)par[2];
     return;
   }
   const double x0 = par[0], y0 = par[1], q = par[2], pa = par[3];
@@ -155,6 +183,7 @@ __device__ inline void setup_component(int kind, const double* par, int H, float
   cc[5] = (float)sin(pa);
   cc[6] = (float)(1.0 / q);
   cc[7] = (float)q;
+  const double lnF = mag ? -0.4 * log(10.0) * (par[4] - m0) : 0.0;  // ln of the total flux
   switch (kind) {
     case SERSIC: {
       const double n = par[6];
@@ -165,17 +194,39 @@ __device__ inline void setup_component(int kind, const double* par, int H, float
       sersic_nu_dnu(n, &nu, &dnu);
       cc[11] = (float)nu;
       cc[12] = (float)dnu;
+      if (mag) {
+        const double re = par[5];
+        cc[8] = (float)exp(2.0 * n * log(nu) + lnF - log(2.0 * kPiD * q * re * re * n) - lgamma(2.0 * n) - nu);
+        cc[13] = (float)(-1.0 / q);
+        cc[14] = (float)(-2.0 / re);
+        cc[15] = (float)(2.0 * log(nu) + 2.0 * n * dnu / nu - 1.0 / n - 2.0 * digamma_pos(2.0 * n) - dnu);
+      }
       break;
     }
     case EXPDISK:
       cc[8] = (float)par[4];
       cc[9] = (float)(1.0 / par[5]);
+      if (mag) {
+        cc[8] = (float)(exp(lnF) / (2.0 * kPiD * q * par[5] * par[5]));
+        cc[13] = (float)(-1.0 / q);
+        cc[14] = (float)(-2.0 / par[5]);
+      }
       break;
     case FERRER:
       cc[8] = (float)par[4];
       cc[9] = (float)(1.0 / par[5]);
       cc[10] = (float)par[6];
       cc[11] = (float)(2.0 - par[7]);
+      if (mag) {
+        const double rout = par[5], a = par[6], b = par[7], cb = 1.0 + 2.0 / (2.0 - b);
+        const double lnbeta = lgamma(a) + lgamma(cb) - lgamma(a + cb);
+        const double psi_acb = digamma_pos(a + cb);
+        cc[8] = (float)exp(lnF - log(kPiD * q * rout * rout * a) - lnbeta);
+        cc[12] = (float)(-1.0 / q);
+        cc[13] = (float)(-2.0 / rout);
+        cc[14] = (float)(-1.0 / a - (digamma_pos(a) - psi_acb));
+        cc[15] = (float)(-(digamma_pos(cb) - psi_acb) * 2.0 / ((2.0 - b) * (2.0 - b)));
+      }
       break;
     case KING: {
       const double rc = par[5], rt = par[6], al = par[7];
@@ -198,6 +249,11 @@ __device__ inline void setup_component(int kind, const double* par, int H, float
       cc[8] = (float)par[4];
       cc[9] = (float)(1.0 / (sig * sig));
       cc[10] = (float)(1.0 / fw);
+      if (mag) {
+        cc[8] = (float)(exp(lnF) / (2.0 * kPiD * q * sig * sig));
+        cc[13] = (float)(-1.0 / q);
+        cc[14] = (float)(-2.0 / fw);
+      }
       break;
     }
     case MOFFAT: {
@@ -209,6 +265,12 @@ __device__ inline void setup_component(int kind, const double* par, int H, float
       cc[10] = (float)n;
       cc[11] = (float)(t * log(2.0) / (2.0 * n * n * (t - 1.0)));  // d ln rd / dn
       cc[12] = (float)(1.0 / fw);
+      if (mag) {
+        cc[8] = (float)((n - 1.0) * exp(lnF) / (kPiD * q * rd * rd));
+        cc[13] = (float)(-1.0 / q);
+        cc[14] = (float)(-2.0 / fw);
+        cc[15] = (float)(1.0 / (n - 1.0) - 2.0 * t * log(2.0) / (2.0 * n * n * (t - 1.0)));
+      }
       break;
     }
     default:
@@ -222,9 +284,18 @@ __device__ inline void setup_component(int kind, const double* par, int H, float
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float eval_component(int kind, const float* __restrict__ cc, int i, int j,
                                                 float (&d)[8]) {
+  const bool mag = kind & kMagFlag;
+  kind &= kMagFlag - 1;
   if (kind == SKY) {
     d[0] = 1.f;
     return cc[8];
+  }
+  if (kind == TSKY) {
+    const float xs = (float)j + cc[0], ys = cc[1] - (float)i;
+    d[0] = 1.f;
+    d[1] = xs;
+    d[2] = ys;
+    return fmaf(cc[9], xs, fmaf(cc[10], ys, cc[8]));
   }
   const float dx = (float)(j + __float_as_int(cc[0])) + cc[2];
   const float dy = (float)(__float_as_int(cc[1]) - i) + cc[3];
@@ -344,6 +415,28 @@ __device__ __forceinline__ float eval_component(int kind, const float* __restric
     d[1] = gr * fmaf(-X, s, -Yq * c * iq);          // dI/dy0
     d[2] = gr * (-Yq * Yq * iq);                    // dI/dq
     d[3] = gr * (X * Yq * (q - iq));                // dI/dpa
+  }
+  if (mag) {
+    // amplitude A(m, shape): dI/dm = I d ln A / dm, and dI/dp gains I d ln A / dp
+    d[4] = -0.92103403719761836f * val;  // -0.4 ln 10
+    switch (kind) {
+      case FERRER:
+        d[2] = fmaf(val, cc[12], d[2]);
+        d[5] = fmaf(val, cc[13], d[5]);
+        d[6] = fmaf(val, cc[14], d[6]);
+        d[7] = fmaf(val, cc[15], d[7]);
+        break;
+      case SERSIC:
+      case MOFFAT:
+        d[6] = fmaf(val, cc[15], d[6]);
+        d[2] = fmaf(val, cc[13], d[2]);
+        d[5] = fmaf(val, cc[14], d[5]);
+        break;
+      default:  // EXPDISK, GAUSSIAN
+        d[2] = fmaf(val, cc[13], d[2]);
+        d[5] = fmaf(val, cc[14], d[5]);
+        break;
+    }
   }
   return val;
 }

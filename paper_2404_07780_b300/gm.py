@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libgm.so")
 
 MAX_COMP = 8
 MAX_SLOTS = 24
-KIND = {"sersic": 1, "expdisk": 2, "ferrer": 3, "king": 4, "gaussian": 5, "moffat": 6, "sky": 7}
+KIND = {"sersic": 1, "expdisk": 2, "ferrer": 3, "king": 4, "gaussian": 5, "moffat": 6, "sky": 7, "tsky": 8}
 STATUS = {0: "RUNNING", 1: "CONVERGED", 2: "MAX_ITER", 3: "STALLED", 4: "SINGULAR", 5: "NONFINITE",
           6: "BAD_INPUT", 7: "NO_DOF"}
 ST_CONVERGED = 1
@@ -31,7 +31,7 @@ ST_CONVERGED = 1
 EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model",
            "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch",
            "gm_fit_last_stats", "gm_chi2_grad_noalloc", "gm_grad_adjoint_workspace_bytes", "gm_grad_adjoint",
-           "gm_tune_set", "gm_tune_clear", "gm_tune_last_shape")
+           "gm_tune_set", "gm_tune_clear", "gm_tune_last_shape", "gm_fit_adam_workspace_bytes", "gm_fit_adam")
 
 
 class GMError(RuntimeError):
@@ -51,6 +51,8 @@ class gm_model_desc(ctypes.Structure):
         ("is_log", ctypes.c_uint8 * MAX_SLOTS),
         ("lo", ctypes.c_double * MAX_SLOTS),
         ("hi", ctypes.c_double * MAX_SLOTS),
+        ("amp_is_mag", ctypes.c_uint8 * MAX_COMP),
+        ("mag_zero", ctypes.c_double * MAX_COMP),
     ]
 
 
@@ -79,6 +81,16 @@ class gm_fit_opts(ctypes.Structure):
         ("lambda_down", ctypes.c_double),
         ("lambda_min", ctypes.c_double),
         ("lambda_max", ctypes.c_double),
+    ]
+
+
+class gm_adam_opts(ctypes.Structure):
+    _fields_ = [
+        ("n_iter", ctypes.c_int32),
+        ("lr", ctypes.c_double),
+        ("beta1", ctypes.c_double),
+        ("beta2", ctypes.c_double),
+        ("eps", ctypes.c_double),
     ]
 
 
@@ -144,6 +156,10 @@ def load() -> ctypes.CDLL:
         lib.gm_grad_adjoint.argtypes = [P, P, P, P, P, P, S, P]
         lib.gm_fit_last_stats.restype = ctypes.c_int
         lib.gm_fit_last_stats.argtypes = [P]
+        lib.gm_fit_adam_workspace_bytes.restype = S
+        lib.gm_fit_adam_workspace_bytes.argtypes = [P, P]
+        lib.gm_fit_adam.restype = ctypes.c_int
+        lib.gm_fit_adam.argtypes = [P, P, P, P, P, P, S, P]
         I32 = ctypes.c_int32
         lib.gm_tune_set.restype = ctypes.c_int
         lib.gm_tune_set.argtypes = [I32, I32, I32, I32, I32]
@@ -173,6 +189,9 @@ def desc_from_spec(spec) -> gm_model_desc:
         d.comp[c].convolve = 1 if comp.convolve else 0
         for k, s in enumerate(comp.slots):
             d.comp[c].slot[k] = int(s)
+        if comp.mag_zero is not None:
+            d.amp_is_mag[c] = 1
+            d.mag_zero[c] = float(comp.mag_zero)
     d.n_slots = spec.n_slots
     for s in range(spec.n_slots):
         d.is_free[s] = 1 if spec.free[s] else 0
@@ -322,6 +341,27 @@ def gm_grad_adjoint(spec_or_desc, params, image, sigma, mask, psf, want_grad: bo
     _check(lib.gm_grad_adjoint(ctypes.byref(d), ctypes.byref(b), _ptr(params), _ptr(chi2), _ptr(grad), _ptr(ws),
                                nbytes, _stream()), "gm_grad_adjoint")
     return chi2, grad
+
+
+def gm_fit_adam(spec_or_desc, params0, image, sigma, mask, psf, n_iter: int = 1000, lr: float = 0.01,
+                beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """Gradient-descent (Adam) fit on the adjoint gradient for n_iter steps; returns
+    {"params": lowest-chi^2 point evaluated [G,S], "chi2": [G]} (CUDA tensors)."""
+    import torch
+    lib = load()
+    d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
+    b, keep = make_batch(image, sigma, mask, psf)
+    params = _cuda_tensor(params0, torch.float64, "params").clone().contiguous()
+    dev = params.device
+    chi2 = torch.empty(b.n_gal, dtype=torch.float64, device=dev)
+    nbytes = lib.gm_fit_adam_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    if nbytes == 0 and b.n_gal > 0:
+        raise GMError(f"gm_fit_adam_workspace_bytes: {lib.gm_last_error().decode()}")
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    o = gm_adam_opts(n_iter, lr, beta1, beta2, eps)
+    _check(lib.gm_fit_adam(ctypes.byref(d), ctypes.byref(b), _ptr(params), ctypes.byref(o), _ptr(chi2), _ptr(ws),
+                           nbytes, _stream()), "gm_fit_adam")
+    return {"params": params, "chi2": chi2}
 
 
 class Chi2(object):

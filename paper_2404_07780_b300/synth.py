@@ -29,6 +29,7 @@ PARAM_NAMES = {
     "gaussian": ("x0", "y0", "q", "pa", "I0", "fwhm"),
     "moffat": ("x0", "y0", "q", "pa", "I0", "fwhm", "n"),
     "sky": ("Isky",),
+    "tsky": ("Isky", "kx", "ky"),
 }
 
 # Fitted in log space (positive scale and amplitude parameters) and default
@@ -68,6 +69,7 @@ class Component:
     kind: str
     convolve: bool
     slots: list[int]
+    mag_zero: float | None = None   # amplitude slot holds a magnitude with this zero point
 
 
 @dataclass
@@ -95,22 +97,26 @@ class ModelSpec:
         return self.names.index(name)
 
     def add(self, kind: str, prefix: str, H: int, W: int, convolve: bool = True,
-            shared: dict[str, int] | None = None, fixed: tuple[str, ...] = ()) -> "ModelSpec":
-        """Append a component; roles in `shared` reuse an existing slot."""
+            shared: dict[str, int] | None = None, fixed: tuple[str, ...] = (),
+            mag_zero: float | None = None) -> "ModelSpec":
+        """Append a component; roles in `shared` reuse an existing slot.  With mag_zero the
+        amplitude slot (Ie / I0) is a magnitude with that zero point (named `mag`, fitted
+        linearly, bounded to 0..40)."""
         shared = shared or {}
         slots = []
-        for role in PARAM_NAMES[kind]:
+        for k, role in enumerate(PARAM_NAMES[kind]):
             if role in shared:
                 slots.append(shared[role])
                 continue
-            lo, hi = _default_bounds(kind, role, H, W)
-            self.names.append(f"{prefix}.{role}")
+            is_mag = mag_zero is not None and k == 4
+            lo, hi = (0.0, 40.0) if is_mag else _default_bounds(kind, role, H, W)
+            self.names.append(f"{prefix}.{'mag' if is_mag else role}")
             self.free.append(role not in fixed)
-            self.log.append(role in _LOG_ROLES)
+            self.log.append(role in _LOG_ROLES and not is_mag)
             self.lo.append(lo)
             self.hi.append(hi)
             slots.append(len(self.names) - 1)
-        self.components.append(Component(kind, convolve, slots))
+        self.components.append(Component(kind, convolve, slots, mag_zero))
         return self
 
 

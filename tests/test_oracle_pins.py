@@ -509,3 +509,117 @@ def test_fit_through_q_one_ends_canonical():
     assert r["params"][0, 2] <= 1.0
     assert r["chi2"][0] == pytest.approx(near["chi2"][0], rel=1e-9)
     np.testing.assert_allclose(r["params"][0], near["params"][0], rtol=1e-5, atol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# tilted sky (Eq. new_sky_I), measured from the stamp centre
+# ---------------------------------------------------------------------------
+
+def test_tilted_sky_is_a_plane_about_the_stamp_centre():
+    H, W = 3, 4
+    a, kx, ky = 2.0, 0.5, -0.25
+    got = oracle.component_image("tsky", [a, kx, ky], H, W)
+    for i in range(H):
+        for j in range(W):
+            x, y = j + 0.5, H - 0.5 - i  # pixel centre, row 0 at the top
+            assert got[i, j] == pytest.approx(a + kx * (x - W / 2) + ky * (y - H / 2), abs=1e-15)
+    # the centre of the stamp carries the sky level: mean over a symmetric stamp
+    assert oracle.component_image("tsky", [a, kx, ky], 6, 8).mean() == pytest.approx(a, abs=1e-14)
+
+
+def test_tilted_sky_jacobian_is_one_x_y():
+    H, W, K = 9, 11, 3
+    spec = synth.ModelSpec().add("sersic", "gal", H, W).add("tsky", "sky", H, W, convolve=False)
+    p = np.array([[5.3, 4.1, 0.7, 0.4, 10.0, 2.0, 1.5, 1.0, 0.1, -0.2]])
+    psf = np.zeros((1, K, K))
+    psf[0, 1, 1] = 1.0
+    J = oracle.jacobian(spec, p, psf, H, W)[0]
+    x = (np.arange(W) + 0.5 - W / 2)[None, :] * np.ones((H, 1))
+    y = (H - 0.5 - np.arange(H) - H / 2)[:, None] * np.ones((1, W))
+    np.testing.assert_allclose(J[7], 1.0, atol=1e-8)
+    np.testing.assert_allclose(J[8], x, atol=1e-7)
+    np.testing.assert_allclose(J[9], y, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# magnitudes instead of amplitudes (Eqs. sersicLtot, expdiskI0, ferrerI0, moffatI0)
+# ---------------------------------------------------------------------------
+
+MAG_PROFILES = [
+    ("sersic", [0, 0, 0.6, 0, 17.0, 5.0, 2.5]),
+    ("sersic", [0, 0, 0.9, 0, 19.0, 3.0, 0.7]),
+    ("expdisk", [0, 0, 0.5, 0, 18.0, 4.0]),
+    ("ferrer", [0, 0, 0.4, 0, 18.5, 12.0, 2.0, 0.5]),
+    ("ferrer", [0, 0, 0.7, 0, 18.5, 9.0, 1.3, -1.0]),
+    ("gaussian", [0, 0, 0.8, 0, 16.0, 3.0]),
+    ("moffat", [0, 0, 0.7, 0, 16.5, 2.5, 3.0]),
+]
+
+
+@pytest.mark.parametrize("kind,par", MAG_PROFILES)
+def test_magnitude_sets_the_total_flux(kind, par):
+    # the amplitude derived from m gives the profile the flux 10^(-0.4 (m - m0)):
+    # 2 pi q int_0^inf I(r) r dr by quadrature along the major axis
+    m0 = 22.5
+    amp = oracle.mag_amplitude(kind, par, m0)
+    p = list(par)
+    p[4] = amp
+    rmax = p[5] if kind == "ferrer" else np.inf
+    f = lambda r: oracle.component_value(kind, p, r, 0.0) * r
+    flux = 2 * math.pi * par[2] * si.quad(f, 0, rmax, limit=400, epsabs=0, epsrel=1e-11)[0]
+    assert flux == pytest.approx(10 ** (-0.4 * (par[4] - m0)), rel=1e-8)
+
+
+def test_magnitude_has_no_relation_for_king_and_the_skies():
+    for kind, par in (("king", [0, 0, 1, 0, 18, 2, 10, 2]), ("sky", [18]), ("tsky", [18, 0, 0])):
+        assert math.isnan(oracle.mag_amplitude(kind, par + [0] * (8 - len(par)), 22.5))
+
+
+def test_model_in_magnitudes_equals_the_model_in_amplitudes():
+    H, W, K = 24, 20, 5
+    spec_m = synth.ModelSpec().add("sersic", "gal", H, W, mag_zero=22.5)
+    spec_a = synth.ModelSpec().add("sersic", "gal", H, W)
+    pm = np.array([[10.2, 11.7, 0.6, 0.3, 17.0, 4.0, 1.7]])
+    pa = pm.copy()
+    pa[0, 4] = oracle.mag_amplitude("sersic", pm[0], 22.5)
+    psf = np.zeros((1, K, K))
+    psf[0, 2, 2] = 1.0
+    np.testing.assert_allclose(oracle.model_images(spec_m, pm, psf, H, W), oracle.model_images(spec_a, pa, psf, H, W),
+                               rtol=1e-13)
+    # one magnitude brighter is a factor 10^0.4 in every pixel
+    pm2 = pm.copy()
+    pm2[0, 4] -= 1.0
+    np.testing.assert_allclose(oracle.model_images(spec_m, pm2, psf, H, W),
+                               10 ** 0.4 * oracle.model_images(spec_m, pm, psf, H, W), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# gradient-descent (Adam) fit, the paper's own optimiser
+# ---------------------------------------------------------------------------
+
+def _sky_case(seed=0, H=6, W=5):
+    rng = np.random.default_rng(seed)
+    spec = synth.ModelSpec().add("sky", "sky", H, W, convolve=False)
+    D = 3.0 + rng.normal(0, 1.0, (1, H, W))
+    S = rng.uniform(0.5, 2.0, (1, H, W))
+    psf = np.ones((1, 1, 1))
+    w = 1.0 / S ** 2
+    return spec, D, S, psf, float((w * D).sum() / w.sum())
+
+
+def test_adam_first_step_moves_by_lr_times_the_scale():
+    # step 1 from zero moments moves u by lr * scale * sign(-g): here up by lr * max(|p0|, 1)
+    spec, D, S, psf, pstar = _sky_case()
+    p0 = np.array([[pstar - 5.0]])
+    best, c2 = oracle.fit_adam(spec, p0, psf, D, S, n_iter=1, lr=0.1, eps=1e-12)
+    assert best[0, 0] == pytest.approx(p0[0, 0] + 0.1 * abs(p0[0, 0]), rel=1e-12)
+    w = 1.0 / S ** 2
+    assert c2[0] == pytest.approx(float((w * (D - best[0, 0]) ** 2).sum()), rel=1e-12)
+
+
+def test_adam_reaches_the_weighted_mean_of_a_flat_sky():
+    spec, D, S, psf, pstar = _sky_case(1)
+    best, _ = oracle.fit_adam(spec, np.array([[0.5]]), psf, D, S, n_iter=1500, lr=1e-2)
+    # steps are at most lr * max(|p0|, 1) = 0.01: the minimum, 2.4 away, is reached after ~240
+    # steps, and Adam with a constant rate then hovers within a few steps of it
+    assert abs(best[0, 0] - pstar) <= 3e-2
