@@ -334,6 +334,32 @@ int gm_fit_adam(const gm_model_desc *desc, const gm_batch *batch, double *params
                 double *chi2_out, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Bootstrap uncertainties (Sec. 5.2): every stamp's unmasked pixels are
+ * resampled with replacement -- as many draws as there are such pixels --
+ * and the galaxy is refitted from params_best; after n_boot replicates
+ *   sigma_boot[g][s] = sqrt((1/M) sum_i (p_i - mean)^2)
+ * over the M replicates whose refit CONVERGED (n_ok[g] = M; NaN when M = 0).
+ * Position angles are taken within pi/2 of the best fit's.  A pixel drawn c
+ * times enters chi^2 with weight c (sigma / sqrt(c)); undrawn pixels are
+ * masked.  The draws come from SplitMix64 (Steele, Lea & Flood 2014) as a
+ * counter-based generator: draw k of replicate b for galaxy g is the (k+1)-th
+ * output of the SplitMix64 stream starting at the state
+ * splitmix64(splitmix64(seed) ^ (g << 32 | b)), mapped to the pixel
+ * floor(r N / 2^64) of the galaxy's N unmasked pixels in row-major order.
+ * gm_bootstrap_counts writes the multiplicities of one replicate
+ * ([n_gal][H][W] uint32) without fitting.  Equal stamps only; opts as
+ * gm_fit_batch (NULL = defaults).  params_best, sigma_boot [n_gal][n_slots]
+ * FP64, n_ok [n_gal] int32 (may be NULL).  Synchronises the stream (inside
+ * each refit).
+ */
+size_t gm_bootstrap_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
+int gm_bootstrap_counts(const gm_model_desc *desc, const gm_batch *batch, uint64_t seed, int32_t replicate,
+                        uint32_t *counts, void *workspace, size_t ws_bytes, void *stream);
+int gm_bootstrap(const gm_model_desc *desc, const gm_batch *batch, const double *params_best, int32_t n_boot,
+                 uint64_t seed, const gm_fit_opts *opts, double *sigma_boot, int32_t *n_ok, void *workspace,
+                 size_t ws_bytes, void *stream);
+
+/*
  * Launch-shape tuning of the fused model+Jacobian pass (not part of the
  * paper's method: the hook of the autotuner in paper_2404_07780_b300/tune.py).
  *

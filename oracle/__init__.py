@@ -352,3 +352,64 @@ def fit_adam(spec, params0, psf, image, sigma, mask=None, n_iter: int = 100, lr:
         u = np.where(logs, np.log(np.where(logs, p, 1.0)), p) - np.where(free, du, 0.0)
         p = np.clip(np.where(logs, np.exp(np.where(logs, u, 0.0)), u), spec.lo, spec.hi)
     return canonicalize(spec, best), best_c2
+
+
+# ---------------------------------------------------------------------------
+# bootstrap (Sec. 5.2)
+# ---------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix64(z: int) -> int:
+    """The SplitMix64 output function (Steele, Lea & Flood 2014) applied to state z."""
+    z &= _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def bootstrap_counts(mask, seed: int, g: int, b: int) -> np.ndarray:
+    """Pixel multiplicities of replicate b of galaxy g: N draws, N = unmasked pixels; draw k is
+    the (k+1)-th SplitMix64 output from the state splitmix64(splitmix64(seed) ^ (g << 32 | b)),
+    mapped to the floor(r N / 2^64)-th unmasked pixel in row-major order."""
+    mask = np.asarray(mask)
+    used = np.flatnonzero(mask.ravel() == 0)
+    N = len(used)
+    key = splitmix64(splitmix64(seed) ^ ((g << 32) | b))
+    counts = np.zeros(mask.size, np.uint32)
+    for k in range(N):
+        r = splitmix64((key + (k + 1) * _GOLDEN) & _M64)
+        counts[used[(r * N) >> 64]] += 1
+    return counts.reshape(mask.shape)
+
+
+def bootstrap(spec, params_best, psf, image, sigma, mask=None, n_boot: int = 100, seed: int = 0,
+              opts: FitOptions | None = None):
+    """Bootstrap error bars: refit every replicate (pixel c drawn c times: weight c, i.e. sigma /
+    sqrt(c); undrawn pixels masked) from params_best; sigma^2 = (1/M) sum (p_i - mean)^2 over the
+    M converged refits, position angles taken within pi/2 of the best fit's.  Returns
+    (sigma_boot [G,S], M [G])."""
+    params_best = _f64(params_best)
+    G, S = params_best.shape
+    image, sigma = _f64(image), _f64(sigma)
+    base = np.zeros(image.shape, np.uint8) if mask is None else np.asarray(mask, np.uint8)
+    pa = np.array([n.endswith(".pa") for n in spec.names])
+    reps = []
+    for b in range(n_boot):
+        counts = np.stack([bootstrap_counts(base[g], seed, g, b) for g in range(G)])
+        m_eff = ((base != 0) | (counts == 0)).astype(np.uint8)
+        s_eff = np.where(counts > 0, sigma / np.sqrt(np.maximum(counts, 1)), 1.0)
+        r = fit(spec, params_best, psf, image, s_eff, m_eff, opts)
+        p = r["params"].copy()
+        d = p[:, pa] - params_best[:, pa]
+        p[:, pa] = params_best[:, pa] + d - np.pi * np.floor(d / np.pi + 0.5)
+        reps.append((p, r["status"] == 1))
+    sig = np.full((G, S), np.nan)
+    M = np.zeros(G, np.int32)
+    for g in range(G):
+        ps = np.array([p[g] for p, ok in reps if ok[g]])
+        M[g] = len(ps)
+        if len(ps):
+            sig[g] = np.sqrt(((ps - ps.mean(0)) ** 2).mean(0))
+    return sig, M

@@ -1397,6 +1397,240 @@ int gm_fit_adam(const gm_model_desc* desc, const gm_batch* batch, double* params
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// bootstrap (Sec. 5.2): pixels resampled with replacement, refits, scatter
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): the finaliser of a Weyl sequence with
+// increment 0x9E3779B97F4A7C15; used as a counter-based generator.
+__host__ __device__ inline unsigned long long splitmix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Draw k of replicate b for galaxy g: the (k+1)-th output of the SplitMix64
+// stream whose state starts at splitmix64(splitmix64(seed) ^ (g << 32 | b)).
+__device__ inline unsigned long long boot_draw(unsigned long long seed, unsigned long long g, unsigned long long b,
+                                               unsigned long long k) {
+  const unsigned long long key = splitmix64(splitmix64(seed) ^ ((g << 32) | b));
+  return splitmix64(key + (k + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+// Row-major list of each galaxy's unmasked pixels and their number (one block per galaxy).
+__global__ void k_boot_compact(int G, int HW, const uint8_t* __restrict__ mask, int* list, int* n_used) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < HW; t0 += blockDim.x) {
+      const int t = t0 + threadIdx.x;
+      const bool used = t < HW && !(mask && mask[(size_t)g * HW + t]);
+      const unsigned bal = __ballot_sync(0xffffffffu, used);
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      if (lane == 0) s_warp[warp] = __popc(bal);
+      __syncthreads();
+      int before = s_base;
+      for (int w = 0; w < warp; ++w) before += s_warp[w];
+      if (used) list[(size_t)g * HW + before + __popc(bal & ((1u << lane) - 1u))] = t;
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s_base += s_warp[w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) n_used[g] = s_base;
+    __syncthreads();
+  }
+}
+
+// Multiplicity of each pixel in replicate b: n_used draws, uniform over the unmasked pixels.
+__global__ void k_boot_draw(int G, int HW, const int* __restrict__ list, const int* __restrict__ n_used,
+                            unsigned long long seed, int b, unsigned* counts) {
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    const unsigned long long N = (unsigned long long)n_used[g];
+    for (unsigned long long k = threadIdx.x; k < N; k += blockDim.x) {
+      const unsigned long long r = boot_draw(seed, (unsigned long long)g, (unsigned long long)b, k);
+      const int idx = (int)__umul64hi(r, N);  // floor(r N / 2^64)
+      atomicAdd(&counts[(size_t)g * HW + list[(size_t)g * HW + idx]], 1u);
+    }
+  }
+}
+
+// The replicate as a batch: sigma / sqrt(count) on drawn pixels, masked where the count is 0.
+__global__ void k_boot_weights(long long n, const float* __restrict__ sigma, const uint8_t* __restrict__ mask,
+                               const unsigned* __restrict__ counts, float* sigma_eff, uint8_t* mask_eff) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const unsigned c = counts[t];
+    const bool off = c == 0u || (mask && mask[t]);
+    mask_eff[t] = off ? 1 : 0;
+    sigma_eff[t] = off ? 1.f : sigma[t] * rsqrtf((float)c);
+  }
+}
+
+// Running mean and sum of squared deviations (Welford) of the converged refits;
+// position angles taken within pi/2 of the best fit's.
+__global__ void k_boot_accum(const __grid_constant__ DescDev D, int G, const double* __restrict__ pb,
+                             const int* __restrict__ status, const double* __restrict__ best, double* mean,
+                             double* m2, int* n_ok) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G || status[g] != ST_CONVERGED) return;
+  const int NS = D.n_slots;
+  const int n = ++n_ok[g];
+  const double pi = 3.14159265358979323846;
+  for (int s = 0; s < NS; ++s) {
+    double x = pb[(size_t)g * NS + s];
+    if (D.is_pa[s]) {
+      const double ref = best[(size_t)g * NS + s];
+      x = ref + (x - ref) - pi * floor((x - ref) / pi + 0.5);
+    }
+    const size_t e = (size_t)g * NS + s;
+    const double d = x - mean[e];
+    mean[e] += d / n;
+    m2[e] += d * (x - mean[e]);
+  }
+}
+
+__global__ void k_boot_finish(int n, const double* __restrict__ m2, const int* __restrict__ n_ok, int NS,
+                              double* sigma_boot) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int c = n_ok[e / NS];
+  sigma_boot[e] = c > 0 ? sqrt(m2[e] / c) : CUDART_NAN;  // (1/M) sum (p_i - mean)^2 (Sec. 5.2)
+}
+
+struct WsBoot {
+  size_t fit, list, n_used, counts, sigma_eff, mask_eff, pb, chi2, dof, iters, status, mean, m2, n_ok, total;
+  size_t fit_bytes;
+};
+
+WsBoot ws_boot(const gm_model_desc* d, const gm_batch* b) {
+  WsBoot w;
+  w.fit_bytes = gm_fit_workspace_bytes(d, b);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  const size_t G = (size_t)std::max(b->n_gal, 0), N = G * (size_t)b->H * b->W, S = d->n_slots;
+  w.fit = take(w.fit_bytes);
+  w.list = take(N * 4);
+  w.n_used = take(G * 4);
+  w.counts = take(N * 4);
+  w.sigma_eff = take(N * 4);
+  w.mask_eff = take(N);
+  w.pb = take(G * S * 8);
+  w.chi2 = take(G * 8);
+  w.dof = take(G * 4);
+  w.iters = take(G * 4);
+  w.status = take(G * 4);
+  w.mean = take(G * S * 8);
+  w.m2 = take(G * S * 8);
+  w.n_ok = take(G * 4);
+  w.total = off;
+  return w;
+}
+
+// Counts of replicate b into ws counts (list and n_used already built).
+int boot_counts(const gm_batch* batch, const WsBoot& w, char* ws, unsigned long long seed, int b, cudaStream_t st) {
+  const int G = batch->n_gal, HW = batch->H * batch->W;
+  GM_CUDA(cudaMemsetAsync(ws + w.counts, 0, (size_t)G * HW * 4, st));
+  k_boot_draw<<<std::max(1, std::min(G, 1184)), 256, 0, st>>>(G, HW, (const int*)(ws + w.list),
+                                                              (const int*)(ws + w.n_used), seed, b,
+                                                              (unsigned*)(ws + w.counts));
+  GM_LAUNCHED("k_boot_draw");
+  return GM_OK;
+}
+
+int boot_check(const gm_model_desc* desc, const gm_batch* batch) {
+  int rc = check_batch(batch, true);
+  if (rc) return rc;
+  if ((rc = check_desc(desc))) return rc;
+  if (batch->geom) return fail(GM_E_UNSUPPORTED, "the bootstrap takes equal stamps only (batch.geom must be NULL)");
+  return GM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gm_bootstrap_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
+  if (!desc || !batch || check_desc(desc) || check_sizes(batch) || batch->geom) return 0;
+  return ws_boot(desc, batch).total;
+}
+
+int gm_bootstrap_counts(const gm_model_desc* desc, const gm_batch* batch, uint64_t seed, int32_t replicate,
+                        uint32_t* counts, void* workspace, size_t ws_bytes, void* stream) {
+  int rc = boot_check(desc, batch);
+  if (rc) return rc;
+  if (batch->n_gal == 0) return GM_OK;
+  if (!counts || replicate < 0) return fail(GM_E_INVAL, "counts is NULL or replicate < 0");
+  const WsBoot w = ws_boot(desc, batch);
+  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const int G = batch->n_gal, HW = batch->H * batch->W;
+  k_boot_compact<<<std::max(1, std::min(G, 1184)), 256, 0, st>>>(G, HW, batch->mask, (int*)(ws + w.list),
+                                                                 (int*)(ws + w.n_used));
+  GM_LAUNCHED("k_boot_compact");
+  if ((rc = boot_counts(batch, w, ws, seed, replicate, st))) return rc;
+  GM_CUDA(cudaMemcpyAsync(counts, ws + w.counts, (size_t)G * HW * 4, cudaMemcpyDeviceToDevice, st));
+  return GM_OK;
+}
+
+int gm_bootstrap(const gm_model_desc* desc, const gm_batch* batch, const double* params_best, int32_t n_boot,
+                 uint64_t seed, const gm_fit_opts* opts, double* sigma_boot, int32_t* n_ok, void* workspace,
+                 size_t ws_bytes, void* stream) {
+  int rc = boot_check(desc, batch);
+  if (rc) return rc;
+  if (batch->n_gal == 0) return GM_OK;
+  if (!params_best || !sigma_boot || n_boot < 1) return fail(GM_E_INVAL, "params_best/sigma_boot NULL or n_boot < 1");
+  const WsBoot w = ws_boot(desc, batch);
+  if (!workspace || ws_bytes < w.total) return fail(GM_E_NOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+  Plan pl;
+  if ((rc = make_plan(desc, MODE_NORMAL, false, &pl))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const int G = batch->n_gal, HW = batch->H * batch->W, NS = desc->n_slots;
+  const long long N = (long long)G * HW;
+  double* pb = (double*)(ws + w.pb);
+  double* mean = (double*)(ws + w.mean);
+  double* m2 = (double*)(ws + w.m2);
+  int* nok = (int*)(ws + w.n_ok);
+  GM_CUDA(cudaMemsetAsync(mean, 0, (size_t)G * NS * 8, st));
+  GM_CUDA(cudaMemsetAsync(m2, 0, (size_t)G * NS * 8, st));
+  GM_CUDA(cudaMemsetAsync(nok, 0, (size_t)G * 4, st));
+  k_boot_compact<<<std::max(1, std::min(G, 1184)), 256, 0, st>>>(G, HW, batch->mask, (int*)(ws + w.list),
+                                                                 (int*)(ws + w.n_used));
+  GM_LAUNCHED("k_boot_compact");
+  gm_batch rep = *batch;
+  rep.sigma = (const float*)(ws + w.sigma_eff);
+  rep.mask = (const uint8_t*)(ws + w.mask_eff);
+  const int ngrid = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, 4096));
+  for (int b = 0; b < n_boot; ++b) {
+    if ((rc = boot_counts(batch, w, ws, (unsigned long long)seed, b, st))) return rc;
+    k_boot_weights<<<ngrid, 256, 0, st>>>(N, batch->sigma, batch->mask, (const unsigned*)(ws + w.counts),
+                                          (float*)(ws + w.sigma_eff), (uint8_t*)(ws + w.mask_eff));
+    GM_LAUNCHED("k_boot_weights");
+    GM_CUDA(cudaMemcpyAsync(pb, params_best, (size_t)G * NS * 8, cudaMemcpyDeviceToDevice, st));
+    if ((rc = gm_fit_batch(desc, &rep, pb, opts, (double*)(ws + w.chi2), (int32_t*)(ws + w.dof),
+                           (int32_t*)(ws + w.iters), (int32_t*)(ws + w.status), nullptr, ws + w.fit, w.fit_bytes,
+                           stream)))
+      return rc;
+    k_boot_accum<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, G, pb, (const int*)(ws + w.status), params_best, mean, m2,
+                                                  nok);
+    GM_LAUNCHED("k_boot_accum");
+  }
+  k_boot_finish<<<(G * NS + 255) / 256, 256, 0, st>>>(G * NS, m2, nok, NS, sigma_boot);
+  GM_LAUNCHED("k_boot_finish");
+  if (n_ok) GM_CUDA(cudaMemcpyAsync(n_ok, nok, (size_t)G * 4, cudaMemcpyDeviceToDevice, st));
+  return GM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};

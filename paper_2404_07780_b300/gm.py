@@ -31,7 +31,8 @@ ST_CONVERGED = 1
 EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model",
            "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch",
            "gm_fit_last_stats", "gm_chi2_grad_noalloc", "gm_grad_adjoint_workspace_bytes", "gm_grad_adjoint",
-           "gm_tune_set", "gm_tune_clear", "gm_tune_last_shape", "gm_fit_adam_workspace_bytes", "gm_fit_adam")
+           "gm_tune_set", "gm_tune_clear", "gm_tune_last_shape", "gm_fit_adam_workspace_bytes", "gm_fit_adam",
+           "gm_bootstrap_workspace_bytes", "gm_bootstrap_counts", "gm_bootstrap")
 
 
 class GMError(RuntimeError):
@@ -156,6 +157,12 @@ def load() -> ctypes.CDLL:
         lib.gm_grad_adjoint.argtypes = [P, P, P, P, P, P, S, P]
         lib.gm_fit_last_stats.restype = ctypes.c_int
         lib.gm_fit_last_stats.argtypes = [P]
+        lib.gm_bootstrap_workspace_bytes.restype = S
+        lib.gm_bootstrap_workspace_bytes.argtypes = [P, P]
+        lib.gm_bootstrap_counts.restype = ctypes.c_int
+        lib.gm_bootstrap_counts.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int32, P, P, S, P]
+        lib.gm_bootstrap.restype = ctypes.c_int
+        lib.gm_bootstrap.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_uint64, P, P, P, P, S, P]
         lib.gm_fit_adam_workspace_bytes.restype = S
         lib.gm_fit_adam_workspace_bytes.argtypes = [P, P]
         lib.gm_fit_adam.restype = ctypes.c_int
@@ -362,6 +369,46 @@ def gm_fit_adam(spec_or_desc, params0, image, sigma, mask, psf, n_iter: int = 10
     _check(lib.gm_fit_adam(ctypes.byref(d), ctypes.byref(b), _ptr(params), ctypes.byref(o), _ptr(chi2), _ptr(ws),
                            nbytes, _stream()), "gm_fit_adam")
     return {"params": params, "chi2": chi2}
+
+
+def _boot_ws(lib, d, b, dev):
+    import torch
+    nbytes = lib.gm_bootstrap_workspace_bytes(ctypes.byref(d), ctypes.byref(b))
+    if nbytes == 0 and b.n_gal > 0:
+        raise GMError(f"gm_bootstrap_workspace_bytes: {lib.gm_last_error().decode()}")
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev), nbytes
+
+
+def gm_bootstrap_counts(spec_or_desc, image, sigma, mask, psf, seed: int, replicate: int):
+    """Pixel multiplicities [G,H,W] (int32 view of uint32) of one bootstrap replicate."""
+    import torch
+    lib = load()
+    d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
+    b, keep = make_batch(image, sigma, mask, psf)
+    dev = keep[0].device
+    counts = torch.empty((b.n_gal, b.H, b.W), dtype=torch.int32, device=dev)
+    ws, nbytes = _boot_ws(lib, d, b, dev)
+    _check(lib.gm_bootstrap_counts(ctypes.byref(d), ctypes.byref(b), seed, replicate, _ptr(counts), _ptr(ws), nbytes,
+                                   _stream()), "gm_bootstrap_counts")
+    return counts
+
+
+def gm_bootstrap(spec_or_desc, params_best, image, sigma, mask, psf, n_boot: int = 100, seed: int = 0,
+                 opts: FitOptions | None = None):
+    """Bootstrap error bars (Sec. 5.2): (sigma_boot [G,S], converged replicates [G])."""
+    import torch
+    lib = load()
+    d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
+    b, keep = make_batch(image, sigma, mask, psf)
+    params_best = _cuda_tensor(params_best, torch.float64, "params_best")
+    dev = params_best.device
+    sig = torch.empty((b.n_gal, d.n_slots), dtype=torch.float64, device=dev)
+    nok = torch.empty(b.n_gal, dtype=torch.int32, device=dev)
+    ws, nbytes = _boot_ws(lib, d, b, dev)
+    o = (opts or FitOptions()).to_c()
+    _check(lib.gm_bootstrap(ctypes.byref(d), ctypes.byref(b), _ptr(params_best), n_boot, seed, ctypes.byref(o),
+                            _ptr(sig), _ptr(nok), _ptr(ws), nbytes, _stream()), "gm_bootstrap")
+    return sig, nok
 
 
 class Chi2(object):

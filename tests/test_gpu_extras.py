@@ -229,3 +229,45 @@ def test_adam_fit_follows_the_oracle(gm):
     # gradient descent lowers chi^2 from the start
     c2_0 = oracle.chi2(spec, b.init, c.psf.astype(np.float64), c.image.astype(np.float64), c.sigma.astype(np.float64))
     assert (got["chi2"] < c2_0).all()
+
+
+# ---------------------------------------------------------------------------
+# bootstrap uncertainties
+# ---------------------------------------------------------------------------
+
+def test_bootstrap_counts_are_bit_exact(gm):
+    import torch
+    G, H, W = 3, 40, 50
+    rng = np.random.default_rng(51)
+    mask = (rng.uniform(size=(G, H, W)) < 0.2).astype(np.uint8)
+    img = torch.zeros((G, H, W), device="cuda")
+    sig = torch.ones((G, H, W), device="cuda")
+    psf = torch.ones((G, 1, 1), device="cuda")
+    spec = synth.single_sersic_sky(H, W)
+    for b in (0, 7):
+        got = _np(gm.gm_bootstrap_counts(spec, img, sig, torch.from_numpy(mask).cuda(), psf, seed=99, replicate=b))
+        for g in range(G):
+            np.testing.assert_array_equal(got[g], oracle.bootstrap_counts(mask[g], 99, g, b).astype(np.int32))
+
+
+def test_bootstrap_error_bars_match_oracle(gm):
+    import torch
+    H, W, K = 40, 40, 9
+    b = synth.draw_small(seed=52, G=3, H=H, W=W, K=K)
+    b.truth[:, 4] = np.maximum(b.truth[:, 4], 20.0)  # bright enough for a well-defined minimum
+    c = _case(b.spec, b.truth, H, W, K, seed=53)
+    opts = dict(tol=1e-12, xtol=1e-10, gtol=1e-13, max_iter=200)
+    best = oracle.fit(b.spec, b.truth, c.psf.astype(np.float64), c.image.astype(np.float64),
+                      c.sigma.astype(np.float64), None, oracle.FitOptions(**opts))["params"]
+    t = c.torch()
+    sig, nok = gm.gm_bootstrap(b.spec, torch.from_numpy(best).cuda(), t["image"], t["sigma"], None, t["psf"], n_boot=4,
+                               seed=5, opts=gm.FitOptions(**opts))
+    sig, nok = _np(sig), _np(nok)
+    rsig, rM = oracle.bootstrap(b.spec, best, c.psf.astype(np.float64), c.image.astype(np.float64),
+                                c.sigma.astype(np.float64), None, n_boot=4, seed=5, opts=oracle.FitOptions(**opts))
+    np.testing.assert_array_equal(nok, rM)
+    free = np.array(b.spec.free, bool)
+    # every replicate's refit matches the oracle's to the fit tolerance; the spread of 4 refits inherits it
+    tol = 0.05 * rsig[:, free] + 1e-4 * np.maximum(np.abs(best[:, free]), 1.0)
+    assert (np.abs(sig[:, free] - rsig[:, free]) <= tol).all(), (np.abs(sig - rsig)[:, free] / tol).max()
+    assert (sig[:, ~free] == 0).all()

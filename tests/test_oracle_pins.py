@@ -623,3 +623,46 @@ def test_adam_reaches_the_weighted_mean_of_a_flat_sky():
     # steps are at most lr * max(|p0|, 1) = 0.01: the minimum, 2.4 away, is reached after ~240
     # steps, and Adam with a constant rate then hovers within a few steps of it
     assert abs(best[0, 0] - pstar) <= 3e-2
+
+
+# ---------------------------------------------------------------------------
+# bootstrap: SplitMix64 and the resampling
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_reference_outputs():
+    # the published generator from state 0: the first outputs of its Weyl sequence
+    s, out = 0, []
+    for _ in range(4):
+        s = (s + 0x9E3779B97F4A7C15) & ((1 << 64) - 1)
+        out.append(oracle.splitmix64(s))
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+
+
+def test_bootstrap_counts_are_a_resampling_with_replacement():
+    mask = np.zeros((40, 50), np.uint8)
+    mask[5:15, 10:30] = 1
+    N = int((mask == 0).sum())
+    c = oracle.bootstrap_counts(mask, seed=7, g=3, b=11)
+    assert c.sum() == N and (c[mask != 0] == 0).all()
+    # multinomial with equal cells: P(count = 0) -> exp(-1), mean count 1, variance 1 - 1/N
+    frac0 = float((c[mask == 0] == 0).mean())
+    assert abs(frac0 - math.exp(-1)) < 4 * math.sqrt(math.exp(-1) * (1 - math.exp(-1)) / N)
+    assert abs(c[mask == 0].var() - (1 - 1 / N)) < 0.1
+    # replicates and galaxies draw differently; the same (seed, g, b) draws the same
+    assert not np.array_equal(c, oracle.bootstrap_counts(mask, seed=7, g=3, b=12))
+    assert not np.array_equal(c, oracle.bootstrap_counts(mask, seed=7, g=4, b=11))
+    assert np.array_equal(c, oracle.bootstrap_counts(mask, seed=7, g=3, b=11))
+
+
+def test_bootstrap_of_a_flat_sky_is_the_error_of_the_weighted_mean():
+    # sky-only model with equal sigma: the refit is the weighted mean of the resampled pixels,
+    # whose spread over replicates is close to the standard error of the mean of the data
+    H, W = 12, 12
+    rng = np.random.default_rng(5)
+    spec = synth.ModelSpec().add("sky", "sky", H, W, convolve=False)
+    D = 3.0 + rng.normal(0, 1.0, (1, H, W))
+    S = np.ones((1, H, W))
+    sig, M = oracle.bootstrap(spec, np.array([[D.mean()]]), np.ones((1, 1, 1)), D, S, n_boot=200, seed=1)
+    assert M[0] == 200
+    sem = D.std() / math.sqrt(H * W)
+    assert abs(sig[0, 0] - sem) <= 0.15 * sem
