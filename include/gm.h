@@ -45,7 +45,8 @@
  *                                                 tilted sky of Eq. new_sky_I, measured from
  *                                                 the stamp centre)
  *   The elliptical radius is r = sqrt(X^2 + (Y/q)^2), X = cos(pa) dx +
- *   sin(pa) dy, Y = -sin(pa) dx + cos(pa) dy, floored at 1e-4 px.  Two
+ *   sin(pa) dy, Y = -sin(pa) dx + cos(pa) dy, floored at 1e-4 px (the general
+ *   form with boxiness: gm_model_desc.has_box).  Two
  *   components that list the same slot share that parameter.
  * Errors.  Every entry point returns GM_OK (0) or a negative GM_E_* code and
  *   never aborts; gm_last_error() returns a message for the calling thread's
@@ -128,6 +129,13 @@ typedef struct {
    * slot must not be fitted in log space. */
   uint8_t amp_is_mag[GM_MAX_COMP];
   double mag_zero[GM_MAX_COMP];
+  /* Boxiness (Eqs. r-rmin): when has_box[c] is 1 the component's radius is
+   * r = (|X|^(B+2) + |Y/q|^(B+2))^(1/(B+2)) with B in slot comp[c].slot[np], np the
+   * profile's parameter count above (B = 0 is the ellipse; B > 0 boxy, B < 0
+   * discy; the slot's lower bound must exceed -2), and a magnitude amplitude
+   * carries r_box = pi (2+B) / (2 beta(1/(2+B), 1/(2+B))) (Eq. rbox).  Sersic,
+   * exponential disk, Gaussian and Moffat only (GM_E_UNSUPPORTED otherwise). */
+  uint8_t has_box[GM_MAX_COMP];
 } gm_model_desc;
 
 /* A batch of stamps.  The struct itself is host memory; image, sigma, mask

@@ -74,6 +74,7 @@ class _Desc(ctypes.Structure):
         ("hi", ctypes.c_double * MAX_SLOTS),
         ("amp_is_mag", ctypes.c_int * MAX_COMP),
         ("mag_zero", ctypes.c_double * MAX_COMP),
+        ("has_box", ctypes.c_int * MAX_COMP),
     ]
 
 
@@ -104,8 +105,10 @@ def _load():
         lib.or_mag_amplitude.restype = ctypes.c_double
         lib.or_mag_amplitude.argtypes = [ctypes.c_int, P, ctypes.c_double]
         lib.or_component_value.restype = ctypes.c_double
-        lib.or_component_value.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_double,
+        lib.or_component_value.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double]
+        lib.or_rbox.restype = ctypes.c_double
+        lib.or_rbox.argtypes = [ctypes.c_double]
         lib.or_component_image.restype = None
         lib.or_component_image.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P]
         lib.or_correlate.restype = None
@@ -157,6 +160,7 @@ def _desc(spec) -> _Desc:
         if getattr(comp, "mag_zero", None) is not None:
             d.amp_is_mag[c] = 1
             d.mag_zero[c] = float(comp.mag_zero)
+        d.has_box[c] = 1 if getattr(comp, "boxy", False) else 0
     d.n_slots = spec.n_slots
     for s in range(spec.n_slots):
         d.is_free[s] = 1 if spec.free[s] else 0
@@ -190,11 +194,16 @@ def mag_amplitude(kind: str, par, m0: float) -> float:
     return _load().or_mag_amplitude(KIND_CODES[kind], _ptr(_f64(par)), float(m0))
 
 
-def component_value(kind: str, par, x: float, y: float) -> float:
-    """One profile's intensity at the point (x, y) (pixel units)."""
+def component_value(kind: str, par, x: float, y: float, B: float = 0.0) -> float:
+    """One profile's intensity at the point (x, y) (pixel units), boxiness B."""
     par = _f64(par)
     nu = sersic_b(par[6]) if kind == "sersic" else 0.0
-    return _load().or_component_value(KIND_CODES[kind], _ptr(par), nu, float(x), float(y))
+    return _load().or_component_value(KIND_CODES[kind], _ptr(par), nu, float(B), float(x), float(y))
+
+
+def rbox(B: float) -> float:
+    """Eq. rbox: pi (2+B) / (2 beta(1/(2+B), 1/(2+B)))."""
+    return _load().or_rbox(float(B))
 
 
 def component_image(kind: str, par, H: int, W: int) -> np.ndarray:

@@ -88,6 +88,7 @@ typedef struct {
   double hi[OR_MAX_SLOTS];
   int amp_is_mag[OR_MAX_COMP];  /* amplitude slot holds a magnitude ... */
   double mag_zero[OR_MAX_COMP]; /* ... with this zero point */
+  int has_box[OR_MAX_COMP];     /* boxiness B in slot[or_n_params(kind)] */
 } or_desc;
 
 typedef struct {
@@ -168,22 +169,38 @@ double or_sersic_b(double n) {
   return 0.5 * (lo + hi);
 }
 
-/* Elliptical radius of Eqs. (r)-(rmin) with B = 0, floored at OR_RFLOOR. */
-static double or_radius(double x, double y, double x0, double y0, double q, double pa) {
+/* Radius of Eqs. (r)-(rmin), floored at OR_RFLOOR: with r_maj = |X|, r_min = |Y|
+ * (the absolute values read around the rotated coordinates),
+ * r = (r_maj^(B+2) + (r_min/q)^(B+2))^(1/(B+2)); B = 0 is the ellipse. */
+static double or_radius(double x, double y, double x0, double y0, double q, double pa, double B) {
   double dx = x - x0, dy = y - y0;
   double X = cos(pa) * dx + sin(pa) * dy;
   double Y = -sin(pa) * dx + cos(pa) * dy;
-  double r = sqrt(X * X + (Y / q) * (Y / q));
+  double r;
+  if (B == 0.0) {
+    r = sqrt(X * X + (Y / q) * (Y / q));
+  } else {
+    double p = B + 2.0;
+    r = pow(pow(fabs(X), p) + pow(fabs(Y / q), p), 1.0 / p);
+  }
   return r < OR_RFLOOR ? OR_RFLOOR : r;
+}
+
+/* Eq. (rbox): the flux correction of a boxy ellipse, pi / (area of the unit
+ * superellipse |x|^(B+2) + |y|^(B+2) = 1). */
+double or_rbox(double B) {
+  double a = 1.0 / (2.0 + B);
+  double lnbeta = 2.0 * lgamma(a) - lgamma(2.0 * a);
+  return M_PI * (2.0 + B) / (2.0 * exp(lnbeta));
 }
 
 /* Intensity of one component at the point (x, y); par in the order above.
  * nu is nu_n of the Sersic index (or_sersic_b(par[6])) for a Sersic
  * component and ignored otherwise. */
-double or_component_value(int kind, const double *par, double nu, double x, double y) {
+double or_component_value(int kind, const double *par, double nu, double B, double x, double y) {
   if (kind == OR_SKY) return par[0]; /* Eq. (sky_I) */
   if (kind == OR_TSKY) return par[0] + par[1] * x + par[2] * y; /* Eq. (new_sky_I); x, y from the stamp centre */
-  double r = or_radius(x, y, par[0], par[1], par[2], par[3]);
+  double r = or_radius(x, y, par[0], par[1], par[2], par[3], B);
   switch (kind) {
     case OR_SERSIC: { /* Eq. (sersic-intensity) */
       double Ie = par[4], Re = par[5], n = par[6];
@@ -250,22 +267,31 @@ double or_mag_amplitude(int kind, const double *par, double m0) {
   }
 }
 
+/* Parameter count of component c: the profile's, plus B when it is boxy. */
+static int or_np(const or_desc *d, int c) { return or_n_params(d->kind[c]) + (d->has_box[c] ? 1 : 0); }
+
 /* Parameters of component c from the slot vector p, in profile units (a
  * magnitude replaced by its amplitude). */
-static void or_gather(const or_desc *d, int c, const double *p, double *par) {
-  int np = or_n_params(d->kind[c]);
+static double or_gather(const or_desc *d, int c, const double *p, double *par) {
+  int np = or_np(d, c);
   for (int k = 0; k < np; ++k) par[k] = p[d->slot[c][k]];
-  if (d->amp_is_mag[c]) par[4] = or_mag_amplitude(d->kind[c], par, d->mag_zero[c]);
+  double B = d->has_box[c] ? par[or_n_params(d->kind[c])] : 0.0;
+  if (d->amp_is_mag[c]) par[4] = or_mag_amplitude(d->kind[c], par, d->mag_zero[c]) * or_rbox(B);
+  return B;
 }
 
 /* Image of one component on the H x W stamp (no PSF). */
-void or_component_image(int kind, const double *par, int H, int W, double *out) {
+void or_component_image_box(int kind, const double *par, double B, int H, int W, double *out) {
   double nu = (kind == OR_SERSIC) ? or_sersic_b(par[6]) : 0.0;
   /* the tilted sky is measured from the stamp centre (W/2, H/2) */
   double xc = kind == OR_TSKY ? 0.5 * W : 0.0, yc = kind == OR_TSKY ? 0.5 * H : 0.0;
   for (int i = 0; i < H; ++i)
     for (int j = 0; j < W; ++j)
-      out[(size_t)i * W + j] = or_component_value(kind, par, nu, j + 0.5 - xc, H - 0.5 - i - yc);
+      out[(size_t)i * W + j] = or_component_value(kind, par, nu, B, j + 0.5 - xc, H - 0.5 - i - yc);
+}
+
+void or_component_image(int kind, const double *par, int H, int W, double *out) {
+  or_component_image_box(kind, par, 0.0, H, W, out);
 }
 
 /* Direct zero-padded cross-correlation with a K x K PSF, same-size output. */
@@ -293,12 +319,12 @@ void or_model_one(const or_desc *d, const double *p, int H, int W, const double 
                   double *model, double *work) {
   size_t N = (size_t)H * W;
   double *conv = work, *comp = work + N;
-  double par[8];
+  double par[9];
   int any_conv = 0;
   for (size_t t = 0; t < N; ++t) { conv[t] = 0.0; model[t] = 0.0; }
   for (int c = 0; c < d->n_comp; ++c) {
-    or_gather(d, c, p, par);
-    or_component_image(d->kind[c], par, H, W, comp);
+    double B = or_gather(d, c, p, par);
+    or_component_image_box(d->kind[c], par, B, H, W, comp);
     double *dst = d->convolve[c] ? conv : model;
     if (d->convolve[c]) any_conv = 1;
     for (size_t t = 0; t < N; ++t) dst[t] += comp[t];
@@ -687,16 +713,16 @@ int or_component_images_batch(const or_desc *d, int G, int H, int W, int K, cons
 #pragma omp parallel for schedule(dynamic, 1)
   for (int gi = 0; gi < G; ++gi) {
     double *tmp = malloc(sizeof(double) * N);
-    double par[8];
+    double par[9];
     const double *p = params + (size_t)gi * d->n_slots;
     for (int c = 0; c < d->n_comp; ++c) {
       double *dst = comp + ((size_t)gi * d->n_comp + c) * N;
-      or_gather(d, c, p, par);
+      double B = or_gather(d, c, p, par);
       if (d->convolve[c]) {
-        or_component_image(d->kind[c], par, H, W, tmp);
+        or_component_image_box(d->kind[c], par, B, H, W, tmp);
         or_correlate(tmp, H, W, psf + (size_t)gi * K * K, K, dst);
       } else {
-        or_component_image(d->kind[c], par, H, W, dst);
+        or_component_image_box(d->kind[c], par, B, H, W, dst);
       }
     }
     free(tmp);

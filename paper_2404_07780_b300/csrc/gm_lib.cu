@@ -86,6 +86,12 @@ struct Plan {
   int comp_chan[kMaxComp];
 };
 
+// Parameter count of component c: the profile's, plus B when it is boxy.
+int comp_np(const gm_model_desc* d, int c) {
+  const int np = n_params(d->comp[c].kind);
+  return np < 0 ? np : np + (d->has_box[c] ? 1 : 0);
+}
+
 int check_desc(const gm_model_desc* d) {
   if (!d) return fail(GM_E_INVAL, "desc is NULL");
   if (d->n_comp < 1 || d->n_comp > GM_MAX_COMP)
@@ -93,7 +99,12 @@ int check_desc(const gm_model_desc* d) {
   if (d->n_slots < 1 || d->n_slots > GM_MAX_SLOTS)
     return fail(GM_E_INVAL, "n_slots=%d outside 1..%d", d->n_slots, GM_MAX_SLOTS);
   for (int c = 0; c < d->n_comp; ++c) {
-    const int np = n_params(d->comp[c].kind);
+    if (d->has_box[c]) {
+      const int k = d->comp[c].kind;
+      if (k != SERSIC && k != EXPDISK && k != GAUSSIAN && k != MOFFAT)
+        return fail(GM_E_UNSUPPORTED, "component %d: boxiness is built for Sersic, exponential, Gaussian and Moffat", c);
+    }
+    const int np = comp_np(d, c);
     if (np < 0) return fail(GM_E_INVAL, "component %d has unknown kind %d", c, d->comp[c].kind);
     for (int k = 0; k < np; ++k)
       if (d->comp[c].slot[k] < 0 || d->comp[c].slot[k] >= d->n_slots)
@@ -115,6 +126,12 @@ int check_desc(const gm_model_desc* d) {
     if (d->is_log[d->comp[c].slot[4]])
       return fail(GM_E_INVAL, "component %d: a magnitude slot is fitted linearly (is_log must be 0)", c);
     if (!std::isfinite(d->mag_zero[c])) return fail(GM_E_INVAL, "component %d: mag_zero is not finite", c);
+  }
+  for (int c = 0; c < d->n_comp; ++c) {
+    if (!d->has_box[c]) continue;
+    const int bs = d->comp[c].slot[n_params(d->comp[c].kind)];
+    if (!(d->lo[bs] > -2.0)) return fail(GM_E_INVAL, "component %d: the boxiness slot needs lo > -2", c);
+    if (d->is_log[bs]) return fail(GM_E_INVAL, "component %d: the boxiness slot is fitted linearly", c);
   }
   return GM_OK;
 }
@@ -158,7 +175,8 @@ int make_plan(const gm_model_desc* d, int mode, bool want_comp, Plan* pl) {
   bool touches_conv[kMaxSlots] = {};
   for (int c = 0; c < d->n_comp; ++c) {
     D.kind[c] = d->comp[c].kind;
-    D.np[c] = n_params(D.kind[c]);
+    D.np[c] = comp_np(d, c);
+    D.box[c] = d->has_box[c] ? 1 : 0;
     D.mag[c] = d->amp_is_mag[c] ? 1 : 0;
     D.mag_zero[c] = d->mag_zero[c];
     pl->conv[c] = d->comp[c].convolve ? 1 : 0;
@@ -264,7 +282,7 @@ ChanMap chan_map(const Plan& pl) {
   const DescDev& D = pl.dd;
   m.n_comp = D.n_comp;
   for (int c = 0; c < D.n_comp; ++c) {
-    m.kind[c] = D.kind[c] | (D.mag[c] ? kMagFlag : 0);
+    m.kind[c] = D.kind[c] | (D.mag[c] ? kMagFlag : 0) | (D.box[c] ? kBoxFlag : 0);
     m.conv[c] = pl.conv[c];
     m.np[c] = D.np[c];
     m.comp_chan[c] = pl.comp_chan[c];
@@ -711,7 +729,7 @@ int pairs_for(const gm_model_desc* d, int mode) {
   for (int c = 0; c < d->n_comp; ++c) {
     if (!d->comp[c].convolve) continue;
     ++n_conv;
-    const int np = n_params(d->comp[c].kind);
+    const int np = comp_np(d, c);
     for (int k = 0; k < np; ++k) touches_conv[d->comp[c].slot[k]] = true;
   }
   int Pc = 0;

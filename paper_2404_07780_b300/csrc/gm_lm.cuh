@@ -39,6 +39,7 @@ struct DescDev {
   CanonGroup canon[kMaxComp];
   int mag[kMaxComp];           // amplitude slot holds a magnitude ...
   double mag_zero[kMaxComp];   // ... with this zero point
+  int box[kMaxComp];           // boxiness B follows the profile's parameters
 };
 
 struct LMOpts {
@@ -70,8 +71,8 @@ __device__ inline void setup_galaxy(const DescDev& D, const double* p, int H, in
                                     float* scale) {
   double par[8];
   for (int c = 0; c < D.n_comp; ++c) {
-    for (int k = 0; k < D.np[c]; ++k) par[k] = p[D.slot[c][k]];
-    setup_component(D.kind[c], par, H, W, D.mag[c], D.mag_zero[c], cc + c * kCC);
+    for (int k = 0; k < D.np[c]; ++k) par[k] = p[D.slot[c][k]];  // D.np includes B when boxy
+    setup_component(D.kind[c], par, H, W, D.mag[c], D.mag_zero[c], D.box[c], cc + c * kCC);
   }
   for (int s = 0; s < D.n_slots; ++s) scale[s] = (use_log && D.is_log[s]) ? (float)p[s] : 1.f;
 }

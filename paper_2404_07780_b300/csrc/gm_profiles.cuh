@@ -22,7 +22,7 @@ namespace gm {
 constexpr int kMaxComp = 8;
 constexpr int kMaxSlots = 24;  // parameter slots of a model
 constexpr int kMaxFree = 16;   // free (fitted) parameters of a model
-constexpr int kCC = 16;          // FP32 constants per component per galaxy
+constexpr int kCC = 20;          // FP32 constants per component per galaxy (a multiple of 4)
 constexpr float kRFloor = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -33,6 +33,8 @@ enum Kind { SERSIC = 1, EXPDISK = 2, FERRER = 3, KING = 4, GAUSSIAN = 5, MOFFAT 
 // Flag on the kind a tile kernel passes to eval_component: the amplitude slot
 // holds a magnitude (the chain-rule constants are in the component's cc).
 constexpr int kMagFlag = 16;
+// Flag for a boxy radius (exponent p = B + 2 in cc[16]).
+constexpr int kBoxFlag = 32;
 
 // Flat and tilted sky: no centre, axis ratio or position angle.
 __host__ __device__ inline bool is_flat(int kind) { return kind == SKY || kind == TSKY; }
@@ -156,7 +158,10 @@ __device__ inline void sersic_nu_dnu(double n, double* nu_out, double* dnu_out) 
 //   FERRER   cc[12] q, cc[13] rout, cc[14] a, cc[15] b
 //   GAUSSIAN cc[13] q, cc[14] fwhm
 //   MOFFAT   cc[13] q, cc[14] fwhm, cc[15] n
-__device__ inline void setup_component(int kind, const double* par, int H, int W, int mag, double m0, float* cc) {
+// Boxiness (box = 1, B = par[n_params(kind)]): cc[16] = p = B + 2, and in
+// magnitude mode the amplitude carries r_box (Eq. rbox) and cc[17] = d ln r_box / dB.
+__device__ inline void setup_component(int kind, const double* par, int H, int W, int mag, double m0, int box,
+                                       float* cc) {
   for (int k = 0; k < kCC; ++k) cc[k] = 0.f;
   if (kind == SKY) {
     cc[8] = (float)par[0];
@@ -183,7 +188,16 @@ __device__ inline void setup_component(int kind, const double* par, int H, int W
   cc[5] = (float)sin(pa);
   cc[6] = (float)(1.0 / q);
   cc[7] = (float)q;
-  const double lnF = mag ? -0.4 * log(10.0) * (par[4] - m0) : 0.0;  // ln of the total flux
+  double lnF = mag ? -0.4 * log(10.0) * (par[4] - m0) : 0.0;  // ln of the total flux
+  if (box) {
+    const double p = par[n_params(kind)] + 2.0, a = 1.0 / p;
+    cc[16] = (float)p;
+    if (mag) {
+      // r_box = pi p / (2 beta(a, a)), beta(a, a) = Gamma(a)^2 / Gamma(2a)
+      lnF += log(kPiD * p / 2.0) - (2.0 * lgamma(a) - lgamma(2.0 * a));
+      cc[17] = (float)(1.0 / p + 2.0 * (digamma_pos(a) - digamma_pos(2.0 * a)) / (p * p));
+    }
+  }
   switch (kind) {
     case SERSIC: {
       const double n = par[6];
@@ -284,7 +298,7 @@ __device__ inline void setup_component(int kind, const double* par, int H, int W
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float eval_component(int kind, const float* __restrict__ cc, int i, int j,
                                                 float (&d)[8]) {
-  const bool mag = kind & kMagFlag;
+  const bool mag = kind & kMagFlag, box = kind & kBoxFlag;
   kind &= kMagFlag - 1;
   if (kind == SKY) {
     d[0] = 1.f;
@@ -303,9 +317,37 @@ __device__ __forceinline__ float eval_component(int kind, const float* __restric
   const float X = fmaf(c, dx, s * dy);
   const float Y = fmaf(-s, dx, c * dy);
   const float Yq = Y * iq;
-  float r = sqrtf(fmaf(X, X, Yq * Yq));
-  const bool floored = r < kRFloor;
-  if (floored) r = kRFloor;
+  // r and its derivatives in X, Y/q and (boxy) the exponent p = B + 2
+  float r, rX, rY, rB = 0.f;
+  bool floored;
+  if (!box) {
+    r = sqrtf(fmaf(X, X, Yq * Yq));
+    floored = r < kRFloor;
+    if (floored) r = kRFloor;
+    const float ir0 = 1.f / r;
+    rX = X * ir0;
+    rY = Yq * ir0;
+  } else {
+    // r = (|X|^p + |Y/q|^p)^(1/p); dr/dX = r |X|^p / (S X); dr/dp = r (-ln S / p^2 + sum |x|^p ln|x| / (p S))
+    const float p = cc[16], ip = 1.f / p;
+    const float ax = fabsf(X), ay = fabsf(Yq);
+    const float lx = log2f(ax), ly = log2f(ay);
+    const float tx = ax > 0.f ? exp2f(p * lx) : 0.f, ty = ay > 0.f ? exp2f(p * ly) : 0.f;
+    const float S = tx + ty;
+    const float lS = log2f(S);
+    r = exp2f(lS * ip);
+    floored = !(r >= kRFloor);
+    if (floored) {
+      r = kRFloor;
+      rX = rY = 0.f;
+    } else {
+      const float iS = 1.f / S;
+      rX = ax > 0.f ? r * tx * iS / X : 0.f;
+      rY = ay > 0.f ? r * ty * iS / Yq : 0.f;
+      const float tl = (ax > 0.f ? tx * lx : 0.f) + (ay > 0.f ? ty * ly : 0.f);
+      rB = r * kLn2 * ip * fmaf(tl, iS, -lS * ip);
+    }
+  }
   const float ir = 1.f / r;
   float val = 0.f, dIdr = 0.f;
   switch (kind) {
@@ -407,15 +449,20 @@ __device__ __forceinline__ float eval_component(int kind, const float* __restric
     default:
       break;
   }
+  const int nb = n_params(kind);  // index of B when boxy
   if (floored) {
     d[0] = d[1] = d[2] = d[3] = 0.f;
+    if (box) d[nb] = 0.f;
   } else {
-    const float gr = dIdr * ir;
-    d[0] = gr * fmaf(-X, c, Yq * s * iq);           // dI/dx0
-    d[1] = gr * fmaf(-X, s, -Yq * c * iq);          // dI/dy0
-    d[2] = gr * (-Yq * Yq * iq);                    // dI/dq
-    d[3] = gr * (X * Yq * (q - iq));                // dI/dpa
+    // X = c dx + s dy, Y/q = (-s dx + c dy)/q: d/dx0 = (-c, s/q), d/dy0 = (-s, -c/q),
+    // d/dq = (0, -Y/q^2), d/dpa = (Y, -X/q)
+    d[0] = dIdr * fmaf(-rX, c, rY * s * iq);        // dI/dx0
+    d[1] = dIdr * fmaf(-rX, s, -rY * c * iq);       // dI/dy0
+    d[2] = dIdr * (-rY * Yq * iq);                  // dI/dq
+    d[3] = dIdr * fmaf(rX, q * Yq, -rY * X * iq);   // dI/dpa
+    if (box) d[nb] = dIdr * rB;                     // dI/dB = dI/dp
   }
+  if (box && mag) d[nb] = fmaf(val, cc[17], d[nb]);  // r_box in the amplitude
   if (mag) {
     // amplitude A(m, shape): dI/dm = I d ln A / dm, and dI/dp gains I d ln A / dp
     d[4] = -0.92103403719761836f * val;  // -0.4 ln 10

@@ -54,6 +54,7 @@ class gm_model_desc(ctypes.Structure):
         ("hi", ctypes.c_double * MAX_SLOTS),
         ("amp_is_mag", ctypes.c_uint8 * MAX_COMP),
         ("mag_zero", ctypes.c_double * MAX_COMP),
+        ("has_box", ctypes.c_uint8 * MAX_COMP),
     ]
 
 
@@ -199,6 +200,7 @@ def desc_from_spec(spec) -> gm_model_desc:
         if comp.mag_zero is not None:
             d.amp_is_mag[c] = 1
             d.mag_zero[c] = float(comp.mag_zero)
+        d.has_box[c] = 1 if getattr(comp, "boxy", False) else 0
     d.n_slots = spec.n_slots
     for s in range(spec.n_slots):
         d.is_free[s] = 1 if spec.free[s] else 0

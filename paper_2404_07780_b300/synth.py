@@ -70,6 +70,7 @@ class Component:
     convolve: bool
     slots: list[int]
     mag_zero: float | None = None   # amplitude slot holds a magnitude with this zero point
+    boxy: bool = False              # a boxiness slot B follows the profile's parameters
 
 
 @dataclass
@@ -98,25 +99,27 @@ class ModelSpec:
 
     def add(self, kind: str, prefix: str, H: int, W: int, convolve: bool = True,
             shared: dict[str, int] | None = None, fixed: tuple[str, ...] = (),
-            mag_zero: float | None = None) -> "ModelSpec":
+            mag_zero: float | None = None, boxy: bool = False) -> "ModelSpec":
         """Append a component; roles in `shared` reuse an existing slot.  With mag_zero the
         amplitude slot (Ie / I0) is a magnitude with that zero point (named `mag`, fitted
-        linearly, bounded to 0..40)."""
+        linearly, bounded to 0..40).  With boxy a boxiness slot `B` (bounds -1.9..10) follows
+        the profile's parameters."""
         shared = shared or {}
         slots = []
-        for k, role in enumerate(PARAM_NAMES[kind]):
+        roles = list(PARAM_NAMES[kind]) + (["B"] if boxy else [])
+        for k, role in enumerate(roles):
             if role in shared:
                 slots.append(shared[role])
                 continue
             is_mag = mag_zero is not None and k == 4
-            lo, hi = (0.0, 40.0) if is_mag else _default_bounds(kind, role, H, W)
+            lo, hi = (0.0, 40.0) if is_mag else ((-1.9, 10.0) if role == "B" else _default_bounds(kind, role, H, W))
             self.names.append(f"{prefix}.{'mag' if is_mag else role}")
             self.free.append(role not in fixed)
             self.log.append(role in _LOG_ROLES and not is_mag)
             self.lo.append(lo)
             self.hi.append(hi)
             slots.append(len(self.names) - 1)
-        self.components.append(Component(kind, convolve, slots, mag_zero))
+        self.components.append(Component(kind, convolve, slots, mag_zero, boxy))
         return self
 
 

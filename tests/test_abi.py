@@ -49,6 +49,7 @@ int main(void) {
   printf("gm_fit_opts %zu\n", sizeof(gm_fit_opts));
   printf("gm_fit_stats %zu\n", sizeof(gm_fit_stats));
   F(gm_model_desc, lo); F(gm_model_desc, hi); F(gm_model_desc, amp_is_mag); F(gm_model_desc, mag_zero);
+  F(gm_model_desc, has_box);
   F(gm_batch, image); F(gm_batch, psf); F(gm_batch, geom);
   F(gm_fit_opts, max_iter); F(gm_fit_opts, lambda0); F(gm_fit_stats, profile_ms);
   return 0;

@@ -271,3 +271,73 @@ def test_bootstrap_error_bars_match_oracle(gm):
     tol = 0.05 * rsig[:, free] + 1e-4 * np.maximum(np.abs(best[:, free]), 1.0)
     assert (np.abs(sig[:, free] - rsig[:, free]) <= tol).all(), (np.abs(sig - rsig)[:, free] / tol).max()
     assert (sig[:, ~free] == 0).all()
+
+
+# ---------------------------------------------------------------------------
+# boxiness
+# ---------------------------------------------------------------------------
+
+def _boxy_spec(H, W, mag):
+    m0 = 22.5 if mag else None
+    s = synth.ModelSpec()
+    s.add("sersic", "bulge", H, W, mag_zero=m0, boxy=True)
+    s.add("expdisk", "disk", H, W, shared={"x0": 0, "y0": 1}, mag_zero=m0, boxy=True)
+    s.add("sky", "sky", H, W, convolve=False)
+    return s
+
+
+def _boxy_params(spec, G, H, W, seed, mag):
+    g = np.random.default_rng(seed)
+    amp_b = g.uniform(15, 16, G) if mag else 10 ** g.uniform(1.5, 2.5, G)
+    amp_d = g.uniform(14.5, 15.5, G) if mag else 10 ** g.uniform(0.8, 1.5, G)
+    vals = {"bulge.x0": W / 2 + g.uniform(-1, 1, G), "bulge.y0": H / 2 + g.uniform(-1, 1, G),
+            "bulge.q": g.uniform(0.5, 0.8, G), "bulge.pa": g.uniform(0.2, 2.8, G),
+            "bulge.mag" if mag else "bulge.Ie": amp_b, "bulge.Re": g.uniform(3, 5, G), "bulge.n": g.uniform(1.5, 3, G),
+            "bulge.B": g.uniform(-0.5, 1.0, G),
+            "disk.q": g.uniform(0.3, 0.6, G), "disk.pa": g.uniform(0.2, 2.8, G),
+            "disk.mag" if mag else "disk.I0": amp_d, "disk.rs": g.uniform(6, 9, G), "disk.B": g.uniform(-0.5, 1.0, G),
+            "sky.Isky": g.uniform(1, 3, G)}
+    return np.stack([vals[n] for n in spec.names], 1)
+
+
+@pytest.mark.parametrize("mag", [False, True])
+def test_boxy_model_and_normal_equations(gm, mag):
+    H, W, K = 64, 56, 25
+    spec = _boxy_spec(H, W, mag)
+    p = _boxy_params(spec, 3, H, W, 61, mag)
+    c = _case(spec, p, H, W, K, seed=62)
+    t = c.torch()
+    got = _np(gm.gm_model(spec, t["params"], t["psf"], H, W))
+    ref = oracle.model_images(spec, c.params, c.psf.astype(np.float64), H, W)
+    for g in range(c.G):
+        assert np.abs(got[g] - ref[g]).max() <= 1e-5 * np.abs(ref[g]).max()
+    c.params = p + np.random.default_rng(63).normal(0, 0.02, p.shape) * np.maximum(np.abs(p), 0.1)
+    _check_normal(gm, c)
+
+
+def test_boxy_fit_matches_oracle(gm):
+    import torch
+    H, W, K = 64, 64, 15
+    spec = synth.ModelSpec().add("sersic", "bulge", H, W, boxy=True).add("sky", "sky", H, W, convolve=False)
+    g = np.random.default_rng(64)
+    G = 5
+    truth = np.stack([W / 2 + g.uniform(-1, 1, G), H / 2 + g.uniform(-1, 1, G), g.uniform(0.4, 0.7, G),
+                      g.uniform(0.2, 2.8, G), 10 ** g.uniform(1.5, 2, G), g.uniform(5, 9, G), g.uniform(0.8, 2, G),
+                      g.uniform(-0.6, 1.5, G), g.uniform(1, 3, G)], 1)
+    c = _case(spec, truth, H, W, K, seed=65)
+    start = truth * (1 + 0.03 * g.uniform(-1, 1, truth.shape))
+    start[:, 7] = 0.0  # an ellipse to start from
+    t = c.torch()
+    opts = dict(tol=1e-12, xtol=1e-10, gtol=1e-13, max_iter=200)
+    got = {k: _np(v) for k, v in gm.gm_fit_batch(spec, torch.from_numpy(start).cuda(), t["image"], t["sigma"], None,
+                                                 t["psf"], gm.FitOptions(**opts)).items()}
+    ref = oracle.fit(spec, start, c.psf.astype(np.float64), c.image.astype(np.float64), c.sigma.astype(np.float64),
+                     None, oracle.FitOptions(**opts))
+    assert (got["status"] == 1).all() and (ref["status"] == 1).all()
+    np.testing.assert_allclose(got["chi2"], ref["chi2"], rtol=1e-5)
+    tol = np.maximum(1e-4 * np.maximum(np.abs(ref["params"]), 1.0), 1e-2 * ref["sigma_p"])
+    d = np.abs(got["params"] - ref["params"])
+    d[:, 3] = np.minimum(d[:, 3] % math.pi, math.pi - d[:, 3] % math.pi)
+    assert (d <= tol).all(), (d / tol).max(0)
+    # the fitted boxiness is the drawn one within its error bar
+    assert (np.abs(got["params"][:, 7] - truth[:, 7]) <= 5 * got["sigma_p"][:, 7]).all()

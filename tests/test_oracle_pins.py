@@ -666,3 +666,40 @@ def test_bootstrap_of_a_flat_sky_is_the_error_of_the_weighted_mean():
     assert M[0] == 200
     sem = D.std() / math.sqrt(H * W)
     assert abs(sig[0, 0] - sem) <= 0.15 * sem
+
+
+# ---------------------------------------------------------------------------
+# boxiness (Eqs. r-rmin with B != 0, Eq. rbox)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("B", [-1.0, -0.5, 0.0, 0.5, 2.0])
+def test_rbox_is_pi_over_the_superellipse_area(B):
+    p = 2.0 + B
+    area = 4 * si.quad(lambda x: (1 - x ** p) ** (1 / p), 0, 1, epsabs=0, epsrel=1e-12)[0]
+    assert oracle.rbox(B) == pytest.approx(math.pi / area, rel=1e-9)
+
+
+def test_boxy_radius_limits():
+    par = [0.0, 0.0, 0.5, 0.3, 1.0, 2.0]  # expdisk: I = exp(-r / 2)
+    c, s = math.cos(0.3), math.sin(0.3)
+    for X, Y in ((1.3, 0.2), (0.7, -0.9), (-2.0, 0.4)):
+        x, y = c * X - s * Y, s * X + c * Y  # the point with rotated coordinates (X, Y)
+        r0 = -2.0 * math.log(oracle.component_value("expdisk", par, x, y))
+        assert r0 == pytest.approx(math.hypot(X, Y / 0.5), rel=1e-12)
+        rb = -2.0 * math.log(oracle.component_value("expdisk", par, x, y, B=1.0))
+        assert rb == pytest.approx((abs(X) ** 3 + abs(Y / 0.5) ** 3) ** (1 / 3), rel=1e-12)
+        rbig = -2.0 * math.log(oracle.component_value("expdisk", par, x, y, B=60.0))
+        assert rbig == pytest.approx(max(abs(X), abs(Y / 0.5)), rel=2e-2)  # towards a box
+
+
+@pytest.mark.parametrize("B", [-0.6, 0.8])
+def test_boxy_magnitude_flux_by_2d_quadrature(B):
+    # the amplitude from m (with r_box) gives the boxy profile the flux 10^(-0.4 (m - m0)):
+    # integrate the image over the plane
+    m0, par = 22.5, [0.0, 0.0, 0.6, 0.4, 17.0, 2.0]  # gaussian, fwhm 2
+    amp = oracle.mag_amplitude("gaussian", par, m0) * oracle.rbox(B)
+    p = list(par)
+    p[4] = amp
+    f = lambda y, x: oracle.component_value("gaussian", p, x, y, B=B)
+    flux = si.dblquad(f, -12, 12, -12, 12, epsabs=0, epsrel=1e-9)[0]
+    assert flux == pytest.approx(10 ** (-0.4 * (par[4] - m0)), rel=1e-6)
