@@ -743,6 +743,26 @@ def run_gradient(args, world, rank, local):
     flops = 2.0 * 2 * taps * G  # model and adjoint correlations, one channel each
     achieved = flops / (ms_adj / 1e3) / 1e12
     gpix = G * H * H / (ms_adj / 1e3) / 1e9
+
+    # the paper's optimiser (Adam, 1,000 steps, as its examples) against LM on the same batch
+    adam_iters = args.adam_iters
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ad = gm.gm_fit_adam(b.spec, p0, image, sigma, mask, psf, n_iter=adam_iters, lr=0.01)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_adam = e0.elapsed_time(e1)
+    lm = gm.gm_fit_batch(b.spec, p0, image, sigma, mask, psf, gm.FitOptions(tol=TOL, max_iter=MAX_ITER))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lm = gm.gm_fit_batch(b.spec, p0, image, sigma, mask, psf, gm.FitOptions(tol=TOL, max_iter=MAX_ITER))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_lm = e0.elapsed_time(e1)
+    c2_ad, c2_lm = ad["chi2"].cpu().numpy(), lm["chi2"].cpu().numpy()
+    dof = lm["dof"].cpu().numpy().astype(np.float64)
+    dchi = (c2_ad - c2_lm) / np.sqrt(2 * dof)
     if rank == 0:
         print(json.dumps({
             "metric": "chi^2 gradient throughput (adjoint correlation)", "value": gpix, "unit": "Gpix/s",
@@ -751,6 +771,12 @@ def run_gradient(args, world, rank, local):
             "config": {"workload": f"bulge+bar+nucleus+sky gradient, {G} x {H}x{H}, Moffat PSF {K}x{K}, 15 free "
                                    "parameters, default start", "galaxies": G},
             "normal_equations_ms_per_step": ms_ne, "speedup_vs_normal_equations": ms_ne / ms_adj,
+            "adam_vs_lm": {"adam_iters": adam_iters, "adam_lr": 0.01, "adam_ms": ms_adam, "lm_ms": ms_lm,
+                           "lm_converged_frac": float((lm["status"] == gm.ST_CONVERGED).float().mean().item()),
+                           "lm_mean_iters": float(lm["iters"].float().mean().item()),
+                           "adam_chi2_above_lm_by_1sigma_frac": float(np.mean(dchi > 1)),
+                           "adam_chi2_below_lm_by_1sigma_frac": float(np.mean(dchi < -1)),
+                           "median_chi2_excess_sigma": float(np.median(dchi))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                          "kernel": "k_adjoint<RESID> + k_adjoint<GRAD> (timed with set-up and profile: a lower bound)",
@@ -769,6 +795,7 @@ def main():
                     help="batch size per GPU (default 8192 for fit, 32768 for uneven; profiling runs use less)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--train-samples", type=int, default=1 << 20, help="learned workload: training stamps")
+    ap.add_argument("--adam-iters", type=int, default=1000, help="gradient workload: Adam steps (the paper's 1,000)")
     ap.add_argument("--epochs", type=int, default=1, help="learned workload: training epochs")
     ap.add_argument("--workload", default="fit", choices=["fit", "uneven", "gradient", "learned"],
                     help="fit: the LM fit of the SDSS-shaped batch (default); uneven: bulge+disk fits on stamps and "

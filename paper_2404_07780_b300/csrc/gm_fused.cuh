@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
           if (MODE == MODE_MODEL) {
             if (m.comp_chan[cm] >= 0) v[m.comp_chan[cm]] += val;
           } else {
-            for (int k = 0; k < m.np[cm]; ++k) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {  // compile-time k keeps d in registers
+              if (k >= m.np[cm]) break;
               const int ch = m.chan[cm][k];
               if (ch >= 0) v[ch] += d[k] * s_scale[m.slot[cm][k]];
             }
@@ -571,7 +573,9 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
           const int ch = m.comp_chan[cm];
           if (ch >= 0) s_out[ch * kTilePix + pix] = v;
         } else {
-          for (int k = 0; k < m.np[cm]; ++k) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {  // compile-time k keeps d in registers
+            if (k >= m.np[cm]) break;
             const int ch = m.chan[cm][k];
             if (ch >= 0) s_out[ch * kTilePix + pix] += d[k] * s_scale[m.slot[cm][k]];
           }

@@ -296,9 +296,12 @@ __device__ inline void setup_component(int kind, const double* par, int H, int W
 // One component at stamp pixel (i, j): value and d value / d p_k for each of
 // the component's parameters (physical units, order of the ABI header).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float eval_component(int kind, const float* __restrict__ cc, int i, int j,
-                                                float (&d)[8]) {
-  const bool mag = kind & kMagFlag, box = kind & kBoxFlag;
+// kExt = false is the plain instance (no magnitude, no boxiness): the hot path of
+// most models, kept free of the extras' instructions.
+template <bool kExt>
+__device__ __forceinline__ float eval_component_t(int kind, const float* __restrict__ cc, int i, int j,
+                                                  float (&d)[8]) {
+  const bool mag = kExt && (kind & kMagFlag), box = kExt && (kind & kBoxFlag);
   kind &= kMagFlag - 1;
   if (kind == SKY) {
     d[0] = 1.f;
@@ -318,15 +321,14 @@ __device__ __forceinline__ float eval_component(int kind, const float* __restric
   const float Y = fmaf(-s, dx, c * dy);
   const float Yq = Y * iq;
   // r and its derivatives in X, Y/q and (boxy) the exponent p = B + 2
-  float r, rX, rY, rB = 0.f;
+  float r, ir, rX, rY, rB = 0.f;
   bool floored;
   if (!box) {
     r = sqrtf(fmaf(X, X, Yq * Yq));
     floored = r < kRFloor;
     if (floored) r = kRFloor;
-    const float ir0 = 1.f / r;
-    rX = X * ir0;
-    rY = Yq * ir0;
+    ir = 1.f / r;
+    rX = rY = 0.f;  // unused: the elliptical radius takes dr/dX = X/r, dr/d(Y/q) = (Y/q)/r below
   } else {
     // r = (|X|^p + |Y/q|^p)^(1/p); dr/dX = r |X|^p / (S X); dr/dp = r (-ln S / p^2 + sum |x|^p ln|x| / (p S))
     const float p = cc[16], ip = 1.f / p;
@@ -347,8 +349,8 @@ __device__ __forceinline__ float eval_component(int kind, const float* __restric
       const float tl = (ax > 0.f ? tx * lx : 0.f) + (ay > 0.f ? ty * ly : 0.f);
       rB = r * kLn2 * ip * fmaf(tl, iS, -lS * ip);
     }
+    ir = 1.f / r;
   }
-  const float ir = 1.f / r;
   float val = 0.f, dIdr = 0.f;
   switch (kind) {
     case SERSIC: {
@@ -449,20 +451,36 @@ __device__ __forceinline__ float eval_component(int kind, const float* __restric
     default:
       break;
   }
-  const int nb = n_params(kind);  // index of B when boxy
   if (floored) {
     d[0] = d[1] = d[2] = d[3] = 0.f;
-    if (box) d[nb] = 0.f;
   } else {
     // X = c dx + s dy, Y/q = (-s dx + c dy)/q: d/dx0 = (-c, s/q), d/dy0 = (-s, -c/q),
     // d/dq = (0, -Y/q^2), d/dpa = (Y, -X/q)
-    d[0] = dIdr * fmaf(-rX, c, rY * s * iq);        // dI/dx0
-    d[1] = dIdr * fmaf(-rX, s, -rY * c * iq);       // dI/dy0
-    d[2] = dIdr * (-rY * Yq * iq);                  // dI/dq
-    d[3] = dIdr * fmaf(rX, q * Yq, -rY * X * iq);   // dI/dpa
-    if (box) d[nb] = dIdr * rB;                     // dI/dB = dI/dp
+    if (!box) {
+      const float gr = dIdr * ir;                   // (dI/dr) / r
+      d[0] = gr * fmaf(-X, c, Yq * s * iq);         // dI/dx0
+      d[1] = gr * fmaf(-X, s, -Yq * c * iq);        // dI/dy0
+      d[2] = gr * (-Yq * Yq * iq);                  // dI/dq
+      d[3] = gr * (X * Yq * (q - iq));              // dI/dpa
+    } else {
+      const float gX = dIdr * rX, gY = dIdr * rY;
+      d[0] = fmaf(-gX, c, gY * s * iq);
+      d[1] = fmaf(-gX, s, -gY * c * iq);
+      d[2] = -gY * Yq * iq;
+      d[3] = fmaf(gX, q * Yq, -gY * X * iq);
+    }
   }
-  if (box && mag) d[nb] = fmaf(val, cc[17], d[nb]);  // r_box in the amplitude
+  if (box) {
+    // dI/dB = dI/dp (rB is zero on the floor), plus I d ln(r_box)/dB with a magnitude.
+    // B follows the profile's own parameters: slot 6 (exponential, Gaussian) or 7
+    // (Sersic, Moffat).  The slot is picked by compile-time indices so that d stays
+    // in registers.
+    float dB = dIdr * rB;
+    if (mag) dB = fmaf(val, cc[17], dB);
+    const bool at6 = kind == EXPDISK || kind == GAUSSIAN;
+    if (at6) d[6] = dB;
+    else d[7] = dB;
+  }
   if (mag) {
     // amplitude A(m, shape): dI/dm = I d ln A / dm, and dI/dp gains I d ln A / dp
     d[4] = -0.92103403719761836f * val;  // -0.4 ln 10
@@ -486,6 +504,14 @@ __device__ __forceinline__ float eval_component(int kind, const float* __restric
     }
   }
   return val;
+}
+
+// The kind carries the magnitude and boxiness flags; the test is uniform across a
+// warp (one component at a time), so only one instance runs.
+__device__ __forceinline__ float eval_component(int kind, const float* __restrict__ cc, int i, int j,
+                                                float (&d)[8]) {
+  if (kind & (kMagFlag | kBoxFlag)) return eval_component_t<true>(kind, cc, i, j, d);
+  return eval_component_t<false>(kind, cc, i, j, d);
 }
 
 }  // namespace gm
