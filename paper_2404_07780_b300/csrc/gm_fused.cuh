@@ -308,54 +308,118 @@ __device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I
 // One 2-tap chunk of the sliding-window correlation.  R is the ring rotation:
 // window element e (input column b + e relative to the thread's first column)
 // lives in w[q][(2R + e) % 10].  Elements 0..7 are present on entry; elements 8
-// and 9 are loaded here.
-template <int CP, int R>
-__device__ __forceinline__ void corr_chunk(u64 (&acc)[CP][8], u64 (&w)[CP][10],
+// and 9 are loaded here.  pp holds the PSF pair (taps b, b+1) on entry and
+// (b+2, b+3) on exit: each chunk fetches the next chunk's pair before its own
+// FMAs, so no FMA waits on a shared-memory load of the tap it multiplies.
+// Odd K leaves one zero tap position per padded row (K+1 positions); the half
+// chunks skip it: HALF = 1 does tap b only (the row's last chunk: no loads),
+// HALF = 2 tap b+1 only (the row's first chunk when the zero is in front).
+template <int CP, int R, int HALF = 0>
+__device__ __forceinline__ void corr_chunk(u64 (&acc)[CP][8], u64 (&w)[CP][10], ulonglong2& pp,
                                            const float2* const (&irow)[CP], const u64* prow, int b) {
   constexpr int L = (2 * R + 8) % 10;
+  ulonglong2 pn = pp;
+  if (HALF != 1) {
+    pn = *reinterpret_cast<const ulonglong2*>(prow + b + 2);
 #pragma unroll
-  for (int q = 0; q < CP; ++q) {
-    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + b + 8);
-    w[q][L] = v.x;
-    w[q][L + 1] = v.y;
-  }
-  const ulonglong2 pp = *reinterpret_cast<const ulonglong2*>(prow + b);
-#pragma unroll
-  for (int q = 0; q < CP; ++q) {
-#pragma unroll
-    for (int rx = 0; rx < 8; ++rx) acc[q][rx] = ffma2(pp.x, w[q][(2 * R + rx) % 10], acc[q][rx]);
-#pragma unroll
-    for (int rx = 0; rx < 8; ++rx) acc[q][rx] = ffma2(pp.y, w[q][(2 * R + 1 + rx) % 10], acc[q][rx]);
-  }
-}
-
-// One PSF row a (K2 = K+1 taps, even) into acc.
-template <int CP>
-__device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const (&irow)[CP], const u64* prow,
-                                         int nsc, int tail) {
-  u64 w[CP][10];
-#pragma unroll
-  for (int q = 0; q < CP; ++q) {
-#pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
-      w[q][e] = v.x;
-      w[q][e + 1] = v.y;
+    for (int q = 0; q < CP; ++q) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + b + 8);
+      w[q][L] = v.x;
+      w[q][L + 1] = v.y;
     }
   }
-  int b = 0;
-  for (int sc = 0; sc < nsc; ++sc) {
-    corr_chunk<CP, 0>(acc, w, irow, prow, b);
-    corr_chunk<CP, 1>(acc, w, irow, prow, b + 2);
-    corr_chunk<CP, 2>(acc, w, irow, prow, b + 4);
-    corr_chunk<CP, 3>(acc, w, irow, prow, b + 6);
-    corr_chunk<CP, 4>(acc, w, irow, prow, b + 8);
-    b += 10;
+#pragma unroll
+  for (int q = 0; q < CP; ++q) {
+    if (HALF != 2) {
+#pragma unroll
+      for (int rx = 0; rx < 8; ++rx) acc[q][rx] = ffma2(pp.x, w[q][(2 * R + rx) % 10], acc[q][rx]);
+    }
+    if (HALF != 1) {
+#pragma unroll
+      for (int rx = 0; rx < 8; ++rx) acc[q][rx] = ffma2(pp.y, w[q][(2 * R + 1 + rx) % 10], acc[q][rx]);
+    }
   }
-  if (tail > 0) corr_chunk<CP, 0>(acc, w, irow, prow, b);
-  if (tail > 1) corr_chunk<CP, 1>(acc, w, irow, prow, b + 2);
-  if (tail > 2) corr_chunk<CP, 2>(acc, w, irow, prow, b + 4);
-  if (tail > 3) corr_chunk<CP, 3>(acc, w, irow, prow, b + 6);
+  pp = pn;
+}
+
+// One PSF row into acc.  The padded row has K+1 positions, the taps at
+// cpad .. cpad+K-1 (cpad = c & 1 keeps each window start 16-byte aligned):
+// nf = (K-1)/2 full chunks plus one half chunk, in front (cpad = 1) or behind.
+// Ten chunks per loop iteration; the last chunk may prefetch two positions past
+// the row (into the next row, or the 16 slack bytes after the last one).
+template <int CP>
+__device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const (&irow)[CP], const u64* prow,
+                                         int nf, int cpad) {
+  u64 w[CP][10];
+  ulonglong2 pp = *reinterpret_cast<const ulonglong2*>(prow);
+  int b = 0;
+  if (cpad) {
+    // start the ring at rotation 4, so that the full chunks after the head half start at 0
+#pragma unroll
+    for (int q = 0; q < CP; ++q)
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
+        w[q][(8 + e) % 10] = v.x;
+        w[q][(9 + e) % 10] = v.y;
+      }
+    corr_chunk<CP, 4, 2>(acc, w, pp, irow, prow, 0);
+    b = 2;
+  } else {
+#pragma unroll
+    for (int q = 0; q < CP; ++q)
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
+        w[q][e] = v.x;
+        w[q][e + 1] = v.y;
+      }
+  }
+  for (; nf >= 10; nf -= 10) {
+    corr_chunk<CP, 0>(acc, w, pp, irow, prow, b);
+    corr_chunk<CP, 1>(acc, w, pp, irow, prow, b + 2);
+    corr_chunk<CP, 2>(acc, w, pp, irow, prow, b + 4);
+    corr_chunk<CP, 3>(acc, w, pp, irow, prow, b + 6);
+    corr_chunk<CP, 4>(acc, w, pp, irow, prow, b + 8);
+    corr_chunk<CP, 0>(acc, w, pp, irow, prow, b + 10);
+    corr_chunk<CP, 1>(acc, w, pp, irow, prow, b + 12);
+    corr_chunk<CP, 2>(acc, w, pp, irow, prow, b + 14);
+    corr_chunk<CP, 3>(acc, w, pp, irow, prow, b + 16);
+    corr_chunk<CP, 4>(acc, w, pp, irow, prow, b + 18);
+    b += 20;
+  }
+  if (nf >= 5) {
+    corr_chunk<CP, 0>(acc, w, pp, irow, prow, b);
+    corr_chunk<CP, 1>(acc, w, pp, irow, prow, b + 2);
+    corr_chunk<CP, 2>(acc, w, pp, irow, prow, b + 4);
+    corr_chunk<CP, 3>(acc, w, pp, irow, prow, b + 6);
+    corr_chunk<CP, 4>(acc, w, pp, irow, prow, b + 8);
+    b += 10;
+    nf -= 5;
+  }
+  // nf = 0..4 full chunks left, then the tail half when the zero position is behind
+  const bool tail = !cpad;
+  if (nf == 0) {
+    if (tail) corr_chunk<CP, 0, 1>(acc, w, pp, irow, prow, b);
+    return;
+  }
+  corr_chunk<CP, 0>(acc, w, pp, irow, prow, b);
+  if (nf == 1) {
+    if (tail) corr_chunk<CP, 1, 1>(acc, w, pp, irow, prow, b + 2);
+    return;
+  }
+  corr_chunk<CP, 1>(acc, w, pp, irow, prow, b + 2);
+  if (nf == 2) {
+    if (tail) corr_chunk<CP, 2, 1>(acc, w, pp, irow, prow, b + 4);
+    return;
+  }
+  corr_chunk<CP, 2>(acc, w, pp, irow, prow, b + 4);
+  if (nf == 3) {
+    if (tail) corr_chunk<CP, 3, 1>(acc, w, pp, irow, prow, b + 6);
+    return;
+  }
+  corr_chunk<CP, 3>(acc, w, pp, irow, prow, b + 6);
+  if (tail) corr_chunk<CP, 4, 1>(acc, w, pp, irow, prow, b + 8);
 }
 
 // Correlate CP pair planes (local indices lp0 .. lp0+CP-1 of the pass buffer)
@@ -370,9 +434,8 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
 #pragma unroll
     for (int rx = 0; rx < 8; ++rx) acc[q][rx] = 0ull;
   const int K2 = K + 1;
-  const int nch = K2 >> 1;   // 2-tap chunks per PSF row
-  const int nsc = nch / 5;   // full 5-chunk rotations
-  const int tail = nch - 5 * nsc;
+  const int nf = (K - 1) >> 1;         // full 2-tap chunks per PSF row
+  const int cpad = ((K - 1) >> 1) & 1;  // zero position in front of the taps
   for (int a0 = a_lo; a0 < a_hi; a0 += kRowBlock) {
     u64 part[CP][8];
 #pragma unroll
@@ -384,7 +447,7 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
       const float2* irow[CP];
 #pragma unroll
       for (int q = 0; q < CP; ++q) irow[q] = s_in + (size_t)(lp0 + q) * plane + (size_t)(row + a) * rw + col0;
-      corr_row<CP>(part, irow, s_psf + a * K2, nsc, tail);
+      corr_row<CP>(part, irow, s_psf + a * K2, nf, cpad);
     }
 #pragma unroll
     for (int q = 0; q < CP; ++q)
@@ -393,19 +456,31 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
   }
 }
 
+// The output tile in shared memory: channel ch, pixel pix = row * kTile + col,
+// at ch * kTilePix + out_idx(pix).  Each row's 4-column groups are permuted by
+// XOR with (row & 7), so the 8 rows that a quarter-warp stores (same columns,
+// 16 bytes per lane) fall in 8 different bank groups; a warp reading one row
+// still touches 32 different banks.
+static_assert(kTile == 32, "out_idx assumes 32-pixel rows");
+__device__ __forceinline__ int out_idx(int pix) { return pix ^ (((pix >> 5) & 7) << 2); }
+
 template <int CP>
 __device__ __forceinline__ void store_pairs(const u64 (&acc)[CP][8], float* s_out, int cp0, int nch_conv,
                                             int row, int col0) {
+  const int o0 = out_idx(row * kTile + col0), o1 = out_idx(row * kTile + col0 + 4);
 #pragma unroll
   for (int q = 0; q < CP; ++q) {
     const int ch = 2 * (cp0 + q);
+    float x[8], y[8];
 #pragma unroll
-    for (int rx = 0; rx < 8; ++rx) {
-      float x, y;
-      unpack2(acc[q][rx], x, y);
-      const int pix = row * kTile + col0 + rx;
-      s_out[ch * kTilePix + pix] = x;
-      if (ch + 1 < nch_conv) s_out[(ch + 1) * kTilePix + pix] = y;
+    for (int rx = 0; rx < 8; ++rx) unpack2(acc[q][rx], x[rx], y[rx]);
+    float* sx = s_out + ch * kTilePix;
+    *reinterpret_cast<float4*>(sx + o0) = make_float4(x[0], x[1], x[2], x[3]);
+    *reinterpret_cast<float4*>(sx + o1) = make_float4(x[4], x[5], x[6], x[7]);
+    if (ch + 1 < nch_conv) {
+      float* sy = sx + kTilePix;
+      *reinterpret_cast<float4*>(sy + o0) = make_float4(y[0], y[1], y[2], y[3]);
+      *reinterpret_cast<float4*>(sy + o1) = make_float4(y[4], y[5], y[6], y[7]);
     }
   }
 }
@@ -417,21 +492,40 @@ template <int P>
 __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_out, float* s_red, size_t base, int H,
                                             int W, size_t prow, int i0, int j0) {
   constexpr int NA = 1 + P + P * (P + 1) / 2;
+  constexpr int kPx = kTilePix / kGroupThreads;  // pixels per thread in the smallest block
   float acc[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) acc[e] = 0.f;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int pix = tid; pix < kTilePix; pix += nthr) {
+  // every image, sigma and mask load of this thread's pixels first, so that the
+  // tile waits for one memory latency rather than one per pixel (loading them
+  // before the correlation instead was measured slower: registers)
+  float dv[kPx], sv[kPx];
+  bool use[kPx];
+#pragma unroll
+  for (int k = 0; k < kPx; ++k) {
+    const int pix = tid + k * nthr;
     const int i = i0 + pix / kTile, j = j0 + pix % kTile;
-    if (i >= H || j >= W) continue;
-    const size_t gp = base + (size_t)i * W + j;
-    if (A.mask && A.mask[gp]) continue;
-    const float isg = 1.f / A.sigma[gp];
-    const float rr = (A.image[gp] - s_out[pix]) * isg;  // (D - M) / sigma
+    use[k] = pix < kTilePix && i < H && j < W;
+    dv[k] = 0.f;
+    sv[k] = 1.f;
+    if (use[k]) {
+      const size_t gp = base + (size_t)i * W + j;
+      dv[k] = A.image[gp];
+      sv[k] = A.sigma[gp];
+      if (A.mask) use[k] = A.mask[gp] == 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPx; ++k) {
+    if (!use[k]) continue;
+    const int op = out_idx(tid + k * nthr);
+    const float isg = 1.f / sv[k];
+    const float rr = (dv[k] - s_out[op]) * isg;  // (D - M) / sigma
     acc[0] = fmaf(rr, rr, acc[0]);
     float jw[P > 0 ? P : 1];
 #pragma unroll
-    for (int f = 0; f < P; ++f) jw[f] = s_out[(1 + f) * kTilePix + pix] * isg;  // J / sigma
+    for (int f = 0; f < P; ++f) jw[f] = s_out[(1 + f) * kTilePix + op] * isg;  // J / sigma
 #pragma unroll
     for (int f = 0; f < P; ++f) acc[1 + f] = fmaf(jw[f], rr, acc[1 + f]);
     int e = 1 + P;
@@ -560,24 +654,37 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
 
     // ---- unconvolved components at the output pixels ----
     for (int pix = tid; pix < kTilePix; pix += nthr) {
-      for (int ch = m.nch_conv; ch < m.nch_tot; ++ch) s_out[ch * kTilePix + pix] = 0.f;
-      if (!m.any_unconv) continue;
-      const int i = i0 + pix / kTile, j = j0 + pix % kTile;
-      if (i >= H || j >= W) continue;
+      const int op = out_idx(pix);
+      for (int ch = m.nch_conv; ch < m.nch_tot; ++ch) s_out[ch * kTilePix + op] = 0.f;
+    }
+    if (m.any_unconv) {
+      // one component at a time: its kind, channels and scales are read once, and the
+      // same thread owns the same pixels as in the loop above
       for (int cm = 0; cm < m.n_comp; ++cm) {
         if (m.conv[cm]) continue;
-        float d[8];
-        const float v = eval_component(m.kind[cm], s_cc + cm * kCC, i, j, d);
-        s_out[pix] += v;
-        if (MODE == MODE_MODEL) {
-          const int ch = m.comp_chan[cm];
-          if (ch >= 0) s_out[ch * kTilePix + pix] = v;
-        } else {
+        const int kind = m.kind[cm];
+        const float* cc = s_cc + cm * kCC;
+        int chs[8];
+        float scs[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {  // compile-time k keeps d in registers
-            if (k >= m.np[cm]) break;
-            const int ch = m.chan[cm][k];
-            if (ch >= 0) s_out[ch * kTilePix + pix] += d[k] * s_scale[m.slot[cm][k]];
+        for (int k = 0; k < 8; ++k) {
+          chs[k] = (MODE != MODE_MODEL && k < m.np[cm]) ? m.chan[cm][k] : -1;
+          scs[k] = chs[k] >= 0 ? s_scale[m.slot[cm][k]] : 0.f;
+        }
+        const int own = m.comp_chan[cm];
+        for (int pix = tid; pix < kTilePix; pix += nthr) {
+          const int i = i0 + pix / kTile, j = j0 + pix % kTile;
+          if (i >= H || j >= W) continue;
+          const int op = out_idx(pix);
+          float d[8];
+          const float v = eval_component(kind, cc, i, j, d);
+          s_out[op] += v;
+          if (MODE == MODE_MODEL) {
+            if (own >= 0) s_out[own * kTilePix + op] = v;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)  // compile-time k keeps d in registers
+              if (chs[k] >= 0) s_out[chs[k] * kTilePix + op] += d[k] * scs[k];
           }
         }
       }
@@ -592,10 +699,11 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
         const int i = i0 + pix / kTile, j = j0 + pix % kTile;
         if (i >= H || j >= W) continue;
         const size_t off = (size_t)i * W + j;
-        A.model_out[pix0 + off] = s_out[pix];
+        const int op = out_idx(pix);
+        A.model_out[pix0 + off] = s_out[op];
         if (A.comp_out) {
           for (int cm = 0; cm < m.n_comp; ++cm)
-            A.comp_out[(size_t)m.n_comp * pix0 + cm * HW + off] = s_out[m.comp_chan[cm] * kTilePix + pix];
+            A.comp_out[(size_t)m.n_comp * pix0 + cm * HW + off] = s_out[m.comp_chan[cm] * kTilePix + op];
         }
       }
     } else {

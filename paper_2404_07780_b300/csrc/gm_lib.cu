@@ -341,7 +341,7 @@ Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp, int cpt
     return (int)o;
   };
   s.off_in = take((size_t)pp * plane_bytes, 128);
-  s.off_psf = take((size_t)K * (K + 1) * 8, 16);
+  s.off_psf = take((size_t)K * (K + 1) * 8 + 16, 16);  // + the last chunk's prefetch slack
   s.off_out = take((size_t)pl.nch_tot * kTilePix * 4, 16);
   s.off_cc = take((size_t)2 * n_comp * kCC * 4, 16);             // two items' constants
   s.off_scale = take((size_t)2 * scale_stride(n_slots) * 4, 16);
@@ -1269,7 +1269,7 @@ int prepare_adjoint(const gm_model_desc* desc, const gm_batch* batch, void* work
     return (int)o;
   };
   A.off_in = take(plane_bytes, 128);
-  A.off_psf = take((size_t)K * (K + 1) * 8, 16);
+  A.off_psf = take((size_t)K * (K + 1) * 8 + 16, 16);  // + the last chunk's prefetch slack
   A.off_cc = take((size_t)2 * desc->n_comp * kCC * 4, 16);
   A.off_red = take((size_t)4 * 2 * (1 + P) * 4, 16);
   A.off_bar = take(16, 16);
