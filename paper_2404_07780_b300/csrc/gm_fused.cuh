@@ -485,6 +485,32 @@ __device__ __forceinline__ void store_pairs(const u64 (&acc)[CP][8], float* s_ou
   }
 }
 
+// store_pairs for the second half of a row-split pass: adds to what the first stored.
+template <int CP>
+__device__ __forceinline__ void add_pairs(const u64 (&acc)[CP][8], float* s_out, int cp0, int nch_conv, int row,
+                                          int col0) {
+  const int o0 = out_idx(row * kTile + col0), o1 = out_idx(row * kTile + col0 + 4);
+#pragma unroll
+  for (int q = 0; q < CP; ++q) {
+    const int ch = 2 * (cp0 + q);
+    float x[8], y[8];
+#pragma unroll
+    for (int rx = 0; rx < 8; ++rx) unpack2(acc[q][rx], x[rx], y[rx]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && ch + 1 >= nch_conv) break;
+      const float* v = h ? y : x;
+      float4* p0 = reinterpret_cast<float4*>(s_out + (ch + h) * kTilePix + o0);
+      float4* p1 = reinterpret_cast<float4*>(s_out + (ch + h) * kTilePix + o1);
+      float4 a = *p0, b = *p1;
+      a.x += v[0]; a.y += v[1]; a.z += v[2]; a.w += v[3];
+      b.x += v[4]; b.y += v[5]; b.z += v[6]; b.w += v[7];
+      *p0 = a;
+      *p1 = b;
+    }
+  }
+}
+
 // Accumulate J^T W J (packed upper triangle), J^T W r and chi^2 for P free
 // parameters over this thread's pixels of the tile, reduce over the block and
 // write the tile's FP64 partial sums.
@@ -591,8 +617,13 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
   const int grp = tid / kGroupThreads;
   const int t = tid - grp * kGroupThreads;
   const int lane = t & 31, wig = t >> 5;
-  const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
-  const int row0 = wig * 8;
+  // warp w runs on scheduler w % 4, next to the warps of the same index in the other
+  // groups: odd groups take the 8-row blocks in reverse order, so that at a stamp's
+  // top or bottom edge (where the row skip shortens some blocks' PSF-row ranges) each
+  // scheduler gets a short and a long block rather than two of the same
+  const int wb = (grp & 1) ? 3 - wig : wig;
+  const int row = wb * 8 + (lane & 7), col0 = (lane >> 3) * 8;
+  const int row0 = wb * 8;
 
   for (;;) {
     __syncthreads();  // the previous item is done with s_psf, s_cc, s_scale, s_out, s_red and s_info[slot ^ 1]
@@ -634,12 +665,17 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
       const int first = pass * A.pp;
       const int npass = min(A.pp, m.ncp - first);
       const int ngroups = nthr / kGroupThreads;
+      // two pairs on two groups: rather than one pair per thread (8 accumulators, measured
+      // ~16% slower per FMA), both groups take both pairs over half of the PSF rows each
+      const bool split = CPT == 2 && npass == 2 && ngroups == 2;
       const int base = npass / ngroups, rem = npass - base * ngroups;
-      const int npair = base + (grp < rem ? 1 : 0);
-      const int lp0 = grp * base + min(grp, rem);
+      const int npair = split ? 2 : base + (grp < rem ? 1 : 0);
+      const int lp0 = split ? 0 : grp * base + min(grp, rem);
+      const int a_mid = (a_lo + a_hi) >> 1;
+      const int ga_lo = split && grp == 1 ? a_mid : a_lo, ga_hi = split && grp == 0 ? a_mid : a_hi;
       u64 acc2[2][8];
       u64 acc1[1][8];
-      if (CPT == 2 && npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
+      if (CPT == 2 && npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, ga_lo, ga_hi);
       else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
       __syncthreads();  // every warp is done reading the window
       if (tid == 0) {
@@ -647,8 +683,15 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
         else if (s_info[slot ^ 1].valid)
           issue_pass(A, s_info[slot ^ 1], s_in, bar, 0, s_psf, s_cc0 + (slot ^ 1) * cc_n, s_scale0 + (slot ^ 1) * sc_n);
       }
-      if (CPT == 2 && npair == 2) store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
-      else if (npair == 1) store_pairs<1>(acc1, s_out, first + lp0, m.nch_conv, row, col0);
+      if (split) {
+        if (grp == 0) store_pairs<2>(acc2, s_out, first, m.nch_conv, row, col0);
+        __syncthreads();
+        if (grp == 1) add_pairs<2>(acc2, s_out, first, m.nch_conv, row, col0);
+      } else if (CPT == 2 && npair == 2) {
+        store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
+      } else if (npair == 1) {
+        store_pairs<1>(acc1, s_out, first + lp0, m.nch_conv, row, col0);
+      }
     }
     __syncthreads();
 
