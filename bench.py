@@ -42,12 +42,12 @@ MAX_ITER = 200
 PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
 # DRAM bytes (read + write) of k_fused<NORMAL, 8, 2> per galaxy evaluated, from one ncu capture of a
-# 1,024-galaxy pass of this workload (704.5 MB); traffic grows in proportion to the galaxies a pass
+# 1,024-galaxy pass of this workload (712.7 MB); traffic grows in proportion to the galaxies a pass
 # evaluates, so a launch's traffic is this times its galaxies
-FUSED_DRAM_BYTES_PER_GALAXY = 704.46e6 / 1024
-# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,615.9 MB
+FUSED_DRAM_BYTES_PER_GALAXY = 712.657e6 / 1024
+# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,627.9 MB
 # for a 2,048-galaxy pass of 45.59 M pixels)
-UNEVEN_DRAM_BYTES_PER_PIXEL = 2615.9e6 / 45591296
+UNEVEN_DRAM_BYTES_PER_PIXEL = 2627.856e6 / 45591296
 
 
 def workload_config(G, H, K):
