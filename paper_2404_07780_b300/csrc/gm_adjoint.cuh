@@ -179,19 +179,35 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
 #pragma unroll
       for (int e = 0; e < NA; ++e) red[h][e] = 0.f;
     const int i = i0 + row;
+    float vv[2][8];
 #pragma unroll
-    for (int rx = 0; rx < 8; ++rx) {
-      const int j = j0 + col0 + rx;
-      float vv[2];
-      unpack2(acc[0][rx], vv[0], vv[1]);
-      if (MODE == ADJ_RESID) {
+    for (int rx = 0; rx < 8; ++rx) unpack2(acc[0][rx], vv[0][rx], vv[1][rx]);
+    // Each gradient term is a sum over pixels of a weight times dI/dp_k.  The
+    // accumulator of (component, k) is run-time data, and a compare-select over the
+    // free parameters keeps red[] in registers; it is paid once per component and
+    // galaxy: the thread first sums each derivative over its 8 pixels.
+    auto scatter = [&](const int (&acc_of)[8], int np, int h, const float (&sd)[8]) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k >= np) break;
+        const int f = acc_of[k];
+#pragma unroll
+        for (int ff = 0; ff < P; ++ff)
+          if (ff == f) red[h][1 + ff] += sd[k];
+      }
+    };
+    if (MODE == ADJ_RESID) {
+      float wr[2][8];  // w r = (D - M) / sigma^2 per pixel; 0 outside the stamp or masked
+#pragma unroll
+      for (int rx = 0; rx < 8; ++rx) {
+        const int j = j0 + col0 + rx;
         float uu[2] = {0.f, 0.f};
         if (i < A.H && j < A.W) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             if (h == 1 && !has1) continue;
             const int g = g0 + h;
-            float Mv = vv[h];
+            float Mv = vv[h][rx];
             for (int cm = 0; cm < m.n_comp; ++cm) {
               if (m.conv[cm]) continue;
               float d[8];
@@ -202,44 +218,53 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
             const float isg = 1.f / A.sigma[gpx];
             const float rr = (A.image[gpx] - Mv) * isg;
             red[h][0] = fmaf(rr, rr, red[h][0]);
-            const float wr = rr * isg;  // w r = (D - M) / sigma^2
-            uu[h] = wr;
-            for (int cm = 0; cm < m.n_comp; ++cm) {
-              if (m.conv[cm]) continue;
-              float d[8];
-              eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                if (k >= m.np[cm]) break;
-                const int f = A.unconv_acc[cm][k];
-#pragma unroll
-                for (int ff = 0; ff < P; ++ff)
-                  if (ff == f) red[h][1 + ff] = fmaf(wr, d[k], red[h][1 + ff]);
-              }
-            }
+            uu[h] = rr * isg;
           }
         }
+        wr[0][rx] = uu[0];
+        wr[1][rx] = uu[1];
         if (i < A.H && j < A.Wp)
           reinterpret_cast<float2*>(A.u_planes)[((size_t)gp * A.H + i) * A.Wp + j] = make_float2(uu[0], uu[1]);
-      } else {
-        if (i < A.H && j < A.W) {
+      }
+      for (int cm = 0; cm < m.n_comp; ++cm) {
+        if (m.conv[cm]) continue;
+        const int np = m.np[cm];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (h == 1 && !has1) continue;
-            for (int cm = 0; cm < m.n_comp; ++cm) {
-              if (!m.conv[cm]) continue;
-              float d[8];
-              eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !has1) continue;
+          float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                if (k >= m.np[cm]) break;
-                const int f = A.conv_acc[cm][k];
+          for (int rx = 0; rx < 8; ++rx) {
+            const int j = j0 + col0 + rx;
+            if (i >= A.H || j >= A.W) continue;
+            float d[8];
+            eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
 #pragma unroll
-                for (int ff = 0; ff < P; ++ff)
-                  if (ff == f) red[h][1 + ff] = fmaf(vv[h], d[k], red[h][1 + ff]);
-              }
-            }
+            for (int k = 0; k < 8; ++k)
+              if (k < np) sd[k] = fmaf(wr[h][rx], d[k], sd[k]);
           }
+          scatter(A.unconv_acc[cm], np, h, sd);
+        }
+      }
+    } else {
+      for (int cm = 0; cm < m.n_comp; ++cm) {
+        if (!m.conv[cm]) continue;
+        const int np = m.np[cm];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !has1) continue;
+          float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int rx = 0; rx < 8; ++rx) {
+            const int j = j0 + col0 + rx;
+            if (i >= A.H || j >= A.W) continue;
+            float d[8];
+            eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (k < np) sd[k] = fmaf(vv[h][rx], d[k], sd[k]);
+          }
+          scatter(A.conv_acc[cm], np, h, sd);
         }
       }
     }
