@@ -162,12 +162,12 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArgs A) {
   __shared__ float s_cc[kMaxComp * kCC];
   __shared__ float s_scale[kMaxSlots];
-  __shared__ float s_v[256 * 2 * kMaxPairs];
+  __shared__ float s_v[256 * 2 * kMaxPairs];  // channel-major: this thread's channel ch at ch * 256 + tid
   const ChanMap& m = A.m;
   const int tid = threadIdx.x;
   if (blockIdx.x == 0 && tid < 3 && A.zero[tid]) *A.zero[tid] = 0;
   const int n = A.n_items_dev ? *A.n_items_dev : A.n_items;
-  float* v = s_v + tid * 2 * kMaxPairs;
+  float* v = s_v + tid;  // v[ch * 256]: consecutive threads, consecutive banks
   float2* out = reinterpret_cast<float2*>(A.planes);
   for (int item = blockIdx.x; item < n; item += gridDim.x) {
     const int2 it = A.items[item];
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
       const int pix = r * 256 + tid;
       const int i = i0 + pix / kTile, j = j0 + pix % kTile;
       if (i >= H || j >= Wp) continue;
-      for (int ch = 0; ch < 2 * m.ncp; ++ch) v[ch] = 0.f;
+      for (int ch = 0; ch < 2 * m.ncp; ++ch) v[ch * 256] = 0.f;
       if (j < W) {
         for (int cm = 0; cm < m.n_comp; ++cm) {
           if (!m.conv[cm]) continue;
@@ -192,19 +192,19 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
           const float val = eval_component(m.kind[cm], s_cc + cm * kCC, i, j, d);
           v[0] += val;
           if (MODE == MODE_MODEL) {
-            if (m.comp_chan[cm] >= 0) v[m.comp_chan[cm]] += val;
+            if (m.comp_chan[cm] >= 0) v[m.comp_chan[cm] * 256] += val;
           } else {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {  // compile-time k keeps d in registers
               if (k >= m.np[cm]) break;
               const int ch = m.chan[cm][k];
-              if (ch >= 0) v[ch] += d[k] * s_scale[m.slot[cm][k]];
+              if (ch >= 0) v[ch * 256] += d[k] * s_scale[m.slot[cm][k]];
             }
           }
         }
       }
       for (int cp = 0; cp < m.ncp; ++cp)
-        out[pbase + ((size_t)cp * H + i) * Wp + j] = make_float2(v[2 * cp], v[2 * cp + 1]);
+        out[pbase + ((size_t)cp * H + i) * Wp + j] = make_float2(v[2 * cp * 256], v[(2 * cp + 1) * 256]);
     }
   }
 }

@@ -984,7 +984,8 @@ int gm_chi2_grad(const gm_model_desc* desc, const gm_batch* batch, const double*
   if ((rc = setup_pass(MODE_NORMAL, desc, batch, params, workspace, ws_bytes, st, &pc))) return rc;
   if ((rc = launch_pass(MODE_NORMAL, &pc, st))) return rc;
   const int G = batch->n_gal;
-  k_chi2_grad_finish<<<(G + 127) / 128, 128, 0, st>>>(pc.pl.dd, G, pc.A.geo, pc.A.partial, chi2, grad, jtj);
+  k_chi2_grad_finish<<<(G + kLmWarps - 1) / kLmWarps, 32 * kLmWarps, 0, st>>>(pc.pl.dd, G, pc.A.geo, pc.A.partial,
+                                                                                chi2, grad, jtj);
   GM_LAUNCHED("k_chi2_grad_finish");
   return GM_OK;
 }
@@ -1107,7 +1108,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
     kf<<<grid, sm.threads, sm.total, cap>>>(A);
     GM_LAUNCHED("k_fused(normal)");
     GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 2], cap, cudaEventRecordExternal));
-    k_lm_step<<<(G + 31) / 32, 32, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst, scale);
+    k_lm_step<<<(G + kLmBlock - 1) / kLmBlock, kLmBlock, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst, scale);
     GM_LAUNCHED("k_lm_step");
     GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 3], cap, cudaEventRecordExternal));
   }

@@ -243,27 +243,44 @@ __device__ inline double gn_decrement(const double* Ap, const double* g, int P) 
 // accepted step lowers chi^2 by less than tol relative, any evaluated step
 // is below xtol, or the Gauss-Newton decrement at the best point is at most
 // gtol chi^2; STALLED / SINGULAR past lambda_max; MAX_ITER at max_iter.
-__global__ void k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O, int cur,
-                          const GalGeom* __restrict__ geo, const double* __restrict__ partial, float* cconst,
-                          float* scale) {
-  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+// One thread per active galaxy, 32 galaxies per block.  The block first sums
+// its galaxies' tile partials together, the lanes taking (galaxy, entry) pairs in
+// turn so that neighbouring lanes read neighbouring entries, each entry over
+// its galaxy's tiles in tile order (deterministic), into shared memory; then
+// every thread takes its galaxy's LM step in FP64.
+constexpr int kLmWarps = 4;   // warps per block of k_chi2_grad_finish (one galaxy per warp)
+constexpr int kLmBlock = 32;  // galaxies (threads) per block of k_lm_step
+
+__global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O,
+                                                      int cur, const GalGeom* __restrict__ geo,
+                                                      const double* __restrict__ partial, float* cconst,
+                                                      float* scale) {
+  __shared__ double s_acc[kLmBlock][kMaxAcc];
+  const int lane = threadIdx.x;
+  const int gi0 = blockIdx.x * kLmBlock, gi = gi0 + lane;
   const int n_cur = *S.count[cur];
   if (gi == 0) atomicAdd(S.evals, (unsigned long long)n_cur);
+  const int nb = min(kLmBlock, n_cur - gi0);  // galaxies of this block (the same for every lane)
+  if (nb <= 0) return;
+  const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
+  for (int x = lane; x < nb * NA; x += kLmBlock) {
+    const int q = x / NA, e = x - q * NA;
+    const int gq = S.list[cur][gi0 + q];
+    const int n_tiles = geo[gq].n_tiles;
+    const double* pp = partial + (size_t)geo[gq].tile0 * NA + e;
+    double a = 0.0;
+    for (int t = 0; t < n_tiles; ++t) a += pp[(size_t)t * NA];
+    s_acc[q][e] = a;
+  }
+  __syncwarp();
   if (gi >= n_cur) return;
   const int g = S.list[cur][gi];
-  const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
+  const double* acc = s_acc[lane];
+
   double* pb = S.p_b + (size_t)g * NS;
   double* pt = S.p_t + (size_t)g * NS;
   double* Ab = S.A_b + (size_t)g * NAp;
   double* gb = S.g_b + (size_t)g * P;
-
-  // sums of the tile partials in tile order (deterministic)
-  double acc[kMaxAcc];
-  for (int e = 0; e < NA; ++e) acc[e] = 0.0;
-  const int n_tiles = geo[g].n_tiles;
-  const double* pp = partial + (size_t)geo[g].tile0 * NA;
-  for (int t = 0; t < n_tiles; ++t)
-    for (int e = 0; e < NA; ++e) acc[e] += pp[t * NA + e];
   const double chi2_t = acc[0];
 
   int st = ST_RUNNING;
@@ -456,17 +473,26 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
 
 #ifdef GM_HOST_TU
 // gm_chi2_grad outputs from the tile partials (physical coordinates).
-__global__ void k_chi2_grad_finish(const __grid_constant__ DescDev D, int G, const GalGeom* __restrict__ geo,
-                                   const double* __restrict__ partial, double* chi2, double* grad, double* jtj) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per galaxy, as k_lm_step: tile sums by the lanes, outputs by lane 0.
+__global__ void __launch_bounds__(32 * kLmWarps) k_chi2_grad_finish(const __grid_constant__ DescDev D, int G,
+                                                                     const GalGeom* __restrict__ geo,
+                                                                     const double* __restrict__ partial,
+                                                                     double* chi2, double* grad, double* jtj) {
+  __shared__ double s_acc[kLmWarps][kMaxAcc];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int g = blockIdx.x * kLmWarps + wl;
   if (g >= G) return;
   const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
-  double acc[kMaxAcc];
-  for (int e = 0; e < NA; ++e) acc[e] = 0.0;
   const int n_tiles = geo[g].n_tiles;
   const double* pp = partial + (size_t)geo[g].tile0 * NA;
-  for (int t = 0; t < n_tiles; ++t)
-    for (int e = 0; e < NA; ++e) acc[e] += pp[t * NA + e];
+  for (int e = lane; e < NA; e += 32) {
+    double a = 0.0;
+    for (int t = 0; t < n_tiles; ++t) a += pp[t * NA + e];
+    s_acc[wl][e] = a;
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  const double* acc = s_acc[wl];
   chi2[g] = acc[0];
   if (grad) {
     double* gr = grad + (size_t)g * NS;
