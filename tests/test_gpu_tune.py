@@ -1,9 +1,10 @@
 """Launch shapes of the fused pass (gm_tune_set) and the autotuner.
 
 Every shape computes the same normal equations: the pairs of a pass are
-spread over the thread groups, and only the split of a tile's pixels over
-threads in the FP32 reduction changes, so results agree with the default
-shape to the parity tolerances of the chi^2 tests."""
+spread over the thread groups (a two-pair pass on two groups is split by PSF
+rows instead, the second group adding its half), so only FP32 summation
+orders change, in the correlation and in the reduction, and results agree
+with the default shape to the parity tolerances of the chi^2 tests."""
 import math
 
 import numpy as np
