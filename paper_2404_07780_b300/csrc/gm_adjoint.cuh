@@ -268,16 +268,15 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
         }
       }
     }
-    // ---- block reduction: warp shuffles, then across the 4 warps, FP64 per tile ----
+    // ---- block reduction: warp sums (recursive halving), then across the 4 warps, FP64 per tile ----
+    {
+      float flat[2 * NA];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int e = 0; e < NA; ++e) {
-        float v = red[h][e];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_red[(wig * 2 + h) * NA + e] = v;
-      }
+        for (int e = 0; e < NA; ++e) flat[h * NA + e] = red[h][e];
+      warp_sum_scatter(flat, lane, [&](int t, float v) { s_red[wig * 2 * NA + t] = v; });
+    }
     __syncthreads();
     for (int t = tid; t < 2 * NA; t += blockDim.x) {
       const int h = t / NA, e = t - h * NA;

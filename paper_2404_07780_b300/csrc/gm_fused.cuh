@@ -511,6 +511,53 @@ __device__ __forceinline__ void add_pairs(const u64 (&acc)[CP][8], float* s_out,
   }
 }
 
+// Warp sums of N values that every lane holds, by recursive halving: at the
+// level with xor mask M each lane keeps one half of its current entries (the
+// upper half when its bit M is set, the odd middle entry with the lower lane)
+// and adds its partner's copy of that half.  After the levels M = 16 .. 1 the
+// warp sum of each entry sits in exactly one lane, where store(entry, sum) is
+// called: about N shuffles instead of 5 N for a butterfly per entry.
+template <int N, int M>
+struct WarpScatter {
+  template <class Store>
+  static __device__ __forceinline__ void run(const float (&v)[N], const int (&idx)[N], int lane, Store& store) {
+    constexpr int H = (N + 1) / 2;  // the lower half, with the odd middle entry
+    constexpr int NP = N - H;       // entries that pair off
+    const bool up = lane & M;
+    float nv[H];
+    int ni[H];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const float send = up ? v[i] : v[H + i];
+      const float keep = up ? v[H + i] : v[i];
+      nv[i] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+      ni[i] = up ? idx[H + i] : idx[i];
+    }
+    if constexpr (H > NP) {
+      nv[H - 1] = v[H - 1] + __shfl_xor_sync(0xffffffffu, v[H - 1], M);
+      ni[H - 1] = up ? -1 : idx[H - 1];  // the upper lane's copy is a duplicate
+    }
+    WarpScatter<H, M / 2>::run(nv, ni, lane, store);
+  }
+};
+template <int N>
+struct WarpScatter<N, 0> {
+  template <class Store>
+  static __device__ __forceinline__ void run(const float (&v)[N], const int (&idx)[N], int, Store& store) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (idx[i] >= 0) store(idx[i], v[i]);
+  }
+};
+
+template <int N, class Store>
+__device__ __forceinline__ void warp_sum_scatter(const float (&v)[N], int lane, Store store) {
+  int idx[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) idx[i] = i;
+  WarpScatter<N, 16>::run(v, idx, lane, store);
+}
+
 // Accumulate J^T W J (packed upper triangle), J^T W r and chi^2 for P free
 // parameters over this thread's pixels of the tile, reduce over the block and
 // write the tile's FP64 partial sums.
@@ -564,13 +611,7 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
       }
   }
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-#pragma unroll
-  for (int e = 0; e < NA; ++e) {
-    float v = acc[e];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_red[warp * NA + e] = v;
-  }
+  warp_sum_scatter(acc, lane, [&](int e, float v) { s_red[warp * NA + e] = v; });
   __syncthreads();
   for (int e = tid; e < NA; e += nthr) {
     double s = 0.0;
