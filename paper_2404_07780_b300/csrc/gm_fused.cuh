@@ -423,8 +423,11 @@ __device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const 
 }
 
 // Correlate CP pair planes (local indices lp0 .. lp0+CP-1 of the pass buffer)
-// for one thread's 8 output pixels over PSF rows [a_lo, a_hi).
-template <int CP>
+// for one thread's 8 output pixels over PSF rows [a_lo, a_hi).  With BLOCKS,
+// each block of kRowBlock PSF rows is summed into its own partial first (lower
+// FP32 accumulation error, at CP x 8 more registers: the 512-thread two-pair
+// instances go without, to stay within 128 registers).
+template <int CP, bool BLOCKS = true>
 __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2* s_in, const u64* s_psf,
                                                 int lp0, int plane, int rw, int K, int row, int col0, int a_lo,
                                                 int a_hi) {
@@ -436,6 +439,15 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
   const int K2 = K + 1;
   const int nf = (K - 1) >> 1;         // full 2-tap chunks per PSF row
   const int cpad = ((K - 1) >> 1) & 1;  // zero position in front of the taps
+  if (!BLOCKS) {
+    for (int a = a_lo; a < a_hi; ++a) {
+      const float2* irow[CP];
+#pragma unroll
+      for (int q = 0; q < CP; ++q) irow[q] = s_in + (size_t)(lp0 + q) * plane + (size_t)(row + a) * rw + col0;
+      corr_row<CP>(acc, irow, s_psf + a * K2, nf, cpad);
+    }
+    return;
+  }
   for (int a0 = a_lo; a0 < a_hi; a0 += kRowBlock) {
     u64 part[CP][8];
 #pragma unroll
@@ -561,11 +573,11 @@ __device__ __forceinline__ void warp_sum_scatter(const float (&v)[N], int lane, 
 // Accumulate J^T W J (packed upper triangle), J^T W r and chi^2 for P free
 // parameters over this thread's pixels of the tile, reduce over the block and
 // write the tile's FP64 partial sums.
-template <int P>
+template <int P, int kMinThreads>
 __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_out, float* s_red, size_t base, int H,
                                             int W, size_t prow, int i0, int j0) {
   constexpr int NA = 1 + P + P * (P + 1) / 2;
-  constexpr int kPx = kTilePix / kGroupThreads;  // pixels per thread in the smallest block
+  constexpr int kPx = kTilePix / kMinThreads;  // pixels per thread in the smallest block of the instance
   float acc[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) acc[e] = 0.f;
@@ -626,8 +638,10 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
 // CPT = channel pairs per thread: 1 (128 threads per pair, up to 512 threads)
 // or 2 (fewer threads with the register budget the reduction of many free
 // parameters needs).
-template <int MODE, int P, int CPT>
-__global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_constant__ FusedArgs A) {
+// WIDE (with CPT = 2): 512 threads in four groups; each two groups share two pairs of
+// a four-pair pass, split by PSF rows (launched only in that shape).
+template <int MODE, int P, int CPT, int WIDE>
+__global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const __grid_constant__ FusedArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   u64* s_psf = reinterpret_cast<u64*>(smem + A.off_psf);
   float2* s_in = reinterpret_cast<float2*>(smem + A.off_in);
@@ -706,17 +720,19 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
       const int first = pass * A.pp;
       const int npass = min(A.pp, m.ncp - first);
       const int ngroups = nthr / kGroupThreads;
-      // two pairs on two groups: rather than one pair per thread (8 accumulators, measured
-      // ~16% slower per FMA), both groups take both pairs over half of the PSF rows each
-      const bool split = CPT == 2 && npass == 2 && ngroups == 2;
+      // as many pairs as groups (two or four): rather than one pair per thread (8
+      // accumulators, measured ~16% slower per FMA), groups 2k and 2k+1 both take pairs
+      // 2k and 2k+1, over half of the PSF rows each
+      const bool split = CPT == 2 && npass == ngroups && (ngroups == 2 || ngroups == 4);
       const int base = npass / ngroups, rem = npass - base * ngroups;
       const int npair = split ? 2 : base + (grp < rem ? 1 : 0);
-      const int lp0 = split ? 0 : grp * base + min(grp, rem);
+      const int lp0 = split ? (grp & ~1) : grp * base + min(grp, rem);
       const int a_mid = (a_lo + a_hi) >> 1;
-      const int ga_lo = split && grp == 1 ? a_mid : a_lo, ga_hi = split && grp == 0 ? a_mid : a_hi;
+      const int ga_lo = split && (grp & 1) ? a_mid : a_lo, ga_hi = split && !(grp & 1) ? a_mid : a_hi;
       u64 acc2[2][8];
       u64 acc1[1][8];
-      if (CPT == 2 && npair == 2) correlate_pairs<2>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, ga_lo, ga_hi);
+      if (CPT == 2 && npair == 2)
+        correlate_pairs<2, !WIDE>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, ga_lo, ga_hi);
       else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
       __syncthreads();  // every warp is done reading the window
       if (tid == 0) {
@@ -725,9 +741,9 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
           issue_pass(A, s_info[slot ^ 1], s_in, bar, 0, s_psf, s_cc0 + (slot ^ 1) * cc_n, s_scale0 + (slot ^ 1) * sc_n);
       }
       if (split) {
-        if (grp == 0) store_pairs<2>(acc2, s_out, first, m.nch_conv, row, col0);
+        if (!(grp & 1)) store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
         __syncthreads();
-        if (grp == 1) add_pairs<2>(acc2, s_out, first, m.nch_conv, row, col0);
+        if (grp & 1) add_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
       } else if (CPT == 2 && npair == 2) {
         store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
       } else if (npair == 1) {
@@ -791,7 +807,7 @@ __global__ void __launch_bounds__(CPT == 1 ? 512 : 256, 1) k_fused(const __grid_
         }
       }
     } else {
-      reduce_tile<P>(A, s_out, s_red, pix0, H, W, (size_t)I.geo.tile0 + I.tile, i0, j0);
+      reduce_tile<P, WIDE ? 512 : kGroupThreads>(A, s_out, s_red, pix0, H, W, (size_t)I.geo.tile0 + I.tile, i0, j0);
     }
     slot ^= 1;
   }

@@ -3,7 +3,7 @@
 #include "gm_instances.h"
 
 namespace gm {
-#define GM_X(M, P, C) template __global__ void k_fused<M, P, C>(const __grid_constant__ FusedArgs);
+#define GM_X(M, P, C, W) template __global__ void k_fused<M, P, C, W>(const __grid_constant__ FusedArgs);
 GM_FUSED_LIST_3(GM_X)
 #undef GM_X
 }  // namespace gm

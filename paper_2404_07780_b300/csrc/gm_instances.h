@@ -4,13 +4,14 @@
 // which launches the instances through function pointers.
 #pragma once
 
-// k_fused<MODE, P, CPT>: MODE_MODEL = 0, MODE_NORMAL = 1; P free parameters;
-// CPT channel pairs per thread (1: up to 512 threads; 2: up to 256 threads
-// with the register budget of many free parameters).
-#define GM_FUSED_LIST_0(X) X(0, 0, 1) X(1, 0, 1) X(1, 1, 1) X(1, 2, 1) X(1, 3, 1) X(1, 4, 1) X(1, 5, 1) X(1, 6, 1)
-#define GM_FUSED_LIST_1(X) X(1, 7, 1) X(1, 8, 1) X(1, 9, 1) X(1, 10, 1) X(1, 0, 2) X(1, 1, 2) X(1, 2, 2) X(1, 3, 2)
-#define GM_FUSED_LIST_2(X) X(1, 4, 2) X(1, 5, 2) X(1, 6, 2) X(1, 7, 2) X(1, 8, 2) X(1, 9, 2) X(1, 10, 2) X(1, 11, 2)
-#define GM_FUSED_LIST_3(X) X(1, 12, 2) X(1, 13, 2) X(1, 14, 2) X(1, 15, 2) X(1, 16, 2)
+// k_fused<MODE, P, CPT, WIDE>: MODE_MODEL = 0, MODE_NORMAL = 1; P free
+// parameters; CPT channel pairs per thread (1: up to 512 threads; 2: up to 256
+// threads with the register budget of many free parameters); WIDE = 1 with
+// CPT = 2: 512 threads in four groups, two groups per two pairs of a pass.
+#define GM_FUSED_LIST_0(X) X(0, 0, 1, 0) X(1, 0, 1, 0) X(1, 1, 1, 0) X(1, 2, 1, 0) X(1, 3, 1, 0) X(1, 4, 1, 0) X(1, 5, 1, 0) X(1, 6, 1, 0)
+#define GM_FUSED_LIST_1(X) X(1, 7, 1, 0) X(1, 8, 1, 0) X(1, 9, 1, 0) X(1, 10, 1, 0) X(1, 0, 2, 0) X(1, 1, 2, 0) X(1, 2, 2, 0) X(1, 3, 2, 0)
+#define GM_FUSED_LIST_2(X) X(1, 4, 2, 0) X(1, 5, 2, 0) X(1, 6, 2, 0) X(1, 7, 2, 0) X(1, 8, 2, 0) X(1, 9, 2, 0) X(1, 10, 2, 0) X(1, 11, 2, 0)
+#define GM_FUSED_LIST_3(X) X(1, 12, 2, 0) X(1, 13, 2, 0) X(1, 14, 2, 0) X(1, 15, 2, 0) X(1, 16, 2, 0)
 
 // k_adjoint<MODE, P>: ADJ_RESID = 0, ADJ_GRAD = 1
 #define GM_ADJ_LIST_0(X) \
@@ -20,5 +21,9 @@
   X(0, 9) X(1, 9) X(0, 10) X(1, 10) X(0, 11) X(1, 11) X(0, 12) X(1, 12) X(0, 13) X(1, 13) X(0, 14) X(1, 14) \
   X(0, 15) X(1, 15) X(0, 16) X(1, 16)
 
-#define GM_FUSED_ALL(X) GM_FUSED_LIST_0(X) GM_FUSED_LIST_1(X) GM_FUSED_LIST_2(X) GM_FUSED_LIST_3(X)
+#define GM_FUSED_LIST_4(X) \
+  X(1, 1, 2, 1) X(1, 2, 2, 1) X(1, 3, 2, 1) X(1, 4, 2, 1) X(1, 5, 2, 1) X(1, 6, 2, 1) X(1, 7, 2, 1) X(1, 8, 2, 1) \
+  X(1, 9, 2, 1)
+
+#define GM_FUSED_ALL(X) GM_FUSED_LIST_0(X) GM_FUSED_LIST_1(X) GM_FUSED_LIST_2(X) GM_FUSED_LIST_3(X) GM_FUSED_LIST_4(X)
 #define GM_ADJ_ALL(X) GM_ADJ_LIST_0(X) GM_ADJ_LIST_1(X)

@@ -24,7 +24,7 @@
 
 namespace gm {
 // the tile kernels are instantiated in gm_inst_*.cu
-#define GM_X(M, P, C) extern template __global__ void k_fused<M, P, C>(const __grid_constant__ FusedArgs);
+#define GM_X(M, P, C, W) extern template __global__ void k_fused<M, P, C, W>(const __grid_constant__ FusedArgs);
 GM_FUSED_ALL(GM_X)
 #undef GM_X
 #define GM_X(M, P) extern template __global__ void k_adjoint<M, P>(const __grid_constant__ AdjArgs);
@@ -301,13 +301,26 @@ ChanMap chan_map(const Plan& pl) {
 
 typedef void (*FusedKernel)(FusedArgs);
 
-// The fused kernel for (mode, P, pairs per thread), or nullptr when not built.
-FusedKernel pick_kernel(int mode, int P, int cpt) {
-#define GM_X(M, PP, C) \
-  if (mode == M && (M == MODE_MODEL || P == PP) && cpt == C) return k_fused<M, PP, C>;
+// A launch shape of two pairs per thread in four groups runs the 512-thread instance.
+bool wide_shape(int cpt, int groups) { return cpt == 2 && groups > 2; }
+
+// The fused kernel for (mode, P, pairs per thread, wide), or nullptr when not built.
+FusedKernel pick_kernel(int mode, int P, int cpt, bool wide) {
+#define GM_X(M, PP, C, W) \
+  if (mode == M && (M == MODE_MODEL || P == PP) && cpt == C && (int)wide == W) return k_fused<M, PP, C, W>;
   GM_FUSED_ALL(GM_X)
 #undef GM_X
   return nullptr;
+}
+
+// Launch shapes: pp pairs per pass, cpt pairs per thread, groups of 128 threads.  One
+// pair per thread: up to 4 groups; two pairs per thread: up to 2 groups, or 4 groups
+// with 4 pairs per pass (each two groups split two pairs by PSF rows).
+bool shape_valid(int pp, int cpt, int groups) {
+  if (pp < 1 || pp > kMaxPassPairs || (cpt != 1 && cpt != 2) || groups < 1) return false;
+  if (cpt == 1) return groups <= 4 && pp <= groups;
+  if (groups == 4) return pp == 4;
+  return groups <= 2 && pp <= 2 * groups;
 }
 
 struct Smem {
@@ -365,9 +378,8 @@ thread_local TuneShape g_last_shape = {0, 0, 0};
 // bound) and the carve-up fits the device.
 bool shape_ok(const Plan& pl, int K, int n_comp, int n_slots, int smem_optin, int mode, const TuneShape& t,
               Smem* out) {
-  if (t.pp < 1 || t.pp > std::min(kMaxPassPairs, pl.ncp) || (t.cpt != 1 && t.cpt != 2)) return false;
-  if (t.groups < 1 || t.groups > (t.cpt == 1 ? 4 : 2) || t.pp > t.cpt * t.groups) return false;
-  if (!pick_kernel(mode, pl.dd.P, t.cpt)) return false;
+  if (!shape_valid(t.pp, t.cpt, t.groups) || t.pp > pl.ncp) return false;
+  if (!pick_kernel(mode, pl.dd.P, t.cpt, wide_shape(t.cpt, t.groups))) return false;
   const Smem s = smem_layout(pl, K, n_comp, n_slots, t.pp, t.cpt, t.groups);
   if (s.total > smem_optin) return false;
   *out = s;
@@ -714,7 +726,7 @@ PlaneArgs plane_args(const Plan& pl, const GalGeom* geo, const float* cconst, co
 }
 
 int prepare_fused(int mode, const Plan& pl, const Smem& sm, FusedKernel* out) {
-  FusedKernel k = pick_kernel(mode, pl.dd.P, sm.cpt);
+  FusedKernel k = pick_kernel(mode, pl.dd.P, sm.cpt, wide_shape(sm.cpt, sm.groups));
   if (!k) return fail(GM_E_UNSUPPORTED, "no fused kernel for %d free parameters", pl.dd.P);
   GM_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm.total));
   *out = k;
@@ -918,8 +930,7 @@ int gm_tune_set(int32_t K, int32_t P, int32_t pairs_per_pass, int32_t pairs_per_
     g_tune.erase(std::make_pair(K, P));
     return GM_OK;
   }
-  if (pairs_per_pass < 1 || pairs_per_pass > kMaxPassPairs || (pairs_per_thread != 1 && pairs_per_thread != 2) ||
-      groups < 1 || groups > (pairs_per_thread == 1 ? 4 : 2) || pairs_per_pass > pairs_per_thread * groups)
+  if (!shape_valid(pairs_per_pass, pairs_per_thread, groups))
     return fail(GM_E_INVAL, "gm_tune_set: shape (%d pairs/pass, %d pairs/thread, %d groups) is not a launch shape",
                 pairs_per_pass, pairs_per_thread, groups);
   g_tune[std::make_pair(K, P)] = TuneShape{pairs_per_pass, pairs_per_thread, groups};
