@@ -41,13 +41,23 @@ TOL = 1e-6
 MAX_ITER = 200
 PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
-# DRAM bytes (read + write) of k_fused<NORMAL, 8, 2> per galaxy evaluated, from one ncu capture of a
-# 1,024-galaxy pass of this workload (712.7 MB); traffic grows in proportion to the galaxies a pass
-# evaluates, so a launch's traffic is this times its galaxies
-FUSED_DRAM_BYTES_PER_GALAXY = 712.657e6 / 1024
-# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,627.9 MB
+# DRAM bytes (read + write) of the SDSS-shaped fit's fused pass (k_fused<NORMAL, 8, 2, WIDE>, the
+# tuned shape) per galaxy evaluated, from one ncu capture of a 1,024-galaxy pass of this workload
+# (711.6 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
+# this times its galaxies
+FUSED_DRAM_BYTES_PER_GALAXY = 711.614e6 / 1024
+
+
+def fused_name(P, shape):
+    """The fused-pass instance a launch shape (pairs per pass, per thread, groups) runs."""
+    pp, cpt, groups = shape
+    wide = ",WIDE" if cpt == 2 and groups > 2 else ""
+    return f"k_fused<NORMAL,{P},{cpt}{wide}> ({pp} pairs per pass, {cpt} per thread, {groups} x 128 threads)"
+
+
+# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,625.3 MB
 # for a 2,048-galaxy pass of 45.59 M pixels)
-UNEVEN_DRAM_BYTES_PER_PIXEL = 2627.856e6 / 45591296
+UNEVEN_DRAM_BYTES_PER_PIXEL = 2625.325e6 / 45591296
 
 
 def workload_config(G, H, K):
@@ -334,7 +344,7 @@ def run_gpu(args, world, rank, local):
             "traffic": FUSED_DRAM_BYTES_PER_GALAXY * evals / max(launches_fused, 1),
             "traffic_unit": "bytes per launch (average launch)",
             "algorithmic_bytes": (9 + 32) * H * H * evals / max(launches_fused, 1),
-            "kernel": "k_fused<NORMAL,8,2>",
+            "kernel": fused_name(8, gm.gm_tune_last_shape()),
             "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
 
     cpu = None
