@@ -121,9 +121,9 @@ struct FusedArgs {
   const float* sigma;
   const uint8_t* mask;
   const float* psf;
-  const u64* psf_pad;        // [G][psf_stride]: each PSF as K rows of K+1 duplicated taps (pack2(v, v)),
-                             // padded as in shared memory, copied into s_psf by the bulk-copy unit
-  int psf_stride;            // u64 elements per galaxy in psf_pad (an even number)
+  const float* psf_pad;      // [G][psf_stride]: each PSF as K rows of psf_row_floats(K) floats, laid
+                             // out as in shared memory, copied into s_psf by the bulk-copy unit
+  int psf_stride;            // floats per galaxy in psf_pad (a multiple of 4)
   const float* cconst;       // [G][n_comp][kCC]
   const float* scale;        // [G][scale_stride(n_slots)]
   double* partial;           // [tile0_g + tile][nacc]
@@ -273,7 +273,7 @@ __device__ __forceinline__ void fetch_item(const FusedArgs& A, int n_items, int 
 // galaxy's padded PSF rows into s_psf and its constants into the item's
 // constant buffers (s_cc, s_scale of `slot`), on the same mbarrier.
 __device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I, float2* s_in, u64* bar, int pass,
-                                           u64* s_psf, float* s_cc, float* s_scale) {
+                                           float* s_psf, float* s_cc, float* s_scale) {
   const GalGeom& G = I.geo;
   const int K = G.K, c = (K - 1) / 2, cpad = c & 1;
   const int i0 = (I.tile / G.tiles_x) * kTile, j0 = (I.tile % G.tiles_x) * kTile;
@@ -287,7 +287,7 @@ __device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<u64>(map))
                  : "memory");
   }
-  const unsigned psf_bytes = (unsigned)K * (K + 1) * 8u;
+  const unsigned psf_bytes = (unsigned)K * psf_row_floats(K) * 4u;
   const unsigned cc_bytes = (unsigned)A.m.n_comp * kCC * 4u;
   const unsigned sc_bytes = (unsigned)scale_stride(A.m.n_slots) * 4u;
   // order this CTA's earlier generic-proxy reads of the buffers before the async-proxy writes
@@ -422,13 +422,153 @@ __device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const 
   if (tail) corr_chunk<CP, 4, 1>(acc, w, pp, irow, prow, b + 8);
 }
 
+// PSF rows of the fused pass in shared memory: single floats, row a of K taps
+// at floats a * psf_row_floats(K) + 3 cpad + t (gm_geom.cuh).
+
+// A chunk of the float-PSF loop: taps t0, t1 (scalars from one float4) become
+// the packed multipliers by register moves.  Ring, window loads and halves as
+// in corr_chunk; measured ~8 % more FMAs per clock than loading packed pairs.
+template <int CP, int R, int HALF = 0>
+__device__ __forceinline__ void corr_chunk_f(u64 (&acc)[CP][8], u64 (&w)[CP][10], float t0, float t1,
+                                             const float2* const (&irow)[CP], int b) {
+  constexpr int L = (2 * R + 8) % 10;
+  if (HALF != 1) {
+#pragma unroll
+    for (int q = 0; q < CP; ++q) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + b + 8);
+      w[q][L] = v.x;
+      w[q][L + 1] = v.y;
+    }
+  }
+  const u64 px = pack2(t0, t0), py = pack2(t1, t1);
+#pragma unroll
+  for (int q = 0; q < CP; ++q) {
+    if (HALF != 2) {
+#pragma unroll
+      for (int rx = 0; rx < 8; ++rx) acc[q][rx] = ffma2(px, w[q][(2 * R + rx) % 10], acc[q][rx]);
+    }
+    if (HALF != 1) {
+#pragma unroll
+      for (int rx = 0; rx < 8; ++rx) acc[q][rx] = ffma2(py, w[q][(2 * R + 1 + rx) % 10], acc[q][rx]);
+    }
+  }
+}
+
+// Two chunks (rotations R0, R1) from the float4 cur; the next float4 is read first.
+template <int CP, int R0, int R1>
+__device__ __forceinline__ void corr_pair_f(u64 (&acc)[CP][8], u64 (&w)[CP][10], float4& cur, const float4* next,
+                                            const float2* const (&irow)[CP], int b) {
+  const float4 nx = *next;
+  corr_chunk_f<CP, R0>(acc, w, cur.x, cur.y, irow, b);
+  corr_chunk_f<CP, R1>(acc, w, cur.z, cur.w, irow, b + 2);
+  cur = nx;
+}
+
+// One PSF row into acc from the float layout above: the head half (cpad = 1,
+// the row's float 3), nf full chunks two per float4 (ten per loop iteration),
+// the tail half (cpad = 0).
+template <int CP>
+__device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const (&irow)[CP], const float* prow,
+                                         int nf, int cpad) {
+  u64 w[CP][10];
+  const float4* pf = reinterpret_cast<const float4*>(prow);
+  int b = 0;
+  if (cpad) {
+#pragma unroll
+    for (int q = 0; q < CP; ++q)
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
+        w[q][(8 + e) % 10] = v.x;
+        w[q][(9 + e) % 10] = v.y;
+      }
+    const float4 h = pf[0];
+    corr_chunk_f<CP, 4, 2>(acc, w, 0.f, h.w, irow, 0);
+    b = 2;
+    ++pf;
+  } else {
+#pragma unroll
+    for (int q = 0; q < CP; ++q)
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
+        w[q][e] = v.x;
+        w[q][e + 1] = v.y;
+      }
+  }
+  float4 cur = pf[0];
+  for (; nf >= 10; nf -= 10) {
+    corr_pair_f<CP, 0, 1>(acc, w, cur, pf + 1, irow, b);
+    corr_pair_f<CP, 2, 3>(acc, w, cur, pf + 2, irow, b + 4);
+    corr_pair_f<CP, 4, 0>(acc, w, cur, pf + 3, irow, b + 8);
+    corr_pair_f<CP, 1, 2>(acc, w, cur, pf + 4, irow, b + 12);
+    corr_pair_f<CP, 3, 4>(acc, w, cur, pf + 5, irow, b + 16);
+    pf += 5;
+    b += 20;
+  }
+  // nf = 0..9 full chunks (rotations 0, 1, ...) from cur on, then the tail half
+  const bool tail = !cpad;
+  if (nf == 0) {
+    if (tail) corr_chunk_f<CP, 0, 1>(acc, w, cur.x, 0.f, irow, b);
+    return;
+  }
+  if (nf == 1) {
+    corr_chunk_f<CP, 0>(acc, w, cur.x, cur.y, irow, b);
+    if (tail) corr_chunk_f<CP, 1, 1>(acc, w, cur.z, 0.f, irow, b + 2);
+    return;
+  }
+  corr_pair_f<CP, 0, 1>(acc, w, cur, pf + 1, irow, b);
+  if (nf == 2) {
+    if (tail) corr_chunk_f<CP, 2, 1>(acc, w, cur.x, 0.f, irow, b + 4);
+    return;
+  }
+  if (nf == 3) {
+    corr_chunk_f<CP, 2>(acc, w, cur.x, cur.y, irow, b + 4);
+    if (tail) corr_chunk_f<CP, 3, 1>(acc, w, cur.z, 0.f, irow, b + 6);
+    return;
+  }
+  corr_pair_f<CP, 2, 3>(acc, w, cur, pf + 2, irow, b + 4);
+  if (nf == 4) {
+    if (tail) corr_chunk_f<CP, 4, 1>(acc, w, cur.x, 0.f, irow, b + 8);
+    return;
+  }
+  if (nf == 5) {
+    corr_chunk_f<CP, 4>(acc, w, cur.x, cur.y, irow, b + 8);
+    if (tail) corr_chunk_f<CP, 0, 1>(acc, w, cur.z, 0.f, irow, b + 10);
+    return;
+  }
+  corr_pair_f<CP, 4, 0>(acc, w, cur, pf + 3, irow, b + 8);
+  if (nf == 6) {
+    if (tail) corr_chunk_f<CP, 1, 1>(acc, w, cur.x, 0.f, irow, b + 12);
+    return;
+  }
+  if (nf == 7) {
+    corr_chunk_f<CP, 1>(acc, w, cur.x, cur.y, irow, b + 12);
+    if (tail) corr_chunk_f<CP, 2, 1>(acc, w, cur.z, 0.f, irow, b + 14);
+    return;
+  }
+  corr_pair_f<CP, 1, 2>(acc, w, cur, pf + 4, irow, b + 12);
+  if (nf == 8) {
+    if (tail) corr_chunk_f<CP, 3, 1>(acc, w, cur.x, 0.f, irow, b + 16);
+    return;
+  }
+  corr_chunk_f<CP, 3>(acc, w, cur.x, cur.y, irow, b + 16);  // nf == 9
+  if (tail) corr_chunk_f<CP, 4, 1>(acc, w, cur.z, 0.f, irow, b + 18);
+}
+
+// Start of PSF row a in either layout.
+__device__ __forceinline__ const u64* psf_row_ptr(const u64* s_psf, int a, int K) { return s_psf + a * (K + 1); }
+__device__ __forceinline__ const float* psf_row_ptr(const float* s_psf, int a, int K) {
+  return s_psf + a * psf_row_floats(K);
+}
+
 // Correlate CP pair planes (local indices lp0 .. lp0+CP-1 of the pass buffer)
 // for one thread's 8 output pixels over PSF rows [a_lo, a_hi).  With BLOCKS,
 // each block of kRowBlock PSF rows is summed into its own partial first (lower
 // FP32 accumulation error, at CP x 8 more registers: the 512-thread two-pair
 // instances go without, to stay within 128 registers).
-template <int CP, bool BLOCKS = true>
-__device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2* s_in, const u64* s_psf,
+template <int CP, bool BLOCKS = true, class PsfT = u64>
+__device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2* s_in, const PsfT* s_psf,
                                                 int lp0, int plane, int rw, int K, int row, int col0, int a_lo,
                                                 int a_hi) {
   const u64 one2 = pack2(1.f, 1.f);
@@ -436,7 +576,6 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
   for (int q = 0; q < CP; ++q)
 #pragma unroll
     for (int rx = 0; rx < 8; ++rx) acc[q][rx] = 0ull;
-  const int K2 = K + 1;
   const int nf = (K - 1) >> 1;         // full 2-tap chunks per PSF row
   const int cpad = ((K - 1) >> 1) & 1;  // zero position in front of the taps
   if (!BLOCKS) {
@@ -444,7 +583,7 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
       const float2* irow[CP];
 #pragma unroll
       for (int q = 0; q < CP; ++q) irow[q] = s_in + (size_t)(lp0 + q) * plane + (size_t)(row + a) * rw + col0;
-      corr_row<CP>(acc, irow, s_psf + a * K2, nf, cpad);
+      corr_row<CP>(acc, irow, psf_row_ptr(s_psf, a, K), nf, cpad);
     }
     return;
   }
@@ -459,7 +598,7 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
       const float2* irow[CP];
 #pragma unroll
       for (int q = 0; q < CP; ++q) irow[q] = s_in + (size_t)(lp0 + q) * plane + (size_t)(row + a) * rw + col0;
-      corr_row<CP>(part, irow, s_psf + a * K2, nf, cpad);
+      corr_row<CP>(part, irow, psf_row_ptr(s_psf, a, K), nf, cpad);
     }
 #pragma unroll
     for (int q = 0; q < CP; ++q)
@@ -643,7 +782,7 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
 template <int MODE, int P, int CPT, int WIDE>
 __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const __grid_constant__ FusedArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
-  u64* s_psf = reinterpret_cast<u64*>(smem + A.off_psf);
+  float* s_psf = reinterpret_cast<float*>(smem + A.off_psf);
   float2* s_in = reinterpret_cast<float2*>(smem + A.off_in);
   float* s_out = reinterpret_cast<float*>(smem + A.off_out);
   float* s_cc0 = reinterpret_cast<float*>(smem + A.off_cc);        // [2][n_comp * kCC], alternating per item

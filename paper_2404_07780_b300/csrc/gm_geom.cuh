@@ -34,6 +34,15 @@ __host__ __device__ inline int scale_stride(int n_slots) { return (n_slots + 3) 
 // >= K + 33 (the register window reads two columns past the last tap) and
 // == 2 mod 4, so the 8 lanes of a quarter warp (8 consecutive rows) hit
 // distinct 16-byte bank groups.
+// Floats per PSF row of the fused pass (shared memory and the padded copy in the
+// workspace): row a holds tap t at a * psf_row_floats(K) + 3 cpad + t with
+// cpad = ((K-1)/2) & 1, zeros elsewhere.  With the window's alignment shift in
+// front (cpad = 1) the taps sit 3 floats in, so that the full 2-tap chunks
+// start on a 16-byte boundary and one float4 always serves two chunks;
+// roundup4(K + 3) floats cover every read of a row (a multiple of 4, so rows
+// and whole PSFs stay 16-byte aligned for the bulk copy).
+__host__ __device__ inline int psf_row_floats(int K) { return (K + 6) & ~3; }
+
 __host__ __device__ inline int window_pitch(int K) {
   int rw = K + 33;
   while (rw % 4 != 2) ++rw;

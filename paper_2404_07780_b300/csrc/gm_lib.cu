@@ -354,7 +354,7 @@ Smem smem_layout(const Plan& pl, int K, int n_comp, int n_slots, int pp, int cpt
     return (int)o;
   };
   s.off_in = take((size_t)pp * plane_bytes, 128);
-  s.off_psf = take((size_t)K * (K + 1) * 8 + 16, 16);  // + the last chunk's prefetch slack
+  s.off_psf = take((size_t)K * psf_row_floats(K) * 4, 16);
   s.off_out = take((size_t)pl.nch_tot * kTilePix * 4, 16);
   s.off_cc = take((size_t)2 * n_comp * kCC * 4, 16);             // two items' constants
   s.off_scale = take((size_t)2 * scale_stride(n_slots) * 4, 16);
@@ -580,7 +580,7 @@ int plan_geom(const gm_batch* b, int ncp, bool tables, GeomPlan* gp) {
 // adjacent so that an uneven batch's host tables go over in one copy.
 struct WsCore {
   size_t geo, order, items, maps, table_end, cconst, scale, psf_pad, planes, partial, err, queue, total;
-  int psf_stride;  // u64 elements per galaxy in psf_pad: K(K+1) for the batch's largest K
+  int psf_stride;  // floats per galaxy in psf_pad: K psf_row_floats(K) for the batch's largest K
 };
 
 WsCore ws_core(const gm_model_desc* d, const GeomPlan& gp, int nacc) {
@@ -599,8 +599,8 @@ WsCore ws_core(const gm_model_desc* d, const GeomPlan& gp, int nacc) {
   w.table_end = off;
   w.cconst = take(G * d->n_comp * kCC * 4);
   w.scale = take(G * scale_stride(d->n_slots) * 4);
-  w.psf_stride = gp.K * (gp.K + 1);
-  w.psf_pad = take(G * (size_t)w.psf_stride * 8);
+  w.psf_stride = gp.K * psf_row_floats(gp.K);  // the largest PSF of the batch (a multiple of 4 floats)
+  w.psf_pad = take(G * (size_t)w.psf_stride * 4);
   w.planes = take(gp.plane_floats * 4);
   w.partial = take(nacc > 0 ? (size_t)gp.n_items * nacc * 8 : 0);
   w.err = take(4);
@@ -785,27 +785,26 @@ LMOpts lm_opts(const gm_fit_opts* o) {
 }
 
 // Each galaxy's PSF as the fused kernel holds it in shared memory: K rows of
-// K+1 taps (one zero on the left when c = (K-1)/2 is odd, else on the right),
-// each tap duplicated into both halves of an f32x2 lane pair.
+// psf_row_floats(K) floats, tap t of row a at a * psf_row_floats(K) + 3 cpad + t
+// (cpad = ((K-1)/2) & 1), zeros elsewhere.
 __global__ void k_psf_pad(int G, const GalGeom* __restrict__ geo, const float* __restrict__ psf, int stride,
-                          unsigned long long* out) {
+                          float* out) {
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
-    const int K = geo[g].K, K2 = K + 1, cpad = ((K - 1) / 2) & 1;
+    const int K = geo[g].K, KF = psf_row_floats(K), cpad = ((K - 1) / 2) & 1;
     const float* p = psf + geo[g].psf;
-    for (int e = threadIdx.x; e < K * K2; e += blockDim.x) {
-      const int a = e / K2, b = e - a * K2 - cpad;
-      const float v = (b >= 0 && b < K) ? p[a * K + b] : 0.f;
-      out[(size_t)g * stride + e] = pack2(v, v);
+    for (int e = threadIdx.x; e < K * KF; e += blockDim.x) {
+      const int a = e / KF, t = e - a * KF - 3 * cpad;
+      out[(size_t)g * stride + e] = (t >= 0 && t < K) ? p[a * K + t] : 0.f;
     }
   }
 }
 
 int launch_psf_pad(int G, const GalGeom* geo, const float* psf, const WsCore& w, char* ws, const DevInfo& di,
                    cudaStream_t st, FusedArgs* A) {
-  A->psf_pad = (const u64*)(ws + w.psf_pad);
+  A->psf_pad = (const float*)(ws + w.psf_pad);
   A->psf_stride = w.psf_stride;
   k_psf_pad<<<std::max(1, std::min(G, 8 * di.sms)), 256, 0, st>>>(G, geo, psf, w.psf_stride,
-                                                                    (unsigned long long*)(ws + w.psf_pad));
+                                                                    (float*)(ws + w.psf_pad));
   GM_LAUNCHED("k_psf_pad");
   return GM_OK;
 }
