@@ -43,9 +43,9 @@ PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
 # DRAM bytes (read + write) of the SDSS-shaped fit's fused pass (k_fused<NORMAL, 8, 2, WIDE>, the
 # tuned shape) per galaxy evaluated, from one ncu capture of a 1,024-galaxy pass of this workload
-# (711.6 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
+# (706.3 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
 # this times its galaxies
-FUSED_DRAM_BYTES_PER_GALAXY = 711.614e6 / 1024
+FUSED_DRAM_BYTES_PER_GALAXY = 706.344e6 / 1024
 
 
 def fused_name(P, shape):
@@ -55,9 +55,9 @@ def fused_name(P, shape):
     return f"k_fused<NORMAL,{P},{cpt}{wide}> ({pp} pairs per pass, {cpt} per thread, {groups} x 128 threads)"
 
 
-# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,625.3 MB
+# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,613.5 MB
 # for a 2,048-galaxy pass of 45.59 M pixels)
-UNEVEN_DRAM_BYTES_PER_PIXEL = 2625.325e6 / 45591296
+UNEVEN_DRAM_BYTES_PER_PIXEL = 2613.519e6 / 45591296
 
 
 def workload_config(G, H, K):
