@@ -377,9 +377,8 @@ int gm_bootstrap(const gm_model_desc *desc, const gm_batch *batch, const double 
  *   pairs_per_pass    channel pairs loaded and correlated per shared-memory pass, 1..4
  *   pairs_per_thread  1 or 2
  *   groups            groups of 128 threads, 1..4 (1..2 with 2 pairs per thread,
- *                     or 4 with 2 pairs per thread and 4 pairs per pass: each
- *                     two groups then split two pairs by PSF rows; built for
- *                     1..9 free parameters);
+ *                     or 4 with 2 pairs per thread and 4 or 2 pairs per pass:
+ *                     each two (four) groups then split two pairs by PSF rows);
  *                     pairs_per_pass <= pairs_per_thread * groups
  * pairs_per_pass = 0 removes the (K, P) entry.  A shape that the device's
  * shared memory or the built kernels cannot run is ignored at launch in favour

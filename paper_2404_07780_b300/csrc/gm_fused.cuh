@@ -709,17 +709,52 @@ __device__ __forceinline__ void warp_sum_scatter(const float (&v)[N], int lane, 
   WarpScatter<N, 16>::run(v, idx, lane, store);
 }
 
+// The accumulators [E0, E1) of the tile's normal equations over this thread's
+// pixels (loaded by reduce_tile), then their warp sums into s_red.  Entry 0 is
+// chi^2, 1..P J^T W r, then J^T W J packed by rows of its upper triangle.
+template <int P, int kPx, int E0, int E1>
+__device__ __forceinline__ void reduce_range(const float* s_out, float* s_red, const float (&dv)[kPx],
+                                             const float (&sv)[kPx], const bool (&use)[kPx], int tid, int nthr,
+                                             int lane, int warp) {
+  constexpr int NA = 1 + P + P * (P + 1) / 2;
+  float acc[E1 - E0];
+#pragma unroll
+  for (int e = 0; e < E1 - E0; ++e) acc[e] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPx; ++k) {
+    if (!use[k]) continue;
+    const int op = out_idx(tid + k * nthr);
+    const float isg = 1.f / sv[k];
+    const float rr = (dv[k] - s_out[op]) * isg;  // (D - M) / sigma
+    if (E0 == 0) acc[0] = fmaf(rr, rr, acc[0]);
+    float jw[P > 0 ? P : 1];
+#pragma unroll
+    for (int f = 0; f < P; ++f) jw[f] = s_out[(1 + f) * kTilePix + op] * isg;  // J / sigma
+#pragma unroll
+    for (int f = 0; f < P; ++f)
+      if (1 + f >= E0 && 1 + f < E1) acc[1 + f - E0] = fmaf(jw[f], rr, acc[1 + f - E0]);
+    int e = 1 + P;
+#pragma unroll
+    for (int f = 0; f < P; ++f)
+#pragma unroll
+      for (int h = f; h < P; ++h) {
+        if (e >= E0 && e < E1) acc[e - E0] = fmaf(jw[f], jw[h], acc[e - E0]);
+        ++e;
+      }
+  }
+  warp_sum_scatter(acc, lane, [&](int e, float v) { s_red[warp * NA + E0 + e] = v; });
+}
+
 // Accumulate J^T W J (packed upper triangle), J^T W r and chi^2 for P free
 // parameters over this thread's pixels of the tile, reduce over the block and
-// write the tile's FP64 partial sums.
-template <int P, int kMinThreads>
+// write the tile's FP64 partial sums.  NCH > 1 accumulates the entries in that
+// many ranges one after the other (fewer live registers, the pixels' loads
+// shared), for the 512-thread instances of many free parameters.
+template <int P, int kMinThreads, int NCH = 1>
 __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_out, float* s_red, size_t base, int H,
                                             int W, size_t prow, int i0, int j0) {
   constexpr int NA = 1 + P + P * (P + 1) / 2;
   constexpr int kPx = kTilePix / kMinThreads;  // pixels per thread in the smallest block of the instance
-  float acc[NA];
-#pragma unroll
-  for (int e = 0; e < NA; ++e) acc[e] = 0.f;
   const int tid = threadIdx.x, nthr = blockDim.x;
   // every image, sigma and mask load of this thread's pixels first, so that the
   // tile waits for one memory latency rather than one per pixel (loading them
@@ -740,29 +775,18 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
       if (A.mask) use[k] = A.mask[gp] == 0;
     }
   }
-#pragma unroll
-  for (int k = 0; k < kPx; ++k) {
-    if (!use[k]) continue;
-    const int op = out_idx(tid + k * nthr);
-    const float isg = 1.f / sv[k];
-    const float rr = (dv[k] - s_out[op]) * isg;  // (D - M) / sigma
-    acc[0] = fmaf(rr, rr, acc[0]);
-    float jw[P > 0 ? P : 1];
-#pragma unroll
-    for (int f = 0; f < P; ++f) jw[f] = s_out[(1 + f) * kTilePix + op] * isg;  // J / sigma
-#pragma unroll
-    for (int f = 0; f < P; ++f) acc[1 + f] = fmaf(jw[f], rr, acc[1 + f]);
-    int e = 1 + P;
-#pragma unroll
-    for (int f = 0; f < P; ++f)
-#pragma unroll
-      for (int h = f; h < P; ++h) {
-        acc[e] = fmaf(jw[f], jw[h], acc[e]);
-        ++e;
-      }
-  }
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-  warp_sum_scatter(acc, lane, [&](int e, float v) { s_red[warp * NA + e] = v; });
+  static_assert(NCH >= 1 && NCH <= 3, "one to three accumulator ranges");
+  if constexpr (NCH == 1) {
+    reduce_range<P, kPx, 0, NA>(s_out, s_red, dv, sv, use, tid, nthr, lane, warp);
+  } else if constexpr (NCH == 2) {
+    reduce_range<P, kPx, 0, NA / 2>(s_out, s_red, dv, sv, use, tid, nthr, lane, warp);
+    reduce_range<P, kPx, NA / 2, NA>(s_out, s_red, dv, sv, use, tid, nthr, lane, warp);
+  } else {
+    reduce_range<P, kPx, 0, NA / 3>(s_out, s_red, dv, sv, use, tid, nthr, lane, warp);
+    reduce_range<P, kPx, NA / 3, 2 * NA / 3>(s_out, s_red, dv, sv, use, tid, nthr, lane, warp);
+    reduce_range<P, kPx, 2 * NA / 3, NA>(s_out, s_red, dv, sv, use, tid, nthr, lane, warp);
+  }
   __syncthreads();
   for (int e = tid; e < NA; e += nthr) {
     double s = 0.0;
@@ -777,8 +801,9 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
 // CPT = channel pairs per thread: 1 (128 threads per pair, up to 512 threads)
 // or 2 (fewer threads with the register budget the reduction of many free
 // parameters needs).
-// WIDE (with CPT = 2): 512 threads in four groups; each two groups share two pairs of
-// a four-pair pass, split by PSF rows (launched only in that shape).
+// WIDE (with CPT = 2): 512 threads in four groups, launched only with 4 pairs per pass
+// (groups 2k and 2k+1 split pairs 2k and 2k+1 by PSF rows) or 2 (all four groups split
+// both pairs); the reduction accumulates in ranges of up to 52 entries.
 template <int MODE, int P, int CPT, int WIDE>
 __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const __grid_constant__ FusedArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -859,15 +884,18 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
       const int first = pass * A.pp;
       const int npass = min(A.pp, m.ncp - first);
       const int ngroups = nthr / kGroupThreads;
-      // as many pairs as groups (two or four): rather than one pair per thread (8
-      // accumulators, measured ~16% slower per FMA), groups 2k and 2k+1 both take pairs
-      // 2k and 2k+1, over half of the PSF rows each
-      const bool split = CPT == 2 && npass == ngroups && (ngroups == 2 || ngroups == 4);
+      // fewer pairs than two per group: rather than one pair per thread (8 accumulators,
+      // measured ~16% slower per FMA), the pass's pairs go in sets of two to gps = 2 or 4
+      // groups each, which take both pairs over their part of each warp's PSF rows
+      const int nsets = npass >> 1;
+      const int gps = nsets > 0 ? ngroups / nsets : 0;
+      const bool split = CPT == 2 && (npass & 1) == 0 && nsets * gps == ngroups && (gps == 2 || (WIDE && gps == 4));
       const int base = npass / ngroups, rem = npass - base * ngroups;
       const int npair = split ? 2 : base + (grp < rem ? 1 : 0);
-      const int lp0 = split ? (grp & ~1) : grp * base + min(grp, rem);
-      const int a_mid = (a_lo + a_hi) >> 1;
-      const int ga_lo = split && (grp & 1) ? a_mid : a_lo, ga_hi = split && !(grp & 1) ? a_mid : a_hi;
+      const int part = split ? grp % gps : 0;
+      const int lp0 = split ? 2 * (grp / gps) : grp * base + min(grp, rem);
+      const int ga_lo = split ? a_lo + part * (a_hi - a_lo) / gps : a_lo;
+      const int ga_hi = split ? a_lo + (part + 1) * (a_hi - a_lo) / gps : a_hi;
       u64 acc2[2][8];
       u64 acc1[1][8];
       if (CPT == 2 && npair == 2)
@@ -880,9 +908,12 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
           issue_pass(A, s_info[slot ^ 1], s_in, bar, 0, s_psf, s_cc0 + (slot ^ 1) * cc_n, s_scale0 + (slot ^ 1) * sc_n);
       }
       if (split) {
-        if (!(grp & 1)) store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
-        __syncthreads();
-        if (grp & 1) add_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
+        // the first part stores, the others add in turn
+        if (part == 0) store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
+        for (int q = 1; q < gps; ++q) {
+          __syncthreads();
+          if (part == q) add_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
+        }
       } else if (CPT == 2 && npair == 2) {
         store_pairs<2>(acc2, s_out, first + lp0, m.nch_conv, row, col0);
       } else if (npair == 1) {
@@ -946,7 +977,9 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
         }
       }
     } else {
-      reduce_tile<P, WIDE ? 512 : kGroupThreads>(A, s_out, s_red, pix0, H, W, (size_t)I.geo.tile0 + I.tile, i0, j0);
+      constexpr int NA = 1 + P + P * (P + 1) / 2;
+      reduce_tile<P, WIDE ? 512 : kGroupThreads, WIDE ? (NA + 51) / 52 : 1>(A, s_out, s_red, pix0, H, W,
+                                                                          (size_t)I.geo.tile0 + I.tile, i0, j0);
     }
     slot ^= 1;
   }

@@ -7,7 +7,7 @@
 // k_fused<MODE, P, CPT, WIDE>: MODE_MODEL = 0, MODE_NORMAL = 1; P free
 // parameters; CPT channel pairs per thread (1: up to 512 threads; 2: up to 256
 // threads with the register budget of many free parameters); WIDE = 1 with
-// CPT = 2: 512 threads in four groups, two groups per two pairs of a pass.
+// CPT = 2: 512 threads in four groups, 2 or 4 groups per two pairs of a pass.
 #define GM_FUSED_LIST_0(X) X(0, 0, 1, 0) X(1, 0, 1, 0) X(1, 1, 1, 0) X(1, 2, 1, 0) X(1, 3, 1, 0) X(1, 4, 1, 0) X(1, 5, 1, 0) X(1, 6, 1, 0)
 #define GM_FUSED_LIST_1(X) X(1, 7, 1, 0) X(1, 8, 1, 0) X(1, 9, 1, 0) X(1, 10, 1, 0) X(1, 0, 2, 0) X(1, 1, 2, 0) X(1, 2, 2, 0) X(1, 3, 2, 0)
 #define GM_FUSED_LIST_2(X) X(1, 4, 2, 0) X(1, 5, 2, 0) X(1, 6, 2, 0) X(1, 7, 2, 0) X(1, 8, 2, 0) X(1, 9, 2, 0) X(1, 10, 2, 0) X(1, 11, 2, 0)
@@ -23,7 +23,7 @@
 
 #define GM_FUSED_LIST_4(X) \
   X(1, 1, 2, 1) X(1, 2, 2, 1) X(1, 3, 2, 1) X(1, 4, 2, 1) X(1, 5, 2, 1) X(1, 6, 2, 1) X(1, 7, 2, 1) X(1, 8, 2, 1) \
-  X(1, 9, 2, 1)
+  X(1, 9, 2, 1) X(1, 10, 2, 1) X(1, 11, 2, 1) X(1, 12, 2, 1) X(1, 13, 2, 1) X(1, 14, 2, 1) X(1, 15, 2, 1) X(1, 16, 2, 1)
 
 #define GM_FUSED_ALL(X) GM_FUSED_LIST_0(X) GM_FUSED_LIST_1(X) GM_FUSED_LIST_2(X) GM_FUSED_LIST_3(X) GM_FUSED_LIST_4(X)
 #define GM_ADJ_ALL(X) GM_ADJ_LIST_0(X) GM_ADJ_LIST_1(X)

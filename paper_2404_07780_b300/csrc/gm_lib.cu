@@ -315,11 +315,12 @@ FusedKernel pick_kernel(int mode, int P, int cpt, bool wide) {
 
 // Launch shapes: pp pairs per pass, cpt pairs per thread, groups of 128 threads.  One
 // pair per thread: up to 4 groups; two pairs per thread: up to 2 groups, or 4 groups
-// with 4 pairs per pass (each two groups split two pairs by PSF rows).
+// with 4 pairs per pass (each two groups split two pairs by PSF rows) or with 2 (all
+// four groups split both pairs).
 bool shape_valid(int pp, int cpt, int groups) {
   if (pp < 1 || pp > kMaxPassPairs || (cpt != 1 && cpt != 2) || groups < 1) return false;
   if (cpt == 1) return groups <= 4 && pp <= groups;
-  if (groups == 4) return pp == 4;
+  if (groups == 4) return pp == 4 || pp == 2;
   return groups <= 2 && pp <= 2 * groups;
 }
 

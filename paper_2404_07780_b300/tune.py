@@ -20,10 +20,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(_HERE, "tuning.json")
 
 # (pairs per pass, pairs per thread, thread groups): every pair of a pass has a group and no
-# group is idle in a full pass; (4, 2, 4) is the 512-thread shape whose group pairs split
-# two pairs each by PSF rows
+# group is idle in a full pass; (4, 2, 4) and (2, 2, 4) are the 512-thread shapes whose
+# groups split two pairs by PSF rows, two or four groups per two pairs
 SHAPES = [(pp, cpt, groups) for cpt in (1, 2) for groups in range(1, (4 if cpt == 1 else 2) + 1)
-          for pp in range(1, 5) if groups <= pp <= cpt * groups] + [(4, 2, 4)]
+          for pp in range(1, 5) if groups <= pp <= cpt * groups] + [(4, 2, 4), (2, 2, 4)]
 
 
 def device_name() -> str:

@@ -176,7 +176,8 @@ def test_tune_set_rejects_shapes_that_are_not_launch_shapes(lib):
     assert lib.gm_tune_set(41, 8, 4, 1, 3) == -1      # a pair without a thread group
     assert lib.gm_tune_set(41, 8, 2, 2, 3) == -1      # 3 groups of 2-pair threads exceed 256 threads
     assert lib.gm_tune_set(41, 8, 4, 2, 4) == 0       # 4 groups of 2-pair threads: the row-split shape
-    assert lib.gm_tune_set(41, 8, 2, 2, 4) == -1      # ... which needs 4 pairs per pass
+    assert lib.gm_tune_set(41, 8, 2, 2, 4) == 0       # ... or with 2 pairs per pass, each split 4 ways
+    assert lib.gm_tune_set(41, 8, 3, 2, 4) == -1      # ... but not with 3
     assert lib.gm_tune_set(41, 8, 0, 0, 0) == 0
     assert lib.gm_tune_set(41, 8, 2, 3, 1) == -1      # 3 pairs per thread is not built
     assert lib.gm_tune_clear() == 0
