@@ -43,9 +43,9 @@ PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
 # DRAM bytes (read + write) of the SDSS-shaped fit's fused pass (k_fused<NORMAL, 8, 2, WIDE>, the
 # tuned shape) per galaxy evaluated, from one ncu capture of a 1,024-galaxy pass of this workload
-# (706.3 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
+# (705.6 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
 # this times its galaxies
-FUSED_DRAM_BYTES_PER_GALAXY = 706.344e6 / 1024
+FUSED_DRAM_BYTES_PER_GALAXY = 705.632e6 / 1024
 
 
 def fused_name(P, shape):
@@ -55,9 +55,9 @@ def fused_name(P, shape):
     return f"k_fused<NORMAL,{P},{cpt}{wide}> ({pp} pairs per pass, {cpt} per thread, {groups} x 128 threads)"
 
 
-# the same for k_fused<NORMAL, 12, 2> on the uneven workload, per stamp pixel evaluated (2,613.5 MB
-# for a 2,048-galaxy pass of 45.59 M pixels)
-UNEVEN_DRAM_BYTES_PER_PIXEL = 2613.519e6 / 45591296
+# the same for the uneven workload's fused pass (k_fused<NORMAL, 12, 2, WIDE>, the tuned shape), per
+# stamp pixel evaluated (2,613.4 MB for a 2,048-galaxy pass of 45.59 M pixels)
+UNEVEN_DRAM_BYTES_PER_PIXEL = 2613.437e6 / 45591296
 
 
 def workload_config(G, H, K):
@@ -469,7 +469,7 @@ def run_uneven(args, world, rank, local):
             "traffic": UNEVEN_DRAM_BYTES_PER_PIXEL * pix / max(sum(st["passes"] for st in stats), 1),
             "traffic_unit": "bytes per launch (average launch)",
             "algorithmic_bytes": 56.0 * pix / max(sum(st["passes"] for st in stats), 1),
-            "kernel": "k_fused<NORMAL,12,2> (uneven items, per-class TMA maps)",
+            "kernel": fused_name(12, gm.gm_tune_last_shape()) + ", uneven items, per-class TMA maps",
             "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
 
     # end to end through the public API from pinned host buffers
@@ -651,7 +651,7 @@ def run_learned(args, world, rank, local):
     achieved = flops / (fused_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-            "kernel": "k_fused<NORMAL,12,2> (evaluations x mean taps of the batch)",
+            "kernel": fused_name(12, gm.gm_tune_last_shape()) + ", evaluations x mean taps of the batch",
             "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz (no FP32 figure is measured)"}
     c2_d, c2_l = d["chi2"].cpu().numpy(), r["chi2"].cpu().numpy()
     dof = d["dof"].cpu().numpy().astype(np.float64)
