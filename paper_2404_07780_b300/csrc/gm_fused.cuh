@@ -23,11 +23,14 @@
 //       padding of conv2d(..., padding="same");
 //     * each thread owns 8 adjacent output pixels of one row and CPT channel
 //       pairs and runs the sliding-window correlation (one 16-byte shared
-//       load per 2 taps per pair, one 16-byte PSF load per 2 taps, 16 packed
+//       load per 2 taps per pair, one 16-byte load of 4 single-float PSF taps
+//       per 2 chunks, the packed multipliers made by register moves, 16
 //       fma.rn.f32x2 per tap pair and channel pair), summing each block of 4
 //       PSF rows into a separate partial (FP32 rounding error ~3x lower than
-//       one running sum); PSF rows whose input rows all fall outside the
-//       stamp for the warp are skipped;
+//       one running sum; the 512-thread instances sum without); PSF rows
+//       whose input rows all fall outside the stamp for the warp are skipped;
+//       a pass with fewer than two pairs per group splits two pairs between
+//       two or four groups by PSF rows;
 //     * the next load (next pass or next item) is issued as soon as every
 //       warp has finished reading the window, so it overlaps the stores and
 //       the reduction.  Thread 0 claims the next item and reads its record at
@@ -38,10 +41,11 @@
 //   FP64 partial per tile); MODEL mode writes the model and component images.
 //
 // The correlation is M[i,j] = sum_ab P[a,b] I[i+a-c, j+b-c] (cross-correlation,
-// torch conv2d semantics, App. C of arxiv 2404.07780).  In shared memory each
-// PSF row is padded to K+1 taps with one zero: on the right when c = (K-1)/2 is
-// even, on the left when c is odd, so that the window's first column j0 - c'
-// (c' = c or c+1) is even and the TMA start coordinate is 16-byte aligned.
+// torch conv2d semantics, App. C of arxiv 2404.07780).  The window starts at
+// column j0 - c' (c' = c or c+1, c = (K-1)/2), whichever is even, so that the
+// TMA start coordinate is 16-byte aligned; the PSF rows carry the matching
+// shift (psf_row_floats in gm_geom.cuh; the adjoint's two-galaxy rows: K+1
+// packed positions with one zero, on the left when c is odd).
 #pragma once
 
 #include <cuda.h>
