@@ -1,0 +1,100 @@
+"""Parity at the size the bench times: the SDSS-shaped batch of 8,192 stamps of
+128 x 128 with 41 x 41 PSFs (1.2 GB of inputs), in the launch shape the tuning
+table gives it, against the FP64 oracle on sampled galaxies.
+
+The oracle cannot render or fit 8,192 galaxies in a test's time, so the batch
+is made of a few galaxies of the recipe rendered by the oracle, repeated: slot g
+holds source g % S.  The GPU runs over the whole batch exactly as the bench
+launches it (every tile of every slot through the persistent item queue); its
+outputs at sampled slots (the first, the last and across the batch) must match
+the oracle's values for their source to the tolerances of test_gpu_parity.py,
+and every copy of a source must give bit-identical results (no interference
+between galaxies, tiles or queue items at full size)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from cases import from_batch
+from paper_2404_07780_b300 import synth
+from test_gpu_parity import FIT_TIGHT, _compare_fits, _oracle_normal, oracle_inputs
+
+pytestmark = pytest.mark.gpu
+
+G_FULL = 8192  # the bench's batch
+S = 6          # oracle-rendered sources
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2404_07780_b300 import gm as gmod
+    from paper_2404_07780_b300.build import build_lib
+    build_lib()
+    gmod.load()
+    c = from_batch(synth.draw_sdss(seed=1000, G=S), at="init")
+    src = np.arange(G_FULL) % S
+    t = dict(params=torch.from_numpy(np.ascontiguousarray(c.params[src])).cuda(),
+             psf=torch.from_numpy(np.ascontiguousarray(c.psf[src])).cuda(),
+             image=torch.from_numpy(np.ascontiguousarray(c.image[src])).cuda(),
+             sigma=torch.from_numpy(np.ascontiguousarray(c.sigma[src])).cuda(),
+             mask=torch.from_numpy(np.ascontiguousarray(c.mask[src])).cuda())
+    return gmod, c, src, t
+
+
+def _sampled():
+    rng = np.random.default_rng(0)
+    return sorted(set([0, 1, S - 1, G_FULL // 2, G_FULL - 2, G_FULL - 1] + list(rng.integers(0, G_FULL, 6))))
+
+
+def _same_per_source(x, src):
+    for s in range(S):
+        rows = x[src == s]
+        assert (rows == rows[0]).all(), s  # bit-identical copies
+
+
+def test_fullsize_normal_equations(full):
+    gm, c, src, t = full
+    chi2, grad, jtj = gm.gm_chi2_grad(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"],
+                                      want_grad=True, want_jtj=True)
+    # the launch shape the bench runs for this workload (K = 41, 8 free parameters)
+    from paper_2404_07780_b300 import tune
+    entries = tune.read_cache().get(tune.device_name(), {}).get("entries", [])
+    tuned = [(e["pairs_per_pass"], e["pairs_per_thread"], e["groups"]) for e in entries if (e["K"], e["P"]) == (41, 8)]
+    if tuned:
+        assert gm.gm_tune_last_shape() == tuned[0]
+    chi2, grad, jtj = (x.cpu().numpy() for x in (chi2, grad, jtj))
+    for x in (chi2, grad, jtj):
+        _same_per_source(x, src)
+    rchi2, rg, rA = _oracle_normal(c)
+    free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
+    for g in _sampled():
+        s = src[g]
+        assert abs(chi2[g] - rchi2[s]) <= 1e-5 * rchi2[s], g
+        d = np.sqrt(np.diag(rA[s]))
+        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 2e-4 * d * math.sqrt(rchi2[s])).all(), g
+        assert (np.abs(jtj[g][np.ix_(free, free)] - rA[s]) <= 1e-4 * np.outer(d, d)).all(), g
+
+
+def test_fullsize_fit(full):
+    gm, c, src, t = full
+    got = gm.gm_fit_batch(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"],
+                          gm.FitOptions(**FIT_TIGHT))
+    got = {k: v.cpu().numpy() for k, v in got.items()}
+    for k in ("params", "chi2", "status", "iters", "sigma_p"):
+        _same_per_source(got[k], src)
+    n = 4  # sources fitted by the oracle
+    oi = oracle_inputs(c)
+    ref = oracle.fit(c.spec, c.params[:n], oi["psf"][:n], oi["image"][:n], oi["sigma"][:n], c.mask[:n],
+                     oracle.FitOptions(**FIT_TIGHT))
+    picks = [g for g in _sampled() if src[g] < n]
+    sub = {k: v[picks] for k, v in got.items()}
+    rsub = {k: np.asarray(v)[src[picks]] for k, v in ref.items() if np.ndim(v) > 0}
+    same, rel = _compare_fits(c.spec, sub, rsub)
+    # from the default start a fit may settle in another minimum; those that reach the
+    # oracle's chi^2 must agree, and at least half of the sources must
+    assert len(set(src[np.array(picks)[same]])) >= n // 2, (sub["status"], rsub["status"], sub["chi2"], rsub["chi2"])
+    assert rel[same].max() <= 1e-4, rel[same].max(axis=1)
