@@ -98,3 +98,46 @@ def test_fullsize_fit(full):
     # oracle's chi^2 must agree, and at least half of the sources must
     assert len(set(src[np.array(picks)[same]])) >= n // 2, (sub["status"], rsub["status"], sub["chi2"], rsub["chi2"])
     assert rel[same].max() <= 1e-4, rel[same].max(axis=1)
+
+
+def test_fullsize_uneven_normal_equations(full):
+    """The uneven workload's batch as the bench draws it: 32,768 bulge+disk stamps of side
+    48-256 with PSF sides 25-51, every slot at its recipe geometry and start.  Sampled slots
+    carry their galaxy rendered by the oracle; the others hold flat images (10 +- 2) and delta
+    PSFs made on the host, so that the pass runs over the full geometry mix while the oracle
+    renders only what is compared."""
+    import torch
+    from test_gpu_uneven import _oracle_normal_one
+    gm = full[0]
+    G = 32768
+    rb = synth.draw_uneven_bulge_disk(seed=2000, G=G, sides=(48, 64, 96, 128, 192, 256), ks=tuple(range(25, 52, 2)))
+    po, ko = rb.pix_offsets(), rb.psf_offsets()
+    image = np.full(po[-1], 10.0, np.float32)
+    sigma = np.full(po[-1], 2.0, np.float32)
+    mask = np.zeros(po[-1], np.uint8)
+    psf = np.zeros(ko[-1], np.float32)
+    k = rb.geom[:, 2].astype(np.int64)
+    psf[ko[:-1] + (k * k) // 2] = 1.0  # centre tap of each odd-sided PSF
+    rng = np.random.default_rng(1)
+    picks = sorted(set([0, G // 2, G - 1] + list(rng.integers(0, G, 9))))
+    cases = {}
+    for g in picks:
+        cg = from_batch(rb.galaxy(g), at="init")
+        cases[g] = cg
+        image[po[g]:po[g + 1]] = cg.image.ravel()
+        sigma[po[g]:po[g + 1]] = cg.sigma.ravel()
+        if cg.mask is not None:
+            mask[po[g]:po[g + 1]] = cg.mask.ravel()
+        psf[ko[g]:ko[g + 1]] = cg.psf.ravel()
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    chi2, grad, jtj = gm.gm_chi2_grad(rb.spec, t(rb.init), t(image), t(sigma), t(mask), t(psf),
+                                      want_grad=True, want_jtj=True, geom=rb.geom)
+    chi2, grad, jtj = (x.cpu().numpy() for x in (chi2, grad, jtj))
+    free = [i for i in range(rb.spec.n_slots) if rb.spec.free[i]]
+    for g in picks:
+        rc, rg, rA = _oracle_normal_one(cases[g])
+        assert abs(chi2[g] - rc) <= 1e-5 * rc, g
+        d = np.sqrt(np.diag(rA))
+        assert (np.abs(grad[g, free] + 2.0 * rg) <= 2e-4 * d * math.sqrt(rc)).all(), g
+        assert (np.abs(jtj[g][np.ix_(free, free)] - rA) <= 1e-4 * np.outer(d, d)).all(), g
