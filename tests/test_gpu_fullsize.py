@@ -141,3 +141,26 @@ def test_fullsize_uneven_normal_equations(full):
         d = np.sqrt(np.diag(rA))
         assert (np.abs(grad[g, free] + 2.0 * rg) <= 2e-4 * d * math.sqrt(rc)).all(), g
         assert (np.abs(jtj[g][np.ix_(free, free)] - rA) <= 1e-4 * np.outer(d, d)).all(), g
+
+
+def test_fullsize_adjoint_gradient(full):
+    """The gradient workload's batch: 4,096 bulge+bar+nucleus stamps of 96 x 96 with 41 x 41
+    PSFs (15 free parameters) through the adjoint pass, from five oracle-rendered galaxies
+    repeated (an odd count, so that the two galaxies sharing a lane pair differ from pair to
+    pair); sampled slots against the oracle's chi^2 and gradient for their source."""
+    import torch
+    gm = full[0]
+    G, S5 = 4096, 5
+    c = from_batch(synth.draw_bulge_bar_nucleus(seed=3000, G=S5, H=96, W=96, K=41), at="init")
+    src = np.arange(G) % S5
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a[src])).cuda()
+    chi2, grad = gm.gm_grad_adjoint(c.spec, t(c.params), t(c.image), t(c.sigma), t(c.mask), t(c.psf))
+    chi2, grad = chi2.cpu().numpy(), grad.cpu().numpy()
+    rchi2, rg, rA = _oracle_normal(c)
+    free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
+    rng = np.random.default_rng(2)
+    for g in sorted(set([0, 1, G // 2, G - 1] + list(rng.integers(0, G, 8)))):
+        s = src[g]
+        assert abs(chi2[g] - rchi2[s]) <= 1e-5 * rchi2[s], g
+        d = np.sqrt(np.diag(rA[s]))
+        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 2e-4 * d * math.sqrt(rchi2[s])).all(), g
