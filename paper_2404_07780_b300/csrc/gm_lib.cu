@@ -14,6 +14,7 @@
 #include <map>
 #include <tuple>
 #include <mutex>
+#include <set>
 
 #include "../../include/gm.h"
 #include "gm_adjoint.cuh"
@@ -419,6 +420,34 @@ int smem_plan(const Plan& pl, int K, int n_comp, int n_slots, int smem_optin, Sm
 struct DevInfo {
   int sms = 0, smem_optin = 0;
 };
+
+// Fills the nu_n node table of the current device on the first call there
+// (k_nu_table, k_nu_ready, then a stream synchronisation so that no other
+// stream can see a partial table).  While the caller's stream is being
+// captured into a graph it does nothing: set-up kernels then solve nu_n
+// directly, which gives the same constants.
+std::mutex g_nu_mu;
+std::set<int> g_nu_devices;
+
+int ensure_nu_table(cudaStream_t st) {
+  int dev = 0;
+  GM_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(g_nu_mu);
+    if (g_nu_devices.count(dev)) return GM_OK;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GM_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return GM_OK;
+  k_nu_table<<<16, 256, 0, st>>>();
+  GM_LAUNCHED("k_nu_table");
+  k_nu_ready<<<1, 1, 0, st>>>();
+  GM_LAUNCHED("k_nu_ready");
+  GM_CUDA(cudaStreamSynchronize(st));
+  std::lock_guard<std::mutex> lock(g_nu_mu);
+  g_nu_devices.insert(dev);
+  return GM_OK;
+}
 
 int dev_info(DevInfo* di) {
   int dev = 0;
@@ -890,6 +919,7 @@ int setup_pass(int mode, const gm_model_desc* desc, const gm_batch* batch, const
   pc->PA.n_items = A.n_items;
   pc->PA.zero[0] = A.queue;
   GM_CUDA(cudaMemsetAsync(A.err, 0, sizeof(int), st));
+  if ((rc = ensure_nu_table(st))) return rc;
   k_setup<<<(G + 31) / 32, 32, 0, st>>>(pc->pl.dd, G, A.geo, 0, 0, params, 0, cconst, scale);
   GM_LAUNCHED("k_setup");
   return GM_OK;
@@ -1091,6 +1121,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   k_validate<<<std::min(G, 4 * di.sms), 256, 0, st>>>(G, A.geo, batch->image, batch->sigma, batch->mask, S.nused,
                                                       S.bad);
   GM_LAUNCHED("k_validate");
+  if ((rc = ensure_nu_table(st))) return rc;
   k_lm_init<<<(G + 31) / 32, 32, 0, st>>>(pl.dd, S, O, G, A.geo, order, params_inout, cconst, scale);
   GM_LAUNCHED("k_lm_init");
 
@@ -1309,6 +1340,7 @@ int prepare_adjoint(const gm_model_desc* desc, const gm_batch* batch, void* work
 int launch_adjoint(const AdjPass& ap, const gm_batch* batch, const double* params, double* chi2, double* grad,
                    cudaStream_t st) {
   const int G = batch->n_gal;
+  if (int rc = ensure_nu_table(st)) return rc;
   k_setup<<<(G + 31) / 32, 32, 0, st>>>(ap.pl.dd, G, nullptr, batch->H, batch->W, params, 0,
                                         (float*)(ap.ws + ap.w.cconst), (float*)(ap.ws + ap.w.scale));
   GM_LAUNCHED("k_setup");
@@ -1402,6 +1434,7 @@ int gm_fit_adam(const gm_model_desc* desc, const gm_batch* batch, double* params
   S.best = params_inout;
   S.best_chi2 = chi2_out;
   GM_CUDA(cudaMemsetAsync(ap.Ar.err, 0, sizeof(int), st));
+  if (int rc = ensure_nu_table(st)) return rc;
   k_adam_init<<<(G + 127) / 128, 128, 0, st>>>(ap.pl.dd, G, params_inout, cur, S);
   GM_LAUNCHED("k_adam_init");
   for (int t = 1; t <= opts->n_iter; ++t) {
