@@ -20,7 +20,11 @@
  * Stream.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  gm_model and gm_chi2_grad only enqueue work; their outputs are
  *   valid once the stream has synchronised.  gm_fit_batch synchronises the
- *   stream to poll convergence and returns when the fit has finished.
+ *   stream to poll convergence and returns when the fit has finished.  The
+ *   first call on a device that sets up profiles also fills the device's
+ *   table of Sersic nu_n nodes and synchronises its stream once; while the
+ *   stream is being captured into a graph that step is skipped and the set-up
+ *   solves nu_n directly (the same constants).
  * Layout.  Stamps are row-major, H rows x W columns; the pixel in row i,
  *   column j has centre x = j + 0.5, y = H - 0.5 - i (row 0 at the top, the
  *   grid of the App. C listing).  Stamps and PSFs may all have one size or
