@@ -391,3 +391,38 @@ def test_chi2_autograd_function_and_adam(gm):
         val.backward()
         opt.step()
     assert float(f(torch.where(free, u, q)).sum().detach()) < first
+
+
+@pytest.mark.parametrize("n", [0.15, 0.2004, 3.00123, 10.19, 10.5, 11.5])
+def test_sersic_index_on_both_sides_of_the_nu_table(gm, n):
+    # the set-up interpolates nu_n and d nu/dn from FP64 nodes over n in [0.2, 10.2] and
+    # solves directly outside it: model, chi^2, gradient and J^T W J match the oracle either
+    # way (values between nodes and beyond both ends, bounds widened to 0.1..12)
+    H = W = 48
+    spec = synth.ModelSpec().add("sersic", "ser", H, W).add("sky", "sky", H, W, convolve=False)
+    ns = spec.slot("ser.n")
+    spec.lo[ns], spec.hi[ns] = 0.1, 12.0
+    p = np.zeros((1, spec.n_slots))
+    for name, v in (("ser.x0", W / 2 + 0.3), ("ser.y0", H / 2 - 0.2), ("ser.q", 0.7), ("ser.pa", 0.8),
+                    ("ser.Ie", 5.0), ("ser.Re", 6.0), ("ser.n", n), ("sky.Isky", 1.0)):
+        p[0, spec.slot(name)] = v
+    truth = p.copy()
+    truth[0, ns] = n * 1.03
+    truth[0, spec.slot("ser.Re")] = 6.3
+    psf = psf_image("gaussian", synth.psf_params("gaussian", np.array([2.0]), 9)[0], 9)[None]
+    M = oracle.model_images(spec, truth, psf.astype(np.float64), H, W)
+    rng = np.random.default_rng(4)
+    image = (M + rng.normal(size=M.shape)).astype(np.float32)
+    c = Case(spec, p, psf, image, np.ones_like(image), None, H, W)
+    t = c.torch()
+    model = _np(gm.gm_model(spec, t["params"], t["psf"], H, W))
+    assert_model_close(model, oracle.model_images(spec, p, psf.astype(np.float64), H, W))
+    chi2, grad, jtj = gm.gm_chi2_grad(spec, t["params"], t["image"], t["sigma"], None, t["psf"],
+                                      want_grad=True, want_jtj=True)
+    chi2, grad, jtj = _np(chi2), _np(grad), _np(jtj)
+    rchi2, rg, rA = _oracle_normal(c)
+    np.testing.assert_allclose(chi2, rchi2, rtol=1e-5)
+    free = [i for i in range(spec.n_slots) if spec.free[i]]
+    d = np.sqrt(np.diag(rA[0]))
+    assert (np.abs(grad[0, free] + 2.0 * rg[0]) <= 2e-4 * d * math.sqrt(rchi2[0])).all()
+    assert (np.abs(jtj[0][np.ix_(free, free)] - rA[0]) <= 1e-4 * np.outer(d, d)).all()
