@@ -32,6 +32,29 @@ namespace gm {
 
 enum AdjMode { ADJ_RESID = 0, ADJ_GRAD = 1 };
 
+// Pixels of a thread's row of 8 that one iteration of the epilogue loop evaluates.
+constexpr int kEpiPx = 1;
+
+template <int N>
+__device__ __forceinline__ void swap_rows(float (&a)[2][N]) {
+#pragma unroll
+  for (int e = 0; e < N; ++e) {
+    const float t = a[0][e];
+    a[0][e] = a[1][e];
+    a[1][e] = t;
+  }
+}
+
+// a[k] <- a[(k + S) mod 8]
+template <int S>
+__device__ __forceinline__ void rotate_left(float (&a)[8]) {
+  float t[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t[k] = a[(k + S) & 7];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = t[k];
+}
+
 struct AdjArgs {
   CUtensorMap tmap;          // input pair planes [(G+1)/2][H][2*Wp] FP32
   ChanMap m;
@@ -113,43 +136,51 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
   const int K = A.K, c = (K - 1) / 2, K2 = K + 1;
   const int n_pairs = (A.G + 1) / 2;
   const int n_items = n_pairs * A.n_tiles;
-  if ((int)blockIdx.x >= n_items) return;
+  // Each block takes a contiguous range of items: the tiles of one galaxy pair run
+  // back to back on it, and the pair's PSF and constants are staged once for them.
+  const int it_lo = (int)((long long)blockIdx.x * n_items / gridDim.x);
+  const int it_hi = (int)((long long)(blockIdx.x + 1) * n_items / gridDim.x);
+  if (it_lo >= it_hi) return;
   if (tid == 0) {
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
   }
   __syncthreads();
-  if (tid == 0) adj_issue(A, s_in, bar, blockIdx.x);
+  if (tid == 0) adj_issue(A, s_in, bar, it_lo);
   unsigned phase = 0;
   const int lane = tid & 31, wig = tid >> 5;
   const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
   const int row0 = wig * 8;
   const int ncc = m.n_comp * kCC;
 
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  int staged = -1;  // galaxy pair whose PSF and constants are in shared memory
+  for (int item = it_lo; item < it_hi; ++item) {
     const int gp = item / A.n_tiles, tile = item - gp * A.n_tiles;
     const int g0 = 2 * gp, g1 = 2 * gp + 1;
     const bool has1 = g1 < A.G;
     const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
 
     __syncthreads();  // the previous item is done with s_psf, s_cc, s_red
-    for (int t = tid; t < 2 * ncc; t += blockDim.x) {
-      const int h = t / ncc, e = t - h * ncc;
-      const int g = g0 + h;
-      s_cc[t] = (g < A.G) ? A.cconst[(size_t)g * ncc + e] : 0.f;
-    }
-    for (int t = tid; t < K * K2; t += blockDim.x) {
-      const int a = t / K2, bb = t - a * K2;
-      const int b = bb - A.cpad;
-      float v0 = 0.f, v1 = 0.f;
-      if (b >= 0 && b < K) {
-        // RESID correlates with P, ADJ with P flipped in both axes (the adjoint)
-        const int src = (MODE == ADJ_RESID) ? a * K + b : (K - 1 - a) * K + (K - 1 - b);
-        v0 = A.psf[(size_t)g0 * K * K + src];
-        v1 = has1 ? A.psf[(size_t)g1 * K * K + src] : 0.f;
+    if (gp != staged) {
+      staged = gp;
+      for (int t = tid; t < 2 * ncc; t += blockDim.x) {
+        const int h = t / ncc, e = t - h * ncc;
+        const int g = g0 + h;
+        s_cc[t] = (g < A.G) ? A.cconst[(size_t)g * ncc + e] : 0.f;
       }
-      s_psf[t] = pack2(v0, v1);
+      for (int t = tid; t < K * K2; t += blockDim.x) {
+        const int a = t / K2, bb = t - a * K2;
+        const int b = bb - A.cpad;
+        float v0 = 0.f, v1 = 0.f;
+        if (b >= 0 && b < K) {
+          // RESID correlates with P, ADJ with P flipped in both axes (the adjoint)
+          const int src = (MODE == ADJ_RESID) ? a * K + b : (K - 1 - a) * K + (K - 1 - b);
+          v0 = A.psf[(size_t)g0 * K * K + src];
+          v1 = has1 ? A.psf[(size_t)g1 * K * K + src] : 0.f;
+        }
+        s_psf[t] = pack2(v0, v1);
+      }
     }
     const int a_lo = max(0, c - i0 - row0 - 7);
     const int a_hi = min(K, c - i0 + A.H - row0);
@@ -170,9 +201,16 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
     u64 acc[1][8];
     correlate_pairs<1>(acc, s_in, s_psf, 0, A.plane, A.rw, K, row, col0, a_lo, a_hi);
     __syncthreads();  // every warp is done reading the window
-    if (tid == 0 && item + (int)gridDim.x < n_items) adj_issue(A, s_in, bar, item + gridDim.x);
+    if (tid == 0 && item + 1 < it_hi) adj_issue(A, s_in, bar, item + 1);
 
     // ---- epilogue: this thread's 8 pixels, both galaxies, straight from registers ----
+    // Code size decides its speed: eval_component is a large inline body, and a fully
+    // unrolled epilogue (2 galaxies x 8 pixels of it) misses the instruction cache.  The
+    // galaxies of the pair therefore run as a loop over h that works on row 0 of each
+    // [2][.] array and swaps the rows after each galaxy, and the 8 pixels as a loop of
+    // kEpiPx-pixel chunks that works on entries 0..kEpiPx-1 and rotates the row by kEpiPx
+    // after each chunk; every index stays a compile-time constant (registers), and both
+    // the swaps and the full turn of rotations leave the arrays in their starting order.
     float red[2][NA];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
@@ -186,87 +224,92 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
     // accumulator of (component, k) is run-time data, and a compare-select over the
     // free parameters keeps red[] in registers; it is paid once per component and
     // galaxy: the thread first sums each derivative over its 8 pixels.
-    auto scatter = [&](const int (&acc_of)[8], int np, int h, const float (&sd)[8]) {
+    auto scatter = [&](const int (&acc_of)[8], int np, const float (&sd)[8]) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         if (k >= np) break;
         const int f = acc_of[k];
 #pragma unroll
         for (int ff = 0; ff < P; ++ff)
-          if (ff == f) red[h][1 + ff] += sd[k];
+          if (ff == f) red[0][1 + ff] += sd[k];
+      }
+    };
+    // sum over the 8 pixels of wt * dI_cm/dp_k for the components cm that are (not) convolved
+    auto deriv_sums = [&](float (&wt)[2][8], bool conv) {
+      for (int cm = 0; cm < m.n_comp; ++cm) {
+        if ((m.conv[cm] != 0) != conv) continue;
+        const int np = m.np[cm];
+        const float* cc = s_cc + cm * kCC;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          if (h == 0 || has1) {
+            float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int rb = 0; rb < 8; rb += kEpiPx) {
+#pragma unroll
+              for (int q = 0; q < kEpiPx; ++q) {
+                const int j = j0 + col0 + rb + q;
+                if (i < A.H && j < A.W) {
+                  float d[8];
+                  eval_component(m.kind[cm], cc + h * ncc, i, j, d);
+#pragma unroll
+                  for (int k = 0; k < 8; ++k)
+                    if (k < np) sd[k] = fmaf(wt[0][q], d[k], sd[k]);
+                }
+              }
+              rotate_left<kEpiPx>(wt[0]);
+            }
+            scatter(conv ? A.conv_acc[cm] : A.unconv_acc[cm], np, sd);
+          }
+          swap_rows(wt);
+          swap_rows(red);
+        }
       }
     };
     if (MODE == ADJ_RESID) {
       float wr[2][8];  // w r = (D - M) / sigma^2 per pixel; 0 outside the stamp or masked
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int g = g0 + h;
+#pragma unroll 1
+        for (int rb = 0; rb < 8; rb += kEpiPx) {
+#pragma unroll
+          for (int q = 0; q < kEpiPx; ++q) {
+            const int j = j0 + col0 + rb + q;
+            float uu = 0.f;
+            if ((h == 0 || has1) && i < A.H && j < A.W) {
+              float Mv = vv[0][q];
+              for (int cm = 0; cm < m.n_comp; ++cm) {
+                if (m.conv[cm]) continue;
+                float d[8];
+                Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
+              }
+              const size_t gpx = ((size_t)g * A.H + i) * A.W + j;
+              if (!(A.mask && A.mask[gpx])) {
+                const float isg = 1.f / A.sigma[gpx];
+                const float rr = (A.image[gpx] - Mv) * isg;
+                red[0][0] = fmaf(rr, rr, red[0][0]);
+                uu = rr * isg;
+              }
+            }
+            wr[0][q] = uu;
+          }
+          rotate_left<kEpiPx>(vv[0]);
+          rotate_left<kEpiPx>(wr[0]);
+        }
+        swap_rows(vv);
+        swap_rows(wr);
+        swap_rows(red);
+      }
 #pragma unroll
       for (int rx = 0; rx < 8; ++rx) {
         const int j = j0 + col0 + rx;
-        float uu[2] = {0.f, 0.f};
-        if (i < A.H && j < A.W) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (h == 1 && !has1) continue;
-            const int g = g0 + h;
-            float Mv = vv[h][rx];
-            for (int cm = 0; cm < m.n_comp; ++cm) {
-              if (m.conv[cm]) continue;
-              float d[8];
-              Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
-            }
-            const size_t gpx = ((size_t)g * A.H + i) * A.W + j;
-            if (A.mask && A.mask[gpx]) continue;
-            const float isg = 1.f / A.sigma[gpx];
-            const float rr = (A.image[gpx] - Mv) * isg;
-            red[h][0] = fmaf(rr, rr, red[h][0]);
-            uu[h] = rr * isg;
-          }
-        }
-        wr[0][rx] = uu[0];
-        wr[1][rx] = uu[1];
         if (i < A.H && j < A.Wp)
-          reinterpret_cast<float2*>(A.u_planes)[((size_t)gp * A.H + i) * A.Wp + j] = make_float2(uu[0], uu[1]);
+          reinterpret_cast<float2*>(A.u_planes)[((size_t)gp * A.H + i) * A.Wp + j] = make_float2(wr[0][rx], wr[1][rx]);
       }
-      for (int cm = 0; cm < m.n_comp; ++cm) {
-        if (m.conv[cm]) continue;
-        const int np = m.np[cm];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !has1) continue;
-          float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-          for (int rx = 0; rx < 8; ++rx) {
-            const int j = j0 + col0 + rx;
-            if (i >= A.H || j >= A.W) continue;
-            float d[8];
-            eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              if (k < np) sd[k] = fmaf(wr[h][rx], d[k], sd[k]);
-          }
-          scatter(A.unconv_acc[cm], np, h, sd);
-        }
-      }
+      deriv_sums(wr, false);
     } else {
-      for (int cm = 0; cm < m.n_comp; ++cm) {
-        if (!m.conv[cm]) continue;
-        const int np = m.np[cm];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !has1) continue;
-          float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-          for (int rx = 0; rx < 8; ++rx) {
-            const int j = j0 + col0 + rx;
-            if (i >= A.H || j >= A.W) continue;
-            float d[8];
-            eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              if (k < np) sd[k] = fmaf(vv[h][rx], d[k], sd[k]);
-          }
-          scatter(A.conv_acc[cm], np, h, sd);
-        }
-      }
+      deriv_sums(vv, true);
     }
     // ---- block reduction: warp sums (recursive halving), then across the 4 warps, FP64 per tile ----
     {
