@@ -367,6 +367,28 @@ def test_grad_adjoint_vs_oracle_finite_differences(gm):
         assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= bound).all(), gi
 
 
+def test_grad_adjoint_block_ranges_across_pairs(gm):
+    # 301 galaxies of 96x96 (K = 41): 151 lane pairs x 9 tiles = 1,359 tiles over a few
+    # hundred blocks, so a block's contiguous range starts and ends inside pairs and
+    # restages the PSF pair where it crosses into the next one; the last pair holds one
+    # galaxy.  Slots repeat 7 oracle-rendered sources (an odd count: every pair mixes two
+    # different galaxies); sampled slots against the oracle for their source.
+    import torch
+    S7, G = 7, 301
+    c = from_batch(synth.draw_bulge_bar_nucleus(seed=41, G=S7), at="init")
+    src = np.arange(G) % S7
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a[src])).cuda()
+    chi2, grad = gm.gm_grad_adjoint(c.spec, t(c.params), t(c.image), t(c.sigma), t(c.mask), t(c.psf))
+    chi2, grad = _np(chi2), _np(grad)
+    rchi2, rg, rA = _oracle_normal(c)
+    free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
+    for g in (0, 1, 2, 17, 18, 149, 150, 151, 298, 299, 300):
+        s = src[g]
+        assert abs(chi2[g] - rchi2[s]) <= 1e-5 * rchi2[s], g
+        d = np.sqrt(np.diag(rA[s]))
+        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 2e-4 * d * math.sqrt(rchi2[s])).all(), g
+
+
 def test_chi2_autograd_function_and_adam(gm):
     import torch
     b = synth.draw_small(seed=13, G=6)
