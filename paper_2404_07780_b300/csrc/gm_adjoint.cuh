@@ -33,9 +33,10 @@ namespace gm {
 enum AdjMode { ADJ_RESID = 0, ADJ_GRAD = 1 };
 
 // Pixels of a thread's row of 8 that one iteration of the epilogue loop evaluates.
-// Smaller is faster on the 15-parameter bulge+bar+nucleus pass (1, 2, 4, 8 pixels:
-// 7.34, 7.68, 8.22, 8.44 ms): the instruction footprint outweighs the lost overlap
-// of independent pixels, as the kernel has 12 warps per SM to interleave.
+// Smaller is faster on the 15-parameter bulge+bar+nucleus pass: 7.34 and 7.68 ms for
+// 1 and 2 pixels; with strided tiles, 7.84, 8.22 and 8.44 ms for 2, 4 and 8.  The
+// instruction footprint outweighs the lost overlap of independent pixels, as the
+// kernel has 12 warps per SM to interleave.
 constexpr int kEpiPx = 1;
 
 template <int N>
