@@ -49,6 +49,59 @@ __device__ __forceinline__ void swap_rows(float (&a)[2][N]) {
   }
 }
 
+// Image D and 1/sigma of 8 consecutive pixels of one stamp row starting at element
+// base, n_in of them inside the stamp (n_in may be below 1 or above 8): two float4
+// loads per array when the row holds all 8 and both addresses are 16-byte aligned,
+// one 8-byte mask load when that is aligned, else element by element within the row.
+// Bit k of excl is set for a pixel outside the stamp or masked (mask byte nonzero);
+// such a pixel gets D = 0 and 1/sigma = 0 and no sigma is divided for it.
+__device__ __forceinline__ void load_row8(const float* __restrict__ image, const float* __restrict__ sigma,
+                                          const uint8_t* __restrict__ mask, size_t base, int n_in,
+                                          float (&D)[8], float (&isg)[8], unsigned& excl) {
+  const float* ip = image + base;
+  const float* sp = sigma + base;
+  float S[8];
+  const bool full = n_in >= 8;
+  if (full && ((reinterpret_cast<uintptr_t>(ip) | reinterpret_cast<uintptr_t>(sp)) & 15) == 0) {
+    const float4 a0 = __ldg(reinterpret_cast<const float4*>(ip)), a1 = __ldg(reinterpret_cast<const float4*>(ip) + 1);
+    const float4 s0 = __ldg(reinterpret_cast<const float4*>(sp)), s1 = __ldg(reinterpret_cast<const float4*>(sp) + 1);
+    D[0] = a0.x; D[1] = a0.y; D[2] = a0.z; D[3] = a0.w; D[4] = a1.x; D[5] = a1.y; D[6] = a1.z; D[7] = a1.w;
+    S[0] = s0.x; S[1] = s0.y; S[2] = s0.z; S[3] = s0.w; S[4] = s1.x; S[5] = s1.y; S[6] = s1.z; S[7] = s1.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      D[k] = k < n_in ? __ldg(ip + k) : 0.f;
+      S[k] = k < n_in ? __ldg(sp + k) : 1.f;
+    }
+  }
+  unsigned ex = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (k >= n_in) ex |= 1u << k;
+  if (mask) {
+    const uint8_t* mp = mask + base;
+    if (full && (reinterpret_cast<uintptr_t>(mp) & 7) == 0) {
+      const uint2 mv = __ldg(reinterpret_cast<const uint2*>(mp));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if ((mv.x >> (8 * k)) & 0xffu) ex |= 1u << k;
+        if ((mv.y >> (8 * k)) & 0xffu) ex |= 1u << (k + 4);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < n_in && __ldg(mp + k)) ex |= 1u << k;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool off = (ex >> k) & 1u;
+    isg[k] = off ? 0.f : 1.f / S[k];
+    if (off) D[k] = 0.f;
+  }
+  excl = ex;
+}
+
 // a[k] <- a[(k + S) mod 8]
 template <int S>
 __device__ __forceinline__ void rotate_left(float (&a)[8]) {
@@ -275,31 +328,40 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
         const int g = g0 + h;
+        // D and 1/sigma of this galaxy's 8 pixels, loaded before the pixel loop
+        float Dv[8], Iv[8];
+        unsigned excl = 0xffu;  // bit k: pixel k is not used (masked, outside the stamp)
+        if ((h == 0 || has1) && i < A.H) {
+          load_row8(A.image, A.sigma, A.mask, ((size_t)g * A.H + i) * A.W + j0 + col0, A.W - (j0 + col0), Dv, Iv,
+                    excl);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) Dv[k] = Iv[k] = 0.f;
+        }
 #pragma unroll 1
         for (int rb = 0; rb < 8; rb += kEpiPx) {
 #pragma unroll
           for (int q = 0; q < kEpiPx; ++q) {
             const int j = j0 + col0 + rb + q;
             float uu = 0.f;
-            if ((h == 0 || has1) && i < A.H && j < A.W) {
+            if (!((excl >> q) & 1u)) {
               float Mv = vv[0][q];
               for (int cm = 0; cm < m.n_comp; ++cm) {
                 if (m.conv[cm]) continue;
                 float d[8];
                 Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
               }
-              const size_t gpx = ((size_t)g * A.H + i) * A.W + j;
-              if (!(A.mask && A.mask[gpx])) {
-                const float isg = 1.f / A.sigma[gpx];
-                const float rr = (A.image[gpx] - Mv) * isg;
-                red[0][0] = fmaf(rr, rr, red[0][0]);
-                uu = rr * isg;
-              }
+              const float rr = (Dv[q] - Mv) * Iv[q];
+              red[0][0] = fmaf(rr, rr, red[0][0]);
+              uu = rr * Iv[q];
             }
             wr[0][q] = uu;
           }
           rotate_left<kEpiPx>(vv[0]);
           rotate_left<kEpiPx>(wr[0]);
+          rotate_left<kEpiPx>(Dv);
+          rotate_left<kEpiPx>(Iv);
+          excl >>= kEpiPx;
         }
         swap_rows(vv);
         swap_rows(wr);
