@@ -124,6 +124,29 @@ def test_bad_arguments_return_codes(lib):
     assert lib.gm_model(ctypes.byref(d), ctypes.byref(b), None, None, None, None, 0, None) == 0
 
 
+def test_empty_batch_is_a_no_op_for_every_entry(lib):
+    # n_gal = 0: every compute entry point validates its arguments and returns success
+    # without a device call (this runs where no GPU is present), and every size query
+    # answers a small positive workspace
+    _, d, b = _desc_batch(G=0)
+    fake = ctypes.c_void_p(16)  # device pointers: never dereferenced on the host
+    b.psf = b.image = b.sigma = fake
+    R = ctypes.byref
+    opts = gm.FitOptions().to_c()
+    adam = gm.gm_adam_opts(10, 0.01, 0.9, 0.999, 1e-8)
+    ws = 1 << 20
+    assert lib.gm_model(R(d), R(b), fake, fake, None, None, 0, None) == 0
+    assert lib.gm_chi2_grad(R(d), R(b), fake, fake, fake, None, fake, ws, None) == 0
+    assert lib.gm_fit_batch(R(d), R(b), fake, R(opts), fake, fake, fake, fake, None, fake, ws, None) == 0
+    assert lib.gm_grad_adjoint(R(d), R(b), fake, fake, fake, fake, ws, None) == 0
+    assert lib.gm_fit_adam(R(d), R(b), fake, R(adam), fake, fake, ws, None) == 0
+    assert lib.gm_bootstrap_counts(R(d), R(b), 1, 0, fake, fake, ws, None) == 0
+    assert lib.gm_bootstrap(R(d), R(b), fake, 4, 1, fake, fake, fake, fake, ws, None) == 0
+    for name in ("gm_model_workspace_bytes", "gm_chi2_grad_workspace_bytes", "gm_fit_workspace_bytes",
+                 "gm_grad_adjoint_workspace_bytes", "gm_fit_adam_workspace_bytes", "gm_bootstrap_workspace_bytes"):
+        assert 0 < getattr(lib, name)(R(d), R(b)) <= 1 << 16, name
+
+
 def test_many_parameter_models_size_their_workspace(lib):
     # bulge+disk (12 free, 13 correlated channels) and bulge+bar+nucleus (15 free) run in
     # several channel-pair passes; the size queries accept them
