@@ -147,6 +147,39 @@ def test_empty_batch_is_a_no_op_for_every_entry(lib):
         assert 0 < getattr(lib, name)(R(d), R(b)) <= 1 << 16, name
 
 
+def test_adjoint_adam_bootstrap_reject_bad_arguments_on_the_host(lib):
+    # each refusal comes from host-side validation, with the documented code and message,
+    # before any device call (this runs where no GPU is present)
+    R = ctypes.byref
+    fake = ctypes.c_void_p(16)
+    spec, d, b = _desc_batch(K=14)
+    b.psf = b.image = b.sigma = fake
+    assert lib.gm_grad_adjoint(R(d), R(b), fake, fake, fake, fake, 1 << 20, None) == -1
+    assert b"must be odd" in lib.gm_last_error()
+    b.K = 15
+    need = lib.gm_grad_adjoint_workspace_bytes(R(d), R(b))
+    assert need > 0
+    assert lib.gm_grad_adjoint(R(d), R(b), fake, fake, fake, fake, need - 1, None) == -3
+    assert lib.gm_grad_adjoint(R(d), R(b), fake, fake, fake, None, need, None) == -3
+    for bad in ((0, 0.01, 0.9, 0.999, 1e-8), (10, 0.0, 0.9, 0.999, 1e-8), (10, 0.01, 1.0, 0.999, 1e-8),
+                (10, 0.01, 0.9, -0.1, 1e-8), (10, 0.01, 0.9, 0.999, 0.0)):
+        assert lib.gm_fit_adam(R(d), R(b), fake, R(gm.gm_adam_opts(*bad)), fake, fake, 1 << 30, None) == -1, bad
+        assert b"Adam options" in lib.gm_last_error()
+    assert lib.gm_fit_adam(R(d), R(b), fake, None, fake, fake, 1 << 30, None) == -1
+    adam = gm.gm_adam_opts(10, 0.01, 0.9, 0.999, 1e-8)
+    na = lib.gm_fit_adam_workspace_bytes(R(d), R(b))
+    assert lib.gm_fit_adam(R(d), R(b), fake, R(adam), fake, fake, na - 1, None) == -3
+    nb = lib.gm_bootstrap_workspace_bytes(R(d), R(b))
+    assert lib.gm_bootstrap(R(d), R(b), fake, 0, 1, fake, fake, fake, fake, nb, None) == -1
+    assert lib.gm_bootstrap(R(d), R(b), fake, 4, 1, fake, fake, fake, fake, nb - 1, None) == -3
+    assert lib.gm_bootstrap_counts(R(d), R(b), 1, 0, fake, fake, nb - 1, None) == -3
+    assert lib.gm_bootstrap_counts(R(d), R(b), 1, -1, fake, fake, nb, None) == -1
+    # equal stamps only: the size queries of the Adam fit and the bootstrap answer 0 for an uneven batch
+    b.geom = fake
+    assert lib.gm_fit_adam_workspace_bytes(R(d), R(b)) == 0
+    assert lib.gm_bootstrap_workspace_bytes(R(d), R(b)) == 0
+
+
 def test_many_parameter_models_size_their_workspace(lib):
     # bulge+disk (12 free, 13 correlated channels) and bulge+bar+nucleus (15 free) run in
     # several channel-pair passes; the size queries accept them
