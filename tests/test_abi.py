@@ -180,6 +180,33 @@ def test_adjoint_adam_bootstrap_reject_bad_arguments_on_the_host(lib):
     assert lib.gm_bootstrap_workspace_bytes(R(d), R(b)) == 0
 
 
+def test_cnn_entry_points_reject_bad_arguments_on_the_host(lib):
+    # the initialiser's layers: channel and feature counts off the multiple of 8, NULL
+    # pointers, short workspaces, odd input sides and bad optimiser steps are refused before
+    # any device call; an empty batch is a no-op
+    from paper_2404_07780_b300 import cnn
+    L = cnn.lib()
+    f = ctypes.c_void_p(256)  # never dereferenced
+    assert L.gm_cnn_conv_fwd(f, f, None, f, 2, 32, 32, 12, 16, 1, None) == -1
+    assert b"conv_fwd" in L.gm_cnn_last_error()
+    assert L.gm_cnn_conv_fwd(f, f, None, f, 2, 32, 32, 8, 12, 1, None) == -1
+    assert L.gm_cnn_conv_fwd(None, f, None, f, 2, 32, 32, 8, 16, 1, None) == -1
+    assert L.gm_cnn_conv_fwd(f, f, None, f, 0, 32, 32, 8, 16, 1, None) == 0
+    assert L.gm_cnn_conv_bwd_data(f, f, None, f, 2, 32, 32, 1, 16, None) == -1
+    ws = L.gm_cnn_conv_bwd_weight_workspace(2, 32, 32, 8, 16)
+    assert ws > 0
+    assert L.gm_cnn_conv_bwd_weight(f, f, f, None, 2, 32, 32, 8, 16, f, ws - 1, None) == -3
+    assert L.gm_cnn_dense_fwd(f, f, None, f, None, 4, 12, 16, 1, None) == -1
+    assert L.gm_cnn_dense_fwd(f, f, None, None, None, 4, 16, 16, 1, None) == -1  # no output
+    wd = L.gm_cnn_dense_bwd_weight_workspace(4, 16, 16)
+    assert wd > 0
+    assert L.gm_cnn_dense_bwd_weight(f, f, f, None, 4, 16, 16, f, wd - 1, None) == -3
+    assert L.gm_cnn_prep(f, 2, 33, 32, 1.0, f, None) == -1
+    assert L.gm_cnn_mse(f, f, 4, 8, 9, f, f, None) == -1
+    assert L.gm_cnn_adam(f, f, f, f, None, 10, 0.01, 0.9, 0.999, 1e-8, 0, None) == -1
+    assert L.gm_cnn_adam(f, f, f, f, None, -1, 0.01, 0.9, 0.999, 1e-8, 1, None) == -1
+
+
 def test_many_parameter_models_size_their_workspace(lib):
     # bulge+disk (12 free, 13 correlated channels) and bulge+bar+nucleus (15 free) run in
     # several channel-pair passes; the size queries accept them
