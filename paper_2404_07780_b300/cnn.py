@@ -258,6 +258,26 @@ class Net:
         self.step_count = 0
         self._ws = None
 
+    def save(self, path) -> None:
+        """Checkpoint: FP32 master weights, Adam moments and step count in one .npz file
+        (the BF16 copy is rebuilt on load; the target codec depends only on the stamp side)."""
+        np.savez(path, p=self.p.cpu().numpy(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(),
+                 step=np.int64(self.step_count), offsets=self.offsets)
+
+    @classmethod
+    def load(cls, path, device="cuda") -> "Net":
+        """A network restored from save(): training resumes where it stopped."""
+        import torch
+        z = np.load(path)
+        net = cls(device=device)
+        if not np.array_equal(z["offsets"], net.offsets):
+            raise ValueError(f"{path}: the checkpoint's layer layout differs from this network's")
+        for name in ("p", "m", "v"):
+            getattr(net, name).copy_(torch.from_numpy(z[name]))
+        net.p_bf.copy_(net.p.to(torch.bfloat16))
+        net.step_count = int(z["step"])
+        return net
+
     def _view(self, buf, j):
         return buf[int(self.offsets[j]):int(self.offsets[j + 1])].view(self.shapes[j])
 
