@@ -367,6 +367,28 @@ def test_grad_adjoint_vs_oracle_finite_differences(gm):
         assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= bound).all(), gi
 
 
+@pytest.mark.parametrize("H,W,K", [(37, 45, 9), (7, 9, 15), (64, 33, 1)])
+def test_normal_equations_and_adjoint_at_ragged_sizes(gm, H, W, K):
+    # stamps that end inside a tile, a 1x1 PSF and a PSF larger than the stamp, with 10% of
+    # the pixels masked: chi^2 and d chi^2/dp of both passes, and J^T W J of the normal
+    # equations, against the oracle (5 galaxies: the last lane pair of the adjoint holds one)
+    c = from_batch(synth.draw_small(seed=H * 7 + W + K, G=5, H=H, W=W, K=K), at="init")
+    c.mask = (np.random.default_rng(K + 1).random((c.G, H, W)) < 0.1).astype(np.uint8)
+    t = c.torch()
+    chi2, grad, jtj = map(_np, gm.gm_chi2_grad(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"],
+                                               want_grad=True, want_jtj=True))
+    achi2, agrad = map(_np, gm.gm_grad_adjoint(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"]))
+    rchi2, rg, rA = _oracle_normal(c)
+    free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
+    for g in range(c.G):
+        d = np.sqrt(np.diag(rA[g]))
+        bound = 2e-4 * d * math.sqrt(rchi2[g])
+        for name, x2, gr in (("normal", chi2, grad), ("adjoint", achi2, agrad)):
+            assert abs(x2[g] - rchi2[g]) <= 1e-5 * rchi2[g], (name, g)
+            assert (np.abs(gr[g, free] + 2.0 * rg[g]) <= bound).all(), (name, g)
+        assert (np.abs(jtj[g][np.ix_(free, free)] - rA[g]) <= 1e-4 * np.outer(d, d)).all(), g
+
+
 def test_grad_adjoint_block_ranges_across_pairs(gm):
     # 301 galaxies of 96x96 (K = 41): 151 lane pairs x 9 tiles = 1,359 tiles over a few
     # hundred blocks, so a block's contiguous range starts and ends inside pairs and
