@@ -232,7 +232,10 @@ int gm_chi2_grad(const gm_model_desc *desc, const gm_batch *batch, const double 
  *   chi2    [n_gal] FP64
  *   grad    NULL or [n_gal][n_slots] FP64, physical units, 0 for fixed slots
  *   workspace  gm_grad_adjoint_workspace_bytes(desc, batch) bytes
- * Asynchronous on `stream` like gm_chi2_grad.
+ * Asynchronous on `stream` like gm_chi2_grad.  Equal stamps only: a batch with
+ * geom returns GM_E_UNSUPPORTED (and the size query 0).  GM_E_INVAL for an even
+ * or out-of-range PSF side, GM_E_NOMEM for a short or NULL workspace; an empty
+ * batch (n_gal = 0) returns GM_OK without device work.
  */
 size_t gm_grad_adjoint_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
 int gm_grad_adjoint(const gm_model_desc *desc, const gm_batch *batch, const double *params, double *chi2,
