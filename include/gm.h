@@ -335,6 +335,8 @@ int gm_fit_batch(const gm_model_desc *desc, const gm_batch *batch, double *param
  * max(|p at the start|, 1), so lr is a relative step for every slot.
  * Synchronises the stream once at the end.  The paper gives no learning rate
  * or moments for its optimiser: they are the caller's choice here.
+ * GM_E_INVAL for NULL opts or n_iter < 1, lr <= 0, beta1 or beta2 outside
+ * [0, 1), eps <= 0; GM_E_NOMEM for a short workspace.
  */
 typedef struct {
   int32_t n_iter;   /* gradient evaluations followed by a step */
@@ -365,7 +367,8 @@ int gm_fit_adam(const gm_model_desc *desc, const gm_batch *batch, double *params
  * ([n_gal][H][W] uint32) without fitting.  Equal stamps only; opts as
  * gm_fit_batch (NULL = defaults).  params_best, sigma_boot [n_gal][n_slots]
  * FP64, n_ok [n_gal] int32 (may be NULL).  Synchronises the stream (inside
- * each refit).
+ * each refit).  GM_E_INVAL for n_boot < 1, replicate < 0 or a NULL
+ * params_best, sigma_boot or counts; GM_E_NOMEM for a short workspace.
  */
 size_t gm_bootstrap_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
 int gm_bootstrap_counts(const gm_model_desc *desc, const gm_batch *batch, uint64_t seed, int32_t replicate,
