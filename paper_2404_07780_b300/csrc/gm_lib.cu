@@ -1175,7 +1175,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
       fused_ms += b;
       step_ms += c;
     }
-    if (kerr) return fail(GM_E_CUDA, "fused kernel: a tile load did not complete within its wait limit");
+    if (kerr) return fail(GM_E_TIMEOUT, "fused kernel: a tile load did not complete within its wait limit");
     if (remaining == 0) break;
   }
   k_lm_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, G, params_inout, chi2_out, dof_out, iters_out,
@@ -1451,7 +1451,7 @@ int gm_fit_adam(const gm_model_desc* desc, const gm_batch* batch, double* params
   int kerr = 0;
   GM_CUDA(cudaMemcpyAsync(&kerr, ap.Ar.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GM_CUDA(cudaStreamSynchronize(st));
-  if (kerr) return fail(GM_E_CUDA, "adjoint kernel: a tile load did not complete within its wait limit");
+  if (kerr) return fail(GM_E_TIMEOUT, "adjoint kernel: a tile load did not complete within its wait limit");
   (void)NS;
   return GM_OK;
 }
