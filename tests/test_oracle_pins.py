@@ -182,6 +182,57 @@ def test_king_alpha2_is_king1962():
     assert oracle.component_value("king", par, rt + 0.1, 0.0) == 0.0
 
 
+@pytest.mark.parametrize("al", [1.5, 2.5, 3.0])
+def test_king_general_alpha_centre_edge_and_monotone(al):
+    # Eq. BE_S with the bracket read as [A(r) - A(r_t)]: I(0) = I0, I(r_t) = 0, and I falls
+    # monotonically in between, for every power alpha (not only King's alpha = 2)
+    I0, rc, rt = 7.0, 1.3, 9.0
+    par = [0.0, 0.0, 1.0, 0.0, I0, rc, rt, al]
+    # (the radius floor of 1e-4 px moves I(0) by ~1e-8 relative)
+    assert oracle.component_value("king", par, 0.0, 0.0) == pytest.approx(I0, rel=1e-7)
+    assert oracle.component_value("king", par, rt, 0.0) == 0.0
+    r = np.linspace(0.0, rt, 400)
+    v = np.array([oracle.component_value("king", par, x, 0.0) for x in r])
+    assert (np.diff(v) < 0).all()
+
+
+@pytest.mark.parametrize("al", [1.5, 2.5, 3.0])
+def test_king_general_alpha_untruncated_limit(al):
+    # r_t -> infinity: A(r_t) -> 0 and [A(r)]^alpha = 1 / (1 + (r/r_c)^2) whatever alpha
+    # (King's untruncated core profile), so a misplaced power of alpha shows here
+    I0, rc, rt = 3.0, 2.0, 2.0e15
+    par = [0.0, 0.0, 1.0, 0.0, I0, rc, rt, al]
+    for x in (0.5, 1.0, 3.0, 10.0, 40.0):
+        v = oracle.component_value("king", par, x, 0.0)
+        assert v == pytest.approx(I0 / (1.0 + (x / rc) ** 2), rel=1e-8)
+
+
+@pytest.mark.parametrize("al", [1.5, 2.5, 3.0])
+def test_king_general_alpha_truncation_edge_power(al):
+    # near r_t, A(r) - A(r_t) is linear in r_t - r, so I ~ (r_t - r)^alpha: the local
+    # log-slope of I against (r_t - r) is alpha
+    I0, rc, rt = 5.0, 1.0, 6.0
+    par = [0.0, 0.0, 1.0, 0.0, I0, rc, rt, al]
+    e1, e2 = 1e-4, 2e-4
+    v1 = oracle.component_value("king", par, rt - e1, 0.0)
+    v2 = oracle.component_value("king", par, rt - e2, 0.0)
+    assert math.log(v2 / v1) / math.log(e2 / e1) == pytest.approx(al, rel=1e-4)
+
+
+@pytest.mark.parametrize("al", [1.5, 2.5, 3.0])
+def test_king_general_alpha_against_mpmath(al):
+    # an independent restatement of Eq. BE_S in 50-digit arithmetic, written as the ratio
+    # ((A(r) - A(r_t)) / (1 - A(r_t)))^alpha with A(x) = (1 + (x/r_c)^2)^(-1/alpha)
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    I0, rc, rt = 4.0, 1.7, 12.0
+    par = [0.0, 0.0, 1.0, 0.0, I0, rc, rt, al]
+    A = lambda x: (1 + (mpmath.mpf(x) / rc) ** 2) ** (-1 / mpmath.mpf(al))
+    for x in (0.3, 1.0, 2.5, 6.0, 11.0):
+        ref = I0 * ((A(x) - A(rt)) / (1 - A(rt))) ** al
+        assert oracle.component_value("king", par, x, 0.0) == pytest.approx(float(ref), rel=1e-12)
+
+
 def test_sersic_reduces_to_gaussian_and_exponential():
     # Sec. 4.1: n = 1/2 is a Gaussian (FWHM = 2 Re, I0 = 2 Ie); n = 1 an exponential
     # disk (rs = Re / nu_1, I0 = Ie e^nu_1)
@@ -435,6 +486,31 @@ def test_lm_reduced_chi2_near_one_at_truth():
     k = b.H * b.W - b.spec.n_free
     # chi^2 at the truth is chi^2_k distributed: mean k, sd sqrt(2k)
     assert abs(c2.mean() / k - 1) < 4 * math.sqrt(2.0 / k) / math.sqrt(b.G)
+
+
+def test_lm_pulls_have_unit_width():
+    # Sec. 5.2: sigma_p from (J^T W J)^-1 is the standard error of the fitted parameter.  On
+    # many noise draws of one bright, well-resolved galaxy (the linear regime), the pulls
+    # (p_fit - p_true) / sigma_p of every free parameter have mean 0 and unit width; a wrong
+    # factor in the covariance (a missing 2, sigma instead of sigma^2, a log slot not mapped
+    # back) moves the width far outside the band.
+    H = W = 24
+    K = 7
+    N = 600
+    spec = synth.single_sersic_sky(H, W)
+    truth = np.array([12.3, 11.8, 0.6, 0.7, 40.0, 3.5, 1.6, 2.0])
+    psf = np.stack([_gauss_psf(K, 1.8)] * N)
+    P = np.tile(truth, (N, 1))
+    Mt = oracle.model_images(spec, P, psf, H, W)
+    z = np.random.default_rng(2024).standard_normal((N, H, W))
+    D, S = synth.noisy_image(Mt, z)
+    res = oracle.fit(spec, P, psf, D, S, None, oracle.FitOptions(tol=1e-10, max_iter=100))
+    assert (res["status"] == 1).all()
+    pull = (res["params"] - truth) / res["sigma_p"]
+    tol_sd = 0.1   # the sample sd of 600 unit normals is 1 +- 0.03
+    for s in range(spec.n_slots):
+        assert abs(pull[:, s].mean()) < 0.15, (spec.names[s], pull[:, s].mean())
+        assert abs(pull[:, s].std() - 1.0) < tol_sd, (spec.names[s], pull[:, s].std())
 
 
 def test_status_codes():
