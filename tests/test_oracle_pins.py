@@ -498,7 +498,7 @@ def test_lm_pulls_have_unit_width():
     K = 7
     N = 600
     spec = synth.single_sersic_sky(H, W)
-    truth = np.array([12.3, 11.8, 0.6, 0.7, 40.0, 3.5, 1.6, 2.0])
+    truth = np.array([12.3, 11.8, 0.6, 0.7, 80.0, 3.5, 1.6, 2.0])
     psf = np.stack([_gauss_psf(K, 1.8)] * N)
     P = np.tile(truth, (N, 1))
     Mt = oracle.model_images(spec, P, psf, H, W)
