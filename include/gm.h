@@ -261,6 +261,9 @@ int gm_grad_adjoint(const gm_model_desc *desc, const gm_batch *batch, const doub
  * reserved on every GPU that loads the library and held until the process
  * exits.  A request whose gm_chi2_grad_workspace_bytes() exceeds it returns
  * GM_E_NOMEM with a message (use gm_chi2_grad with your own workspace then).
+ * Arguments are checked as by gm_chi2_grad, with the same messages (a bad
+ * geometry of an uneven batch names the galaxy and the reason); an empty batch
+ * (n_gal = 0) returns GM_OK without touching the device.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  Every
  * call shares the one array: calls that overlap on the GPU (two streams, or

@@ -1723,8 +1723,12 @@ extern "C" int gm_chi2_grad_noalloc(const gm_model_desc* desc, const gm_batch* b
   int rc = check_batch(batch, true);
   if (rc) return rc;
   if ((rc = check_desc(desc))) return rc;
-  const size_t need = gm_chi2_grad_workspace_bytes(desc, batch);
-  if (need == 0) return fail(GM_E_INVAL, "gm_chi2_grad_noalloc: %s", g_err);
+  // the geometry is planned here rather than through the size query, so that a
+  // refusal keeps plan_geom's own reason in the error message
+  GeomPlan gp;
+  if ((rc = plan_geom(batch, pairs_for(desc, MODE_NORMAL), false, &gp))) return rc;
+  if (batch->n_gal == 0) return GM_OK;  // no device call, as for every other entry point
+  const size_t need = ws_core(desc, gp, n_acc(count_free(desc))).total;
   if (need > (size_t)GM_NOALLOC_SCRATCH_BYTES)
     return fail(GM_E_NOMEM,
                 "gm_chi2_grad_noalloc: this batch needs %zu bytes of scratch but the built-in array holds %u; "

@@ -152,6 +152,8 @@ def load() -> ctypes.CDLL:
         lib.gm_chi2_grad.argtypes = [P, P, P, P, P, P, P, S, P]
         lib.gm_fit_batch.restype = ctypes.c_int
         lib.gm_fit_batch.argtypes = [P, P, P, P, P, P, P, P, P, P, S, P]
+        lib.gm_chi2_grad_noalloc.restype = ctypes.c_int
+        lib.gm_chi2_grad_noalloc.argtypes = [P, P, P, P, P, P, P]
         lib.gm_grad_adjoint_workspace_bytes.restype = S
         lib.gm_grad_adjoint_workspace_bytes.argtypes = [P, P]
         lib.gm_grad_adjoint.restype = ctypes.c_int
@@ -331,6 +333,28 @@ def gm_chi2_grad(spec_or_desc, params, image, sigma, mask, psf, want_grad: bool 
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
     _check(lib.gm_chi2_grad(ctypes.byref(d), ctypes.byref(b), _ptr(params), _ptr(chi2), _ptr(grad), _ptr(jtj),
                             _ptr(ws), nbytes, _stream()), "gm_chi2_grad")
+    return chi2, grad, jtj
+
+
+def gm_chi2_grad_noalloc(spec_or_desc, params, image, sigma, mask, psf, want_grad: bool = True,
+                         want_jtj: bool = False, geom=None):
+    """gm_chi2_grad without a workspace: the library's fixed scratch array serves the call.
+
+    For callers that may not allocate device memory when they evaluate chi^2 (the outputs
+    here are still allocated by torch; a caller with that constraint passes its own through
+    the C ABI).  Calls that overlap on the GPU share the array and race."""
+    import torch
+    lib = load()
+    d = spec_or_desc if isinstance(spec_or_desc, gm_model_desc) else desc_from_spec(spec_or_desc)
+    b, keep = make_batch(image, sigma, mask, psf, geom)
+    params = _cuda_tensor(params, torch.float64, "params")
+    G, S = b.n_gal, d.n_slots
+    dev = keep[0].device
+    chi2 = torch.empty(G, dtype=torch.float64, device=dev)
+    grad = torch.empty((G, S), dtype=torch.float64, device=dev) if want_grad else None
+    jtj = torch.empty((G, S, S), dtype=torch.float64, device=dev) if want_jtj else None
+    _check(lib.gm_chi2_grad_noalloc(ctypes.byref(d), ctypes.byref(b), _ptr(params), _ptr(chi2), _ptr(grad),
+                                    _ptr(jtj), _stream()), "gm_chi2_grad_noalloc")
     return chi2, grad, jtj
 
 

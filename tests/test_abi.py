@@ -137,6 +137,7 @@ def test_empty_batch_is_a_no_op_for_every_entry(lib):
     ws = 1 << 20
     assert lib.gm_model(R(d), R(b), fake, fake, None, None, 0, None) == 0
     assert lib.gm_chi2_grad(R(d), R(b), fake, fake, fake, None, fake, ws, None) == 0
+    assert lib.gm_chi2_grad_noalloc(R(d), R(b), fake, fake, fake, None, None) == 0
     assert lib.gm_fit_batch(R(d), R(b), fake, R(opts), fake, fake, fake, fake, None, fake, ws, None) == 0
     assert lib.gm_grad_adjoint(R(d), R(b), fake, fake, fake, fake, ws, None) == 0
     assert lib.gm_fit_adam(R(d), R(b), fake, R(adam), fake, fake, ws, None) == 0
@@ -241,6 +242,14 @@ def test_uneven_geometry_sizes_and_rejections(lib):
         b, keep = batch(bad)
         assert lib.gm_fit_workspace_bytes(ctypes.byref(d), ctypes.byref(b)) == 0
         assert "uneven batch" in lib.gm_last_error().decode()
+    # the entry point without a workspace refuses a bad geometry with the planner's own reason
+    b, keep = batch([(40, 64, 25), (64, 64, 14)])
+    fake = ctypes.c_void_p(16)
+    b.image = b.sigma = b.psf = fake
+    rc = lib.gm_chi2_grad_noalloc(ctypes.byref(d), ctypes.byref(b), fake, fake, None, None, None)
+    msg = lib.gm_last_error().decode()
+    assert rc == -1 and "uneven batch" in msg and "must be odd" in msg, msg
+    assert msg.count("gm_chi2_grad_noalloc") <= 1, msg
     # the adjoint gradient takes equal stamps only: refused before any device work
     b, keep = batch([(40, 64, 25)])
     fake = ctypes.c_void_p(16)
