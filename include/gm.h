@@ -181,6 +181,7 @@ typedef struct {
   double lambda_down;  /* lambda *= lambda_down on an accepted step ... */
   double lambda_min;   /* ... but not below lambda_min */
   double lambda_max;   /* STALLED / SINGULAR beyond this */
+  int32_t polish;      /* 1: a CONVERGED fit takes one final Gauss-Newton step (gm_fit_batch); 0: none */
 } gm_fit_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -288,7 +289,7 @@ int gm_chi2_grad_noalloc(const gm_model_desc *desc, const gm_batch *batch, const
  *                r_c, r_t, fwhm) times q, which leaves the image unchanged,
  *                when those slots are not shared with components of another q
  *   opts         host; NULL = defaults (tol 1e-6, xtol 1e-10, gtol 1e-10, max_iter 100,
- *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10)
+ *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10, polish 1)
  *   chi2_out     [n_gal] FP64 chi^2 at the best point
  *   dof_out      [n_gal] int32: used pixels - free parameters (Sec. 5.1)
  *   iters_out    [n_gal] int32: model+Jacobian evaluations spent
@@ -301,6 +302,16 @@ int gm_chi2_grad_noalloc(const gm_model_desc *desc, const gm_batch *batch, const
  * running, then one LM step per galaxy: solve (A + lambda diag A) delta = g
  * by FP64 Cholesky (A = J^T W J, g = J^T W r in internal coordinates: ln p
  * for log slots), trial = clamp(p + delta), accept if chi^2 drops.
+ * Final Gauss-Newton step (opts->polish = 1): a fit that reaches CONVERGED
+ * with evaluations to spare takes one undamped step delta = A^-1 g from its
+ * best point (diag A floored at 1e-12 max diag A), evaluated in one more
+ * iteration; its point becomes the result unless its chi^2 is non-finite or
+ * above the best by more than 1e-6 relative.  The acceptance test above
+ * compares chi^2 values accumulated from FP32 pixels, whose rounding (~1e-8
+ * relative) exceeds what the last steps towards the minimum gain (~1e-10),
+ * so that test alone can stop a fit short of the minimum; the final step is
+ * taken from the gradient, whose FP32 error moves the minimum by ~1e-3 of the
+ * parameters' 1e-4 relative tolerance.
  * Synchronises `stream` every few iterations to poll how many galaxies are
  * still running; returns when none is or all have spent max_iter.
  */

@@ -89,6 +89,7 @@ class _Opts(ctypes.Structure):
         ("lambda_down", ctypes.c_double),
         ("lambda_min", ctypes.c_double),
         ("lambda_max", ctypes.c_double),
+        ("polish", ctypes.c_int),
     ]
 
 
@@ -146,6 +147,7 @@ class FitOptions:
     lambda_down: float = 0.1
     lambda_min: float = 1e-7
     lambda_max: float = 1e10
+    polish: int = 1
 
 
 def _desc(spec) -> _Desc:
@@ -299,7 +301,7 @@ def fit(spec, params0, psf, image, sigma, mask=None, opts: FitOptions | None = N
     sigma_p = np.zeros_like(params)
     d = _desc(spec)
     o = _Opts(opts.tol, opts.xtol, opts.gtol, opts.max_iter, opts.lambda0, opts.lambda_up, opts.lambda_down,
-              opts.lambda_min, opts.lambda_max)
+              opts.lambda_min, opts.lambda_max, opts.polish)
     _load().or_fit_batch(ctypes.byref(d), ctypes.byref(o), G, H, W, K, _ptr(params), _ptr(psf),
                          _ptr(image), _ptr(sigma), _ptr(mask), _ptr(chi2_out), _ptr(dof),
                          _ptr(iters), _ptr(status), _ptr(sigma_p))

@@ -97,6 +97,7 @@ typedef struct {
   double gtol;       /* Gauss-Newton decrement (relative to chi^2) that ends the fit */
   int max_iter;      /* model+Jacobian evaluations allowed */
   double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
+  int polish;        /* 1: one final Gauss-Newton step after CONVERGED (step 7 of or_fit_one) */
 } or_opts;
 
 int or_n_params(int kind) {
@@ -552,14 +553,24 @@ static double or_gn_decrement(const double *A, const double *g, int nf) {
  *      multiplies lambda by lambda_up and retries (SINGULAR past lambda_max).
  *   3. Trial p' = clamp(from_u(u + delta)); evaluate it (one iteration).
  *   4. The step is "small" when every internal step satisfies
- *      |u'_s - u_s| <= xtol (|u_s| + xtol).
- *      chi^2' < chi^2: accept, lambda = max(lambda*lambda_down, lambda_min);
- *      CONVERGED if (chi^2 - chi^2')/chi^2 < tol or the step was small.
+ *      |u'_s - u_s| <= xtol (|u_s| + xtol).  Its predicted decrease is
+ *      pred = 2 g^T delta - delta^T A delta (the quadratic model of chi^2),
+ *      taken as infinite when the clamp moved p'; the step is "resolved" when
+ *      pred >= 1e-7 chi^2.
+ *      chi^2' < chi^2, or an unresolved step with chi^2' <= chi^2 (1 + 1e-7):
+ *      accept, lambda = max(lambda*lambda_down, lambda_min); CONVERGED if the
+ *      step's decrease -- (chi^2 - chi^2')/chi^2 when resolved, pred/chi^2 when
+ *      not -- is below tol, or the step was small.
  *      Otherwise reject: CONVERGED at the kept point if the step was small,
  *      else lambda *= lambda_up and STALLED past lambda_max.
  *   5. At the start and after every accepted step: CONVERGED when the
  *      Gauss-Newton decrement g^T A^-1 g <= gtol chi^2 (no step can gain more).
  *   6. MAX_ITER once max_iter evaluations have been spent.
+ *   7. With polish, a fit that ended CONVERGED with evaluations to spare takes
+ *      one undamped Gauss-Newton step delta = A^-1 g from its best point (diag
+ *      A floored at 1e-12 max diag A), p' = clamp(from_u(u + delta)), and
+ *      evaluates it (one iteration); p' replaces the best point unless its
+ *      chi^2 is non-finite or above the best by more than 1e-6 relative.
  * At exit an axis ratio above 1 is rewritten as its reciprocal (or_canonical_q).
  * The covariance of Sec. 5.2 is taken from A at the best point; for a log
  * slot sigma_p = p sigma_u.  Position angles are wrapped to [0, pi) at exit.
@@ -627,6 +638,14 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
       int s = fidx[a];
       pt[s] = or_from_u(d, s, or_to_u(d, s, p[s]) + delta[a]);
     }
+    double pred = 0.0;
+    for (int a = 0; a < nf; ++a) {
+      double ad = 0.0;
+      for (int b = 0; b < nf; ++b) ad += A[a * nf + b] * delta[b];
+      pred += delta[a] * (2.0 * g[a] - ad);
+    }
+    for (int s = 0; s < d->n_slots; ++s)
+      if (pt[s] < d->lo[s] || pt[s] > d->hi[s]) pred = INFINITY;
     or_clamp(d, pt);
     double chi2t = or_normal_eq(d, pt, H, W, psf, K, image, sigma, mask, nf, At, gt, J, model, work);
     ++it;
@@ -636,8 +655,9 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
       double u0 = or_to_u(d, s, p[s]), u1 = or_to_u(d, s, pt[s]);
       if (fabs(u1 - u0) > o->xtol * (fabs(u0) + o->xtol)) small = 0;
     }
-    if (isfinite(chi2t) && chi2t < chi2) {
-      double act = (chi2 - chi2t) / chi2;
+    int resolved = pred >= 1e-7 * chi2;
+    if (isfinite(chi2t) && (chi2t < chi2 || (!resolved && chi2t <= chi2 * (1.0 + 1e-7)))) {
+      double act = resolved ? (chi2 - chi2t) / chi2 : fmax(pred, 0.0) / chi2;
       memcpy(p, pt, sizeof(double) * d->n_slots);
       memcpy(A, At, sizeof(double) * nf * nf);
       memcpy(g, gt, sizeof(double) * nf);
@@ -653,6 +673,30 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
     } else {
       lambda *= o->lambda_up;
       if (lambda > o->lambda_max) status = OR_STALLED;
+    }
+  }
+
+  if (status == OR_CONVERGED && o->polish && it < o->max_iter && chi2 > 0.0) {
+    double dmax = 0.0;
+    for (int a = 0; a < nf; ++a) dmax = fmax(dmax, A[a * nf + a]);
+    for (int a = 0; a < nf * nf; ++a) M[a] = A[a];
+    for (int a = 0; a < nf; ++a) M[a * nf + a] += 1e-12 * dmax;
+    if (or_cholesky(M, nf) == 0) {
+      or_chol_solve(M, nf, g, delta);
+      memcpy(pt, p, sizeof(double) * d->n_slots);
+      for (int a = 0; a < nf; ++a) {
+        int s = fidx[a];
+        pt[s] = or_from_u(d, s, or_to_u(d, s, p[s]) + delta[a]);
+      }
+      or_clamp(d, pt);
+      double chi2t = or_normal_eq(d, pt, H, W, psf, K, image, sigma, mask, nf, At, gt, J, model, work);
+      ++it;
+      if (isfinite(chi2t) && chi2t <= chi2 * (1.0 + 1e-6)) {
+        memcpy(p, pt, sizeof(double) * d->n_slots);
+        memcpy(A, At, sizeof(double) * nf * nf);
+        memcpy(g, gt, sizeof(double) * nf);
+        chi2 = chi2t;
+      }
     }
   }
 

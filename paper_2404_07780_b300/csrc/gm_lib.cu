@@ -641,8 +641,8 @@ WsCore ws_core(const gm_model_desc* d, const GeomPlan& gp, int nacc) {
 
 struct WsFit {
   WsCore c;
-  size_t p_b, p_t, A_b, g_b, chi2_b, lam, it, status, nused, bad, list0, list1, counts, items0, items1, icounts,
-      evals, total;
+  size_t p_b, p_t, A_b, g_b, chi2_b, lam, pred, it, status, nused, bad, list0, list1, counts, items0, items1,
+      icounts, evals, total;
 };
 
 WsFit ws_fit(const gm_model_desc* d, const GeomPlan& gp, int P) {
@@ -661,6 +661,7 @@ WsFit ws_fit(const gm_model_desc* d, const GeomPlan& gp, int P) {
   w.g_b = take(G * (size_t)(P + 1) * 8);
   w.chi2_b = take(G * 8);
   w.lam = take(G * 8);
+  w.pred = take(G * 8);
   w.it = take(G * 4);
   w.status = take(G * 4);
   w.nused = take(G * 4);
@@ -800,6 +801,7 @@ LMOpts lm_opts(const gm_fit_opts* o) {
     L.lambda_down = o->lambda_down;
     L.lambda_min = o->lambda_min;
     L.lambda_max = o->lambda_max;
+    L.polish = o->polish;
   } else {
     L.tol = 1e-6;
     L.xtol = 1e-10;
@@ -810,6 +812,7 @@ LMOpts lm_opts(const gm_fit_opts* o) {
     L.lambda_down = 0.1;
     L.lambda_min = 1e-7;
     L.lambda_max = 1e10;
+    L.polish = 1;
   }
   return L;
 }
@@ -1052,6 +1055,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
     return fail(GM_E_INVAL, "an output pointer is NULL");
   const LMOpts O = lm_opts(opts);
   if (O.max_iter < 1) return fail(GM_E_INVAL, "max_iter=%d < 1", O.max_iter);
+  if (O.polish != 0 && O.polish != 1) return fail(GM_E_INVAL, "polish=%d must be 0 or 1", O.polish);
   if (!(O.lambda_up > 1.0) || !(O.lambda_down > 0.0) || !(O.lambda_down < 1.0) || !(O.lambda0 > 0.0))
     return fail(GM_E_INVAL, "lambda controls must satisfy lambda0 > 0, up > 1, 0 < down < 1");
   const WsFit w = ws_fit(desc, gp, pl.dd.P);
@@ -1077,6 +1081,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   S.g_b = (double*)(ws + w.g_b);
   S.chi2_b = (double*)(ws + w.chi2_b);
   S.lam = (double*)(ws + w.lam);
+  S.pred = (double*)(ws + w.pred);
   S.it = (int*)(ws + w.it);
   S.status = (int*)(ws + w.status);
   S.nused = (int*)(ws + w.nused);

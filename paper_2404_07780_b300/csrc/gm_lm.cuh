@@ -12,6 +12,16 @@ namespace gm {
 
 constexpr int ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAX_ITER = 2, ST_STALLED = 3, ST_SINGULAR = 4,
               ST_NONFINITE = 5, ST_BAD_INPUT = 6, ST_NO_DOF = 7;
+// Internal: CONVERGED, with the final Gauss-Newton step queued for evaluation
+// (never an output: the next pass evaluates it and the step resolves it).
+constexpr int ST_POLISH = 16;
+// The final step's point is kept unless its chi^2 exceeds the best by more than
+// this (relative): far above the FP32 rounding of chi^2, far below any real loss.
+constexpr double kPolishSlack = 1e-6;
+// chi^2 changes below this fraction of chi^2 are not resolved by the tile sums of
+// FP32 pixel terms (their rounding is ~1e-8 relative): a step whose predicted
+// decrease is smaller is judged by its prediction, not by the measured change.
+constexpr double kChi2Res = 1e-7;
 
 constexpr int kMaxAcc = 1 + kMaxFree + kMaxFree * (kMaxFree + 1) / 2;
 
@@ -46,6 +56,7 @@ struct LMOpts {
   double tol, xtol, gtol;
   int max_iter;
   double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
+  int polish;  // one final Gauss-Newton step after CONVERGED
 };
 
 // Per-galaxy LM state, struct of arrays in the caller's workspace.
@@ -56,6 +67,7 @@ struct LMState {
   double* g_b;     // [G][P] J^T W r at p_b
   double* chi2_b;  // [G]
   double* lam;     // [G]
+  double* pred;    // [G] chi^2 decrease the quadratic model predicts for the pending step (inf: clamped)
   int* it;         // [G] evaluations done
   int* status;     // [G]
   int* nused;      // [G] unmasked pixels
@@ -217,6 +229,18 @@ __device__ inline double packed(const double* Ap, int P, int f, int h) {
   return Ap[f * P - (f * (f - 1)) / 2 + (h - f)];
 }
 
+// chi^2 decrease that the quadratic model chi^2(u + delta) = chi^2 - 2 g^T delta +
+// delta^T A delta predicts for the step delta (A packed).
+__device__ inline double predicted_decrease(const double* Ap, const double* g, const double* delta, int P) {
+  double s = 0.0;
+  for (int f = 0; f < P; ++f) {
+    double ad = 0.0;
+    for (int h = 0; h < P; ++h) ad += packed(Ap, P, f, h) * delta[h];
+    s += delta[f] * (2.0 * g[f] - ad);
+  }
+  return s;
+}
+
 // Gauss-Newton decrement g^T A^-1 g (A packed, regularised by 1e-12 max(diag A)
 // on the diagonal): the chi^2 reduction a full Gauss-Newton step predicts.
 // Negative when A cannot be factorised.
@@ -239,10 +263,18 @@ __device__ inline double gn_decrement(const double* Ap, const double* g, int P) 
 // sum the tile partials of the pass, accept or reject the evaluated point,
 // test convergence, solve the damped normal equations for the next trial point
 // and queue the galaxy for the next pass (list `cur ^ 1`).  The rules are the
-// ones the FP64 oracle states: accept when chi^2 drops; CONVERGED when an
+// ones the FP64 oracle states: accept when chi^2 drops -- or, for a step whose
+// predicted decrease is below kChi2Res chi^2, unless chi^2 rose by more than
+// kChi2Res chi^2, the step's decrease then taken as the predicted one (not
+// clamped steps); CONVERGED when an
 // accepted step lowers chi^2 by less than tol relative, any evaluated step
 // is below xtol, or the Gauss-Newton decrement at the best point is at most
 // gtol chi^2; STALLED / SINGULAR past lambda_max; MAX_ITER at max_iter.
+// With O.polish, a galaxy that reaches CONVERGED before max_iter queues one
+// undamped Gauss-Newton step from its best point instead of stopping; the
+// next step call adopts that point unless its chi^2 is non-finite or above
+// the best by more than kPolishSlack relative (FP32-accumulated chi^2 cannot
+// resolve the last decreases towards the minimum; the gradient can).
 // One thread per active galaxy, 32 galaxies per block.  The block first sums
 // its galaxies' tile partials together, the lanes taking (galaxy, entry) pairs in
 // turn so that neighbouring lanes read neighbouring entries, each entry over
@@ -288,6 +320,19 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
   S.it[g] = it;
   double lam = S.lam[g];
   bool accepted = false;
+  if (S.status[g] == ST_POLISH) {
+    // the final Gauss-Newton step's point, evaluated: it becomes the result unless
+    // its chi^2 is non-finite or above the best by more than the slack
+    const double chi2_b = S.chi2_b[g];
+    if (isfinite(chi2_t) && chi2_t <= chi2_b * (1.0 + kPolishSlack)) {
+      for (int s = 0; s < NS; ++s) pb[s] = pt[s];
+      for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
+      for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
+      S.chi2_b[g] = chi2_t;
+    }
+    S.status[g] = ST_CONVERGED;
+    return;
+  }
   if (it == 1) {
     if (!isfinite(chi2_t)) {
       st = ST_NONFINITE;
@@ -306,8 +351,12 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
       if (fabs(u1 - u0) > O.xtol * (fabs(u0) + O.xtol)) small = false;
     }
     const double chi2_b = S.chi2_b[g];
-    if (isfinite(chi2_t) && chi2_t < chi2_b) {
-      const double act = (chi2_b - chi2_t) / chi2_b;
+    // a step whose predicted decrease is below the resolution of chi^2 is accepted unless
+    // chi^2 rose by more than that resolution, and its decrease is the predicted one
+    const double pred = S.pred[g];
+    const bool resolved = pred >= kChi2Res * chi2_b;
+    if (isfinite(chi2_t) && (chi2_t < chi2_b || (!resolved && chi2_t <= chi2_b * (1.0 + kChi2Res)))) {
+      const double act = resolved ? (chi2_b - chi2_t) / chi2_b : fmax(pred, 0.0) / chi2_b;
       for (int s = 0; s < NS; ++s) pb[s] = pt[s];
       for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
       for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
@@ -328,6 +377,29 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
     if (gn >= 0.0 && gn <= O.gtol * S.chi2_b[g]) st = ST_CONVERGED;
   }
   if (st == ST_RUNNING && it >= O.max_iter) st = ST_MAX_ITER;
+  if (st == ST_CONVERGED && O.polish && it < O.max_iter && S.chi2_b[g] > 0.0) {
+    // final Gauss-Newton step from the best point: delta = A^-1 g with the diagonal
+    // floored as in the damped solve, evaluated in the next pass
+    double M[kMaxFree * kMaxFree], delta[kMaxFree];
+    double dmax = 0.0;
+    for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ab, P, f, f));
+    for (int f = 0; f < P; ++f)
+      for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
+    for (int f = 0; f < P; ++f) M[f * P + f] += 1e-12 * dmax;
+    if (cholesky(M, P)) {
+      chol_solve(M, P, gb, delta);
+      for (int s = 0; s < NS; ++s) pt[s] = pb[s];
+      for (int f = 0; f < P; ++f) {
+        const int s = D.free_slot[f];
+        pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
+      }
+      clamp_slots(D, pt);
+      setup_galaxy(D, pt, geo[g].H, geo[g].W, 1, cconst + (size_t)g * D.n_comp * kCC,
+                   scale + (size_t)g * scale_stride(NS));
+      queue_galaxy(S, cur ^ 1, g, geo[g]);
+      st = ST_POLISH;
+    }
+  }
   if (st == ST_RUNNING) {
     double M[kMaxFree * kMaxFree], delta[kMaxFree];
     double dmax = 0.0;
@@ -351,6 +423,9 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
         const int s = D.free_slot[f];
         pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
       }
+      S.pred[g] = predicted_decrease(Ab, gb, delta, P);
+      for (int s = 0; s < NS; ++s)
+        if (pt[s] < D.lo[s] || pt[s] > D.hi[s]) S.pred[g] = CUDART_INF;  // clamped: judged by chi^2
       clamp_slots(D, pt);
       setup_galaxy(D, pt, geo[g].H, geo[g].W, 1, cconst + (size_t)g * D.n_comp * kCC,
                    scale + (size_t)g * scale_stride(NS));

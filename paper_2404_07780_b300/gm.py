@@ -83,6 +83,7 @@ class gm_fit_opts(ctypes.Structure):
         ("lambda_down", ctypes.c_double),
         ("lambda_min", ctypes.c_double),
         ("lambda_max", ctypes.c_double),
+        ("polish", ctypes.c_int32),
     ]
 
 
@@ -120,10 +121,11 @@ class FitOptions:
     lambda_down: float = 0.1
     lambda_min: float = 1e-7
     lambda_max: float = 1e10
+    polish: int = 1
 
     def to_c(self) -> gm_fit_opts:
         return gm_fit_opts(self.tol, self.xtol, self.gtol, self.max_iter, self.lambda0, self.lambda_up, self.lambda_down,
-                           self.lambda_min, self.lambda_max)
+                           self.lambda_min, self.lambda_max, self.polish)
 
 
 _lib = None

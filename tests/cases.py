@@ -61,11 +61,13 @@ def from_batch(b: synth.Batch, at: str = "init") -> Case:
 
 
 def scale_of(spec) -> np.ndarray:
-    """Per-slot absolute scale used for parameter tolerances: 1 px, 1 rad, 1 sky unit, else |p|."""
+    """Per-slot absolute scale used for parameter tolerances: 1 px (centre), 1 rad (position
+    angle), 1 sky unit (sky level, and per pixel for the tilted sky's slopes), 1 for the
+    boxiness B (its exponent is B + 2); 0 (purely relative) for the rest."""
     s = np.zeros(spec.n_slots)
     for i, name in enumerate(spec.names):
         role = name.split(".")[-1]
-        s[i] = 1.0 if role in ("x0", "y0", "pa", "Isky") else 0.0
+        s[i] = 1.0 if role in ("x0", "y0", "pa", "Isky", "kx", "ky", "B") else 0.0
     return s
 
 

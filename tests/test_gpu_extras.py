@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import Case, psf_image
+from cases import Case, psf_image, scale_of
 from paper_2404_07780_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -57,7 +57,7 @@ def _check_normal(gm, c):
     free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
     for g in range(c.G):
         d = np.sqrt(np.diag(rA[g]))
-        assert (np.abs(grad[g, free] + 2.0 * rg[g]) <= 2e-4 * d * math.sqrt(rc2[g]) + 1e-300).all(), g
+        assert (np.abs(grad[g, free] + 2.0 * rg[g]) <= 1e-4 * d * math.sqrt(rc2[g]) + 1e-300).all(), g
         assert (np.abs(jtj[g][np.ix_(free, free)] - rA[g]) <= 1e-4 * np.outer(d, d) + 1e-300).all(), g
 
 
@@ -104,7 +104,7 @@ def test_tilted_sky_fit_recovers_the_plane(gm):
                      None, oracle.FitOptions(**opts))
     assert (got["status"] == 1).all() and (ref["status"] == 1).all()
     np.testing.assert_allclose(got["chi2"], ref["chi2"], rtol=1e-5)
-    tol = np.maximum(1e-4 * np.maximum(np.abs(ref["params"]), 1.0), 1e-2 * ref["sigma_p"])
+    tol = 1e-4 * np.maximum(np.abs(ref["params"]), scale_of(spec))
     d = np.abs(got["params"] - ref["params"])
     d[:, 3] = np.minimum(d[:, 3] % math.pi, math.pi - d[:, 3] % math.pi)
     assert (d <= tol).all(), (d / tol).max(0)
@@ -186,11 +186,11 @@ def test_magnitude_fit_matches_oracle(gm):
                      None, oracle.FitOptions(**opts))
     assert (got["status"] == 1).all() and (ref["status"] == 1).all()
     np.testing.assert_allclose(got["chi2"], ref["chi2"], rtol=1e-5)
-    tol = np.maximum(1e-4 * np.maximum(np.abs(ref["params"]), 1.0), 1e-2 * ref["sigma_p"])
+    tol = 1e-4 * np.maximum(np.abs(ref["params"]), scale_of(spec))
     d = np.abs(got["params"] - ref["params"])
     d[:, 3] = np.minimum(d[:, 3] % math.pi, math.pi - d[:, 3] % math.pi)
     assert (d <= tol).all(), (d / tol).max(0)
-    np.testing.assert_allclose(got["sigma_p"][:, 4], ref["sigma_p"][:, 4], rtol=1e-2)  # magnitude error bars
+    np.testing.assert_allclose(got["sigma_p"][:, 4], ref["sigma_p"][:, 4], rtol=1e-4)  # magnitude error bars
 
 
 def test_magnitude_for_king_is_unsupported(gm):
@@ -335,7 +335,7 @@ def test_boxy_fit_matches_oracle(gm):
                      None, oracle.FitOptions(**opts))
     assert (got["status"] == 1).all() and (ref["status"] == 1).all()
     np.testing.assert_allclose(got["chi2"], ref["chi2"], rtol=1e-5)
-    tol = np.maximum(1e-4 * np.maximum(np.abs(ref["params"]), 1.0), 1e-2 * ref["sigma_p"])
+    tol = 1e-4 * np.maximum(np.abs(ref["params"]), scale_of(spec))
     d = np.abs(got["params"] - ref["params"])
     d[:, 3] = np.minimum(d[:, 3] % math.pi, math.pi - d[:, 3] % math.pi)
     assert (d <= tol).all(), (d / tol).max(0)

@@ -75,7 +75,7 @@ def test_fullsize_normal_equations(full):
         s = src[g]
         assert abs(chi2[g] - rchi2[s]) <= 1e-5 * rchi2[s], g
         d = np.sqrt(np.diag(rA[s]))
-        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 2e-4 * d * math.sqrt(rchi2[s])).all(), g
+        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 1e-4 * d * math.sqrt(rchi2[s])).all(), g
         assert (np.abs(jtj[g][np.ix_(free, free)] - rA[s]) <= 1e-4 * np.outer(d, d)).all(), g
 
 
@@ -94,9 +94,10 @@ def test_fullsize_fit(full):
     sub = {k: v[picks] for k, v in got.items()}
     rsub = {k: np.asarray(v)[src[picks]] for k, v in ref.items() if np.ndim(v) > 0}
     same, rel = _compare_fits(c.spec, sub, rsub)
-    # from the default start a fit may settle in another minimum; those that reach the
-    # oracle's chi^2 must agree, and at least half of the sources must
-    assert len(set(src[np.array(picks)[same]])) >= n // 2, (sub["status"], rsub["status"], sub["chi2"], rsub["chi2"])
+    # from the default start every fit ends with the oracle's status, and every converged
+    # fit at the oracle's minimum: the same chi^2 and the same parameters
+    np.testing.assert_array_equal(sub["status"], rsub["status"])
+    assert (same == (rsub["status"] == 1)).all(), (sub["chi2"], rsub["chi2"])
     assert rel[same].max() <= 1e-4, rel[same].max(axis=1)
 
 
@@ -139,7 +140,7 @@ def test_fullsize_uneven_normal_equations(full):
         rc, rg, rA = _oracle_normal_one(cases[g])
         assert abs(chi2[g] - rc) <= 1e-5 * rc, g
         d = np.sqrt(np.diag(rA))
-        assert (np.abs(grad[g, free] + 2.0 * rg) <= 2e-4 * d * math.sqrt(rc)).all(), g
+        assert (np.abs(grad[g, free] + 2.0 * rg) <= 1e-4 * d * math.sqrt(rc)).all(), g
         assert (np.abs(jtj[g][np.ix_(free, free)] - rA) <= 1e-4 * np.outer(d, d)).all(), g
 
 
@@ -163,4 +164,4 @@ def test_fullsize_adjoint_gradient(full):
         s = src[g]
         assert abs(chi2[g] - rchi2[s]) <= 1e-5 * rchi2[s], g
         d = np.sqrt(np.diag(rA[s]))
-        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 2e-4 * d * math.sqrt(rchi2[s])).all(), g
+        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 1e-4 * d * math.sqrt(rchi2[s])).all(), g

@@ -158,7 +158,7 @@ def test_chi2_grad_jtj_small(gm, at):
     for gi in range(c.G):
         d = np.sqrt(np.diag(rA[gi]))
         gbound = 1e-4 * d * math.sqrt(rchi2[gi])
-        assert (np.abs(grad[gi, free] - (-2.0 * rg[gi])) <= 2.0 * gbound).all(), gi
+        assert (np.abs(grad[gi, free] - (-2.0 * rg[gi])) <= gbound).all(), gi
         Asub = jtj[gi][np.ix_(free, free)]
         assert (np.abs(Asub - rA[gi]) <= 1e-4 * np.outer(d, d)).all(), gi
 
@@ -173,7 +173,7 @@ def test_chi2_with_mask_and_contaminants(gm):
     free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
     grad = _np(grad)
     for gi in range(c.G):
-        bound = 2e-4 * np.sqrt(np.diag(rA[gi])) * math.sqrt(rchi2[gi])
+        bound = 1e-4 * np.sqrt(np.diag(rA[gi])) * math.sqrt(rchi2[gi])
         assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= bound).all(), gi
 
 
@@ -193,7 +193,7 @@ def test_chi2_grad_many_parameters(gm, draw, K):
     free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
     for gi in range(c.G):
         d = np.sqrt(np.diag(rA[gi]))
-        assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= 2e-4 * d * math.sqrt(rchi2[gi])).all(), gi
+        assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= 1e-4 * d * math.sqrt(rchi2[gi])).all(), gi
         Asub = jtj[gi][np.ix_(free, free)]
         assert (np.abs(Asub - rA[gi]) <= 1e-4 * np.outer(d, d)).all(), gi
 
@@ -205,12 +205,8 @@ def test_chi2_grad_many_parameters(gm, draw, K):
 def _compare_fits(spec, got, ref, tol=1e-4):
     """Indices compared and the worst parameter difference in units of the tolerance.
 
-    A parameter agrees when |dp| <= max(1e-4 max(|p|, s_p), 1e-2 sigma_p): the relative bar,
-    or 1% of the parameter's own statistical error.  The second clause matters only for
-    ill-conditioned fits (faint galaxies with strongly correlated parameters), where FP32
-    rounding in the Jacobian displaces the minimum along the soft directions by up to
-    ~1e-2 sigma_p; well-conditioned fits meet the relative bar alone."""
-    s = np.maximum(np.maximum(np.abs(ref["params"]), scale_of(spec)) * tol, 1e-2 * ref["sigma_p"]) / tol
+    A parameter agrees when |dp| <= 1e-4 max(|p|, s_p) (s_p = 1 px, 1 rad, 1 sky unit)."""
+    s = np.maximum(np.abs(ref["params"]), scale_of(spec))
     both = (got["status"] == 1) & (ref["status"] == 1)
     # the same minimum: chi^2 within the parity tolerance
     same = both & (np.abs(got["chi2"] - ref["chi2"]) <= 1e-5 * ref["chi2"])
@@ -268,13 +264,12 @@ def test_fit_near_truth_matches_oracle(gm):
     np.testing.assert_array_equal(got["dof"], ref["dof"])
     free = np.array(c.spec.free, bool)
     sig_rel = np.abs(got["sigma_p"] - ref["sigma_p"])[:, free] / ref["sigma_p"][:, free]
-    assert sig_rel.max() <= 1e-2, sig_rel.max()  # an error bar from N pixels is itself uncertain by ~(2N)^-1/2 ~ 1%
+    assert sig_rel.max() <= 1e-4, sig_rel.max()
 
 
 def test_fit_default_start_same_minimum(gm):
-    # from the default start the LM trajectory is chaotic (a 1e-7 relative change
-    # of the start moves the FP64 oracle itself to other minima on some galaxies);
-    # fits that reach the same chi^2 must agree, and most of them do
+    # from the default start (the centre of the prior ranges) every fit must reach the
+    # oracle's minimum: the same chi^2 and the same parameters
     b = synth.draw_small(seed=0, G=16)
     c = from_batch(b, at="init")
     t = c.torch()
@@ -284,7 +279,7 @@ def test_fit_default_start_same_minimum(gm):
     oi = oracle_inputs(c)
     ref = oracle.fit(c.spec, c.params, oi["psf"], oi["image"], oi["sigma"], c.mask, oracle.FitOptions(**FIT_TIGHT))
     same, rel = _compare_fits(c.spec, got, ref)
-    assert same.sum() >= 8, (got["status"], ref["status"])
+    assert same.all(), (got["status"], ref["status"], got["chi2"], ref["chi2"])
     assert rel[same].max() <= 1e-4, rel[same].max(axis=1)
 
 
@@ -305,11 +300,11 @@ def test_fit_through_q_one_matches_oracle(gm):
     ref = oracle.fit(c.spec, c.params, oi["psf"], oi["image"], oi["sigma"], c.mask, oracle.FitOptions(**FIT_TIGHT))
     assert (got["params"][:, 2] <= 1.0).all() and (ref["params"][:, 2] <= 1.0).all()
     same, rel = _compare_fits(c.spec, got, ref)
-    assert same.sum() >= 6, (got["status"], ref["status"], got["chi2"], ref["chi2"])
+    assert same.all(), (got["status"], ref["status"], got["chi2"], ref["chi2"])
     assert rel[same].max() <= 1e-4, rel[same].max(axis=1)
     free = np.array(c.spec.free, bool)
     sig_rel = np.abs(got["sigma_p"] - ref["sigma_p"])[same][:, free] / ref["sigma_p"][same][:, free]
-    assert sig_rel.max() <= 1e-2, sig_rel.max()  # an error bar from N pixels is itself uncertain by ~(2N)^-1/2 ~ 1%
+    assert sig_rel.max() <= 1e-4, sig_rel.max()
 
 
 def test_fit_status_codes(gm):
@@ -347,7 +342,7 @@ def test_grad_adjoint_matches_normal_equations(gm, draw, G, H, W, K):
     chi2, grad, rchi2, rgrad, rjtj = map(_np, (chi2, grad, rchi2, rgrad, rjtj))
     np.testing.assert_allclose(chi2, rchi2, rtol=1e-5)
     for gi in range(c.G):
-        bound = 2e-4 * np.sqrt(np.abs(np.diag(rjtj[gi]))) * math.sqrt(rchi2[gi])
+        bound = 1e-4 * np.sqrt(np.abs(np.diag(rjtj[gi]))) * math.sqrt(rchi2[gi])
         assert (np.abs(grad[gi] - rgrad[gi]) <= bound + 1e-300).all(), gi
 
 
@@ -363,7 +358,7 @@ def test_grad_adjoint_vs_oracle_finite_differences(gm):
     np.testing.assert_allclose(chi2, rchi2, rtol=1e-5)
     free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
     for gi in range(c.G):
-        bound = 2e-4 * np.sqrt(np.diag(rA[gi])) * math.sqrt(rchi2[gi])
+        bound = 1e-4 * np.sqrt(np.diag(rA[gi])) * math.sqrt(rchi2[gi])
         assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= bound).all(), gi
 
 
@@ -382,7 +377,7 @@ def test_normal_equations_and_adjoint_at_ragged_sizes(gm, H, W, K):
     free = [i for i in range(c.spec.n_slots) if c.spec.free[i]]
     for g in range(c.G):
         d = np.sqrt(np.diag(rA[g]))
-        bound = 2e-4 * d * math.sqrt(rchi2[g])
+        bound = 1e-4 * d * math.sqrt(rchi2[g])
         for name, x2, gr in (("normal", chi2, grad), ("adjoint", achi2, agrad)):
             assert abs(x2[g] - rchi2[g]) <= 1e-5 * rchi2[g], (name, g)
             assert (np.abs(gr[g, free] + 2.0 * rg[g]) <= bound).all(), (name, g)
@@ -408,7 +403,7 @@ def test_grad_adjoint_block_ranges_across_pairs(gm):
         s = src[g]
         assert abs(chi2[g] - rchi2[s]) <= 1e-5 * rchi2[s], g
         d = np.sqrt(np.diag(rA[s]))
-        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 2e-4 * d * math.sqrt(rchi2[s])).all(), g
+        assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 1e-4 * d * math.sqrt(rchi2[s])).all(), g
 
 
 def test_chi2_autograd_function_and_adam(gm):
@@ -468,5 +463,5 @@ def test_sersic_index_on_both_sides_of_the_nu_table(gm, n):
     np.testing.assert_allclose(chi2, rchi2, rtol=1e-5)
     free = [i for i in range(spec.n_slots) if spec.free[i]]
     d = np.sqrt(np.diag(rA[0]))
-    assert (np.abs(grad[0, free] + 2.0 * rg[0]) <= 2e-4 * d * math.sqrt(rchi2[0])).all()
+    assert (np.abs(grad[0, free] + 2.0 * rg[0]) <= 1e-4 * d * math.sqrt(rchi2[0])).all()
     assert (np.abs(jtj[0][np.ix_(free, free)] - rA[0]) <= 1e-4 * np.outer(d, d)).all()

@@ -90,7 +90,7 @@ def test_uneven_chi2_grad_jtj_matches_oracle(gm, which):
         rchi2, rg, rA = _oracle_normal_one(cg)
         assert abs(chi2[g] - rchi2) <= 1e-5 * rchi2, (g, chi2[g], rchi2)
         d = np.sqrt(np.diag(rA))
-        assert (np.abs(grad[g, free] + 2.0 * rg) <= 2e-4 * d * math.sqrt(rchi2) + 1e-300).all(), g
+        assert (np.abs(grad[g, free] + 2.0 * rg) <= 1e-4 * d * math.sqrt(rchi2) + 1e-300).all(), g
         assert (np.abs(jtj[g][np.ix_(free, free)] - rA) <= 1e-4 * np.outer(d, d) + 1e-300).all(), g
 
 
@@ -134,7 +134,7 @@ def test_uneven_fit_near_truth_matches_oracle(gm):
         assert abs(got["chi2"][g] - ref["chi2"][0]) <= 1e-5 * ref["chi2"][0], g
         assert got["dof"][g] == ref["dof"][0]
         scale = np.array([1.0 if n.split(".")[-1] in ("x0", "y0", "pa", "Isky") else 0.0 for n in c.spec.names])
-        tol = np.maximum(1e-4 * np.maximum(np.abs(ref["params"][0]), scale), 1e-2 * ref["sigma_p"][0])
+        tol = 1e-4 * np.maximum(np.abs(ref["params"][0]), scale)
         diff = np.abs(got["params"][g] - ref["params"][0])
         pa = c.spec.slot("bulge.pa")
         d = diff[pa] % math.pi
