@@ -81,9 +81,13 @@ extern "C" {
 #define GM_E_NOMEM (-3)        /* workspace smaller than the *_workspace_bytes() query */
 #define GM_E_UNSUPPORTED (-4)  /* valid request outside what this build handles */
 #define GM_E_TIMEOUT (-5)      /* a kernel's bounded wait for a tile load ran out (the
-                                  kernel stopped instead of hanging); reported by the
+                                  kernel stopped instead of hanging); returned by the
                                   calls that synchronise (gm_fit_batch, gm_fit_adam,
-                                  gm_bootstrap) */
+                                  gm_bootstrap).  The asynchronous calls (gm_model,
+                                  gm_chi2_grad, gm_chi2_grad_noalloc, gm_grad_adjoint)
+                                  return GM_OK and write NaN to every output element of
+                                  the call instead (which galaxy lost a tile is not
+                                  recorded) */
 
 /* per-galaxy fit status (status_out) */
 #define GM_ST_RUNNING 0
@@ -276,6 +280,19 @@ int gm_grad_adjoint(const gm_model_desc *desc, const gm_batch *batch, const doub
 #define GM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int gm_chi2_grad_noalloc(const gm_model_desc *desc, const gm_batch *batch, const double *params,
                          double *chi2, double *grad, double *jtj, void *stream);
+
+/*
+ * gm_test_starve_next_pass -- a test of the timeout path; not part of the
+ * paper's method.  Arms a one-shot fault on the host: the next tile-kernel
+ * launch made by the calling thread (the fused pass of gm_model, gm_chi2_grad,
+ * gm_chi2_grad_noalloc and the first iteration of gm_fit_batch, or the first
+ * adjoint pass of gm_grad_adjoint and gm_fit_adam) has its first block skip the
+ * load of its first window, so that its bounded wait finds nothing arriving and
+ * gives up after `polls` polls instead of the normal limit, with no copy in
+ * flight.  The call then reports the timeout as any other would (GM_E_TIMEOUT,
+ * or NaN outputs; see GM_E_TIMEOUT).  polls = 0 disarms.  Always GM_OK.
+ */
+int gm_test_starve_next_pass(uint32_t polls);
 
 /*
  * gm_fit_batch -- Levenberg-Marquardt fit of every galaxy (damped Gauss-Newton

@@ -129,6 +129,8 @@ struct AdjArgs {
   double* partial;           // [G][n_tiles][nacc]: RESID writes [0] chi^2 and unconvolved terms,
                              //                     ADJ adds the convolved terms to a second copy
   int* err;
+  unsigned wait_polls;       // polls of a window wait before it gives up (kWaitTries)
+  int starve;                // test of the timeout path: block 0 issues no load for its first window
   int off_psf, off_in, off_cc, off_red, off_bar;
 };
 
@@ -204,7 +206,11 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
     *s_flag = 0;
   }
   __syncthreads();
-  if (tid == 0) adj_issue(A, s_in, bar, it_lo);
+  bool inflight = false;  // thread 0: a window load is outstanding on the mbarrier
+  if (tid == 0 && !(A.starve && blockIdx.x == 0)) {
+    adj_issue(A, s_in, bar, it_lo);
+    inflight = true;
+  }
   unsigned phase = 0;
   const int lane = tid & 31, wig = tid >> 5;
   const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
@@ -243,13 +249,14 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
     const int a_hi = min(K, c - i0 + A.H - row0);
 
     if (tid == 0) {
-      if (!mbar_wait_bounded(bar, phase)) *s_flag = 1;
+      if (mbar_wait_bounded(bar, phase, A.wait_polls)) inflight = false;
+      else *s_flag = 1;
     }
     __syncthreads();
     if (*s_flag) {
       if (tid == 0) {
         atomicExch(A.err, 1);
-        mbar_wait_bounded(bar, phase);
+        if (inflight) mbar_wait_bounded(bar, phase);  // let the copy in flight land before leaving
       }
       return;
     }
@@ -258,7 +265,10 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
     u64 acc[1][8];
     correlate_pairs<1>(acc, s_in, s_psf, 0, A.plane, A.rw, K, row, col0, a_lo, a_hi);
     __syncthreads();  // every warp is done reading the window
-    if (tid == 0 && item + 1 < it_hi) adj_issue(A, s_in, bar, item + 1);
+    if (tid == 0 && item + 1 < it_hi) {
+      adj_issue(A, s_in, bar, item + 1);
+      inflight = true;
+    }
 
     // ---- epilogue: this thread's 8 pixels, both galaxies, straight from registers ----
     // Code size decides its speed: eval_component is a large inline body, and a fully
@@ -400,12 +410,19 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
 
 #ifdef GM_HOST_TU
 // chi^2 and d chi^2/dp = -2 (unconvolved + convolved terms) from the two passes' partials.
+// A tile load that timed out (*err set) leaves partial sums unwritten: every output is NaN then.
 __global__ void k_adjoint_finish(const __grid_constant__ DescDev D, int G, int n_tiles,
                                  const double* __restrict__ part_resid, const double* __restrict__ part_adj,
-                                 double* chi2, double* grad) {
+                                 const int* __restrict__ err, double* chi2, double* grad) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
   const int P = D.P, n_slots = D.n_slots;
+  if (*err) {
+    chi2[g] = CUDART_NAN;
+    if (grad)
+      for (int s = 0; s < n_slots; ++s) grad[(size_t)g * n_slots + s] = CUDART_NAN;
+    return;
+  }
   const int* free_slot = D.free_slot;
   const int NA = 1 + P;
   double acc[1 + kMaxFree];

@@ -134,6 +134,9 @@ struct FusedArgs {
   float* model_out;          // stamp g from geo[g].pix
   float* comp_out;           // [n_comp] images per stamp from n_comp * geo[g].pix, or nullptr
   int* err;                  // set to 1 when a TMA wait times out
+  unsigned wait_polls;       // polls of a window wait before it gives up (kWaitTries)
+  int starve;                // test of the timeout path: CTA 0 issues no load for its first window, so
+                             // that wait runs out with nothing in flight
   int off_psf, off_in, off_out, off_cc, off_scale, off_red, off_bar, off_info;
 };
 
@@ -239,9 +242,9 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, unsigned phase) {
   return done != 0;
 }
 
-// Bounded wait for a phase of the mbarrier; false after kWaitTries polls.
-__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, unsigned phase) {
-  for (unsigned t = 0; t < kWaitTries; ++t)
+// Bounded wait for a phase of the mbarrier; false after `polls` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, unsigned phase, unsigned polls = kWaitTries) {
+  for (unsigned t = 0; t < polls; ++t)
     if (mbar_try_wait(bar, phase)) return true;
   return false;
 }
@@ -827,12 +830,16 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
   const int n_items = A.n_items_dev ? *A.n_items_dev : A.n_items;
   if ((int)blockIdx.x >= n_items) return;
 
+  bool inflight = false;  // thread 0: a window load is outstanding on the mbarrier
   if (tid == 0) {
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
     fetch_item(A, n_items, blockIdx.x, &s_info[0]);
-    issue_pass(A, s_info[0], s_in, bar, 0, s_psf, s_cc0, s_scale0);
+    if (!(A.starve && blockIdx.x == 0)) {
+      issue_pass(A, s_info[0], s_in, bar, 0, s_psf, s_cc0, s_scale0);
+      inflight = true;
+    }
   }
   unsigned phase = 0;
   int slot = 0;
@@ -870,13 +877,14 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
     for (int pass = 0; pass < A.passes; ++pass) {
       // wait for this pass's window (thread 0 polls with a bound, the CTA agrees)
       if (tid == 0) {
-        if (!mbar_wait_bounded(bar, phase)) *s_flag = 1;
+        if (mbar_wait_bounded(bar, phase, A.wait_polls)) inflight = false;
+        else *s_flag = 1;
       }
       __syncthreads();
       if (*s_flag) {
         if (tid == 0) {
           atomicExch(A.err, 1);
-          mbar_wait_bounded(bar, phase);  // let the copy in flight land before leaving
+          if (inflight) mbar_wait_bounded(bar, phase);  // let the copy in flight land before leaving
         }
         return;
       }
@@ -907,9 +915,13 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
       else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
       __syncthreads();  // every warp is done reading the window
       if (tid == 0) {
-        if (pass + 1 < A.passes) issue_pass(A, I, s_in, bar, pass + 1, s_psf, nullptr, nullptr);
-        else if (s_info[slot ^ 1].valid)
+        if (pass + 1 < A.passes) {
+          issue_pass(A, I, s_in, bar, pass + 1, s_psf, nullptr, nullptr);
+          inflight = true;
+        } else if (s_info[slot ^ 1].valid) {
           issue_pass(A, s_info[slot ^ 1], s_in, bar, 0, s_psf, s_cc0 + (slot ^ 1) * cc_n, s_scale0 + (slot ^ 1) * sc_n);
+          inflight = true;
+        }
       }
       if (split) {
         // the first part stores, the others add in turn

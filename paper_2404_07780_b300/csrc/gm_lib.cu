@@ -44,6 +44,17 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GM_NOALLOC_SCRA
 namespace {
 
 thread_local char g_err[512] = "no error";
+// gm_test_starve_next_pass: the poll limit of the next tile-kernel launch made by
+// this thread whose first block is to skip its first window load (0: none armed).
+thread_local unsigned g_starve_polls = 0;
+
+// The armed starvation (once), or false.
+bool take_starve(unsigned* polls) {
+  if (!g_starve_polls) return false;
+  *polls = g_starve_polls;
+  g_starve_polls = 0;
+  return true;
+}
 thread_local gm_fit_stats g_stats;
 thread_local bool g_have_stats = false;
 // CUDA events timing the passes of gm_fit_batch, created on first use and kept
@@ -680,6 +691,7 @@ WsFit ws_fit(const gm_model_desc* d, const GeomPlan& gp, int P) {
 // Kernel arguments that depend only on the model and the shared-memory plan.
 void fill_args(FusedArgs& A, const Plan& pl, const Smem& sm) {
   std::memset(&A, 0, sizeof(A));
+  A.wait_polls = kWaitTries;
   A.m = chan_map(pl);
   A.nacc = pl.nacc;
   A.pp = sm.pp;
@@ -935,9 +947,21 @@ int launch_pass(int mode, PassCall* pc, cudaStream_t st) {
   else k_planes<MODE_NORMAL><<<pgrid, 256, 0, st>>>(pc->PA);
   GM_LAUNCHED("k_planes");
   const int grid = (int)std::max<long long>(1, std::min<long long>(n, pc->di.sms));
-  pc->kf<<<grid, pc->sm.threads, pc->sm.total, st>>>(pc->A);
+  FusedArgs A = pc->A;
+  if (take_starve(&A.wait_polls)) A.starve = 1;
+  pc->kf<<<grid, pc->sm.threads, pc->sm.total, st>>>(A);
   GM_LAUNCHED("k_fused");
   return GM_OK;
+}
+
+// Every element of a and b set to NaN when *err is set (a tile load of the pass timed out).
+__global__ void k_nan_if_err(const int* __restrict__ err, float* a, size_t na, float* b, size_t nb) {
+  if (!*err) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
+    if (i < na) a[i] = CUDART_NAN_F;
+    else b[i - na] = CUDART_NAN_F;
+  }
 }
 
 }  // namespace
@@ -954,6 +978,11 @@ int gm_fit_last_stats(gm_fit_stats* out) {
 }
 
 const char* gm_last_error(void) { return g_err; }
+
+int gm_test_starve_next_pass(uint32_t polls) {
+  g_starve_polls = polls;
+  return GM_OK;
+}
 
 int gm_tune_set(int32_t K, int32_t P, int32_t pairs_per_pass, int32_t pairs_per_thread, int32_t groups) {
   if (K < 1 || K > 63 || (K % 2) == 0) return fail(GM_E_INVAL, "gm_tune_set: K=%d must be odd, 1..63", K);
@@ -1005,7 +1034,16 @@ int gm_model(const gm_model_desc* desc, const gm_batch* batch, const double* par
   if ((rc = setup_pass(MODE_MODEL, desc, batch, params, workspace, ws_bytes, st, &pc))) return rc;
   pc.A.model_out = model_out;
   pc.A.comp_out = comp_out;
-  return launch_pass(MODE_MODEL, &pc, st);
+  if ((rc = launch_pass(MODE_MODEL, &pc, st))) return rc;
+  size_t npix = (size_t)batch->n_gal * (size_t)batch->H * (size_t)batch->W;
+  if (batch->geom) {
+    npix = 0;
+    for (int g = 0; g < batch->n_gal; ++g) npix += (size_t)batch->geom[3 * g] * (size_t)batch->geom[3 * g + 1];
+  }
+  k_nan_if_err<<<4 * pc.di.sms, 256, 0, st>>>(pc.A.err, model_out, npix, comp_out,
+                                               comp_out ? npix * (size_t)desc->n_comp : 0);
+  GM_LAUNCHED("k_nan_if_err");
+  return GM_OK;
 }
 
 size_t gm_chi2_grad_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {
@@ -1029,7 +1067,7 @@ int gm_chi2_grad(const gm_model_desc* desc, const gm_batch* batch, const double*
   if ((rc = launch_pass(MODE_NORMAL, &pc, st))) return rc;
   const int G = batch->n_gal;
   k_chi2_grad_finish<<<(G + kLmWarps - 1) / kLmWarps, 32 * kLmWarps, 0, st>>>(pc.pl.dd, G, pc.A.geo, pc.A.partial,
-                                                                                chi2, grad, jtj);
+                                                                                pc.A.err, chi2, grad, jtj);
   GM_LAUNCHED("k_chi2_grad_finish");
   return GM_OK;
 }
@@ -1152,7 +1190,9 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
     k_planes<MODE_NORMAL><<<pgrid, 256, 0, cap>>>(PA);
     GM_LAUNCHED("k_planes");
     GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 1], cap, cudaEventRecordExternal));
-    kf<<<grid, sm.threads, sm.total, cap>>>(A);
+    FusedArgs Au = A;
+    if (u == 0 && take_starve(&Au.wait_polls)) Au.starve = 1;
+    kf<<<grid, sm.threads, sm.total, cap>>>(Au);
     GM_LAUNCHED("k_fused(normal)");
     GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 2], cap, cudaEventRecordExternal));
     k_lm_step<<<(G + kLmBlock - 1) / kLmBlock, kLmBlock, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst, scale);
@@ -1309,6 +1349,7 @@ int prepare_adjoint(const gm_model_desc* desc, const gm_batch* batch, void* work
   A.psf = batch->psf;
   A.cconst = cconst;
   A.err = (int*)(ws + w.err);
+  A.wait_polls = kWaitTries;
   size_t off = 0;
   auto take = [&](size_t bytes, size_t align) {
     off = (off + align - 1) / align * align;
@@ -1351,12 +1392,14 @@ int launch_adjoint(const AdjPass& ap, const gm_batch* batch, const double* param
   GM_LAUNCHED("k_setup");
   k_profile_pairs<<<ap.pgrid, 256, 0, st>>>(ap.PA);
   GM_LAUNCHED("k_profile_pairs");
-  ap.kr<<<ap.grid, 128, ap.smem, st>>>(ap.Ar);
+  AdjArgs Ar = ap.Ar;
+  if (take_starve(&Ar.wait_polls)) Ar.starve = 1;
+  ap.kr<<<ap.grid, 128, ap.smem, st>>>(Ar);
   GM_LAUNCHED("k_adjoint(resid)");
   ap.ka<<<ap.grid, 128, ap.smem, st>>>(ap.Aa);
   GM_LAUNCHED("k_adjoint(grad)");
-  k_adjoint_finish<<<(G + 127) / 128, 128, 0, st>>>(ap.pl.dd, G, ap.Ar.n_tiles, ap.Ar.partial, ap.Aa.partial, chi2,
-                                                    grad);
+  k_adjoint_finish<<<(G + 127) / 128, 128, 0, st>>>(ap.pl.dd, G, ap.Ar.n_tiles, ap.Ar.partial, ap.Aa.partial,
+                                                    ap.Ar.err, chi2, grad);
   GM_LAUNCHED("k_adjoint_finish");
   return GM_OK;
 }

@@ -552,12 +552,22 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
 __global__ void __launch_bounds__(32 * kLmWarps) k_chi2_grad_finish(const __grid_constant__ DescDev D, int G,
                                                                      const GalGeom* __restrict__ geo,
                                                                      const double* __restrict__ partial,
-                                                                     double* chi2, double* grad, double* jtj) {
+                                                                     const int* __restrict__ err, double* chi2,
+                                                                     double* grad, double* jtj) {
   __shared__ double s_acc[kLmWarps][kMaxAcc];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int g = blockIdx.x * kLmWarps + wl;
   if (g >= G) return;
   const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
+  if (*err) {
+    // a tile load timed out: some partial sums were never written, so every output is NaN
+    for (int e = lane; e < NS * NS; e += 32) {
+      if (e == 0) chi2[g] = CUDART_NAN;
+      if (grad && e < NS) grad[(size_t)g * NS + e] = CUDART_NAN;
+      if (jtj) jtj[(size_t)g * NS * NS + e] = CUDART_NAN;
+    }
+    return;
+  }
   const int n_tiles = geo[g].n_tiles;
   const double* pp = partial + (size_t)geo[g].tile0 * NA;
   for (int e = lane; e < NA; e += 32) {

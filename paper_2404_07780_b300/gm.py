@@ -32,7 +32,7 @@ EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model"
            "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch",
            "gm_fit_last_stats", "gm_chi2_grad_noalloc", "gm_grad_adjoint_workspace_bytes", "gm_grad_adjoint",
            "gm_tune_set", "gm_tune_clear", "gm_tune_last_shape", "gm_fit_adam_workspace_bytes", "gm_fit_adam",
-           "gm_bootstrap_workspace_bytes", "gm_bootstrap_counts", "gm_bootstrap")
+           "gm_bootstrap_workspace_bytes", "gm_bootstrap_counts", "gm_bootstrap", "gm_test_starve_next_pass")
 
 
 class GMError(RuntimeError):
@@ -173,6 +173,8 @@ def load() -> ctypes.CDLL:
         lib.gm_fit_adam.restype = ctypes.c_int
         lib.gm_fit_adam.argtypes = [P, P, P, P, P, P, S, P]
         I32 = ctypes.c_int32
+        lib.gm_test_starve_next_pass.restype = ctypes.c_int
+        lib.gm_test_starve_next_pass.argtypes = [ctypes.c_uint32]
         lib.gm_tune_set.restype = ctypes.c_int
         lib.gm_tune_set.argtypes = [I32, I32, I32, I32, I32]
         lib.gm_tune_clear.restype = ctypes.c_int
