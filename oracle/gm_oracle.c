@@ -529,19 +529,45 @@ static void or_pa_slots(const or_desc *d, int *is_pa) {
     if (!or_flat(d->kind[c])) is_pa[d->slot[c][3]] = 1;
 }
 
-/* Gauss-Newton decrement g^T A^-1 g: the chi^2 reduction a full Gauss-Newton
- * step predicts from the current point (A regularised by 1e-12 max(diag A)
- * on the diagonal).  Negative when A cannot be factorised. */
-static double or_gn_decrement(const double *A, const double *g, int nf) {
-  double M[OR_MAX_SLOTS * OR_MAX_SLOTS], x[OR_MAX_SLOTS];
+/* held[a] = 1 for a free parameter that sits on a bound while chi^2 falls
+ * beyond it (g = J^T W r is the descent direction): at its lower bound with
+ * g_a < 0, or at its upper bound with g_a > 0.  A held parameter does not move
+ * in the next step. */
+static void or_held(const or_desc *d, const int *fidx, int nf, const double *p, const double *g, int *held) {
+  for (int a = 0; a < nf; ++a) {
+    int s = fidx[a];
+    held[a] = (p[s] <= d->lo[s] && g[a] < 0.0) || (p[s] >= d->hi[s] && g[a] > 0.0);
+  }
+}
+
+/* The linear system of a step over the parameters not held:
+ * M = A + lambda max(A_aa, 1e-12 max diag A) on the diagonal (lambda = 0: the
+ * 1e-12 max diag A term alone), with the rows and columns of held parameters
+ * replaced by those of the identity; rhs r = g with zeros at held parameters. */
+static void or_step_system(const double *A, const double *g, int nf, double lambda, const int *held, double *M,
+                           double *r) {
   double dmax = 0.0;
   for (int a = 0; a < nf; ++a) dmax = fmax(dmax, A[a * nf + a]);
-  for (int a = 0; a < nf * nf; ++a) M[a] = A[a];
-  for (int a = 0; a < nf; ++a) M[a * nf + a] += 1e-12 * dmax;
+  double dfloor = 1e-12 * dmax;
+  for (int a = 0; a < nf; ++a) {
+    for (int b = 0; b < nf; ++b)
+      M[a * nf + b] = (held[a] || held[b]) ? (a == b ? 1.0 : 0.0) : A[a * nf + b];
+    if (!held[a]) M[a * nf + a] += lambda > 0.0 ? lambda * fmax(A[a * nf + a], dfloor) : dfloor;
+    r[a] = held[a] ? 0.0 : g[a];
+  }
+}
+
+/* Gauss-Newton decrement g^T A^-1 g over the parameters not held: the chi^2
+ * reduction a full Gauss-Newton step predicts from the current point (A
+ * regularised by 1e-12 max(diag A) on the diagonal).  Negative when A cannot
+ * be factorised. */
+static double or_gn_decrement(const double *A, const double *g, int nf, const int *held) {
+  double M[OR_MAX_SLOTS * OR_MAX_SLOTS], r[OR_MAX_SLOTS], x[OR_MAX_SLOTS];
+  or_step_system(A, g, nf, 0.0, held, M, r);
   if (or_cholesky(M, nf) != 0) return -1.0;
-  or_chol_solve(M, nf, g, x);
+  or_chol_solve(M, nf, r, x);
   double s = 0.0;
-  for (int a = 0; a < nf; ++a) s += g[a] * x[a];
+  for (int a = 0; a < nf; ++a) s += r[a] * x[a];
   return s;
 }
 
@@ -551,6 +577,9 @@ static double or_gn_decrement(const double *A, const double *g, int nf) {
  *   2. Damped step: solve (A + lambda diag(A)) delta = g by Cholesky, the
  *      diagonal floored at 1e-12 max(diag A); a failed factorisation
  *      multiplies lambda by lambda_up and retries (SINGULAR past lambda_max).
+ *      A free parameter on a bound with the descent direction g pointing out
+ *      of the box is held (its delta is 0): steps 2, 5 and 7 solve over the
+ *      other parameters (or_held, or_step_system).
  *   3. Trial p' = clamp(from_u(u + delta)); evaluate it (one iteration).
  *   4. The step is "small" when every internal step satisfies
  *      |u'_s - u_s| <= xtol (|u_s| + xtol).  Its predicted decrease is
@@ -613,26 +642,25 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
   double lambda = o->lambda0;
   if (!isfinite(chi2)) status = OR_NONFINITE;
   else if (chi2 == 0.0) status = OR_CONVERGED;
+  int held[OR_MAX_SLOTS];
+  double rhs[OR_MAX_SLOTS];
   if (status == OR_RUNNING) {
-    double gn = or_gn_decrement(A, g, nf);
+    or_held(d, fidx, nf, p, g, held);
+    double gn = or_gn_decrement(A, g, nf, held);
     if (gn >= 0.0 && gn <= o->gtol * chi2) status = OR_CONVERGED;
   }
 
   while (status == OR_RUNNING) {
     if (it >= o->max_iter) { status = OR_MAX_ITER; break; }
-    double dmax = 0.0;
-    for (int a = 0; a < nf; ++a) dmax = fmax(dmax, A[a * nf + a]);
-    double dfloor = 1e-12 * dmax;
+    or_held(d, fidx, nf, p, g, held);
     for (;;) {
-      for (int a = 0; a < nf; ++a)
-        for (int b = 0; b < nf; ++b) M[a * nf + b] = A[a * nf + b];
-      for (int a = 0; a < nf; ++a) M[a * nf + a] += lambda * fmax(A[a * nf + a], dfloor);
+      or_step_system(A, g, nf, lambda, held, M, rhs);
       if (or_cholesky(M, nf) == 0) break;
       lambda *= o->lambda_up;
       if (lambda > o->lambda_max) { status = OR_SINGULAR; break; }
     }
     if (status != OR_RUNNING) break;
-    or_chol_solve(M, nf, g, delta);
+    or_chol_solve(M, nf, rhs, delta);
     memcpy(pt, p, sizeof(double) * d->n_slots);
     for (int a = 0; a < nf; ++a) {
       int s = fidx[a];
@@ -665,7 +693,8 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
       lambda = fmax(lambda * o->lambda_down, o->lambda_min);
       if (act < o->tol || small || chi2 == 0.0) status = OR_CONVERGED;
       if (status == OR_RUNNING) {
-        double gn = or_gn_decrement(A, g, nf);
+        or_held(d, fidx, nf, p, g, held);
+        double gn = or_gn_decrement(A, g, nf, held);
         if (gn >= 0.0 && gn <= o->gtol * chi2) status = OR_CONVERGED;
       }
     } else if (small) {
@@ -677,12 +706,10 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
   }
 
   if (status == OR_CONVERGED && o->polish && it < o->max_iter && chi2 > 0.0) {
-    double dmax = 0.0;
-    for (int a = 0; a < nf; ++a) dmax = fmax(dmax, A[a * nf + a]);
-    for (int a = 0; a < nf * nf; ++a) M[a] = A[a];
-    for (int a = 0; a < nf; ++a) M[a * nf + a] += 1e-12 * dmax;
+    or_held(d, fidx, nf, p, g, held);
+    or_step_system(A, g, nf, 0.0, held, M, rhs);
     if (or_cholesky(M, nf) == 0) {
-      or_chol_solve(M, nf, g, delta);
+      or_chol_solve(M, nf, rhs, delta);
       memcpy(pt, p, sizeof(double) * d->n_slots);
       for (int a = 0; a < nf; ++a) {
         int s = fidx[a];

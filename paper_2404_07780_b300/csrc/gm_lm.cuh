@@ -241,20 +241,46 @@ __device__ inline double predicted_decrease(const double* Ap, const double* g, c
   return s;
 }
 
-// Gauss-Newton decrement g^T A^-1 g (A packed, regularised by 1e-12 max(diag A)
-// on the diagonal): the chi^2 reduction a full Gauss-Newton step predicts.
-// Negative when A cannot be factorised.
-__device__ inline double gn_decrement(const double* Ap, const double* g, int P) {
-  double M[kMaxFree * kMaxFree], x[kMaxFree];
+// Free parameters held at a bound for the next step (bit f): at the lower bound
+// with a gradient that points below it, or at the upper bound with one that points
+// above it (g = J^T W r: chi^2 falls along +g).  Their step is zero, so the step
+// is taken in the feasible subspace.
+__device__ inline unsigned held_at_bound(const DescDev& D, const double* p, const double* g, int P) {
+  unsigned m = 0u;
+  for (int f = 0; f < P; ++f) {
+    const int s = D.free_slot[f];
+    if ((p[s] <= D.lo[s] && g[f] < 0.0) || (p[s] >= D.hi[s] && g[f] > 0.0)) m |= 1u << f;
+  }
+  return m;
+}
+
+// The system of a step: M = A with lam max(A_ff, 1e-12 max diag A) added on the
+// diagonal (lam = 0: 1e-12 max diag A alone), the rows and columns of held
+// parameters replaced by the identity; rhs r = g with zeros at held parameters.
+__device__ inline void step_system(const double* Ap, const double* g, int P, double lam, unsigned held, double* M,
+                                   double* r) {
   double dmax = 0.0;
   for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ap, P, f, f));
-  for (int f = 0; f < P; ++f)
-    for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ap, P, f, h);
-  for (int f = 0; f < P; ++f) M[f * P + f] += 1e-12 * dmax;
+  const double dfloor = 1e-12 * dmax;
+  for (int f = 0; f < P; ++f) {
+    const bool hf = (held >> f) & 1u;
+    for (int h = 0; h < P; ++h)
+      M[f * P + h] = (hf || ((held >> h) & 1u)) ? (f == h ? 1.0 : 0.0) : packed(Ap, P, f, h);
+    if (!hf) M[f * P + f] += lam > 0.0 ? lam * fmax(packed(Ap, P, f, f), dfloor) : dfloor;
+    r[f] = hf ? 0.0 : g[f];
+  }
+}
+
+// Gauss-Newton decrement g^T A^-1 g over the parameters not held (A packed,
+// regularised by 1e-12 max(diag A) on the diagonal): the chi^2 reduction a full
+// Gauss-Newton step predicts.  Negative when A cannot be factorised.
+__device__ inline double gn_decrement(const double* Ap, const double* g, int P, unsigned held) {
+  double M[kMaxFree * kMaxFree], r[kMaxFree], x[kMaxFree];
+  step_system(Ap, g, P, 0.0, held, M, r);
   if (!cholesky(M, P)) return -1.0;
-  chol_solve(M, P, g, x);
+  chol_solve(M, P, r, x);
   double s = 0.0;
-  for (int f = 0; f < P; ++f) s += g[f] * x[f];
+  for (int f = 0; f < P; ++f) s += r[f] * x[f];
   return s;
 }
 
@@ -372,22 +398,19 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
     }
   }
 
+  const unsigned held = held_at_bound(D, pb, gb, P);
   if (st == ST_RUNNING && accepted) {
-    const double gn = gn_decrement(Ab, gb, P);
+    const double gn = gn_decrement(Ab, gb, P, held);
     if (gn >= 0.0 && gn <= O.gtol * S.chi2_b[g]) st = ST_CONVERGED;
   }
   if (st == ST_RUNNING && it >= O.max_iter) st = ST_MAX_ITER;
   if (st == ST_CONVERGED && O.polish && it < O.max_iter && S.chi2_b[g] > 0.0) {
     // final Gauss-Newton step from the best point: delta = A^-1 g with the diagonal
     // floored as in the damped solve, evaluated in the next pass
-    double M[kMaxFree * kMaxFree], delta[kMaxFree];
-    double dmax = 0.0;
-    for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ab, P, f, f));
-    for (int f = 0; f < P; ++f)
-      for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
-    for (int f = 0; f < P; ++f) M[f * P + f] += 1e-12 * dmax;
+    double M[kMaxFree * kMaxFree], r[kMaxFree], delta[kMaxFree];
+    step_system(Ab, gb, P, 0.0, held, M, r);
     if (cholesky(M, P)) {
-      chol_solve(M, P, gb, delta);
+      chol_solve(M, P, r, delta);
       for (int s = 0; s < NS; ++s) pt[s] = pb[s];
       for (int f = 0; f < P; ++f) {
         const int s = D.free_slot[f];
@@ -401,14 +424,9 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
     }
   }
   if (st == ST_RUNNING) {
-    double M[kMaxFree * kMaxFree], delta[kMaxFree];
-    double dmax = 0.0;
-    for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ab, P, f, f));
-    const double dfloor = 1e-12 * dmax;
+    double M[kMaxFree * kMaxFree], r[kMaxFree], delta[kMaxFree];
     for (;;) {
-      for (int f = 0; f < P; ++f)
-        for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
-      for (int f = 0; f < P; ++f) M[f * P + f] += lam * fmax(packed(Ab, P, f, f), dfloor);
+      step_system(Ab, gb, P, lam, held, M, r);
       if (cholesky(M, P)) break;
       lam *= O.lambda_up;
       if (lam > O.lambda_max) {
@@ -417,7 +435,7 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
       }
     }
     if (st == ST_RUNNING) {
-      chol_solve(M, P, gb, delta);
+      chol_solve(M, P, r, delta);
       for (int s = 0; s < NS; ++s) pt[s] = pb[s];
       for (int f = 0; f < P; ++f) {
         const int s = D.free_slot[f];
