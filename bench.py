@@ -181,7 +181,7 @@ def inbounds_taps(H, W, K):
 # CPU oracle timing (the cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_fit(b: synth.Batch, idx, keep=None):
+def oracle_sample_fit(b: synth.Batch, idx, keep=None, max_iter=None):
     """Render galaxies idx of the workload with the oracle and fit them with its LM; returns (converged, seconds).
     With keep (a dict), also stores the float32 inputs, the start and the oracle's result there."""
     import oracle
@@ -195,7 +195,7 @@ def oracle_sample_fit(b: synth.Batch, idx, keep=None):
     D = D.astype(np.float32).astype(np.float64)
     S = S.astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
-    r = oracle.fit(sub.spec, sub.init, psf, D, S, sub.mask, oracle.FitOptions(tol=TOL, max_iter=MAX_ITER))
+    r = oracle.fit(sub.spec, sub.init, psf, D, S, sub.mask, oracle.FitOptions(tol=TOL, max_iter=max_iter or MAX_ITER))
     dt = time.perf_counter() - t0
     if keep is not None:
         keep.update(spec=sub.spec, init=sub.init, psf=psf.astype(np.float32), image=D.astype(np.float32),
@@ -203,7 +203,7 @@ def oracle_sample_fit(b: synth.Batch, idx, keep=None):
     return int((r["status"] == 1).sum()), dt
 
 
-def oracle_match(keep, device) -> dict:
+def oracle_match(keep, device, max_iter=None) -> dict:
     """The GPU fit of the galaxies the oracle fitted (same float32 inputs, start and options) against the
     oracle's: the fraction that ends with the oracle's status and, when converged, at its minimum (chi^2
     within 1e-5 relative and every parameter within 1e-4 max(|p|, s_p), s_p = 1 px / 1 rad / 1 sky
@@ -213,7 +213,7 @@ def oracle_match(keep, device) -> dict:
     spec, ref = keep["spec"], keep["ref"]
     t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)
     got = gm.gm_fit_batch(spec, t(keep["init"]), t(keep["image"]), t(keep["sigma"]), t(keep["mask"]),
-                          t(keep["psf"]), gm.FitOptions(tol=TOL, max_iter=MAX_ITER))
+                          t(keep["psf"]), gm.FitOptions(tol=TOL, max_iter=max_iter or MAX_ITER))
     got = {k: v.cpu().numpy() for k, v in got.items()}
     scale = np.array([1.0 if n.split(".")[-1] in ("x0", "y0", "pa", "Isky") else 0.0 for n in spec.names])
     bar = 1e-4 * np.maximum(np.abs(ref["params"]), scale)
@@ -235,7 +235,8 @@ def oracle_match(keep, device) -> dict:
             "gpu_chi2_higher_by_sigma_frac": float((got["chi2"] - ref["chi2"] > sd).mean()),
             "gpu_chi2_lower_by_sigma_frac": float((ref["chi2"] - got["chi2"] > sd).mean()),
             "worst_param_over_bar": float(np.max(diff[conv] / bar[conv])) if conv.any() else None,
-            "options": f"tol {TOL:g}, max_iter {MAX_ITER}, same start (the default start) and float32 inputs"}
+            "options": f"tol {TOL:g}, max_iter {max_iter or MAX_ITER}, same start (the default start) and float32 "
+                       "inputs"}
 
 
 def cpu_cores() -> int:
@@ -593,6 +594,132 @@ def run_uneven(args, world, rank, local):
 
 
 # ---------------------------------------------------------------------------
+# small workload: the plain single-Sersic batch, launch-latency bound
+# ---------------------------------------------------------------------------
+
+SMALL_MAX_ITER = 100
+
+
+def run_small(args, world, rank, local):
+    """16 x 64x64 single-Sersic+sky fits with a 15x15 Gaussian PSF (FWHM 1.5 px), no mask, LM from the
+    default start, max_iter 100: one gm_fit_batch call per step.  At this size a pass is a few tiles,
+    so the time per LM iteration (the three kernels of a pass and the host poll) is what is reported."""
+    import torch
+    from paper_2404_07780_b300 import gm
+    from paper_2404_07780_b300.build import build_lib
+
+    build_lib()
+    gm.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    G = args.galaxies
+    b = synth.draw_small(seed=rank_seed(rank), G=G)
+    image, sigma, mask, psf = render_workload(b, dev)
+    p0 = torch.from_numpy(b.init).to(dev)
+    fitter = gm.Fitter(b.spec, G, b.H, b.W, b.K, device=dev)
+    opts = gm.FitOptions(tol=TOL, max_iter=SMALL_MAX_ITER)
+    params = torch.empty_like(p0)
+
+    def step():
+        params.copy_(p0)
+        return fitter.fit(params, image, sigma, mask, psf, opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        step()
+        stats.append(gm.gm_fit_last_stats())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    passes = sum(st["passes"] for st in stats)
+    converged = sum(st["converged"] for st in stats)
+    fused_ms = sum(st["fused_ms"] for st in stats)
+    profile_ms = sum(st["profile_ms"] for st in stats)
+    step_ms = sum(st["step_ms"] for st in stats)
+    evals = sum(st["galaxy_evals"] for st in stats)
+    ms_max = reduce_max(ms, world, dev)
+    value = reduce_sum(converged, world, dev) / (ms_max / 1e3)
+    iters = fitter.iters.cpu().numpy().astype(np.float64)
+    taps = inbounds_taps(b.H, b.W, b.K)
+    achieved = 2.0 * 8 * taps * evals / (fused_ms / 1e3) / 1e12
+
+    # end to end through the public API from pinned host buffers
+    hosts = [t.cpu().pin_memory() for t in (image, sigma, psf, p0)]
+    h_out = [torch.empty_like(fitter.status, device="cpu").pin_memory(),
+             torch.empty_like(fitter.chi2, device="cpu").pin_memory(), torch.empty_like(p0, device="cpu").pin_memory()]
+    h2d = sum(t.numel() * t.element_size() for t in hosts)
+    d2h = sum(t.numel() * t.element_size() for t in h_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_conv = 0
+    for _ in range(args.steps):
+        d_img, d_sig, d_psf, d_p = (h.to(dev, non_blocking=True) for h in hosts)
+        out = fitter.fit(d_p, d_img, d_sig, None, d_psf, opts)
+        h_out[0].copy_(out["status"], non_blocking=True)
+        h_out[1].copy_(out["chi2"], non_blocking=True)
+        h_out[2].copy_(out["params"], non_blocking=True)
+        stream.synchronize()
+        e_conv += int((h_out[0] == gm.ST_CONVERGED).sum().item())
+    e_secs = reduce_max(time.perf_counter() - t0, world, dev)
+    e_value = reduce_sum(e_conv, world, dev) / e_secs
+
+    cpu = None
+    match = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = oracle.max_threads()
+        keep = {}
+        c, dt = oracle_sample_fit(b, np.arange(G), keep, max_iter=SMALL_MAX_ITER)
+        cpu = {"value": c / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"the whole workload ({G} galaxies, seed {rank_seed(0)}), rendered and fitted by the FP64 "
+                         f"oracle, default start, tol {TOL:g}, max_iter {SMALL_MAX_ITER}",
+               "us_per_iteration": 1e6 * dt / max(int(keep["ref"]["iters"].max()), 1)}
+        match = oracle_match(keep, dev, max_iter=SMALL_MAX_ITER)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"plain single-Sersic+sky fit, {G} x {b.H}x{b.W} float32 stamps, Gaussian PSF "
+                                       f"FWHM 1.5 px on {b.K}x{b.K}, no mask, default-start LM to dchi2/chi2<{TOL:g}",
+                           "galaxies": G, "stamp": [b.H, b.W], "psf": [b.K, b.K], "free_params": 8, "tol": TOL,
+                           "max_iter": SMALL_MAX_ITER, "l2": "inputs 0.5 MB, resident in L2 (a latency-bound case)"},
+                "us_per_iteration": 1e3 * ms_max / max(passes, 1),
+                "us_per_iteration_kernels": {"k_planes": 1e3 * profile_ms / max(passes, 1),
+                                             "k_fused": 1e3 * fused_ms / max(passes, 1),
+                                             "k_lm_step": 1e3 * step_ms / max(passes, 1)},
+                "passes_per_fit": passes / args.steps,
+                "converged_frac": converged / (G * args.steps), "mean_iters": float(iters.mean()),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                             "kernel": fused_name(8, gm.gm_tune_last_shape()) + " (a few tiles per launch: latency)",
+                             "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 FLOP x 2032 MHz"},
+                "cpu_baseline": cpu, "oracle_match": match,
+                "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": sum(4 + 3 * st["passes"] for st in stats), "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # learned-initialiser workload
 # ---------------------------------------------------------------------------
 
@@ -869,12 +996,13 @@ def main():
     ap.add_argument("--train-samples", type=int, default=1 << 20, help="learned workload: training stamps")
     ap.add_argument("--adam-iters", type=int, default=1000, help="gradient workload: Adam steps (the paper's 1,000)")
     ap.add_argument("--epochs", type=int, default=1, help="learned workload: training epochs")
-    ap.add_argument("--workload", default="fit", choices=["fit", "uneven", "gradient", "learned"],
+    ap.add_argument("--workload", default="fit", choices=["fit", "uneven", "gradient", "learned", "small"],
                     help="fit: the LM fit of the SDSS-shaped batch (default); uneven: bulge+disk fits on stamps and "
-                         "PSFs of mixed size; gradient: adjoint chi^2 gradient")
+                         "PSFs of mixed size; gradient: adjoint chi^2 gradient; learned: the CNN start; small: 16 "
+                         "stamps of 64x64 (time per LM iteration)")
     args = ap.parse_args()
     if args.galaxies is None:
-        args.galaxies = {"uneven": 32768, "learned": 65536}.get(args.workload, 8192)
+        args.galaxies = {"uneven": 32768, "learned": 65536, "small": 16}.get(args.workload, 8192)
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
@@ -884,6 +1012,8 @@ def main():
         return run_uneven(args, world, rank, local)
     if args.workload == "learned":
         return run_learned(args, world, rank, local)
+    if args.workload == "small":
+        return run_small(args, world, rank, local)
     return run_gpu(args, world, rank, local)
 
 

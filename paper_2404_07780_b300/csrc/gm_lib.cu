@@ -1195,7 +1195,8 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
     kf<<<grid, sm.threads, sm.total, cap>>>(Au);
     GM_LAUNCHED("k_fused(normal)");
     GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 2], cap, cudaEventRecordExternal));
-    k_lm_step<<<(G + kLmBlock - 1) / kLmBlock, kLmBlock, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst, scale);
+    k_lm_step<<<(G + kLmGals - 1) / kLmGals, 32 * kLmGals, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst,
+                                                                       scale);
     GM_LAUNCHED("k_lm_step");
     GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 3], cap, cudaEventRecordExternal));
   }

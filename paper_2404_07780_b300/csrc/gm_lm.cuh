@@ -229,62 +229,124 @@ __device__ inline double packed(const double* Ap, int P, int f, int h) {
   return Ap[f * P - (f * (f - 1)) / 2 + (h - f)];
 }
 
-// chi^2 decrease that the quadratic model chi^2(u + delta) = chi^2 - 2 g^T delta +
-// delta^T A delta predicts for the step delta (A packed).
-__device__ inline double predicted_decrease(const double* Ap, const double* g, const double* delta, int P) {
-  double s = 0.0;
-  for (int f = 0; f < P; ++f) {
-    double ad = 0.0;
-    for (int h = 0; h < P; ++h) ad += packed(Ap, P, f, h) * delta[h];
-    s += delta[f] * (2.0 * g[f] - ad);
-  }
-  return s;
+#ifdef GM_HOST_TU
+// ---------------------------------------------------------------------------
+// Warp-cooperative pieces of the LM step (one warp per galaxy).  Matrices are
+// P x P row-major in shared memory; lane f owns row / parameter f (P <= 16).
+// ---------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
 }
 
-// Free parameters held at a bound for the next step (bit f): at the lower bound
-// with a gradient that points below it, or at the upper bound with one that points
-// above it (g = J^T W r: chi^2 falls along +g).  Their step is zero, so the step
-// is taken in the feasible subspace.
-__device__ inline unsigned held_at_bound(const DescDev& D, const double* p, const double* g, int P) {
-  unsigned m = 0u;
-  for (int f = 0; f < P; ++f) {
-    const int s = D.free_slot[f];
-    if ((p[s] <= D.lo[s] && g[f] < 0.0) || (p[s] >= D.hi[s] && g[f] > 0.0)) m |= 1u << f;
+// In-place Cholesky (lower triangle) of M, column by column: lanes i >= j form
+// their entry of column j at once.  Each entry is computed with the same
+// operations in the same order as cholesky().  false (on every lane) if M is not
+// positive definite.
+__device__ inline bool warp_cholesky(double* M, int P, int lane) {
+  for (int j = 0; j < P; ++j) {
+    double t = 0.0;
+    if (lane >= j && lane < P) {
+      t = M[lane * P + j];
+      for (int k = 0; k < j; ++k) t -= M[lane * P + k] * M[j * P + k];
+    }
+    const double d = __shfl_sync(kFull, t, j);
+    if (!(d > 0.0)) return false;
+    const double l = sqrt(d);
+    if (lane == j) M[j * P + j] = l;
+    else if (lane > j && lane < P) M[lane * P + j] = t / l;
+    __syncwarp();
   }
-  return m;
+  return true;
 }
 
-// The system of a step: M = A with lam max(A_ff, 1e-12 max diag A) added on the
-// diagonal (lam = 0: 1e-12 max diag A alone), the rows and columns of held
-// parameters replaced by the identity; rhs r = g with zeros at held parameters.
-__device__ inline void step_system(const double* Ap, const double* g, int P, double lam, unsigned held, double* M,
-                                   double* r) {
+// Solve L L^T x = b (L from warp_cholesky); b and x are lane-owned (entry f on
+// lane f); returns x on every lane f < P.
+__device__ inline double warp_chol_solve(const double* L, int P, int lane, double b) {
+  double r = b, y = 0.0;
+  for (int i = 0; i < P; ++i) {  // forward: y_i = (b_i - sum_{k<i} L_ik y_k) / L_ii
+    const double yi = __shfl_sync(kFull, r, i) / L[i * P + i];
+    if (lane == i) y = yi;
+    if (lane > i && lane < P) r -= L[lane * P + i] * yi;
+  }
+  r = y;
+  double x = 0.0;
+  for (int i = P - 1; i >= 0; --i) {  // back: x_i = (y_i - sum_{k>i} L_ki x_k) / L_ii
+    const double xi = __shfl_sync(kFull, r, i) / L[i * P + i];
+    if (lane == i) x = xi;
+    if (lane < i) r -= L[i * P + lane] * xi;
+  }
+  return x;
+}
+
+// The system of a step, lane f writing row f of M and returning r_f: M = A with
+// lam max(A_ff, 1e-12 max diag A) added on the diagonal (lam = 0: 1e-12 max diag
+// A alone), the rows and columns of held parameters (bits of `held`) replaced by
+// the identity; r = g with zeros at held parameters.
+__device__ inline double warp_step_system(const double* Ap, const double* g, int P, double lam, unsigned held,
+                                          double* M, int lane) {
   double dmax = 0.0;
   for (int f = 0; f < P; ++f) dmax = fmax(dmax, packed(Ap, P, f, f));
   const double dfloor = 1e-12 * dmax;
-  for (int f = 0; f < P; ++f) {
+  double r = 0.0;
+  if (lane < P) {
+    const int f = lane;
     const bool hf = (held >> f) & 1u;
     for (int h = 0; h < P; ++h)
       M[f * P + h] = (hf || ((held >> h) & 1u)) ? (f == h ? 1.0 : 0.0) : packed(Ap, P, f, h);
     if (!hf) M[f * P + f] += lam > 0.0 ? lam * fmax(packed(Ap, P, f, f), dfloor) : dfloor;
-    r[f] = hf ? 0.0 : g[f];
+    r = hf ? 0.0 : g[f];
   }
+  __syncwarp();
+  return r;
 }
 
-// Gauss-Newton decrement g^T A^-1 g over the parameters not held (A packed,
-// regularised by 1e-12 max(diag A) on the diagonal): the chi^2 reduction a full
-// Gauss-Newton step predicts.  Negative when A cannot be factorised.
-__device__ inline double gn_decrement(const double* Ap, const double* g, int P, unsigned held) {
-  double M[kMaxFree * kMaxFree], r[kMaxFree], x[kMaxFree];
-  step_system(Ap, g, P, 0.0, held, M, r);
-  if (!cholesky(M, P)) return -1.0;
-  chol_solve(M, P, r, x);
-  double s = 0.0;
-  for (int f = 0; f < P; ++f) s += r[f] * x[f];
-  return s;
+// setup_galaxy() by the lanes: lane c sets up component c, lanes s the slot scales.
+__device__ inline void warp_setup_galaxy(const DescDev& D, const double* p, int H, int W, float* cc, float* scale,
+                                         int lane) {
+  if (lane < D.n_comp) {
+    double par[8];
+    for (int k = 0; k < D.np[lane]; ++k) par[k] = p[D.slot[lane][k]];
+    setup_component(D.kind[lane], par, H, W, D.mag[lane], D.mag_zero[lane], D.box[lane], cc + lane * kCC);
+  }
+  for (int s = lane; s < D.n_slots; s += 32) scale[s] = D.is_log[s] ? (float)p[s] : 1.f;
 }
 
-#ifdef GM_HOST_TU
+// queue_galaxy() by the lanes: lane 0 takes the list and item positions, every lane writes items.
+__device__ inline void warp_queue_galaxy(const LMState& S, int l, int g, const GalGeom& geo, int lane) {
+  const int nt = geo.n_tiles;
+  int ipos = 0;
+  if (lane == 0) {
+    const int pos = atomicAdd(S.count[l], 1);
+    S.list[l][pos] = g;
+    ipos = atomicAdd(S.icount[l], nt);
+  }
+  ipos = __shfl_sync(kFull, ipos, 0);
+  for (int t = lane; t < nt; t += 32) S.items[l][ipos + t] = make_int2(g, t);
+}
+
+// pt = clamp(from_u(to_u(pb) + delta)) by the lanes (delta lane-owned), with the
+// galaxy's constants for it; returns whether the clamp moved a slot.
+__device__ inline bool warp_trial_point(const DescDev& D, const double* pb, double* pt, double delta, int lane) {
+  const int NS = D.n_slots, P = D.P;
+  for (int s = lane; s < NS; s += 32) pt[s] = pb[s];
+  __syncwarp();
+  if (lane < P) {
+    const int s = D.free_slot[lane];
+    pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta);
+  }
+  __syncwarp();
+  bool out = false;
+  for (int s = lane; s < NS; s += 32) {
+    out = out || pt[s] < D.lo[s] || pt[s] > D.hi[s];
+    pt[s] = fmin(fmax(pt[s], D.lo[s]), D.hi[s]);
+  }
+  __syncwarp();
+  return __any_sync(kFull, out);
+}
+
 // One LM step for every galaxy evaluated in this iteration (list `cur`):
 // sum the tile partials of the pass, accept or reject the evaluated point,
 // test convergence, solve the damped normal equations for the next trial point
@@ -296,97 +358,106 @@ __device__ inline double gn_decrement(const double* Ap, const double* g, int P, 
 // accepted step lowers chi^2 by less than tol relative, any evaluated step
 // is below xtol, or the Gauss-Newton decrement at the best point is at most
 // gtol chi^2; STALLED / SINGULAR past lambda_max; MAX_ITER at max_iter.
+// Free parameters on a bound whose descent direction leaves the box are held
+// (zero step) in the damped solve, the decrement and the final step.
 // With O.polish, a galaxy that reaches CONVERGED before max_iter queues one
 // undamped Gauss-Newton step from its best point instead of stopping; the
 // next step call adopts that point unless its chi^2 is non-finite or above
 // the best by more than kPolishSlack relative (FP32-accumulated chi^2 cannot
 // resolve the last decreases towards the minimum; the gradient can).
-// One thread per active galaxy, 32 galaxies per block.  The block first sums
-// its galaxies' tile partials together, the lanes taking (galaxy, entry) pairs in
-// turn so that neighbouring lanes read neighbouring entries, each entry over
-// its galaxy's tiles in tile order (deterministic), into shared memory; then
-// every thread takes its galaxy's LM step in FP64.
+// One warp per active galaxy, kLmGals galaxies per block: the lanes sum the
+// tile partials (entry e over the galaxy's tiles in tile order: deterministic),
+// form the Cholesky factor a column at a time, and split the per-parameter,
+// per-component and per-tile work; the scalar decisions are taken alike by
+// every lane.
 constexpr int kLmWarps = 4;   // warps per block of k_chi2_grad_finish (one galaxy per warp)
-constexpr int kLmBlock = 32;  // galaxies (threads) per block of k_lm_step
+constexpr int kLmGals = 4;    // galaxies (warps) per block of k_lm_step
 
-__global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O,
-                                                      int cur, const GalGeom* __restrict__ geo,
-                                                      const double* __restrict__ partial, float* cconst,
-                                                      float* scale) {
-  __shared__ double s_acc[kLmBlock][kMaxAcc];
-  const int lane = threadIdx.x;
-  const int gi0 = blockIdx.x * kLmBlock, gi = gi0 + lane;
+__global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant__ DescDev D, LMState S, LMOpts O,
+                                                         int cur, const GalGeom* __restrict__ geo,
+                                                         const double* __restrict__ partial, float* cconst,
+                                                         float* scale) {
+  __shared__ double s_acc[kLmGals][kMaxAcc];
+  __shared__ double s_M[kLmGals][kMaxFree * kMaxFree];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int gi = blockIdx.x * kLmGals + wl;
   const int n_cur = *S.count[cur];
-  if (gi == 0) atomicAdd(S.evals, (unsigned long long)n_cur);
-  const int nb = min(kLmBlock, n_cur - gi0);  // galaxies of this block (the same for every lane)
-  if (nb <= 0) return;
+  if (gi == 0 && lane == 0) atomicAdd(S.evals, (unsigned long long)n_cur);
+  if (gi >= n_cur) return;
   const int NS = D.n_slots, P = D.P, NAp = P * (P + 1) / 2, NA = 1 + P + NAp;
-  for (int x = lane; x < nb * NA; x += kLmBlock) {
-    const int q = x / NA, e = x - q * NA;
-    const int gq = S.list[cur][gi0 + q];
-    const int n_tiles = geo[gq].n_tiles;
-    const double* pp = partial + (size_t)geo[gq].tile0 * NA + e;
-    double a = 0.0;
-    for (int t = 0; t < n_tiles; ++t) a += pp[(size_t)t * NA];
-    s_acc[q][e] = a;
+  const int g = S.list[cur][gi];
+  double* acc = s_acc[wl];
+  double* M = s_M[wl];
+  {
+    const int n_tiles = geo[g].n_tiles;
+    const double* pp = partial + (size_t)geo[g].tile0 * NA;
+    for (int e = lane; e < NA; e += 32) {
+      double a = 0.0;
+      for (int t = 0; t < n_tiles; ++t) a += pp[(size_t)t * NA + e];
+      acc[e] = a;
+    }
   }
   __syncwarp();
-  if (gi >= n_cur) return;
-  const int g = S.list[cur][gi];
-  const double* acc = s_acc[lane];
 
   double* pb = S.p_b + (size_t)g * NS;
   double* pt = S.p_t + (size_t)g * NS;
   double* Ab = S.A_b + (size_t)g * NAp;
   double* gb = S.g_b + (size_t)g * P;
   const double chi2_t = acc[0];
+  float* ccg = cconst + (size_t)g * D.n_comp * kCC;
+  float* scg = scale + (size_t)g * scale_stride(NS);
+
+  // adopt the evaluated point and its normal equations as the best
+  auto adopt = [&]() {
+    for (int s = lane; s < NS; s += 32) pb[s] = pt[s];
+    for (int f = lane; f < P; f += 32) gb[f] = acc[1 + f];
+    for (int e = lane; e < NAp; e += 32) Ab[e] = acc[1 + P + e];
+  };
 
   int st = ST_RUNNING;
   const int it = S.it[g] + 1;
-  S.it[g] = it;
   double lam = S.lam[g];
+  const double chi2_b = S.chi2_b[g];
+  const int status_in = S.status[g];
+  __syncwarp();
+  if (lane == 0) S.it[g] = it;
   bool accepted = false;
-  if (S.status[g] == ST_POLISH) {
+  if (status_in == ST_POLISH) {
     // the final Gauss-Newton step's point, evaluated: it becomes the result unless
     // its chi^2 is non-finite or above the best by more than the slack
-    const double chi2_b = S.chi2_b[g];
     if (isfinite(chi2_t) && chi2_t <= chi2_b * (1.0 + kPolishSlack)) {
-      for (int s = 0; s < NS; ++s) pb[s] = pt[s];
-      for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
-      for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
-      S.chi2_b[g] = chi2_t;
+      adopt();
+      if (lane == 0) S.chi2_b[g] = chi2_t;
     }
-    S.status[g] = ST_CONVERGED;
+    if (lane == 0) S.status[g] = ST_CONVERGED;
     return;
   }
   if (it == 1) {
     if (!isfinite(chi2_t)) {
       st = ST_NONFINITE;
     } else {
-      for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
-      for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
-      S.chi2_b[g] = chi2_t;
+      adopt();
+      if (lane == 0) S.chi2_b[g] = chi2_t;
       accepted = true;
       if (chi2_t == 0.0) st = ST_CONVERGED;
     }
   } else {
-    bool small = true;
-    for (int f = 0; f < P; ++f) {
-      const int s = D.free_slot[f];
+    bool big = false;
+    if (lane < P) {
+      const int s = D.free_slot[lane];
       const double u0 = to_u(D, s, pb[s]), u1 = to_u(D, s, pt[s]);
-      if (fabs(u1 - u0) > O.xtol * (fabs(u0) + O.xtol)) small = false;
+      big = fabs(u1 - u0) > O.xtol * (fabs(u0) + O.xtol);
     }
-    const double chi2_b = S.chi2_b[g];
+    const bool small = !__any_sync(kFull, big);
     // a step whose predicted decrease is below the resolution of chi^2 is accepted unless
     // chi^2 rose by more than that resolution, and its decrease is the predicted one
     const double pred = S.pred[g];
     const bool resolved = pred >= kChi2Res * chi2_b;
     if (isfinite(chi2_t) && (chi2_t < chi2_b || (!resolved && chi2_t <= chi2_b * (1.0 + kChi2Res)))) {
       const double act = resolved ? (chi2_b - chi2_t) / chi2_b : fmax(pred, 0.0) / chi2_b;
-      for (int s = 0; s < NS; ++s) pb[s] = pt[s];
-      for (int f = 0; f < P; ++f) gb[f] = acc[1 + f];
-      for (int e = 0; e < NAp; ++e) Ab[e] = acc[1 + P + e];
-      S.chi2_b[g] = chi2_t;
+      __syncwarp();
+      adopt();
+      if (lane == 0) S.chi2_b[g] = chi2_t;
       lam = fmax(lam * O.lambda_down, O.lambda_min);
       accepted = true;
       if (act < O.tol || small || chi2_t == 0.0) st = ST_CONVERGED;
@@ -397,37 +468,45 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
       if (lam > O.lambda_max) st = ST_STALLED;
     }
   }
+  __syncwarp();
+  const double chi2_best = accepted ? chi2_t : chi2_b;
 
-  const unsigned held = held_at_bound(D, pb, gb, P);
+  // parameters held at a bound for the next step (bit f), from the best point
+  bool hb = false;
+  if (lane < P) {
+    const int s = D.free_slot[lane];
+    hb = (pb[s] <= D.lo[s] && gb[lane] < 0.0) || (pb[s] >= D.hi[s] && gb[lane] > 0.0);
+  }
+  const unsigned held = __ballot_sync(kFull, hb) & ((1u << P) - 1u);
+  const double gf = lane < P ? gb[lane] : 0.0;
+
   if (st == ST_RUNNING && accepted) {
-    const double gn = gn_decrement(Ab, gb, P, held);
-    if (gn >= 0.0 && gn <= O.gtol * S.chi2_b[g]) st = ST_CONVERGED;
+    // Gauss-Newton decrement g^T A^-1 g over the parameters not held
+    const double r = warp_step_system(Ab, gb, P, 0.0, held, M, lane);
+    if (warp_cholesky(M, P, lane)) {
+      const double x = warp_chol_solve(M, P, lane, r);
+      const double gn = warp_sum(lane < P ? r * x : 0.0);
+      if (gn >= 0.0 && gn <= O.gtol * chi2_best) st = ST_CONVERGED;
+    }
   }
   if (st == ST_RUNNING && it >= O.max_iter) st = ST_MAX_ITER;
-  if (st == ST_CONVERGED && O.polish && it < O.max_iter && S.chi2_b[g] > 0.0) {
+  if (st == ST_CONVERGED && O.polish && it < O.max_iter && chi2_best > 0.0) {
     // final Gauss-Newton step from the best point: delta = A^-1 g with the diagonal
     // floored as in the damped solve, evaluated in the next pass
-    double M[kMaxFree * kMaxFree], r[kMaxFree], delta[kMaxFree];
-    step_system(Ab, gb, P, 0.0, held, M, r);
-    if (cholesky(M, P)) {
-      chol_solve(M, P, r, delta);
-      for (int s = 0; s < NS; ++s) pt[s] = pb[s];
-      for (int f = 0; f < P; ++f) {
-        const int s = D.free_slot[f];
-        pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
-      }
-      clamp_slots(D, pt);
-      setup_galaxy(D, pt, geo[g].H, geo[g].W, 1, cconst + (size_t)g * D.n_comp * kCC,
-                   scale + (size_t)g * scale_stride(NS));
-      queue_galaxy(S, cur ^ 1, g, geo[g]);
+    const double r = warp_step_system(Ab, gb, P, 0.0, held, M, lane);
+    if (warp_cholesky(M, P, lane)) {
+      const double delta = warp_chol_solve(M, P, lane, r);
+      warp_trial_point(D, pb, pt, delta, lane);
+      warp_setup_galaxy(D, pt, geo[g].H, geo[g].W, ccg, scg, lane);
+      warp_queue_galaxy(S, cur ^ 1, g, geo[g], lane);
       st = ST_POLISH;
     }
   }
   if (st == ST_RUNNING) {
-    double M[kMaxFree * kMaxFree], r[kMaxFree], delta[kMaxFree];
+    double r = 0.0;
     for (;;) {
-      step_system(Ab, gb, P, lam, held, M, r);
-      if (cholesky(M, P)) break;
+      r = warp_step_system(Ab, gb, P, lam, held, M, lane);
+      if (warp_cholesky(M, P, lane)) break;
       lam *= O.lambda_up;
       if (lam > O.lambda_max) {
         st = ST_SINGULAR;
@@ -435,23 +514,24 @@ __global__ void __launch_bounds__(kLmBlock) k_lm_step(const __grid_constant__ De
       }
     }
     if (st == ST_RUNNING) {
-      chol_solve(M, P, r, delta);
-      for (int s = 0; s < NS; ++s) pt[s] = pb[s];
-      for (int f = 0; f < P; ++f) {
-        const int s = D.free_slot[f];
-        pt[s] = from_u(D, s, to_u(D, s, pb[s]) + delta[f]);
+      const double delta = warp_chol_solve(M, P, lane, r);
+      // predicted decrease 2 g^T delta - delta^T A delta (every lane's delta_h by shuffles)
+      double ad = 0.0;
+      for (int h = 0; h < P; ++h) {
+        const double dh = __shfl_sync(kFull, delta, h);
+        if (lane < P) ad += packed(Ab, P, lane, h) * dh;
       }
-      S.pred[g] = predicted_decrease(Ab, gb, delta, P);
-      for (int s = 0; s < NS; ++s)
-        if (pt[s] < D.lo[s] || pt[s] > D.hi[s]) S.pred[g] = CUDART_INF;  // clamped: judged by chi^2
-      clamp_slots(D, pt);
-      setup_galaxy(D, pt, geo[g].H, geo[g].W, 1, cconst + (size_t)g * D.n_comp * kCC,
-                   scale + (size_t)g * scale_stride(NS));
-      queue_galaxy(S, cur ^ 1, g, geo[g]);
+      double pred = warp_sum(lane < P ? delta * (2.0 * gf - ad) : 0.0);
+      if (warp_trial_point(D, pb, pt, delta, lane)) pred = CUDART_INF;  // clamped: judged by chi^2
+      if (lane == 0) S.pred[g] = pred;
+      warp_setup_galaxy(D, pt, geo[g].H, geo[g].W, ccg, scg, lane);
+      warp_queue_galaxy(S, cur ^ 1, g, geo[g], lane);
     }
   }
-  S.lam[g] = lam;
-  S.status[g] = st;
+  if (lane == 0) {
+    S.lam[g] = lam;
+    S.status[g] = st;
+  }
 }
 #endif  // GM_HOST_TU
 
