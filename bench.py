@@ -43,9 +43,9 @@ PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
 # DRAM bytes (read + write) of the SDSS-shaped fit's fused pass (k_fused<NORMAL, 8, 2, WIDE>, the
 # tuned shape) per galaxy evaluated, from one ncu capture of a 1,024-galaxy pass of this workload
-# (705.6 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
+# (704.8 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
 # this times its galaxies
-FUSED_DRAM_BYTES_PER_GALAXY = 705.632e6 / 1024
+FUSED_DRAM_BYTES_PER_GALAXY = 704.828e6 / 1024
 
 
 def fused_name(P, shape):
