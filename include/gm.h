@@ -186,6 +186,10 @@ typedef struct {
   double lambda_min;   /* ... but not below lambda_min */
   double lambda_max;   /* STALLED / SINGULAR beyond this */
   int32_t polish;      /* 1: a CONVERGED fit takes one final Gauss-Newton step (gm_fit_batch); 0: none */
+  int32_t canonical;   /* 1: at exit q > 1 is rewritten and position angles wrapped (gm_fit_batch);
+                          0: params_out is the best point exactly as the fit holds it (a checkpoint) */
+  double *lambda_inout;  /* NULL, or DEVICE [n_gal] FP64: each galaxy's starting damping (used
+                            instead of lambda0 when > 0 and finite) in, its damping at exit out */
 } gm_fit_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -306,7 +310,8 @@ int gm_test_starve_next_pass(uint32_t polls);
  *                r_c, r_t, fwhm) times q, which leaves the image unchanged,
  *                when those slots are not shared with components of another q
  *   opts         host; NULL = defaults (tol 1e-6, xtol 1e-10, gtol 1e-10, max_iter 100,
- *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10, polish 1)
+ *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10, polish 1, canonical 1,
+ *                lambda_inout NULL)
  *   chi2_out     [n_gal] FP64 chi^2 at the best point
  *   dof_out      [n_gal] int32: used pixels - free parameters (Sec. 5.1)
  *   iters_out    [n_gal] int32: model+Jacobian evaluations spent
@@ -331,6 +336,16 @@ int gm_test_starve_next_pass(uint32_t polls);
  * parameters' 1e-4 relative tolerance.
  * Synchronises `stream` every few iterations to poll how many galaxies are
  * still running; returns when none is or all have spent max_iter.
+ * Checkpoint and resume: a fit stopped at max_iter = k with canonical = 0 and
+ * lambda_inout returns each galaxy's best point and damping as the fit holds
+ * them; calling again from those (same lambda_inout) continues exactly: the
+ * first evaluation reproduces the best point's normal equations bit for bit
+ * (fixed-order sums), so every later step is the one the uninterrupted fit
+ * takes.  For a galaxy still running at k, the resumed call with max_iter
+ * N - k + 1 ends with the uninterrupted N-iteration fit's results, bit for
+ * bit, its iters_out being one more than the remaining evaluations (the
+ * best point is evaluated again).  Galaxies that finished before k are
+ * resumed as new fits: pass only the ones still running.
  */
 size_t gm_fit_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
 

@@ -90,6 +90,8 @@ class _Opts(ctypes.Structure):
         ("lambda_min", ctypes.c_double),
         ("lambda_max", ctypes.c_double),
         ("polish", ctypes.c_int),
+        ("canonical", ctypes.c_int),
+        ("lambda_inout", ctypes.c_void_p),
     ]
 
 
@@ -148,6 +150,7 @@ class FitOptions:
     lambda_min: float = 1e-7
     lambda_max: float = 1e10
     polish: int = 1
+    canonical: int = 1
 
 
 def _desc(spec) -> _Desc:
@@ -284,8 +287,12 @@ def jacobian(spec, params, psf, H: int, W: int, internal: bool = False) -> np.nd
     return out
 
 
-def fit(spec, params0, psf, image, sigma, mask=None, opts: FitOptions | None = None) -> dict:
-    """Levenberg-Marquardt fit of every galaxy; returns a dict of numpy arrays."""
+def fit(spec, params0, psf, image, sigma, mask=None, opts: FitOptions | None = None, lambda_inout=None) -> dict:
+    """Levenberg-Marquardt fit of every galaxy; returns a dict of numpy arrays.
+
+    lambda_inout: None, or a float64 [G] array holding each galaxy's starting damping (used when
+    > 0 and finite), overwritten with its damping at exit (checkpoint and resume, with
+    opts.canonical = 0 for the checkpoint)."""
     opts = opts or FitOptions()
     params = _f64(params0).copy()
     psf = _f64(psf)
@@ -300,8 +307,12 @@ def fit(spec, params0, psf, image, sigma, mask=None, opts: FitOptions | None = N
     status = np.zeros(G, np.int32)
     sigma_p = np.zeros_like(params)
     d = _desc(spec)
+    if lambda_inout is not None:
+        assert isinstance(lambda_inout, np.ndarray) and lambda_inout.dtype == np.float64 and \
+            lambda_inout.shape == (G,) and lambda_inout.flags.c_contiguous
     o = _Opts(opts.tol, opts.xtol, opts.gtol, opts.max_iter, opts.lambda0, opts.lambda_up, opts.lambda_down,
-              opts.lambda_min, opts.lambda_max, opts.polish)
+              opts.lambda_min, opts.lambda_max, opts.polish, opts.canonical,
+              None if lambda_inout is None else lambda_inout.ctypes.data)
     _load().or_fit_batch(ctypes.byref(d), ctypes.byref(o), G, H, W, K, _ptr(params), _ptr(psf),
                          _ptr(image), _ptr(sigma), _ptr(mask), _ptr(chi2_out), _ptr(dof),
                          _ptr(iters), _ptr(status), _ptr(sigma_p))

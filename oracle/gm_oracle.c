@@ -98,6 +98,8 @@ typedef struct {
   int max_iter;      /* model+Jacobian evaluations allowed */
   double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
   int polish;        /* 1: one final Gauss-Newton step after CONVERGED (step 7 of or_fit_one) */
+  int canonical;     /* 1: rewrite q > 1 and wrap position angles at exit; 0: the best point as held */
+  double *lambda_inout; /* NULL, or [G]: each galaxy's starting damping (when > 0, finite) in, its final one out */
 } or_opts;
 
 int or_n_params(int kind) {
@@ -600,14 +602,18 @@ static double or_gn_decrement(const double *A, const double *g, int nf, const in
  *      A floored at 1e-12 max diag A), p' = clamp(from_u(u + delta)), and
  *      evaluates it (one iteration); p' replaces the best point unless its
  *      chi^2 is non-finite or above the best by more than 1e-6 relative.
- * At exit an axis ratio above 1 is rewritten as its reciprocal (or_canonical_q).
+ *   8. The damping starts at *lam_io instead of lambda0 when given (> 0,
+ *      finite), and its final value is written back: with canonical = 0 the
+ *      best point is returned as held, so that a fit stopped at max_iter can
+ *      be resumed (the first evaluation repeats the best point's A, g, chi^2).
+ * At exit (canonical = 1) an axis ratio above 1 is rewritten as its reciprocal (or_canonical_q).
  * The covariance of Sec. 5.2 is taken from A at the best point; for a log
  * slot sigma_p = p sigma_u.  Position angles are wrapped to [0, pi) at exit.
  */
 static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int W,
                        const double *psf, int K, const double *image, const double *sigma,
                        const unsigned char *mask, double *chi2_out, int *dof_out, int *iters_out,
-                       int *status_out, double *sigma_p) {
+                       int *status_out, double *sigma_p, double *lam_io) {
   size_t N = (size_t)H * W;
   int nf = 0, fidx[OR_MAX_SLOTS];
   for (int s = 0; s < d->n_slots; ++s)
@@ -639,7 +645,7 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
   double chi2 = or_normal_eq(d, p, H, W, psf, K, image, sigma, mask, nf, A, g, J, model, work);
   int it = 1;
   int status = OR_RUNNING;
-  double lambda = o->lambda0;
+  double lambda = (lam_io && *lam_io > 0.0 && isfinite(*lam_io)) ? *lam_io : o->lambda0;
   if (!isfinite(chi2)) status = OR_NONFINITE;
   else if (chi2 == 0.0) status = OR_CONVERGED;
   int held[OR_MAX_SLOTS];
@@ -732,7 +738,8 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
   *status_out = status;
   /* canonical axis ratios (q <= 1); the covariance is then taken at the rewritten
    * point from a fresh finite-difference Jacobian */
-  if (status != OR_NONFINITE && or_canonical_q(d, p) > 0)
+  if (lam_io) *lam_io = lambda;
+  if (status != OR_NONFINITE && o->canonical && or_canonical_q(d, p) > 0)
     or_normal_eq(d, p, H, W, psf, K, image, sigma, mask, nf, A, g, J, model, work);
   if (sigma_p && status != OR_NONFINITE) {
     /* covariance: diag of A^-1 column by column through the Cholesky factor */
@@ -753,7 +760,7 @@ static void or_fit_one(const or_desc *d, const or_opts *o, double *p, int H, int
   int is_pa[OR_MAX_SLOTS];
   or_pa_slots(d, is_pa);
   for (int s = 0; s < d->n_slots; ++s)
-    if (is_pa[s]) p[s] -= M_PI * floor(p[s] / M_PI);
+    if (is_pa[s] && o->canonical) p[s] -= M_PI * floor(p[s] / M_PI);
   free(J);
   free(model);
   free(work);
@@ -846,7 +853,8 @@ int or_fit_batch(const or_desc *d, const or_opts *o, int G, int H, int W, int K,
     or_fit_one(d, o, params + (size_t)gi * d->n_slots, H, W, psf + (size_t)gi * K * K, K,
                image + (size_t)gi * N, sigma + (size_t)gi * N, mask ? mask + (size_t)gi * N : NULL,
                chi2 + gi, dof + gi, iters + gi, status + gi,
-               sigma_p ? sigma_p + (size_t)gi * d->n_slots : NULL);
+               sigma_p ? sigma_p + (size_t)gi * d->n_slots : NULL,
+               o->lambda_inout ? o->lambda_inout + gi : NULL);
   }
   return 0;
 }

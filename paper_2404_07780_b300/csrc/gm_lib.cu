@@ -814,6 +814,8 @@ LMOpts lm_opts(const gm_fit_opts* o) {
     L.lambda_min = o->lambda_min;
     L.lambda_max = o->lambda_max;
     L.polish = o->polish;
+    L.canonical = o->canonical;
+    L.lambda_inout = o->lambda_inout;
   } else {
     L.tol = 1e-6;
     L.xtol = 1e-10;
@@ -825,6 +827,8 @@ LMOpts lm_opts(const gm_fit_opts* o) {
     L.lambda_min = 1e-7;
     L.lambda_max = 1e10;
     L.polish = 1;
+    L.canonical = 1;
+    L.lambda_inout = nullptr;
   }
   return L;
 }
@@ -1094,6 +1098,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   const LMOpts O = lm_opts(opts);
   if (O.max_iter < 1) return fail(GM_E_INVAL, "max_iter=%d < 1", O.max_iter);
   if (O.polish != 0 && O.polish != 1) return fail(GM_E_INVAL, "polish=%d must be 0 or 1", O.polish);
+  if (O.canonical != 0 && O.canonical != 1) return fail(GM_E_INVAL, "canonical=%d must be 0 or 1", O.canonical);
   if (!(O.lambda_up > 1.0) || !(O.lambda_down > 0.0) || !(O.lambda_down < 1.0) || !(O.lambda0 > 0.0))
     return fail(GM_E_INVAL, "lambda controls must satisfy lambda0 > 0, up > 1, 0 < down < 1");
   const WsFit w = ws_fit(desc, gp, pl.dd.P);
@@ -1224,8 +1229,8 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
     if (kerr) return fail(GM_E_TIMEOUT, "fused kernel: a tile load did not complete within its wait limit");
     if (remaining == 0) break;
   }
-  k_lm_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, G, params_inout, chi2_out, dof_out, iters_out,
-                                               status_out, sigma_p_out);
+  k_lm_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, G, O.canonical, O.lambda_inout, params_inout, chi2_out,
+                                               dof_out, iters_out, status_out, sigma_p_out);
   GM_LAUNCHED("k_lm_finish");
   unsigned long long counters[3] = {0, 0, 0};
   GM_CUDA(cudaMemcpyAsync(counters, S.evals, sizeof(counters), cudaMemcpyDeviceToHost, st));
@@ -1718,6 +1723,15 @@ int gm_bootstrap(const gm_model_desc* desc, const gm_batch* batch, const double*
   gm_batch rep = *batch;
   rep.sigma = (const float*)(ws + w.sigma_eff);
   rep.mask = (const uint8_t*)(ws + w.mask_eff);
+  // every replicate's refit starts fresh and returns canonical parameters (PA aligned below)
+  gm_fit_opts ropts;
+  const gm_fit_opts* ropts_p = nullptr;
+  if (opts) {
+    ropts = *opts;
+    ropts.canonical = 1;
+    ropts.lambda_inout = nullptr;
+    ropts_p = &ropts;
+  }
   const int ngrid = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, 4096));
   for (int b = 0; b < n_boot; ++b) {
     if ((rc = boot_counts(batch, w, ws, (unsigned long long)seed, b, st))) return rc;
@@ -1725,7 +1739,7 @@ int gm_bootstrap(const gm_model_desc* desc, const gm_batch* batch, const double*
                                           (float*)(ws + w.sigma_eff), (uint8_t*)(ws + w.mask_eff));
     GM_LAUNCHED("k_boot_weights");
     GM_CUDA(cudaMemcpyAsync(pb, params_best, (size_t)G * NS * 8, cudaMemcpyDeviceToDevice, st));
-    if ((rc = gm_fit_batch(desc, &rep, pb, opts, (double*)(ws + w.chi2), (int32_t*)(ws + w.dof),
+    if ((rc = gm_fit_batch(desc, &rep, pb, ropts_p, (double*)(ws + w.chi2), (int32_t*)(ws + w.dof),
                            (int32_t*)(ws + w.iters), (int32_t*)(ws + w.status), nullptr, ws + w.fit, w.fit_bytes,
                            stream)))
       return rc;

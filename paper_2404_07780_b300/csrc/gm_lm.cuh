@@ -57,6 +57,8 @@ struct LMOpts {
   int max_iter;
   double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
   int polish;  // one final Gauss-Newton step after CONVERGED
+  int canonical;         // rewrite q > 1 and wrap position angles at exit
+  double* lambda_inout;  // [G] starting damping in (when > 0 and finite), final damping out; or nullptr
 };
 
 // Per-galaxy LM state, struct of arrays in the caller's workspace.
@@ -173,7 +175,8 @@ __global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O
   clamp_slots(D, pb);
   for (int s = 0; s < NS; ++s) pt[s] = pb[s];
   S.it[g] = 0;
-  S.lam[g] = O.lambda0;
+  const double li = O.lambda_inout ? O.lambda_inout[g] : 0.0;
+  S.lam[g] = (li > 0.0 && isfinite(li)) ? li : O.lambda0;
   S.chi2_b[g] = CUDART_NAN;
   int st = ST_RUNNING;
   if (S.bad[g]) st = ST_BAD_INPUT;
@@ -542,9 +545,9 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
 // and its scale lengths multiplied by q (the same image), and the covariance
 // is carried along: Sigma' = T Sigma T^T with T the Jacobian of the rewrite.
 // Position angles are wrapped to [0, pi).
-__global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G, double* params_out,
-                            double* chi2_out, int* dof_out, int* iters_out, int* status_out,
-                            double* sigma_p_out) {
+__global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G, int canonical,
+                            double* lambda_out, double* params_out, double* chi2_out, int* dof_out,
+                            int* iters_out, int* status_out, double* sigma_p_out) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
   const int NS = D.n_slots, P = D.P;
@@ -555,6 +558,7 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
   dof_out[g] = S.nused[g] - P;
   iters_out[g] = S.it[g];
   status_out[g] = S.status[g];
+  if (lambda_out) lambda_out[g] = S.lam[g];
   const bool evaluated = S.it[g] > 0 && S.status[g] != ST_NONFINITE;
 
   // covariance of the free parameters in physical units at the best point
@@ -585,7 +589,7 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
   }
 
   // canonical axis ratios
-  if (evaluated) {
+  if (evaluated && canonical) {
     int fidx[kMaxSlots];
     for (int s = 0; s < NS; ++s) fidx[s] = -1;
     for (int f = 0; f < P; ++f) fidx[D.free_slot[f]] = f;
@@ -631,7 +635,7 @@ __global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
 
   for (int s = 0; s < NS; ++s) {
     double v = p[s];
-    if (D.is_pa[s]) v -= pi * floor(v / pi);
+    if (D.is_pa[s] && canonical) v -= pi * floor(v / pi);
     params_out[(size_t)g * NS + s] = v;
   }
   if (sigma_p_out) {

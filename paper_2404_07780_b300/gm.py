@@ -84,6 +84,8 @@ class gm_fit_opts(ctypes.Structure):
         ("lambda_min", ctypes.c_double),
         ("lambda_max", ctypes.c_double),
         ("polish", ctypes.c_int32),
+        ("canonical", ctypes.c_int32),
+        ("lambda_inout", ctypes.c_void_p),
     ]
 
 
@@ -122,10 +124,18 @@ class FitOptions:
     lambda_min: float = 1e-7
     lambda_max: float = 1e10
     polish: int = 1
+    canonical: int = 1
+    lambda_inout: object = None  # None, or a float64 CUDA tensor [G]: damping in and out (checkpoint / resume)
 
     def to_c(self) -> gm_fit_opts:
+        li = None if self.lambda_inout is None else ctypes.c_void_p(self.lambda_inout.data_ptr())
+        if self.lambda_inout is not None:
+            import torch
+            t = self.lambda_inout
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise GMError("lambda_inout must be a contiguous float64 CUDA tensor")
         return gm_fit_opts(self.tol, self.xtol, self.gtol, self.max_iter, self.lambda0, self.lambda_up, self.lambda_down,
-                           self.lambda_min, self.lambda_max, self.polish)
+                           self.lambda_min, self.lambda_max, self.polish, self.canonical, li)
 
 
 _lib = None
@@ -514,6 +524,8 @@ class Fitter:
             raise GMError(f"batch shape {shape} != fitter shape {self.shape}")
         if not (params.is_cuda and params.dtype == torch.float64 and params.is_contiguous()):
             raise GMError("params must be a contiguous float64 CUDA tensor")
+        if opts is not None and opts.lambda_inout is not None and opts.lambda_inout.numel() != b.n_gal:
+            raise GMError(f"lambda_inout holds {opts.lambda_inout.numel()} values for {b.n_gal} galaxies")
         o = (opts or FitOptions()).to_c()
         _check(self.lib.gm_fit_batch(ctypes.byref(self.d), ctypes.byref(b), _ptr(params), ctypes.byref(o),
                                      _ptr(self.chi2), _ptr(self.dof), _ptr(self.iters), _ptr(self.status),

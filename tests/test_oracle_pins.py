@@ -779,3 +779,26 @@ def test_boxy_magnitude_flux_by_2d_quadrature(B):
     f = lambda y, x: oracle.component_value("gaussian", p, x, y, B=B)
     flux = si.dblquad(f, -12, 12, -12, 12, epsabs=0, epsrel=1e-9)[0]
     assert flux == pytest.approx(10 ** (-0.4 * (par[4] - m0)), rel=1e-6)
+
+
+def test_lm_checkpoint_and_resume_is_exact():
+    # a fit stopped at max_iter = k with the raw best point (canonical = 0) and its damping,
+    # then resumed from them with max_iter N - k + 1, ends exactly where the uninterrupted
+    # N-iteration fit ends: the first resumed evaluation repeats the best point's A, g, chi^2
+    b = synth.draw_small(seed=17, G=8, H=32, W=32, K=7)
+    psf = np.stack([_gauss_psf(b.K, 1.5)] * b.G)
+    truth = synth.galaxy_slots(b)
+    Mt = oracle.model_images(b.spec, truth, psf, b.H, b.W)
+    D, S = synth.noisy_image(Mt, b.z)
+    N, k = 60, 5
+    tight = dict(tol=1e-12, xtol=1e-10, gtol=1e-13)
+    full = oracle.fit(b.spec, b.init, psf, D, S, None, oracle.FitOptions(max_iter=N, **tight))
+    lam = np.zeros(b.G)
+    part = oracle.fit(b.spec, b.init, psf, D, S, None, oracle.FitOptions(max_iter=k, canonical=0, **tight), lam)
+    run = part["status"] == 2
+    assert run.sum() >= 4 and (lam[run] > 0).all()
+    rest = oracle.fit(b.spec, part["params"][run], psf[run], D[run], S[run], None,
+                      oracle.FitOptions(max_iter=N - k + 1, **tight), lam[run].copy())
+    for key in ("params", "chi2", "status", "sigma_p"):
+        np.testing.assert_array_equal(rest[key], full[key][run])
+    np.testing.assert_array_equal(rest["iters"], full["iters"][run] - k + 1)
