@@ -254,6 +254,23 @@ size_t gm_grad_adjoint_workspace_bytes(const gm_model_desc *desc, const gm_batch
 int gm_grad_adjoint(const gm_model_desc *desc, const gm_batch *batch, const double *params, double *chi2,
                     double *grad, void *workspace, size_t ws_bytes, void *stream);
 
+/* Device time of each kernel group of one gm_grad_adjoint call (host memory).  Not
+ * part of the paper's method: it lets a caller relate throughput to the kernels'
+ * own time (the correlations are bound by the FP32 FMA pipe, the rest by issue). */
+typedef struct {
+  double setup_ms;     /* per-galaxy constants and the convolved profiles' pair planes */
+  double resid_ms;     /* correlation of the profile planes with the PSFs (model) */
+  double residual_ms;  /* residuals, chi^2 and the unconvolved components' terms */
+  double grad_ms;      /* correlation of w r with the flipped PSFs (the adjoint) */
+  double deriv_ms;     /* the convolved profiles' derivative sums and the per-galaxy totals */
+} gm_adjoint_stats;
+
+/* Kernel times of the calling thread's last gm_grad_adjoint (CUDA events recorded on
+ * its stream; waits for that call to finish).  GM_E_INVAL if out is NULL or no call
+ * has been timed on this thread (calls made while their stream was being captured
+ * into a CUDA graph are not timed). */
+int gm_grad_adjoint_last_stats(gm_adjoint_stats *out);
+
 /*
  * gm_chi2_grad_noalloc -- gm_chi2_grad for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a convenience of the library.

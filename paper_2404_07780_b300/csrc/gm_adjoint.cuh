@@ -11,14 +11,20 @@
 // zero-padded correlation with the PSF flipped in both axes
 // (sum_ab P[a,b] u[i-a+c, j-b+c] = sum_a'b' P[K-1-a', K-1-b'] u[i+a'-c, j+b'-c]).
 //
-// Each pass is three kernels:
+// Each pass is five kernels:
 //   k_profile_pairs   I_conv of two galaxies per pixel into one pair plane
-//   k_adjoint<RESID>  correlate I_conv with P -> M, add the unconvolved part,
-//                     write u = w r into a second pair plane; chi^2 and the
-//                     unconvolved gradient terms per tile
-//   k_adjoint<ADJ>    correlate u with the flipped P -> v, evaluate the
-//                     convolved profiles' derivatives at the pixel and
-//                     accumulate sum v dI/dp per tile
+//   k_adjoint<RESID>  correlate the I_conv plane with the pair's PSFs -> M_conv plane
+//   k_adj_resid       M = M_conv + the unconvolved components, u = w r written over
+//                     M_conv; chi^2 and sum u dI_unconv/dp per tile
+//   k_adjoint<GRAD>   correlate the u plane with the PSFs flipped -> v plane
+//   k_adj_deriv       the convolved profiles' derivatives at every pixel: sum
+//                     v dI_conv/dp per tile
+// The correlations are bound by the FMA pipe, the pixel kernels by instruction
+// issue (profile code per pixel, component and galaxy); kept apart, each runs at
+// its own limit with the registers and occupancy it needs (inside the
+// correlation kernel the epilogues doubled its instructions per window and held
+// the registers of both phases).  The planes between them cost one write and one
+// read of 8 bytes per pixel pair.
 // Two galaxies share one f32x2 lane pair: the plane holds (galaxy 2k, galaxy
 // 2k+1) and the PSF pair is (P_2k[a,b], P_2k+1[a,b]), so every packed FMA does
 // useful work although each galaxy has a single channel.  Windows are loaded
@@ -32,13 +38,6 @@ namespace gm {
 
 enum AdjMode { ADJ_RESID = 0, ADJ_GRAD = 1 };
 
-// Pixels of a thread's row of 8 that one iteration of the epilogue loop evaluates.
-// Smaller is faster on the 15-parameter bulge+bar+nucleus pass: 7.34 and 7.68 ms for
-// 1 and 2 pixels; with strided tiles, 7.84, 8.22 and 8.44 ms for 2, 4 and 8.  The
-// instruction footprint outweighs the lost overlap of independent pixels, as the
-// kernel has 12 warps per SM to interleave.
-constexpr int kEpiPx = 1;
-
 template <int N>
 __device__ __forceinline__ void swap_rows(float (&a)[2][N]) {
 #pragma unroll
@@ -49,89 +48,25 @@ __device__ __forceinline__ void swap_rows(float (&a)[2][N]) {
   }
 }
 
-// Image D and 1/sigma of 8 consecutive pixels of one stamp row starting at element
-// base, n_in of them inside the stamp (n_in may be below 1 or above 8): two float4
-// loads per array when the row holds all 8 and both addresses are 16-byte aligned,
-// one 8-byte mask load when that is aligned, else element by element within the row.
-// Bit k of excl is set for a pixel outside the stamp or masked (mask byte nonzero);
-// such a pixel gets D = 0 and 1/sigma = 0 and no sigma is divided for it.
-__device__ __forceinline__ void load_row8(const float* __restrict__ image, const float* __restrict__ sigma,
-                                          const uint8_t* __restrict__ mask, size_t base, int n_in,
-                                          float (&D)[8], float (&isg)[8], unsigned& excl) {
-  const float* ip = image + base;
-  const float* sp = sigma + base;
-  float S[8];
-  const bool full = n_in >= 8;
-  if (full && ((reinterpret_cast<uintptr_t>(ip) | reinterpret_cast<uintptr_t>(sp)) & 15) == 0) {
-    const float4 a0 = __ldg(reinterpret_cast<const float4*>(ip)), a1 = __ldg(reinterpret_cast<const float4*>(ip) + 1);
-    const float4 s0 = __ldg(reinterpret_cast<const float4*>(sp)), s1 = __ldg(reinterpret_cast<const float4*>(sp) + 1);
-    D[0] = a0.x; D[1] = a0.y; D[2] = a0.z; D[3] = a0.w; D[4] = a1.x; D[5] = a1.y; D[6] = a1.z; D[7] = a1.w;
-    S[0] = s0.x; S[1] = s0.y; S[2] = s0.z; S[3] = s0.w; S[4] = s1.x; S[5] = s1.y; S[6] = s1.z; S[7] = s1.w;
-  } else {
+// a[k] <- a[(k + S) mod N]
+template <int S, int N>
+__device__ __forceinline__ void rotate_left(float (&a)[N]) {
+  float t[N];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      D[k] = k < n_in ? __ldg(ip + k) : 0.f;
-      S[k] = k < n_in ? __ldg(sp + k) : 1.f;
-    }
-  }
-  unsigned ex = 0;
+  for (int k = 0; k < N; ++k) t[k] = a[(k + S) % N];
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (k >= n_in) ex |= 1u << k;
-  if (mask) {
-    const uint8_t* mp = mask + base;
-    if (full && (reinterpret_cast<uintptr_t>(mp) & 7) == 0) {
-      const uint2 mv = __ldg(reinterpret_cast<const uint2*>(mp));
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if ((mv.x >> (8 * k)) & 0xffu) ex |= 1u << k;
-        if ((mv.y >> (8 * k)) & 0xffu) ex |= 1u << (k + 4);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (k < n_in && __ldg(mp + k)) ex |= 1u << k;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const bool off = (ex >> k) & 1u;
-    isg[k] = off ? 0.f : 1.f / S[k];
-    if (off) D[k] = 0.f;
-  }
-  excl = ex;
-}
-
-// a[k] <- a[(k + S) mod 8]
-template <int S>
-__device__ __forceinline__ void rotate_left(float (&a)[8]) {
-  float t[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) t[k] = a[(k + S) & 7];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) a[k] = t[k];
+  for (int k = 0; k < N; ++k) a[k] = t[k];
 }
 
 struct AdjArgs {
   CUtensorMap tmap;          // input pair planes [(G+1)/2][H][2*Wp] FP32
-  ChanMap m;
-  int P;                     // free slots (accumulator order)
-  int conv_acc[kMaxComp][8]; // accumulator of d/dp_k of a convolved comp c (-1 none)
-  int unconv_acc[kMaxComp][8];  // same for unconvolved comps
-  int nacc;                  // 1 + P
   int G, H, W, Wp, K, cpad, tiles_x, n_tiles, rw, plane;
-  const float* image;
-  const float* sigma;
-  const uint8_t* mask;
   const float* psf;
-  const float* cconst;
-  float* u_planes;           // RESID: output pair planes of u = w r
-  double* partial;           // [G][n_tiles][nacc]: RESID writes [0] chi^2 and unconvolved terms,
-                             //                     ADJ adds the convolved terms to a second copy
+  float* out_planes;         // output pair planes [(G+1)/2][H][Wp] float2
   int* err;
   unsigned wait_polls;       // polls of a window wait before it gives up (kWaitTries)
   int starve;                // test of the timeout path: block 0 issues no load for its first window
-  int off_psf, off_in, off_cc, off_red, off_bar;
+  int off_psf, off_in, off_bar;
 };
 
 #ifdef GM_HOST_TU
@@ -179,24 +114,22 @@ __device__ __forceinline__ void adj_issue(const AdjArgs& A, float2* s_in, u64* b
   tma_load_3d(s_in, &A.tmap, 2 * (j0 - c - A.cpad), i0 - c, gp, bar);
 }
 
-template <int MODE, int P>
-__global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjArgs A) {
+// Correlation of one pair plane with the pair's PSFs (RESID: P as given; GRAD: P
+// flipped in both axes, the adjoint), written to the output pair plane.  Items
+// are (galaxy pair, 32 x 32 tile); each block takes a contiguous range of them,
+// so a pair's tiles run back to back and its PSF pair is staged once for them.
+template <int MODE>
+__global__ void __launch_bounds__(128, 4) k_adjoint(const __grid_constant__ AdjArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   u64* s_psf = reinterpret_cast<u64*>(smem + A.off_psf);
   float2* s_in = reinterpret_cast<float2*>(smem + A.off_in);
-  float* s_cc = reinterpret_cast<float*>(smem + A.off_cc);
-  float* s_red = reinterpret_cast<float*>(smem + A.off_red);
   u64* bar = reinterpret_cast<u64*>(smem + A.off_bar);
   int* s_flag = reinterpret_cast<int*>(smem + A.off_bar + 8);
-  const ChanMap& m = A.m;
-  constexpr int NA = 1 + P;
 
   const int tid = threadIdx.x;
   const int K = A.K, c = (K - 1) / 2, K2 = K + 1;
   const int n_pairs = (A.G + 1) / 2;
   const int n_items = n_pairs * A.n_tiles;
-  // Each block takes a contiguous range of items: the tiles of one galaxy pair run
-  // back to back on it, and the pair's PSF and constants are staged once for them.
   const int it_lo = (int)((long long)blockIdx.x * n_items / gridDim.x);
   const int it_hi = (int)((long long)(blockIdx.x + 1) * n_items / gridDim.x);
   if (it_lo >= it_hi) return;
@@ -215,29 +148,22 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
   const int lane = tid & 31, wig = tid >> 5;
   const int row = wig * 8 + (lane & 7), col0 = (lane >> 3) * 8;
   const int row0 = wig * 8;
-  const int ncc = m.n_comp * kCC;
 
-  int staged = -1;  // galaxy pair whose PSF and constants are in shared memory
+  int staged = -1;  // galaxy pair whose PSF pair is in shared memory
   for (int item = it_lo; item < it_hi; ++item) {
     const int gp = item / A.n_tiles, tile = item - gp * A.n_tiles;
     const int g0 = 2 * gp, g1 = 2 * gp + 1;
     const bool has1 = g1 < A.G;
     const int i0 = (tile / A.tiles_x) * kTile, j0 = (tile % A.tiles_x) * kTile;
 
-    __syncthreads();  // the previous item is done with s_psf, s_cc, s_red
+    __syncthreads();  // the previous item is done with s_psf
     if (gp != staged) {
       staged = gp;
-      for (int t = tid; t < 2 * ncc; t += blockDim.x) {
-        const int h = t / ncc, e = t - h * ncc;
-        const int g = g0 + h;
-        s_cc[t] = (g < A.G) ? A.cconst[(size_t)g * ncc + e] : 0.f;
-      }
       for (int t = tid; t < K * K2; t += blockDim.x) {
         const int a = t / K2, bb = t - a * K2;
         const int b = bb - A.cpad;
         float v0 = 0.f, v1 = 0.f;
         if (b >= 0 && b < K) {
-          // RESID correlates with P, ADJ with P flipped in both axes (the adjoint)
           const int src = (MODE == ADJ_RESID) ? a * K + b : (K - 1 - a) * K + (K - 1 - b);
           v0 = A.psf[(size_t)g0 * K * K + src];
           v1 = has1 ? A.psf[(size_t)g1 * K * K + src] : 0.f;
@@ -269,143 +195,269 @@ __global__ void __launch_bounds__(128, 3) k_adjoint(const __grid_constant__ AdjA
       adj_issue(A, s_in, bar, item + 1);
       inflight = true;
     }
-
-    // ---- epilogue: this thread's 8 pixels, both galaxies, straight from registers ----
-    // Code size decides its speed: eval_component is a large inline body, and a fully
-    // unrolled epilogue (2 galaxies x 8 pixels of it) misses the instruction cache.  The
-    // galaxies of the pair therefore run as a loop over h that works on row 0 of each
-    // [2][.] array and swaps the rows after each galaxy, and the 8 pixels as a loop of
-    // kEpiPx-pixel chunks that works on entries 0..kEpiPx-1 and rotates the row by kEpiPx
-    // after each chunk; every index stays a compile-time constant (registers), and both
-    // the swaps and the full turn of rotations leave the arrays in their starting order.
-    float red[2][NA];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int e = 0; e < NA; ++e) red[h][e] = 0.f;
     const int i = i0 + row;
-    float vv[2][8];
-#pragma unroll
-    for (int rx = 0; rx < 8; ++rx) unpack2(acc[0][rx], vv[0][rx], vv[1][rx]);
-    // Each gradient term is a sum over pixels of a weight times dI/dp_k.  The
-    // accumulator of (component, k) is run-time data, and a compare-select over the
-    // free parameters keeps red[] in registers; it is paid once per component and
-    // galaxy: the thread first sums each derivative over its 8 pixels.
-    auto scatter = [&](const int (&acc_of)[8], int np, const float (&sd)[8]) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (k >= np) break;
-        const int f = acc_of[k];
-#pragma unroll
-        for (int ff = 0; ff < P; ++ff)
-          if (ff == f) red[0][1 + ff] += sd[k];
-      }
-    };
-    // sum over the 8 pixels of wt * dI_cm/dp_k for the components cm that are (not) convolved
-    auto deriv_sums = [&](float (&wt)[2][8], bool conv) {
-      for (int cm = 0; cm < m.n_comp; ++cm) {
-        if ((m.conv[cm] != 0) != conv) continue;
-        const int np = m.np[cm];
-        const float* cc = s_cc + cm * kCC;
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          if (h == 0 || has1) {
-            float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-            for (int rb = 0; rb < 8; rb += kEpiPx) {
-#pragma unroll
-              for (int q = 0; q < kEpiPx; ++q) {
-                const int j = j0 + col0 + rb + q;
-                if (i < A.H && j < A.W) {
-                  float d[8];
-                  eval_component(m.kind[cm], cc + h * ncc, i, j, d);
-#pragma unroll
-                  for (int k = 0; k < 8; ++k)
-                    if (k < np) sd[k] = fmaf(wt[0][q], d[k], sd[k]);
-                }
-              }
-              rotate_left<kEpiPx>(wt[0]);
-            }
-            scatter(conv ? A.conv_acc[cm] : A.unconv_acc[cm], np, sd);
-          }
-          swap_rows(wt);
-          swap_rows(red);
-        }
-      }
-    };
-    if (MODE == ADJ_RESID) {
-      float wr[2][8];  // w r = (D - M) / sigma^2 per pixel; 0 outside the stamp or masked
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        const int g = g0 + h;
-        // D and 1/sigma of this galaxy's 8 pixels, loaded before the pixel loop
-        float Dv[8], Iv[8];
-        unsigned excl = 0xffu;  // bit k: pixel k is not used (masked, outside the stamp)
-        if ((h == 0 || has1) && i < A.H) {
-          load_row8(A.image, A.sigma, A.mask, ((size_t)g * A.H + i) * A.W + j0 + col0, A.W - (j0 + col0), Dv, Iv,
-                    excl);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) Dv[k] = Iv[k] = 0.f;
-        }
-#pragma unroll 1
-        for (int rb = 0; rb < 8; rb += kEpiPx) {
-#pragma unroll
-          for (int q = 0; q < kEpiPx; ++q) {
-            const int j = j0 + col0 + rb + q;
-            float uu = 0.f;
-            if (!((excl >> q) & 1u)) {
-              float Mv = vv[0][q];
-              for (int cm = 0; cm < m.n_comp; ++cm) {
-                if (m.conv[cm]) continue;
-                float d[8];
-                Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, i, j, d);
-              }
-              const float rr = (Dv[q] - Mv) * Iv[q];
-              red[0][0] = fmaf(rr, rr, red[0][0]);
-              uu = rr * Iv[q];
-            }
-            wr[0][q] = uu;
-          }
-          rotate_left<kEpiPx>(vv[0]);
-          rotate_left<kEpiPx>(wr[0]);
-          rotate_left<kEpiPx>(Dv);
-          rotate_left<kEpiPx>(Iv);
-          excl >>= kEpiPx;
-        }
-        swap_rows(vv);
-        swap_rows(wr);
-        swap_rows(red);
-      }
+    if (i < A.H) {
+      float2* out = reinterpret_cast<float2*>(A.out_planes) + ((size_t)gp * A.H + i) * A.Wp;
 #pragma unroll
       for (int rx = 0; rx < 8; ++rx) {
         const int j = j0 + col0 + rx;
-        if (i < A.H && j < A.Wp)
-          reinterpret_cast<float2*>(A.u_planes)[((size_t)gp * A.H + i) * A.Wp + j] = make_float2(wr[0][rx], wr[1][rx]);
+        float x, y;
+        unpack2(acc[0][rx], x, y);
+        if (j < A.Wp) out[j] = make_float2(x, y);
       }
-      deriv_sums(wr, false);
-    } else {
-      deriv_sums(vv, true);
-    }
-    // ---- block reduction: warp sums (recursive halving), then across the 4 warps, FP64 per tile ----
-    {
-      float flat[2 * NA];
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int e = 0; e < NA; ++e) flat[h * NA + e] = red[h][e];
-      warp_sum_scatter(flat, lane, [&](int t, float v) { s_red[wig * 2 * NA + t] = v; });
-    }
-    __syncthreads();
-    for (int t = tid; t < 2 * NA; t += blockDim.x) {
-      const int h = t / NA, e = t - h * NA;
-      const int g = g0 + h;
-      if (g >= A.G) continue;
-      double s = 0.0;
-      for (int w = 0; w < 4; ++w) s += (double)s_red[(w * 2 + h) * NA + e];
-      A.partial[((size_t)g * A.n_tiles + tile) * NA + e] = s;
     }
   }
+}
+
+// Arguments of k_adj_resid and k_adj_deriv (equal stamps).
+struct PixArgs {
+  ChanMap m;
+  int acc_of[kMaxComp][8];    // k_adj_resid: accumulator of d/dp_k of an unconvolved comp c, k_adj_deriv:
+                              // of a convolved one (-1 none)
+  int G, H, W, Wp, tiles_x, n_tiles;
+  const float* image;
+  const float* sigma;
+  const uint8_t* mask;
+  const float* cconst;        // [G][n_comp][kCC]
+  float* planes;              // [(G+1)/2][H][Wp] float2: k_adj_resid reads M_conv and writes u = w r in
+                              // place; k_adj_deriv reads v
+  double* partial;            // [G][pix_parts(H, W)][1 + P]: the galaxy's sums over each part of its stamp
+};
+
+constexpr int kPixThreads = 256;
+constexpr int kPixPerThread = 4;  // pixels per thread in one chunk of a pixel kernel
+constexpr int kPixPart = 2 * kPixThreads * kPixPerThread;  // pixels of a stamp per block (FP32 sums of <= 8
+                                                           // terms per thread before the FP64 block sum)
+
+__host__ __device__ inline int pix_parts(int H, int W) { return (H * W + kPixPart - 1) / kPixPart; }
+
+// The pair's sums over one part of the stamp into its partials: warp sums by
+// recursive halving, then FP64 over the warps in warp order (deterministic).
+template <int NA>
+__device__ __forceinline__ void pix_pair_sums(const PixArgs& A, float (&red)[2][NA], float* s_red, int g0, int part,
+                                              int n_parts) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float flat[2 * NA];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int e = 0; e < NA; ++e) flat[h * NA + e] = red[h][e];
+  warp_sum_scatter(flat, lane, [&](int t, float v) { s_red[warp * 2 * NA + t] = v; });
+  __syncthreads();
+  for (int t = tid; t < 2 * NA; t += kPixThreads) {
+    const int h = t / NA, e = t - h * NA;
+    const int g = g0 + h;
+    if (g >= A.G) continue;
+    double s = 0.0;
+    for (int w = 0; w < kPixThreads / 32; ++w) s += (double)s_red[(w * 2 + h) * NA + e];
+    A.partial[((size_t)g * n_parts + part) * NA + e] = s;
+  }
+}
+
+// red[0][1 + f] += sd[k] for the accumulator f of each of the component's np derivatives
+// (a compare-select over the P free parameters keeps red in registers)
+template <int P, int NA>
+__device__ __forceinline__ void scatter_sums(float (&red)[2][NA], const int (&acc_of)[8], int np,
+                                             const float (&sd)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k >= np) break;
+    const int f = acc_of[k];
+#pragma unroll
+    for (int ff = 0; ff < P; ++ff)
+      if (ff == f) red[0][1 + ff] += sd[k];
+  }
+}
+
+// For the components with conv[cm] == conv: red[h][1 + f] += sum over the chunk's
+// pixels of wt[h][q] dI_cm/dp_k (f the accumulator of slot k).  The galaxies run as a
+// loop over row 0 of each [2][.] array, the rows swapped after each galaxy, and the
+// pixels as a loop that rotates row 0 (compile-time indices: registers; one copy of
+// the profile code).
+template <int P, int NA>
+__device__ __forceinline__ void chunk_deriv_sums(const PixArgs& A, const float* s_cc, int ncc, bool has1,
+                                                 const int (&pi)[kPixPerThread], const int (&pj)[kPixPerThread],
+                                                 float (&wt)[2][kPixPerThread], float (&red)[2][NA], bool conv) {
+  const ChanMap& m = A.m;
+  for (int cm = 0; cm < m.n_comp; ++cm) {
+    if ((m.conv[cm] != 0) != conv) continue;
+    const int np = m.np[cm];
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      if (h == 0 || has1) {
+        const float* cc = s_cc + h * ncc + cm * kCC;
+        float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int q = 0; q < kPixPerThread; ++q) {
+          if (pi[q] >= 0) {
+            float d[8];
+            eval_component(m.kind[cm], cc, pi[q], pj[q], d);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (k < np) sd[k] = fmaf(wt[0][0], d[k], sd[k]);
+          }
+          rotate_left<1>(wt[0]);
+        }
+        scatter_sums<P>(red, A.acc_of[cm], np, sd);
+      }
+      swap_rows(wt);
+      swap_rows(red);
+    }
+  }
+}
+
+// Residuals of one galaxy pair, one block of 256 threads per kPixPart pixels of the
+// stamp, in chunks of 4 pixels per thread (pixel p, row-major, on thread p % 256:
+// each warp reads consecutive pixels): M = M_conv + the unconvolved components,
+// r = D - M, u = w r (0 for masked pixels) written over M_conv, and the pair's
+// chi^2 and sum u dI_unconv/dp.
+template <int P>
+__global__ void __launch_bounds__(kPixThreads, 2) k_adj_resid(const __grid_constant__ PixArgs A) {
+  constexpr int NA = 1 + P;
+  __shared__ float s_cc[2 * kMaxComp * kCC];
+  __shared__ float s_red[(kPixThreads / 32) * 2 * NA];
+  const ChanMap& m = A.m;
+  const int tid = threadIdx.x;
+  const int ncc = m.n_comp * kCC;
+  const int HW = A.H * A.W, n_parts = pix_parts(A.H, A.W);
+  const int gp = blockIdx.x / n_parts, part = blockIdx.x - gp * n_parts;
+  const int g0 = 2 * gp;
+  const bool has1 = g0 + 1 < A.G;
+  const int p_end = min(HW, (part + 1) * kPixPart);
+  float2* planes = reinterpret_cast<float2*>(A.planes);
+  for (int t = tid; t < 2 * ncc; t += kPixThreads) s_cc[t] = (t < ncc || has1) ? A.cconst[(size_t)g0 * ncc + t] : 0.f;
+  if ((A.W & 1) && part == 0)  // the pad column of an odd width: u = 0, the zero padding of the next correlation
+    for (int i = tid; i < A.H; i += kPixThreads) planes[((size_t)gp * A.H + i) * A.Wp + A.W] = make_float2(0.f, 0.f);
+  __syncthreads();
+  float red[2][NA];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int e = 0; e < NA; ++e) red[h][e] = 0.f;
+  for (int p0 = part * kPixPart; p0 < p_end; p0 += kPixThreads * kPixPerThread) {
+    // every load of the chunk first (one memory latency for all of them), then the arithmetic
+    int pi[kPixPerThread], pj[kPixPerThread];
+    float2 mc[kPixPerThread];
+    float Dv[2][kPixPerThread], Sv[2][kPixPerThread];
+    bool use[2][kPixPerThread];
+#pragma unroll
+    for (int q = 0; q < kPixPerThread; ++q) {
+      const int p = p0 + tid + q * kPixThreads;
+      const bool in = p < p_end;
+      const int i = in ? p / A.W : 0, j = in ? p - i * A.W : 0;
+      pi[q] = in ? i : -1;
+      pj[q] = j;
+      mc[q] = in ? planes[((size_t)gp * A.H + i) * A.Wp + j] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const size_t gpx = (size_t)(g0 + h) * HW + p;
+        use[h][q] = in && (h == 0 || has1);
+        Dv[h][q] = use[h][q] ? __ldg(A.image + gpx) : 0.f;
+        Sv[h][q] = use[h][q] ? __ldg(A.sigma + gpx) : 1.f;
+        if (use[h][q] && A.mask && __ldg(A.mask + gpx)) use[h][q] = false;
+      }
+    }
+    float uu[2][kPixPerThread];
+#pragma unroll
+    for (int q = 0; q < kPixPerThread; ++q) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uu[h][q] = 0.f;
+        if (!use[h][q]) continue;
+        float Mv = h ? mc[q].y : mc[q].x;
+        for (int cm = 0; cm < m.n_comp; ++cm) {
+          if (m.conv[cm]) continue;
+          float d[8];
+          Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, pi[q], pj[q], d);
+        }
+        const float isg = 1.f / Sv[h][q];
+        const float rr = (Dv[h][q] - Mv) * isg;
+        red[h][0] = fmaf(rr, rr, red[h][0]);
+        uu[h][q] = rr * isg;
+      }
+      if (pi[q] >= 0) planes[((size_t)gp * A.H + pi[q]) * A.Wp + pj[q]] = make_float2(uu[0][q], uu[1][q]);
+    }
+    if (m.any_unconv) chunk_deriv_sums<P>(A, s_cc, ncc, has1, pi, pj, uu, red, false);
+  }
+  pix_pair_sums(A, red, s_red, g0, part, n_parts);
+}
+
+// sum over the stamp of v dI_conv/dp for both galaxies of a pair, one block of 256
+// threads per kPixPart pixels of the stamp, in chunks of 4 pixels per thread as in
+// k_adj_resid.  Each thread keeps its 2 (1 + P) sums in a row of shared memory
+// indexed by parameter (an odd row pitch: the lanes of a warp hit distinct banks),
+// so adding a derivative's sum costs one shared-memory update instead of a
+// compare-select over the P accumulators.
+template <int P>
+__global__ void __launch_bounds__(kPixThreads, 3) k_adj_deriv(const __grid_constant__ PixArgs A) {
+  constexpr int NA = 1 + P, RP = 2 * NA + 1;
+  __shared__ float s_cc[2 * kMaxComp * kCC];
+  __shared__ float s_red[(kPixThreads / 32) * 2 * NA];
+  __shared__ float s_sum[kPixThreads * RP];
+  const ChanMap& m = A.m;
+  const int tid = threadIdx.x;
+  const int ncc = m.n_comp * kCC;
+  const int HW = A.H * A.W, n_parts = pix_parts(A.H, A.W);
+  const int gp = blockIdx.x / n_parts, part = blockIdx.x - gp * n_parts;
+  const int g0 = 2 * gp;
+  const bool has1 = g0 + 1 < A.G;
+  const int p_end = min(HW, (part + 1) * kPixPart);
+  for (int t = tid; t < 2 * ncc; t += kPixThreads) s_cc[t] = (t < ncc || has1) ? A.cconst[(size_t)g0 * ncc + t] : 0.f;
+  float* my = s_sum + tid * RP;
+#pragma unroll
+  for (int e = 0; e < 2 * NA; ++e) my[e] = 0.f;
+  __syncthreads();
+  for (int p0 = part * kPixPart; p0 < p_end; p0 += kPixThreads * kPixPerThread) {
+    int pi[kPixPerThread], pj[kPixPerThread];
+    float vv[2][kPixPerThread];
+#pragma unroll
+    for (int q = 0; q < kPixPerThread; ++q) {
+      const int p = p0 + tid + q * kPixThreads;
+      const bool in = p < p_end;
+      const int i = in ? p / A.W : 0, j = in ? p - i * A.W : 0;
+      pi[q] = in ? i : -1;
+      pj[q] = j;
+      const float2 v = in ? reinterpret_cast<const float2*>(A.planes)[((size_t)gp * A.H + i) * A.Wp + j]
+                          : make_float2(0.f, 0.f);
+      vv[0][q] = v.x;
+      vv[1][q] = v.y;
+    }
+    for (int cm = 0; cm < m.n_comp; ++cm) {
+      if (!m.conv[cm]) continue;
+      const int np = m.np[cm];
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        if (h == 0 || has1) {
+          const float* cc = s_cc + h * ncc + cm * kCC;
+          float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+          for (int q = 0; q < kPixPerThread; ++q) {
+            if (pi[q] >= 0) {
+              float d[8];
+              eval_component(m.kind[cm], cc, pi[q], pj[q], d);
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if (k < np) sd[k] = fmaf(vv[0][0], d[k], sd[k]);
+            }
+            rotate_left<1>(vv[0]);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (k >= np) break;
+            const int f = A.acc_of[cm][k];
+            if (f >= 0) my[h * NA + 1 + f] += sd[k];
+          }
+        }
+        swap_rows(vv);
+      }
+    }
+  }
+  float red[2][NA];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int e = 0; e < NA; ++e) red[h][e] = my[h * NA + e];
+  pix_pair_sums(A, red, s_red, g0, part, n_parts);
 }
 
 #ifdef GM_HOST_TU

@@ -13,17 +13,17 @@
 #define GM_FUSED_LIST_2(X) X(1, 4, 2, 0) X(1, 5, 2, 0) X(1, 6, 2, 0) X(1, 7, 2, 0) X(1, 8, 2, 0) X(1, 9, 2, 0) X(1, 10, 2, 0) X(1, 11, 2, 0)
 #define GM_FUSED_LIST_3(X) X(1, 12, 2, 0) X(1, 13, 2, 0) X(1, 14, 2, 0) X(1, 15, 2, 0) X(1, 16, 2, 0)
 
-// k_adjoint<MODE, P>: ADJ_RESID = 0, ADJ_GRAD = 1
-#define GM_ADJ_LIST_0(X) \
-  X(0, 0) X(1, 0) X(0, 1) X(1, 1) X(0, 2) X(1, 2) X(0, 3) X(1, 3) X(0, 4) X(1, 4) X(0, 5) X(1, 5) X(0, 6) X(1, 6) \
-  X(0, 7) X(1, 7) X(0, 8) X(1, 8)
-#define GM_ADJ_LIST_1(X) \
-  X(0, 9) X(1, 9) X(0, 10) X(1, 10) X(0, 11) X(1, 11) X(0, 12) X(1, 12) X(0, 13) X(1, 13) X(0, 14) X(1, 14) \
-  X(0, 15) X(1, 15) X(0, 16) X(1, 16)
+// k_adjoint<MODE> (ADJ_RESID = 0, ADJ_GRAD = 1) in list 0; k_adj_resid<P> and
+// k_adj_deriv<P>, the pixel kernels of the adjoint gradient, for P free parameters
+#define GM_RESID_LIST_0(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
+#define GM_RESID_LIST_1(X) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+#define GM_DERIV_LIST_0(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
+#define GM_DERIV_LIST_1(X) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
 #define GM_FUSED_LIST_4(X) \
   X(1, 1, 2, 1) X(1, 2, 2, 1) X(1, 3, 2, 1) X(1, 4, 2, 1) X(1, 5, 2, 1) X(1, 6, 2, 1) X(1, 7, 2, 1) X(1, 8, 2, 1) \
   X(1, 9, 2, 1) X(1, 10, 2, 1) X(1, 11, 2, 1) X(1, 12, 2, 1) X(1, 13, 2, 1) X(1, 14, 2, 1) X(1, 15, 2, 1) X(1, 16, 2, 1)
 
 #define GM_FUSED_ALL(X) GM_FUSED_LIST_0(X) GM_FUSED_LIST_1(X) GM_FUSED_LIST_2(X) GM_FUSED_LIST_3(X) GM_FUSED_LIST_4(X)
-#define GM_ADJ_ALL(X) GM_ADJ_LIST_0(X) GM_ADJ_LIST_1(X)
+#define GM_RESID_ALL(X) GM_RESID_LIST_0(X) GM_RESID_LIST_1(X)
+#define GM_DERIV_ALL(X) GM_DERIV_LIST_0(X) GM_DERIV_LIST_1(X)

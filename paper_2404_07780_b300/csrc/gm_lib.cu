@@ -28,8 +28,13 @@ namespace gm {
 #define GM_X(M, P, C, W) extern template __global__ void k_fused<M, P, C, W>(const __grid_constant__ FusedArgs);
 GM_FUSED_ALL(GM_X)
 #undef GM_X
-#define GM_X(M, P) extern template __global__ void k_adjoint<M, P>(const __grid_constant__ AdjArgs);
-GM_ADJ_ALL(GM_X)
+extern template __global__ void k_adjoint<ADJ_RESID>(const __grid_constant__ AdjArgs);
+extern template __global__ void k_adjoint<ADJ_GRAD>(const __grid_constant__ AdjArgs);
+#define GM_X(P) extern template __global__ void k_adj_resid<P>(const __grid_constant__ PixArgs);
+GM_RESID_ALL(GM_X)
+#undef GM_X
+#define GM_X(P) extern template __global__ void k_adj_deriv<P>(const __grid_constant__ PixArgs);
+GM_DERIV_ALL(GM_X)
 #undef GM_X
 }  // namespace gm
 
@@ -61,6 +66,10 @@ thread_local bool g_have_stats = false;
 // for the life of the thread (four per iteration: profile start, tile kernel
 // start, tile kernel end, LM step end).
 thread_local std::vector<cudaEvent_t> g_events;
+// CUDA events around the kernel groups of gm_grad_adjoint (six boundaries), and
+// whether the thread's last call recorded them.
+thread_local cudaEvent_t g_adj_events[6] = {};
+thread_local bool g_adj_timed = false;
 
 int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 int fail(int code, const char* fmt, ...) {
@@ -1258,10 +1267,21 @@ namespace {
 
 typedef void (*AdjKernel)(AdjArgs);
 
-AdjKernel pick_adjoint(int mode, int P) {
-#define GM_X(M, PP) \
-  if (mode == M && P == PP) return k_adjoint<M, PP>;
-  GM_ADJ_ALL(GM_X)
+
+typedef void (*PixKernel)(PixArgs);
+
+PixKernel pick_resid(int P) {
+#define GM_X(PP) \
+  if (P == PP) return k_adj_resid<PP>;
+  GM_RESID_ALL(GM_X)
+#undef GM_X
+  return nullptr;
+}
+
+PixKernel pick_deriv(int P) {
+#define GM_X(PP) \
+  if (P == PP) return k_adj_deriv<PP>;
+  GM_DERIV_ALL(GM_X)
 #undef GM_X
   return nullptr;
 }
@@ -1276,7 +1296,6 @@ WsAdj ws_adj(const gm_model_desc* d, const gm_batch* b, int P) {
   size_t off = 0;
   const size_t G = (size_t)std::max(b->n_gal, 0);
   const size_t pairs = (G + 1) / 2;
-  const size_t tiles = (size_t)((b->W + kTile - 1) / kTile) * ((b->H + kTile - 1) / kTile);
   w.Wp = b->W + (b->W & 1);
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -1287,8 +1306,10 @@ WsAdj ws_adj(const gm_model_desc* d, const gm_batch* b, int P) {
   w.scale = take(G * scale_stride(d->n_slots) * 4);
   w.mplanes = take(pairs * b->H * w.Wp * 8);
   w.uplanes = take(pairs * b->H * w.Wp * 8);
-  w.part_r = take(G * tiles * (1 + P) * 8);
-  w.part_a = take(G * tiles * (1 + P) * 8);
+  // the pixel kernels' sums, per galaxy and part of its stamp
+  const size_t parts = (size_t)pix_parts(std::max(b->H, 0), std::max(b->W, 0));
+  w.part_r = take(G * parts * (1 + P) * 8);
+  w.part_a = take(G * parts * (1 + P) * 8);
   w.err = take(4);
   w.total = off;
   return w;
@@ -1299,8 +1320,10 @@ WsAdj ws_adj(const gm_model_desc* d, const gm_batch* b, int P) {
 struct AdjPass {
   Plan pl;
   WsAdj w;
-  AdjArgs Ar, Aa;  // RESID over the model planes, GRAD over the u = w r planes
+  AdjArgs Ar, Aa;  // correlations: RESID over the I_conv planes, GRAD over the u = w r planes
   AdjKernel kr, ka;
+  PixArgs Xr, Xd;  // pixel kernels: residuals over the M_conv planes, derivative sums over the v planes
+  PixKernel kres, kd;  // kd: nullptr without free parameters
   ProfileArgs PA;
   int grid, pgrid, smem;
   char* ws;
@@ -1327,17 +1350,10 @@ int prepare_adjoint(const gm_model_desc* desc, const gm_batch* batch, void* work
   float* scale = (float*)(ws + w.scale);
   float* mplanes = (float*)(ws + w.mplanes);
   float* uplanes = (float*)(ws + w.uplanes);
+  // the correlations: RESID reads I_conv (model planes) and writes M_conv to the u planes;
+  // k_adj_resid turns M_conv into u = w r in place; GRAD reads u and writes v to the model planes
   AdjArgs& A = ap->Ar;
   std::memset(&A, 0, sizeof(A));
-  A.m = chan_map(pl);
-  A.P = P;
-  A.nacc = 1 + P;
-  for (int c = 0; c < desc->n_comp; ++c)
-    for (int k = 0; k < 8; ++k) {
-      const int f = (k < pl.dd.np[c]) ? pl.chan_of_slot[pl.dd.slot[c][k]] - 1 : -1;
-      A.conv_acc[c][k] = pl.conv[c] ? f : -1;
-      A.unconv_acc[c][k] = pl.conv[c] ? -1 : f;
-    }
   A.G = G;
   A.H = H;
   A.W = batch->W;
@@ -1349,11 +1365,7 @@ int prepare_adjoint(const gm_model_desc* desc, const gm_batch* batch, void* work
   A.rw = window_pitch(K);
   const size_t plane_bytes = ((size_t)(kTile + K - 1) * A.rw * 8 + 127) / 128 * 128;
   A.plane = (int)(plane_bytes / 8);
-  A.image = batch->image;
-  A.sigma = batch->sigma;
-  A.mask = batch->mask;
   A.psf = batch->psf;
-  A.cconst = cconst;
   A.err = (int*)(ws + w.err);
   A.wait_polls = kWaitTries;
   size_t off = 0;
@@ -1365,14 +1377,14 @@ int prepare_adjoint(const gm_model_desc* desc, const gm_batch* batch, void* work
   };
   A.off_in = take(plane_bytes, 128);
   A.off_psf = take((size_t)K * (K + 1) * 8 + 16, 16);  // + the last chunk's prefetch slack
-  A.off_cc = take((size_t)2 * desc->n_comp * kCC * 4, 16);
-  A.off_red = take((size_t)4 * 2 * (1 + P) * 4, 16);
   A.off_bar = take(16, 16);
   ap->smem = (int)off;
   if (ap->smem > di.smem_optin) return fail(GM_E_UNSUPPORTED, "adjoint tile needs %d bytes of shared memory", ap->smem);
-  ap->kr = pick_adjoint(ADJ_RESID, P);
-  ap->ka = pick_adjoint(ADJ_GRAD, P);
-  if (!ap->kr || !ap->ka) return fail(GM_E_UNSUPPORTED, "no adjoint kernel for %d free parameters", P);
+  ap->kr = k_adjoint<ADJ_RESID>;
+  ap->ka = k_adjoint<ADJ_GRAD>;
+  ap->kres = pick_resid(P);
+  ap->kd = P > 0 ? pick_deriv(P) : nullptr;
+  if (!ap->kres || (P > 0 && !ap->kd)) return fail(GM_E_UNSUPPORTED, "no adjoint kernel for %d free parameters", P);
   GM_CUDA(cudaFuncSetAttribute((const void*)ap->kr, cudaFuncAttributeMaxDynamicSharedMemorySize, ap->smem));
   GM_CUDA(cudaFuncSetAttribute((const void*)ap->ka, cudaFuncAttributeMaxDynamicSharedMemorySize, ap->smem));
   int occ = 1;
@@ -1380,34 +1392,80 @@ int prepare_adjoint(const gm_model_desc* desc, const gm_batch* batch, void* work
   ap->grid = std::max(1, std::min(n_pairs * A.n_tiles, std::max(occ, 1) * di.sms));
   ap->PA = profile_args(pl, batch, cconst, scale, mplanes, w.Wp);
   ap->pgrid = std::max(1, std::min(n_pairs * ((H * w.Wp + 255) / 256), 8 * di.sms));
-  A.u_planes = uplanes;
-  A.partial = (double*)(ws + w.part_r);
+  A.out_planes = uplanes;
   if ((rc = encode_planes(&A.tmap, mplanes, H, batch->W, K, n_pairs))) return rc;
   ap->Aa = A;
-  ap->Aa.partial = (double*)(ws + w.part_a);
-  return encode_planes(&ap->Aa.tmap, uplanes, H, batch->W, K, n_pairs);
+  ap->Aa.out_planes = mplanes;
+  if ((rc = encode_planes(&ap->Aa.tmap, uplanes, H, batch->W, K, n_pairs))) return rc;
+  // the pixel kernels
+  PixArgs X;
+  std::memset(&X, 0, sizeof(X));
+  X.m = chan_map(pl);
+  X.G = G;
+  X.H = H;
+  X.W = batch->W;
+  X.Wp = w.Wp;
+  X.tiles_x = A.tiles_x;
+  X.n_tiles = A.n_tiles;
+  X.image = batch->image;
+  X.sigma = batch->sigma;
+  X.mask = batch->mask;
+  X.cconst = cconst;
+  ap->Xr = X;
+  ap->Xd = X;
+  for (int c = 0; c < desc->n_comp; ++c)
+    for (int k = 0; k < 8; ++k) {
+      const int f = (k < pl.dd.np[c]) ? pl.chan_of_slot[pl.dd.slot[c][k]] - 1 : -1;
+      ap->Xr.acc_of[c][k] = pl.conv[c] ? -1 : f;
+      ap->Xd.acc_of[c][k] = pl.conv[c] ? f : -1;
+    }
+  ap->Xr.planes = uplanes;
+  ap->Xr.partial = (double*)(ws + w.part_r);
+  ap->Xd.planes = mplanes;
+  ap->Xd.partial = (double*)(ws + w.part_a);
+  return GM_OK;
 }
 
 // chi^2 and d chi^2/dp at params: set-up, profile planes, both correlations, per-galaxy sums.
 int launch_adjoint(const AdjPass& ap, const gm_batch* batch, const double* params, double* chi2, double* grad,
-                   cudaStream_t st) {
+                   cudaStream_t st, const cudaEvent_t* ev = nullptr) {
   const int G = batch->n_gal;
+  auto mark = [&](int k) -> int {
+    if (ev) GM_CUDA(cudaEventRecord(ev[k], st));
+    return GM_OK;
+  };
+  int rc;
+  if ((rc = mark(0))) return rc;
   if (int rc = ensure_nu_table(st)) return rc;
   k_setup<<<(G + 31) / 32, 32, 0, st>>>(ap.pl.dd, G, nullptr, batch->H, batch->W, params, 0,
                                         (float*)(ap.ws + ap.w.cconst), (float*)(ap.ws + ap.w.scale));
   GM_LAUNCHED("k_setup");
   k_profile_pairs<<<ap.pgrid, 256, 0, st>>>(ap.PA);
   GM_LAUNCHED("k_profile_pairs");
+  if ((rc = mark(1))) return rc;
+  const int n_parts = pix_parts(batch->H, batch->W), blocks = (G + 1) / 2 * n_parts;
   AdjArgs Ar = ap.Ar;
   if (take_starve(&Ar.wait_polls)) Ar.starve = 1;
   ap.kr<<<ap.grid, 128, ap.smem, st>>>(Ar);
   GM_LAUNCHED("k_adjoint(resid)");
+  if ((rc = mark(2))) return rc;
+  ap.kres<<<blocks, kPixThreads, 0, st>>>(ap.Xr);
+  GM_LAUNCHED("k_adj_resid");
+  if ((rc = mark(3))) return rc;
   ap.ka<<<ap.grid, 128, ap.smem, st>>>(ap.Aa);
   GM_LAUNCHED("k_adjoint(grad)");
-  k_adjoint_finish<<<(G + 127) / 128, 128, 0, st>>>(ap.pl.dd, G, ap.Ar.n_tiles, ap.Ar.partial, ap.Aa.partial,
-                                                    ap.Ar.err, chi2, grad);
+  if ((rc = mark(4))) return rc;
+  if (ap.kd) {
+    ap.kd<<<blocks, kPixThreads, 0, st>>>(ap.Xd);
+    GM_LAUNCHED("k_adj_deriv");
+  } else {
+    GM_CUDA(cudaMemsetAsync(ap.Xd.partial, 0, (size_t)G * n_parts * (1 + ap.pl.dd.P) * 8, st));
+  }
+  // the pixel kernels leave one partial per galaxy and part of its stamp
+  k_adjoint_finish<<<(G + 127) / 128, 128, 0, st>>>(ap.pl.dd, G, n_parts, ap.Xr.partial, ap.Xd.partial, ap.Ar.err,
+                                                    chi2, grad);
   GM_LAUNCHED("k_adjoint_finish");
-  return GM_OK;
+  return mark(5);
 }
 
 // Workspace of gm_fit_adam: the adjoint pass's, then the current point, its chi^2
@@ -1454,7 +1512,33 @@ int gm_grad_adjoint(const gm_model_desc* desc, const gm_batch* batch, const doub
   if (!params || !chi2) return fail(GM_E_INVAL, "params/chi2 is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   GM_CUDA(cudaMemsetAsync(ap.Ar.err, 0, sizeof(int), st));
-  return launch_adjoint(ap, batch, params, chi2, grad, st);
+  // kernel timing events, unless the stream is being captured into a graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  GM_CUDA(cudaStreamIsCapturing(st, &cs));
+  g_adj_timed = false;
+  const cudaEvent_t* ev = nullptr;
+  if (cs == cudaStreamCaptureStatusNone) {
+    for (auto& e : g_adj_events)
+      if (!e) GM_CUDA(cudaEventCreate(&e));
+    ev = g_adj_events;
+  }
+  if ((rc = launch_adjoint(ap, batch, params, chi2, grad, st, ev))) return rc;
+  g_adj_timed = ev != nullptr;
+  return GM_OK;
+}
+
+int gm_grad_adjoint_last_stats(gm_adjoint_stats* out) {
+  if (!out) return fail(GM_E_INVAL, "out is NULL");
+  if (!g_adj_timed) return fail(GM_E_INVAL, "no timed gm_grad_adjoint call on this thread");
+  GM_CUDA(cudaEventSynchronize(g_adj_events[5]));
+  float t[5];
+  for (int k = 0; k < 5; ++k) GM_CUDA(cudaEventElapsedTime(&t[k], g_adj_events[k], g_adj_events[k + 1]));
+  out->setup_ms = t[0];
+  out->resid_ms = t[1];
+  out->residual_ms = t[2];
+  out->grad_ms = t[3];
+  out->deriv_ms = t[4];
+  return GM_OK;
 }
 
 size_t gm_fit_adam_workspace_bytes(const gm_model_desc* desc, const gm_batch* batch) {

@@ -32,7 +32,8 @@ EXPORTS = ("gm_version", "gm_last_error", "gm_model_workspace_bytes", "gm_model"
            "gm_chi2_grad_workspace_bytes", "gm_chi2_grad", "gm_fit_workspace_bytes", "gm_fit_batch",
            "gm_fit_last_stats", "gm_chi2_grad_noalloc", "gm_grad_adjoint_workspace_bytes", "gm_grad_adjoint",
            "gm_tune_set", "gm_tune_clear", "gm_tune_last_shape", "gm_fit_adam_workspace_bytes", "gm_fit_adam",
-           "gm_bootstrap_workspace_bytes", "gm_bootstrap_counts", "gm_bootstrap", "gm_test_starve_next_pass")
+           "gm_bootstrap_workspace_bytes", "gm_bootstrap_counts", "gm_bootstrap", "gm_test_starve_next_pass",
+           "gm_grad_adjoint_last_stats")
 
 
 class GMError(RuntimeError):
@@ -86,6 +87,16 @@ class gm_fit_opts(ctypes.Structure):
         ("polish", ctypes.c_int32),
         ("canonical", ctypes.c_int32),
         ("lambda_inout", ctypes.c_void_p),
+    ]
+
+
+class gm_adjoint_stats(ctypes.Structure):
+    _fields_ = [
+        ("setup_ms", ctypes.c_double),
+        ("resid_ms", ctypes.c_double),
+        ("residual_ms", ctypes.c_double),
+        ("grad_ms", ctypes.c_double),
+        ("deriv_ms", ctypes.c_double),
     ]
 
 
@@ -170,6 +181,8 @@ def load() -> ctypes.CDLL:
         lib.gm_grad_adjoint_workspace_bytes.argtypes = [P, P]
         lib.gm_grad_adjoint.restype = ctypes.c_int
         lib.gm_grad_adjoint.argtypes = [P, P, P, P, P, P, S, P]
+        lib.gm_grad_adjoint_last_stats.restype = ctypes.c_int
+        lib.gm_grad_adjoint_last_stats.argtypes = [P]
         lib.gm_fit_last_stats.restype = ctypes.c_int
         lib.gm_fit_last_stats.argtypes = [P]
         lib.gm_bootstrap_workspace_bytes.restype = S
@@ -548,6 +561,14 @@ def gm_tune_last_shape() -> tuple[int, int, int]:
     a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().gm_tune_last_shape(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "gm_tune_last_shape")
     return a.value, b.value, c.value
+
+
+def gm_grad_adjoint_last_stats() -> dict:
+    """Kernel times (ms) of this thread's last gm_grad_adjoint: setup_ms, resid_ms, residual_ms, grad_ms,
+    deriv_ms."""
+    st = gm_adjoint_stats()
+    _check(load().gm_grad_adjoint_last_stats(ctypes.byref(st)), "gm_grad_adjoint_last_stats")
+    return {name: getattr(st, name) for name, _ in gm_adjoint_stats._fields_}
 
 
 def gm_fit_last_stats() -> dict:

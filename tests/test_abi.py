@@ -218,6 +218,12 @@ def test_many_parameter_models_size_their_workspace(lib):
         assert lib.gm_fit_workspace_bytes(ctypes.byref(d), ctypes.byref(b)) > 0
 
 
+def test_adjoint_stats_before_any_call(lib):
+    st = gm.gm_adjoint_stats()
+    assert lib.gm_grad_adjoint_last_stats(ctypes.byref(st)) == -1
+    assert lib.gm_grad_adjoint_last_stats(None) == -1
+
+
 def test_fit_stats_before_any_fit(lib):
     st = gm.gm_fit_stats()
     assert lib.gm_fit_last_stats(ctypes.byref(st)) == -1

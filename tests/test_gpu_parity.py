@@ -346,6 +346,24 @@ def test_grad_adjoint_matches_normal_equations(gm, draw, G, H, W, K):
         assert (np.abs(grad[gi] - rgrad[gi]) <= bound + 1e-300).all(), gi
 
 
+def test_grad_adjoint_kernel_times(gm):
+    # the library's CUDA events around the pass's kernel groups: all positive, summing to
+    # about the call's own event time
+    import torch
+    c = from_batch(synth.draw_bulge_bar_nucleus(seed=4, G=64), at="init")
+    t = c.torch()
+    call = lambda: gm.gm_grad_adjoint(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"])
+    call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call()
+    e1.record()
+    st = gm.gm_grad_adjoint_last_stats()
+    torch.cuda.synchronize()
+    assert all(v > 0 for v in st.values()), st
+    assert sum(st.values()) <= e0.elapsed_time(e1) * 1.05 + 0.05, (st, e0.elapsed_time(e1))
+
+
 def test_grad_adjoint_vs_oracle_finite_differences(gm):
     # 64 galaxies of the bulge + bar + nucleus model (96x96, K = 41): d chi^2 / dp against
     # central FP64 finite differences of the oracle's chi^2 (relative step 1e-6)
