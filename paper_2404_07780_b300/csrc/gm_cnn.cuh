@@ -289,16 +289,32 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const __grid_constant__ GemmA
       if (*s_flag) break;
     }
     const int k0 = kb + kt * kBK;
-    // A: 128 rows x 8 k-chunks; consecutive threads take consecutive rows of one chunk
-    for (int c = tid; c < kBM * 8; c += kThreads) {
-      const int row = c & (kBM - 1), kc = c >> 7;
-      const uint4 v = load_a<OP>(G, m0 + row, k0 + kc * 8);
-      *reinterpret_cast<uint4*>(sa + core_off(row, kc)) = v;
+    // A: 128 rows x 8 k-chunks, B: BN rows x 8; consecutive threads take consecutive rows
+    // of one chunk.  Every load of the slice is issued before any store, so that a thread
+    // has all of them in flight at once (a load followed by its store in each loop
+    // iteration waited one memory latency per chunk).
+    constexpr int NA = kBM * 8 / kThreads, NB = BN * 8 / kThreads;
+    static_assert(NA * kThreads == kBM * 8 && NB * kThreads == BN * 8, "whole chunks per thread");
+    uint4 va[NA], vb[NB];
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      const int c = tid + r * kThreads, row = c & (kBM - 1), kc = c >> 7;
+      va[r] = load_a<OP>(G, m0 + row, k0 + kc * 8);
     }
-    for (int c = tid; c < BN * 8; c += kThreads) {
-      const int row = c % BN, kc = c / BN;
-      const uint4 v = load_b<OP>(G, n0 + row, k0 + kc * 8);
-      *reinterpret_cast<uint4*>(sb + core_off(row, kc)) = v;
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const int c = tid + r * kThreads, row = c % BN, kc = c / BN;
+      vb[r] = load_b<OP>(G, n0 + row, k0 + kc * 8);
+    }
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      const int c = tid + r * kThreads, row = c & (kBM - 1), kc = c >> 7;
+      *reinterpret_cast<uint4*>(sa + core_off(row, kc)) = va[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const int c = tid + r * kThreads, row = c % BN, kc = c / BN;
+      *reinterpret_cast<uint4*>(sb + core_off(row, kc)) = vb[r];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
     __syncthreads();
@@ -319,6 +335,42 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const __grid_constant__ GemmA
 
   // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31
   const int row = m0 + warp * 32 + lane;
+  if (G.out_bf && !G.out_f && !G.mask) {
+    // BF16 tile through shared memory (the operand stages are free once every MMA has
+    // completed): each thread writes its row's 8-column runs, then consecutive threads
+    // copy consecutive 16-byte runs of a row to global memory (coalesced)
+    constexpr int PITCH = BN * 2 + 16;  // bytes per tile row; the 16-byte pad spreads rows over the banks
+    static_assert(kBM * PITCH <= 2 * STAGE, "the output tile fits the operand stages");
+    unsigned char* so = smem;
+    for (int j = 0; j < BN; j += 8) {
+      float v[8];
+      if (nk > 0) tc_ld8(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)j, v);
+      else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
+      }
+      bf16 o[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int col = n0 + j + e;
+        float t = v[e];
+        if (G.bias && col < G.N) t += G.bias[col];
+        if (G.relu) t = fmaxf(t, 0.f);
+        o[e] = __float2bfloat16(t);
+      }
+      *reinterpret_cast<uint4*>(so + (warp * 32 + lane) * PITCH + j * 2) = pack8(o);
+    }
+    __syncthreads();
+    if (ok) {
+      for (int c = tid; c < kBM * (BN / 8); c += kThreads) {
+        const int r = c / (BN / 8), ch = c - r * (BN / 8);
+        const int grow = m0 + r, col = n0 + ch * 8;
+        if (grow < G.M && col < G.N)  // N is a multiple of 8: a run is wholly inside or outside
+          *reinterpret_cast<uint4*>(G.out_bf + (size_t)grow * G.N + col) =
+              *reinterpret_cast<const uint4*>(so + r * PITCH + ch * 16);
+      }
+    }
+  } else
   for (int j = 0; j < BN; j += 8) {
     float v[8];
     if (nk > 0) tc_ld8(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)j, v);
