@@ -56,8 +56,8 @@ def fused_name(P, shape):
 
 
 # the same for the uneven workload's fused pass (k_fused<NORMAL, 12, 2, WIDE>, the tuned shape), per
-# stamp pixel evaluated (2,613.4 MB for a 2,048-galaxy pass of 45.59 M pixels)
-UNEVEN_DRAM_BYTES_PER_PIXEL = 2613.437e6 / 45591296
+# stamp pixel evaluated (2,616.6 MB for a 2,048-galaxy pass of 45.59 M pixels)
+UNEVEN_DRAM_BYTES_PER_PIXEL = 2616.575e6 / 45591296
 
 
 def workload_config(G, H, K):
