@@ -327,7 +327,7 @@ int gm_test_starve_next_pass(uint32_t polls);
  *                r_c, r_t, fwhm) times q, which leaves the image unchanged,
  *                when those slots are not shared with components of another q
  *   opts         host; NULL = defaults (tol 1e-6, xtol 1e-10, gtol 1e-10, max_iter 100,
- *                lambda0 0.1, up 10, down 0.1, min 1e-7, max 1e10, polish 1, canonical 1,
+ *                lambda0 0.1, up 10, down 0.2, min 1e-7, max 1e10, polish 1, canonical 1,
  *                lambda_inout NULL)
  *   chi2_out     [n_gal] FP64 chi^2 at the best point
  *   dof_out      [n_gal] int32: used pixels - free parameters (Sec. 5.1)

@@ -146,7 +146,7 @@ class FitOptions:
     max_iter: int = 100
     lambda0: float = 1e-1
     lambda_up: float = 10.0
-    lambda_down: float = 0.1
+    lambda_down: float = 0.2
     lambda_min: float = 1e-7
     lambda_max: float = 1e10
     polish: int = 1

@@ -832,7 +832,7 @@ LMOpts lm_opts(const gm_fit_opts* o) {
     L.max_iter = 100;
     L.lambda0 = 0.1;
     L.lambda_up = 10.0;
-    L.lambda_down = 0.1;
+    L.lambda_down = 0.2;
     L.lambda_min = 1e-7;
     L.lambda_max = 1e10;
     L.polish = 1;
