@@ -11,7 +11,12 @@ every LM iteration of fused model+Jacobian+chi^2 pass and FP64 step, final
 covariance).  `value` counts galaxies that ended CONVERGED.  Inputs are 1.2 GB
 per batch, larger than the 126 MB L2, so no flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extra]
+
+On one GPU the default line also carries `other_workloads`: the small, gradient, uneven and
+learned-start workloads, each run once at its full size in a child process after the fit's own
+measurement (a few minutes in all; --no-extra leaves them out, and so does a run on N > 1 GPUs).
+Their figures are context: `value`, `e2e` and `roofline` are the SDSS-shaped fit's.
 
 The reference arm (--impl reference) is the FP64 CPU oracle timed on this
 host's cores on a bounded sample of the same workload.
@@ -441,10 +446,82 @@ def run_gpu(args, world, rank, local):
                 "roofline": roof, "cpu_baseline": cpu, "oracle_match": match, "oracle_match_tight": match_tight,
                 "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks}
+        if world == 1 and not args.no_extra:
+            line["other_workloads"] = run_other_workloads()
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# the other workloads, summarised in the default line
+# ---------------------------------------------------------------------------
+
+# (workload, extra arguments, child time limit in s): each runs at its full size in a process of its
+# own after the SDSS-shaped fit's line is complete, so that nothing there can change that line
+OTHER_WORKLOADS = (("small", (), 180), ("gradient", ("--no-cpu-baseline",), 240),
+                   ("uneven", ("--no-cpu-baseline", "--steps", "1", "--warmup", "1"), 360),
+                   ("learned", ("--steps", "1", "--warmup", "1"), 420))
+
+
+def summarize_workload(name: str, l: dict) -> dict:
+    """The figures of a workload's own JSON line that the default line carries."""
+    keys = ("value", "unit", "ms_per_step", "steps", "warmup", "converged_frac", "mean_iters", "gpu_launches")
+    s = {k: l[k] for k in keys if k in l}
+    s["workload"] = l["config"]["workload"]
+    r = l.get("roofline") or {}
+    s["roofline"] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "pass_frac", "kernel") if k in r}
+    if l.get("e2e"):
+        s["e2e"] = l["e2e"]["value"]
+    c = l.get("clocks") or {}
+    s["clocks"] = {"sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz"), "reasons": c.get("reasons")}
+    if name == "small":
+        s["us_per_iteration"] = l["us_per_iteration"]
+        s["us_per_iteration_kernels"] = l["us_per_iteration_kernels"]
+        if l.get("cpu_baseline"):
+            s["oracle_fits_per_s"] = l["cpu_baseline"]["value"]
+            s["oracle_us_per_iteration"] = l["cpu_baseline"]["us_per_iteration"]
+        if l.get("oracle_match"):
+            s["oracle_match_frac"] = l["oracle_match"]["oracle_match_frac"]
+    elif name == "gradient":
+        s["normal_equations_ms_per_step"] = l["normal_equations_ms_per_step"]
+        s["speedup_vs_normal_equations"] = l["speedup_vs_normal_equations"]
+        s["adam_vs_lm"] = l["adam_vs_lm"]
+    elif name == "learned":
+        s["speedup_vs_default_start"] = l["speedup_vs_default_start"]
+        s["default_start"] = l["default_start"]
+        s["learned_start"] = l["learned_start"]
+        s["inference"] = {k: l["inference"][k] for k in ("ms", "tflops", "frac")}
+        s["train_s"] = l["training"]["train_s"]
+    return s
+
+
+def run_other_workloads() -> dict:
+    """Run every other workload of this file once, in a child process each, and summarise its line;
+    a child that fails or runs out of time is recorded as such."""
+    out = {}
+    for name, extra, limit in OTHER_WORKLOADS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--no-extra", *extra]
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=limit, cwd=_ROOT)
+        except subprocess.TimeoutExpired:
+            out[name] = {"error": f"no line within {limit} s", "args": list(extra)}
+            continue
+        lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+        if r.returncode != 0 or not lines:
+            tail = (r.stderr.strip().splitlines() or ["(no output)"])[-1]
+            out[name] = {"error": f"exit {r.returncode}: {tail[:200]}", "args": list(extra)}
+            continue
+        try:
+            s = summarize_workload(name, json.loads(lines[-1]))
+        except (KeyError, TypeError, ValueError) as e:
+            s = {"error": f"unreadable line: {e!r}"}
+        s["args"] = list(extra)
+        s["wall_s"] = time.perf_counter() - t0
+        out[name] = s
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -1015,6 +1092,8 @@ def main():
     ap.add_argument("--galaxies", type=int, default=None,
                     help="batch size per GPU (default 8192 for fit, 32768 for uneven; profiling runs use less)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="fit workload: leave out the summaries of the other workloads (each run in a child process)")
     ap.add_argument("--train-samples", type=int, default=1 << 20, help="learned workload: training stamps")
     ap.add_argument("--adam-iters", type=int, default=1000, help="gradient workload: Adam steps (the paper's 1,000)")
     ap.add_argument("--epochs", type=int, default=1, help="learned workload: training epochs")
