@@ -990,6 +990,160 @@ def run_learned(args, world, rank, local):
     return 0
 
 
+# algorithmic DRAM bytes of one stamp through the network input preparation and the forward
+# layers: each layer reads its input activation and writes its output once (BF16 NHWC; weights
+# are shared by the batch and negligible per stamp)
+def inference_bytes_per_stamp() -> dict:
+    """Per kernel of Net.predict: the input preparation, the fused first two convolutions (the
+    input read, the second layer's output written), then one kernel per layer."""
+    from paper_2404_07780_b300 import cnn
+    side = 2 * cnn.INPUT_SIDE
+    b = {"prep": side * side * 4 + cnn.INPUT_SIDE * cnn.INPUT_SIDE * 2}
+    hw, feats = cnn.INPUT_SIDE, cnn.INPUT_SIDE * cnn.INPUT_SIDE
+    for li, (kind, i, o) in enumerate(cnn.LAYERS):
+        last = li == len(cnn.LAYERS) - 1
+        if kind == "conv":
+            hw //= 2
+            out = hw * hw * o
+        else:
+            out = o
+        if li == 0:
+            first = feats * 2
+        elif li == 1:
+            b["conv12"] = first + out * 2
+        else:
+            b[f"{kind}{li + 1}"] = feats * 2 + out * (4 if last else 2)
+        feats = out
+    return b
+
+
+def inference_flops_per_stamp() -> float:
+    from paper_2404_07780_b300 import cnn
+    macs, hw = 0, cnn.INPUT_SIDE
+    for kind, i, o in cnn.LAYERS:
+        if kind == "conv":
+            hw //= 2
+            macs += hw * hw * o * 9 * i
+        else:
+            macs += i * o
+    return 2.0 * macs
+
+
+def run_inference(args, world, rank, local):
+    """The learned initialiser's inference alone: network input preparation (2x2 block mean,
+    asinh) of G float32 128x128 stamps and the forward pass in batches, with the network's seeded
+    initial weights (the timing does not depend on the weights' values).  One step = one predict()
+    of the whole set; each layer is also timed on its own in one extra pass."""
+    import torch
+    from paper_2404_07780_b300 import cnn, gm
+    from paper_2404_07780_b300.build import build_lib
+
+    build_lib()
+    gm.load()
+    cnn.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    G = args.galaxies
+    side = 2 * cnn.INPUT_SIDE
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5000 + rank)
+    image = 2.0 * torch.randn((G, side, side), generator=gen, device=dev)  # sky noise, sigma 2
+    net = cnn.Net(seed=rank, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return net.predict(cnn.prep(image, 1.0 / cnn.SKY_SIGMA), batch=args.infer_batch)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+
+    # each kernel on its own (events between the calls, one pass over the whole set)
+    names = ["prep", "conv12"] + [f"{k}{li + 1}" for li, (k, _, _) in enumerate(cnn.LAYERS) if li >= 2]
+    layer_ms = dict.fromkeys(names, 0.0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+    x = cnn.prep(image, 1.0 / cnn.SKY_SIGMA)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    x = cnn.prep(image, 1.0 / cnn.SKY_SIGMA)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    layer_ms["prep"] = ev[0].elapsed_time(ev[1])
+    for s0 in range(0, G, args.infer_batch):
+        a = x[s0:s0 + args.infer_batch].contiguous()
+        ev[1].record(stream)
+        a = cnn.conv12_fwd(a, net.w(0), net.b(0), net.w(1), net.b(1))
+        ev[2].record(stream)
+        for li in range(2, len(cnn.LAYERS)):
+            kind, i, o = cnn.LAYERS[li]
+            last = li == len(cnn.LAYERS) - 1
+            if kind == "conv":
+                a = cnn.conv_fwd(a, net.w(li), net.b(li), relu=True)
+            else:
+                a = cnn.dense_fwd(a.reshape(a.shape[0], -1), net.w(li), net.b(li), relu=not last, fp32_out=last)
+            ev[li + 1].record(stream)
+        torch.cuda.synchronize()
+        for k in range(1, len(names)):
+            layer_ms[names[k]] += ev[k].elapsed_time(ev[k + 1])
+    bpp = inference_bytes_per_stamp()
+    peaks = {}
+    try:
+        with open(PEAKS_PATH) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm, bf16 = peaks.get("hbm_gbs"), peaks.get("bf16_tflops")
+    flops = inference_flops_per_stamp() * G
+    tflops = flops / (ms / 1e3) / 1e12
+    gbs = sum(bpp.values()) * G / (ms / 1e3) / 1e9
+    layers = {}
+    hw = cnn.INPUT_SIDE // 4
+    for k, name in enumerate(names):
+        t = layer_ms[name]
+        d = {"ms": t, "gbs": bpp[name] * G / (t / 1e3) / 1e9}
+        if k == 1:
+            d["path"] = "fused conv1 + conv2 (tensor cores, conv1 kept in shared memory)"
+        elif k > 1:
+            kind, i, o = cnn.LAYERS[k]
+            last = k == len(cnn.LAYERS) - 1
+            if kind == "conv":
+                d["path"] = ["gather", "tma"][cnn.fwd_path("conv", args.infer_batch, hw, hw, i, o)]
+                hw //= 2
+            else:
+                d["path"] = ["gather", "tma"][cnn.fwd_path("dense", args.infer_batch, 0, 0, i, o, fp32_out=last)]
+        if hbm:
+            d["hbm_frac"] = d["gbs"] / hbm
+        layers[name] = d
+    line = {"metric": "CNN initialiser inference (input preparation + forward)", "value": G / (ms / 1e3),
+            "unit": "stamps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (FP32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": f"{G} float32 128x128 stamps (sky noise) -> 64x64 BF16 input -> 4 conv + 2 dense "
+                                   f"layers (the first two fused), batches of {args.infer_batch}", "stamps": G, "batch": args.infer_batch,
+                       "l2": f"inputs {G * side * side * 4 / 1e9:.1f} GB > 126 MB L2 (no flush)"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm if hbm else None, "traffic": None,
+                         "algorithmic_bytes_per_stamp": sum(bpp.values()),
+                         "kernel": "whole inference (prep, fused conv1+conv2, 4 more layers): each kernel's input read once, "
+                                   "output written once",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+            "tensor": {"tflops": tflops, "bf16_peak_tflops": bf16, "frac": tflops / bf16 if bf16 else None,
+                       "flops_per_stamp": inference_flops_per_stamp()},
+            "layers": layers, "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def run_gradient(args, world, rank, local):
     """Gradient workload: d chi^2/dp of the bulge + bar + nucleus + sky model (15 free
     parameters) for 4,096 galaxies of 96x96 with a 41x41 Moffat PSF, by the adjoint
@@ -1097,13 +1251,15 @@ def main():
     ap.add_argument("--train-samples", type=int, default=1 << 20, help="learned workload: training stamps")
     ap.add_argument("--adam-iters", type=int, default=1000, help="gradient workload: Adam steps (the paper's 1,000)")
     ap.add_argument("--epochs", type=int, default=1, help="learned workload: training epochs")
-    ap.add_argument("--workload", default="fit", choices=["fit", "uneven", "gradient", "learned", "small"],
+    ap.add_argument("--infer-batch", type=int, default=16384, help="inference workload: stamps per forward batch")
+    ap.add_argument("--workload", default="fit",
+                    choices=["fit", "uneven", "gradient", "learned", "small", "inference"],
                     help="fit: the LM fit of the SDSS-shaped batch (default); uneven: bulge+disk fits on stamps and "
                          "PSFs of mixed size; gradient: adjoint chi^2 gradient; learned: the CNN start; small: 16 "
-                         "stamps of 64x64 (time per LM iteration)")
+                         "stamps of 64x64 (time per LM iteration); inference: the CNN initialiser's forward pass")
     args = ap.parse_args()
     if args.galaxies is None:
-        args.galaxies = {"uneven": 32768, "learned": 65536, "small": 16}.get(args.workload, 8192)
+        args.galaxies = {"uneven": 32768, "learned": 65536, "small": 16, "inference": 65536}.get(args.workload, 8192)
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
@@ -1115,6 +1271,8 @@ def main():
         return run_learned(args, world, rank, local)
     if args.workload == "small":
         return run_small(args, world, rank, local)
+    if args.workload == "inference":
+        return run_inference(args, world, rank, local)
     return run_gpu(args, world, rank, local)
 
 

@@ -21,7 +21,9 @@
  *     y[b][i][j][o] = b[o] + sum_{ky,kx,c} x[b][2i+ky-1][2j+kx-1][c] w[o][ky][kx][c]
  *   (x = 0 outside the image), followed by max(0, .) when relu is set.
  *   Channel counts and feature counts are multiples of 8 (a convolution's
- *   input may also have 1 channel).  `stream` is a cudaStream_t (NULL = legacy
+ *   input may also have 1 channel).  Every device operand (activations,
+ *   weights, gradients, masks, workspaces) starts on a 16-byte boundary;
+ *   GM_CNN_E_INVAL otherwise.  `stream` is a cudaStream_t (NULL = legacy
  *   default stream); calls only enqueue work.
  *   Returns GM_CNN_OK or a negative code; gm_cnn_last_error() describes the
  *   calling thread's last failure.  A kernel whose internal wait gives up
@@ -48,9 +50,34 @@ const char *gm_cnn_last_error(void);
  * work (synchronous; host int). */
 int gm_cnn_check_error(int *flag);
 
+/* Kernels that compute a forward layer (the value gm_cnn_fwd_path returns). */
+#define GM_CNN_PATH_GATHER 0 /* GEMM whose threads gather the operands into shared memory */
+#define GM_CNN_PATH_TMA 1    /* persistent GEMM fed by tensor-map copies into swizzled tiles */
+
+/* Which kernel gm_cnn_conv_fwd (kind 0: nb, h, w_, ci, co) or gm_cnn_dense_fwd
+ * (kind 1: nb = n, ci = fin, co = fout, fp32_out = an FP32 output is asked for;
+ * h, w_ ignored) runs for these sizes:
+ *   GM_CNN_PATH_TMA: convolution with ci a multiple of 32, h and w even, co a
+ *     multiple of 64, (w/2) dividing 128 and (h/2)(w/2) a multiple or a divisor
+ *     of 128 (a tile of 128 output pixels is whole rows of whole images); dense
+ *     layer with a BF16 output only, fin >= 64 and fout a multiple of 64;
+ *   GM_CNN_PATH_GATHER: every other case.
+ * All paths give the same sums up to FP32 accumulation order.  Host only; returns
+ * GM_CNN_E_INVAL for sizes the layer calls refuse. */
+int gm_cnn_fwd_path(int kind, int nb, int h, int w_, int ci, int co, int fp32_out);
+
 /* Forward convolution: y = [relu](conv3x3_s2(x, w) + b).  b may be NULL. */
 int gm_cnn_conv_fwd(const void *x, const void *w, const float *b, void *y, int nb, int h, int w_, int ci, int co,
                     int relu, void *stream);
+
+/* The network's first two convolutions in one kernel (inference; nothing of the
+ * first layer's output is stored): y = relu(conv3x3_s2(relu(conv3x3_s2(x, w1) + b1),
+ * w2) + b2) for x [nb][64][64][1] BF16, w1 [32][3][3][1] BF16, b1 [32] FP32 (or
+ * NULL), w2 [64][3][3][32] BF16, b2 [64] FP32 (or NULL), y [nb][16][16][64] BF16.
+ * Equal bit for bit to gm_cnn_conv_fwd(x, w1, b1) followed by gm_cnn_conv_fwd(.,
+ * w2, b2), both with relu. */
+int gm_cnn_conv12_fwd(const void *x, const void *w1, const float *b1, const void *w2, const float *b2, void *y,
+                      int nb, void *stream);
 
 /* Gradient of the input: dx = conv3x3_s2^T(dy, w), times (mask > 0) element by
  * element when mask (the ReLU output of the layer below, shaped like dx) is

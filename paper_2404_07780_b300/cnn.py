@@ -69,13 +69,29 @@ def lib():
         L.gm_cnn_mse.argtypes = [P, P, I, I, I, P, P, P]
         L.gm_cnn_adam.restype = I
         L.gm_cnn_adam.argtypes = [P, P, P, P, P, ctypes.c_longlong, F, F, F, F, I, P]
+        L.gm_cnn_fwd_path.restype = I
+        L.gm_cnn_fwd_path.argtypes = [I, I, I, I, I, I, I]
+        L.gm_cnn_conv12_fwd.restype = I
+        L.gm_cnn_conv12_fwd.argtypes = [P, P, P, P, P, P, I, P]
         _cnn = L
     return _cnn
 
 
 EXPORTS = ("gm_cnn_last_error", "gm_cnn_check_error", "gm_cnn_conv_fwd", "gm_cnn_conv_bwd_data",
            "gm_cnn_conv_bwd_weight_workspace", "gm_cnn_conv_bwd_weight", "gm_cnn_dense_fwd", "gm_cnn_dense_bwd_data",
-           "gm_cnn_dense_bwd_weight_workspace", "gm_cnn_dense_bwd_weight", "gm_cnn_prep", "gm_cnn_mse", "gm_cnn_adam")
+           "gm_cnn_dense_bwd_weight_workspace", "gm_cnn_dense_bwd_weight", "gm_cnn_prep", "gm_cnn_mse", "gm_cnn_adam",
+           "gm_cnn_fwd_path", "gm_cnn_conv12_fwd")
+
+PATH_GATHER, PATH_TMA = 0, 1  # kernels of a forward layer (gm_cnn_fwd_path)
+
+
+def fwd_path(kind: str, n: int, h: int, w: int, ci: int, co: int, fp32_out: bool = False) -> int:
+    """The kernel a forward layer of these sizes runs on: PATH_TMA or PATH_GATHER
+    (kind "conv": n x h x w x ci input, co outputs; kind "dense": n rows, ci = fin, co = fout)."""
+    rc = lib().gm_cnn_fwd_path(0 if kind == "conv" else 1, n, h, w, ci, co, int(fp32_out))
+    if rc < 0:
+        raise CNNError(f"fwd_path: sizes refused ({kind} n={n} {h}x{w} ci={ci} co={co})")
+    return rc
 
 
 def _check(rc, what):
@@ -114,6 +130,20 @@ def conv_fwd(x, w, b, relu=True):
     y = torch.empty((n, (h + 1) // 2, (wd + 1) // 2, co), dtype=bf, device=x.device)
     _check(lib().gm_cnn_conv_fwd(_p(_need(x, bf, "x")), _p(_need(w, bf, "w")), _p(_need(b, f32, "b")), _p(y), n, h,
                                  wd, ci, co, int(relu), _stream()), "gm_cnn_conv_fwd")
+    return y
+
+
+def conv12_fwd(x, w1, b1, w2, b2):
+    """The first two convolutions fused (both with ReLU): x [n,64,64,1] bf16 -> [n,16,16,64] bf16."""
+    import torch
+    bf, f32 = torch.bfloat16, torch.float32
+    n = x.shape[0]
+    if tuple(x.shape[1:]) != (64, 64, 1) or tuple(w1.shape) != (32, 3, 3, 1) or tuple(w2.shape) != (64, 3, 3, 32):
+        raise CNNError("conv12_fwd: the network's first two layers on 64x64x1 inputs only")
+    y = torch.empty((n, 16, 16, 64), dtype=bf, device=x.device)
+    _check(lib().gm_cnn_conv12_fwd(_p(_need(x, bf, "x")), _p(_need(w1, bf, "w1")), _p(_need(b1, f32, "b1")),
+                                   _p(_need(w2, bf, "w2")), _p(_need(b2, f32, "b2")), _p(y), n, _stream()),
+           "gm_cnn_conv12_fwd")
     return y
 
 
@@ -338,11 +368,24 @@ class Net:
         self.adam_step(lr)
         return loss
 
-    def predict(self, x, batch: int = 4096):
+    def infer(self, x):
+        """Prediction [n,16] FP32 without keeping activations: the first two convolutions run
+        fused (their result equals forward()'s bit for bit), the rest layer by layer."""
+        a = conv12_fwd(x, self.w(0), self.b(0), self.w(1), self.b(1))
+        for li in range(2, len(LAYERS)):
+            kind, i, o = LAYERS[li]
+            last = li == len(LAYERS) - 1
+            if kind == "conv":
+                a = conv_fwd(a, self.w(li), self.b(li), relu=True)
+            else:
+                a = dense_fwd(a.reshape(a.shape[0], -1), self.w(li), self.b(li), relu=not last, fp32_out=last)
+        return a
+
+    def predict(self, x, batch: int = 16384):
         import torch
         out = torch.empty((x.shape[0], OUT), dtype=torch.float32, device=x.device)
         for s in range(0, x.shape[0], batch):
-            out[s:s + batch] = self.forward(x[s:s + batch].contiguous())[1]
+            out[s:s + batch] = self.infer(x[s:s + batch].contiguous())
         return out
 
 

@@ -2,6 +2,8 @@
 // BF16 tensor-core GEMMs for 3x3 stride-2 convolutions and dense layers,
 // forward and backward, plus the input preparation, the loss, bias-gradient
 // sums, split-K reduction and the Adam update.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -9,10 +11,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 
 #include "../../include/gm_cnn.h"
 #include "gm_cnn.cuh"
+#include "gm_cnn_fwd.cuh"
 
 using namespace gm::cnn;
 
@@ -120,6 +124,227 @@ int run_gemm(int op, GemmArgs G, int splits, cudaStream_t st, int* used = nullpt
   return GM_CNN_OK;
 }
 
+// ---------------------------------------------------------------------------
+// forward layers on the TMA path (k_fwd) and the fused first two convolutions (k_conv12)
+// ---------------------------------------------------------------------------
+// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
+int encode_fn(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CNN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !f) return fail(GM_CNN_E_CUDA, "cuTensorMapEncodeTiled is not available");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  *out = fn;
+  return GM_CNN_OK;
+}
+
+// BF16 tensor map: dims[0] innermost, byte strides of dims 1.., box and traversal strides.
+int encode_bf16(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                const cuuint32_t* box, const cuuint32_t* estr, CUtensorMapSwizzle sw) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  int rc = encode_fn(&enc);
+  if (rc) return rc;
+  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return fail(GM_CNN_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  return GM_CNN_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Every operand 16-byte aligned (NULL counts as aligned: optional operands are checked for
+// presence separately); the kernels move BF16 rows in 16-byte units.
+bool all16(std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (!aligned16(p)) return false;
+  return true;
+}
+
+#define CNN_ALIGNED(what, ...)                                                         \
+  do {                                                                                 \
+    if (!all16({__VA_ARGS__}))                                                         \
+      return fail(GM_CNN_E_INVAL, "%s: operands must be 16-byte aligned", what);       \
+  } while (0)
+
+// Geometry of a convolution on the TMA path: the 128 output pixels of a tile are TH
+// full-width rows of TB images.  False when the layer does not fit the path.
+bool conv_tile(int H, int W, int ci, int co, int* TH, int* TB) {
+  if (ci < 32 || ci % 32 != 0 || co % 64 != 0 || (H & 1) || (W & 1) || H < 2 || W < 2) return false;
+  const int Ho = H / 2, Wo = W / 2, P = Ho * Wo;
+  if (128 % Wo != 0 || 2 * Wo > 256) return false;
+  if (P >= 128) {
+    if (P % 128 != 0) return false;
+    *TH = 128 / Wo;
+    *TB = 1;
+  } else {
+    if (128 % P != 0) return false;
+    *TH = Ho;
+    *TB = 128 / P;
+  }
+  return 2 * *TH <= 256 && *TB <= 256;
+}
+
+int fwd_path(int kind, int H, int W, int ci, int co, int fp32_out) {
+  if (kind == 0) {
+    int th = 0, tb = 0;
+    return conv_tile(H, W, ci, co, &th, &tb) ? GM_CNN_PATH_TMA : GM_CNN_PATH_GATHER;
+  }
+  return (!fp32_out && ci >= 64 && ci % 8 == 0 && co % 64 == 0) ? GM_CNN_PATH_TMA : GM_CNN_PATH_GATHER;
+}
+
+// Shared-memory stages: as many as fit beside the output tile in ~200 KB for 128-byte
+// operand rows (one block per SM); six for 64-byte rows (two blocks per SM).
+int fwd_stages(int BN, int KC) {
+  if (KC == 32) return 6;
+  const int stage = (kBM + BN) * KC * 2;
+  return std::max(2, std::min(8, (200 * 1024 - (BN / 64) * kOutHalf - 1024 - 256) / stage));
+}
+
+template <int BN, int KC>
+int launch_fwd(FwdArgs& F, cudaStream_t st) {
+  void (*k)(FwdArgs) = k_fwd<BN, KC>;
+  F.stages = fwd_stages(BN, KC);
+  const int smem = fwd_smem_bytes(BN, KC, F.stages);
+  CNN_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int occ = 0;
+  CNN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kFwdThreads, smem));
+  const int grid = std::max(1, std::min(F.n_tiles, sms() * std::max(occ, 1)));
+  k<<<grid, kFwdThreads, smem, st>>>(F);
+  CNN_LAUNCHED("k_fwd");
+  return GM_CNN_OK;
+}
+
+int run_fwd(FwdArgs& F, int BN, int KC, cudaStream_t st) {
+  if (BN == 128) return KC == 64 ? launch_fwd<128, 64>(F, st) : launch_fwd<128, 32>(F, st);
+  return KC == 64 ? launch_fwd<64, 64>(F, st) : launch_fwd<64, 32>(F, st);
+}
+
+int fwd_common(FwdArgs& F, const float* b, int relu, int M, int N, void* y) {
+  F.M = M;
+  F.N = N;
+  F.bias = b;
+  F.relu = relu;
+  int rc = err_flag(&F.err);
+  if (rc) return rc;
+  const int BN = N % 128 == 0 ? 128 : 64;
+  F.n_ntiles = N / BN;
+  F.n_tiles = ((M + kBM - 1) / kBM) * F.n_ntiles;
+  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+  const cuuint64_t strides[1] = {(cuuint64_t)N * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode_bf16(&F.tc, 2, y, dims, strides, box, estr, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+int conv_fwd_tma(const void* x, const void* w, const float* b, void* y, int nb, int H, int W, int ci, int co,
+                 int relu, cudaStream_t st) {
+  int TH = 0, TB = 0;
+  conv_tile(H, W, ci, co, &TH, &TB);
+  const int Ho = H / 2, Wo = W / 2, KC = ci % 64 == 0 ? 64 : 32;
+  FwdArgs F;
+  std::memset(&F, 0, sizeof(F));
+  int rc = fwd_common(F, b, relu, nb * Ho * Wo, co, y);
+  if (rc) return rc;
+  const int BN = co / F.n_ntiles;
+  const CUtensorMapSwizzle sw = KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)ci, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nb};
+    const cuuint64_t strides[3] = {(cuuint64_t)ci * 2, (cuuint64_t)W * ci * 2, (cuuint64_t)H * W * ci * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)KC, (cuuint32_t)(2 * Wo), (cuuint32_t)(2 * TH), (cuuint32_t)TB};
+    const cuuint32_t estr[4] = {1, 2, 2, 1};
+    rc = encode_bf16(&F.ta, 4, x, dims, strides, box, estr, sw);
+    if (rc) return rc;
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)9 * ci, (cuuint64_t)co};
+    const cuuint64_t strides[1] = {(cuuint64_t)9 * ci * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)BN};
+    const cuuint32_t estr[2] = {1, 1};
+    rc = encode_bf16(&F.tb, 2, w, dims, strides, box, estr, sw);
+    if (rc) return rc;
+  }
+  F.conv = 1;
+  F.cchunks = ci / KC;
+  F.Ci = ci;
+  F.P = Ho * Wo;
+  F.Wo = Wo;
+  F.nk = 9 * F.cchunks;
+  return run_fwd(F, BN, KC, st);
+}
+
+int dense_fwd_tma(const void* x, const void* w, const float* b, void* y, int n, int fin, int fout, int relu,
+                  cudaStream_t st) {
+  FwdArgs F;
+  std::memset(&F, 0, sizeof(F));
+  int rc = fwd_common(F, b, relu, n, fout, y);
+  if (rc) return rc;
+  const int BN = fout / F.n_ntiles;
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)fin, (cuuint64_t)n, 1, 1};
+    const cuuint64_t row = (cuuint64_t)fin * 2;
+    const cuuint64_t strides[3] = {row, row * (cuuint64_t)n, row * (cuuint64_t)n};
+    const cuuint32_t box[4] = {64, (cuuint32_t)kBM, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    rc = encode_bf16(&F.ta, 4, x, dims, strides, box, estr, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)fin, (cuuint64_t)fout};
+    const cuuint64_t strides[1] = {(cuuint64_t)fin * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)BN};
+    const cuuint32_t estr[2] = {1, 1};
+    rc = encode_bf16(&F.tb, 2, w, dims, strides, box, estr, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+  }
+  F.conv = 0;
+  F.nk = (fin + 63) / 64;
+  return run_fwd(F, BN, 64, st);
+}
+
+int conv12(const void* x, const void* w1, const float* b1, const void* w2, const float* b2, void* y, int nb,
+           cudaStream_t st) {
+  Conv12Args C;
+  std::memset(&C, 0, sizeof(C));
+  int rc = err_flag(&C.err);
+  if (rc) return rc;
+  const cuuint32_t e2[2] = {1, 1}, e3[3] = {1, 1, 1};
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)kC12In, (cuuint64_t)kC12In, (cuuint64_t)nb};
+    const cuuint64_t strides[2] = {(cuuint64_t)kC12In * 2, (cuuint64_t)kC12In * kC12In * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kC12In, (cuuint32_t)kC12Rows, 1};
+    rc = encode_bf16(&C.tx, 3, x, dims, strides, box, e3, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (rc) return rc;
+  }
+  {
+    const cuuint64_t dims[2] = {288, 64};
+    const cuuint64_t strides[1] = {288 * 2};
+    const cuuint32_t box[2] = {32, 64};
+    rc = encode_bf16(&C.tw2, 2, w2, dims, strides, box, e2, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (rc) return rc;
+  }
+  {
+    const cuuint64_t dims[2] = {64, (cuuint64_t)nb * 256};
+    const cuuint64_t strides[1] = {64 * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)kBM};
+    rc = encode_bf16(&C.ty, 2, y, dims, strides, box, e2, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+  }
+  C.w1 = (const bf16*)w1;
+  C.b1 = b1;
+  C.b2 = b2;
+  C.n_tiles = 2 * nb;
+  CNN_CUDA(cudaFuncSetAttribute((const void*)k_conv12, cudaFuncAttributeMaxDynamicSharedMemorySize, kC12Smem));
+  k_conv12<<<std::min(C.n_tiles, sms()), kC12Threads, kC12Smem, st>>>(C);
+  CNN_LAUNCHED("k_conv12");
+  return GM_CNN_OK;
+}
+
 GemmArgs blank() {
   GemmArgs G;
   std::memset(&G, 0, sizeof(G));
@@ -215,6 +440,14 @@ extern "C" {
 
 const char* gm_cnn_last_error(void) { return g_cnn_err; }
 
+int gm_cnn_fwd_path(int kind, int nb, int h, int w, int ci, int co, int fp32_out) {
+  if (kind == 0) return bad_conv(nb, h, w, ci, co) ? GM_CNN_E_INVAL : fwd_path(0, h, w, ci, co, 0);
+  if (kind == 1)
+    return (nb < 0 || ci < 1 || co < 1 || ci % 8 != 0 || co % 8 != 0) ? GM_CNN_E_INVAL
+                                                                          : fwd_path(1, 0, 0, ci, co, fp32_out);
+  return GM_CNN_E_INVAL;
+}
+
 int gm_cnn_check_error(int* flag) {
   int* d = nullptr;
   int rc = err_flag(&d);
@@ -229,6 +462,10 @@ int gm_cnn_conv_fwd(const void* x, const void* w, const float* b, void* y, int n
                     int relu, void* stream) {
   if (bad_conv(nb, H, W, ci, co) || !x || !w || !y)
     return fail(GM_CNN_E_INVAL, "conv_fwd: bad arguments (nb=%d %dx%d ci=%d co=%d)", nb, H, W, ci, co);
+  CNN_ALIGNED("conv_fwd", x, w, y);
+  if (nb == 0) return GM_CNN_OK;
+  const int path = fwd_path(0, H, W, ci, co, 0);
+  if (path == GM_CNN_PATH_TMA) return conv_fwd_tma(x, w, b, y, nb, H, W, ci, co, relu, (cudaStream_t)stream);
   GemmArgs G = blank();
   G.Ho = (H + 1) / 2;
   G.Wo = (W + 1) / 2;
@@ -244,10 +481,19 @@ int gm_cnn_conv_fwd(const void* x, const void* w, const float* b, void* y, int n
   return run_gemm(CONV_FWD, G, 1, (cudaStream_t)stream);
 }
 
+int gm_cnn_conv12_fwd(const void* x, const void* w1, const float* b1, const void* w2, const float* b2, void* y,
+                      int nb, void* stream) {
+  if (nb < 0 || !x || !w1 || !w2 || !y) return fail(GM_CNN_E_INVAL, "conv12_fwd: bad arguments (nb=%d)", nb);
+  CNN_ALIGNED("conv12_fwd", x, w1, w2, y);
+  if (nb == 0) return GM_CNN_OK;
+  return conv12(x, w1, b1, w2, b2, y, nb, (cudaStream_t)stream);
+}
+
 int gm_cnn_conv_bwd_data(const void* dy, const void* w, const void* mask, void* dx, int nb, int H, int W, int ci,
                          int co, void* stream) {
   if (bad_conv(nb, H, W, ci, co) || ci % 8 != 0 || !dy || !w || !dx)
     return fail(GM_CNN_E_INVAL, "conv_bwd_data: bad arguments (nb=%d %dx%d ci=%d co=%d)", nb, H, W, ci, co);
+  CNN_ALIGNED("conv_bwd_data", dy, w, mask, dx);
   GemmArgs G = blank();
   G.Ho = (H + 1) / 2;
   G.Wo = (W + 1) / 2;
@@ -271,6 +517,7 @@ int gm_cnn_conv_bwd_weight(const void* x, const void* dy, float* dw, float* db, 
                            void* workspace, size_t ws_bytes, void* stream) {
   if (bad_conv(nb, H, W, ci, co) || !x || !dy || !dw)
     return fail(GM_CNN_E_INVAL, "conv_bwd_weight: bad arguments (nb=%d %dx%d ci=%d co=%d)", nb, H, W, ci, co);
+  CNN_ALIGNED("conv_bwd_weight", x, dy, workspace);
   if (!workspace || ws_bytes < gm_cnn_conv_bwd_weight_workspace(nb, H, W, ci, co))
     return fail(GM_CNN_E_NOMEM, "conv_bwd_weight: workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
@@ -302,6 +549,10 @@ int gm_cnn_dense_fwd(const void* x, const void* w, const float* b, void* y_bf16,
                      int fout, int relu, void* stream) {
   if (n < 0 || fin < 1 || fout < 1 || fin % 8 != 0 || fout % 8 != 0 || !x || !w || (!y_bf16 && !y_f32))
     return fail(GM_CNN_E_INVAL, "dense_fwd: bad arguments (n=%d fin=%d fout=%d)", n, fin, fout);
+  CNN_ALIGNED("dense_fwd", x, w, y_bf16, y_f32);
+  if (n == 0) return GM_CNN_OK;
+  if (!y_f32 && fwd_path(1, 0, 0, fin, fout, 0) == GM_CNN_PATH_TMA)
+    return dense_fwd_tma(x, w, b, y_bf16, n, fin, fout, relu, (cudaStream_t)stream);
   GemmArgs G = blank();
   G.M = n;
   G.N = fout;
@@ -320,6 +571,7 @@ int gm_cnn_dense_bwd_data(const void* dy, const void* w, const void* mask, void*
                           void* stream) {
   if (n < 0 || fin < 1 || fout < 1 || fin % 8 != 0 || fout % 8 != 0 || !dy || !w || !dx)
     return fail(GM_CNN_E_INVAL, "dense_bwd_data: bad arguments (n=%d fin=%d fout=%d)", n, fin, fout);
+  CNN_ALIGNED("dense_bwd_data", dy, w, mask, dx);
   GemmArgs G = blank();
   G.M = n;
   G.N = fin;
@@ -341,6 +593,7 @@ int gm_cnn_dense_bwd_weight(const void* x, const void* dy, float* dw, float* db,
                             void* workspace, size_t ws_bytes, void* stream) {
   if (n < 0 || fin < 1 || fout < 1 || fin % 8 != 0 || fout % 8 != 0 || !x || !dy || !dw)
     return fail(GM_CNN_E_INVAL, "dense_bwd_weight: bad arguments (n=%d fin=%d fout=%d)", n, fin, fout);
+  CNN_ALIGNED("dense_bwd_weight", x, dy, workspace);
   if (!workspace || ws_bytes < gm_cnn_dense_bwd_weight_workspace(n, fin, fout))
     return fail(GM_CNN_E_NOMEM, "dense_bwd_weight: workspace too small");
   cudaStream_t st = (cudaStream_t)stream;

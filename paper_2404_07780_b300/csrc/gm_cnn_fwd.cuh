@@ -1,0 +1,662 @@
+// gm_cnn_fwd.cuh -- forward layers of the learned initialiser on the TMA path.
+//
+// k_fwd: C[M][N] = relu(A B^T + bias) in BF16 for the 3x3 stride-2 convolutions
+// with 32 or more input channels and for the hidden dense layer.  A persistent,
+// warp-specialised kernel:
+//   * warp 0, one thread: tensor-map copies (cp.async.bulk.tensor) of the A and B
+//     slices of a tile into a ring of shared-memory stages, each signalled on its
+//     "full" mbarrier by the copy's byte count;
+//   * warp 1: allocates 2 x BN TMEM columns (two accumulators), and one thread
+//     issues tcgen05.mma (M = 128, N = BN, K = 16 each) on each stage, whose
+//     completion tcgen05.commit signals on the stage's "empty" mbarrier; the last
+//     slice of a tile commits to the accumulator's "full" barrier;
+//   * warps 2-5: the epilogue.  tcgen05.ld of the accumulator (warp w reads TMEM
+//     lanes 32 (w % 4) ..), bias and ReLU, BF16 into a swizzled shared-memory tile,
+//     the accumulator released to the MMA thread, and one tensor-map store per
+//     64 columns.  With two accumulators the epilogue of tile i overlaps the MMAs
+//     of tile i + 1.
+// Operand layouts are the K-major swizzled ones the copies write and the MMA
+// descriptors name: rows of KC BF16 (128 bytes with the 128-byte swizzle for
+// KC = 64, 64 bytes with the 64-byte swizzle for KC = 32), 8-row groups 8 KC x 2
+// bytes apart; the K step of 16 elements moves the start address by 32 bytes.
+//
+// The convolution's im2col operand needs no gather: for tap (ky, kx) and channel
+// chunk c, the A slice of 128 output pixels (b, y, x) is the box of the NHWC input
+// tensor at (c KC, kx - 1, 2 y0 + ky - 1, b0) with traversal stride 2 in the two
+// spatial dimensions (Wo x TH x TB elements land, TH x TB images' rows of full
+// width), zero-filled outside the image.  K runs over (tap, channel) in the
+// order of the weights [co][3][3][ci].
+//
+// k_conv12: the network's first two convolutions fused for inference (below).
+#pragma once
+
+#include <cuda.h>
+
+#include "gm_cnn.cuh"
+
+namespace gm {
+namespace cnn {
+
+constexpr int kFwdThreads = 192;  // warp 0: copies; warp 1: TMEM and MMA; warps 2-5: epilogue
+constexpr int kOutHalf = kBM * 128;  // one 64-column BF16 half of an output tile (bytes)
+// Polls of one wait before it gives up: a wait lasts microseconds (one tile's copies and
+// MMAs), a poll tens of nanoseconds or more.
+constexpr unsigned kFwdWait = 1u << 22;
+
+struct FwdArgs {
+  CUtensorMap ta;  // A: conv -- NHWC input (ci, w, h, n), box (KC, 2 Wo, 2 TH, TB), strides (1, 2, 2, 1);
+                   //    dense -- (K, M, 1, 1), box (KC, 128, 1, 1)
+  CUtensorMap tb;  // B: weights [N][K], box (KC, BN)
+  CUtensorMap tc;  // output [M][N] BF16, box (64, 128), 128-byte swizzle
+  int M, N;
+  int n_ntiles;    // N / BN
+  int n_tiles;     // ceil(M / 128) * n_ntiles
+  int nk;          // K slices of a tile
+  int conv;        // 1: A is the convolution input
+  int cchunks;     // conv: channel chunks of KC per tap (ci / KC)
+  int Ci;          // conv: input channels
+  int P;           // conv: output pixels per image (Ho Wo; a multiple or a divisor of 128)
+  int Wo;          // conv: output width (a divisor of 128)
+  int stages;      // shared-memory stages of the ring
+  const float* bias;  // [N] or nullptr
+  int relu;
+  int* err;        // set when a wait gives up
+};
+
+__device__ __forceinline__ void mbar_init_n(u64* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(u64* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(u64* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait that also gives up soon after another role of the block has given up.
+__device__ __forceinline__ bool fwd_wait(u64* bar, unsigned parity, volatile int* abort) {
+  for (unsigned t = 0; t < kFwdWait; ++t) {
+    if (mbar_test(bar, parity)) return true;
+    if ((t & 255u) == 255u && *abort) return false;
+  }
+  return false;
+}
+
+// Bounded wait with no early exit (the copies and MMAs in flight when a block leaves).
+__device__ __forceinline__ bool fwd_drain(u64* bar, unsigned parity) {
+  for (unsigned t = 0; t < kFwdWait; ++t)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fwd_fail(volatile int* abort, int* err) {
+  *abort = 1;
+  atomicExch(err, 1);
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            u64* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<u64>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<u64>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<u64>(map)),
+               "r"(c0), "r"(c1), "r"(smem_addr(src))
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void named_sync(unsigned id, unsigned n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Barrier over n threads that returns whether any of them passed true (the same answer in all).
+__device__ __forceinline__ bool named_any(unsigned id, unsigned n, bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void tc_ld16(unsigned addr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+// Shared-memory descriptor of a K-major swizzled operand: start address, leading
+// byte offset 16 (unused by these layouts), stride byte offset = one 8-row group,
+// version bits 46-48 = 0b001, swizzle mode at bits 61-63 (2: 128-byte, 4: 64-byte).
+template <int KC>
+__device__ __forceinline__ u64 sw_desc(unsigned saddr) {
+  constexpr unsigned sbo = 8u * KC * 2u;
+  constexpr u64 mode = KC == 64 ? 2 : 4;
+  u64 d = (u64)((saddr & 0x3FFFFu) >> 4);
+  d |= (u64)1 << 16;
+  d |= (u64)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (u64)1 << 46;
+  d |= mode << 61;
+  return d;
+}
+
+// Dynamic shared memory of k_fwd<BN, KC> with `stages` stages (1,024 bytes of
+// alignment slack included).
+__host__ __device__ constexpr int fwd_smem_bytes(int BN, int KC, int stages) {
+  return 1024 + stages * (kBM + BN) * KC * 2 + (BN / 64) * kOutHalf + (2 * stages + 5) * 8 + 16;
+}
+
+template <int BN, int KC>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ FwdArgs F) {
+  static_assert(KC == 32 || KC == 64, "64- or 128-byte operand rows");
+  static_assert(BN % 64 == 0 && BN <= 128, "output tiles of whole 64-column halves");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  constexpr int A_BYTES = kBM * KC * 2, B_BYTES = BN * KC * 2, STAGE = A_BYTES + B_BYTES;
+  constexpr int OUT_BYTES = (BN / 64) * kOutHalf;
+  constexpr unsigned ncols = 2 * BN;
+  const int S = F.stages;
+  unsigned char* s_out = smem + S * STAGE;
+  u64* full = reinterpret_cast<u64*>(s_out + OUT_BYTES);
+  u64* empty = full + S;
+  u64* tfull = empty + S;
+  u64* tempty = tfull + 2;
+  u64* drain = tempty + 2;
+  unsigned* s_tmem = reinterpret_cast<unsigned*>(drain + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init_n(&full[s], 1);
+      mbar_init_n(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init_n(&tfull[a], 1);
+      mbar_init_n(&tempty[a], 128);
+    }
+    mbar_init_n(drain, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&F.ta)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&F.tb)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&F.tc)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- copies ----
+      unsigned g = 0;  // slices issued (over every tile of this block)
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < F.n_tiles; t += gridDim.x) {
+        const int mt = t / F.n_ntiles, n0 = (t - mt * F.n_ntiles) * BN, m0 = mt * kBM;
+        int b0 = 0, y0 = 0;
+        if (F.conv) {
+          b0 = m0 / F.P;
+          y0 = (m0 - b0 * F.P) / F.Wo;
+        }
+        for (int j = 0; j < F.nk; ++j, ++g) {
+          const int s = (int)(g % (unsigned)S);
+          if (g >= (unsigned)S && !fwd_wait(&empty[s], ((g / S) - 1) & 1u, s_abort)) {
+            fwd_fail(s_abort, F.err);
+            ok = false;
+            break;
+          }
+          unsigned char* sa = smem + s * STAGE;
+          mbar_expect_tx(&full[s], STAGE);
+          int kb;
+          if (F.conv) {
+            const int tap = j / F.cchunks, ch = j - tap * F.cchunks, ky = tap / 3, kx = tap - 3 * ky;
+            tma_load_4d(sa, &F.ta, ch * KC, kx - 1, 2 * y0 + ky - 1, b0, &full[s]);
+            kb = tap * F.Ci + ch * KC;
+          } else {
+            tma_load_4d(sa, &F.ta, j * KC, m0, 0, 0, &full[s]);
+            kb = j * KC;
+          }
+          tma_load_2d(sa + A_BYTES, &F.tb, kb, n0, &full[s]);
+        }
+      }
+      if (!ok) {  // the copies still in flight land before the block leaves
+        for (unsigned h = g > (unsigned)S ? g - S : 0u; h < g; ++h) fwd_drain(&full[h % S], (h / S) & 1u);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA ----
+      constexpr unsigned idesc = idesc_bf16(kBM, BN);
+      unsigned g = 0;
+      int i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < F.n_tiles; t += gridDim.x, ++i) {
+        const int acc = i & 1;
+        if (i >= 2 && !fwd_wait(&tempty[acc], ((i >> 1) - 1) & 1, s_abort)) {
+          fwd_fail(s_abort, F.err);
+          break;
+        }
+        tc_fence_after();
+        const unsigned d = tmem + (unsigned)(acc * BN);
+        for (int j = 0; j < F.nk; ++j, ++g) {
+          const int s = (int)(g % (unsigned)S);
+          if (!fwd_wait(&full[s], (g / S) & 1u, s_abort)) {
+            fwd_fail(s_abort, F.err);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const unsigned a0 = smem_addr(smem + s * STAGE), b0 = a0 + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk)
+            tc_mma(d, sw_desc<KC>(a0 + kk * 32), sw_desc<KC>(b0 + kk * 32), idesc, (j | kk) ? 1u : 0u);
+          tc_commit(&empty[s]);
+        }
+        if (ok) tc_commit(&tfull[acc]);
+      }
+      tc_commit(drain);  // arrives once every MMA issued above has completed
+      fwd_drain(drain, 0);
+    }
+  } else {
+    // ---- epilogue: 128 threads, tile row r = TMEM lane ----
+    const int q = warp & 3, r = q * 32 + lane, et = threadIdx.x - 64;
+    int i = 0;
+    for (int t = blockIdx.x; t < F.n_tiles; t += gridDim.x, ++i) {
+      const int mt = t / F.n_ntiles, n0 = (t - mt * F.n_ntiles) * BN, m0 = mt * kBM;
+      const int acc = i & 1;
+      bool bad = false;
+      if (lane == 0) bad = !fwd_wait(&tfull[acc], (i >> 1) & 1, s_abort);
+      __syncwarp();
+      if (named_any(1, 128, bad)) {  // the same decision in every epilogue thread
+        if (bad) fwd_fail(s_abort, F.err);
+        break;
+      }
+      tc_fence_after();
+      if (et == 0) bulk_wait_read0();  // the previous tile's stores have read the staging tile
+      named_sync(1, 128);
+      const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(acc * BN);
+#pragma unroll 1
+      for (int j = 0; j < BN; j += 16) {
+        float v[16];
+        tc_ld16(taddr + (unsigned)j, v);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          bf16 o[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float x = v[h * 8 + e];
+            if (F.bias) x += F.bias[n0 + j + h * 8 + e];
+            if (F.relu) x = fmaxf(x, 0.f);
+            o[e] = __float2bfloat16(x);
+          }
+          const int c = (j >> 3) + h;  // 8-column chunk of the tile row
+          unsigned char* dst = s_out + (c >> 3) * kOutHalf + r * 128 + (((c & 7) ^ (r & 7)) << 4);
+          *reinterpret_cast<uint4*>(dst) = pack8(o);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);  // the accumulator may take the next tile
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      named_sync(1, 128);
+      if (et == 0) {
+#pragma unroll
+        for (int h = 0; h < BN / 64; ++h) tma_store_2d(&F.tc, s_out + h * kOutHalf, n0 + h * 64, m0);
+        bulk_commit();
+      }
+    }
+    if (et == 0) bulk_wait0();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the first two convolutions fused (inference)
+// ---------------------------------------------------------------------------
+// y2 = relu(conv3x3_s2(relu(conv3x3_s2(x, w1) + b1), w2) + b2) for 64x64 single-channel
+// images, with conv1 (1 -> 32 channels, 32x32) kept in shared memory.  A tile is 8 rows x 16
+// columns of one image's conv2 output (16x16, 64 channels: 128 TMEM lanes).  It needs conv1
+// at rows 2 y0 - 1 .. 2 y0 + 15 and columns -1 .. 31 (17 x 33 positions p = 33 rr + cc;
+// those at -1 are conv2's zero padding), which need input rows 4 y0 - 3 .. 4 y0 + 31 (one
+// 35 x 64 tensor-map box, zero-filled above the image).  Per tile:
+//   1. im2col of conv1: row p holds the 9 input values of position p and 7 zeros (K = 16,
+//      no-swizzle K-major core matrices); five MMAs (M = 128, N = 32, K = 16) give conv1 for
+//      640 rows in TMEM;
+//   2. the conv1 rows come back through tcgen05.ld: + b1, ReLU, BF16, zero at the padding
+//      positions, into a dense [561][32] tile in shared memory;
+//   3. the nine tap operands of conv2 are copied out of it (tap (ky, kx), row m = (y - y0) 16
+//      + x holds position (2 (y - y0) + ky, 2 x + kx); 32 channels in a 64-byte row with the
+//      64-byte swizzle) and 18 MMAs (N = 64, K = 16) accumulate conv2;
+//   4. the epilogue of the previous tile runs while the tensor cores work: TMEM -> + b2,
+//      ReLU, BF16 -> swizzled staging tile -> one tensor-map store.
+// conv1 is the same single K = 16 MMA per row as the gathered GEMM's (whose other K steps add
+// zero products) and conv2 the same 18 K steps as k_fwd's, so the output equals the two layers
+// run one after the other bit for bit.  One block per SM, persistent, 512 threads; the next
+// tile's input rows are fetched during the current one.
+constexpr int kC12Threads = 512;
+constexpr int kC12In = 64;                   // input side
+constexpr int kC12Rows = 35;                 // input rows of a tile
+constexpr int kC12Pos = 17 * 33;             // conv1 positions of a tile
+constexpr int kC12Rows1 = 640;               // conv1 GEMM rows (5 MMAs of 128)
+constexpr int kC12Pitch = 80;                // bytes per conv1 position in shared memory (64 + 16)
+constexpr int kC12B = 0;                     // conv2 weights: 9 taps x [64][32], 64-byte swizzle
+constexpr int kC12A = 9 * 4096;              // conv2 A operands: 9 taps x [128][32], 64-byte swizzle
+constexpr int kC12X = kC12A + 9 * 8192;      // input rows: 2 buffers x [35][64] BF16
+constexpr int kC12XBuf = 5120;
+constexpr int kC12Out = kC12X + 2 * kC12XBuf;  // output staging [128][64] BF16, 128-byte swizzle
+constexpr int kC12A1 = kC12Out + kOutHalf;     // conv1 im2col [640][16], core matrices
+constexpr int kC12C1 = kC12A1 + kC12Rows1 * 32;  // conv1 output [561][32] BF16, 80-byte pitch
+constexpr int kC12B1 = kC12C1 + 44 * 1024;       // conv1 weights [32][16], core matrices
+constexpr int kC12Bias = kC12B1 + 1024;          // b1 [32], b2 [64] FP32
+constexpr int kC12Bar = kC12Bias + 512;
+constexpr int kC12Smem = 1024 + kC12Bar + 64;
+constexpr unsigned kC12Cols = 512;  // TMEM: conv2 accumulators at 0 and 64, conv1 at 128 + 32 b
+static_assert(kC12A % 1024 == 0 && kC12X % 1024 == 0 && kC12Out % 1024 == 0 && kC12A1 % 1024 == 0 &&
+                  kC12C1 % 1024 == 0 && kC12B1 % 1024 == 0 && kC12Pos * kC12Pitch <= 44 * 1024,
+              "aligned regions");
+static_assert(kC12Threads / 4 == kBM, "one tap copy per thread and tap");
+
+struct Conv12Args {
+  CUtensorMap tx;   // input [nb][64][64] BF16: dims (64, 64, nb), box (64, 35, 1), zero fill
+  CUtensorMap tw2;  // conv2 weights [64][288] BF16: box (32, 64), 64-byte swizzle
+  CUtensorMap ty;   // output [nb * 256][64] BF16: box (64, 128), 128-byte swizzle
+  const bf16* w1;   // conv1 weights [32][3][3][1]
+  const float* b1;  // [32] or nullptr
+  const float* b2;  // [64] or nullptr
+  int n_tiles;      // 2 nb
+  int* err;
+};
+
+__device__ __forceinline__ void tma_load_3d_cnn(void* dst, const CUtensorMap* map, int c0, int c1, int c2, u64* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<u64>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// byte offset of 16-byte chunk kc (0, 1) of row r in a no-swizzle K-major [rows][16] operand
+__device__ __forceinline__ unsigned k16_off(int r, int kc) {
+  return (unsigned)((r >> 3) * 256 + kc * 128 + (r & 7) * 16);
+}
+
+// 8 FP32 accumulator values + 8 biases, ReLU (or zero at a padding position), as 8 BF16
+__device__ __forceinline__ uint4 bias_relu8(const float* v, const float* b, bool zero) {
+  const float4 b0 = *reinterpret_cast<const float4*>(b), b1 = *reinterpret_cast<const float4*>(b + 4);
+  const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  bf16 o[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) o[e] = __float2bfloat16(zero ? 0.f : fmaxf(v[e] + bb[e], 0.f));
+  return pack8(o);
+}
+
+__global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant__ Conv12Args C) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  u64* xfull = reinterpret_cast<u64*>(smem + kC12Bar);  // [2] input rows of a buffer landed
+  u64* mma = xfull + 2;                                  // [2] conv2 MMAs of an accumulator done
+  u64* bfull = mma + 2;                                  // conv2 weights landed
+  u64* d1 = bfull + 1;                                   // conv1 MMAs done
+  u64* drain = d1 + 1;
+  unsigned* s_tmem = reinterpret_cast<unsigned*>(drain + 1);
+  float* s_b1 = reinterpret_cast<float*>(smem + kC12Bias);
+  float* s_b2 = s_b1 + 32;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr unsigned kXBytes = kC12Rows * kC12In * 2;
+  constexpr unsigned idesc2 = idesc_bf16(kBM, 64), idesc1 = idesc_bf16(kBM, 32);
+  unsigned char* A2 = smem + kC12A;
+  unsigned char* A1 = smem + kC12A1;
+  unsigned char* C1 = smem + kC12C1;
+  unsigned char* out = smem + kC12Out;
+
+  if (tid == 0) {
+    for (int k = 0; k < 7; ++k) mbar_init_n(&xfull[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.tx)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.tw2)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.ty)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                 "r"(kC12Cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // conv1 weights as the B operand (row co = the 9 taps and 7 zeros), the biases, and the
+  // im2col rows past the last position (zero for good)
+  if (tid < 64) {
+    const int co = tid >> 1, kc = tid & 1;
+    bf16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = kc * 8 + e;
+      v[e] = k < 9 ? C.w1[co * 9 + k] : __float2bfloat16(0.f);
+    }
+    *reinterpret_cast<uint4*>(smem + kC12B1 + k16_off(co, kc)) = pack8(v);
+  } else if (tid < 64 + 96) {
+    const int k = tid - 64;
+    if (k < 32) s_b1[k] = C.b1 ? C.b1[k] : 0.f;
+    else s_b2[k - 32] = C.b2 ? C.b2[k - 32] : 0.f;
+  }
+  for (int k = tid; k < (kC12Rows1 - kC12Pos) * 2; k += kC12Threads)
+    *reinterpret_cast<uint4*>(A1 + k16_off(kC12Pos + (k >> 1), k & 1)) = zero4();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *s_tmem;
+
+  unsigned x_issued = 0, x_done = 0;  // input-row loads issued and waited for (thread 0)
+  bool bad = false;
+  if (tid == 0) {
+    mbar_expect_tx(bfull, 9 * 4096);
+    for (int tap = 0; tap < 9; ++tap) tma_load_2d(smem + kC12B + tap * 4096, &C.tw2, tap * 32, 0, bfull);
+    if ((int)blockIdx.x < C.n_tiles) {
+      const int t = blockIdx.x;
+      mbar_expect_tx(&xfull[0], kXBytes);
+      tma_load_3d_cnn(smem + kC12X, &C.tx, 0, 32 * (t & 1) - 3, t >> 1, &xfull[0]);
+      ++x_issued;
+    }
+    bad = !fwd_drain(bfull, 0);
+  }
+  bool ok = !__syncthreads_or(bad);
+
+  // this thread's tap copies: row m, chunk ch of every tap tile (one per tap)
+  const int cp_ch = tid & 3, cp_m = tid >> 2;
+  const int cp_src = ((2 * (cp_m >> 4)) * 33 + 2 * (cp_m & 15)) * kC12Pitch + cp_ch * 16;
+  const int cp_dst = cp_m * 64 + ((cp_ch ^ ((cp_m >> 1) & 3)) << 4);
+  const int q = warp & 3, grp = warp >> 2;  // TMEM lane quarter and column group of this warp
+
+  // epilogue of tile t from conv2 accumulator s (its MMA commit of use parity)
+  auto epilogue = [&](int t, int s, unsigned parity) -> bool {
+    bool b = false;
+    if (tid == 0) b = !fwd_drain(&mma[s], parity);
+    if (__syncthreads_or(b)) return false;
+    tc_fence_after();
+    if (tid == 0) bulk_wait_read0();  // the previous store has read the staging tile
+    __syncthreads();
+    const int r = q * 32 + lane;
+    float v[16];
+    tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(s * 64 + grp * 16), v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = grp * 2 + h;
+      *reinterpret_cast<uint4*>(out + r * 128 + ((c ^ (r & 7)) << 4)) = bias_relu8(v + h * 8, s_b2 + c * 8, false);
+    }
+    tc_fence_before();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_2d(&C.ty, out, 0, t * kBM);
+      bulk_commit();
+    }
+    return true;
+  };
+
+  int i = 0, prev = -1;
+  for (int t = blockIdx.x; ok && t < C.n_tiles; t += gridDim.x, ++i) {
+    const int s = i & 1;
+    if (tid == 0) {
+      const int tn = t + gridDim.x;  // the next tile's input rows, into the other buffer
+      if (tn < C.n_tiles) {
+        mbar_expect_tx(&xfull[s ^ 1], kXBytes);
+        tma_load_3d_cnn(smem + kC12X + (s ^ 1) * kC12XBuf, &C.tx, 0, 32 * (tn & 1) - 3, tn >> 1, &xfull[s ^ 1]);
+        ++x_issued;
+      }
+      bad = !fwd_drain(&xfull[s], (i >> 1) & 1);
+      if (!bad) ++x_done;
+    }
+    if (__syncthreads_or(bad)) {
+      ok = false;
+      break;
+    }
+    const int y0 = 8 * (t & 1);
+    // 1. im2col of conv1: row p = 33 rr + cc, input rows 2 rr + ky of the box, columns 2 c + kx - 1
+    {
+      const unsigned char* X = smem + kC12X + s * kC12XBuf;
+      for (int p = tid; p < kC12Pos; p += kC12Threads) {
+        const int rr = p / 33, cc = p - rr * 33;
+        const int r = 2 * y0 - 1 + rr, c = cc - 1;
+        unsigned v[5] = {0u, 0u, 0u, 0u, 0u};
+        if (r >= 0 && c >= 0) {
+          unsigned e[9];
+#pragma unroll
+          for (int ky = 0; ky < 3; ++ky) {
+            const unsigned char* row = X + (2 * rr + ky) * (kC12In * 2);
+            const unsigned pair = *reinterpret_cast<const unsigned*>(row + 4 * c);  // columns 2c, 2c + 1
+            e[ky * 3] = c > 0 ? *reinterpret_cast<const unsigned short*>(row + 4 * c - 2) : 0u;
+            e[ky * 3 + 1] = pair & 0xFFFFu;
+            e[ky * 3 + 2] = pair >> 16;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[k] = e[2 * k] | (e[2 * k + 1] << 16);
+          v[4] = e[8];
+        }
+        *reinterpret_cast<uint4*>(A1 + k16_off(p, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<uint4*>(A1 + k16_off(p, 1)) = make_uint4(v[4], 0u, 0u, 0u);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const unsigned a0 = smem_addr(A1), b0 = smem_addr(smem + kC12B1);
+#pragma unroll
+      for (int b = 0; b < kC12Rows1 / kBM; ++b)
+        tc_mma(tmem + 128u + (unsigned)(32 * b), smem_desc(a0 + b * (kBM * 32), 128, 256), smem_desc(b0, 128, 256),
+               idesc1, 0u);
+      tc_commit(d1);
+    }
+    // 4. the previous tile's epilogue while conv1's MMAs run
+    if (prev >= 0 && !epilogue(prev, s ^ 1, ((i - 1) >> 1) & 1)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) bad = !fwd_drain(d1, i & 1);
+    if (__syncthreads_or(bad)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    // 2. conv1 back from TMEM: 10 jobs of 16 columns per lane quarter (block b = j / 2, columns
+    //    16 (j % 2)), dealt to the quarter's four warps
+    for (int j = grp; j < 2 * (kC12Rows1 / kBM); j += 4) {
+      const int b = j >> 1, hcol = j & 1;
+      float v[16];
+      tc_ld16(tmem + ((unsigned)(q * 32) << 16) + 128u + (unsigned)(32 * b + 16 * hcol), v);
+      const int p = b * kBM + q * 32 + lane;
+      if (p < kC12Pos) {
+        const int rr = p / 33, cc = p - rr * 33;
+        const bool pad = (2 * y0 - 1 + rr) < 0 || cc == 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int ch = 2 * hcol + h;
+          *reinterpret_cast<uint4*>(C1 + p * kC12Pitch + ch * 16) = bias_relu8(v + h * 8, s_b1 + ch * 8, pad);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    // 3. the tap operands of conv2 out of the conv1 tile, then its 18 MMAs
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap - 3 * ky;
+      *reinterpret_cast<uint4*>(A2 + tap * 8192 + cp_dst) =
+          *reinterpret_cast<const uint4*>(C1 + cp_src + (ky * 33 + kx) * kC12Pitch);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const unsigned a0 = smem_addr(A2), b0 = smem_addr(smem + kC12B);
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          tc_mma(tmem + (unsigned)(s * 64), sw_desc<32>(a0 + tap * 8192 + kk * 32), sw_desc<32>(b0 + tap * 4096 + kk * 32),
+                 idesc2, (tap | kk) ? 1u : 0u);
+      tc_commit(&mma[s]);
+    }
+    prev = t;
+  }
+  if (ok && prev >= 0 && !epilogue(prev, (i - 1) & 1, ((i - 1) >> 1) & 1)) ok = false;
+  if (tid == 0) {
+    if (!ok) {
+      atomicExch(C.err, 1);
+      for (unsigned h = x_done; h < x_issued; ++h) fwd_drain(&xfull[h & 1], (h >> 1) & 1);  // loads in flight land
+    }
+    tc_commit(drain);  // arrives once every MMA issued above has completed
+    fwd_drain(drain, 0);
+    bulk_wait0();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kC12Cols) : "memory");
+  }
+}
+
+}  // namespace cnn
+}  // namespace gm

@@ -208,6 +208,52 @@ def test_cnn_entry_points_reject_bad_arguments_on_the_host(lib):
     assert L.gm_cnn_adam(f, f, f, f, None, -1, 0.01, 0.9, 0.999, 1e-8, 1, None) == -1
 
 
+def test_cnn_operands_must_be_16_byte_aligned(lib):
+    # every layer moves BF16 rows in 16-byte units: a misaligned operand is refused on the
+    # host, before any device call
+    from paper_2404_07780_b300 import cnn
+    L = cnn.lib()
+    f, m = ctypes.c_void_p(256), ctypes.c_void_p(256 + 2)  # never dereferenced
+    for args in ((m, f, None, f), (f, m, None, f), (f, f, None, m)):
+        assert L.gm_cnn_conv_fwd(*args, 2, 32, 32, 32, 64, 1, None) == -1
+        assert b"16-byte aligned" in L.gm_cnn_last_error()
+    assert L.gm_cnn_conv_bwd_data(f, f, m, f, 2, 32, 32, 32, 64, None) == -1
+    assert L.gm_cnn_dense_fwd(f, f, None, m, None, 4, 64, 64, 1, None) == -1
+    assert L.gm_cnn_dense_bwd_data(m, f, None, f, 4, 64, 64, None) == -1
+    ws = L.gm_cnn_dense_bwd_weight_workspace(4, 64, 64)
+    assert L.gm_cnn_dense_bwd_weight(f, m, f, None, 4, 64, 64, f, ws, None) == -1
+
+
+def test_cnn_forward_layers_take_the_tensor_map_path(lib):
+    # the network's layers: the single-channel first convolution (K = 9) and the FP32-output
+    # last layer on the gathered GEMM, the other convolutions and the hidden dense layer on
+    # the TMA-fed tensor-core GEMM (inference fuses the first two: gm_cnn_conv12_fwd)
+    from paper_2404_07780_b300 import cnn
+    T, G = cnn.PATH_TMA, cnn.PATH_GATHER
+    side = cnn.INPUT_SIDE
+    hw = side
+    ci = 1
+    got = []
+    for kind, i, o in cnn.LAYERS:
+        if kind == "conv":
+            got.append(cnn.fwd_path("conv", 512, hw, hw, i, o))
+            hw //= 2
+        else:
+            got.append(cnn.fwd_path("dense", 512, 0, 0, i, o, fp32_out=o == cnn.LAYERS[-1][2]))
+    assert got == [G, T, T, T, T, G], got
+    # tiles of 128 output pixels must be whole rows of whole images
+    assert cnn.fwd_path("conv", 3, 13, 9, 8, 16) == G          # odd sides, 8 channels
+    assert cnn.fwd_path("conv", 2, 24, 24, 32, 64) == G        # 12 x 12 output: 144 pixels
+    assert cnn.fwd_path("conv", 2, 32, 32, 32, 96) == G        # co not a multiple of 64
+    assert cnn.fwd_path("conv", 2, 32, 32, 32, 128) == T
+    assert cnn.fwd_path("dense", 7, 0, 0, 2048, 256) == T
+    assert cnn.fwd_path("dense", 7, 0, 0, 32, 64) == G         # fin below one 64-wide slice
+    assert cnn.fwd_path("dense", 7, 0, 0, 256, 264) == G
+    assert cnn.fwd_path("dense", 7, 0, 0, 256, 256, fp32_out=True) == G
+    with pytest.raises(cnn.CNNError):
+        cnn.fwd_path("conv", 2, 32, 32, 12, 16)
+
+
 def test_many_parameter_models_size_their_workspace(lib):
     # bulge+disk (12 free, 13 correlated channels) and bulge+bar+nucleus (15 free) run in
     # several channel-pair passes; the size queries accept them

@@ -53,9 +53,14 @@ def _np(t):
 # large enough for many M tiles
 CONVS = [(4, 64, 64, 1, 32), (4, 32, 32, 32, 64), (4, 16, 16, 64, 128), (4, 8, 8, 128, 128), (3, 13, 9, 8, 16),
          (64, 16, 16, 64, 128)]
+# the tensor-map path's own cases: a last tile with images past the batch (37 and 5 images of
+# 16 and 64 output pixels), every stage/tile shape (64-byte rows with 64 and 128 outputs, 128-byte
+# rows with 64), and tiles that wrap the ring of stages many times
+TMA_CONVS = [(37, 8, 8, 128, 128), (5, 16, 16, 64, 128), (3, 32, 32, 32, 64), (2, 16, 16, 32, 128),
+             (2, 32, 32, 64, 64), (300, 16, 16, 64, 128)]
 
 
-@pytest.mark.parametrize("shape", CONVS)
+@pytest.mark.parametrize("shape", CONVS + TMA_CONVS)
 def test_conv_forward(C, shape):
     n, h, w, ci, co = shape
     rng = np.random.default_rng(1)
@@ -119,6 +124,65 @@ def test_dense_forward_and_backward(C, n, fin, fout):
     _close(_np(dw), ww, np.sqrt((dyr ** 2).T @ (xr ** 2)), False)
     _close(_np(db), wb, np.sqrt((dyr ** 2).sum(0)), False)
     C.check_device_error()
+
+
+@pytest.mark.parametrize("n,fin,fout", [(300, 2048, 256), (129, 64, 64), (1000, 200, 128), (4096, 2048, 256)])
+def test_dense_forward_tma_path(C, n, fin, fout):
+    # BF16 output on the tensor-map path against the oracle, and bit for bit against the
+    # gathered GEMM's FP32 output rounded to BF16: both sum the same K = 16 MMA steps in the
+    # same order, so only the final rounding differs, and it is the same rounding
+    import torch
+    assert C.fwd_path("dense", n, 0, 0, fin, fout) == C.PATH_TMA
+    assert C.fwd_path("dense", n, 0, 0, fin, fout, fp32_out=True) == C.PATH_GATHER
+    rng = np.random.default_rng(6)
+    x, xr = _bf(rng.normal(size=(n, fin)))
+    W, Wr = _bf(rng.normal(size=(fout, fin)) / np.sqrt(fin))
+    b, br = _f32(rng.normal(size=fout) * 0.1)
+    scale = np.sqrt((xr ** 2) @ (Wr ** 2).T + br ** 2)
+    for relu in (False, True):
+        y = C.dense_fwd(x, W, b, relu=relu)
+        _close(_np(y), ref.dense_fwd(xr, Wr, br, relu=relu), scale, True)
+        y32 = C.dense_fwd(x, W, b, relu=relu, fp32_out=True)
+        assert torch.equal(y.view(torch.int16), y32.to(torch.bfloat16).view(torch.int16))
+    C.check_device_error()
+
+
+@pytest.mark.parametrize("n", [1, 3, 300])
+def test_fused_first_two_convolutions(C, n):
+    # the fused kernel equals the two layers it replaces bit for bit (the same single K = 16
+    # MMA per row for the first, the same 18 K steps for the second), and the oracle within
+    # the BF16 bounds; 300 images are 600 tiles, several per block on both accumulators
+    import torch
+    rng = np.random.default_rng(7)
+    x, xr = _bf(rng.normal(size=(n, 64, 64, 1)))
+    w1, w1r = _bf(rng.normal(size=(32, 3, 3, 1)) / 3.0)
+    b1, b1r = _f32(rng.normal(size=32) * 0.1)
+    w2, w2r = _bf(rng.normal(size=(64, 3, 3, 32)) / np.sqrt(9 * 32))
+    b2, b2r = _f32(rng.normal(size=64) * 0.1)
+    y = C.conv12_fwd(x, w1, b1, w2, b2)
+    two = C.conv_fwd(C.conv_fwd(x, w1, b1, relu=True), w2, b2, relu=True)
+    assert torch.equal(y.view(torch.int16), two.view(torch.int16))
+    a1 = _np(C.conv_fwd(x, w1, b1, relu=True))  # the BF16 first layer both paths feed the second
+    want = ref.conv_fwd(a1, w2r, b2r, relu=True)
+    scale = np.sqrt(ref.conv_fwd(a1 ** 2, w2r ** 2) + b2r ** 2)
+    _close(_np(y), want, scale, True)
+    C.check_device_error()
+
+
+def test_predict_equals_forward(C):
+    # inference (fused first layers, batches of any size) against the training forward pass
+    import torch
+    net = C.Net(seed=3, device="cuda")
+    rng = np.random.default_rng(8)
+    x, _ = _bf(np.arcsinh(rng.normal(size=(700, 64, 64, 1)) * 3.0))
+    assert torch.equal(net.predict(x, batch=256), net.forward(x)[1])
+    C.check_device_error()
+
+
+def test_conv_forward_paths_of_the_network(C):
+    # the layers of the network on a training batch, each on the path the sizes select
+    assert [C.fwd_path("conv", 512, h, h, i, o) for h, i, o in ((64, 1, 32), (32, 32, 64), (16, 64, 128),
+                                                                 (8, 128, 128))] == [C.PATH_GATHER] + [C.PATH_TMA] * 3
 
 
 def test_prep_loss_and_adam(C):
