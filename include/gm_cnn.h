@@ -58,9 +58,10 @@ int gm_cnn_check_error(int *flag);
  * (kind 1: nb = n, ci = fin, co = fout, fp32_out = an FP32 output is asked for;
  * h, w_ ignored) runs for these sizes:
  *   GM_CNN_PATH_TMA: convolution with ci a multiple of 32, h and w even, co a
- *     multiple of 64, (w/2) dividing 128 and (h/2)(w/2) a multiple or a divisor
- *     of 128 (a tile of 128 output pixels is whole rows of whole images); dense
- *     layer with a BF16 output only, fin >= 64 and fout a multiple of 64;
+ *     multiple of 64 up to 256, (w/2) dividing 128 and (h/2)(w/2) a multiple or
+ *     a divisor of 128 (a tile of 128 output pixels is whole rows of whole
+ *     images); dense layer with a BF16 output only, fin >= 64 and fout a
+ *     multiple of 64 up to 256;
  *   GM_CNN_PATH_GATHER: every other case.
  * All paths give the same sums up to FP32 accumulation order.  Host only; returns
  * GM_CNN_E_INVAL for sizes the layer calls refuse. */

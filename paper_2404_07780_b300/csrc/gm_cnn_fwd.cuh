@@ -42,6 +42,7 @@ constexpr int kOutHalf = kBM * 128;  // one 64-column BF16 half of an output til
 // Polls of one wait before it gives up: a wait lasts microseconds (one tile's copies and
 // MMAs), a poll tens of nanoseconds or more.
 constexpr unsigned kFwdWait = 1u << 22;
+constexpr int kFwdMaxN = 256;  // output columns of a layer on this path (the bias in shared memory)
 
 struct FwdArgs {
   CUtensorMap ta;  // A: conv -- NHWC input (ci, w, h, n), box (KC, 2 Wo, 2 TH, TB), strides (1, 2, 2, 1);
@@ -167,10 +168,39 @@ __device__ __forceinline__ u64 sw_desc(unsigned saddr) {
   return d;
 }
 
+// round(max(x, 0)) to BF16 for two values, packed (x0 in the low half): the same result as
+// __float2bfloat16(fmaxf(x, 0.f)) element by element, in one instruction
+__device__ __forceinline__ unsigned relu_bf16x2(float x0, float x1) {
+  unsigned r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+
+// round(x) to BF16 for two values, packed (x0 in the low half)
+__device__ __forceinline__ unsigned bf16x2(float x0, float x1) {
+  unsigned r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+
+// 8 FP32 accumulator values + 8 biases (16-byte aligned in shared memory), ReLU, as 8 BF16
+__device__ __forceinline__ uint4 bias_relu8(const float* v, const float* b) {
+  const float4 b0 = *reinterpret_cast<const float4*>(b), b1 = *reinterpret_cast<const float4*>(b + 4);
+  return make_uint4(relu_bf16x2(v[0] + b0.x, v[1] + b0.y), relu_bf16x2(v[2] + b0.z, v[3] + b0.w),
+                    relu_bf16x2(v[4] + b1.x, v[5] + b1.y), relu_bf16x2(v[6] + b1.z, v[7] + b1.w));
+}
+
+// the same without the ReLU
+__device__ __forceinline__ uint4 bias_id8(const float* v, const float* b) {
+  const float4 b0 = *reinterpret_cast<const float4*>(b), b1 = *reinterpret_cast<const float4*>(b + 4);
+  return make_uint4(bf16x2(v[0] + b0.x, v[1] + b0.y), bf16x2(v[2] + b0.z, v[3] + b0.w),
+                    bf16x2(v[4] + b1.x, v[5] + b1.y), bf16x2(v[6] + b1.z, v[7] + b1.w));
+}
+
 // Dynamic shared memory of k_fwd<BN, KC> with `stages` stages (1,024 bytes of
 // alignment slack included).
 __host__ __device__ constexpr int fwd_smem_bytes(int BN, int KC, int stages) {
-  return 1024 + stages * (kBM + BN) * KC * 2 + (BN / 64) * kOutHalf + (2 * stages + 5) * 8 + 16;
+  return 1024 + stages * (kBM + BN) * KC * 2 + (BN / 64) * kOutHalf + kFwdMaxN * 4 + (2 * stages + 5) * 8 + 16;
 }
 
 template <int BN, int KC>
@@ -184,7 +214,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
   constexpr unsigned ncols = 2 * BN;
   const int S = F.stages;
   unsigned char* s_out = smem + S * STAGE;
-  u64* full = reinterpret_cast<u64*>(s_out + OUT_BYTES);
+  float* s_bias = reinterpret_cast<float*>(s_out + OUT_BYTES);  // [N], zeros without a bias
+  u64* full = reinterpret_cast<u64*>(s_bias + kFwdMaxN);
   u64* empty = full + S;
   u64* tfull = empty + S;
   u64* tempty = tfull + 2;
@@ -215,6 +246,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  for (int c = threadIdx.x; c < F.N; c += kFwdThreads) s_bias[c] = F.bias ? F.bias[c] : 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -315,17 +347,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
         tc_ld16(taddr + (unsigned)j, v);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          bf16 o[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            float x = v[h * 8 + e];
-            if (F.bias) x += F.bias[n0 + j + h * 8 + e];
-            if (F.relu) x = fmaxf(x, 0.f);
-            o[e] = __float2bfloat16(x);
-          }
+          const float* b = s_bias + n0 + j + h * 8;
           const int c = (j >> 3) + h;  // 8-column chunk of the tile row
           unsigned char* dst = s_out + (c >> 3) * kOutHalf + r * 128 + (((c & 7) ^ (r & 7)) << 4);
-          *reinterpret_cast<uint4*>(dst) = pack8(o);
+          *reinterpret_cast<uint4*>(dst) = F.relu ? bias_relu8(v + h * 8, b) : bias_id8(v + h * 8, b);
         }
       }
       tc_fence_before();
@@ -362,39 +387,40 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
 //   1. im2col of conv1: row p holds the 9 input values of position p and 7 zeros (K = 16,
 //      no-swizzle K-major core matrices); five MMAs (M = 128, N = 32, K = 16) give conv1 for
 //      640 rows in TMEM;
-//   2. the conv1 rows come back through tcgen05.ld: + b1, ReLU, BF16, zero at the padding
-//      positions, into a dense [561][32] tile in shared memory;
-//   3. the nine tap operands of conv2 are copied out of it (tap (ky, kx), row m = (y - y0) 16
-//      + x holds position (2 (y - y0) + ky, 2 x + kx); 32 channels in a 64-byte row with the
-//      64-byte swizzle) and 18 MMAs (N = 64, K = 16) accumulate conv2;
-//   4. the epilogue of the previous tile runs while the tensor cores work: TMEM -> + b2,
-//      ReLU, BF16 -> swizzled staging tile -> one tensor-map store.
+//   2. the conv1 rows come back through tcgen05.ld: + b1, ReLU, BF16 (zero at the padding
+//      positions), each written straight into the conv2 operand rows that read it: tap (ky, kx),
+//      row m = (y - y0) 16 + x holds position (2 (y - y0) + ky, 2 x + kx) (1, 2 or 4 rows per
+//      position; 32 channels in a 64-byte row with the 64-byte swizzle);
+//   3. 18 MMAs (N = 64, K = 16) accumulate conv2 into one of two TMEM accumulators;
+//   4. the epilogue of the tile two back runs meanwhile: TMEM -> + b2, ReLU, BF16 -> one of two
+//      swizzled staging tiles -> one tensor-map store.
 // conv1 is the same single K = 16 MMA per row as the gathered GEMM's (whose other K steps add
 // zero products) and conv2 the same 18 K steps as k_fwd's, so the output equals the two layers
-// run one after the other bit for bit.  One block per SM, persistent, 512 threads; the next
-// tile's input rows are fetched during the current one.
-constexpr int kC12Threads = 512;
+// run one after the other bit for bit.  One block per SM, persistent: 20 compute warps do
+// steps 1-4; one control thread issues the copies (the next tile's input rows during the
+// current one), both MMA stages and the stores, each on an mbarrier the compute warps arrive
+// on, so the tensor cores and copies never wait for a block-wide barrier.
+constexpr int kC12Compute = 640;             // compute threads (20 warps: 5 per TMEM lane quarter)
+constexpr int kC12Groups = kC12Compute / 128;  // compute warps per lane quarter
+constexpr int kC12Threads = kC12Compute + 32;  // + one control warp
 constexpr int kC12In = 64;                   // input side
 constexpr int kC12Rows = 35;                 // input rows of a tile
 constexpr int kC12Pos = 17 * 33;             // conv1 positions of a tile
 constexpr int kC12Rows1 = 640;               // conv1 GEMM rows (5 MMAs of 128)
-constexpr int kC12Pitch = 80;                // bytes per conv1 position in shared memory (64 + 16)
 constexpr int kC12B = 0;                     // conv2 weights: 9 taps x [64][32], 64-byte swizzle
 constexpr int kC12A = 9 * 4096;              // conv2 A operands: 9 taps x [128][32], 64-byte swizzle
 constexpr int kC12X = kC12A + 9 * 8192;      // input rows: 2 buffers x [35][64] BF16
 constexpr int kC12XBuf = 5120;
-constexpr int kC12Out = kC12X + 2 * kC12XBuf;  // output staging [128][64] BF16, 128-byte swizzle
-constexpr int kC12A1 = kC12Out + kOutHalf;     // conv1 im2col [640][16], core matrices
-constexpr int kC12C1 = kC12A1 + kC12Rows1 * 32;  // conv1 output [561][32] BF16, 80-byte pitch
-constexpr int kC12B1 = kC12C1 + 44 * 1024;       // conv1 weights [32][16], core matrices
+constexpr int kC12Out = kC12X + 2 * kC12XBuf;  // output staging: 2 x [128][64] BF16, 128-byte swizzle
+constexpr int kC12A1 = kC12Out + 2 * kOutHalf;   // conv1 im2col [640][16], core matrices
+constexpr int kC12B1 = kC12A1 + kC12Rows1 * 32;  // conv1 weights [32][16], core matrices
 constexpr int kC12Bias = kC12B1 + 1024;          // b1 [32], b2 [64] FP32
 constexpr int kC12Bar = kC12Bias + 512;
-constexpr int kC12Smem = 1024 + kC12Bar + 64;
+constexpr int kC12Smem = 1024 + kC12Bar + 128;
 constexpr unsigned kC12Cols = 512;  // TMEM: conv2 accumulators at 0 and 64, conv1 at 128 + 32 b
 static_assert(kC12A % 1024 == 0 && kC12X % 1024 == 0 && kC12Out % 1024 == 0 && kC12A1 % 1024 == 0 &&
-                  kC12C1 % 1024 == 0 && kC12B1 % 1024 == 0 && kC12Pos * kC12Pitch <= 44 * 1024,
+                  kC12B1 % 1024 == 0,
               "aligned regions");
-static_assert(kC12Threads / 4 == kBM, "one tap copy per thread and tap");
 
 struct Conv12Args {
   CUtensorMap tx;   // input [nb][64][64] BF16: dims (64, 64, nb), box (64, 35, 1), zero fill
@@ -420,43 +446,56 @@ __device__ __forceinline__ unsigned k16_off(int r, int kc) {
   return (unsigned)((r >> 3) * 256 + kc * 128 + (r & 7) * 16);
 }
 
-// 8 FP32 accumulator values + 8 biases, ReLU (or zero at a padding position), as 8 BF16
-__device__ __forceinline__ uint4 bias_relu8(const float* v, const float* b, bool zero) {
-  const float4 b0 = *reinterpret_cast<const float4*>(b), b1 = *reinterpret_cast<const float4*>(b + 4);
-  const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-  bf16 o[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) o[e] = __float2bfloat16(zero ? 0.f : fmaxf(v[e] + bb[e], 0.f));
-  return pack8(o);
+// A compute warp's wait: lane 0 polls (unless the warp has already failed), the warp learns
+// the outcome; returns false on failure.
+__device__ __forceinline__ bool warp_wait(u64* bar, unsigned parity, volatile int* abort, bool ok) {
+  bool got = ok;
+  if (ok && (threadIdx.x & 31) == 0) got = fwd_wait(bar, parity, abort);
+  return __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+}
+
+__device__ __forceinline__ void warp_arrive(u64* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
 }
 
 __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant__ Conv12Args C) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-  u64* xfull = reinterpret_cast<u64*>(smem + kC12Bar);  // [2] input rows of a buffer landed
-  u64* mma = xfull + 2;                                  // [2] conv2 MMAs of an accumulator done
-  u64* bfull = mma + 2;                                  // conv2 weights landed
-  u64* d1 = bfull + 1;                                   // conv1 MMAs done
-  u64* drain = d1 + 1;
+  u64* xfull = reinterpret_cast<u64*>(smem + kC12Bar);  // [2] input rows of a buffer landed (copy)
+  u64* mma = xfull + 2;        // [2] conv2 MMAs into an accumulator done (commit)
+  u64* bfull = mma + 2;        // conv2 weights landed (copy)
+  u64* d1 = bfull + 1;         // conv1 MMAs done (commit)
+  u64* a1full = d1 + 1;        // im2col written (every compute warp)
+  u64* a2full = a1full + 1;    // tap operands written (every compute warp)
+  u64* outfull = a2full + 1;   // [2] output staging tile written (every compute warp)
+  u64* outfree = outfull + 2;  // [2] output staging tile read by its store (control thread)
+  u64* drain = outfree + 2;
   unsigned* s_tmem = reinterpret_cast<unsigned*>(drain + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
   float* s_b1 = reinterpret_cast<float*>(smem + kC12Bias);
   float* s_b2 = s_b1 + 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr unsigned kXBytes = kC12Rows * kC12In * 2;
-  constexpr unsigned idesc2 = idesc_bf16(kBM, 64), idesc1 = idesc_bf16(kBM, 32);
   unsigned char* A2 = smem + kC12A;
   unsigned char* A1 = smem + kC12A1;
-  unsigned char* C1 = smem + kC12C1;
   unsigned char* out = smem + kC12Out;
+  constexpr int kCtl = kC12Compute / 32;  // the control warp
 
   if (tid == 0) {
-    for (int k = 0; k < 7; ++k) mbar_init_n(&xfull[k], 1);
+    for (int k = 0; k < 5; ++k) mbar_init_n(&xfull[k], 1);  // xfull[2], mma[2], bfull
+    mbar_init_n(d1, 1);
+    mbar_init_n(a1full, kC12Compute / 32);
+    mbar_init_n(a2full, kC12Compute / 32);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init_n(&outfull[k], kC12Compute / 32);
+      mbar_init_n(&outfree[k], 1);
+    }
+    mbar_init_n(drain, 1);
+    *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.tx)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.tw2)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.ty)) : "memory");
   }
-  if (warp == 0) {
+  if (warp == kCtl) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
                  "r"(kC12Cols)
                  : "memory");
@@ -486,173 +525,190 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
   tc_fence_after();
   const unsigned tmem = *s_tmem;
 
-  unsigned x_issued = 0, x_done = 0;  // input-row loads issued and waited for (thread 0)
-  bool bad = false;
-  if (tid == 0) {
-    mbar_expect_tx(bfull, 9 * 4096);
-    for (int tap = 0; tap < 9; ++tap) tma_load_2d(smem + kC12B + tap * 4096, &C.tw2, tap * 32, 0, bfull);
-    if ((int)blockIdx.x < C.n_tiles) {
-      const int t = blockIdx.x;
-      mbar_expect_tx(&xfull[0], kXBytes);
-      tma_load_3d_cnn(smem + kC12X, &C.tx, 0, 32 * (t & 1) - 3, t >> 1, &xfull[0]);
-      ++x_issued;
-    }
-    bad = !fwd_drain(bfull, 0);
-  }
-  bool ok = !__syncthreads_or(bad);
-
-  // this thread's tap copies: row m, chunk ch of every tap tile (one per tap)
-  const int cp_ch = tid & 3, cp_m = tid >> 2;
-  const int cp_src = ((2 * (cp_m >> 4)) * 33 + 2 * (cp_m & 15)) * kC12Pitch + cp_ch * 16;
-  const int cp_dst = cp_m * 64 + ((cp_ch ^ ((cp_m >> 1) & 3)) << 4);
-  const int q = warp & 3, grp = warp >> 2;  // TMEM lane quarter and column group of this warp
-
-  // epilogue of tile t from conv2 accumulator s (its MMA commit of use parity)
-  auto epilogue = [&](int t, int s, unsigned parity) -> bool {
-    bool b = false;
-    if (tid == 0) b = !fwd_drain(&mma[s], parity);
-    if (__syncthreads_or(b)) return false;
-    tc_fence_after();
-    if (tid == 0) bulk_wait_read0();  // the previous store has read the staging tile
-    __syncthreads();
-    const int r = q * 32 + lane;
-    float v[16];
-    tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(s * 64 + grp * 16), v);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = grp * 2 + h;
-      *reinterpret_cast<uint4*>(out + r * 128 + ((c ^ (r & 7)) << 4)) = bias_relu8(v + h * 8, s_b2 + c * 8, false);
-    }
-    tc_fence_before();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      tma_store_2d(&C.ty, out, 0, t * kBM);
-      bulk_commit();
-    }
-    return true;
-  };
-
-  int i = 0, prev = -1;
-  for (int t = blockIdx.x; ok && t < C.n_tiles; t += gridDim.x, ++i) {
-    const int s = i & 1;
-    if (tid == 0) {
-      const int tn = t + gridDim.x;  // the next tile's input rows, into the other buffer
-      if (tn < C.n_tiles) {
-        mbar_expect_tx(&xfull[s ^ 1], kXBytes);
-        tma_load_3d_cnn(smem + kC12X + (s ^ 1) * kC12XBuf, &C.tx, 0, 32 * (tn & 1) - 3, tn >> 1, &xfull[s ^ 1]);
+  if (warp == kCtl) {
+    if (lane == 0) {
+      // ---- control thread: copies, MMAs, stores ----
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.tx)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.ty)) : "memory");
+      constexpr unsigned idesc2 = idesc_bf16(kBM, 64), idesc1 = idesc_bf16(kBM, 32);
+      const u64 da1 = smem_desc(smem_addr(A1), 128, 256), db1 = smem_desc(smem_addr(smem + kC12B1), 128, 256);
+      const u64 da2 = sw_desc<32>(smem_addr(A2)), db2 = sw_desc<32>(smem_addr(smem + kC12B));
+      unsigned x_issued = 0;
+      bool ok = true;
+      mbar_expect_tx(bfull, 9 * 4096);
+      for (int tap = 0; tap < 9; ++tap) tma_load_2d(smem + kC12B + tap * 4096, &C.tw2, tap * 32, 0, bfull);
+      if ((int)blockIdx.x < C.n_tiles) {
+        const int t = blockIdx.x;
+        mbar_expect_tx(&xfull[0], kXBytes);
+        tma_load_3d_cnn(smem + kC12X, &C.tx, 0, 32 * (t & 1) - 3, t >> 1, &xfull[0]);
         ++x_issued;
       }
-      bad = !fwd_drain(&xfull[s], (i >> 1) & 1);
-      if (!bad) ++x_done;
-    }
-    if (__syncthreads_or(bad)) {
-      ok = false;
-      break;
-    }
-    const int y0 = 8 * (t & 1);
-    // 1. im2col of conv1: row p = 33 rr + cc, input rows 2 rr + ky of the box, columns 2 c + kx - 1
-    {
-      const unsigned char* X = smem + kC12X + s * kC12XBuf;
-      for (int p = tid; p < kC12Pos; p += kC12Threads) {
-        const int rr = p / 33, cc = p - rr * 33;
-        const int r = 2 * y0 - 1 + rr, c = cc - 1;
-        unsigned v[5] = {0u, 0u, 0u, 0u, 0u};
-        if (r >= 0 && c >= 0) {
-          unsigned e[9];
-#pragma unroll
-          for (int ky = 0; ky < 3; ++ky) {
-            const unsigned char* row = X + (2 * rr + ky) * (kC12In * 2);
-            const unsigned pair = *reinterpret_cast<const unsigned*>(row + 4 * c);  // columns 2c, 2c + 1
-            e[ky * 3] = c > 0 ? *reinterpret_cast<const unsigned short*>(row + 4 * c - 2) : 0u;
-            e[ky * 3 + 1] = pair & 0xFFFFu;
-            e[ky * 3 + 2] = pair >> 16;
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k) v[k] = e[2 * k] | (e[2 * k + 1] << 16);
-          v[4] = e[8];
+      if (!fwd_wait(bfull, 0, s_abort)) ok = false;
+      int i = 0;
+      for (int t = blockIdx.x; ok && t < C.n_tiles; t += gridDim.x, ++i) {
+        const int s = i & 1;
+        const unsigned ph = i & 1;
+        const int tn = t + gridDim.x;  // the next tile's input rows: the other buffer, free once
+        if (tn < C.n_tiles) {          // im2col of the previous tile is done (waited below)
+          mbar_expect_tx(&xfull[s ^ 1], kXBytes);
+          tma_load_3d_cnn(smem + kC12X + (s ^ 1) * kC12XBuf, &C.tx, 0, 32 * (tn & 1) - 3, tn >> 1, &xfull[s ^ 1]);
+          ++x_issued;
         }
-        *reinterpret_cast<uint4*>(A1 + k16_off(p, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<uint4*>(A1 + k16_off(p, 1)) = make_uint4(v[4], 0u, 0u, 0u);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const unsigned a0 = smem_addr(A1), b0 = smem_addr(smem + kC12B1);
+        if (!fwd_wait(a1full, ph, s_abort)) { ok = false; break; }
+        tc_fence_after();
 #pragma unroll
-      for (int b = 0; b < kC12Rows1 / kBM; ++b)
-        tc_mma(tmem + 128u + (unsigned)(32 * b), smem_desc(a0 + b * (kBM * 32), 128, 256), smem_desc(b0, 128, 256),
-               idesc1, 0u);
-      tc_commit(d1);
+        for (int b = 0; b < kC12Rows1 / kBM; ++b)
+          tc_mma(tmem + 128u + (unsigned)(32 * b), da1 + (u64)((b * kBM * 32) >> 4), db1, idesc1, 0u);
+        tc_commit(d1);
+        if (i >= 2) {  // the output of the tile two back (staging buffer i % 2), once written
+          if (!fwd_wait(&outfull[s], ((i - 2) >> 1) & 1, s_abort)) { ok = false; break; }
+          tma_store_2d(&C.ty, out + s * kOutHalf, 0, (t - 2 * (int)gridDim.x) * kBM);
+          bulk_commit();
+        }
+        if (!fwd_wait(a2full, ph, s_abort)) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+            tc_mma(tmem + (unsigned)(s * 64), da2 + (u64)((tap * 8192 + kk * 32) >> 4),
+                   db2 + (u64)((tap * 4096 + kk * 32) >> 4), idesc2, (tap | kk) ? 1u : 0u);
+        tc_commit(&mma[s]);
+        if (i >= 2) {
+          bulk_wait_read0();
+          mbar_arrive(&outfree[s]);
+        }
+      }
+      for (int j = i >= 2 ? i - 2 : 0; ok && j < i; ++j) {  // the last two tiles' outputs
+        if (!fwd_wait(&outfull[j & 1], (j >> 1) & 1, s_abort)) {
+          ok = false;
+          break;
+        }
+        tma_store_2d(&C.ty, out + (j & 1) * kOutHalf, 0, (blockIdx.x + j * (int)gridDim.x) * kBM);
+        bulk_commit();
+      }
+      if (!ok) {
+        fwd_fail(s_abort, C.err);
+        for (unsigned h = x_issued > 2 ? x_issued - 2 : 0u; h < x_issued; ++h)
+          fwd_drain(&xfull[h & 1], (h >> 1) & 1);  // the input loads in flight land
+      }
+      tc_commit(drain);  // arrives once every MMA issued above has completed
+      fwd_drain(drain, 0);
+      bulk_wait0();
     }
-    // 4. the previous tile's epilogue while conv1's MMAs run
-    if (prev >= 0 && !epilogue(prev, s ^ 1, ((i - 1) >> 1) & 1)) {
-      ok = false;
-      break;
-    }
-    if (tid == 0) bad = !fwd_drain(d1, i & 1);
-    if (__syncthreads_or(bad)) {
-      ok = false;
-      break;
-    }
-    tc_fence_after();
-    // 2. conv1 back from TMEM: 10 jobs of 16 columns per lane quarter (block b = j / 2, columns
-    //    16 (j % 2)), dealt to the quarter's four warps
-    for (int j = grp; j < 2 * (kC12Rows1 / kBM); j += 4) {
-      const int b = j >> 1, hcol = j & 1;
-      float v[16];
-      tc_ld16(tmem + ((unsigned)(q * 32) << 16) + 128u + (unsigned)(32 * b + 16 * hcol), v);
-      const int p = b * kBM + q * 32 + lane;
-      if (p < kC12Pos) {
-        const int rr = p / 33, cc = p - rr * 33;
-        const bool pad = (2 * y0 - 1 + rr) < 0 || cc == 0;
+  } else {
+    // ---- compute warps ----
+    const int q = warp & 3, grp = warp >> 2;  // TMEM lane quarter and column group of this warp
+
+    // staging buffer j % 2 of tile number j (this block's j-th) from conv2 accumulator j % 2; the
+    // buffer is free once the store of tile j - 2 has read it
+    auto epilogue = [&](int j, bool ok) -> bool {
+      ok = warp_wait(&mma[j & 1], (j >> 1) & 1, s_abort, ok);
+      if (j >= 2) ok = warp_wait(&outfree[j & 1], ((j - 2) >> 1) & 1, s_abort, ok);
+      if (ok && grp < 4) {  // four column groups of 16
+        tc_fence_after();
+        const int r = q * 32 + lane;
+        unsigned char* o = out + (j & 1) * kOutHalf;
+        float v[16];
+        tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)((j & 1) * 64 + grp * 16), v);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int ch = 2 * hcol + h;
-          *reinterpret_cast<uint4*>(C1 + p * kC12Pitch + ch * 16) = bias_relu8(v + h * 8, s_b1 + ch * 8, pad);
+          const int c = grp * 2 + h;
+          *reinterpret_cast<uint4*>(o + r * 128 + ((c ^ (r & 7)) << 4)) = bias_relu8(v + h * 8, s_b2 + c * 8);
         }
+        tc_fence_before();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      if (ok) warp_arrive(&outfull[j & 1]);
+      return ok;
+    };
+
+    int i = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; ok && t < C.n_tiles; t += gridDim.x, ++i) {
+      const int s = i & 1;
+      const int y0 = 8 * (t & 1);
+      // 1. im2col of conv1: row p = 33 rr + cc, input rows 2 rr + ky of the box, columns 2 c + kx - 1
+      //    (A1 is free: the conv1 MMAs of the previous tile are done, waited below)
+      ok = warp_wait(&xfull[s], (i >> 1) & 1, s_abort, ok);
+      if (ok) {
+        const unsigned char* X = smem + kC12X + s * kC12XBuf;
+        for (int p = tid; p < kC12Pos; p += kC12Compute) {
+          const int rr = p / 33, cc = p - rr * 33;
+          const int r = 2 * y0 - 1 + rr, c = cc - 1;
+          unsigned v[5] = {0u, 0u, 0u, 0u, 0u};
+          if (r >= 0 && c >= 0) {
+            unsigned e[9];
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              const unsigned char* row = X + (2 * rr + ky) * (kC12In * 2);
+              const unsigned pair = *reinterpret_cast<const unsigned*>(row + 4 * c);  // columns 2c, 2c + 1
+              e[ky * 3] = c > 0 ? *reinterpret_cast<const unsigned short*>(row + 4 * c - 2) : 0u;
+              e[ky * 3 + 1] = pair & 0xFFFFu;
+              e[ky * 3 + 2] = pair >> 16;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = e[2 * k] | (e[2 * k + 1] << 16);
+            v[4] = e[8];
+          }
+          *reinterpret_cast<uint4*>(A1 + k16_off(p, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<uint4*>(A1 + k16_off(p, 1)) = make_uint4(v[4], 0u, 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        warp_arrive(a1full);
+      }
+      // 4. the epilogue of the tile two back (its MMAs finished long ago)
+      if (i >= 2) ok = epilogue(i - 2, ok);
+      // 2-3. conv1 back from TMEM (10 jobs of 16 columns per lane quarter: block b = j / 2,
+      //    columns 16 (j % 2), dealt to the quarter's five warps), each value written straight
+      //    into the tap operands that read it.  d1 also covers the previous tile's conv2 MMAs
+      //    (issued before this tile's conv1), so the tap operands are free.
+      ok = warp_wait(d1, i & 1, s_abort, ok);
+      if (ok) {
+        tc_fence_after();
+        for (int j = grp; j < 2 * (kC12Rows1 / kBM); j += kC12Groups) {
+          const int b = j >> 1, hcol = j & 1;
+          float v[16];
+          tc_ld16(tmem + ((unsigned)(q * 32) << 16) + 128u + (unsigned)(32 * b + 16 * hcol), v);
+          const int p = b * kBM + q * 32 + lane;
+          if (p < kC12Pos) {
+            const int rr = p / 33, cc = p - rr * 33;
+            const bool pad = (2 * y0 - 1 + rr) < 0 || cc == 0;
+            uint4 val[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) val[h] = pad ? zero4() : bias_relu8(v + h * 8, s_b1 + (2 * hcol + h) * 8);
+            // position (rr, cc) feeds row (y - y0, x) of tap (ky, kx) when rr = 2 (y - y0) + ky and
+            // cc = 2 x + kx: ky = rr % 2 with y - y0 = rr / 2, or ky = 2 with y - y0 = rr / 2 - 1
+            // (rr even); likewise for the columns
+            const int ky0 = rr & 1, ym0 = rr >> 1, kx0 = cc & 1, xm0 = cc >> 1;
+            const bool y_a = ym0 < 8, y_b = !(rr & 1) && rr >= 2;
+            const bool x_a = xm0 < 16, x_b = !(cc & 1) && cc >= 2;
+#pragma unroll
+            for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+              for (int ox = 0; ox < 2; ++ox) {
+                if (!(oy ? y_b : y_a) || !(ox ? x_b : x_a)) continue;
+                const int ky = oy ? 2 : ky0, kx = ox ? 2 : kx0;
+                const int m = (oy ? ym0 - 1 : ym0) * 16 + (ox ? xm0 - 1 : xm0);
+                unsigned char* row = A2 + (ky * 3 + kx) * 8192 + m * 64;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                  *reinterpret_cast<uint4*>(row + (((2 * hcol + h) ^ ((m >> 1) & 3)) << 4)) = val[h];
+              }
+          }
+        }
+        tc_fence_before();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        warp_arrive(a2full);
       }
     }
-    tc_fence_before();
-    __syncthreads();
-    // 3. the tap operands of conv2 out of the conv1 tile, then its 18 MMAs
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap - 3 * ky;
-      *reinterpret_cast<uint4*>(A2 + tap * 8192 + cp_dst) =
-          *reinterpret_cast<const uint4*>(C1 + cp_src + (ky * 33 + kx) * kC12Pitch);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const unsigned a0 = smem_addr(A2), b0 = smem_addr(smem + kC12B);
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk)
-          tc_mma(tmem + (unsigned)(s * 64), sw_desc<32>(a0 + tap * 8192 + kk * 32), sw_desc<32>(b0 + tap * 4096 + kk * 32),
-                 idesc2, (tap | kk) ? 1u : 0u);
-      tc_commit(&mma[s]);
-    }
-    prev = t;
-  }
-  if (ok && prev >= 0 && !epilogue(prev, (i - 1) & 1, ((i - 1) >> 1) & 1)) ok = false;
-  if (tid == 0) {
-    if (!ok) {
-      atomicExch(C.err, 1);
-      for (unsigned h = x_done; h < x_issued; ++h) fwd_drain(&xfull[h & 1], (h >> 1) & 1);  // loads in flight land
-    }
-    tc_commit(drain);  // arrives once every MMA issued above has completed
-    fwd_drain(drain, 0);
-    bulk_wait0();
+    for (int j = i >= 2 ? i - 2 : 0; ok && j < i; ++j) ok = epilogue(j, ok);  // the last two tiles
+    if (!ok && lane == 0) fwd_fail(s_abort, C.err);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == kCtl) {
+    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kC12Cols) : "memory");
   }

@@ -249,6 +249,8 @@ def test_cnn_forward_layers_take_the_tensor_map_path(lib):
     assert cnn.fwd_path("dense", 7, 0, 0, 2048, 256) == T
     assert cnn.fwd_path("dense", 7, 0, 0, 32, 64) == G         # fin below one 64-wide slice
     assert cnn.fwd_path("dense", 7, 0, 0, 256, 264) == G
+    assert cnn.fwd_path("dense", 7, 0, 0, 256, 320) == G         # more than 256 outputs
+    assert cnn.fwd_path("conv", 2, 16, 16, 64, 320) == G
     assert cnn.fwd_path("dense", 7, 0, 0, 256, 256, fp32_out=True) == G
     with pytest.raises(cnn.CNNError):
         cnn.fwd_path("conv", 2, 32, 32, 12, 16)

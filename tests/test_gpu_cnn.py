@@ -185,6 +185,25 @@ def test_conv_forward_paths_of_the_network(C):
                                                                  (8, 128, 128))] == [C.PATH_GATHER] + [C.PATH_TMA] * 3
 
 
+def test_prep_vector_path_matches_the_scalar_one(C):
+    # 128-pixel rows take the four-outputs-per-thread kernel; an image that starts 4 bytes past
+    # a 16-byte boundary takes the one-output kernel: both give the same BF16 bits (same sums in
+    # the same order), and the oracle within one BF16 rounding
+    import torch
+    rng = np.random.default_rng(9)
+    G, H, W = 37, 128, 128
+    a = rng.normal(size=(G, H, W)).astype(np.float32) * 20.0
+    img = torch.from_numpy(a).cuda()
+    buf = torch.empty(G * H * W + 1, dtype=torch.float32, device="cuda")
+    off = buf[1:].view(G, H, W)
+    off.copy_(img)
+    fast, slow = C.prep(img, 0.5), C.prep(off, 0.5)
+    assert torch.equal(fast.view(torch.int16), slow.view(torch.int16))
+    want = ref.prep(a.astype(np.float64), 0.5)
+    got = _np(fast)[..., 0]
+    assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 1e-6)
+
+
 def test_prep_loss_and_adam(C):
     import torch
     rng = np.random.default_rng(5)
