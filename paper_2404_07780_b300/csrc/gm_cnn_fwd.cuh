@@ -381,25 +381,33 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
 // y2 = relu(conv3x3_s2(relu(conv3x3_s2(x, w1) + b1), w2) + b2) for 64x64 single-channel
 // images, with conv1 (1 -> 32 channels, 32x32) kept in shared memory.  A tile is 8 rows x 16
 // columns of one image's conv2 output (16x16, 64 channels: 128 TMEM lanes).  It needs conv1
-// at rows 2 y0 - 1 .. 2 y0 + 15 and columns -1 .. 31 (17 x 33 positions p = 33 rr + cc;
-// those at -1 are conv2's zero padding), which need input rows 4 y0 - 3 .. 4 y0 + 31 (one
+// at rows 2 y0 - 1 .. 2 y0 + 15 and columns -1 .. 31 (17 x 33 positions (rr, cc), offsets from
+// the first; those at -1 are conv2's zero padding), which need input rows 4 y0 - 3 .. 4 y0 + 31 (one
 // 35 x 64 tensor-map box, zero-filled above the image).  Per tile:
 //   1. im2col of conv1: row p holds the 9 input values of position p and 7 zeros (K = 16,
 //      no-swizzle K-major core matrices); five MMAs (M = 128, N = 32, K = 16) give conv1 for
-//      640 rows in TMEM;
+//      640 rows in TMEM (rows past the 561 positions read whatever follows and are not used);
 //   2. the conv1 rows come back through tcgen05.ld: + b1, ReLU, BF16 (zero at the padding
 //      positions), each written straight into the conv2 operand rows that read it: tap (ky, kx),
 //      row m = (y - y0) 16 + x holds position (2 (y - y0) + ky, 2 x + kx) (1, 2 or 4 rows per
 //      position; 32 channels in a 64-byte row with the 64-byte swizzle);
-//   3. 18 MMAs (N = 64, K = 16) accumulate conv2 into one of two TMEM accumulators;
-//   4. the epilogue of the tile two back runs meanwhile: TMEM -> + b2, ReLU, BF16 -> one of two
-//      swizzled staging tiles -> one tensor-map store.
+//   3. 18 MMAs (N = 64, K = 16) accumulate conv2;
+//   4. TMEM -> + b2, ReLU, BF16 -> swizzled staging tile -> one tensor-map store.
 // conv1 is the same single K = 16 MMA per row as the gathered GEMM's (whose other K steps add
 // zero products) and conv2 the same 18 K steps as k_fwd's, so the output equals the two layers
-// run one after the other bit for bit.  One block per SM, persistent: 20 compute warps do
-// steps 1-4; one control thread issues the copies (the next tile's input rows during the
-// current one), both MMA stages and the stores, each on an mbarrier the compute warps arrive
-// on, so the tensor cores and copies never wait for a block-wide barrier.
+// run one after the other bit for bit.
+//
+// One block per SM, persistent.  20 compute warps do steps 1, 2 and 4; one control thread
+// issues the input copies (two tiles ahead), both MMA stages and the stores, each on an
+// mbarrier the compute warps arrive on.  Steps are pipelined across tiles: conv1's MMAs run one
+// tile ahead of conv2's (two conv1 accumulators in TMEM, two sets of conv2 operands in shared
+// memory), so while the tensor cores contract tile i the compute warps build tile i + 1's
+// im2col and read tile i + 1's conv1 back; the epilogue runs two tiles behind (two conv2
+// accumulators).  In tile i the compute warps: wait conv1(i) -> im2col(i + 1) -> epilogue(i - 2)
+// -> conv1(i) back into operand set i % 2; the control thread: conv1 MMAs of tile i + 1 ->
+// store of tile i - 2 -> conv2 MMAs of tile i.  Waiting for conv1(i) also covers every MMA the
+// control thread issued before it (conv2 of tile i - 2), which frees operand set i % 2 and the
+// im2col buffer.
 constexpr int kC12Compute = 640;             // compute threads (20 warps: 5 per TMEM lane quarter)
 constexpr int kC12Groups = kC12Compute / 128;  // compute warps per lane quarter
 constexpr int kC12Threads = kC12Compute + 32;  // + one control warp
@@ -408,19 +416,26 @@ constexpr int kC12Rows = 35;                 // input rows of a tile
 constexpr int kC12Pos = 17 * 33;             // conv1 positions of a tile
 constexpr int kC12Rows1 = 640;               // conv1 GEMM rows (5 MMAs of 128)
 constexpr int kC12B = 0;                     // conv2 weights: 9 taps x [64][32], 64-byte swizzle
-constexpr int kC12A = 9 * 4096;              // conv2 A operands: 9 taps x [128][32], 64-byte swizzle
-constexpr int kC12X = kC12A + 9 * 8192;      // input rows: 2 buffers x [35][64] BF16
-constexpr int kC12XBuf = 5120;
-constexpr int kC12Out = kC12X + 2 * kC12XBuf;  // output staging: 2 x [128][64] BF16, 128-byte swizzle
-constexpr int kC12A1 = kC12Out + 2 * kOutHalf;   // conv1 im2col [640][16], core matrices
-constexpr int kC12B1 = kC12A1 + kC12Rows1 * 32;  // conv1 weights [32][16], core matrices
-constexpr int kC12Bias = kC12B1 + 1024;          // b1 [32], b2 [64] FP32
+constexpr int kC12A = 9 * 4096;              // conv2 operands: 2 sets x 9 taps x [128][32], 64-byte swizzle
+constexpr int kC12ASet = 9 * 8192;
+constexpr int kC12X = kC12A + 2 * kC12ASet;  // input rows: 2 buffers x [35][64] BF16
+constexpr int kC12XBuf = 4608;
+constexpr int kC12Out = kC12X + 2 * kC12XBuf;  // output staging [128][64] BF16, 128-byte swizzle
+constexpr int kC12A1 = kC12Out + kOutHalf;     // conv1 im2col [561][16], core matrices
+constexpr int kC12B1 = kC12A1 + 18 * 1024;     // conv1 weights [32][16], core matrices
+constexpr int kC12Bias = kC12B1 + 1024;        // b1 [32], b2 [64] FP32
 constexpr int kC12Bar = kC12Bias + 512;
-constexpr int kC12Smem = 1024 + kC12Bar + 128;
-constexpr unsigned kC12Cols = 512;  // TMEM: conv2 accumulators at 0 and 64, conv1 at 128 + 32 b
+constexpr int kC12End = kC12Bar + 128;
+// the conv1 MMAs read 640 rows of the im2col buffer: the block's shared memory must reach there
+constexpr int kC12Smem = 1024 + (kC12End > kC12A1 + kC12Rows1 * 32 ? kC12End : kC12A1 + kC12Rows1 * 32);
+constexpr unsigned kC12Cols = 512;  // TMEM: conv2 accumulators at 0 and 64, conv1 at 128 and 288
+constexpr unsigned kC12D1 = 128, kC12D1Stride = 160;
 static_assert(kC12A % 1024 == 0 && kC12X % 1024 == 0 && kC12Out % 1024 == 0 && kC12A1 % 1024 == 0 &&
-                  kC12B1 % 1024 == 0,
+                  kC12B1 % 1024 == 0 && kC12XBuf >= kC12Rows * kC12In * 2,
               "aligned regions");
+static_assert((((kC12Pos - 1) >> 3) + 1) * 256 <= 18 * 1024, "the 561 im2col rows fit their buffer");
+static_assert(kC12Smem <= 227 * 1024, "one block's shared memory");
+static_assert(kC12D1 + 2 * kC12D1Stride <= kC12Cols, "TMEM columns");
 
 struct Conv12Args {
   CUtensorMap tx;   // input [nb][64][64] BF16: dims (64, 64, nb), box (64, 35, 1), zero fill
@@ -459,38 +474,120 @@ __device__ __forceinline__ void warp_arrive(u64* bar) {
   if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
 }
 
+// Input rows of tile t (image t / 2, output rows 8 (t % 2) ..) into an input buffer.
+__device__ __forceinline__ void c12_load_x(const Conv12Args& C, unsigned char* dst, int t, u64* bar) {
+  mbar_expect_tx(bar, kC12Rows * kC12In * 2);
+  tma_load_3d_cnn(dst, &C.tx, 0, 32 * (t & 1) - 3, t >> 1, bar);
+}
+
+// The conv1 position (rr, cc) of im2col row p: row rr = p / 33 holds the 17 even columns cc
+// first, then the 16 odd ones, so that a warp's lanes (consecutive rows) read back positions of
+// one column parity, whose operand rows lie in one tap tile (no bank conflicts between lanes)
+__device__ __forceinline__ void c12_pos(int p, int& rr, int& cc) {
+  rr = p / 33;
+  const int j = p - rr * 33;
+  cc = j < 17 ? 2 * j : 2 * (j - 17) + 1;
+}
+
+// im2col of conv1 for a tile with first output row y0 (compute threads): row p holds position
+// (rr, cc), input rows 2 rr + ky of the box, columns 2 c + kx - 1 (c = cc - 1)
+__device__ __forceinline__ void c12_im2col(const unsigned char* X, unsigned char* A1, int y0, int ctid) {
+  for (int p = ctid; p < kC12Pos; p += kC12Compute) {
+    int rr, cc;
+    c12_pos(p, rr, cc);
+    const int r = 2 * y0 - 1 + rr, c = cc - 1;
+    unsigned v[5] = {0u, 0u, 0u, 0u, 0u};
+    if (r >= 0 && c >= 0) {
+      unsigned e[9];
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const unsigned char* row = X + (2 * rr + ky) * (kC12In * 2);
+        const unsigned pair = *reinterpret_cast<const unsigned*>(row + 4 * c);  // columns 2c, 2c + 1
+        e[ky * 3] = c > 0 ? *reinterpret_cast<const unsigned short*>(row + 4 * c - 2) : 0u;
+        e[ky * 3 + 1] = pair & 0xFFFFu;
+        e[ky * 3 + 2] = pair >> 16;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = e[2 * k] | (e[2 * k + 1] << 16);
+      v[4] = e[8];
+    }
+    *reinterpret_cast<uint4*>(A1 + k16_off(p, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<uint4*>(A1 + k16_off(p, 1)) = make_uint4(v[4], 0u, 0u, 0u);
+  }
+}
+
+// conv1 back from TMEM accumulator d1 (compute warp with lane quarter q and group grp): 10 jobs
+// of 16 columns per lane quarter (block b = j / 2, columns 16 (j % 2)), dealt to the quarter's
+// warps; + b1, ReLU, BF16 (zero at the padding positions), each value written straight into the
+// conv2 operand rows that read it.  Position (rr, cc) feeds row (y - y0, x) of tap (ky, kx) when
+// rr = 2 (y - y0) + ky and cc = 2 x + kx: ky = rr % 2 with y - y0 = rr / 2, or ky = 2 with
+// y - y0 = rr / 2 - 1 (rr even); likewise for the columns.
+__device__ __forceinline__ void c12_readout(unsigned d1, unsigned char* A2, const float* s_b1, int y0, int q, int grp,
+                                            int lane) {
+  for (int j = grp; j < 2 * (kC12Rows1 / kBM); j += kC12Groups) {
+    const int b = j >> 1, hcol = j & 1;
+    float v[16];
+    tc_ld16(d1 + ((unsigned)(q * 32) << 16) + (unsigned)(32 * b + 16 * hcol), v);
+    const int p = b * kBM + q * 32 + lane;
+    if (p < kC12Pos) {
+      int rr, cc;
+      c12_pos(p, rr, cc);
+      const bool pad = (2 * y0 - 1 + rr) < 0 || cc == 0;
+      uint4 val[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) val[h] = pad ? zero4() : bias_relu8(v + h * 8, s_b1 + (2 * hcol + h) * 8);
+      const int ky0 = rr & 1, ym0 = rr >> 1, kx0 = cc & 1, xm0 = cc >> 1;
+      const bool y_a = ym0 < 8, y_b = !(rr & 1) && rr >= 2;
+      const bool x_a = xm0 < 16, x_b = !(cc & 1) && cc >= 2;
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+          if (!(oy ? y_b : y_a) || !(ox ? x_b : x_a)) continue;
+          const int ky = oy ? 2 : ky0, kx = ox ? 2 : kx0;
+          const int m = (oy ? ym0 - 1 : ym0) * 16 + (ox ? xm0 - 1 : xm0);
+          unsigned char* row = A2 + (ky * 3 + kx) * 8192 + m * 64;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            *reinterpret_cast<uint4*>(row + (((2 * hcol + h) ^ ((m >> 1) & 3)) << 4)) = val[h];
+        }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant__ Conv12Args C) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
   u64* xfull = reinterpret_cast<u64*>(smem + kC12Bar);  // [2] input rows of a buffer landed (copy)
   u64* mma = xfull + 2;        // [2] conv2 MMAs into an accumulator done (commit)
-  u64* bfull = mma + 2;        // conv2 weights landed (copy)
-  u64* d1 = bfull + 1;         // conv1 MMAs done (commit)
-  u64* a1full = d1 + 1;        // im2col written (every compute warp)
-  u64* a2full = a1full + 1;    // tap operands written (every compute warp)
-  u64* outfull = a2full + 1;   // [2] output staging tile written (every compute warp)
-  u64* outfree = outfull + 2;  // [2] output staging tile read by its store (control thread)
-  u64* drain = outfree + 2;
+  u64* d1 = mma + 2;           // [2] conv1 MMAs into an accumulator done (commit)
+  u64* a2full = d1 + 2;        // [2] a conv2 operand set written (every compute warp)
+  u64* bfull = a2full + 2;     // conv2 weights landed (copy)
+  u64* a1full = bfull + 1;     // im2col written (every compute warp)
+  u64* outfull = a1full + 1;   // output staging tile written (every compute warp)
+  u64* outfree = outfull + 1;  // output staging tile read by its store (control thread)
+  u64* drain = outfree + 1;
   unsigned* s_tmem = reinterpret_cast<unsigned*>(drain + 1);
   volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
   float* s_b1 = reinterpret_cast<float*>(smem + kC12Bias);
   float* s_b2 = s_b1 + 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr unsigned kXBytes = kC12Rows * kC12In * 2;
-  unsigned char* A2 = smem + kC12A;
   unsigned char* A1 = smem + kC12A1;
   unsigned char* out = smem + kC12Out;
   constexpr int kCtl = kC12Compute / 32;  // the control warp
+  // this block's tiles: t_i = blockIdx.x + i gridDim.x, i < n
+  const int n = (C.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  auto tile = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
+  auto xbuf = [&](int i) { return smem + kC12X + (i & 1) * kC12XBuf; };
+  auto aset = [&](int i) { return smem + kC12A + (i & 1) * kC12ASet; };
 
   if (tid == 0) {
-    for (int k = 0; k < 5; ++k) mbar_init_n(&xfull[k], 1);  // xfull[2], mma[2], bfull
-    mbar_init_n(d1, 1);
+    for (int k = 0; k < 6; ++k) mbar_init_n(&xfull[k], 1);  // xfull, mma, d1: two each
+    for (int k = 0; k < 2; ++k) mbar_init_n(&a2full[k], kC12Compute / 32);
+    mbar_init_n(bfull, 1);
     mbar_init_n(a1full, kC12Compute / 32);
-    mbar_init_n(a2full, kC12Compute / 32);
-    for (int k = 0; k < 2; ++k) {
-      mbar_init_n(&outfull[k], kC12Compute / 32);
-      mbar_init_n(&outfree[k], 1);
-    }
+    mbar_init_n(outfull, kC12Compute / 32);
+    mbar_init_n(outfree, 1);
     mbar_init_n(drain, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -501,8 +598,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // conv1 weights as the B operand (row co = the 9 taps and 7 zeros), the biases, and the
-  // im2col rows past the last position (zero for good)
+  // conv1 weights as the B operand (row co = the 9 taps and 7 zeros) and the biases
   if (tid < 64) {
     const int co = tid >> 1, kc = tid & 1;
     bf16 v[8];
@@ -517,8 +613,6 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
     if (k < 32) s_b1[k] = C.b1 ? C.b1[k] : 0.f;
     else s_b2[k - 32] = C.b2 ? C.b2[k - 32] : 0.f;
   }
-  for (int k = tid; k < (kC12Rows1 - kC12Pos) * 2; k += kC12Threads)
-    *reinterpret_cast<uint4*>(A1 + k16_off(kC12Pos + (k >> 1), k & 1)) = zero4();
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
@@ -532,64 +626,64 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&C.ty)) : "memory");
       constexpr unsigned idesc2 = idesc_bf16(kBM, 64), idesc1 = idesc_bf16(kBM, 32);
       const u64 da1 = smem_desc(smem_addr(A1), 128, 256), db1 = smem_desc(smem_addr(smem + kC12B1), 128, 256);
-      const u64 da2 = sw_desc<32>(smem_addr(A2)), db2 = sw_desc<32>(smem_addr(smem + kC12B));
-      unsigned x_issued = 0;
+      const u64 db2 = sw_desc<32>(smem_addr(smem + kC12B));
+      auto conv1 = [&](int i) {  // the conv1 MMAs of tile i (im2col in place)
+        tc_fence_after();
+        const unsigned d = tmem + kC12D1 + (unsigned)((i & 1) * kC12D1Stride);
+#pragma unroll
+        for (int b = 0; b < kC12Rows1 / kBM; ++b)
+          tc_mma(d + (unsigned)(32 * b), da1 + (u64)((b * kBM * 32) >> 4), db1, idesc1, 0u);
+        tc_commit(&d1[i & 1]);
+      };
+      int x_issued = 0;
       bool ok = true;
       mbar_expect_tx(bfull, 9 * 4096);
       for (int tap = 0; tap < 9; ++tap) tma_load_2d(smem + kC12B + tap * 4096, &C.tw2, tap * 32, 0, bfull);
-      if ((int)blockIdx.x < C.n_tiles) {
-        const int t = blockIdx.x;
-        mbar_expect_tx(&xfull[0], kXBytes);
-        tma_load_3d_cnn(smem + kC12X, &C.tx, 0, 32 * (t & 1) - 3, t >> 1, &xfull[0]);
-        ++x_issued;
-      }
-      if (!fwd_wait(bfull, 0, s_abort)) ok = false;
+      for (; x_issued < 2 && x_issued < n; ++x_issued) c12_load_x(C, xbuf(x_issued), tile(x_issued), &xfull[x_issued]);
+      if (!fwd_wait(bfull, 0, s_abort) || !fwd_wait(a1full, 0, s_abort)) ok = false;
+      if (ok) conv1(0);
       int i = 0;
-      for (int t = blockIdx.x; ok && t < C.n_tiles; t += gridDim.x, ++i) {
-        const int s = i & 1;
-        const unsigned ph = i & 1;
-        const int tn = t + gridDim.x;  // the next tile's input rows: the other buffer, free once
-        if (tn < C.n_tiles) {          // im2col of the previous tile is done (waited below)
-          mbar_expect_tx(&xfull[s ^ 1], kXBytes);
-          tma_load_3d_cnn(smem + kC12X + (s ^ 1) * kC12XBuf, &C.tx, 0, 32 * (tn & 1) - 3, tn >> 1, &xfull[s ^ 1]);
+      for (; ok && i < n; ++i) {
+        if (i + 2 < n) {  // the input buffer of tile i is free: its im2col was waited for
+          c12_load_x(C, xbuf(i), tile(i + 2), &xfull[i & 1]);
           ++x_issued;
         }
-        if (!fwd_wait(a1full, ph, s_abort)) { ok = false; break; }
-        tc_fence_after();
-#pragma unroll
-        for (int b = 0; b < kC12Rows1 / kBM; ++b)
-          tc_mma(tmem + 128u + (unsigned)(32 * b), da1 + (u64)((b * kBM * 32) >> 4), db1, idesc1, 0u);
-        tc_commit(d1);
-        if (i >= 2) {  // the output of the tile two back (staging buffer i % 2), once written
-          if (!fwd_wait(&outfull[s], ((i - 2) >> 1) & 1, s_abort)) { ok = false; break; }
-          tma_store_2d(&C.ty, out + s * kOutHalf, 0, (t - 2 * (int)gridDim.x) * kBM);
-          bulk_commit();
+        if (i + 1 < n) {  // conv1 of the next tile
+          if (!fwd_wait(a1full, (i + 1) & 1, s_abort)) { ok = false; break; }
+          conv1(i + 1);
         }
-        if (!fwd_wait(a2full, ph, s_abort)) { ok = false; break; }
+        if (i >= 2) {  // the output of tile i - 2, once its staging tile is written; the tile is
+                       // handed back as soon as the store has read it
+          if (!fwd_wait(outfull, i & 1, s_abort)) { ok = false; break; }
+          tma_store_2d(&C.ty, out, 0, tile(i - 2) * kBM);
+          bulk_commit();
+          bulk_wait_read0();
+          mbar_arrive(outfree);
+        }
+        if (!fwd_wait(&a2full[i & 1], (i >> 1) & 1, s_abort)) { ok = false; break; }
         tc_fence_after();
+        const u64 da2 = sw_desc<32>(smem_addr(aset(i)));
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
-            tc_mma(tmem + (unsigned)(s * 64), da2 + (u64)((tap * 8192 + kk * 32) >> 4),
+            tc_mma(tmem + (unsigned)((i & 1) * 64), da2 + (u64)((tap * 8192 + kk * 32) >> 4),
                    db2 + (u64)((tap * 4096 + kk * 32) >> 4), idesc2, (tap | kk) ? 1u : 0u);
-        tc_commit(&mma[s]);
-        if (i >= 2) {
-          bulk_wait_read0();
-          mbar_arrive(&outfree[s]);
-        }
+        tc_commit(&mma[i & 1]);
       }
       for (int j = i >= 2 ? i - 2 : 0; ok && j < i; ++j) {  // the last two tiles' outputs
-        if (!fwd_wait(&outfull[j & 1], (j >> 1) & 1, s_abort)) {
+        if (!fwd_wait(outfull, j & 1, s_abort)) {
           ok = false;
           break;
         }
-        tma_store_2d(&C.ty, out + (j & 1) * kOutHalf, 0, (blockIdx.x + j * (int)gridDim.x) * kBM);
+        tma_store_2d(&C.ty, out, 0, tile(j) * kBM);
         bulk_commit();
+        bulk_wait_read0();
+        mbar_arrive(outfree);
       }
       if (!ok) {
         fwd_fail(s_abort, C.err);
-        for (unsigned h = x_issued > 2 ? x_issued - 2 : 0u; h < x_issued; ++h)
+        for (int h = x_issued > 2 ? x_issued - 2 : 0; h < x_issued; ++h)
           fwd_drain(&xfull[h & 1], (h >> 1) & 1);  // the input loads in flight land
       }
       tc_commit(drain);  // arrives once every MMA issued above has completed
@@ -600,106 +694,60 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
     // ---- compute warps ----
     const int q = warp & 3, grp = warp >> 2;  // TMEM lane quarter and column group of this warp
 
-    // staging buffer j % 2 of tile number j (this block's j-th) from conv2 accumulator j % 2; the
-    // buffer is free once the store of tile j - 2 has read it
+    // staging tile of tile number j from conv2 accumulator j % 2; the tile is free once the store
+    // of tile j - 1 has read it
     auto epilogue = [&](int j, bool ok) -> bool {
       ok = warp_wait(&mma[j & 1], (j >> 1) & 1, s_abort, ok);
-      if (j >= 2) ok = warp_wait(&outfree[j & 1], ((j - 2) >> 1) & 1, s_abort, ok);
+      if (j >= 1) ok = warp_wait(outfree, (j - 1) & 1, s_abort, ok);
       if (ok && grp < 4) {  // four column groups of 16
         tc_fence_after();
         const int r = q * 32 + lane;
-        unsigned char* o = out + (j & 1) * kOutHalf;
         float v[16];
         tc_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)((j & 1) * 64 + grp * 16), v);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c = grp * 2 + h;
-          *reinterpret_cast<uint4*>(o + r * 128 + ((c ^ (r & 7)) << 4)) = bias_relu8(v + h * 8, s_b2 + c * 8);
+          *reinterpret_cast<uint4*>(out + r * 128 + ((c ^ (r & 7)) << 4)) = bias_relu8(v + h * 8, s_b2 + c * 8);
         }
         tc_fence_before();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      if (ok) warp_arrive(&outfull[j & 1]);
+      if (ok) warp_arrive(outfull);
       return ok;
     };
 
-    int i = 0;
     bool ok = true;
-    for (int t = blockIdx.x; ok && t < C.n_tiles; t += gridDim.x, ++i) {
-      const int s = i & 1;
-      const int y0 = 8 * (t & 1);
-      // 1. im2col of conv1: row p = 33 rr + cc, input rows 2 rr + ky of the box, columns 2 c + kx - 1
-      //    (A1 is free: the conv1 MMAs of the previous tile are done, waited below)
-      ok = warp_wait(&xfull[s], (i >> 1) & 1, s_abort, ok);
+    if (n > 0) {  // im2col of the first tile
+      ok = warp_wait(&xfull[0], 0, s_abort, ok);
       if (ok) {
-        const unsigned char* X = smem + kC12X + s * kC12XBuf;
-        for (int p = tid; p < kC12Pos; p += kC12Compute) {
-          const int rr = p / 33, cc = p - rr * 33;
-          const int r = 2 * y0 - 1 + rr, c = cc - 1;
-          unsigned v[5] = {0u, 0u, 0u, 0u, 0u};
-          if (r >= 0 && c >= 0) {
-            unsigned e[9];
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-              const unsigned char* row = X + (2 * rr + ky) * (kC12In * 2);
-              const unsigned pair = *reinterpret_cast<const unsigned*>(row + 4 * c);  // columns 2c, 2c + 1
-              e[ky * 3] = c > 0 ? *reinterpret_cast<const unsigned short*>(row + 4 * c - 2) : 0u;
-              e[ky * 3 + 1] = pair & 0xFFFFu;
-              e[ky * 3 + 2] = pair >> 16;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = e[2 * k] | (e[2 * k + 1] << 16);
-            v[4] = e[8];
-          }
-          *reinterpret_cast<uint4*>(A1 + k16_off(p, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
-          *reinterpret_cast<uint4*>(A1 + k16_off(p, 1)) = make_uint4(v[4], 0u, 0u, 0u);
-        }
+        c12_im2col(xbuf(0), A1, 8 * (tile(0) & 1), tid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         warp_arrive(a1full);
       }
-      // 4. the epilogue of the tile two back (its MMAs finished long ago)
+    }
+    int i = 0;
+    for (; ok && i < n; ++i) {
+      // conv1 of tile i done: so are the conv2 MMAs of tile i - 2 (issued before it), which read
+      // operand set i % 2, and the im2col buffer is free
+      ok = warp_wait(&d1[i & 1], (i >> 1) & 1, s_abort, ok);
+      if (ok && i + 1 < n) {
+        ok = warp_wait(&xfull[(i + 1) & 1], ((i + 1) >> 1) & 1, s_abort, ok);
+        if (ok) {
+          c12_im2col(xbuf(i + 1), A1, 8 * (tile(i + 1) & 1), tid);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          warp_arrive(a1full);
+        }
+      }
+      // the epilogue of tile i - 2 before operand set i % 2 is handed over: conv2 of tile i
+      // reuses its accumulator
       if (i >= 2) ok = epilogue(i - 2, ok);
-      // 2-3. conv1 back from TMEM (10 jobs of 16 columns per lane quarter: block b = j / 2,
-      //    columns 16 (j % 2), dealt to the quarter's five warps), each value written straight
-      //    into the tap operands that read it.  d1 also covers the previous tile's conv2 MMAs
-      //    (issued before this tile's conv1), so the tap operands are free.
-      ok = warp_wait(d1, i & 1, s_abort, ok);
       if (ok) {
         tc_fence_after();
-        for (int j = grp; j < 2 * (kC12Rows1 / kBM); j += kC12Groups) {
-          const int b = j >> 1, hcol = j & 1;
-          float v[16];
-          tc_ld16(tmem + ((unsigned)(q * 32) << 16) + 128u + (unsigned)(32 * b + 16 * hcol), v);
-          const int p = b * kBM + q * 32 + lane;
-          if (p < kC12Pos) {
-            const int rr = p / 33, cc = p - rr * 33;
-            const bool pad = (2 * y0 - 1 + rr) < 0 || cc == 0;
-            uint4 val[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) val[h] = pad ? zero4() : bias_relu8(v + h * 8, s_b1 + (2 * hcol + h) * 8);
-            // position (rr, cc) feeds row (y - y0, x) of tap (ky, kx) when rr = 2 (y - y0) + ky and
-            // cc = 2 x + kx: ky = rr % 2 with y - y0 = rr / 2, or ky = 2 with y - y0 = rr / 2 - 1
-            // (rr even); likewise for the columns
-            const int ky0 = rr & 1, ym0 = rr >> 1, kx0 = cc & 1, xm0 = cc >> 1;
-            const bool y_a = ym0 < 8, y_b = !(rr & 1) && rr >= 2;
-            const bool x_a = xm0 < 16, x_b = !(cc & 1) && cc >= 2;
-#pragma unroll
-            for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-              for (int ox = 0; ox < 2; ++ox) {
-                if (!(oy ? y_b : y_a) || !(ox ? x_b : x_a)) continue;
-                const int ky = oy ? 2 : ky0, kx = ox ? 2 : kx0;
-                const int m = (oy ? ym0 - 1 : ym0) * 16 + (ox ? xm0 - 1 : xm0);
-                unsigned char* row = A2 + (ky * 3 + kx) * 8192 + m * 64;
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                  *reinterpret_cast<uint4*>(row + (((2 * hcol + h) ^ ((m >> 1) & 3)) << 4)) = val[h];
-              }
-          }
-        }
+        c12_readout(tmem + kC12D1 + (unsigned)((i & 1) * kC12D1Stride), aset(i), s_b1, 8 * (tile(i) & 1), q, grp,
+                    lane);
         tc_fence_before();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        warp_arrive(a2full);
+        warp_arrive(&a2full[i & 1]);
       }
     }
     for (int j = i >= 2 ? i - 2 : 0; ok && j < i; ++j) ok = epilogue(j, ok);  // the last two tiles
