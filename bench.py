@@ -13,8 +13,8 @@ per batch, larger than the 126 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extra]
 
-On one GPU the default line also carries `other_workloads`: the small, gradient, uneven and
-learned-start workloads, each run once at its full size in a child process after the fit's own
+On one GPU the default line also carries `other_workloads`: the small, gradient, inference,
+uneven and learned-start workloads, each run once at its full size in a child process after the fit's own
 measurement (a few minutes in all; --no-extra leaves them out, and so does a run on N > 1 GPUs).
 Their figures are context: `value`, `e2e` and `roofline` are the SDSS-shaped fit's.
 
@@ -460,7 +460,7 @@ def run_gpu(args, world, rank, local):
 
 # (workload, extra arguments, child time limit in s): each runs at its full size in a process of its
 # own after the SDSS-shaped fit's line is complete, so that nothing there can change that line
-OTHER_WORKLOADS = (("small", (), 180), ("gradient", ("--no-cpu-baseline",), 240),
+OTHER_WORKLOADS = (("small", (), 180), ("gradient", ("--no-cpu-baseline",), 240), ("inference", (), 180),
                    ("uneven", ("--no-cpu-baseline", "--steps", "1", "--warmup", "1"), 360),
                    ("learned", ("--steps", "1", "--warmup", "1"), 420))
 
@@ -488,6 +488,9 @@ def summarize_workload(name: str, l: dict) -> dict:
         s["normal_equations_ms_per_step"] = l["normal_equations_ms_per_step"]
         s["speedup_vs_normal_equations"] = l["speedup_vs_normal_equations"]
         s["adam_vs_lm"] = l["adam_vs_lm"]
+    elif name == "inference":
+        s["tensor"] = l["tensor"]
+        s["layers_ms"] = {k: v["ms"] for k, v in l["layers"].items()}
     elif name == "learned":
         s["speedup_vs_default_start"] = l["speedup_vs_default_start"]
         s["default_start"] = l["default_start"]

@@ -36,6 +36,9 @@ def test_summary_of_each_workload():
         inference={"ms": 20.0, "tflops": 80.0, "frac": 0.05, "stamps_per_s": 3e6}, training={"train_s": 6.0}))
     assert learned["speedup_vs_default_start"] == 1.8
     assert learned["inference"] == {"ms": 20.0, "tflops": 80.0, "frac": 0.05}
+    inf = bench.summarize_workload("inference", _line(
+        tensor={"tflops": 360.0, "frac": 0.2}, layers={"prep": {"ms": 0.8, "gbs": 6000.0}}))
+    assert inf["tensor"]["frac"] == 0.2 and inf["layers_ms"] == {"prep": 0.8}
 
 
 def test_failing_child_is_recorded(monkeypatch):
