@@ -42,6 +42,7 @@ constexpr int kOutHalf = kBM * 128;  // one 64-column BF16 half of an output til
 // Polls of one wait before it gives up: a wait lasts microseconds (one tile's copies and
 // MMAs), a poll tens of nanoseconds or more.
 constexpr unsigned kFwdWait = 1u << 22;
+constexpr unsigned kFwdWaitSleep = 1u << 20;  // tests that may each suspend the thread (at most ~2 s in all)
 constexpr int kFwdMaxN = 256;  // output columns of a layer on this path (the bias in shared memory)
 
 struct FwdArgs {
@@ -76,11 +77,25 @@ __device__ __forceinline__ void mbar_arrive(u64* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// One test of an mbarrier phase that may suspend the thread until the phase completes or
+// kSleepNs nanoseconds pass, so that a waiting lane does not take issue slots from the warps
+// that work beside it.
+constexpr unsigned kSleepNs = 2000;
+__device__ __forceinline__ bool mbar_test_sleep(u64* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(kSleepNs)
+      : "memory");
+  return done != 0;
+}
+
 // Bounded wait that also gives up soon after another role of the block has given up.
 __device__ __forceinline__ bool fwd_wait(u64* bar, unsigned parity, volatile int* abort) {
-  for (unsigned t = 0; t < kFwdWait; ++t) {
-    if (mbar_test(bar, parity)) return true;
-    if ((t & 255u) == 255u && *abort) return false;
+  for (unsigned t = 0; t < kFwdWaitSleep; ++t) {
+    if (mbar_test_sleep(bar, parity)) return true;
+    if ((t & 15u) == 15u && *abort) return false;
   }
   return false;
 }
@@ -489,68 +504,101 @@ __device__ __forceinline__ void c12_pos(int p, int& rr, int& cc) {
   cc = j < 17 ? 2 * j : 2 * (j - 17) + 1;
 }
 
-// im2col of conv1 for a tile with first output row y0 (compute threads): row p holds position
-// (rr, cc), input rows 2 rr + ky of the box, columns 2 c + kx - 1 (c = cc - 1)
-__device__ __forceinline__ void c12_im2col(const unsigned char* X, unsigned char* A1, int y0, int ctid) {
-  for (int p = ctid; p < kC12Pos; p += kC12Compute) {
-    int rr, cc;
-    c12_pos(p, rr, cc);
-    const int r = 2 * y0 - 1 + rr, c = cc - 1;
-    unsigned v[5] = {0u, 0u, 0u, 0u, 0u};
-    if (r >= 0 && c >= 0) {
-      unsigned e[9];
+// What one compute thread writes in every tile, worked out once: its im2col row (640 threads,
+// 561 rows) and its two conv1 read-back jobs (10 jobs of 16 columns per TMEM lane quarter,
+// block b = j / 2, columns 16 (j % 2), dealt to the quarter's five warps), each with the conv2
+// operand rows its value feeds.  Position (rr, cc) feeds row (y - y0, x) of tap (ky, kx) when
+// rr = 2 (y - y0) + ky and cc = 2 x + kx: ky = rr % 2 with y - y0 = rr / 2, or ky = 2 with
+// y - y0 = rr / 2 - 1 (rr even); likewise for the columns.  Only the padding of conv1 row -1 at
+// the top of an image depends on the tile.
+struct C12Plan {
+  int xo;          // im2col: byte offset of input row 2 rr, column 2 c (c = cc - 1) in the box
+  unsigned a1o;    // im2col: byte offset of the row's first 16-byte chunk (the second is 128 on)
+  bool row, cpos, cgt0, top;   // a row of this thread; c >= 0; c > 0; rr == 0
+  unsigned tcol[2];            // read-back: TMEM column of each job
+  bool jok[2], jpad[2], jtop[2];  // position exists; cc == 0 (padding); rr == 0
+  int off[2][4];   // operand rows fed: byte offset (tap 8192 + m 64 + swizzled chunk of channels
+                   // 16 hcol ..) of the first 8 channels in the operand set, -1 for none; the next 8
+                   // channels are at off ^ 16 (the chunk index's low bit)
+};
+
+__device__ __forceinline__ C12Plan c12_plan(int ctid, int q, int grp, int lane) {
+  C12Plan P;
+  int rr, cc;
+  P.row = ctid < kC12Pos;
+  c12_pos(P.row ? ctid : 0, rr, cc);
+  const int c = cc - 1;
+  P.xo = 2 * rr * (kC12In * 2) + 4 * c;
+  P.a1o = k16_off(P.row ? ctid : 0, 0);
+  P.cpos = c >= 0;
+  P.cgt0 = c > 0;
+  P.top = rr == 0;
 #pragma unroll
-      for (int ky = 0; ky < 3; ++ky) {
-        const unsigned char* row = X + (2 * rr + ky) * (kC12In * 2);
-        const unsigned pair = *reinterpret_cast<const unsigned*>(row + 4 * c);  // columns 2c, 2c + 1
-        e[ky * 3] = c > 0 ? *reinterpret_cast<const unsigned short*>(row + 4 * c - 2) : 0u;
-        e[ky * 3 + 1] = pair & 0xFFFFu;
-        e[ky * 3 + 2] = pair >> 16;
-      }
+  for (int k = 0; k < 2; ++k) {
+    const int j = grp + k * kC12Groups, b = j >> 1, hcol = j & 1;
+    const int p = b * kBM + q * 32 + lane;
+    P.tcol[k] = (unsigned)(32 * b + 16 * hcol);
+    P.jok[k] = p < kC12Pos;
+    c12_pos(P.jok[k] ? p : 0, rr, cc);
+    P.jpad[k] = cc == 0;
+    P.jtop[k] = rr == 0;
+    const int ky0 = rr & 1, ym0 = rr >> 1, kx0 = cc & 1, xm0 = cc >> 1;
+    const bool y_ok[2] = {ym0 < 8, !(rr & 1) && rr >= 2}, x_ok[2] = {xm0 < 16, !(cc & 1) && cc >= 2};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) v[k] = e[2 * k] | (e[2 * k + 1] << 16);
-      v[4] = e[8];
+    for (int d = 0; d < 4; ++d) {
+      const int oy = d >> 1, ox = d & 1;
+      const int ky = oy ? 2 : ky0, kx = ox ? 2 : kx0;
+      const int m = (oy ? ym0 - 1 : ym0) * 16 + (ox ? xm0 - 1 : xm0);
+      P.off[k][d] = (P.jok[k] && y_ok[oy] && x_ok[ox])
+                        ? (ky * 3 + kx) * 8192 + m * 64 + (((2 * hcol) ^ ((m >> 1) & 3)) << 4)
+                        : -1;
     }
-    *reinterpret_cast<uint4*>(A1 + k16_off(p, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
-    *reinterpret_cast<uint4*>(A1 + k16_off(p, 1)) = make_uint4(v[4], 0u, 0u, 0u);
   }
+  return P;
 }
 
-// conv1 back from TMEM accumulator d1 (compute warp with lane quarter q and group grp): 10 jobs
-// of 16 columns per lane quarter (block b = j / 2, columns 16 (j % 2)), dealt to the quarter's
-// warps; + b1, ReLU, BF16 (zero at the padding positions), each value written straight into the
-// conv2 operand rows that read it.  Position (rr, cc) feeds row (y - y0, x) of tap (ky, kx) when
-// rr = 2 (y - y0) + ky and cc = 2 x + kx: ky = rr % 2 with y - y0 = rr / 2, or ky = 2 with
-// y - y0 = rr / 2 - 1 (rr even); likewise for the columns.
-__device__ __forceinline__ void c12_readout(unsigned d1, unsigned char* A2, const float* s_b1, int y0, int q, int grp,
-                                            int lane) {
-  for (int j = grp; j < 2 * (kC12Rows1 / kBM); j += kC12Groups) {
-    const int b = j >> 1, hcol = j & 1;
+// im2col row of conv1 for a tile with first output row y0: the 9 input values of the position
+// (rows 2 rr + ky of the box, columns 2 c + kx - 1) and 7 zeros
+__device__ __forceinline__ void c12_im2col(const C12Plan& P, const unsigned char* X, unsigned char* A1, int y0) {
+  if (!P.row) return;
+  unsigned v[5] = {0u, 0u, 0u, 0u, 0u};
+  if (P.cpos && !(P.top && y0 == 0)) {
+    unsigned e[9];
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      const unsigned char* row = X + P.xo + ky * (kC12In * 2);
+      const unsigned pair = *reinterpret_cast<const unsigned*>(row);  // columns 2c, 2c + 1
+      e[ky * 3] = P.cgt0 ? *reinterpret_cast<const unsigned short*>(row - 2) : 0u;
+      e[ky * 3 + 1] = pair & 0xFFFFu;
+      e[ky * 3 + 2] = pair >> 16;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = e[2 * k] | (e[2 * k + 1] << 16);
+    v[4] = e[8];
+  }
+  *reinterpret_cast<uint4*>(A1 + P.a1o) = make_uint4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<uint4*>(A1 + P.a1o + 128) = make_uint4(v[4], 0u, 0u, 0u);
+}
+
+// conv1 back from TMEM accumulator d1 (this warp's lane quarter q): + b1, ReLU, BF16 (zero at
+// the padding positions), each value written into the conv2 operand rows it feeds
+__device__ __forceinline__ void c12_readout(const C12Plan& P, unsigned d1, unsigned char* A2, const float* s_b1,
+                                            int y0, int q, int grp) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
     float v[16];
-    tc_ld16(d1 + ((unsigned)(q * 32) << 16) + (unsigned)(32 * b + 16 * hcol), v);
-    const int p = b * kBM + q * 32 + lane;
-    if (p < kC12Pos) {
-      int rr, cc;
-      c12_pos(p, rr, cc);
-      const bool pad = (2 * y0 - 1 + rr) < 0 || cc == 0;
-      uint4 val[2];
+    tc_ld16(d1 + ((unsigned)(q * 32) << 16) + P.tcol[k], v);
+    if (!P.jok[k]) continue;
+    const int hcol = (grp + k * kC12Groups) & 1;
+    const bool pad = P.jpad[k] || (P.jtop[k] && y0 == 0);
+    const uint4 v0 = pad ? zero4() : bias_relu8(v, s_b1 + 16 * hcol);
+    const uint4 v1 = pad ? zero4() : bias_relu8(v + 8, s_b1 + 16 * hcol + 8);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) val[h] = pad ? zero4() : bias_relu8(v + h * 8, s_b1 + (2 * hcol + h) * 8);
-      const int ky0 = rr & 1, ym0 = rr >> 1, kx0 = cc & 1, xm0 = cc >> 1;
-      const bool y_a = ym0 < 8, y_b = !(rr & 1) && rr >= 2;
-      const bool x_a = xm0 < 16, x_b = !(cc & 1) && cc >= 2;
-#pragma unroll
-      for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-        for (int ox = 0; ox < 2; ++ox) {
-          if (!(oy ? y_b : y_a) || !(ox ? x_b : x_a)) continue;
-          const int ky = oy ? 2 : ky0, kx = ox ? 2 : kx0;
-          const int m = (oy ? ym0 - 1 : ym0) * 16 + (ox ? xm0 - 1 : xm0);
-          unsigned char* row = A2 + (ky * 3 + kx) * 8192 + m * 64;
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-            *reinterpret_cast<uint4*>(row + (((2 * hcol + h) ^ ((m >> 1) & 3)) << 4)) = val[h];
-        }
+    for (int d = 0; d < 4; ++d) {
+      const int o = P.off[k][d];
+      if (o < 0) continue;
+      *reinterpret_cast<uint4*>(A2 + o) = v0;
+      *reinterpret_cast<uint4*>(A2 + (o ^ 16)) = v1;
     }
   }
 }
@@ -693,6 +741,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
   } else {
     // ---- compute warps ----
     const int q = warp & 3, grp = warp >> 2;  // TMEM lane quarter and column group of this warp
+    const C12Plan plan = c12_plan(tid, q, grp, lane);
 
     // staging tile of tile number j from conv2 accumulator j % 2; the tile is free once the store
     // of tile j - 1 has read it
@@ -720,7 +769,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
     if (n > 0) {  // im2col of the first tile
       ok = warp_wait(&xfull[0], 0, s_abort, ok);
       if (ok) {
-        c12_im2col(xbuf(0), A1, 8 * (tile(0) & 1), tid);
+        c12_im2col(plan, xbuf(0), A1, 8 * (tile(0) & 1));
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         warp_arrive(a1full);
       }
@@ -733,7 +782,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
       if (ok && i + 1 < n) {
         ok = warp_wait(&xfull[(i + 1) & 1], ((i + 1) >> 1) & 1, s_abort, ok);
         if (ok) {
-          c12_im2col(xbuf(i + 1), A1, 8 * (tile(i + 1) & 1), tid);
+          c12_im2col(plan, xbuf(i + 1), A1, 8 * (tile(i + 1) & 1));
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           warp_arrive(a1full);
         }
@@ -743,8 +792,8 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
       if (i >= 2) ok = epilogue(i - 2, ok);
       if (ok) {
         tc_fence_after();
-        c12_readout(tmem + kC12D1 + (unsigned)((i & 1) * kC12D1Stride), aset(i), s_b1, 8 * (tile(i) & 1), q, grp,
-                    lane);
+        c12_readout(plan, tmem + kC12D1 + (unsigned)((i & 1) * kC12D1Stride), aset(i), s_b1, 8 * (tile(i) & 1), q,
+                    grp);
         tc_fence_before();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         warp_arrive(&a2full[i & 1]);
