@@ -165,3 +165,32 @@ def test_fullsize_adjoint_gradient(full):
         assert abs(chi2[g] - rchi2[s]) <= 1e-5 * rchi2[s], g
         d = np.sqrt(np.diag(rA[s]))
         assert (np.abs(grad[g, free] + 2.0 * rg[s]) <= 1e-4 * d * math.sqrt(rchi2[s])).all(), g
+
+
+def test_fullsize_cnn_inference():
+    # the initialiser's inference as the bench times it: 65,536 stamps through predict() in
+    # batches of 16,384 (the fused first two layers take ~221 tiles per block, both
+    # accumulators and both operand sets many times over); sampled rows equal the training
+    # forward pass on the same stamps bit for bit, and the first layer of the sample equals the
+    # FP64 reference to the BF16 bounds
+    import torch
+    from oracle import cnn as ref
+    from paper_2404_07780_b300 import cnn
+    cnn.lib()
+    net = cnn.Net(seed=11, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(12)
+    n = 65536
+    x = torch.asinh(3.0 * torch.randn((n, 64, 64, 1), generator=gen, device="cuda")).to(torch.bfloat16)
+    pred = net.predict(x)
+    idx = torch.tensor([0, 1, 16383, 16384, 40000, 65534, 65535] + list(range(997, 65536, 4099)), device="cuda")
+    want = net.forward(x[idx].contiguous())[1]
+    assert torch.equal(pred[idx], want)
+    a1 = cnn.conv_fwd(x[idx].contiguous(), net.w(0), net.b(0), relu=True).float().cpu().numpy().astype(np.float64)
+    xr = x[idx].float().cpu().numpy().astype(np.float64)
+    w1 = net.w(0).float().cpu().numpy().astype(np.float64)
+    b1 = net.b(0).float().cpu().numpy().astype(np.float64)
+    r1 = ref.conv_fwd(xr, w1, b1, relu=True)
+    scale = np.sqrt(ref.conv_fwd(xr ** 2, w1 ** 2) + b1 ** 2)
+    assert np.all(np.abs(a1 - r1) <= 2.0 ** -8 * np.abs(r1) + 1e-4 * scale + 1e-30)
+    cnn.check_device_error()
