@@ -178,10 +178,12 @@ def test_chi2_with_mask_and_contaminants(gm):
 
 
 @pytest.mark.parametrize("draw,K", [(synth.draw_bulge_disk, 25), (synth.draw_bulge_disk, 51),
-                                    (synth.draw_bulge_bar_nucleus, 41)])
+                                    (synth.draw_bulge_bar_nucleus, 41), (synth.draw_bulge_disk, 63),
+                                    (synth.draw_sdss, 63)])
 def test_chi2_grad_many_parameters(gm, draw, K):
     # 12 and 15 free parameters: 13 and 16 correlated channels in several channel-pair
-    # passes, two pairs per thread in the reduction-heavy variant
+    # passes, two pairs per thread in the reduction-heavy variant; and the largest PSF side the
+    # calls take (63, on a 64 x 72 stamp: the PSF nearly as wide as the stamp)
     b = draw(seed=7, G=4, H=64, W=72, K=K)
     c = from_batch(b, at="init")
     t = c.torch()
@@ -330,7 +332,8 @@ def test_fit_status_codes(gm):
 
 @pytest.mark.parametrize("draw,G,H,W,K", [(synth.draw_small, 7, 64, 64, 15),
                                           (synth.draw_bulge_bar_nucleus, 5, 96, 96, 41),
-                                          (synth.draw_bulge_disk, 4, 64, 72, 25)])
+                                          (synth.draw_bulge_disk, 4, 64, 72, 25),
+                                          (synth.draw_bulge_bar_nucleus, 3, 64, 72, 63)])
 def test_grad_adjoint_matches_normal_equations(gm, draw, G, H, W, K):
     # the adjoint gradient (two correlations) against the 1+P-channel pass, odd G included
     b = draw(seed=9, G=G) if draw is synth.draw_small else draw(seed=9, G=G, H=H, W=W, K=K)
