@@ -46,9 +46,19 @@ extern "C" {
 
 const char *gm_cnn_last_error(void);
 
-/* *flag = 1 if any CNN kernel on this device gave up waiting for its tensor-core
- * work (synchronous; host int). */
+/* *flag = 1 if any CNN kernel on this device gave up waiting for its copies or its
+ * tensor-core work since the last call (the flag is cleared when read; synchronous;
+ * host int).  The outputs of the call whose kernel gave up are undefined; later calls
+ * are not affected. */
 int gm_cnn_check_error(int *flag);
+
+/* A test of the timeout path (not part of the paper's method): in the next launch of
+ * the TMA-fed GEMM (a GM_CNN_PATH_TMA forward layer) made by the calling thread, block
+ * 0 issues no copy for its first K slice, so the MMA thread's wait for it runs out
+ * after `polls` tests (each at most ~2 us) with nothing in flight; the kernel sets the
+ * flag gm_cnn_check_error reads and every block leaves normally.  One launch only;
+ * polls = 0 cancels. */
+int gm_cnn_test_starve_next(unsigned polls);
 
 /* Kernels that compute a forward layer (the value gm_cnn_fwd_path returns). */
 #define GM_CNN_PATH_GATHER 0 /* GEMM whose threads gather the operands into shared memory */

@@ -73,6 +73,8 @@ def lib():
         L.gm_cnn_fwd_path.argtypes = [I, I, I, I, I, I, I]
         L.gm_cnn_conv12_fwd.restype = I
         L.gm_cnn_conv12_fwd.argtypes = [P, P, P, P, P, P, I, P]
+        L.gm_cnn_test_starve_next.restype = I
+        L.gm_cnn_test_starve_next.argtypes = [ctypes.c_uint]
         _cnn = L
     return _cnn
 
@@ -80,7 +82,7 @@ def lib():
 EXPORTS = ("gm_cnn_last_error", "gm_cnn_check_error", "gm_cnn_conv_fwd", "gm_cnn_conv_bwd_data",
            "gm_cnn_conv_bwd_weight_workspace", "gm_cnn_conv_bwd_weight", "gm_cnn_dense_fwd", "gm_cnn_dense_bwd_data",
            "gm_cnn_dense_bwd_weight_workspace", "gm_cnn_dense_bwd_weight", "gm_cnn_prep", "gm_cnn_mse", "gm_cnn_adam",
-           "gm_cnn_fwd_path", "gm_cnn_conv12_fwd")
+           "gm_cnn_fwd_path", "gm_cnn_conv12_fwd", "gm_cnn_test_starve_next")
 
 PATH_GATHER, PATH_TMA = 0, 1  # kernels of a forward layer (gm_cnn_fwd_path)
 

@@ -226,11 +226,20 @@ int run_fwd(FwdArgs& F, int BN, int KC, cudaStream_t st) {
   return KC == 64 ? launch_fwd<64, 64>(F, st) : launch_fwd<64, 32>(F, st);
 }
 
+// gm_cnn_test_starve_next: the poll limit of the next k_fwd launch made by this thread, 0 = none.
+thread_local unsigned g_cnn_starve_polls = 0;
+
 int fwd_common(FwdArgs& F, const float* b, int relu, int M, int N, void* y) {
   F.M = M;
   F.N = N;
   F.bias = b;
   F.relu = relu;
+  F.polls = kFwdWaitSleep;
+  if (g_cnn_starve_polls) {
+    F.polls = g_cnn_starve_polls;
+    F.starve = 1;
+    g_cnn_starve_polls = 0;
+  }
   int rc = err_flag(&F.err);
   if (rc) return rc;
   const int BN = N % 128 == 0 ? 128 : 64;
@@ -476,7 +485,13 @@ int gm_cnn_check_error(int* flag) {
   if (rc) return rc;
   int h = 0;
   CNN_CUDA(cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) CNN_CUDA(cudaMemset(d, 0, sizeof(int)));
   if (flag) *flag = h;
+  return GM_CNN_OK;
+}
+
+int gm_cnn_test_starve_next(unsigned polls) {
+  g_cnn_starve_polls = polls;
   return GM_CNN_OK;
 }
 

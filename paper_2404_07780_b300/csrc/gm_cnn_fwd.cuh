@@ -63,6 +63,8 @@ struct FwdArgs {
   const float* bias;  // [N] or nullptr
   int relu;
   int* err;        // set when a wait gives up
+  unsigned polls;  // tests of a wait before it gives up (kFwdWaitSleep)
+  int starve;      // test of the timeout path: block 0 issues no copy for its first slice
 };
 
 __device__ __forceinline__ void mbar_init_n(u64* bar, unsigned count) {
@@ -91,9 +93,11 @@ __device__ __forceinline__ bool mbar_test_sleep(u64* bar, unsigned parity) {
   return done != 0;
 }
 
-// Bounded wait that also gives up soon after another role of the block has given up.
-__device__ __forceinline__ bool fwd_wait(u64* bar, unsigned parity, volatile int* abort) {
-  for (unsigned t = 0; t < kFwdWaitSleep; ++t) {
+// Bounded wait (`polls` tests) that also gives up soon after another role of the block has
+// given up.
+__device__ __forceinline__ bool fwd_wait(u64* bar, unsigned parity, volatile int* abort,
+                                         unsigned polls = kFwdWaitSleep) {
+  for (unsigned t = 0; t < polls; ++t) {
     if (mbar_test_sleep(bar, parity)) return true;
     if ((t & 15u) == 15u && *abort) return false;
   }
@@ -281,12 +285,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
         }
         for (int j = 0; j < F.nk; ++j, ++g) {
           const int s = (int)(g % (unsigned)S);
-          if (g >= (unsigned)S && !fwd_wait(&empty[s], ((g / S) - 1) & 1u, s_abort)) {
+          if (g >= (unsigned)S && !fwd_wait(&empty[s], ((g / S) - 1) & 1u, s_abort, F.polls)) {
             fwd_fail(s_abort, F.err);
             ok = false;
             break;
           }
           unsigned char* sa = smem + s * STAGE;
+          if (F.starve && blockIdx.x == 0 && g == 0) continue;  // nothing arrives on full[0]
           mbar_expect_tx(&full[s], STAGE);
           int kb;
           if (F.conv) {
@@ -300,8 +305,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
           tma_load_2d(sa + A_BYTES, &F.tb, kb, n0, &full[s]);
         }
       }
-      if (!ok) {  // the copies still in flight land before the block leaves
-        for (unsigned h = g > (unsigned)S ? g - S : 0u; h < g; ++h) fwd_drain(&full[h % S], (h / S) & 1u);
+      if (!ok) {  // the copies still in flight land before the block leaves (none for a starved slice)
+        for (unsigned h = g > (unsigned)S ? g - S : 0u; h < g; ++h)
+          if (!(F.starve && blockIdx.x == 0 && h == 0)) fwd_drain(&full[h % S], (h / S) & 1u);
       }
     }
   } else if (warp == 1) {
@@ -313,7 +319,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
       bool ok = true;
       for (int t = blockIdx.x; ok && t < F.n_tiles; t += gridDim.x, ++i) {
         const int acc = i & 1;
-        if (i >= 2 && !fwd_wait(&tempty[acc], ((i >> 1) - 1) & 1, s_abort)) {
+        if (i >= 2 && !fwd_wait(&tempty[acc], ((i >> 1) - 1) & 1, s_abort, F.polls)) {
           fwd_fail(s_abort, F.err);
           break;
         }
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
         const unsigned d = tmem + (unsigned)(acc * BN);
         for (int j = 0; j < F.nk; ++j, ++g) {
           const int s = (int)(g % (unsigned)S);
-          if (!fwd_wait(&full[s], (g / S) & 1u, s_abort)) {
+          if (!fwd_wait(&full[s], (g / S) & 1u, s_abort, F.polls)) {
             fwd_fail(s_abort, F.err);
             ok = false;
             break;
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
       const int mt = t / F.n_ntiles, n0 = (t - mt * F.n_ntiles) * BN, m0 = mt * kBM;
       const int acc = i & 1;
       bool bad = false;
-      if (lane == 0) bad = !fwd_wait(&tfull[acc], (i >> 1) & 1, s_abort);
+      if (lane == 0) bad = !fwd_wait(&tfull[acc], (i >> 1) & 1, s_abort, F.polls);
       __syncwarp();
       if (named_any(1, 128, bad)) {  // the same decision in every epilogue thread
         if (bad) fwd_fail(s_abort, F.err);

@@ -102,3 +102,34 @@ def test_uneven_batch_timeout(gm):
     fit = lambda: gm.gm_fit_batch(c.spec, t["params"], t["image"], t["sigma"], t["mask"], t["psf"], geom=rb.geom)
     _timeout(gm, fit)
     assert (_np(fit()["status"]) > 0).all()
+
+
+def test_cnn_tma_gemm_wait_runs_out_and_recovers(gm):
+    # the learned initialiser's TMA-fed GEMM: gm_cnn_test_starve_next has block 0 of the next
+    # launch issue no copy for its first K slice; the MMA thread's bounded wait runs out, every
+    # role of the block leaves (copies in flight drained, TMEM freed), the device flag reads 1
+    # once (cleared when read), and the next call gives the normal result
+    import ctypes
+    import torch
+    from oracle import cnn as ref
+    from paper_2404_07780_b300 import cnn
+    L = cnn.lib()
+    rng = np.random.default_rng(21)
+    bf = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda().to(torch.bfloat16)
+    x = bf(rng.normal(size=(4, 16, 16, 64)))
+    w = bf(rng.normal(size=(128, 3, 3, 64)) / 24.0)
+    b = torch.from_numpy((rng.normal(size=128) * 0.1).astype(np.float32)).cuda()
+    assert cnn.fwd_path("conv", 4, 16, 16, 64, 128) == cnn.PATH_TMA
+    flag = ctypes.c_int(0)
+    assert L.gm_cnn_check_error(ctypes.byref(flag)) == 0  # clear anything left before
+    assert L.gm_cnn_test_starve_next(POLLS) == 0
+    cnn.conv_fwd(x, w, b, relu=True)
+    torch.cuda.synchronize()
+    assert L.gm_cnn_check_error(ctypes.byref(flag)) == 0 and flag.value == 1
+    assert L.gm_cnn_check_error(ctypes.byref(flag)) == 0 and flag.value == 0
+    y = cnn.conv_fwd(x, w, b, relu=True).float().cpu().numpy().astype(np.float64)
+    xr, wr, br = (t.float().cpu().numpy().astype(np.float64) for t in (x, w, b))
+    want = ref.conv_fwd(xr, wr, br, relu=True)
+    scale = np.sqrt(ref.conv_fwd(xr ** 2, wr ** 2) + br ** 2)
+    assert np.all(np.abs(y - want) <= 2.0 ** -8 * np.abs(want) + 1e-4 * scale + 1e-30)
+    cnn.check_device_error()
