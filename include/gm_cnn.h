@@ -52,12 +52,12 @@ const char *gm_cnn_last_error(void);
  * are not affected. */
 int gm_cnn_check_error(int *flag);
 
-/* A test of the timeout path (not part of the paper's method): in the next launch of
- * the TMA-fed GEMM (a GM_CNN_PATH_TMA forward layer) made by the calling thread, block
- * 0 issues no copy for its first K slice, so the MMA thread's wait for it runs out
- * after `polls` tests (each at most ~2 us) with nothing in flight; the kernel sets the
- * flag gm_cnn_check_error reads and every block leaves normally.  One launch only;
- * polls = 0 cancels. */
+/* A test of the timeout path (not part of the paper's method): in the next launch made
+ * by the calling thread of the TMA-fed GEMM (a GM_CNN_PATH_TMA forward layer) or of the
+ * fused first two layers (gm_cnn_conv12_fwd), block 0 issues no copy for its first K
+ * slice (its first input rows), so the wait for it runs out after `polls` tests (each
+ * at most ~2 us) with nothing in flight; the kernel sets the flag gm_cnn_check_error
+ * reads and every block leaves normally.  One launch only; polls = 0 cancels. */
 int gm_cnn_test_starve_next(unsigned polls);
 
 /* Kernels that compute a forward layer (the value gm_cnn_fwd_path returns). */

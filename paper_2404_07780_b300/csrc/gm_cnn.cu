@@ -349,6 +349,12 @@ int conv12(const void* x, const void* w1, const float* b1, const void* w2, const
   C.b1 = b1;
   C.b2 = b2;
   C.n_tiles = 2 * nb;
+  C.polls = kFwdWaitSleep;
+  if (g_cnn_starve_polls) {
+    C.polls = g_cnn_starve_polls;
+    C.starve = 1;
+    g_cnn_starve_polls = 0;
+  }
   CNN_CUDA(cudaFuncSetAttribute((const void*)k_conv12, cudaFuncAttributeMaxDynamicSharedMemorySize, kC12Smem));
   k_conv12<<<std::min(C.n_tiles, sms()), kC12Threads, kC12Smem, st>>>(C);
   CNN_LAUNCHED("k_conv12");

@@ -467,6 +467,8 @@ struct Conv12Args {
   const float* b2;  // [64] or nullptr
   int n_tiles;      // 2 nb
   int* err;
+  unsigned polls;   // tests of a wait before it gives up (kFwdWaitSleep)
+  int starve;       // test of the timeout path: block 0 issues no copy of its first input rows
 };
 
 __device__ __forceinline__ void tma_load_3d_cnn(void* dst, const CUtensorMap* map, int c0, int c1, int c2, u64* bar) {
@@ -484,9 +486,9 @@ __device__ __forceinline__ unsigned k16_off(int r, int kc) {
 
 // A compute warp's wait: lane 0 polls (unless the warp has already failed), the warp learns
 // the outcome; returns false on failure.
-__device__ __forceinline__ bool warp_wait(u64* bar, unsigned parity, volatile int* abort, bool ok) {
+__device__ __forceinline__ bool warp_wait(u64* bar, unsigned parity, volatile int* abort, bool ok, unsigned polls) {
   bool got = ok;
-  if (ok && (threadIdx.x & 31) == 0) got = fwd_wait(bar, parity, abort);
+  if (ok && (threadIdx.x & 31) == 0) got = fwd_wait(bar, parity, abort, polls);
   return __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
 }
 
@@ -693,8 +695,10 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
       bool ok = true;
       mbar_expect_tx(bfull, 9 * 4096);
       for (int tap = 0; tap < 9; ++tap) tma_load_2d(smem + kC12B + tap * 4096, &C.tw2, tap * 32, 0, bfull);
-      for (; x_issued < 2 && x_issued < n; ++x_issued) c12_load_x(C, xbuf(x_issued), tile(x_issued), &xfull[x_issued]);
-      if (!fwd_wait(bfull, 0, s_abort) || !fwd_wait(a1full, 0, s_abort)) ok = false;
+      const bool starved = C.starve && blockIdx.x == 0;  // load 0 not issued: nothing arrives on xfull[0]
+      for (; x_issued < 2 && x_issued < n; ++x_issued)
+        if (!(starved && x_issued == 0)) c12_load_x(C, xbuf(x_issued), tile(x_issued), &xfull[x_issued]);
+      if (!fwd_wait(bfull, 0, s_abort, C.polls) || !fwd_wait(a1full, 0, s_abort, C.polls)) ok = false;
       if (ok) conv1(0);
       int i = 0;
       for (; ok && i < n; ++i) {
@@ -703,18 +707,18 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
           ++x_issued;
         }
         if (i + 1 < n) {  // conv1 of the next tile
-          if (!fwd_wait(a1full, (i + 1) & 1, s_abort)) { ok = false; break; }
+          if (!fwd_wait(a1full, (i + 1) & 1, s_abort, C.polls)) { ok = false; break; }
           conv1(i + 1);
         }
         if (i >= 2) {  // the output of tile i - 2, once its staging tile is written; the tile is
                        // handed back as soon as the store has read it
-          if (!fwd_wait(outfull, i & 1, s_abort)) { ok = false; break; }
+          if (!fwd_wait(outfull, i & 1, s_abort, C.polls)) { ok = false; break; }
           tma_store_2d(&C.ty, out, 0, tile(i - 2) * kBM);
           bulk_commit();
           bulk_wait_read0();
           mbar_arrive(outfree);
         }
-        if (!fwd_wait(&a2full[i & 1], (i >> 1) & 1, s_abort)) { ok = false; break; }
+        if (!fwd_wait(&a2full[i & 1], (i >> 1) & 1, s_abort, C.polls)) { ok = false; break; }
         tc_fence_after();
         const u64 da2 = sw_desc<32>(smem_addr(aset(i)));
 #pragma unroll
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
         tc_commit(&mma[i & 1]);
       }
       for (int j = i >= 2 ? i - 2 : 0; ok && j < i; ++j) {  // the last two tiles' outputs
-        if (!fwd_wait(outfull, j & 1, s_abort)) {
+        if (!fwd_wait(outfull, j & 1, s_abort, C.polls)) {
           ok = false;
           break;
         }
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
       if (!ok) {
         fwd_fail(s_abort, C.err);
         for (int h = x_issued > 2 ? x_issued - 2 : 0; h < x_issued; ++h)
-          fwd_drain(&xfull[h & 1], (h >> 1) & 1);  // the input loads in flight land
+          if (!(starved && h == 0)) fwd_drain(&xfull[h & 1], (h >> 1) & 1);  // the input loads in flight land
       }
       tc_commit(drain);  // arrives once every MMA issued above has completed
       fwd_drain(drain, 0);
@@ -752,8 +756,8 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
     // staging tile of tile number j from conv2 accumulator j % 2; the tile is free once the store
     // of tile j - 1 has read it
     auto epilogue = [&](int j, bool ok) -> bool {
-      ok = warp_wait(&mma[j & 1], (j >> 1) & 1, s_abort, ok);
-      if (j >= 1) ok = warp_wait(outfree, (j - 1) & 1, s_abort, ok);
+      ok = warp_wait(&mma[j & 1], (j >> 1) & 1, s_abort, ok, C.polls);
+      if (j >= 1) ok = warp_wait(outfree, (j - 1) & 1, s_abort, ok, C.polls);
       if (ok && grp < 4) {  // four column groups of 16
         tc_fence_after();
         const int r = q * 32 + lane;
@@ -773,7 +777,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
 
     bool ok = true;
     if (n > 0) {  // im2col of the first tile
-      ok = warp_wait(&xfull[0], 0, s_abort, ok);
+      ok = warp_wait(&xfull[0], 0, s_abort, ok, C.polls);
       if (ok) {
         c12_im2col(plan, xbuf(0), A1, 8 * (tile(0) & 1));
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -784,9 +788,9 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
     for (; ok && i < n; ++i) {
       // conv1 of tile i done: so are the conv2 MMAs of tile i - 2 (issued before it), which read
       // operand set i % 2, and the im2col buffer is free
-      ok = warp_wait(&d1[i & 1], (i >> 1) & 1, s_abort, ok);
+      ok = warp_wait(&d1[i & 1], (i >> 1) & 1, s_abort, ok, C.polls);
       if (ok && i + 1 < n) {
-        ok = warp_wait(&xfull[(i + 1) & 1], ((i + 1) >> 1) & 1, s_abort, ok);
+        ok = warp_wait(&xfull[(i + 1) & 1], ((i + 1) >> 1) & 1, s_abort, ok, C.polls);
         if (ok) {
           c12_im2col(plan, xbuf(i + 1), A1, 8 * (tile(i + 1) & 1));
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -133,3 +133,30 @@ def test_cnn_tma_gemm_wait_runs_out_and_recovers(gm):
     scale = np.sqrt(ref.conv_fwd(xr ** 2, wr ** 2) + br ** 2)
     assert np.all(np.abs(y - want) <= 2.0 ** -8 * np.abs(want) + 1e-4 * scale + 1e-30)
     cnn.check_device_error()
+
+
+def test_cnn_fused_layers_wait_runs_out_and_recovers(gm):
+    # the fused first two layers: block 0 of the next launch issues no copy of its first input
+    # rows, so the compute warps' wait runs out; the flag reads 1 once and the next call equals
+    # the two layers bit for bit
+    import ctypes
+    import torch
+    from paper_2404_07780_b300 import cnn
+    L = cnn.lib()
+    rng = np.random.default_rng(22)
+    bf = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda().to(torch.bfloat16)
+    x = bf(rng.normal(size=(5, 64, 64, 1)))
+    w1, w2 = bf(rng.normal(size=(32, 3, 3, 1)) / 3.0), bf(rng.normal(size=(64, 3, 3, 32)) / 17.0)
+    b1 = torch.from_numpy((rng.normal(size=32) * 0.1).astype(np.float32)).cuda()
+    b2 = torch.from_numpy((rng.normal(size=64) * 0.1).astype(np.float32)).cuda()
+    flag = ctypes.c_int(0)
+    assert L.gm_cnn_check_error(ctypes.byref(flag)) == 0
+    assert L.gm_cnn_test_starve_next(POLLS) == 0
+    cnn.conv12_fwd(x, w1, b1, w2, b2)
+    torch.cuda.synchronize()
+    assert L.gm_cnn_check_error(ctypes.byref(flag)) == 0 and flag.value == 1
+    assert L.gm_cnn_check_error(ctypes.byref(flag)) == 0 and flag.value == 0
+    y = cnn.conv12_fwd(x, w1, b1, w2, b2)
+    two = cnn.conv_fwd(cnn.conv_fwd(x, w1, b1, relu=True), w2, b2, relu=True)
+    assert torch.equal(y.view(torch.int16), two.view(torch.int16))
+    cnn.check_device_error()
