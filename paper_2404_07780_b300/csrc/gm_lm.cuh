@@ -484,9 +484,13 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
   const double gf = lane < P ? gb[lane] : 0.0;
 
   if (st == ST_RUNNING && accepted) {
-    // Gauss-Newton decrement g^T A^-1 g over the parameters not held
+    // Gauss-Newton decrement g^T A^-1 g over the parameters not held.  The system matrix is
+    // positive definite, so g^T A^-1 g >= |g|^2 / lambda_max >= |g|^2 / trace: while that bound
+    // is above the threshold the test cannot pass, and the factorisation is skipped (the
+    // sums are the same in every lane, so the warp takes one branch)
     const double r = warp_step_system(Ab, gb, P, 0.0, held, M, lane);
-    if (warp_cholesky(M, P, lane)) {
+    const double r2 = warp_sum(r * r), tr = warp_sum(lane < P ? M[lane * P + lane] : 0.0);
+    if (!(r2 > O.gtol * chi2_best * tr) && warp_cholesky(M, P, lane)) {
       const double x = warp_chol_solve(M, P, lane, r);
       const double gn = warp_sum(lane < P ? r * x : 0.0);
       if (gn >= 0.0 && gn <= O.gtol * chi2_best) st = ST_CONVERGED;
