@@ -227,12 +227,13 @@ struct PixArgs {
 constexpr int kPixThreads = 256;
 constexpr int kPixPerThread = 4;  // pixels per thread in one chunk of a pixel kernel
 constexpr int kPixPart = 2 * kPixThreads * kPixPerThread;  // pixels of a stamp per block (FP32 sums of <= 8
-                                                           // terms per thread before the FP64 block sum)
+                                                           // terms per thread before the block sum)
 
 __host__ __device__ inline int pix_parts(int H, int W) { return (H * W + kPixPart - 1) / kPixPart; }
 
 // The pair's sums over one part of the stamp into its partials: warp sums by
-// recursive halving, then FP64 over the warps in warp order (deterministic).
+// recursive halving, then the compensated sum over the warps in warp order
+// (deterministic).
 template <int NA>
 __device__ __forceinline__ void pix_pair_sums(const PixArgs& A, float (&red)[2][NA], float* s_red, int g0, int part,
                                               int n_parts) {
@@ -248,9 +249,7 @@ __device__ __forceinline__ void pix_pair_sums(const PixArgs& A, float (&red)[2][
     const int h = t / NA, e = t - h * NA;
     const int g = g0 + h;
     if (g >= A.G) continue;
-    double s = 0.0;
-    for (int w = 0; w < kPixThreads / 32; ++w) s += (double)s_red[(w * 2 + h) * NA + e];
-    A.partial[((size_t)g * n_parts + part) * NA + e] = s;
+    A.partial[((size_t)g * n_parts + part) * NA + e] = compensated_sum(s_red + h * NA + e, 2 * NA, kPixThreads / 32);
   }
 }
 

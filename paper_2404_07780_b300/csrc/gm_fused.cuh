@@ -37,8 +37,9 @@
 //       the start of the current one, while the other warps correlate.
 //   Then the unconvolved components (the sky) are added at the output pixels,
 //   and NORMAL mode forms r = D - M, w = Omega/sigma^2 and accumulates chi^2,
-//   J^T W r and J^T W J (FP32 per thread, warp shuffles, cross-warp sum, one
-//   FP64 partial per tile); MODEL mode writes the model and component images.
+//   J^T W r and J^T W J (FP32 per thread, warp shuffles, a compensated FP32
+//   cross-warp sum, one FP64 partial per tile); MODEL mode writes the model and
+//   component images.
 //
 // The correlation is M[i,j] = sum_ab P[a,b] I[i+a-c, j+b-c] (cross-correlation,
 // torch conv2d semantics, App. C of arxiv 2404.07780).  The window starts at
@@ -752,6 +753,23 @@ __device__ __forceinline__ void reduce_range(const float* s_out, float* s_red, c
   warp_sum_scatter(acc, lane, [&](int e, float v) { s_red[warp * NA + E0 + e] = v; });
 }
 
+// Sum of n FP32 values v[0], v[stride], ... in that order, in FP32 with a running
+// compensation term (Neumaier's variant of Kahan summation): s + c is within about
+// n u^2 sum|v| of the exact sum (u = 2^-24), as close as an FP64 accumulation of the
+// same values, at the FP32 rate.  FP64 arithmetic issues at a small fraction of that
+// rate here, and a chain of n FP64 conversions and additions on the few summing
+// threads held the whole block for about a microsecond per tile.
+__device__ __forceinline__ double compensated_sum(const float* v, int stride, int n) {
+  float s = v[0], c = 0.f;
+  for (int w = 1; w < n; ++w) {
+    const float x = v[w * stride];
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  return (double)s + (double)c;
+}
+
 // Accumulate J^T W J (packed upper triangle), J^T W r and chi^2 for P free
 // parameters over this thread's pixels of the tile, reduce over the block and
 // write the tile's FP64 partial sums.  NCH > 1 accumulates the entries in that
@@ -795,11 +813,7 @@ __device__ __forceinline__ void reduce_tile(const FusedArgs& A, const float* s_o
     reduce_range<P, kPx, 2 * NA / 3, NA>(s_out, s_red, dv, sv, use, tid, nthr, lane, warp);
   }
   __syncthreads();
-  for (int e = tid; e < NA; e += nthr) {
-    double s = 0.0;
-    for (int w = 0; w < nwarp; ++w) s += (double)s_red[w * NA + e];
-    A.partial[prow * NA + e] = s;
-  }
+  for (int e = tid; e < NA; e += nthr) A.partial[prow * NA + e] = compensated_sum(s_red + e, NA, nwarp);
 }
 
 // ---------------------------------------------------------------------------
@@ -867,6 +881,19 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
     const int H = I.geo.H, W = I.geo.W, K = I.geo.K, rw = I.geo.rw;
     const int c = (K - 1) / 2;
     const int i0 = (I.tile / I.geo.tiles_x) * kTile, j0 = (I.tile % I.geo.tiles_x) * kTile;
+    if (MODE == MODE_NORMAL && tid < 6 * kTile) {
+      // bring the tile's image, sigma and mask rows into L1 while the CTA correlates, so
+      // that the reduction's loads do not wait on DRAM: one line at each end of a row
+      // segment (the segment may straddle two 128-byte lines)
+      const int r = tid % kTile, which = tid / kTile;
+      const int arr = which >> 1, end = which & 1;
+      if (i0 + r < H && (arr < 2 || A.mask)) {
+        const size_t gp = (size_t)I.geo.pix + (size_t)(i0 + r) * W + j0 + (end ? min(kTile, W - j0) - 1 : 0);
+        const void* ptr = arr == 0 ? (const void*)(A.image + gp)
+                        : arr == 1 ? (const void*)(A.sigma + gp) : (const void*)(A.mask + gp);
+        asm volatile("prefetch.L1 [%0];" ::"l"(ptr));
+      }
+    }
     // this item's PSF rows (s_psf) and constants arrive with its first window
     const float* s_cc = s_cc0 + slot * cc_n;
     const float* s_scale = s_scale0 + slot * sc_n;
