@@ -16,8 +16,9 @@
 //   items by decreasing cost (PSF area, then stamp size), so the last items
 //   handed out are the cheap ones.  Per item and per "pass" of up to four
 //   channel pairs:
-//     * one thread issues a TMA tile load (cp.async.bulk.tensor.3d) of the
-//       (32+K-1) x rw window of every pair plane of the pass into shared
+//     * TMA tile loads (cp.async.bulk.tensor.3d, one per pair plane, issued
+//       by lane 0 of different warps) bring the (32+K-1) x rw window of every
+//       pair plane of the pass into shared
 //       memory, through the tensor map of the galaxy's (H, W, K) class;
 //       out-of-stamp rows and columns come back as zeros, which is the zero
 //       padding of conv2d(..., padding="same");
@@ -33,8 +34,9 @@
 //       two or four groups by PSF rows;
 //     * the next load (next pass or next item) is issued as soon as every
 //       warp has finished reading the window, so it overlaps the stores and
-//       the reduction.  Thread 0 claims the next item and reads its record at
-//       the start of the current one, while the other warps correlate.
+//       the reduction.  Thread 0 claims the next item and reads its record
+//       once the current item's first window has landed, while the other warps
+//       correlate.
 //   Then the unconvolved components (the sky) are added at the output pixels,
 //   and NORMAL mode forms r = D - M, w = Omega/sigma^2 and accumulates chi^2,
 //   J^T W r and J^T W J (FP32 per thread, warp shuffles, a compensated FP32
@@ -277,37 +279,48 @@ __device__ __forceinline__ void fetch_item(const FusedArgs& A, int n_items, int 
   dst->geo = A.geo[it.x];
 }
 
-// Thread 0: issue the loads of pass `pass` of item I.  Pass 0 also brings the
-// galaxy's padded PSF rows into s_psf and its constants into the item's
-// constant buffers (s_cc, s_scale of `slot`), on the same mbarrier.
+// Issue the loads of pass `pass` of item I: the pass's pair-plane windows
+// (copies 0 .. npairs-1) and, for pass 0, the galaxy's padded PSF rows into
+// s_psf and its constants into the item's constant buffers (s_cc, s_scale of
+// `slot`; copies npairs .. npairs+2), all on one mbarrier.  The calling thread
+// issues copies k0, k0 + kstep, ... and, with `arrive`, makes the barrier's one
+// arrival with the pass's byte count.  The copies may be spread over several
+// threads (one per warp: each copy instruction holds its thread for hundreds of
+// cycles) and may complete before the arrival: an mbarrier's transaction count
+// may go below zero, and the phase completes only once the arrival is made and
+// every byte has landed.
 __device__ __forceinline__ void issue_pass(const FusedArgs& A, const ItemInfo& I, float2* s_in, u64* bar, int pass,
-                                           float* s_psf, float* s_cc, float* s_scale) {
+                                           float* s_psf, float* s_cc, float* s_scale, int k0 = 0, int kstep = 1,
+                                           bool arrive = true) {
   const GalGeom& G = I.geo;
   const int K = G.K, c = (K - 1) / 2, cpad = c & 1;
-  const int i0 = (I.tile / G.tiles_x) * kTile, j0 = (I.tile % G.tiles_x) * kTile;
   const int first = pass * A.pp;
   const int npairs = min(A.pp, A.m.ncp - first);
+  const int ncopy = npairs + (pass == 0 ? 3 : 0);
   const unsigned plane_bytes = (unsigned)(kTile + K - 1) * G.rw * 8u;
-  const CUtensorMap* map = &A.tmap;
-  if (A.maps) {
-    map = A.maps + G.cls;
-    // the map was written to global memory by an ordinary copy: order that write before the TMA unit reads it
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<u64>(map))
-                 : "memory");
-  }
   const unsigned psf_bytes = (unsigned)K * psf_row_floats(K) * 4u;
   const unsigned cc_bytes = (unsigned)A.m.n_comp * kCC * 4u;
   const unsigned sc_bytes = (unsigned)scale_stride(A.m.n_slots) * 4u;
-  // order this CTA's earlier generic-proxy reads of the buffers before the async-proxy writes
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(bar, plane_bytes * npairs + (pass == 0 ? psf_bytes + cc_bytes + sc_bytes : 0u));
-  const int x = 2 * (j0 - c - cpad);  // even pair index: 16-byte aligned start
-  for (int q = 0; q < npairs; ++q) tma_load_3d(s_in + (size_t)q * A.plane, map, x, i0 - c, G.z0 + first + q, bar);
-  if (pass == 0) {
-    bulk_load(s_psf, A.psf_pad + (size_t)I.g * A.psf_stride, psf_bytes, bar);
-    bulk_load(s_cc, A.cconst + (size_t)I.g * A.m.n_comp * kCC, cc_bytes, bar);
-    bulk_load(s_scale, A.scale + (size_t)I.g * scale_stride(A.m.n_slots), sc_bytes, bar);
+  if (k0 < ncopy) {
+    const int i0 = (I.tile / G.tiles_x) * kTile, j0 = (I.tile % G.tiles_x) * kTile;
+    const CUtensorMap* map = &A.tmap;
+    if (A.maps) {
+      map = A.maps + G.cls;
+      // the map was written to global memory by an ordinary copy: order that write before the TMA unit reads it
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<u64>(map))
+                   : "memory");
+    }
+    // order this CTA's earlier generic-proxy reads of the buffers before the async-proxy writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const int x = 2 * (j0 - c - cpad);  // even pair index: 16-byte aligned start
+    for (int k = k0; k < ncopy; k += kstep) {
+      if (k < npairs) tma_load_3d(s_in + (size_t)k * A.plane, map, x, i0 - c, G.z0 + first + k, bar);
+      else if (k == npairs) bulk_load(s_psf, A.psf_pad + (size_t)I.g * A.psf_stride, psf_bytes, bar);
+      else if (k == npairs + 1) bulk_load(s_cc, A.cconst + (size_t)I.g * A.m.n_comp * kCC, cc_bytes, bar);
+      else bulk_load(s_scale, A.scale + (size_t)I.g * scale_stride(A.m.n_slots), sc_bytes, bar);
+    }
   }
+  if (arrive) mbar_expect_tx(bar, plane_bytes * npairs + (pass == 0 ? psf_bytes + cc_bytes + sc_bytes : 0u));
 }
 
 // ---------------------------------------------------------------------------
@@ -873,11 +886,6 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
     __syncthreads();  // the previous item is done with s_psf, s_cc, s_scale, s_out, s_red and s_info[slot ^ 1]
     const ItemInfo& I = s_info[slot];
     if (!I.valid) break;
-    if (tid == 0) {
-      // claim and read the next item now; its loads are issued after this item's last window
-      const int nxt = (int)gridDim.x + atomicAdd(A.queue, 1);
-      fetch_item(A, n_items, nxt, &s_info[slot ^ 1]);
-    }
     const int H = I.geo.H, W = I.geo.W, K = I.geo.K, rw = I.geo.rw;
     const int c = (K - 1) / 2;
     const int i0 = (I.tile / I.geo.tiles_x) * kTile, j0 = (I.tile % I.geo.tiles_x) * kTile;
@@ -917,6 +925,14 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
       }
       mbar_try_wait(bar, phase);  // completes at once: acquires the TMA writes for this thread
       phase ^= 1u;
+      if (pass == 0 && tid == 0) {
+        // claim and read the next item; its loads are issued after this item's last window.
+        // Done here rather than before the wait, so that the other warps do not wait for
+        // the claim's round trips: warp 0 starts correlating late, and the other warps of
+        // its scheduler keep the FMA pipe busy meanwhile
+        const int nxt = (int)gridDim.x + atomicAdd(A.queue, 1);
+        fetch_item(A, n_items, nxt, &s_info[slot ^ 1]);
+      }
 
       // the pass's pairs spread evenly over the groups: group q takes npass / ngroups
       // pairs, one more for the first npass % ngroups groups (at most CPT)
@@ -941,13 +957,18 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
         correlate_pairs<2, !WIDE>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, ga_lo, ga_hi);
       else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
       __syncthreads();  // every warp is done reading the window
-      if (tid == 0) {
+      {
+        // the next window's copies, one per warp from the last warp down (lane 0), so that no
+        // warp is held for all of them; thread 0 makes the barrier's arrival
+        const int nwarp = nthr >> 5, wid = tid >> 5;
+        const int k0 = (tid & 31) ? 1 << 30 : nwarp - 1 - wid;
         if (pass + 1 < A.passes) {
-          issue_pass(A, I, s_in, bar, pass + 1, s_psf, nullptr, nullptr);
-          inflight = true;
+          issue_pass(A, I, s_in, bar, pass + 1, s_psf, nullptr, nullptr, k0, nwarp, tid == 0);
+          inflight = tid == 0;
         } else if (s_info[slot ^ 1].valid) {
-          issue_pass(A, s_info[slot ^ 1], s_in, bar, 0, s_psf, s_cc0 + (slot ^ 1) * cc_n, s_scale0 + (slot ^ 1) * sc_n);
-          inflight = true;
+          issue_pass(A, s_info[slot ^ 1], s_in, bar, 0, s_psf, s_cc0 + (slot ^ 1) * cc_n, s_scale0 + (slot ^ 1) * sc_n,
+                     k0, nwarp, tid == 0);
+          inflight = tid == 0;
         }
       }
       if (split) {
