@@ -875,10 +875,13 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
   const int t = tid - grp * kGroupThreads;
   const int lane = t & 31, wig = t >> 5;
   // warp w runs on scheduler w % 4, next to the warps of the same index in the other
-  // groups: odd groups take the 8-row blocks in reverse order, so that at a stamp's
-  // top or bottom edge (where the row skip shortens some blocks' PSF-row ranges) each
-  // scheduler gets a short and a long block rather than two of the same
-  const int wb = (grp & 1) ? 3 - wig : wig;
+  // groups.  At a stamp's top or bottom edge the row skip shortens some 8-row blocks'
+  // PSF-row ranges (28, 36, 41, 41 rows for K = 41), so the blocks are dealt out such
+  // that every scheduler gets the same mix: with four groups, group g takes block
+  // (w + g) mod 4 (each scheduler one of every block); with two, the odd group takes
+  // them in reverse order (a short and a long block per scheduler)
+  const int ngroup = nthr / kGroupThreads;
+  const int wb = ngroup == 4 ? (wig + grp) & 3 : (grp & 1) ? 3 - wig : wig;
   const int row = wb * 8 + (lane & 7), col0 = (lane >> 3) * 8;
   const int row0 = wb * 8;
 
@@ -958,10 +961,12 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
       else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
       __syncthreads();  // every warp is done reading the window
       {
-        // the next window's copies, one per warp from the last warp down (lane 0), so that no
-        // warp is held for all of them; thread 0 makes the barrier's arrival
-        const int nwarp = nthr >> 5, wid = tid >> 5;
-        const int k0 = (tid & 31) ? 1 << 30 : nwarp - 1 - wid;
+        // the next window's copies, one per warp (lane 0), so that no warp is held for all
+        // of them; thread 0 makes the barrier's arrival
+        // (odd groups first: in a pass split by PSF rows they store after the even ones)
+        const int nwarp = nthr >> 5;
+        const int rank = (grp & 1) ? (ngroup - 1 - grp) >> 1 : ngroup / 2 + (ngroup - 1 - grp) / 2;
+        const int k0 = (tid & 31) ? 1 << 30 : rank * 4 + 3 - wig;
         if (pass + 1 < A.passes) {
           issue_pass(A, I, s_in, bar, pass + 1, s_psf, nullptr, nullptr, k0, nwarp, tid == 0);
           inflight = tid == 0;
@@ -1023,7 +1028,9 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
         }
       }
     }
-    __syncthreads();
+    // no barrier here: the loops above and the outputs below touch only this thread's own
+    // pixels (tid, tid + nthr, ...), and the barrier after the passes ordered the
+    // correlation's stores before both
 
     // ---- outputs ----
     const size_t pix0 = (size_t)I.geo.pix;
