@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128, 4) k_adjoint(const __grid_constant__ AdjA
     mbar_try_wait(bar, phase);
     phase ^= 1u;
     u64 acc[1][8];
-    correlate_pairs<1>(acc, s_in, s_psf, 0, A.plane, A.rw, K, row, col0, a_lo, a_hi);
+    correlate_pairs<1>(acc, s_in, s_psf, 0, A.plane, A.rw, K, row, col0, a_lo, a_hi, col_all(K));
     __syncthreads();  // every warp is done reading the window
     if (tid == 0 && item + 1 < it_hi) {
       adj_issue(A, s_in, bar, item + 1);

@@ -485,16 +485,54 @@ __device__ __forceinline__ void corr_pair_f(u64 (&acc)[CP][8], u64 (&w)[CP][10],
   cur = nx;
 }
 
+// The taps of a PSF row that one warp runs, from the float layout's chunk
+// structure: the head half (cpad = 1: the zero position and tap 0), nf full
+// 2-tap chunks starting at position 2 cpad + 4 m (m float4s of leading chunks
+// skipped), the tail half (cpad = 0: tap K-1 and the zero position).  A warp
+// whose 8-column range sees `lead` leading and `trail` trailing taps outside
+// the stamp for every one of its pixels skips the whole chunks and halves
+// among them (lead + trail < K; a warp with no tap inside runs no row).
+struct ColSkip {
+  int head, m, nf, tail;
+};
+
+__device__ __forceinline__ ColSkip col_skip(int K, int lead, int trail) {
+  const int cpad = ((K - 1) >> 1) & 1;
+  ColSkip r;
+  r.head = cpad && lead == 0;
+  r.m = max(0, (lead - cpad) >> 2);  // chunk 2k (k < 2m) covers taps up to cpad + 4m - 1 < lead
+  r.tail = !cpad && trail == 0;
+  const int nt = cpad ? trail >> 1 : max(0, (trail - 1) >> 1);  // trailing full chunks all outside
+  r.nf = ((K - 1) >> 1) - 2 * r.m - nt;
+  return r;
+}
+
+__device__ __forceinline__ ColSkip col_all(int K) { return col_skip(K, 0, 0); }
+
 // One PSF row into acc from the float layout above: the head half (cpad = 1,
 // the row's float 3), nf full chunks two per float4 (ten per loop iteration),
-// the tail half (cpad = 0).
+// the tail half (cpad = 0); the chunks a warp skips at the stamp's left or
+// right edge are left out (cs).
 template <int CP>
 __device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const (&irow)[CP], const float* prow,
-                                         int nf, int cpad) {
+                                         const ColSkip& cs, int cpad) {
   u64 w[CP][10];
   const float4* pf = reinterpret_cast<const float4*>(prow);
   int b = 0;
-  if (cpad) {
+  int nf = cs.nf;
+  if (!cs.head) {
+    // first full chunk at position 2 cpad + 4 m, ring at rotation 0
+    b = 2 * cpad + 4 * cs.m;
+    pf += cpad + cs.m;
+#pragma unroll
+    for (int q = 0; q < CP; ++q)
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + b + e);
+        w[q][e] = v.x;
+        w[q][e + 1] = v.y;
+      }
+  } else {
 #pragma unroll
     for (int q = 0; q < CP; ++q)
 #pragma unroll
@@ -507,15 +545,6 @@ __device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const 
     corr_chunk_f<CP, 4, 2>(acc, w, 0.f, h.w, irow, 0);
     b = 2;
     ++pf;
-  } else {
-#pragma unroll
-    for (int q = 0; q < CP; ++q)
-#pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(irow[q] + e);
-        w[q][e] = v.x;
-        w[q][e + 1] = v.y;
-      }
   }
   float4 cur = pf[0];
   for (; nf >= 10; nf -= 10) {
@@ -528,7 +557,7 @@ __device__ __forceinline__ void corr_row(u64 (&acc)[CP][8], const float2* const 
     b += 20;
   }
   // nf = 0..9 full chunks (rotations 0, 1, ...) from cur on, then the tail half
-  const bool tail = !cpad;
+  const bool tail = cs.tail;
   if (nf == 0) {
     if (tail) corr_chunk_f<CP, 0, 1>(acc, w, cur.x, 0.f, irow, b);
     return;
@@ -583,15 +612,28 @@ __device__ __forceinline__ const float* psf_row_ptr(const float* s_psf, int a, i
   return s_psf + a * psf_row_floats(K);
 }
 
+// A row in either PSF layout (the packed-pair rows of the adjoint take no column skip).
+template <int CP>
+__device__ __forceinline__ void corr_row_any(u64 (&acc)[CP][8], const float2* const (&irow)[CP], const float* prow,
+                                             const ColSkip& cs, int, int cpad) {
+  corr_row<CP>(acc, irow, prow, cs, cpad);
+}
+template <int CP>
+__device__ __forceinline__ void corr_row_any(u64 (&acc)[CP][8], const float2* const (&irow)[CP], const u64* prow,
+                                             const ColSkip&, int nf, int cpad) {
+  corr_row<CP>(acc, irow, prow, nf, cpad);
+}
+
 // Correlate CP pair planes (local indices lp0 .. lp0+CP-1 of the pass buffer)
-// for one thread's 8 output pixels over PSF rows [a_lo, a_hi).  With BLOCKS,
+// for one thread's 8 output pixels over PSF rows [a_lo, a_hi), each row's taps
+// as cs gives them (float PSF rows).  With BLOCKS,
 // each block of kRowBlock PSF rows is summed into its own partial first (lower
 // FP32 accumulation error, at CP x 8 more registers: the 512-thread two-pair
 // instances go without, to stay within 128 registers).
 template <int CP, bool BLOCKS = true, class PsfT = u64>
 __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2* s_in, const PsfT* s_psf,
                                                 int lp0, int plane, int rw, int K, int row, int col0, int a_lo,
-                                                int a_hi) {
+                                                int a_hi, const ColSkip& cs) {
   const u64 one2 = pack2(1.f, 1.f);
 #pragma unroll
   for (int q = 0; q < CP; ++q)
@@ -604,7 +646,7 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
       const float2* irow[CP];
 #pragma unroll
       for (int q = 0; q < CP; ++q) irow[q] = s_in + (size_t)(lp0 + q) * plane + (size_t)(row + a) * rw + col0;
-      corr_row<CP>(acc, irow, psf_row_ptr(s_psf, a, K), nf, cpad);
+      corr_row_any<CP>(acc, irow, psf_row_ptr(s_psf, a, K), cs, nf, cpad);
     }
     return;
   }
@@ -619,7 +661,7 @@ __device__ __forceinline__ void correlate_pairs(u64 (&acc)[CP][8], const float2*
       const float2* irow[CP];
 #pragma unroll
       for (int q = 0; q < CP; ++q) irow[q] = s_in + (size_t)(lp0 + q) * plane + (size_t)(row + a) * rw + col0;
-      corr_row<CP>(part, irow, psf_row_ptr(s_psf, a, K), nf, cpad);
+      corr_row_any<CP>(part, irow, psf_row_ptr(s_psf, a, K), cs, nf, cpad);
     }
 #pragma unroll
     for (int q = 0; q < CP; ++q)
@@ -882,8 +924,6 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
   // them in reverse order (a short and a long block per scheduler)
   const int ngroup = nthr / kGroupThreads;
   const int wb = ngroup == 4 ? (wig + grp) & 3 : (grp & 1) ? 3 - wig : wig;
-  const int row = wb * 8 + (lane & 7), col0 = (lane >> 3) * 8;
-  const int row0 = wb * 8;
 
   for (;;) {
     __syncthreads();  // the previous item is done with s_psf, s_cc, s_scale, s_out, s_red and s_info[slot ^ 1]
@@ -908,9 +948,27 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
     // this item's PSF rows (s_psf) and constants arrive with its first window
     const float* s_cc = s_cc0 + slot * cc_n;
     const float* s_scale = s_scale0 + slot * sc_n;
-    // PSF rows whose 8 input rows (for this warp) all fall outside the stamp are skipped
-    const int a_lo = max(0, c - i0 - row0 - 7);
-    const int a_hi = min(K, c - i0 + H - row0);
+    // The item's lane map.  Warp block wb is 8 rows x 32 columns, and PSF rows whose
+    // input rows all fall outside the stamp for the warp's 8 rows are skipped -- or, for
+    // a tile whose zero padding lies in columns only (a left or right edge tile away from
+    // the top and bottom), 32 rows x 8 columns, and each PSF row's taps whose input
+    // columns fall outside the stamp for all of the warp's columns are skipped (col_skip)
+    const bool row_pad = i0 - c < 0 || i0 + kTile - 1 + c >= H;
+    const bool col_pad = j0 - c < 0 || j0 + kTile - 1 + c >= W;
+    const bool by_col = col_pad && !row_pad;
+    const int row = by_col ? lane : wb * 8 + (lane & 7);
+    const int col0 = by_col ? wb * 8 : (lane >> 3) * 8;
+    int a_lo = 0, a_hi = K;
+    ColSkip cs = col_all(K);
+    if (by_col) {
+      const int jl = j0 + col0;
+      const int lead = max(0, c - (jl + 7)), trail = max(0, K - (c + W - jl));
+      if (lead + trail >= K) a_hi = 0;  // none of the warp's taps reads inside the stamp
+      else cs = col_skip(K, lead, trail);
+    } else {
+      a_lo = max(0, c - i0 - wb * 8 - 7);
+      a_hi = min(K, c - i0 + H - wb * 8);
+    }
 
     for (int pass = 0; pass < A.passes; ++pass) {
       // wait for this pass's window (thread 0 polls with a bound, the CTA agrees)
@@ -957,8 +1015,8 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
       u64 acc2[2][8];
       u64 acc1[1][8];
       if (CPT == 2 && npair == 2)
-        correlate_pairs<2, !WIDE>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, ga_lo, ga_hi);
-      else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi);
+        correlate_pairs<2, !WIDE>(acc2, s_in, s_psf, lp0, A.plane, rw, K, row, col0, ga_lo, ga_hi, cs);
+      else if (npair == 1) correlate_pairs<1>(acc1, s_in, s_psf, lp0, A.plane, rw, K, row, col0, a_lo, a_hi, cs);
       __syncthreads();  // every warp is done reading the window
       {
         // the next window's copies, one per warp (lane 0), so that no warp is held for all
