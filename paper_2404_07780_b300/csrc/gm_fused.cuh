@@ -81,6 +81,9 @@ struct ChanMap {
   int chan[kMaxComp][8];     // d/dp_k of comp c -> channel (-1: not needed)
   int comp_chan[kMaxComp];   // MODEL mode: channel holding comp c's own image (-1: none)
   int any_unconv;
+  int sky_comp;              // NORMAL mode: the one unconvolved component when it is a flat sky
+                             // (-1: none such), written without evaluating the component
+  int sky_ch;                // that sky's derivative channel, the last one (-1: its level is fixed)
   int nch_conv;              // correlated channels
   int ncp;                   // channel pairs = ceil(nch_conv / 2)
   int nch_tot;               // channels at the output pixels (correlated + unconvolved-only)
@@ -1050,11 +1053,25 @@ __global__ void __launch_bounds__(CPT == 1 || WIDE ? 512 : 256, 1) k_fused(const
     __syncthreads();
 
     // ---- unconvolved components at the output pixels ----
-    for (int pix = tid; pix < kTilePix; pix += nthr) {
+    const bool sky_fast = MODE == MODE_NORMAL && m.sky_comp >= 0;
+    if (sky_fast) {
+      // a lone flat sky: its level onto the model and 1 x its slot scale as its derivative
+      // channel, the values the general loop below writes, without evaluating the component
+      const float level = s_cc[m.sky_comp * kCC + 8];
+      const int sch = m.sky_ch;
+      const float dsc = sch >= 0 ? 1.f * s_scale[m.slot[m.sky_comp][0]] : 0.f;
+      for (int pix = tid; pix < kTilePix; pix += nthr) {
+        const int i = i0 + pix / kTile, j = j0 + pix % kTile;
+        const int op = out_idx(pix);
+        if (sch >= 0) s_out[sch * kTilePix + op] = (i < H && j < W) ? dsc : 0.f;
+        if (i < H && j < W) s_out[op] += level;
+      }
+    }
+    for (int pix = tid; pix < kTilePix && !sky_fast; pix += nthr) {
       const int op = out_idx(pix);
       for (int ch = m.nch_conv; ch < m.nch_tot; ++ch) s_out[ch * kTilePix + op] = 0.f;
     }
-    if (m.any_unconv) {
+    if (m.any_unconv && !sky_fast) {
       // one component at a time: its kind, channels and scales are read once, and the
       // same thread owns the same pixels as in the loop above
       for (int cm = 0; cm < m.n_comp; ++cm) {

@@ -317,6 +317,19 @@ ChanMap chan_map(const Plan& pl) {
   m.ncp = pl.ncp;
   m.nch_tot = pl.nch_tot;
   m.n_slots = D.n_slots;
+  // a lone unconvolved flat sky (no magnitude or boxiness flag) whose level, when free,
+  // owns the last channel: the tile kernel writes it without evaluating the component
+  m.sky_comp = m.sky_ch = -1;
+  int n_unconv = 0, last = -1;
+  for (int c = 0; c < D.n_comp; ++c)
+    if (!m.conv[c]) ++n_unconv, last = c;
+  if (n_unconv == 1 && m.kind[last] == SKY) {
+    const int ch = m.chan[last][0];
+    if (ch < 0 ? m.nch_tot == m.nch_conv : (ch == m.nch_tot - 1 && m.nch_tot == m.nch_conv + 1)) {
+      m.sky_comp = last;
+      m.sky_ch = ch;
+    }
+  }
   return m;
 }
 
