@@ -84,6 +84,8 @@ struct ChanMap {
   int sky_comp;              // NORMAL mode: the one unconvolved component when it is a flat sky
                              // (-1: none such), written without evaluating the component
   int sky_ch;                // that sky's derivative channel, the last one (-1: its level is fixed)
+  int ident_comp;            // NORMAL mode: the one convolved component when its parameters are all
+                             // free and own channels 1 .. np in order (-1: none such)
   int nch_conv;              // correlated channels
   int ncp;                   // channel pairs = ceil(nch_conv / 2)
   int nch_tot;               // channels at the output pixels (correlated + unconvolved-only)
@@ -193,6 +195,32 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
     for (int t = tid; t < m.n_comp * kCC; t += 256) s_cc[t] = A.cconst[(size_t)g * m.n_comp * kCC + t];
     for (int t = tid; t < m.n_slots; t += 256) s_scale[t] = A.scale[(size_t)g * scale_stride(m.n_slots) + t];
     __syncthreads();
+    if (MODE == MODE_NORMAL && m.ident_comp >= 0) {
+      // one convolved component whose derivatives fill channels 1 .. np in order: the
+      // channels stay in registers (the same values as the scatter below)
+      const int cm = m.ident_comp, np = m.np[cm], kind = m.kind[cm];
+      const float* cc = s_cc + cm * kCC;
+      float sc[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sc[k] = k < np ? s_scale[m.slot[cm][k]] : 0.f;
+      for (int r = 0; r < kTilePix / 256; ++r) {
+        const int pix = r * 256 + tid;
+        const int i = i0 + pix / kTile, j = j0 + pix % kTile;
+        if (i >= H || j >= Wp) continue;
+        float vr[2 * 5] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (j < W) {
+          float d[8];
+          vr[0] = eval_component(kind, cc, i, j, d);
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (k < np) vr[1 + k] = d[k] * sc[k];
+        }
+#pragma unroll
+        for (int cp = 0; cp < 5; ++cp)
+          if (cp < m.ncp) out[pbase + ((size_t)cp * H + i) * Wp + j] = make_float2(vr[2 * cp], vr[2 * cp + 1]);
+      }
+      continue;
+    }
     for (int r = 0; r < kTilePix / 256; ++r) {
       const int pix = r * 256 + tid;
       const int i = i0 + pix / kTile, j = j0 + pix % kTile;

@@ -323,6 +323,15 @@ ChanMap chan_map(const Plan& pl) {
   int n_unconv = 0, last = -1;
   for (int c = 0; c < D.n_comp; ++c)
     if (!m.conv[c]) ++n_unconv, last = c;
+  // one convolved component, every parameter free, d/dp_k on channel 1 + k
+  m.ident_comp = -1;
+  if (pl.nacc > 0 && D.n_comp - n_unconv == 1) {
+    int cm = 0;
+    while (!m.conv[cm]) ++cm;
+    bool ident = m.nch_conv == 1 + m.np[cm] && m.np[cm] <= 8;
+    for (int k = 0; k < m.np[cm]; ++k) ident = ident && m.chan[cm][k] == 1 + k;
+    if (ident) m.ident_comp = cm;
+  }
   if (n_unconv == 1 && m.kind[last] == SKY) {
     const int ch = m.chan[last][0];
     if (ch < 0 ? m.nch_tot == m.nch_conv : (ch == m.nch_tot - 1 && m.nch_tot == m.nch_conv + 1)) {
