@@ -48,9 +48,9 @@ PEAKS_PATH = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
 # DRAM bytes (read + write) of the SDSS-shaped fit's fused pass (k_fused<NORMAL, 8, 2, WIDE>, the
 # tuned shape) per galaxy evaluated, from one ncu capture of a 1,024-galaxy pass of this workload
-# (705.5 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
+# (705.6 MB); traffic grows in proportion to the galaxies a pass evaluates, so a launch's traffic is
 # this times its galaxies
-FUSED_DRAM_BYTES_PER_GALAXY = 705.504e6 / 1024
+FUSED_DRAM_BYTES_PER_GALAXY = 705.609e6 / 1024
 
 
 def fused_name(P, shape):
@@ -61,8 +61,8 @@ def fused_name(P, shape):
 
 
 # the same for the uneven workload's fused pass (k_fused<NORMAL, 12, 2, WIDE>, the tuned shape), per
-# stamp pixel evaluated (2,618.9 MB for a 2,048-galaxy pass of 45.59 M pixels)
-UNEVEN_DRAM_BYTES_PER_PIXEL = 2618.902e6 / 45591296
+# stamp pixel evaluated (2,617.4 MB for a 2,048-galaxy pass of 45.59 M pixels)
+UNEVEN_DRAM_BYTES_PER_PIXEL = 2617.424e6 / 45591296
 
 
 def workload_config(G, H, K):
