@@ -834,6 +834,7 @@ int n_acc(int P) { return 1 + P + P * (P + 1) / 2; }
 
 LMOpts lm_opts(const gm_fit_opts* o) {
   LMOpts L;
+  std::memset(&L, 0, sizeof(L));  // zero padding: the options are part of the fit graph's key
   if (o) {
     L.tol = o->tol;
     L.xtol = o->xtol;
@@ -908,6 +909,40 @@ struct GraphGuard {
     if (graph) cudaGraphDestroy(graph);
   }
 };
+
+// Everything the launches of a fit graph take: a graph captured from these
+// values replays the same launches.
+struct FitGraphKey {
+  PlaneArgs PA;
+  FusedArgs A;
+  DescDev dd;
+  LMState S;
+  LMOpts O;
+  const void* kf;
+  size_t smem;
+  int U, G, grid, pgrid, threads, dev;
+  cudaEvent_t ev[4 * kGraphIters];
+};
+
+// The calling thread's last fit graph, replayed by the next gm_fit_batch whose
+// key matches byte for byte (the same model, options, batch buffers and
+// workspace: a fit repeated on new data in the same buffers): that call skips
+// the capture and the instantiation, which are most of a small fit's host time.
+// `valid` is set only once a fit has run the graph to its end without an error.
+struct FitGraphCache {
+  FitGraphKey key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool valid = false;
+  void clear() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    valid = false;
+  }
+};
+thread_local FitGraphCache g_fit_graph;
 
 // A stream of the current device used only to record the fit graph (the
 // caller's stream may be the legacy default stream, which cannot capture).
@@ -1210,39 +1245,74 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   // U iterations captured once as a CUDA graph and replayed, one convergence poll per
   // replay.  U is even (or covers max_iter in one replay), so every replay starts on list 0.
   const int U = std::min(kGraphIters, O.max_iter);
+  unsigned starve_polls = 0;
+  const bool starve = take_starve(&starve_polls);  // a timeout test: this graph is not kept
+  FitGraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  std::memcpy(&key.PA, &PA, sizeof(PA));
+  std::memcpy(&key.A, &A, sizeof(A));
+  std::memcpy(&key.dd, &pl.dd, sizeof(pl.dd));
+  std::memcpy(&key.S, &S, sizeof(S));
+  std::memcpy(&key.O, &O, sizeof(O));
+  key.kf = (const void*)kf;
+  key.smem = sm.total;
+  key.U = U;
+  key.G = G;
+  key.grid = grid;
+  key.pgrid = pgrid;
+  key.threads = sm.threads;
+  GM_CUDA(cudaGetDevice(&key.dev));
+  for (int e = 0; e < 4 * U; ++e) key.ev[e] = g_events[e];
+  FitGraphCache& fc = g_fit_graph;
+  const bool hit = !starve && fc.valid && std::memcmp(&fc.key, &key, sizeof(key)) == 0;
+  fc.valid = false;  // until this call has run the graph without an error
   GraphGuard gg;
-  cudaStream_t cap;
-  if ((rc = capture_stream(&cap))) return rc;
-  GM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-  gg.capturing = cap;
-  for (int u = 0; u < U; ++u) {
-    const int cur = u & 1;
-    A.items = PA.items = S.items[cur];
-    A.n_items_dev = PA.n_items_dev = S.icount[cur];
-    PA.zero[0] = queue;
-    PA.zero[1] = S.count[cur ^ 1];
-    PA.zero[2] = S.icount[cur ^ 1];
-    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u], cap, cudaEventRecordExternal));
-    k_planes<MODE_NORMAL><<<pgrid, 256, 0, cap>>>(PA);
-    GM_LAUNCHED("k_planes");
-    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 1], cap, cudaEventRecordExternal));
-    FusedArgs Au = A;
-    if (u == 0 && take_starve(&Au.wait_polls)) Au.starve = 1;
-    kf<<<grid, sm.threads, sm.total, cap>>>(Au);
-    GM_LAUNCHED("k_fused(normal)");
-    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 2], cap, cudaEventRecordExternal));
-    k_lm_step<<<(G + kLmGals - 1) / kLmGals, 32 * kLmGals, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst,
-                                                                       scale);
-    GM_LAUNCHED("k_lm_step");
-    GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 3], cap, cudaEventRecordExternal));
+  if (!hit) {
+    fc.clear();
+    cudaStream_t cap;
+    if ((rc = capture_stream(&cap))) return rc;
+    GM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    gg.capturing = cap;
+    for (int u = 0; u < U; ++u) {
+      const int cur = u & 1;
+      A.items = PA.items = S.items[cur];
+      A.n_items_dev = PA.n_items_dev = S.icount[cur];
+      PA.zero[0] = queue;
+      PA.zero[1] = S.count[cur ^ 1];
+      PA.zero[2] = S.icount[cur ^ 1];
+      GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u], cap, cudaEventRecordExternal));
+      k_planes<MODE_NORMAL><<<pgrid, 256, 0, cap>>>(PA);
+      GM_LAUNCHED("k_planes");
+      GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 1], cap, cudaEventRecordExternal));
+      FusedArgs Au = A;
+      if (u == 0 && starve) {
+        Au.wait_polls = starve_polls;
+        Au.starve = 1;
+      }
+      kf<<<grid, sm.threads, sm.total, cap>>>(Au);
+      GM_LAUNCHED("k_fused(normal)");
+      GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 2], cap, cudaEventRecordExternal));
+      k_lm_step<<<(G + kLmGals - 1) / kLmGals, 32 * kLmGals, 0, cap>>>(pl.dd, S, O, cur, A.geo, partial, cconst,
+                                                                         scale);
+      GM_LAUNCHED("k_lm_step");
+      GM_CUDA(cudaEventRecordWithFlags(g_events[4 * u + 3], cap, cudaEventRecordExternal));
+    }
+    gg.capturing = nullptr;
+    GM_CUDA(cudaStreamEndCapture(cap, &gg.graph));
+    GM_CUDA(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+    if (!starve) {  // the cache owns it from here
+      std::memcpy(&fc.key, &key, sizeof(key));
+      fc.graph = gg.graph;
+      fc.exec = gg.exec;
+      gg.graph = nullptr;
+      gg.exec = nullptr;
+    }
   }
-  gg.capturing = nullptr;
-  GM_CUDA(cudaStreamEndCapture(cap, &gg.graph));
-  GM_CUDA(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+  const cudaGraphExec_t exec = starve ? gg.exec : fc.exec;
   int passes = 0;
   double profile_ms = 0.0, fused_ms = 0.0, step_ms = 0.0;
   for (int k = 0; k < O.max_iter; k += U) {
-    GM_CUDA(cudaGraphLaunch(gg.exec, st));
+    GM_CUDA(cudaGraphLaunch(exec, st));
     passes += U;
     int remaining = 0, kerr = 0;
     GM_CUDA(cudaMemcpyAsync(&remaining, S.count[U & 1], sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1260,14 +1330,17 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
     if (kerr) return fail(GM_E_TIMEOUT, "fused kernel: a tile load did not complete within its wait limit");
     if (remaining == 0) break;
   }
-  k_lm_finish<<<(G + 127) / 128, 128, 0, st>>>(pl.dd, S, G, O.canonical, O.lambda_inout, params_inout, chi2_out,
-                                               dof_out, iters_out, status_out, sigma_p_out);
+  fc.valid = !starve;
+  k_lm_finish<<<(G + kLmGals - 1) / kLmGals, 32 * kLmGals, 0, st>>>(pl.dd, S, G, O.canonical, O.lambda_inout,
+                                                                     params_inout, chi2_out, dof_out, iters_out,
+                                                                     status_out, sigma_p_out);
   GM_LAUNCHED("k_lm_finish");
   unsigned long long counters[3] = {0, 0, 0};
   GM_CUDA(cudaMemcpyAsync(counters, S.evals, sizeof(counters), cudaMemcpyDeviceToHost, st));
   GM_CUDA(cudaStreamSynchronize(st));
   gm_fit_stats fs;
   fs.passes = passes;
+  fs.graph_reused = hit ? 1 : 0;
   fs.galaxy_evals = (int64_t)counters[0];
   fs.converged = (int64_t)counters[1];
   fs.iters_sum = (int64_t)counters[2];

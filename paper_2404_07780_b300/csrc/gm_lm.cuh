@@ -548,107 +548,144 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
 // ratio above 1 is rewritten as 1/q with its position angles turned by pi/2
 // and its scale lengths multiplied by q (the same image), and the covariance
 // is carried along: Sigma' = T Sigma T^T with T the Jacobian of the rewrite.
-// Position angles are wrapped to [0, pi).
-__global__ void k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G, int canonical,
-                            double* lambda_out, double* params_out, double* chi2_out, int* dof_out,
-                            int* iters_out, int* status_out, double* sigma_p_out) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+// Position angles are wrapped to [0, pi).  One warp per galaxy, as k_lm_step:
+// lane f solves for column f of the inverse and forms row f of the products,
+// with the operations of cholesky() and chol_solve() in their order, so every
+// entry is the one a single thread computes; the rewrite of the point itself
+// (a few groups, in order) is lane 0's.
+__global__ void __launch_bounds__(32 * kLmGals) k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
+                                                           int canonical, double* lambda_out, double* params_out,
+                                                           double* chi2_out, int* dof_out, int* iters_out,
+                                                           int* status_out, double* sigma_p_out) {
+  __shared__ double s_M[kLmGals][kMaxFree * kMaxFree];  // Cholesky factor, then T Sigma
+  __shared__ double s_C[kLmGals][kMaxFree * kMaxFree];  // Sigma
+  __shared__ double s_T[kLmGals][kMaxFree * kMaxFree];  // Jacobian of the q > 1 rewrite
+  __shared__ double s_p[kLmGals][kMaxSlots];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int g = blockIdx.x * kLmGals + wl;
   if (g >= G) return;
   const int NS = D.n_slots, P = D.P;
   const double pi = 3.14159265358979323846;
-  double p[kMaxSlots];
-  for (int s = 0; s < NS; ++s) p[s] = S.p_b[(size_t)g * NS + s];
-  chi2_out[g] = S.chi2_b[g];
-  dof_out[g] = S.nused[g] - P;
-  iters_out[g] = S.it[g];
-  status_out[g] = S.status[g];
-  if (lambda_out) lambda_out[g] = S.lam[g];
+  double* p = s_p[wl];
+  double* M = s_M[wl];
+  double* cov = s_C[wl];
+  double* T = s_T[wl];
+  for (int s = lane; s < NS; s += 32) p[s] = S.p_b[(size_t)g * NS + s];
+  if (lane == 0) {
+    chi2_out[g] = S.chi2_b[g];
+    dof_out[g] = S.nused[g] - P;
+    iters_out[g] = S.it[g];
+    status_out[g] = S.status[g];
+    if (lambda_out) lambda_out[g] = S.lam[g];
+  }
   const bool evaluated = S.it[g] > 0 && S.status[g] != ST_NONFINITE;
+  __syncwarp();
 
   // covariance of the free parameters in physical units at the best point
-  double cov[kMaxFree * kMaxFree];
   bool have_cov = false;
   if (sigma_p_out && evaluated) {
     const double* Ab = S.A_b + (size_t)g * (P * (P + 1) / 2);
-    double M[kMaxFree * kMaxFree];
-    for (int f = 0; f < P; ++f)
-      for (int h = 0; h < P; ++h) M[f * P + h] = packed(Ab, P, f, h);
-    if (cholesky(M, P)) {
+    if (lane < P)
+      for (int h = 0; h < P; ++h) M[lane * P + h] = packed(Ab, P, lane, h);
+    __syncwarp();
+    if (warp_cholesky(M, P, lane)) {
       have_cov = true;
-      for (int f = 0; f < P; ++f) {
-        double e[kMaxFree], x[kMaxFree];
-        for (int h = 0; h < P; ++h) e[h] = (h == f) ? 1.0 : 0.0;
-        chol_solve(M, P, e, x);
+      if (lane < P) {
+        const int f = lane;
+        double y[kMaxFree], x[kMaxFree];
+        for (int i = 0; i < P; ++i) {
+          double t = (i == f) ? 1.0 : 0.0;
+          for (int k = 0; k < i; ++k) t -= M[i * P + k] * y[k];
+          y[i] = t / M[i * P + i];
+        }
+        for (int i = P - 1; i >= 0; --i) {
+          double t = y[i];
+          for (int k = i + 1; k < P; ++k) t -= M[k * P + i] * x[k];
+          x[i] = t / M[i * P + i];
+        }
         for (int h = 0; h < P; ++h) cov[h * P + f] = x[h];
       }
-      for (int f = 0; f < P; ++f) {
-        const int sf = D.free_slot[f];
+      __syncwarp();
+      if (lane < P) {
+        const int f = lane, sf = D.free_slot[f];
         const double df = D.is_log[sf] ? p[sf] : 1.0;
         for (int h = 0; h < P; ++h) {
           const int sh = D.free_slot[h];
           cov[f * P + h] *= df * (D.is_log[sh] ? p[sh] : 1.0);
         }
       }
+      __syncwarp();
     }
   }
 
   // canonical axis ratios
   if (evaluated && canonical) {
-    int fidx[kMaxSlots];
-    for (int s = 0; s < NS; ++s) fidx[s] = -1;
-    for (int f = 0; f < P; ++f) fidx[D.free_slot[f]] = f;
-    double T[kMaxFree * kMaxFree];
-    bool any = false;
-    for (int f = 0; f < P * P; ++f) T[f] = 0.0;
-    for (int f = 0; f < P; ++f) T[f * P + f] = 1.0;
-    for (int k = 0; k < D.n_canon; ++k) {
-      const CanonGroup& cg = D.canon[k];
-      const double q = p[cg.q_slot];
-      if (!(q > 1.0)) continue;
-      any = true;
-      const int fq = fidx[cg.q_slot];
-      for (int i = 0; i < cg.n_scale; ++i) {
-        const int ss = cg.scale[i];
-        const int fs = fidx[ss];
-        if (fs >= 0) {
-          T[fs * P + fs] = q;
-          if (fq >= 0) T[fs * P + fq] = p[ss];
+    int any = 0;
+    if (lane == 0) {
+      int fidx[kMaxSlots];
+      for (int s = 0; s < NS; ++s) fidx[s] = -1;
+      for (int f = 0; f < P; ++f) fidx[D.free_slot[f]] = f;
+      for (int f = 0; f < P * P; ++f) T[f] = 0.0;
+      for (int f = 0; f < P; ++f) T[f * P + f] = 1.0;
+      for (int k = 0; k < D.n_canon; ++k) {
+        const CanonGroup& cg = D.canon[k];
+        const double q = p[cg.q_slot];
+        if (!(q > 1.0)) continue;
+        any = 1;
+        const int fq = fidx[cg.q_slot];
+        for (int i = 0; i < cg.n_scale; ++i) {
+          const int ss = cg.scale[i];
+          const int fs = fidx[ss];
+          if (fs >= 0) {
+            T[fs * P + fs] = q;
+            if (fq >= 0) T[fs * P + fq] = p[ss];
+          }
+          p[ss] *= q;
         }
-        p[ss] *= q;
+        for (int i = 0; i < cg.n_pa; ++i) p[cg.pa[i]] += 0.5 * pi;
+        if (fq >= 0) T[fq * P + fq] = -1.0 / (q * q);
+        p[cg.q_slot] = 1.0 / q;
       }
-      for (int i = 0; i < cg.n_pa; ++i) p[cg.pa[i]] += 0.5 * pi;
-      if (fq >= 0) T[fq * P + fq] = -1.0 / (q * q);
-      p[cg.q_slot] = 1.0 / q;
     }
-    if (any && have_cov) {  // cov <- T cov T^T
-      double tmp[kMaxFree * kMaxFree];
-      for (int f = 0; f < P; ++f)
+    any = __shfl_sync(kFull, any, 0);
+    __syncwarp();
+    if (any && have_cov) {  // cov <- T cov T^T, row f on lane f
+      if (lane < P) {
+        const int f = lane;
         for (int h = 0; h < P; ++h) {
           double acc = 0.0;
           for (int k = 0; k < P; ++k) acc += T[f * P + k] * cov[k * P + h];
-          tmp[f * P + h] = acc;
+          M[f * P + h] = acc;
         }
-      for (int f = 0; f < P; ++f)
+      }
+      __syncwarp();
+      if (lane < P) {
+        const int f = lane;
         for (int h = 0; h < P; ++h) {
           double acc = 0.0;
-          for (int k = 0; k < P; ++k) acc += tmp[f * P + k] * T[h * P + k];
+          for (int k = 0; k < P; ++k) acc += M[f * P + k] * T[h * P + k];
           cov[f * P + h] = acc;
         }
+      }
+      __syncwarp();
     }
   }
 
-  for (int s = 0; s < NS; ++s) {
+  for (int s = lane; s < NS; s += 32) {
     double v = p[s];
     if (D.is_pa[s] && canonical) v -= pi * floor(v / pi);
     params_out[(size_t)g * NS + s] = v;
   }
   if (sigma_p_out) {
     double* sp = sigma_p_out + (size_t)g * NS;
-    for (int s = 0; s < NS; ++s) sp[s] = 0.0;
-    for (int f = 0; f < P; ++f) sp[D.free_slot[f]] = have_cov ? sqrt(cov[f * P + f]) : CUDART_NAN;
+    for (int s = lane; s < NS; s += 32) sp[s] = 0.0;
+    __syncwarp();
+    if (lane < P) sp[D.free_slot[lane]] = have_cov ? sqrt(cov[lane * P + lane]) : CUDART_NAN;
   }
-  if (S.status[g] == ST_CONVERGED) atomicAdd(S.evals + 1, 1ull);
-  atomicAdd(S.evals + 2, (unsigned long long)S.it[g]);
+  if (lane == 0) {
+    if (S.status[g] == ST_CONVERGED) atomicAdd(S.evals + 1, 1ull);
+    atomicAdd(S.evals + 2, (unsigned long long)S.it[g]);
+  }
 }
 #endif  // GM_HOST_TU
 

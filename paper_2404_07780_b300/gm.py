@@ -113,6 +113,7 @@ class gm_adam_opts(ctypes.Structure):
 class gm_fit_stats(ctypes.Structure):
     _fields_ = [
         ("passes", ctypes.c_int32),
+        ("graph_reused", ctypes.c_int32),
         ("galaxy_evals", ctypes.c_int64),
         ("converged", ctypes.c_int64),
         ("iters_sum", ctypes.c_int64),
@@ -572,8 +573,8 @@ def gm_grad_adjoint_last_stats() -> dict:
 
 
 def gm_fit_last_stats() -> dict:
-    """Counters of this thread's last gm_fit_batch: passes, galaxy_evals, converged, iters_sum, profile_ms,
-    fused_ms, step_ms, wall_ms."""
+    """Counters of this thread's last gm_fit_batch: passes, graph_reused, galaxy_evals, converged, iters_sum,
+    profile_ms, fused_ms, step_ms, wall_ms."""
     st = gm_fit_stats()
     _check(load().gm_fit_last_stats(ctypes.byref(st)), "gm_fit_last_stats")
     return {name: getattr(st, name) for name, _ in gm_fit_stats._fields_}
