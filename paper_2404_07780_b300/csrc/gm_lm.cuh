@@ -190,38 +190,6 @@ __global__ void k_lm_init(const __grid_constant__ DescDev D, LMState S, LMOpts O
 }
 #endif  // GM_HOST_TU
 
-// In-place Cholesky of an n x n row-major matrix (lower triangle); false if not
-// positive definite.
-__device__ inline bool cholesky(double* M, int n) {
-  for (int j = 0; j < n; ++j) {
-    double s = M[j * n + j];
-    for (int k = 0; k < j; ++k) s -= M[j * n + k] * M[j * n + k];
-    if (!(s > 0.0)) return false;
-    const double l = sqrt(s);
-    M[j * n + j] = l;
-    for (int i = j + 1; i < n; ++i) {
-      double t = M[i * n + j];
-      for (int k = 0; k < j; ++k) t -= M[i * n + k] * M[j * n + k];
-      M[i * n + j] = t / l;
-    }
-  }
-  return true;
-}
-
-__device__ inline void chol_solve(const double* L, int n, const double* b, double* x) {
-  double y[kMaxFree];
-  for (int i = 0; i < n; ++i) {
-    double s = b[i];
-    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
-    y[i] = s / L[i * n + i];
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    double s = y[i];
-    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
-    x[i] = s / L[i * n + i];
-  }
-}
-
 // Entry (f, h) of a row-major packed upper triangle of a symmetric P x P matrix.
 __device__ inline double packed(const double* Ap, int P, int f, int h) {
   if (f > h) {
@@ -245,10 +213,13 @@ __device__ inline double warp_sum(double v) {
 }
 
 // In-place Cholesky (lower triangle) of M, column by column: lanes i >= j form
-// their entry of column j at once.  Each entry is computed with the same
-// operations in the same order as cholesky().  false (on every lane) if M is not
-// positive definite.
-__device__ inline bool warp_cholesky(double* M, int P, int lane) {
+// their entry of column j at once.  The pivot is l_jj = d rsqrt(d) and the
+// entries below it are multiplied by rsqrt(d), which is also kept in dinv[j]
+// for the solves: an FP64 square root or division is a long chain of FP64
+// instructions at sm_103a's FP64 issue rate, on the critical path of every
+// column, and rsqrt is one approximation and a short refinement.  false (on
+// every lane) if M is not positive definite.
+__device__ inline bool warp_cholesky(double* M, double* dinv, int P, int lane) {
   for (int j = 0; j < P; ++j) {
     double t = 0.0;
     if (lane >= j && lane < P) {
@@ -257,27 +228,31 @@ __device__ inline bool warp_cholesky(double* M, int P, int lane) {
     }
     const double d = __shfl_sync(kFull, t, j);
     if (!(d > 0.0)) return false;
-    const double l = sqrt(d);
-    if (lane == j) M[j * P + j] = l;
-    else if (lane > j && lane < P) M[lane * P + j] = t / l;
+    const double il = rsqrt(d);
+    if (lane == j) {
+      M[j * P + j] = d * il;
+      dinv[j] = il;
+    } else if (lane > j && lane < P) {
+      M[lane * P + j] = t * il;
+    }
     __syncwarp();
   }
   return true;
 }
 
-// Solve L L^T x = b (L from warp_cholesky); b and x are lane-owned (entry f on
-// lane f); returns x on every lane f < P.
-__device__ inline double warp_chol_solve(const double* L, int P, int lane, double b) {
+// Solve L L^T x = b (L and dinv from warp_cholesky); b and x are lane-owned
+// (entry f on lane f); returns x on every lane f < P.
+__device__ inline double warp_chol_solve(const double* L, const double* dinv, int P, int lane, double b) {
   double r = b, y = 0.0;
   for (int i = 0; i < P; ++i) {  // forward: y_i = (b_i - sum_{k<i} L_ik y_k) / L_ii
-    const double yi = __shfl_sync(kFull, r, i) / L[i * P + i];
+    const double yi = __shfl_sync(kFull, r, i) * dinv[i];
     if (lane == i) y = yi;
     if (lane > i && lane < P) r -= L[lane * P + i] * yi;
   }
   r = y;
   double x = 0.0;
   for (int i = P - 1; i >= 0; --i) {  // back: x_i = (y_i - sum_{k>i} L_ki x_k) / L_ii
-    const double xi = __shfl_sync(kFull, r, i) / L[i * P + i];
+    const double xi = __shfl_sync(kFull, r, i) * dinv[i];
     if (lane == i) x = xi;
     if (lane < i) r -= L[i * P + lane] * xi;
   }
@@ -382,6 +357,7 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
                                                          float* scale) {
   __shared__ double s_acc[kLmGals][kMaxAcc];
   __shared__ double s_M[kLmGals][kMaxFree * kMaxFree];
+  __shared__ double s_dinv[kLmGals][kMaxFree];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int gi = blockIdx.x * kLmGals + wl;
   const int n_cur = *S.count[cur];
@@ -391,6 +367,7 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
   const int g = S.list[cur][gi];
   double* acc = s_acc[wl];
   double* M = s_M[wl];
+  double* dinv = s_dinv[wl];
   {
     const int n_tiles = geo[g].n_tiles;
     const double* pp = partial + (size_t)geo[g].tile0 * NA;
@@ -490,8 +467,8 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
     // sums are the same in every lane, so the warp takes one branch)
     const double r = warp_step_system(Ab, gb, P, 0.0, held, M, lane);
     const double r2 = warp_sum(r * r), tr = warp_sum(lane < P ? M[lane * P + lane] : 0.0);
-    if (!(r2 > O.gtol * chi2_best * tr) && warp_cholesky(M, P, lane)) {
-      const double x = warp_chol_solve(M, P, lane, r);
+    if (!(r2 > O.gtol * chi2_best * tr) && warp_cholesky(M, dinv, P, lane)) {
+      const double x = warp_chol_solve(M, dinv, P, lane, r);
       const double gn = warp_sum(lane < P ? r * x : 0.0);
       if (gn >= 0.0 && gn <= O.gtol * chi2_best) st = ST_CONVERGED;
     }
@@ -501,8 +478,8 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
     // final Gauss-Newton step from the best point: delta = A^-1 g with the diagonal
     // floored as in the damped solve, evaluated in the next pass
     const double r = warp_step_system(Ab, gb, P, 0.0, held, M, lane);
-    if (warp_cholesky(M, P, lane)) {
-      const double delta = warp_chol_solve(M, P, lane, r);
+    if (warp_cholesky(M, dinv, P, lane)) {
+      const double delta = warp_chol_solve(M, dinv, P, lane, r);
       warp_trial_point(D, pb, pt, delta, lane);
       warp_setup_galaxy(D, pt, geo[g].H, geo[g].W, ccg, scg, lane);
       warp_queue_galaxy(S, cur ^ 1, g, geo[g], lane);
@@ -513,7 +490,7 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
     double r = 0.0;
     for (;;) {
       r = warp_step_system(Ab, gb, P, lam, held, M, lane);
-      if (warp_cholesky(M, P, lane)) break;
+      if (warp_cholesky(M, dinv, P, lane)) break;
       lam *= O.lambda_up;
       if (lam > O.lambda_max) {
         st = ST_SINGULAR;
@@ -521,7 +498,7 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
       }
     }
     if (st == ST_RUNNING) {
-      const double delta = warp_chol_solve(M, P, lane, r);
+      const double delta = warp_chol_solve(M, dinv, P, lane, r);
       // predicted decrease 2 g^T delta - delta^T A delta (every lane's delta_h by shuffles)
       double ad = 0.0;
       for (int h = 0; h < P; ++h) {
@@ -549,15 +526,16 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_step(const __grid_constant_
 // and its scale lengths multiplied by q (the same image), and the covariance
 // is carried along: Sigma' = T Sigma T^T with T the Jacobian of the rewrite.
 // Position angles are wrapped to [0, pi).  One warp per galaxy, as k_lm_step:
-// lane f solves for column f of the inverse and forms row f of the products,
-// with the operations of cholesky() and chol_solve() in their order, so every
-// entry is the one a single thread computes; the rewrite of the point itself
-// (a few groups, in order) is lane 0's.
+// lane f solves for column f of the inverse (its own forward and back
+// substitution, with the factor's reciprocal pivots) and forms row f of the
+// products; the rewrite of the point itself (a few groups, in order) is lane
+// 0's.
 __global__ void __launch_bounds__(32 * kLmGals) k_lm_finish(const __grid_constant__ DescDev D, LMState S, int G,
                                                            int canonical, double* lambda_out, double* params_out,
                                                            double* chi2_out, int* dof_out, int* iters_out,
                                                            int* status_out, double* sigma_p_out) {
   __shared__ double s_M[kLmGals][kMaxFree * kMaxFree];  // Cholesky factor, then T Sigma
+  __shared__ double s_dinv[kLmGals][kMaxFree];          // 1 / the factor's diagonal
   __shared__ double s_C[kLmGals][kMaxFree * kMaxFree];  // Sigma
   __shared__ double s_T[kLmGals][kMaxFree * kMaxFree];  // Jacobian of the q > 1 rewrite
   __shared__ double s_p[kLmGals][kMaxSlots];
@@ -568,6 +546,7 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_finish(const __grid_constan
   const double pi = 3.14159265358979323846;
   double* p = s_p[wl];
   double* M = s_M[wl];
+  double* dinv = s_dinv[wl];
   double* cov = s_C[wl];
   double* T = s_T[wl];
   for (int s = lane; s < NS; s += 32) p[s] = S.p_b[(size_t)g * NS + s];
@@ -588,7 +567,7 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_finish(const __grid_constan
     if (lane < P)
       for (int h = 0; h < P; ++h) M[lane * P + h] = packed(Ab, P, lane, h);
     __syncwarp();
-    if (warp_cholesky(M, P, lane)) {
+    if (warp_cholesky(M, dinv, P, lane)) {
       have_cov = true;
       if (lane < P) {
         const int f = lane;
@@ -596,12 +575,12 @@ __global__ void __launch_bounds__(32 * kLmGals) k_lm_finish(const __grid_constan
         for (int i = 0; i < P; ++i) {
           double t = (i == f) ? 1.0 : 0.0;
           for (int k = 0; k < i; ++k) t -= M[i * P + k] * y[k];
-          y[i] = t / M[i * P + i];
+          y[i] = t * dinv[i];
         }
         for (int i = P - 1; i >= 0; --i) {
           double t = y[i];
           for (int k = i + 1; k < P; ++k) t -= M[k * P + i] * x[k];
-          x[i] = t / M[i * P + i];
+          x[i] = t * dinv[i];
         }
         for (int h = 0; h < P; ++h) cov[h * P + f] = x[h];
       }
