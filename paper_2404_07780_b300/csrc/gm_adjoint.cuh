@@ -305,6 +305,27 @@ __device__ __forceinline__ void chunk_deriv_sums(const PixArgs& A, const float* 
   }
 }
 
+// chunk_deriv_sums for a lone flat sky (ChanMap::sky_comp): its one derivative is
+// 1 at every pixel, so the sums are the weights' own, added in the same order.
+template <int P, int NA>
+__device__ __forceinline__ void chunk_sky_sums(const PixArgs& A, int sky, bool has1, const int (&pi)[kPixPerThread],
+                                               float (&wt)[2][kPixPerThread], float (&red)[2][NA]) {
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    if (h == 0 || has1) {
+      float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+      for (int q = 0; q < kPixPerThread; ++q) {
+        if (pi[q] >= 0) sd[0] = fmaf(wt[0][0], 1.f, sd[0]);
+        rotate_left<1>(wt[0]);
+      }
+      scatter_sums<P>(red, A.acc_of[sky], 1, sd);
+    }
+    swap_rows(wt);
+    swap_rows(red);
+  }
+}
+
 // Residuals of one galaxy pair, one block of 256 threads per kPixPart pixels of the
 // stamp, in chunks of 4 pixels per thread (pixel p, row-major, on thread p % 256:
 // each warp reads consecutive pixels): M = M_conv + the unconvolved components,
@@ -364,10 +385,14 @@ __global__ void __launch_bounds__(kPixThreads, 2) k_adj_resid(const __grid_const
         uu[h][q] = 0.f;
         if (!use[h][q]) continue;
         float Mv = h ? mc[q].y : mc[q].x;
-        for (int cm = 0; cm < m.n_comp; ++cm) {
-          if (m.conv[cm]) continue;
-          float d[8];
-          Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, pi[q], pj[q], d);
+        if (m.sky_comp >= 0) {  // a lone flat sky: its level, without evaluating the component
+          Mv += s_cc[h * ncc + m.sky_comp * kCC + 8];
+        } else {
+          for (int cm = 0; cm < m.n_comp; ++cm) {
+            if (m.conv[cm]) continue;
+            float d[8];
+            Mv += eval_component(m.kind[cm], s_cc + h * ncc + cm * kCC, pi[q], pj[q], d);
+          }
         }
         const float isg = 1.f / Sv[h][q];
         const float rr = (Dv[h][q] - Mv) * isg;
@@ -376,7 +401,8 @@ __global__ void __launch_bounds__(kPixThreads, 2) k_adj_resid(const __grid_const
       }
       if (pi[q] >= 0) planes[((size_t)gp * A.H + pi[q]) * A.Wp + pj[q]] = make_float2(uu[0][q], uu[1][q]);
     }
-    if (m.any_unconv) chunk_deriv_sums<P>(A, s_cc, ncc, has1, pi, pj, uu, red, false);
+    if (m.sky_comp >= 0) chunk_sky_sums<P>(A, m.sky_comp, has1, pi, uu, red);
+    else if (m.any_unconv) chunk_deriv_sums<P>(A, s_cc, ncc, has1, pi, pj, uu, red, false);
   }
   pix_pair_sums(A, red, s_red, g0, part, n_parts);
 }

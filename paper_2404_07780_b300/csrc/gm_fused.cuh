@@ -81,8 +81,8 @@ struct ChanMap {
   int chan[kMaxComp][8];     // d/dp_k of comp c -> channel (-1: not needed)
   int comp_chan[kMaxComp];   // MODEL mode: channel holding comp c's own image (-1: none)
   int any_unconv;
-  int sky_comp;              // NORMAL mode: the one unconvolved component when it is a flat sky
-                             // (-1: none such), written without evaluating the component
+  int sky_comp;              // NORMAL mode and the adjoint's residuals: the one unconvolved component
+                             // when it is a flat sky (-1: none such), applied without evaluating it
   int sky_ch;                // that sky's derivative channel, the last one (-1: its level is fixed)
   int ident_comp;            // NORMAL mode: the one convolved component when its parameters are all
                              // free and own channels 1 .. np in order (-1: none such)
