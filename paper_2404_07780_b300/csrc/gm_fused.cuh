@@ -173,6 +173,12 @@ __device__ __forceinline__ void unpack2(u64 v, float& x, float& y) {
 // ---------------------------------------------------------------------------
 // k_planes
 // ---------------------------------------------------------------------------
+// Work units of k_planes: a whole item (its 1024 pixels, four per thread) or, when a
+// pass has so few items that their quarters fit in one wave of the grid, a quarter
+// of one (256 pixels, one per thread), so that a small pass still spreads over the
+// SMs; a large pass keeps whole items (the per-unit set-up costs at that size).
+constexpr int kPlaneUnits = kTilePix / 256;
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArgs A) {
   __shared__ float s_cc[kMaxComp * kCC];
@@ -182,9 +188,11 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
   const int tid = threadIdx.x;
   if (blockIdx.x == 0 && tid < 3 && A.zero[tid]) *A.zero[tid] = 0;
   const int n = A.n_items_dev ? *A.n_items_dev : A.n_items;
+  const int upi = kPlaneUnits * n <= (int)gridDim.x ? kPlaneUnits : 1;  // units per item
   float* v = s_v + tid;  // v[ch * 256]: consecutive threads, consecutive banks
   float2* out = reinterpret_cast<float2*>(A.planes);
-  for (int item = blockIdx.x; item < n; item += gridDim.x) {
+  for (int u = blockIdx.x; u < upi * n; u += gridDim.x) {
+    const int item = u / upi, r0 = u - item * upi;
     const int2 it = A.items[item];
     const int g = it.x;
     const GalGeom& G = A.geo[g];
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
       float sc[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) sc[k] = k < np ? s_scale[m.slot[cm][k]] : 0.f;
-      for (int r = 0; r < kTilePix / 256; ++r) {
+      for (int r = r0; r < kPlaneUnits; r += upi) {
         const int pix = r * 256 + tid;
         const int i = i0 + pix / kTile, j = j0 + pix % kTile;
         if (i >= H || j >= Wp) continue;
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneArg
       }
       continue;
     }
-    for (int r = 0; r < kTilePix / 256; ++r) {
+    for (int r = r0; r < kPlaneUnits; r += upi) {
       const int pix = r * 256 + tid;
       const int i = i0 + pix / kTile, j = j0 + pix % kTile;
       if (i >= H || j >= Wp) continue;

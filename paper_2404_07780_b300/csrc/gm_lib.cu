@@ -1012,7 +1012,7 @@ int setup_pass(int mode, const gm_model_desc* desc, const gm_batch* batch, const
 
 int launch_pass(int mode, PassCall* pc, cudaStream_t st) {
   const long long n = pc->gp.n_items;
-  const int pgrid = (int)std::max<long long>(1, std::min<long long>(n, 8LL * pc->di.sms));
+  const int pgrid = (int)std::max<long long>(1, std::min<long long>(kPlaneUnits * (long long)n, 8LL * pc->di.sms));
   if (mode == MODE_MODEL) k_planes<MODE_MODEL><<<pgrid, 256, 0, st>>>(pc->PA);
   else k_planes<MODE_NORMAL><<<pgrid, 256, 0, st>>>(pc->PA);
   GM_LAUNCHED("k_planes");
@@ -1241,7 +1241,7 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
 
   PlaneArgs PA = plane_args(pl, A.geo, cconst, scale, planes);
   const int grid = (int)std::max<long long>(1, std::min<long long>(gp.n_items, di.sms));
-  const int pgrid = (int)std::max<long long>(1, std::min<long long>(gp.n_items, 8LL * di.sms));
+  const int pgrid = (int)std::max<long long>(1, std::min<long long>(kPlaneUnits * gp.n_items, 8LL * di.sms));
   // U iterations captured once as a CUDA graph and replayed, one convergence poll per
   // replay.  U is even (or covers max_iter in one replay), so every replay starts on list 0.
   const int U = std::min(kGraphIters, O.max_iter);
