@@ -318,7 +318,8 @@ ChanMap chan_map(const Plan& pl) {
   m.nch_tot = pl.nch_tot;
   m.n_slots = D.n_slots;
   // a lone unconvolved flat sky (no magnitude or boxiness flag) whose level, when free,
-  // owns the last channel: the tile kernel writes it without evaluating the component
+  // owns the last channel: the tile kernel and the adjoint's residuals apply it without
+  // evaluating the component
   m.sky_comp = m.sky_ch = -1;
   int n_unconv = 0, last = -1;
   for (int c = 0; c < D.n_comp; ++c)
@@ -927,8 +928,8 @@ struct FitGraphKey {
 // The calling thread's last fit graph, replayed by the next gm_fit_batch whose
 // key matches byte for byte (the same model, options, batch buffers and
 // workspace: a fit repeated on new data in the same buffers): that call skips
-// the capture and the instantiation, which are most of a small fit's host time.
-// `valid` is set only once a fit has run the graph to its end without an error.
+// the capture and the instantiation of the graph.  `valid` is set only once a
+// fit has run the graph to its end without an error.
 struct FitGraphCache {
   FitGraphKey key;
   cudaGraph_t graph = nullptr;
