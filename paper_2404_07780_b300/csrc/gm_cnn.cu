@@ -209,7 +209,7 @@ int fwd_stages(int BN, int KC) {
 
 template <int BN, int KC>
 int launch_fwd(FwdArgs& F, cudaStream_t st) {
-  void (*k)(FwdArgs) = k_fwd<BN, KC>;
+  void (*k)(FwdArgs) = F.starve ? k_fwd<BN, KC, true> : k_fwd<BN, KC, false>;
   F.stages = fwd_stages(BN, KC);
   const int smem = fwd_smem_bytes(BN, KC, F.stages);
   CNN_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -355,8 +355,9 @@ int conv12(const void* x, const void* w1, const float* b1, const void* w2, const
     C.starve = 1;
     g_cnn_starve_polls = 0;
   }
-  CNN_CUDA(cudaFuncSetAttribute((const void*)k_conv12, cudaFuncAttributeMaxDynamicSharedMemorySize, kC12Smem));
-  k_conv12<<<std::min(C.n_tiles, sms()), kC12Threads, kC12Smem, st>>>(C);
+  void (*k)(Conv12Args) = C.starve ? k_conv12<true> : k_conv12<false>;
+  CNN_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, kC12Smem));
+  k<<<std::min(C.n_tiles, sms()), kC12Threads, kC12Smem, st>>>(C);
   CNN_LAUNCHED("k_conv12");
   return GM_CNN_OK;
 }

@@ -222,8 +222,13 @@ __host__ __device__ constexpr int fwd_smem_bytes(int BN, int KC, int stages) {
   return 1024 + stages * (kBM + BN) * KC * 2 + (BN / 64) * kOutHalf + kFwdMaxN * 4 + (2 * stages + 5) * 8 + 16;
 }
 
-template <int BN, int KC>
+// kTest: the instance the timeout test launches, with the poll limit and the starved slice
+// of FwdArgs; the other instance waits kFwdWaitSleep tests and has no test branch (reading
+// the limit from the arguments cost the layers ~20 % of their time).
+template <int BN, int KC, bool kTest>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ FwdArgs F) {
+  const unsigned polls = kTest ? F.polls : kFwdWaitSleep;
+  const bool starve = kTest && F.starve && blockIdx.x == 0;
   static_assert(KC == 32 || KC == 64, "64- or 128-byte operand rows");
   static_assert(BN % 64 == 0 && BN <= 128, "output tiles of whole 64-column halves");
   extern __shared__ unsigned char smem_raw[];
@@ -285,13 +290,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
         }
         for (int j = 0; j < F.nk; ++j, ++g) {
           const int s = (int)(g % (unsigned)S);
-          if (g >= (unsigned)S && !fwd_wait(&empty[s], ((g / S) - 1) & 1u, s_abort, F.polls)) {
+          if (g >= (unsigned)S && !fwd_wait(&empty[s], ((g / S) - 1) & 1u, s_abort, polls)) {
             fwd_fail(s_abort, F.err);
             ok = false;
             break;
           }
           unsigned char* sa = smem + s * STAGE;
-          if (F.starve && blockIdx.x == 0 && g == 0) continue;  // nothing arrives on full[0]
+          if (starve && g == 0) continue;  // nothing arrives on full[0]
           mbar_expect_tx(&full[s], STAGE);
           int kb;
           if (F.conv) {
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
       }
       if (!ok) {  // the copies still in flight land before the block leaves (none for a starved slice)
         for (unsigned h = g > (unsigned)S ? g - S : 0u; h < g; ++h)
-          if (!(F.starve && blockIdx.x == 0 && h == 0)) fwd_drain(&full[h % S], (h / S) & 1u);
+          if (!(starve && h == 0)) fwd_drain(&full[h % S], (h / S) & 1u);
       }
     }
   } else if (warp == 1) {
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
       bool ok = true;
       for (int t = blockIdx.x; ok && t < F.n_tiles; t += gridDim.x, ++i) {
         const int acc = i & 1;
-        if (i >= 2 && !fwd_wait(&tempty[acc], ((i >> 1) - 1) & 1, s_abort, F.polls)) {
+        if (i >= 2 && !fwd_wait(&tempty[acc], ((i >> 1) - 1) & 1, s_abort, polls)) {
           fwd_fail(s_abort, F.err);
           break;
         }
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
         const unsigned d = tmem + (unsigned)(acc * BN);
         for (int j = 0; j < F.nk; ++j, ++g) {
           const int s = (int)(g % (unsigned)S);
-          if (!fwd_wait(&full[s], (g / S) & 1u, s_abort, F.polls)) {
+          if (!fwd_wait(&full[s], (g / S) & 1u, s_abort, polls)) {
             fwd_fail(s_abort, F.err);
             ok = false;
             break;
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd(const __grid_constant__ 
       const int mt = t / F.n_ntiles, n0 = (t - mt * F.n_ntiles) * BN, m0 = mt * kBM;
       const int acc = i & 1;
       bool bad = false;
-      if (lane == 0) bad = !fwd_wait(&tfull[acc], (i >> 1) & 1, s_abort, F.polls);
+      if (lane == 0) bad = !fwd_wait(&tfull[acc], (i >> 1) & 1, s_abort, polls);
       __syncwarp();
       if (named_any(1, 128, bad)) {  // the same decision in every epilogue thread
         if (bad) fwd_fail(s_abort, F.err);
@@ -611,7 +616,9 @@ __device__ __forceinline__ void c12_readout(const C12Plan& P, unsigned d1, unsig
   }
 }
 
+template <bool kTest>  // as k_fwd's
 __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant__ Conv12Args C) {
+  const unsigned polls = kTest ? C.polls : kFwdWaitSleep;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
   u64* xfull = reinterpret_cast<u64*>(smem + kC12Bar);  // [2] input rows of a buffer landed (copy)
@@ -695,10 +702,10 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
       bool ok = true;
       mbar_expect_tx(bfull, 9 * 4096);
       for (int tap = 0; tap < 9; ++tap) tma_load_2d(smem + kC12B + tap * 4096, &C.tw2, tap * 32, 0, bfull);
-      const bool starved = C.starve && blockIdx.x == 0;  // load 0 not issued: nothing arrives on xfull[0]
+      const bool starved = kTest && C.starve && blockIdx.x == 0;  // load 0 not issued: nothing arrives on xfull[0]
       for (; x_issued < 2 && x_issued < n; ++x_issued)
         if (!(starved && x_issued == 0)) c12_load_x(C, xbuf(x_issued), tile(x_issued), &xfull[x_issued]);
-      if (!fwd_wait(bfull, 0, s_abort, C.polls) || !fwd_wait(a1full, 0, s_abort, C.polls)) ok = false;
+      if (!fwd_wait(bfull, 0, s_abort, polls) || !fwd_wait(a1full, 0, s_abort, polls)) ok = false;
       if (ok) conv1(0);
       int i = 0;
       for (; ok && i < n; ++i) {
@@ -707,18 +714,18 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
           ++x_issued;
         }
         if (i + 1 < n) {  // conv1 of the next tile
-          if (!fwd_wait(a1full, (i + 1) & 1, s_abort, C.polls)) { ok = false; break; }
+          if (!fwd_wait(a1full, (i + 1) & 1, s_abort, polls)) { ok = false; break; }
           conv1(i + 1);
         }
         if (i >= 2) {  // the output of tile i - 2, once its staging tile is written; the tile is
                        // handed back as soon as the store has read it
-          if (!fwd_wait(outfull, i & 1, s_abort, C.polls)) { ok = false; break; }
+          if (!fwd_wait(outfull, i & 1, s_abort, polls)) { ok = false; break; }
           tma_store_2d(&C.ty, out, 0, tile(i - 2) * kBM);
           bulk_commit();
           bulk_wait_read0();
           mbar_arrive(outfree);
         }
-        if (!fwd_wait(&a2full[i & 1], (i >> 1) & 1, s_abort, C.polls)) { ok = false; break; }
+        if (!fwd_wait(&a2full[i & 1], (i >> 1) & 1, s_abort, polls)) { ok = false; break; }
         tc_fence_after();
         const u64 da2 = sw_desc<32>(smem_addr(aset(i)));
 #pragma unroll
@@ -730,7 +737,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
         tc_commit(&mma[i & 1]);
       }
       for (int j = i >= 2 ? i - 2 : 0; ok && j < i; ++j) {  // the last two tiles' outputs
-        if (!fwd_wait(outfull, j & 1, s_abort, C.polls)) {
+        if (!fwd_wait(outfull, j & 1, s_abort, polls)) {
           ok = false;
           break;
         }
@@ -756,8 +763,8 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
     // staging tile of tile number j from conv2 accumulator j % 2; the tile is free once the store
     // of tile j - 1 has read it
     auto epilogue = [&](int j, bool ok) -> bool {
-      ok = warp_wait(&mma[j & 1], (j >> 1) & 1, s_abort, ok, C.polls);
-      if (j >= 1) ok = warp_wait(outfree, (j - 1) & 1, s_abort, ok, C.polls);
+      ok = warp_wait(&mma[j & 1], (j >> 1) & 1, s_abort, ok, polls);
+      if (j >= 1) ok = warp_wait(outfree, (j - 1) & 1, s_abort, ok, polls);
       if (ok && grp < 4) {  // four column groups of 16
         tc_fence_after();
         const int r = q * 32 + lane;
@@ -777,7 +784,7 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
 
     bool ok = true;
     if (n > 0) {  // im2col of the first tile
-      ok = warp_wait(&xfull[0], 0, s_abort, ok, C.polls);
+      ok = warp_wait(&xfull[0], 0, s_abort, ok, polls);
       if (ok) {
         c12_im2col(plan, xbuf(0), A1, 8 * (tile(0) & 1));
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -788,9 +795,9 @@ __global__ void __launch_bounds__(kC12Threads, 1) k_conv12(const __grid_constant
     for (; ok && i < n; ++i) {
       // conv1 of tile i done: so are the conv2 MMAs of tile i - 2 (issued before it), which read
       // operand set i % 2, and the im2col buffer is free
-      ok = warp_wait(&d1[i & 1], (i >> 1) & 1, s_abort, ok, C.polls);
+      ok = warp_wait(&d1[i & 1], (i >> 1) & 1, s_abort, ok, polls);
       if (ok && i + 1 < n) {
-        ok = warp_wait(&xfull[(i + 1) & 1], ((i + 1) >> 1) & 1, s_abort, ok, C.polls);
+        ok = warp_wait(&xfull[(i + 1) & 1], ((i + 1) >> 1) & 1, s_abort, ok, polls);
         if (ok) {
           c12_im2col(plan, xbuf(i + 1), A1, 8 * (tile(i + 1) & 1));
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
