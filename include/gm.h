@@ -369,8 +369,9 @@ size_t gm_fit_workspace_bytes(const gm_model_desc *desc, const gm_batch *batch);
 /* Counters of one gm_fit_batch call (host memory). */
 typedef struct {
   int32_t passes;        /* fused model+Jacobian+reduction passes launched */
-  int32_t graph_reused;  /* 1: the call replayed the fit graph of the thread's previous call (every launch
-                            argument equal: same model, options, batch buffers, workspace); 0: it recorded one */
+  int32_t graph_reused;  /* 1: the call replayed one of the thread's two most recent fit graphs (every
+                            launch argument equal: same model, options, batch buffers, workspace); 0: it
+                            recorded one */
   int64_t galaxy_evals;  /* galaxies evaluated, summed over the passes */
   int64_t converged;     /* galaxies that ended GM_ST_CONVERGED */
   int64_t iters_sum;     /* iters_out summed over the galaxies */

@@ -925,11 +925,11 @@ struct FitGraphKey {
   cudaEvent_t ev[4 * kGraphIters];
 };
 
-// The calling thread's last fit graph, replayed by the next gm_fit_batch whose
-// key matches byte for byte (the same model, options, batch buffers and
-// workspace: a fit repeated on new data in the same buffers): that call skips
-// the capture and the instantiation of the graph.  `valid` is set only once a
-// fit has run the graph to its end without an error.
+// The calling thread's last two fit graphs, each replayed by a later gm_fit_batch whose
+// key matches byte for byte (the same model, options, batch buffers and workspace: a
+// fit repeated on new data in the same buffers, or alternating between two input
+// sets): that call skips the capture and the instantiation of the graph.  `valid` is
+// set only once a fit has run the graph to its end without an error.
 struct FitGraphCache {
   FitGraphKey key;
   cudaGraph_t graph = nullptr;
@@ -943,7 +943,8 @@ struct FitGraphCache {
     valid = false;
   }
 };
-thread_local FitGraphCache g_fit_graph;
+thread_local FitGraphCache g_fit_graph[2];
+thread_local int g_fit_graph_last = 0;  // the entry used most recently
 
 // A stream of the current device used only to record the fit graph (the
 // caller's stream may be the legacy default stream, which cannot capture).
@@ -1264,8 +1265,13 @@ int gm_fit_batch(const gm_model_desc* desc, const gm_batch* batch, double* param
   key.threads = sm.threads;
   GM_CUDA(cudaGetDevice(&key.dev));
   for (int e = 0; e < 4 * U; ++e) key.ev[e] = g_events[e];
-  FitGraphCache& fc = g_fit_graph;
-  const bool hit = !starve && fc.valid && std::memcmp(&fc.key, &key, sizeof(key)) == 0;
+  int slot = -1;
+  for (int i = 0; i < 2 && !starve; ++i)
+    if (g_fit_graph[i].valid && std::memcmp(&g_fit_graph[i].key, &key, sizeof(key)) == 0) slot = i;
+  const bool hit = slot >= 0;
+  if (!hit) slot = g_fit_graph_last ^ 1;  // replace the entry used least recently
+  g_fit_graph_last = slot;
+  FitGraphCache& fc = g_fit_graph[slot];
   fc.valid = false;  // until this call has run the graph without an error
   GraphGuard gg;
   if (!hit) {

@@ -1,9 +1,10 @@
-"""The fit graph kept between gm_fit_batch calls.
+"""The fit graphs kept between gm_fit_batch calls.
 
-A call whose launch arguments all equal the previous call's (same model,
-options, batch buffers and workspace) replays the previous call's CUDA graph
-instead of recording one.  The replay must be indistinguishable from a fresh
-recording: same results bit for bit, also when the buffers hold new data.
+A call whose launch arguments all equal those of one of the thread's two most
+recent calls (same model, options, batch buffers and workspace) replays that
+call's CUDA graph instead of recording one.  The replay must be
+indistinguishable from a fresh recording: same results bit for bit, also when
+the buffers hold new data.
 """
 import numpy as np
 import pytest
@@ -54,20 +55,31 @@ def test_replayed_graph_gives_the_recorded_graphs_results(gm):
     assert st2["graph_reused"] == 1
     _same(first, again)
 
-    # other options: a new graph, then the first options again (recorded afresh)
-    _, st3 = _fit(gm, f, p1, d1, gm.FitOptions(tol=1e-8, max_iter=100))
+    # other options: a second graph, kept beside the first; a third evicts the one used
+    # least recently (the second), so the first is replayed until then and recorded afresh
+    # after two more new graphs
+    opts_b = gm.FitOptions(tol=1e-8, max_iter=100)
+    opts_c = gm.FitOptions(tol=1e-7, max_iter=100)
+    _, st3 = _fit(gm, f, p1, d1, opts_b)
     assert st3["graph_reused"] == 0
     third, st4 = _fit(gm, f, p1, d1, opts)
-    assert st4["graph_reused"] == 0
+    assert st4["graph_reused"] == 1
     _same(first, third)
+    _, st5 = _fit(gm, f, p1, d1, opts_c)
+    assert st5["graph_reused"] == 0
+    _, st6 = _fit(gm, f, p1, d1, opts_b)
+    assert st6["graph_reused"] == 0
+    fourth, st7 = _fit(gm, f, p1, d1, opts)
+    assert st7["graph_reused"] == 0
+    _same(first, fourth)
 
     # new data copied into the same buffers: replayed, and equal to a fresh fitter's fit
     for dst, src in zip(d1, d2):
         if dst is not None:
             dst.copy_(src)
-    replayed, st5 = _fit(gm, f, p2, d1, opts)
-    assert st5["graph_reused"] == 1
-    fresh, st6 = _fit(gm, gm.Fitter(b2.spec, 16, b2.H, b2.W, b2.K, device=dev), p2, d2, opts)
-    assert st6["graph_reused"] == 0
+    replayed, st8 = _fit(gm, f, p2, d1, opts)
+    assert st8["graph_reused"] == 1
+    fresh, st9 = _fit(gm, gm.Fitter(b2.spec, 16, b2.H, b2.W, b2.K, device=dev), p2, d2, opts)
+    assert st9["graph_reused"] == 0
     _same(replayed, fresh)
     assert (replayed["status"] == gm.ST_CONVERGED).sum() >= 15
