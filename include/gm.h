@@ -79,7 +79,7 @@ extern "C" {
 #define GM_E_INVAL (-1)        /* bad argument (null pointer, bad size, bad descriptor) */
 #define GM_E_CUDA (-2)         /* a CUDA runtime call failed */
 #define GM_E_NOMEM (-3)        /* workspace smaller than the *_workspace_bytes() query */
-#define GM_E_UNSUPPORTED (-4)  /* valid request outside what this build handles */
+#define GM_E_UNSUPPORTED (-4)  /* valid request outside what the library handles */
 #define GM_E_TIMEOUT (-5)      /* a kernel's bounded wait for a tile load ran out (the
                                   kernel stopped instead of hanging); returned by the
                                   calls that synchronise (gm_fit_batch, gm_fit_adam,
