@@ -383,11 +383,14 @@ def test_grad_adjoint_vs_oracle_finite_differences(gm):
         assert (np.abs(grad[gi, free] + 2.0 * rg[gi]) <= bound).all(), gi
 
 
-@pytest.mark.parametrize("H,W,K", [(37, 45, 9), (7, 9, 15), (64, 33, 1)])
+@pytest.mark.parametrize("H,W,K", [(37, 45, 9), (7, 9, 15), (64, 33, 1), (96, 70, 41), (100, 45, 25)])
 def test_normal_equations_and_adjoint_at_ragged_sizes(gm, H, W, K):
     # stamps that end inside a tile, a 1x1 PSF and a PSF larger than the stamp, with 10% of
     # the pixels masked: chi^2 and d chi^2/dp of both passes, and J^T W J of the normal
-    # equations, against the oracle (5 galaxies: the last lane pair of the adjoint holds one)
+    # equations, against the oracle (5 galaxies: the last lane pair of the adjoint holds one).
+    # The two taller stamps have a tile row away from the top and bottom whose left and
+    # right tiles run by columns, skipping the taps outside the stamp (some of their warps
+    # lie wholly outside it)
     c = from_batch(synth.draw_small(seed=H * 7 + W + K, G=5, H=H, W=W, K=K), at="init")
     c.mask = (np.random.default_rng(K + 1).random((c.G, H, W)) < 0.1).astype(np.uint8)
     t = c.torch()
